@@ -1,0 +1,216 @@
+"""Python access to the FP64 CPU oracle (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's timed CPU-baseline leg may
+import this module.  It compiles `ecris_oracle.c` with gcc into a shared
+library beside it and wraps it with ctypes.  The oracle shares no code with the
+CUDA path: its inputs come from `paper_1507_03392_gb300.inputs` and nothing
+else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "ecris_oracle.c")
+LIB = os.path.join(HERE, "libecris_oracle.so")
+
+F_PUSH, F_IONIZE, F_CX, F_EIKICK, F_COULOMB, F_RECYCLE = 1, 2, 4, 8, 16, 32
+EV_WALL, EV_EXTRACT, EV_IONIZE, EV_CX, EV_COULOMB = 1, 2, 4, 8, 16
+G_CELL, G_BOUNDARY, G_IONIZE, G_CX = 1, 2, 4, 8
+QMAX_SLOTS = 64
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, FP64, OpenMP over particles)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", SRC, "-o", LIB, "-lm"]
+        subprocess.run(cmd, check=True)
+    return LIB
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("R0", ctypes.c_double), ("L", ctypes.c_double), ("r_ap", ctypes.c_double),
+        ("inlet", ctypes.c_double * 3),
+        ("B_inj", ctypes.c_double), ("B_min", ctypes.c_double), ("B_ext", ctypes.c_double),
+        ("B_hex", ctypes.c_double), ("B_ecr", ctypes.c_double),
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("qmax", ctypes.c_int32),
+        ("mass_amu", ctypes.c_double),
+        ("Te_warm", ctypes.c_double), ("Te_cold", ctypes.c_double),
+        ("n0_m3", ctypes.c_double), ("T0_eV", ctypes.c_double), ("sigma1_m2", ctypes.c_double),
+        ("E_cx_eV", ctypes.c_double), ("lnL_ii", ctypes.c_double), ("lnL_ei", ctypes.c_double),
+        ("ei_charge_power", ctypes.c_int32), ("flags", ctypes.c_uint32),
+        ("weight", ctypes.c_double), ("seed", ctypes.c_uint64), ("dt", ctypes.c_double),
+    ]
+
+
+class Tally(ctypes.Structure):
+    _fields_ = [
+        ("extracted", ctypes.c_int64 * QMAX_SLOTS),
+        ("lost", ctypes.c_int64 * QMAX_SLOTS),
+        ("ke_lost_eV", ctypes.c_double),
+        ("coulomb_pairs", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        d, i32, u32, i64, p = (ctypes.c_double, ctypes.c_int32, ctypes.c_uint32,
+                               ctypes.c_int64, ctypes.c_void_p)
+        pp = ctypes.POINTER(Params)
+        _lib.or_philox.argtypes = [p, p, p]
+        _lib.or_zmin.argtypes = [pp]
+        _lib.or_zmin.restype = d
+        _lib.or_b0.argtypes = [pp, d, p]
+        _lib.or_bfield.argtypes = [pp, d, d, d, p]
+        _lib.or_efield.argtypes = [pp, p, d, d, d, p]
+        _lib.or_lotz_rate.argtypes = [d, ctypes.c_int, d]
+        _lib.or_lotz_rate.restype = d
+        _lib.or_build_rates.argtypes = [pp, p, p, p]
+        _lib.or_setup_cells.argtypes = [pp, p, d, d, p, p, p, p, p]
+        _lib.or_boris.argtypes = [d, p, p, d, p]
+        _lib.or_emit.argtypes = [d, p, p, p, p, p]
+        _lib.or_nanbu_A.argtypes = [d]
+        _lib.or_nanbu_A.restype = d
+        _lib.or_nanbu_cos.argtypes = [d, d]
+        _lib.or_nanbu_cos.restype = d
+        _lib.or_nanbu_s.argtypes = [d, d, d, d, d, d, d]
+        _lib.or_nanbu_s.restype = d
+        _lib.or_scatter_pair.argtypes = [p, p, d, d]
+        _lib.or_step.argtypes = [pp, p, p, p, p, p, p, i64, p, p, p, p, p, p, p, p, u32, p, p,
+                                 ctypes.POINTER(Tally), p, p]
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox(ctr, key):
+    """Philox4x32-10 of a 4-word counter and 2-word key -> 4 uint32 words."""
+    c = np.asarray(ctr, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().or_philox(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def make_params(rp, dt=None) -> Params:
+    """Oracle parameter block from an `inputs.RunParams` (cm units converted to SI)."""
+    p = Params()
+    p.R0, p.L, p.r_ap = rp.R0, rp.L, rp.r_ap
+    for k in range(3):
+        p.inlet[k] = rp.inlet[k]
+    p.B_inj, p.B_min, p.B_ext, p.B_hex, p.B_ecr = rp.B_inj, rp.B_min, rp.B_ext, rp.B_hex, rp.B_ecr
+    p.nx, p.ny, p.nz, p.qmax = rp.nx, rp.ny, rp.nz, rp.species.qmax
+    p.mass_amu = rp.species.mass_amu
+    p.Te_warm, p.Te_cold = rp.Te_warm_eV, rp.Te_cold_eV
+    p.n0_m3 = rp.n0_cm3 * 1e6
+    p.T0_eV = rp.T0_eV
+    p.sigma1_m2 = rp.sigma1_cm2 * 1e-4
+    p.E_cx_eV, p.lnL_ii, p.lnL_ei = rp.E_cx_eV, rp.lnL_ii, rp.lnL_ei
+    p.ei_charge_power = rp.ei_charge_power
+    p.flags = rp.flags
+    p.weight = rp.weight
+    p.seed = rp.seed
+    p.dt = rp.dt if dt is None else dt
+    return p
+
+
+def bfield(p: Params, x, y, z):
+    out = np.zeros(3)
+    lib().or_bfield(ctypes.byref(p), float(x), float(y), float(z), _ptr(out))
+    return out
+
+
+def b0(p: Params, z):
+    out = np.zeros(3)
+    lib().or_b0(ctypes.byref(p), float(z), _ptr(out))
+    return out
+
+
+def lotz_rate(P_eV, q_outer, Te_eV):
+    return lib().or_lotz_rate(float(P_eV), int(q_outer), float(Te_eV))
+
+
+def boris(qm, E, B, dt, v):
+    v = np.array(v, dtype=np.float64)
+    lib().or_boris(float(qm), _ptr(np.asarray(E, np.float64)), _ptr(np.asarray(B, np.float64)),
+                   float(dt), _ptr(v))
+    return v
+
+
+class OracleRun:
+    """One run advanced by the oracle: parameters, per-cell data, state, tallies."""
+
+    def __init__(self, rp, state, E=None, ne_cells=None, dt=None, deposit=True):
+        self.rp = rp
+        self.p = make_params(rp, dt)
+        nc = rp.ncells
+        qmax = rp.species.qmax
+        ip, nout = rp.species.ladder()
+        self.rates = np.zeros(2 * qmax)
+        lib().or_build_rates(ctypes.byref(self.p), _ptr(np.ascontiguousarray(ip, np.float64)),
+                             _ptr(np.ascontiguousarray(nout, np.int32)), _ptr(self.rates))
+        self.ne = np.zeros(nc)
+        self.zone = np.zeros(nc, dtype=np.int32)
+        self.Bmag = np.zeros(nc)
+        self.dlx = np.zeros(nc)
+        self.dly = np.zeros(nc)
+        nec = None if ne_cells is None else np.ascontiguousarray(ne_cells, np.float32)
+        lib().or_setup_cells(ctypes.byref(self.p), _ptr(nec), rp.ne_in_cm3, rp.ne_out_cm3,
+                             _ptr(self.ne), _ptr(self.zone), _ptr(self.Bmag), _ptr(self.dlx),
+                             _ptr(self.dly))
+        self.E = np.zeros(3 * nc) if E is None else np.ascontiguousarray(E, np.float64).reshape(-1)
+        self.n = len(state["x"])
+        self.set_state(state)
+        self.status = np.zeros(self.n, dtype=np.uint32)
+        self.tally = Tally()
+        self.dep_count = np.zeros(nc, dtype=np.int64) if deposit else None
+        self.dep_charge = np.zeros(nc, dtype=np.int64) if deposit else None
+        self.events = np.zeros(self.n, dtype=np.uint8)
+        self.guard = np.zeros(self.n, dtype=np.uint8)
+        self.step_index = 0
+
+    def set_state(self, s):
+        for k in ("x", "y", "z", "vx", "vy", "vz"):
+            setattr(self, k, np.ascontiguousarray(s[k], dtype=np.float64).copy())
+        self.q = np.ascontiguousarray(s["q"], dtype=np.int32).copy()
+
+    def state(self):
+        return {k: getattr(self, k) for k in ("x", "y", "z", "vx", "vy", "vz", "q")}
+
+    def step(self, nsteps=1, accumulate_guard=False):
+        """Advance nsteps; events/guard hold the last step (or the OR over steps)."""
+        acc_ev = np.zeros(self.n, dtype=np.uint8)
+        acc_g = np.zeros(self.n, dtype=np.uint8)
+        for _ in range(nsteps):
+            lib().or_step(ctypes.byref(self.p), _ptr(self.rates), _ptr(self.ne), _ptr(self.zone),
+                          _ptr(self.dlx), _ptr(self.dly), _ptr(self.E), self.n,
+                          _ptr(self.x), _ptr(self.y), _ptr(self.z), _ptr(self.vx), _ptr(self.vy),
+                          _ptr(self.vz), _ptr(self.q), _ptr(self.status), self.step_index,
+                          _ptr(self.events), _ptr(self.guard), ctypes.byref(self.tally),
+                          _ptr(self.dep_count), _ptr(self.dep_charge))
+            self.step_index += 1
+            acc_ev |= self.events
+            acc_g |= self.guard
+        if accumulate_guard:
+            self.events_acc, self.guard_acc = acc_ev, acc_g
+        return self
+
+    def extracted(self):
+        return np.array(self.tally.extracted[: self.rp.species.qmax + 1], dtype=np.int64)
+
+    def lost(self):
+        return np.array(self.tally.lost[: self.rp.species.qmax + 1], dtype=np.int64)

@@ -1,0 +1,148 @@
+"""Pins of the oracle's ion-ion Coulomb collisions (Sec. II: Takizawa-Abe
+pairing of partners in a cell, Nanbu's scattering angle each time step,
+Coulomb logarithm 10).
+
+Nanbu's angle is defined so that <cos chi> over one step equals exp(-s); the
+pairwise rotation conserves momentum and energy exactly; the ensemble relaxes
+two temperatures at the Spitzer rate
+    1/tau = (8 sqrt(2 pi)/3) n_b Z^4 e^4 lnL / ((4 pi eps0)^2 m^2) (m/(T_a+T_b))^1.5
+(the rate NRL tabulates), which checks the magnitude of s independently.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1507_03392_gb300 import inputs as I
+
+QE = 1.602176634e-19
+AMU = 1.66053906660e-27
+EPS0 = 8.8541878128e-12
+
+
+@pytest.mark.parametrize("s", [1e-5, 1e-3, 0.05, 0.3, 1.0, 2.5, 5.5])
+def test_mean_cos_chi_is_exp_minus_s(s):
+    m = 200000
+    U = (np.arange(m) + 0.5) / m
+    c = np.array([O.lib().or_nanbu_cos(s, u) for u in U[:: max(1, m // 20000)]])
+    # midpoint rule on a sub-grid; the integrand is smooth except near U=0
+    Us = U[:: max(1, m // 20000)]
+    mean = np.trapezoid(c, Us) + c[0] * Us[0]
+    assert mean == pytest.approx(math.exp(-s), abs=2e-4)
+
+
+def test_nanbu_A_solves_its_equation():
+    for s in (1e-2, 0.1, 1.0, 3.0, 5.9):
+        A = O.lib().or_nanbu_A(s)
+        assert 1 / math.tanh(A) - 1 / A == pytest.approx(math.exp(-s), rel=1e-10)
+    assert O.lib().or_nanbu_A(1e-6) == pytest.approx(1e6, rel=1e-5)
+
+
+def test_pair_rotation_conserves_momentum_and_energy():
+    rng = np.random.default_rng(0)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    for _ in range(200):
+        va = rng.normal(0, 1000, 3)
+        vb = rng.normal(0, 1000, 3)
+        if rng.random() < 0.1:
+            vb = va.copy()
+            vb[0] -= 300.0        # relative velocity along x only (g_perp = 0)
+        cchi = rng.uniform(-1, 1)
+        eps = rng.uniform(0, 2 * math.pi)
+        a, b = va.copy(), vb.copy()
+        O.lib().or_scatter_pair(ptr(a), ptr(b), cchi, eps)
+        assert np.allclose(a + b, va + vb, rtol=0, atol=1e-9)
+        assert a @ a + b @ b == pytest.approx(va @ va + vb @ vb, rel=1e-12)
+        g0, g1 = va - vb, a - b
+        assert np.linalg.norm(g1) == pytest.approx(np.linalg.norm(g0), rel=1e-12)
+        assert g0 @ g1 / (g0 @ g0) == pytest.approx(cchi, abs=1e-12)
+
+
+def _cell_params(**kw):
+    base = dict(flags=I.F_COULOMB, nx=8, ny=8, nz=8, weight=1e8, dt=1e-8)
+    base.update(kw)
+    return I.RunParams(**base)
+
+
+def _grouped_state(rp, cells, per_cell, q, rng, T_eV=1.0):
+    """per_cell ions at the centres of the listed cells, Maxwellian at T_eV."""
+    dx, dy, dz = 2 * rp.R0 / rp.nx, 2 * rp.R0 / rp.ny, rp.L / rp.nz
+    xs, ys, zs = [], [], []
+    for c, m in zip(cells, per_cell):
+        ix, iy, iz = c % rp.nx, (c // rp.nx) % rp.ny, c // (rp.nx * rp.ny)
+        xs += [-rp.R0 + (ix + 0.5) * dx] * m
+        ys += [-rp.R0 + (iy + 0.5) * dy] * m
+        zs += [(iz + 0.5) * dz] * m
+    n = len(xs)
+    sig = math.sqrt(T_eV * QE / (rp.species.mass_amu * AMU))
+    v = rng.normal(0, sig, (3, n))
+    return {"x": np.array(xs), "y": np.array(ys), "z": np.array(zs),
+            "vx": v[0], "vy": v[1], "vz": v[2], "q": np.asarray(q, dtype=np.int32)}
+
+
+def test_coulomb_step_conserves_per_cell_and_pairs_as_stated():
+    rp = _cell_params()
+    rng = np.random.default_rng(1)
+    cells = [100, 101, 250, 333, 400]
+    per = [1, 2, 5, 8, 11]
+    n = sum(per)
+    q = rng.integers(1, 9, n)
+    st = _grouped_state(rp, cells, per, q, rng)
+    st["q"][3] = 0                       # an atom in cell 250 takes no part
+    r = O.OracleRun(rp, st, deposit=False)
+    cell_of = np.repeat(cells, per)
+    p0 = {c: (np.array([r.vx, r.vy, r.vz])[:, cell_of == c] * 1).copy() for c in cells}
+    r.step(1)
+    v1 = np.array([r.vx, r.vy, r.vz])
+    for c in cells:
+        a, b = p0[c], v1[:, cell_of == c]
+        assert np.allclose(a.sum(axis=1), b.sum(axis=1), rtol=0, atol=1e-8)
+        assert (a ** 2).sum() == pytest.approx((b ** 2).sum(), rel=1e-12)
+    # brute force of the pairing rule: ions of a cell sorted by (stream-1 word 0,
+    # pid); an odd count puts the first three in a triplet; a lone ion is left alone
+    touched = (r.events & O.EV_COULOMB) != 0
+    start = 0
+    for c, m in zip(cells, per):
+        pids = [i for i in range(start, start + m) if st["q"][i] >= 1]
+        start += m
+        if len(pids) < 2:
+            assert not touched[pids].any()
+        else:
+            assert touched[pids].all()
+    assert not touched[3]
+    assert r.tally.coulomb_pairs == sum(
+        (m // 2) + (2 if m % 2 and m >= 3 else 0)
+        for m in [len([i for i in range(s0, s0 + mm) if st["q"][i] >= 1])
+                  for s0, mm in zip(np.cumsum([0] + per[:-1]), per)])
+
+
+@pytest.mark.slow
+def test_two_temperature_relaxation_matches_spitzer_rate():
+    rp = _cell_params(weight=2e6, dt=2e-6)
+    rng = np.random.default_rng(7)
+    n = 20000
+    c0 = 4 * 64 + 4 * 8 + 4
+    st = _grouped_state(rp, [c0], [n], np.ones(n), rng, T_eV=1.0)
+    M = rp.species.mass_amu * AMU
+    hot = np.arange(n) < n // 2
+    Ta0, Tb0 = 3.0, 0.5
+    for comp in ("vx", "vy", "vz"):
+        st[comp][hot] *= math.sqrt(Ta0)
+        st[comp][~hot] *= math.sqrt(Tb0)
+    r = O.OracleRun(rp, st, deposit=False)
+    vcell = (2 * rp.R0 / rp.nx) * (2 * rp.R0 / rp.ny) * (rp.L / rp.nz)
+    n_b = rp.weight * (n // 2) / vcell
+    temp = lambda m: M * (r.vx[m] ** 2 + r.vy[m] ** 2 + r.vz[m] ** 2).mean() / 3 / QE
+    Ta, Tb = temp(hot), temp(~hot)
+    rate = (8 * math.sqrt(2 * math.pi) / 3) * n_b * QE ** 4 * rp.lnL_ii / ((4 * math.pi * EPS0) ** 2 * M ** 2) \
+        * (M / ((Ta + Tb) * QE)) ** 1.5
+    # dT_a/dt = rate (T_b - T_a) and symmetrically, so T_a - T_b decays at 2 rate
+    steps = int(0.3 / (2 * rate * rp.dt))
+    d0 = Ta - Tb
+    r.step(steps)
+    d1 = temp(hot) - temp(~hot)
+    got = -math.log(d1 / d0) / (steps * rp.dt)
+    assert got == pytest.approx(2 * rate, rel=0.12)
+    assert temp(hot) + temp(~hot) == pytest.approx(Ta + Tb, rel=1e-9)
