@@ -1,0 +1,341 @@
+"""Throughput of the ECRIS ion time step on GB300 (ion macroparticle-steps/s).
+
+Workload: the scaled plain run -- argon, 4e6 macroparticles (75 % atoms, 25 %
+ions), 64x64x128 mesh, n_e per zone cell log-uniform 1e11-1e12 cm^-3, neutral
+density 1e10 cm^-3, every process of the step on.  Inputs are synthetic
+(seeded generators); a "step" is one time step of the whole hot path over all
+particles.  L2 is flushed (a 512 MB write) between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank runs an independent
+replica with its own seed: runs do not exchange data, so there is no
+collective on the data path ("weak" scaling).  `--impl reference` times the
+FP64 CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALGO_BYTES_STEP_KERNEL = 56   # read + write of x,y,z,vx,vy,vz (f32) and meta (u32)
+ALGO_BYTES_CKEY = 4           # Coulomb cell key written by the step kernel when collisions are on
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("step_kernel.cu", "ecris_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1507_03392_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(n_particles):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    scaled to n particles; None if the kernel changed since it was measured."""
+    path = os.path.join(ROOT, "profiles", "k_step_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_sha") != kernel_source_hash():
+        return None
+    return d["dram_bytes_per_particle"] * n_particles
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(rank, n=None):
+    from paper_1507_03392_gb300 import inputs as I
+    wl = I.config_scaled(seed=2 + rank)
+    wl.params.flags = I.F_ALL_NO_COULOMB   # collisions kernel not built yet
+    if n is not None:
+        wl.n = n
+    return wl
+
+
+def cpu_baseline(wl, target_s=12.0, sample=200_000):
+    """The oracle as it stands, on the host cores, over a bounded sample."""
+    ncores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
+    from oracle import oracle as O
+    from paper_1507_03392_gb300 import inputs as I
+    st = I.make_particles(wl)
+    m = min(sample, wl.n)
+    sub = {k: v[:m] for k, v in st.items()}
+    orc = O.OracleRun(wl.params, sub, ne_cells=I.make_ne_cells(wl))
+    t0 = time.perf_counter()
+    orc.step(1)
+    one = time.perf_counter() - t0
+    steps = max(1, min(200, int(target_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    orc.step(steps)
+    el = time.perf_counter() - t0
+    return {"value": m * steps / el, "unit": "ion-steps/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle",
+            "sample": f"first {m} of the {wl.n} particles of the workload, {steps} steps, FP64 C oracle"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    wl = make_workload(0)
+    ncores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
+    from oracle import oracle as O
+    from paper_1507_03392_gb300 import inputs as I
+    O.build()
+    st = I.make_particles(wl)
+    m = min(args.ref_sample, wl.n)
+    sub = {k: v[:m] for k, v in st.items()}
+    orc = O.OracleRun(wl.params, sub, ne_cells=I.make_ne_cells(wl))
+    for _ in range(args.warmup):
+        orc.step(1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.step(1)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = m * args.steps / total
+    cores = int(os.environ["OMP_NUM_THREADS"])
+    line = {
+        "impl": "reference", "metric": "ion macroparticle-steps/s", "value": value,
+        "unit": "ion-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(wl, coulomb=bool(wl.params.flags & I.F_COULOMB)),
+        "cpu_baseline": {"value": value, "unit": "ion-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {m} of the {wl.n} particles, one time step per step"},
+        "e2e": {"value": value, "unit": "ion-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(wl, coulomb):
+    p = wl.params
+    return {"workload": wl.name, "species": p.species.name, "particles": wl.n,
+            "mesh": [p.nx, p.ny, p.nz], "dt_s": p.dt, "n0_cm3": p.n0_cm3,
+            "ne_zone_cm3": "log-uniform 1e11-1e12 per cell", "coulomb": coulomb,
+            "l2": "flushed between timed steps (512 MB write)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=None, help="override the particle count")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=50_000)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = env_int("RANK", 0)
+    world = env_int("WORLD_SIZE", 1)
+    local = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1507_03392_gb300 import ecris as E
+    from paper_1507_03392_gb300 import inputs as I
+
+    wl = make_workload(rank, args.n)
+    rp = wl.params
+    coulomb = bool(rp.flags & I.F_COULOMB)
+    st = I.make_particles(wl)
+    ne_cells = I.make_ne_cells(wl)
+    # a dedicated stream: torch's legacy default stream has handle 0, which the
+    # library would read as "create your own"
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    run = E.Run(rp, ne_cells=ne_cells, device=local, stream=stream.cuda_stream)
+    run.load(st)
+    n = wl.n
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    run.step(args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    run.set_profiling(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        run.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    prof = run.profile()
+    run.set_profiling(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    total_ms = float(tmax.item())
+    value = world * n * args.steps / (total_ms * 1e-3)
+    launches = prof["step_launches"] + prof["coulomb_launches"] + prof["other_launches"]
+
+    # roofline of the dominant kernel (the fused step kernel)
+    k_ms = prof["step_ms"] / max(1, prof["step_launches"])
+    algo = n * (ALGO_BYTES_STEP_KERNEL + (ALGO_BYTES_CKEY if coulomb else 0))
+    achieved = algo / (k_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    roofline = {"bound": "hbm", "kernel": "k_step", "achieved": achieved, "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic(n), "algorithmic_bytes_per_launch": algo,
+                "kernel_ms": k_ms,
+                "share_of_step": prof["step_ms"] / max(1e-9, prof["step_ms"] + prof["coulomb_ms"] + prof["other_ms"])}
+
+    # end to end through the public API with host buffers: H2D of the state,
+    # one step, D2H of the diagnostics, every iteration
+    pinned = {}
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        t = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        t.numpy()[:] = st[k]
+        pinned[k] = t.numpy()
+    tq = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    tq.numpy()[:] = st["q"]
+    pinned["q"] = tq.numpy()
+    e2e_times = []
+    for i in range(args.e2e_steps + 2):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run.load(pinned)
+        run.step(1)
+        d = run.diag()
+        t1 = time.perf_counter()
+        if i >= 2:
+            e2e_times.append(t1 - t0)
+    e2e_t = torch.tensor([sum(e2e_times)], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * n * len(e2e_times) / float(e2e_t.item())
+    h2d = n * (6 * 4 + 1)
+    d2h = (132 + 64) * 8
+
+    line = {
+        "metric": "ion macroparticle-steps/s", "value": value, "unit": "ion-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(wl, coulomb),
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": "ion-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "note": "per iteration: ecris_load_ions from pinned host memory, ecris_step(1), ecris_diag"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "step_ms_median": statistics.median(step_ms),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    run.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,229 @@
+/*
+ * ecris.h - C ABI of the GB300 (sm_103a) ECRIS ion time step.
+ *
+ * The library advances the macroparticles of the particle-in-cell /
+ * Monte-Carlo-collision model of Mironov et al., "Numerical model of Electron
+ * Cyclotron Resonance Ion Source" (arXiv:1507.03392, Sec. II).  One time step
+ * of one run is, in the paper's order:
+ *   push        Boris push of ions in the static minimum-B field (solenoid
+ *               mirror plus the printed analytic hexapole) and the electric
+ *               field interpolated from a cell-centred 3-D grid; atoms move in
+ *               straight lines (Sec. II, "standard particle-in-cell technique");
+ *   MCC         step-wise electron-impact ionisation Q -> Q+1 from the cell's
+ *               electron density and temperature, charge exchange with the
+ *               neutral background, the electron-ion heating kick (equation for
+ *               D with the delta stencil), and Takizawa-Abe / Nanbu ion-ion
+ *               Coulomb collisions (Sec. II, collision block);
+ *   boundaries  neutralisation and cosine-law re-emission at the walls;
+ *               extraction through the round aperture at z = L with
+ *               reinjection at the gas inlet, so N stays constant (Sec. II);
+ *   deposition  nearest-grid-point count and charge per cell (Sec. II: the
+ *               electron density equals the ion charge density).
+ *
+ * Conventions for every entry point:
+ *   - Units are SI (m, s, m/s, T, V/m) except where a name says cm^-3, cm^2
+ *     or eV.  The injection flange is at z = 0, the extraction flange at z = L;
+ *     the mesh spans [-R0, R0] x [-R0, R0] x [0, L] with cell index
+ *     c = (iz * ny + iy) * nx + ix (x fastest).
+ *   - Every call returns an ecris_status; nothing is thrown or aborted across
+ *     the ABI.  ecris_last_error() describes the last failure on a context.
+ *   - Inputs are validated before any device work; an invalid argument leaves
+ *     the context unchanged and returns ECRIS_EINVAL.
+ *   - The library owns all device memory it allocates (stream-ordered, on the
+ *     context's stream).  Pointers passed in are only read during the call
+ *     (host memory) or until the call's stream work completes (device memory);
+ *     the caller keeps ownership.
+ *   - Calls on one context must not run concurrently from several host
+ *     threads.  Device work is ordered on the context's stream; calls that
+ *     return data to the host synchronise that stream.
+ */
+#ifndef ECRIS_H
+#define ECRIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ecris_ctx ecris_ctx;
+
+typedef enum {
+    ECRIS_OK = 0,
+    ECRIS_EINVAL = 1,   /* invalid argument; nothing was changed */
+    ECRIS_ENOMEM = 2,   /* device or host allocation failed */
+    ECRIS_ECUDA = 3,    /* a CUDA call failed; the message names it */
+    ECRIS_ETIMEOUT = 4, /* a bounded device wait ran out */
+    ECRIS_ESTATE = 5    /* call out of order (e.g. step before load), or the
+                           context is unusable after an earlier device error */
+} ecris_status;
+
+/* Process switches (ecris_mcc.flags). */
+#define ECRIS_F_PUSH (1u << 0)    /* move particles (off: positions frozen, 0-D tests) */
+#define ECRIS_F_IONIZE (1u << 1)  /* electron-impact ionisation Q -> Q+1 */
+#define ECRIS_F_CX (1u << 2)      /* charge exchange with the neutral background */
+#define ECRIS_F_EIKICK (1u << 3)  /* electron-ion heating / diffusion kick */
+#define ECRIS_F_COULOMB (1u << 4) /* ion-ion Coulomb collisions */
+#define ECRIS_F_RECYCLE (1u << 5) /* re-emit at walls, reinject extracted particles;
+                                     off: leavers are frozen and counted once */
+
+/* Per-particle state word (ecris_get_state meta): bits 0-7 charge state Q,
+ * bits 8-15 events of the last step, bits 16-23 status. */
+#define ECRIS_META_Q(m) ((m) & 0xFFu)
+#define ECRIS_EV_WALL (1u << 8)     /* hit the wall (neutralised, re-emitted) */
+#define ECRIS_EV_EXTRACT (1u << 9)  /* left through the aperture (reinjected) */
+#define ECRIS_EV_IONIZE (1u << 10)  /* ionised this step */
+#define ECRIS_EV_CX (1u << 11)      /* charge exchange this step */
+#define ECRIS_EV_COULOMB (1u << 12) /* took part in a Coulomb collision */
+#define ECRIS_ST_FROZEN (1u << 16)  /* left the chamber with recycling off */
+
+/* Chamber geometry (Sec. II, Table I shapes). */
+typedef struct {
+    double R0;       /* chamber radius, m (> r_ap) */
+    double L;        /* chamber length, m */
+    double r_ap;     /* extraction aperture radius, m (> 0) */
+    double inlet[3]; /* gas inlet point where extracted particles are reinjected, m;
+                        must lie inside the chamber */
+} ecris_geometry;
+
+/* Static magnetic field (Sec. II, Fig. 3 extremes and the hexapole equations).
+ * The solenoid maps of the paper are not available: the on-axis profile is a
+ * synthetic mirror through B_inj (z=0), B_min (at z_m) and B_ext (z=L) made of
+ * raised-cosine halves with continuous second derivative, extended off axis
+ * by the paraxial expansion B_r = -(r/2) B0', B_z = B0 - (r^2/4) B0''.  The
+ * hexapole adds B_x = B_H sin(2 theta) R^2/R0^2, B_y = B_H cos(2 theta) R^2/R0^2. */
+typedef struct {
+    double B_inj, B_min, B_ext; /* T; B_inj > B_min >= 0, B_ext > B_min */
+    double B_hex;               /* hexapole field at r = R0, T */
+    double B_ecr;               /* resonance field, T (0.5 T at 14 GHz) */
+} ecris_bfield;
+
+/* Mesh and electron background (Sec. II: 3-D Cartesian mesh; warm electrons
+ * T_ew inside the ECR zone, cold T_ec outside; n_e per cell).  A cell is in
+ * the zone when |B| at its centre is below B_ecr. */
+typedef struct {
+    int32_t nx, ny, nz;        /* cells, each >= 2 */
+    const float* E;            /* host, 3*Nc floats (Ex,Ey,Ez per cell centre, V/m),
+                                  or NULL for E = 0 (the paper's case) */
+    double ne_in_cm3;          /* n_e inside the zone, cm^-3 (when ne_in_cells == NULL) */
+    const float* ne_in_cells;  /* host, Nc floats, cm^-3: per-cell n_e used inside the
+                                  zone; may be NULL */
+    double ne_out_cm3;         /* n_e outside the zone, cm^-3 */
+    double Te_warm_eV;         /* T_ew, eV (> 0) */
+    double Te_cold_eV;         /* T_ec, eV (> 0) */
+} ecris_grid;
+
+/* Ion species.  The paper's rate datasets [20-23] are not available: the
+ * library builds the rate of Q -> Q+1 as the Maxwellian average of the
+ * single-term Lotz cross section from the ionisation potential P_Q and the
+ * number of outer electrons q_Q. */
+typedef struct {
+    double mass_amu;           /* > 0 */
+    int32_t qmax;              /* highest charge state, 1..63 */
+    const double* ip_eV;       /* host, qmax values: P_Q for Q = 0..qmax-1 (> 0) */
+    const int32_t* n_outer;    /* host, qmax values: q_Q >= 1 */
+} ecris_species;
+
+/* Collisions and switches (Sec. II collision block). */
+typedef struct {
+    double n0_cm3;          /* neutral background density for charge exchange, cm^-3 */
+    double T0_eV;           /* gas / wall temperature, eV (0.025-0.026) */
+    double sigma1_cm2;      /* charge-exchange cross section of Q=1 (scaled by Q), cm^2 */
+    double E_cx_eV;         /* charge-exchange energy release (10 eV), half to the ion */
+    double lnL_ii;          /* ion-ion Coulomb logarithm (10) */
+    double lnL_ei;          /* electron-ion Coulomb logarithm (17) */
+    int32_t ei_charge_power;/* 1 or 2: power of Q in the kick's D^2 (2 = the text's
+                               quadratic dependence) */
+    uint32_t flags;         /* ECRIS_F_* */
+} ecris_mcc;
+
+/* Diagnostics filled by ecris_diag.  Arrays are caller-owned; each array
+ * pointer may be NULL to skip it; lengths are stated per field. */
+typedef struct {
+    int32_t qmax;             /* out: the run's qmax */
+    uint64_t steps;           /* out: steps since ecris_load_ions */
+    double time_s;            /* out: simulated time since load (sum of dt) */
+    int64_t* extracted;       /* qmax+1: particles that left through the aperture, per Q */
+    int64_t* lost;            /* qmax+1: wall hits, per Q at the hit */
+    int64_t* alive_by_q;      /* qmax+1: current census of particles in the chamber */
+    double* current_A;        /* qmax+1: extracted current Q e w count / time (Sec. III) */
+    double ke_lost_eV;        /* out: kinetic energy of ions (Q >= 1) that left, per
+                                 macroparticle, summed (multiply by the weight for real ions) */
+    double power_W;           /* out: power balance of Sec. II over the time since load:
+                                 w * sum over ions that left of (kinetic + ionisation
+                                 potential energy + Q * 3/2 T_ew) / time */
+    int64_t coulomb_collisions; /* out: pair collisions performed */
+    uint64_t* cell_count;     /* Nc: time-summed NGP particle counts per cell */
+    uint64_t* cell_charge;    /* Nc: time-summed NGP charge (sum of Q) per cell */
+} ecris_diag_out;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to order all work on, or NULL to let the library create its own.  On
+ * success *out receives the context. */
+ecris_status ecris_create(ecris_ctx** out, int device, void* cuda_stream);
+
+/* Release the context and all device memory it owns (synchronises its stream). */
+void ecris_destroy(ecris_ctx* ctx);
+
+/* Message for the last failure on ctx (empty string if none); valid until the
+ * next call on ctx.  ctx may be NULL (then describes the last ecris_create
+ * failure on this thread). */
+const char* ecris_last_error(const ecris_ctx* ctx);
+
+/* Per-run setup (Sec. II model inputs): validates the inputs, builds in FP64
+ * on the host the ionisation rates for T_ew and T_ec, the ECR zone, n_e and the
+ * delta vector of every cell (printed 3x3 stencil scaled by
+ * R_L = 2.38e-6 sqrt(T_e)/(B dX)), and copies them and the E grid to the device.
+ * Must precede ecris_load_ions; calling it again replaces the fields and
+ * requires a new ecris_load_ions. */
+ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const ecris_bfield* bf,
+                               const ecris_grid* grid, const ecris_species* sp,
+                               const ecris_mcc* mcc);
+
+/* Load n macroparticles (Sec. II: position, velocity, charge state, weight).
+ * xyzv[0..5] point to n floats each: x, y, z (m), vx, vy, vz (m/s); q to n
+ * bytes (Q, 0 = atom, <= qmax).  Host pointers when src_is_device == 0,
+ * device pointers otherwise.  Positions must lie inside the chamber.
+ * weight: real particles per macroparticle (> 0).  seed: key of the
+ * counter-based random numbers (Philox4x32-10 with counter (particle, 0,
+ * 4*step + stream, 0)).  Copies the data; resets tallies, deposit grids and the
+ * step counter.  n may be 0.  n * max(qmax, 1) must stay below 2^32. */
+ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6], const uint8_t* q,
+                             double weight, uint64_t seed, int src_is_device);
+
+/* Advance nsteps time steps of length dt (s, > 0).  Asynchronous on the
+ * context's stream.  The total step count since load must stay below 2^30. */
+ecris_status ecris_step(ecris_ctx* ctx, uint32_t nsteps, double dt);
+
+/* Copy the diagnostics of the run to caller memory (synchronises). */
+ecris_status ecris_diag(ecris_ctx* ctx, ecris_diag_out* out);
+
+/* Copy the particle state out: xyzv[0..5] n floats each, meta n words (see
+ * ECRIS_META_Q / ECRIS_EV_* / ECRIS_ST_*), any pointer may be NULL.  Host
+ * pointers when dst_is_device == 0 (synchronises), device pointers otherwise
+ * (ordered on the context's stream). */
+ecris_status ecris_get_state(ecris_ctx* ctx, float* const xyzv[6], uint32_t* meta, int dst_is_device);
+
+/* Kernel timing (tracing aid, not part of the paper's model).  When enabled,
+ * every kernel launch of ecris_step on the context's stream is bracketed by
+ * CUDA events; ecris_get_profile synchronises and reports, per kernel kind,
+ * the number of launches and their summed device time since the last reset. */
+typedef struct {
+    int64_t step_launches;     /* fused push/MCC/boundary/deposit kernel */
+    double step_ms;
+    int64_t coulomb_launches;  /* ion-ion collision kernels (binning, pairing) */
+    double coulomb_ms;
+    int64_t other_launches;    /* deposit fold and bookkeeping kernels */
+    double other_ms;
+} ecris_profile;
+
+/* enable != 0 turns timing on (and resets the counters), 0 turns it off */
+ecris_status ecris_set_profiling(ecris_ctx* ctx, int enable);
+ecris_status ecris_get_profile(ecris_ctx* ctx, ecris_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ECRIS_H */

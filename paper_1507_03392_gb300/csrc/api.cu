@@ -1,0 +1,858 @@
+// Host side of the C ABI declared in include/ecris.h: validation, FP64 run
+// setup (rates, ECR zone, electron density and delta per cell), device memory
+// (stream-ordered, owned by the context), kernel launches and diagnostics.
+//
+// Model: Mironov et al., arXiv:1507.03392, Sec. II.  The FP64 set-up here is
+// written independently of any test oracle: the rate of Q -> Q+1 uses the
+// closed form of the Maxwellian-averaged single-term Lotz cross section,
+//   k = sqrt(8 e / (pi m_e)) a q E1(P/T) / ((P/T) T^1.5),  a = 4.5e-14 cm^2 eV^2,
+// with E1 from its power series (x <= 1) and continued fraction (x > 1).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ecris.h"
+#include "ecris_internal.cuh"
+
+using namespace ecris;
+
+namespace {
+
+constexpr double kE = 1.602176634e-19;       // C
+constexpr double kAmu = 1.66053906660e-27;   // kg
+constexpr double kMe = 9.1093837015e-31;     // kg
+constexpr double kEps0 = 8.8541878128e-12;   // F/m
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kLotzA = 4.5e-18;           // m^2 eV^2
+constexpr uint32_t kMaxSteps = 1u << 30;     // RNG counter word 2 holds 4*step + stream
+
+thread_local std::string g_create_error;
+
+// Exponential integral E1(x), x > 0 (Abramowitz & Stegun 5.1.11 and 5.1.22).
+double expint_e1(double x)
+{
+    if (x <= 1.0) {
+        const double euler = 0.57721566490153286061;
+        double sum = 0.0, term = 1.0;
+        for (int k = 1; k < 200; ++k) {
+            term *= -x / k;                 // (-x)^k / k!
+            const double add = term / k;
+            sum += add;
+            if (std::fabs(add) < 1e-18 * std::fabs(sum)) break;
+        }
+        return -euler - std::log(x) - sum;
+    }
+    // modified Lentz evaluation of E1(x) = e^-x / (x + 1 - 1^2/(x + 3 - 2^2/(x + 5 - ...)))
+    const double tiny = 1e-300;
+    double b = x + 1.0, c = 1.0 / tiny, d = 1.0 / b, h = d;
+    for (int i = 1; i < 1000; ++i) {
+        const double a = -(double)i * i;
+        b += 2.0;
+        d = 1.0 / (a * d + b);
+        c = b + a / c;
+        const double del = c * d;
+        h *= del;
+        if (std::fabs(del - 1.0) < 1e-16) break;
+    }
+    return h * std::exp(-x);
+}
+
+// Maxwellian-averaged Lotz rate, m^3/s
+double lotz_rate(double P_eV, int q, double Te_eV)
+{
+    const double x = P_eV / Te_eV;
+    if (x > 700.0) return 0.0;
+    return std::sqrt(8.0 * kE / (kPi * kMe)) * kLotzA * q * expint_e1(x) / (x * std::pow(Te_eV, 1.5));
+}
+
+// Nanbu's A(s): root of coth(A) - 1/A = exp(-s), by bisection on ln A in FP64.
+// L(A) = coth A - 1/A is evaluated from its series for small A.
+double nanbu_A_host(double s)
+{
+    const double y = std::exp(-s);
+    auto L = [](double A) {
+        if (A < 1e-3) return A / 3.0 - A * A * A / 45.0;
+        return 1.0 / std::tanh(A) - 1.0 / A;
+    };
+    double lo = std::log(1e-12), hi = std::log(2.0 / (-std::expm1(-s)) + 10.0);
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (L(std::exp(mid)) < y) lo = mid; else hi = mid;
+    }
+    return std::exp(0.5 * (lo + hi));
+}
+
+struct HostRun {
+    ecris_geometry geo;
+    ecris_bfield bf;
+    int nx, ny, nz;
+    double ne_in, ne_out, Te_w, Te_c;
+    double mass_amu;
+    int qmax;
+    std::vector<double> ip;
+    std::vector<int> nout;
+    std::vector<double> rate[2];   // m^3/s per Q, zone 0 cold, 1 warm
+    ecris_mcc mcc;
+    double zm;
+};
+
+// synthetic on-axis mirror and its first two derivatives
+void b0_host(const HostRun& h, double z, double& b0, double& b1, double& b2)
+{
+    const double bmin = h.bf.B_min;
+    if (z <= h.zm) {
+        const double a = 0.5 * (h.bf.B_inj - bmin), k = kPi / h.zm;
+        b0 = bmin + a * (1.0 + std::cos(k * z));
+        b1 = -a * k * std::sin(k * z);
+        b2 = -a * k * k * std::cos(k * z);
+    } else {
+        const double a = 0.5 * (h.bf.B_ext - bmin), k = kPi / (h.geo.L - h.zm);
+        b0 = bmin + a * (1.0 - std::cos(k * (z - h.zm)));
+        b1 = a * k * std::sin(k * (z - h.zm));
+        b2 = a * k * k * std::cos(k * (z - h.zm));
+    }
+}
+
+double bmag_host(const HostRun& h, double x, double y, double z)
+{
+    double b0, b1, b2;
+    b0_host(h, z, b0, b1, b2);
+    const double hc = h.bf.B_hex / (h.geo.R0 * h.geo.R0);
+    const double Bx = -0.5 * x * b1 + hc * 2.0 * x * y;
+    const double By = -0.5 * y * b1 + hc * (x * x - y * y);
+    const double Bz = b0 - 0.25 * (x * x + y * y) * b2;
+    return std::sqrt(Bx * Bx + By * By + Bz * Bz);
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+}  // namespace
+
+struct ecris_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sm_count = 0;
+    int step_grid = 0;
+    std::string err;
+    bool failed = false;
+
+    bool have_fields = false;
+    HostRun h;
+    float4* d_cell = nullptr;
+    float4* d_E = nullptr;
+    float* d_kdt = nullptr;
+    float* d_nanbu = nullptr;
+
+    bool have_ions = false;     // device buffers allocated
+    bool loaded = false;        // a valid ensemble is loaded
+    size_t cap = 0, cap_cells = 0;
+    size_t n = 0, n4 = 0;
+    std::vector<uint2> tiles_h;
+    uint8_t* d_q8 = nullptr;
+    unsigned int* d_bad = nullptr;
+    uint32_t* d_crank = nullptr;
+    uint32_t* d_ccount = nullptr;
+    uint32_t* d_coff = nullptr;
+    uint32_t* d_cblk = nullptr;
+    unsigned long long* d_ckeys = nullptr;
+    uint32_t* d_occ = nullptr;
+    uint32_t* d_occ_n = nullptr;
+    int collide_grid = 0;
+    float* d_soa[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint32_t* d_meta = nullptr;
+    uint32_t* d_ckey = nullptr;
+    unsigned long long* d_dep = nullptr;
+    unsigned long long* d_count = nullptr;
+    unsigned long long* d_charge = nullptr;
+    unsigned long long* d_tally = nullptr;
+    unsigned long long* d_census = nullptr;
+    uint32_t* d_step = nullptr;
+    unsigned int* d_ticket = nullptr;
+    RunDev* d_run = nullptr;
+    uint2* d_tiles = nullptr;
+    uint32_t ntiles = 0;
+    RunDev* h_run = nullptr;    // pinned staging copy of the parameter block
+    float* h_kdt = nullptr;     // pinned staging copy of the rate table
+    double weight = 0.0;
+    uint64_t seed = 0;
+    uint64_t steps_done = 0;
+    double time_s = 0.0;
+    double dt_loaded = -1.0;
+    uint32_t fold_every = 1, since_fold = 0;
+
+    // kernel timing (ecris_set_profiling)
+    bool prof = false;
+    struct Timed { int kind; int kernels; cudaEvent_t a, b; };
+    std::vector<Timed> pending;
+    std::vector<cudaEvent_t> event_pool;
+    int64_t launches[3] = {0, 0, 0};
+    double ms[3] = {0.0, 0.0, 0.0};
+};
+
+namespace {
+
+ecris_status fail(ecris_ctx* c, ecris_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+    return st;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            ctx->failed = true;                                                           \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? ECRIS_ENOMEM : ECRIS_ECUDA, \
+                        "%s: %s", #call, cudaGetErrorString(e_));                         \
+        }                                                                                 \
+    } while (0)
+
+enum { kKindStep = 0, kKindCoulomb = 1, kKindOther = 2 };
+
+cudaEvent_t take_event(ecris_ctx* ctx)
+{
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// launch `fn` on the context stream; with profiling on, bracket it by events
+template <class F>
+cudaError_t timed(ecris_ctx* ctx, int kind, F fn, int kernels = 1)
+{
+    if (!ctx->prof) return fn();
+    cudaEvent_t a = take_event(ctx), b = take_event(ctx);
+    if (!a || !b) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaEventRecord(a, ctx->stream);
+    if (e == cudaSuccess) e = fn();
+    if (e == cudaSuccess) e = cudaEventRecord(b, ctx->stream);
+    ctx->pending.push_back({kind, kernels, a, b});
+    return e;
+}
+
+cudaError_t collect_profile(ecris_ctx* ctx)
+{
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return e;
+    for (auto& t : ctx->pending) {
+        float ms = 0.0f;
+        e = cudaEventElapsedTime(&ms, t.a, t.b);
+        if (e != cudaSuccess) return e;
+        ctx->launches[t.kind] += t.kernels;
+        ctx->ms[t.kind] += ms;
+        ctx->event_pool.push_back(t.a);
+        ctx->event_pool.push_back(t.b);
+    }
+    ctx->pending.clear();
+    return cudaSuccess;
+}
+
+template <class T>
+void free_async(ecris_ctx* ctx, T*& p)
+{
+    if (p) cudaFreeAsync(p, ctx->stream);
+    p = nullptr;
+}
+
+void free_ions(ecris_ctx* ctx)
+{
+    for (auto& p : ctx->d_soa) free_async(ctx, p);
+    free_async(ctx, ctx->d_meta);
+    free_async(ctx, ctx->d_ckey);
+    free_async(ctx, ctx->d_dep);
+    free_async(ctx, ctx->d_count);
+    free_async(ctx, ctx->d_charge);
+    free_async(ctx, ctx->d_tally);
+    free_async(ctx, ctx->d_census);
+    free_async(ctx, ctx->d_step);
+    free_async(ctx, ctx->d_ticket);
+    free_async(ctx, ctx->d_run);
+    free_async(ctx, ctx->d_tiles);
+    free_async(ctx, ctx->d_q8);
+    free_async(ctx, ctx->d_bad);
+    free_async(ctx, ctx->d_crank);
+    free_async(ctx, ctx->d_ccount);
+    free_async(ctx, ctx->d_coff);
+    free_async(ctx, ctx->d_cblk);
+    free_async(ctx, ctx->d_ckeys);
+    free_async(ctx, ctx->d_occ);
+    free_async(ctx, ctx->d_occ_n);
+    ctx->have_ions = false;
+    ctx->loaded = false;
+    ctx->cap = ctx->cap_cells = 0;
+}
+
+void free_fields(ecris_ctx* ctx)
+{
+    free_async(ctx, ctx->d_cell);
+    free_async(ctx, ctx->d_E);
+    free_async(ctx, ctx->d_kdt);
+    free_async(ctx, ctx->d_nanbu);
+    ctx->have_fields = false;
+}
+
+// FP32 kernel constants of the run for time step dt (built in FP64)
+void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
+{
+    const HostRun& h = ctx->h;
+    const double M = h.mass_amu * kAmu;
+    std::memset(&R, 0, sizeof R);
+    R.R0 = (float)h.geo.R0;
+    R.R0sq = (float)(h.geo.R0 * h.geo.R0);
+    R.L = (float)h.geo.L;
+    R.r_ap_sq = (float)(h.geo.r_ap * h.geo.r_ap);
+    R.eps_wall = (float)(1e-6 * h.geo.L);
+    R.inlet_x = (float)h.geo.inlet[0];
+    R.inlet_y = (float)h.geo.inlet[1];
+    R.inlet_z = (float)h.geo.inlet[2];
+    R.B_min = (float)h.bf.B_min;
+    const double aL = 0.5 * (h.bf.B_inj - h.bf.B_min), aR = 0.5 * (h.bf.B_ext - h.bf.B_min);
+    const double kL = kPi / h.zm, kR = kPi / (h.geo.L - h.zm);
+    R.aL = (float)aL;
+    R.aR = (float)aR;
+    R.zm = (float)h.zm;
+    R.inv_zm = (float)(1.0 / h.zm);
+    R.inv_zr = (float)(1.0 / (h.geo.L - h.zm));
+    R.aLk = (float)(aL * kL);
+    R.aLk2 = (float)(aL * kL * kL);
+    R.aRk = (float)(aR * kR);
+    R.aRk2 = (float)(aR * kR * kR);
+    R.hex_c = (float)(h.bf.B_hex / (h.geo.R0 * h.geo.R0));
+    R.B_ecr = (float)h.bf.B_ecr;
+    R.nx = h.nx;
+    R.ny = h.ny;
+    R.nz = h.nz;
+    const double dx = 2.0 * h.geo.R0 / h.nx, dy = 2.0 * h.geo.R0 / h.ny, dz = h.geo.L / h.nz;
+    R.inv_dx = (float)(1.0 / dx);
+    R.inv_dy = (float)(1.0 / dy);
+    R.inv_dz = (float)(1.0 / dz);
+    R.qmax = h.qmax;
+    R.qm_unit = (float)(kE / M);
+    R.dt = (float)dt;
+    R.half_dt = (float)(0.5 * dt);
+    R.flags = h.mcc.flags;
+    R.sig0 = (float)std::sqrt(h.mcc.T0_eV * kE / M);
+    R.n0s1 = (float)(h.mcc.n0_cm3 * 1e6 * h.mcc.sigma1_cm2 * 1e-4);
+    R.vth2 = (float)(8.0 * h.mcc.T0_eV * kE / (kPi * M));
+    R.dv_cx = (float)std::sqrt(2.0 * 0.5 * h.mcc.E_cx_eV * kE / M);
+    for (int zone = 0; zone < 2; ++zone) {
+        const double Te = zone ? h.Te_w : h.Te_c;
+        R.ei_coef[zone] = (float)(3.715e-6 * h.mcc.lnL_ei * dt / (h.mass_amu * h.mass_amu * std::sqrt(Te)));
+    }
+    R.ei_pow = h.mcc.ei_charge_power;
+    R.ke_scale = (float)(0.5 * M / kE * 1e6);
+    {
+        const double mu = 0.5 * M;
+        const double k = kE * kE / (kEps0 * mu);
+        R.lnl_ii_coef = (float)(h.mcc.lnL_ii / (4.0 * kPi) * k * k * ctx->weight / (dx * dy * dz));
+    }
+    R.seed_lo = (uint32_t)ctx->seed;
+    R.seed_hi = (uint32_t)(ctx->seed >> 32);
+    R.x = ctx->d_soa[0];
+    R.y = ctx->d_soa[1];
+    R.z = ctx->d_soa[2];
+    R.vx = ctx->d_soa[3];
+    R.vy = ctx->d_soa[4];
+    R.vz = ctx->d_soa[5];
+    R.meta = ctx->d_meta;
+    R.cell = ctx->d_cell;
+    R.E = ctx->d_E;
+    R.kdt = ctx->d_kdt;
+    R.dep = ctx->d_dep;
+    R.tally = ctx->d_tally;
+    R.ckey = ctx->d_ckey;
+    R.crank = ctx->d_crank;
+    R.ccount = ctx->d_ccount;
+    R.coff = ctx->d_coff;
+    R.cblk = ctx->d_cblk;
+    R.ckeys = ctx->d_ckeys;
+    R.occ = ctx->d_occ;
+    R.occ_n = ctx->d_occ_n;
+    R.nanbu = ctx->d_nanbu;
+    R.nanbu_lnlo = (float)std::log(kNanbuSLo);
+    R.nanbu_inv_dln = (float)((kNanbuN - 1) / std::log(kNanbuSHi / kNanbuSLo));
+    R.step = ctx->d_step;
+    R.n = (uint32_t)ctx->n;
+    R.n4 = (uint32_t)ctx->n4;
+    R.ncells = (uint32_t)((size_t)h.nx * h.ny * h.nz);
+}
+
+// upload the parameter block and rate table for step length dt
+ecris_status upload_dt(ecris_ctx* ctx, double dt)
+{
+    if (dt == ctx->dt_loaded) return ECRIS_OK;
+    // the pinned staging buffers may still feed an earlier copy
+    CK(cudaStreamSynchronize(ctx->stream));
+    fill_rundev(ctx, dt, *ctx->h_run);
+    for (int zone = 0; zone < 2; ++zone)
+        for (int q = 0; q < kQSlots; ++q)
+            ctx->h_kdt[zone * kQSlots + q] = q < ctx->h.qmax ? (float)(ctx->h.rate[zone][q] * dt) : 0.0f;
+    CK(cudaMemcpyAsync(ctx->d_run, ctx->h_run, sizeof(RunDev), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_kdt, ctx->h_kdt, 2 * kQSlots * sizeof(float), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    ctx->dt_loaded = dt;
+    return ECRIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ecris_status ecris_create(ecris_ctx** out, int device, void* cuda_stream)
+{
+    if (!out) {
+        g_create_error = "ecris_create: out is NULL";
+        return ECRIS_EINVAL;
+    }
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        g_create_error = std::string("ecris_create: no CUDA device ") + std::to_string(device) +
+                         (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : std::string());
+        return e != cudaSuccess ? ECRIS_ECUDA : ECRIS_EINVAL;
+    }
+    ecris_ctx* ctx = new (std::nothrow) ecris_ctx();
+    if (!ctx) {
+        g_create_error = "ecris_create: out of host memory";
+        return ECRIS_ENOMEM;
+    }
+    ctx->device = device;
+    e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            ctx->stream = (cudaStream_t)cuda_stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+            ctx->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_run, sizeof(RunDev));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_kdt, 2 * kQSlots * sizeof(float));
+    if (e != cudaSuccess) {
+        g_create_error = std::string("ecris_create: ") + cudaGetErrorString(e);
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        if (ctx->h_run) cudaFreeHost(ctx->h_run);
+        delete ctx;
+        return ECRIS_ECUDA;
+    }
+    ctx->step_grid = ctx->sm_count * step_blocks_per_sm();   // one wave of resident blocks
+    ctx->collide_grid = ctx->sm_count * 8;
+    *out = ctx;
+    return ECRIS_OK;
+}
+
+void ecris_destroy(ecris_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    free_ions(ctx);
+    free_fields(ctx);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& t : ctx->pending) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->h_run) cudaFreeHost(ctx->h_run);
+    if (ctx->h_kdt) cudaFreeHost(ctx->h_kdt);
+    delete ctx;
+}
+
+const char* ecris_last_error(const ecris_ctx* ctx)
+{
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const ecris_bfield* bf,
+                               const ecris_grid* grid, const ecris_species* sp, const ecris_mcc* mcc)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    if (!geo || !bf || !grid || !sp || !mcc) return fail(ctx, ECRIS_EINVAL, "init_fields: NULL argument");
+    if (!finite_pos(geo->R0) || !finite_pos(geo->L) || !finite_pos(geo->r_ap) || !(geo->r_ap < geo->R0))
+        return fail(ctx, ECRIS_EINVAL, "init_fields: need R0 > r_ap > 0 and L > 0");
+    {
+        const double ix = geo->inlet[0], iy = geo->inlet[1], iz = geo->inlet[2];
+        if (!(ix * ix + iy * iy < geo->R0 * geo->R0) || !(iz > 0.0) || !(iz < geo->L))
+            return fail(ctx, ECRIS_EINVAL, "init_fields: gas inlet must lie inside the chamber");
+    }
+    if (!(std::isfinite(bf->B_min) && bf->B_min >= 0.0) || !(bf->B_inj > bf->B_min) ||
+        !(bf->B_ext > bf->B_min) || !std::isfinite(bf->B_inj) || !std::isfinite(bf->B_ext) ||
+        !std::isfinite(bf->B_hex) || !std::isfinite(bf->B_ecr))
+        return fail(ctx, ECRIS_EINVAL, "init_fields: need B_inj > B_min >= 0 and B_ext > B_min");
+    if (grid->nx < 2 || grid->ny < 2 || grid->nz < 2 ||
+        (double)grid->nx * grid->ny * grid->nz > 4.0e8)
+        return fail(ctx, ECRIS_EINVAL, "init_fields: mesh sizes must be >= 2 and Nc <= 4e8");
+    if (!(grid->ne_in_cm3 >= 0.0) || !(grid->ne_out_cm3 >= 0.0) || !std::isfinite(grid->ne_in_cm3) ||
+        !std::isfinite(grid->ne_out_cm3) || !finite_pos(grid->Te_warm_eV) || !finite_pos(grid->Te_cold_eV))
+        return fail(ctx, ECRIS_EINVAL, "init_fields: need n_e >= 0 and T_e > 0");
+    if (!finite_pos(sp->mass_amu) || sp->qmax < 1 || sp->qmax > 63 || !sp->ip_eV || !sp->n_outer)
+        return fail(ctx, ECRIS_EINVAL, "init_fields: need mass > 0, 1 <= qmax <= 63, ip and n_outer");
+    for (int q = 0; q < sp->qmax; ++q)
+        if (!finite_pos(sp->ip_eV[q]) || sp->n_outer[q] < 1)
+            return fail(ctx, ECRIS_EINVAL, "init_fields: ionisation potential %d must be > 0 with q >= 1", q);
+    if (!(mcc->n0_cm3 >= 0.0) || !std::isfinite(mcc->n0_cm3) || !finite_pos(mcc->T0_eV) ||
+        !(mcc->sigma1_cm2 >= 0.0) || !(mcc->E_cx_eV >= 0.0) || !(mcc->lnL_ii >= 0.0) ||
+        !(mcc->lnL_ei >= 0.0) || (mcc->ei_charge_power != 1 && mcc->ei_charge_power != 2) ||
+        (mcc->flags & ~0x3Fu))
+        return fail(ctx, ECRIS_EINVAL, "init_fields: invalid collision parameters");
+
+    CK(cudaSetDevice(ctx->device));
+    free_ions(ctx);
+    free_fields(ctx);
+    HostRun& h = ctx->h;
+    h.geo = *geo;
+    h.bf = *bf;
+    h.nx = grid->nx;
+    h.ny = grid->ny;
+    h.nz = grid->nz;
+    h.ne_in = grid->ne_in_cm3;
+    h.ne_out = grid->ne_out_cm3;
+    h.Te_w = grid->Te_warm_eV;
+    h.Te_c = grid->Te_cold_eV;
+    h.mass_amu = sp->mass_amu;
+    h.qmax = sp->qmax;
+    h.ip.assign(sp->ip_eV, sp->ip_eV + sp->qmax);
+    h.nout.assign(sp->n_outer, sp->n_outer + sp->qmax);
+    h.mcc = *mcc;
+    h.zm = geo->L / (1.0 + std::sqrt((bf->B_ext - bf->B_min) / (bf->B_inj - bf->B_min)));
+    for (int zone = 0; zone < 2; ++zone) {
+        h.rate[zone].resize(sp->qmax);
+        const double Te = zone ? h.Te_w : h.Te_c;
+        for (int q = 0; q < sp->qmax; ++q) h.rate[zone][q] = lotz_rate(h.ip[q], h.nout[q], Te);
+    }
+
+    // per-cell electron data in FP64: zone by |B| at the centre, n_e, delta
+    const size_t nc = (size_t)h.nx * h.ny * h.nz;
+    const double dx = 2.0 * geo->R0 / h.nx, dy = 2.0 * geo->R0 / h.ny, dz = geo->L / h.nz;
+    std::vector<double> ne(nc), bm(nc);
+    std::vector<unsigned char> zone(nc);
+    for (int iz = 0; iz < h.nz; ++iz)
+        for (int iy = 0; iy < h.ny; ++iy)
+            for (int ix = 0; ix < h.nx; ++ix) {
+                const size_t c = ((size_t)iz * h.ny + iy) * h.nx + ix;
+                const double b = bmag_host(h, -geo->R0 + (ix + 0.5) * dx, -geo->R0 + (iy + 0.5) * dy,
+                                           (iz + 0.5) * dz);
+                bm[c] = b;
+                zone[c] = b < bf->B_ecr;
+                const double nin = grid->ne_in_cells ? (double)grid->ne_in_cells[c] : grid->ne_in_cm3;
+                if (zone[c] && !(nin >= 0.0 && std::isfinite(nin)))
+                    return fail(ctx, ECRIS_EINVAL, "init_fields: ne_in_cells[%zu] must be finite and >= 0", c);
+                ne[c] = 1e6 * (zone[c] ? nin : grid->ne_out_cm3);
+            }
+    std::vector<float4> cell(nc);
+    auto NE = [&](int iz, int iy, int ix) {
+        iy = iy < 0 ? 0 : (iy >= h.ny ? h.ny - 1 : iy);
+        ix = ix < 0 ? 0 : (ix >= h.nx ? h.nx - 1 : ix);
+        return ne[((size_t)iz * h.ny + iy) * h.nx + ix];
+    };
+    for (int iz = 0; iz < h.nz; ++iz)
+        for (int iy = 0; iy < h.ny; ++iy)
+            for (int ix = 0; ix < h.nx; ++ix) {
+                const size_t c = ((size_t)iz * h.ny + iy) * h.nx + ix;
+                double dlx = 0.0, dly = 0.0;
+                if (ne[c] > 0.0) {
+                    const double Te = zone[c] ? h.Te_w : h.Te_c;
+                    const double rl = 2.38e-6 * std::sqrt(Te) / (bm[c] * dx) / ne[c];
+                    // printed stencil: y-differences for delta_x, x-differences for delta_y
+                    const double sx = NE(iz, iy - 1, ix) - NE(iz, iy + 1, ix) +
+                                      0.5 * (NE(iz, iy - 1, ix + 1) + NE(iz, iy - 1, ix - 1) -
+                                             NE(iz, iy + 1, ix - 1) - NE(iz, iy + 1, ix + 1));
+                    const double sy = NE(iz, iy, ix + 1) - NE(iz, iy, ix - 1) +
+                                      0.5 * (NE(iz, iy + 1, ix + 1) + NE(iz, iy - 1, ix + 1) -
+                                             NE(iz, iy + 1, ix - 1) - NE(iz, iy - 1, ix - 1));
+                    dlx = -rl * sx;
+                    dly = -rl * sy;
+                }
+                cell[c] = make_float4((float)ne[c], zone[c] ? 1.0f : 0.0f, (float)dlx, (float)dly);
+            }
+    std::vector<float4> E(nc, make_float4(0.f, 0.f, 0.f, 0.f));
+    if (grid->E) {
+        for (size_t c = 0; c < nc; ++c) {
+            const float ex = grid->E[3 * c], ey = grid->E[3 * c + 1], ez = grid->E[3 * c + 2];
+            if (!std::isfinite(ex) || !std::isfinite(ey) || !std::isfinite(ez))
+                return fail(ctx, ECRIS_EINVAL, "init_fields: E[%zu] is not finite", c);
+            E[c] = make_float4(ex, ey, ez, 0.f);
+        }
+    }
+    CK(cudaMallocAsync((void**)&ctx->d_cell, nc * sizeof(float4), ctx->stream));
+    CK(cudaMallocAsync((void**)&ctx->d_E, nc * sizeof(float4), ctx->stream));
+    CK(cudaMallocAsync((void**)&ctx->d_kdt, 2 * kQSlots * sizeof(float), ctx->stream));
+    std::vector<float> nanbu(kNanbuN);
+    {
+        const double l0 = std::log(kNanbuSLo), dl = std::log(kNanbuSHi / kNanbuSLo) / (kNanbuN - 1);
+        for (int i = 0; i < kNanbuN; ++i) nanbu[i] = (float)std::log(nanbu_A_host(std::exp(l0 + i * dl)));
+    }
+    CK(cudaMallocAsync((void**)&ctx->d_nanbu, kNanbuN * sizeof(float), ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_nanbu, nanbu.data(), kNanbuN * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_cell, cell.data(), nc * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_E, E.data(), nc * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
+    // the host vectors die at return: wait for the copies
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->have_fields = true;
+    ctx->failed = false;
+    ctx->err.clear();
+    return ECRIS_OK;
+}
+
+ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6], const uint8_t* q,
+                             double weight, uint64_t seed, int src_is_device)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    if (!ctx->have_fields) return fail(ctx, ECRIS_ESTATE, "load_ions: call ecris_init_fields first");
+    if (!finite_pos(weight)) return fail(ctx, ECRIS_EINVAL, "load_ions: weight must be > 0");
+    const HostRun& h = ctx->h;
+    if ((double)n * (double)(h.qmax > 1 ? h.qmax : 1) >= 4294967296.0 || n > 0xFFFFFFF0ull)
+        return fail(ctx, ECRIS_EINVAL, "load_ions: n * qmax must stay below 2^32 (packed deposit)");
+    if (n > 0) {
+        if (!xyzv || !q) return fail(ctx, ECRIS_EINVAL, "load_ions: NULL particle arrays");
+        for (int k = 0; k < 6; ++k)
+            if (!xyzv[k]) return fail(ctx, ECRIS_EINVAL, "load_ions: NULL particle array %d", k);
+    }
+    CK(cudaSetDevice(ctx->device));
+    const size_t n4 = (n + 3) / 4;
+    const size_t cap = n4 > 0 ? 4 * n4 : 4;
+    const size_t nc = (size_t)h.nx * h.ny * h.nz;
+    // device buffers are kept across loads while they are large enough
+    if (!ctx->have_ions || cap > ctx->cap || nc != ctx->cap_cells) {
+        free_ions(ctx);
+        for (int k = 0; k < 6; ++k)
+            CK(cudaMallocAsync((void**)&ctx->d_soa[k], cap * sizeof(float), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_meta, cap * sizeof(uint32_t), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_ckey, cap * sizeof(uint32_t), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_q8, cap, ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_dep, nc * sizeof(unsigned long long), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_count, nc * sizeof(unsigned long long), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_charge, nc * sizeof(unsigned long long), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_tally, kTallyWords * sizeof(unsigned long long), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_census, kQSlots * sizeof(unsigned long long), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_step, sizeof(uint32_t), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_ticket, sizeof(unsigned int), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_bad, 2 * sizeof(unsigned int), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_run, sizeof(RunDev), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_tiles, (cap / kTile + 1) * sizeof(uint2), ctx->stream));
+        if (h.mcc.flags & kFCoulomb) {
+            CK(cudaMallocAsync((void**)&ctx->d_crank, cap * sizeof(uint32_t), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_ckeys, cap * sizeof(unsigned long long), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_ccount, nc * sizeof(uint32_t), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_coff, (nc + 1) * sizeof(uint32_t), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_cblk, (size_t)coulomb_scan_blocks((uint32_t)nc) * sizeof(uint32_t),
+                               ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_occ, nc * sizeof(uint32_t), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_occ_n, sizeof(uint32_t), ctx->stream));
+        }
+        ctx->cap = cap;
+        ctx->cap_cells = nc;
+        ctx->have_ions = true;
+    }
+    ctx->n = n;
+    ctx->n4 = n4;
+    ctx->ntiles = (uint32_t)((n4 + kThreads - 1) / kThreads);
+    ctx->tiles_h.resize(ctx->ntiles > 0 ? ctx->ntiles : 1);
+    for (uint32_t t = 0; t < ctx->ntiles; ++t) ctx->tiles_h[t] = make_uint2(0u, t * (uint32_t)kThreads);
+    const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (n) {
+        for (int k = 0; k < 6; ++k)
+            CK(cudaMemcpyAsync(ctx->d_soa[k], xyzv[k], n * sizeof(float), kind, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d_q8, q, n, kind, ctx->stream));
+    }
+    CK(cudaMemcpyAsync(ctx->d_tiles, ctx->tiles_h.data(), ctx->tiles_h.size() * sizeof(uint2),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_ckey, 0xFF, cap * sizeof(uint32_t), ctx->stream));
+    if (ctx->d_ccount) CK(cudaMemsetAsync(ctx->d_ccount, 0, nc * sizeof(uint32_t), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_dep, 0, nc * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_count, 0, nc * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_charge, 0, nc * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_tally, 0, kTallyWords * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(uint32_t), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_ticket, 0, sizeof(unsigned int), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_bad, 0, sizeof(unsigned int), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_bad + 1, 0xFF, sizeof(unsigned int), ctx->stream));
+    // validate on the device, build the meta words and fill the padding slots
+    LoadCheck lc;
+    lc.R0sq = (float)(h.geo.R0 * h.geo.R0);
+    lc.L = (float)h.geo.L;
+    lc.qmax = (uint32_t)h.qmax;
+    lc.inlet_x = (float)h.geo.inlet[0];
+    lc.inlet_y = (float)h.geo.inlet[1];
+    lc.inlet_z = (float)h.geo.inlet[2];
+    CK(launch_load_init(lc, ctx->d_soa, ctx->d_q8, ctx->d_meta, (uint32_t)n, (uint32_t)cap, ctx->d_bad,
+                        ctx->stream));
+    unsigned int bad[2] = {0u, 0u};
+    CK(cudaMemcpyAsync(bad, ctx->d_bad, sizeof bad, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (bad[0]) {
+        ctx->n = 0;
+        ctx->n4 = 0;
+        ctx->ntiles = 0;
+        ctx->loaded = false;
+        return fail(ctx, ECRIS_EINVAL,
+                    "load_ions: %u particle(s) outside the chamber, not finite or with Q > qmax "
+                    "(first index %u)", bad[0], bad[1]);
+    }
+    ctx->weight = weight;
+    ctx->seed = seed;
+    ctx->steps_done = 0;
+    ctx->time_s = 0.0;
+    ctx->dt_loaded = -1.0;
+    ctx->since_fold = 0;
+    // fold the packed deposit before its low word (charge) can carry
+    const double per_step = (double)(n ? n : 1) * (h.qmax > 1 ? h.qmax : 1);
+    const double k = std::floor(4294967295.0 / per_step);
+    ctx->fold_every = (uint32_t)(k < 1.0 ? 1.0 : (k > 1e6 ? 1e6 : k));
+    ctx->loaded = true;
+    ctx->failed = false;
+    ctx->err.clear();
+    return ECRIS_OK;
+}
+
+ecris_status ecris_step(ecris_ctx* ctx, uint32_t nsteps, double dt)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    if (ctx->failed) return fail(ctx, ECRIS_ESTATE, "step: context failed earlier (%s); reload", ctx->err.c_str());
+    if (!ctx->loaded) return fail(ctx, ECRIS_ESTATE, "step: call ecris_load_ions first");
+    if (!finite_pos(dt)) return fail(ctx, ECRIS_EINVAL, "step: dt must be finite and > 0");
+    if (ctx->steps_done + nsteps >= kMaxSteps)
+        return fail(ctx, ECRIS_EINVAL, "step: more than 2^30 steps since load");
+    CK(cudaSetDevice(ctx->device));
+    ecris_status st = upload_dt(ctx, dt);
+    if (st != ECRIS_OK) return st;
+    const bool coulomb = (ctx->h.mcc.flags & kFCoulomb) != 0;
+    const uint32_t nc = (uint32_t)((size_t)ctx->h.nx * ctx->h.ny * ctx->h.nz);
+    for (uint32_t s = 0; s < nsteps; ++s) {
+        CK(timed(ctx, kKindStep, [&] {
+            return launch_step(ctx->d_run, ctx->d_tiles, ctx->ntiles, 1, ctx->d_ticket, coulomb ? 0 : 1,
+                               ctx->step_grid, ctx->stream);
+        }));
+        if (coulomb) {
+            CK(timed(ctx, kKindCoulomb, [&] {
+                return launch_coulomb(ctx->d_run, 0, nc, (uint32_t)ctx->n4, ctx->d_ticket, ctx->collide_grid,
+                                      nullptr, ctx->stream);
+            }, kCoulombKernels));
+        }
+        if (++ctx->since_fold >= ctx->fold_every) {
+            CK(timed(ctx, kKindOther, [&] {
+                return launch_fold(ctx->d_run, 0, nc, ctx->d_count, ctx->d_charge, ctx->stream);
+            }));
+            ctx->since_fold = 0;
+        }
+    }
+    ctx->steps_done += nsteps;
+    ctx->time_s += dt * nsteps;
+    return ECRIS_OK;
+}
+
+ecris_status ecris_diag(ecris_ctx* ctx, ecris_diag_out* out)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    if (!out) return fail(ctx, ECRIS_EINVAL, "diag: out is NULL");
+    if (!ctx->loaded) return fail(ctx, ECRIS_ESTATE, "diag: call ecris_load_ions first");
+    if (ctx->failed) return fail(ctx, ECRIS_ESTATE, "diag: context failed earlier (%s)", ctx->err.c_str());
+    CK(cudaSetDevice(ctx->device));
+    const HostRun& h = ctx->h;
+    const size_t nc = (size_t)h.nx * h.ny * h.nz;
+    if (ctx->dt_loaded < 0.0) {
+        ecris_status st = upload_dt(ctx, 1e-9);   // parameter block for the census kernel
+        if (st != ECRIS_OK) return st;
+    }
+    CK(launch_fold(ctx->d_run, 0, (uint32_t)nc, ctx->d_count, ctx->d_charge, ctx->stream));
+    ctx->since_fold = 0;
+    CK(cudaMemsetAsync(ctx->d_census, 0, kQSlots * sizeof(unsigned long long), ctx->stream));
+    CK(launch_census(ctx->d_run, 0, (uint32_t)ctx->n4, ctx->d_census, ctx->stream));
+    unsigned long long tally[kTallyWords], census[kQSlots];
+    CK(cudaMemcpyAsync(tally, ctx->d_tally, sizeof tally, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(census, ctx->d_census, sizeof census, cudaMemcpyDeviceToHost, ctx->stream));
+    if (out->cell_count)
+        CK(cudaMemcpyAsync(out->cell_count, ctx->d_count, nc * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (out->cell_charge)
+        CK(cudaMemcpyAsync(out->cell_charge, ctx->d_charge, nc * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int Q1 = h.qmax + 1;
+    out->qmax = h.qmax;
+    out->steps = ctx->steps_done;
+    out->time_s = ctx->time_s;
+    for (int q = 0; q < Q1; ++q) {
+        if (out->extracted) out->extracted[q] = (int64_t)tally[kTallyExtracted + q];
+        if (out->lost) out->lost[q] = (int64_t)tally[kTallyLost + q];
+        if (out->alive_by_q) out->alive_by_q[q] = (int64_t)census[q];
+        if (out->current_A)
+            out->current_A[q] = ctx->time_s > 0.0
+                                    ? q * kE * ctx->weight * (double)tally[kTallyExtracted + q] / ctx->time_s
+                                    : 0.0;
+    }
+    out->ke_lost_eV = 1e-6 * (double)tally[kTallyKe];
+    out->coulomb_collisions = (int64_t)tally[kTallyCoulomb];
+    // power balance: kinetic + potential energy of the ions that left plus
+    // 3/2 T_ew per electron that left with them
+    double e_eV = out->ke_lost_eV, ipcum = 0.0;
+    for (int q = 1; q < Q1; ++q) {
+        ipcum += h.ip[q - 1];
+        const double nleft = (double)tally[kTallyExtracted + q] + (double)tally[kTallyLost + q];
+        e_eV += nleft * (ipcum + 1.5 * q * h.Te_w);
+    }
+    out->power_W = ctx->time_s > 0.0 ? ctx->weight * e_eV * kE / ctx->time_s : 0.0;
+    return ECRIS_OK;
+}
+
+ecris_status ecris_get_state(ecris_ctx* ctx, float* const xyzv[6], uint32_t* meta, int dst_is_device)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    if (!ctx->loaded) return fail(ctx, ECRIS_ESTATE, "get_state: call ecris_load_ions first");
+    CK(cudaSetDevice(ctx->device));
+    const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (ctx->n) {
+        for (int k = 0; k < 6; ++k)
+            if (xyzv && xyzv[k])
+                CK(cudaMemcpyAsync(xyzv[k], ctx->d_soa[k], ctx->n * sizeof(float), kind, ctx->stream));
+        if (meta) CK(cudaMemcpyAsync(meta, ctx->d_meta, ctx->n * sizeof(uint32_t), kind, ctx->stream));
+    }
+    if (!dst_is_device) CK(cudaStreamSynchronize(ctx->stream));
+    return ECRIS_OK;
+}
+
+ecris_status ecris_set_profiling(ecris_ctx* ctx, int enable)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    CK(collect_profile(ctx));
+    ctx->prof = enable != 0;
+    for (int k = 0; k < 3; ++k) {
+        ctx->launches[k] = 0;
+        ctx->ms[k] = 0.0;
+    }
+    return ECRIS_OK;
+}
+
+ecris_status ecris_get_profile(ecris_ctx* ctx, ecris_profile* out)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    if (!out) return fail(ctx, ECRIS_EINVAL, "get_profile: out is NULL");
+    CK(cudaSetDevice(ctx->device));
+    CK(collect_profile(ctx));
+    out->step_launches = ctx->launches[kKindStep];
+    out->step_ms = ctx->ms[kKindStep];
+    out->coulomb_launches = ctx->launches[kKindCoulomb];
+    out->coulomb_ms = ctx->ms[kKindCoulomb];
+    out->other_launches = ctx->launches[kKindOther];
+    out->other_ms = ctx->ms[kKindOther];
+    return ECRIS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,257 @@
+// Internal definitions shared by the CUDA translation units of the ECRIS
+// library: the per-run device parameter block, the tally layout and the
+// device-side building blocks of the time step (Philox words, field model,
+// E-grid gather).  Host-side API code lives in api.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ecris {
+
+constexpr int kQSlots = 64;            // charge-state slots per tally array
+constexpr int kThreads = 256;          // threads per block of the step kernel
+constexpr int kVec = 4;                // particles per thread (one float4 per SoA array)
+constexpr int kTile = kThreads * kVec; // particles per tile
+
+// Tally words per run (u64): extracted[64], lost[64], kinetic energy of ions
+// that left (micro-eV), Coulomb pair collisions.
+constexpr int kTallyExtracted = 0;
+constexpr int kTallyLost = 64;
+constexpr int kTallyKe = 128;
+constexpr int kTallyCoulomb = 129;
+constexpr int kTallyWords = 132;
+
+// meta word layout (matches the public header)
+constexpr uint32_t kQMask = 0xFFu;
+constexpr uint32_t kEvWall = 1u << 8;
+constexpr uint32_t kEvExtract = 1u << 9;
+constexpr uint32_t kEvIonize = 1u << 10;
+constexpr uint32_t kEvCx = 1u << 11;
+constexpr uint32_t kEvCoulomb = 1u << 12;
+constexpr uint32_t kStFrozen = 1u << 16;
+constexpr uint32_t kStPad = 1u << 17;   // padding slot, never processed
+
+// process switches (match ECRIS_F_*)
+constexpr uint32_t kFPush = 1u << 0;
+constexpr uint32_t kFIonize = 1u << 1;
+constexpr uint32_t kFCx = 1u << 2;
+constexpr uint32_t kFEikick = 1u << 3;
+constexpr uint32_t kFCoulomb = 1u << 4;
+constexpr uint32_t kFRecycle = 1u << 5;
+
+constexpr uint32_t kNoCell = 0xFFFFFFFFu;
+
+// Nanbu A(s) table: ln A tabulated on a uniform grid in ln s over [1e-3, 6]
+constexpr int kNanbuN = 2048;
+constexpr double kNanbuSLo = 1e-3;
+constexpr double kNanbuSHi = 6.0;
+
+// scan of the per-cell participant counts: cells per block of the first pass
+constexpr int kScanThreads = 256;
+constexpr int kScanPerThread = 8;
+constexpr int kScanBlock = kScanThreads * kScanPerThread;
+
+// Device parameter block of one run: FP32 constants of the kernels (built in
+// FP64 on the host) and the run's device arrays.
+struct RunDev {
+    // geometry
+    float R0, R0sq, L, r_ap_sq, eps_wall;
+    float inlet_x, inlet_y, inlet_z;
+    float gband;                 // unused by kernels; kept for layout stability
+    // synthetic mirror B0(z): raised-cosine halves around z_m
+    float B_min, aL, aR;         // half amplitudes (B_inj-B_min)/2, (B_ext-B_min)/2
+    float zm, inv_zm, inv_zr;    // z_m, 1/z_m, 1/(L-z_m)
+    float aLk, aLk2, aRk, aRk2;  // a k and a k^2 of each half (k = pi/z_m, pi/(L-z_m))
+    float hex_c;                 // B_hex / R0^2
+    float B_ecr;
+    // mesh
+    int32_t nx, ny, nz;
+    float inv_dx, inv_dy, inv_dz;
+    // species and push
+    int32_t qmax;
+    float qm_unit;               // e / (M amu)
+    float dt, half_dt;
+    // collisions
+    uint32_t flags;
+    float sig0;                  // sqrt(kT0/M): thermal speed of re-emitted atoms
+    float n0s1;                  // n0 * sigma_1 (1/m)
+    float vth2;                  // 8 kT0 / (pi M)
+    float dv_cx;                 // kick of a Q>=3 charge exchange: sqrt(2 (E_cx/2) / M)
+    float ei_coef[2];            // D^2 = ei_coef[zone] * n_e * Q^p (zone 0 cold, 1 warm)
+    int32_t ei_pow;
+    float ke_scale;              // (M/2) / e * 1e6: micro-eV per (m/s)^2
+    float lnl_ii_coef;           // Nanbu s prefactor lnL/(4 pi) (e^2/(eps0 mu))^2 w / V_cell
+    uint32_t seed_lo, seed_hi;
+    // arrays
+    float *x, *y, *z, *vx, *vy, *vz;
+    uint32_t *meta;
+    const float4 *cell;          // {n_e (m^-3), zone (0/1), delta_x, delta_y}
+    const float4 *E;             // {E_x, E_y, E_z, 0} per cell centre
+    const float *kdt;            // ionisation rate * dt, [zone * 64 + Q]
+    unsigned long long *dep;     // packed deposit accumulator: count << 32 | charge
+    unsigned long long *tally;   // kTallyWords
+    uint32_t *ckey;              // Coulomb cell key per particle (kNoCell if not taking part)
+    uint32_t *crank;             // arrival rank of a Coulomb participant in its cell
+    uint32_t *ccount;            // Coulomb participants per cell (zeroed by the scan)
+    uint32_t *coff;              // exclusive scan of ccount, Nc + 1 entries
+    uint32_t *cblk;              // scan block totals
+    unsigned long long *ckeys;   // (pairing hash << 32 | pid) per participant, grouped by cell
+    uint32_t *occ;               // cells with >= 2 participants this step
+    uint32_t *occ_n;             // number of entries in occ
+    const float *nanbu;          // ln A at ln s = nanbu_lnlo + i / nanbu_inv_dln, i < kNanbuN
+    float nanbu_lnlo, nanbu_inv_dln;
+    uint32_t *step;              // device step counter of the run
+    uint32_t n;                  // particles
+    uint32_t n4;                 // float4 groups = ceil(n/4)
+    uint32_t ncells;
+    uint32_t pad_;
+};
+
+// ----------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11), counter (c0, 0, c2, 0), key (k0, k1).
+// ----------------------------------------------------------------------------
+struct Words { uint32_t w0, w1, w2, w3; };
+
+__device__ __forceinline__ Words philox(uint32_t c0, uint32_t c2, uint32_t k0, uint32_t k1)
+{
+    uint32_t c1 = 0u, c3 = 0u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return Words{c0, c1, c2, c3};
+}
+
+// words of particle pid at step s, stream st: counter (pid, 0, 4 s + st, 0)
+__device__ __forceinline__ Words rng_words(const RunDev& R, uint32_t pid, uint32_t step, uint32_t st)
+{
+    return philox(pid, step * 4u + st, R.seed_lo, R.seed_hi);
+}
+
+// uniform in (0, 1]: (top 24 bits + 1) * 2^-24, exact in FP32
+__device__ __forceinline__ float unit01(uint32_t w)
+{
+    return (float)((w >> 8) + 1u) * (1.0f / 16777216.0f);
+}
+
+// event test: fires when the word is below floor(p * 2^32)
+__device__ __forceinline__ bool fires(uint32_t w, float p)
+{
+    const float t = p * 4294967296.0f;
+    if (t >= 4294967296.0f) return true;
+    return w < __float2uint_rz(t);
+}
+
+// ----------------------------------------------------------------------------
+// Static magnetic field: synthetic mirror, paraxial off axis, plus the
+// hexapole B_H (2xy, x^2 - y^2) / R0^2 (the printed sin/cos(2 theta) R^2 form).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void bfield(const RunDev& R, float x, float y, float z,
+                                       float& Bx, float& By, float& Bz)
+{
+    float b0, b1, b2, s, c;
+    if (z <= R.zm) {
+        sincospif(z * R.inv_zm, &s, &c);
+        b0 = R.B_min + R.aL * (1.0f + c);
+        b1 = -R.aLk * s;
+        b2 = -R.aLk2 * c;
+    } else {
+        sincospif((z - R.zm) * R.inv_zr, &s, &c);
+        b0 = R.B_min + R.aR * (1.0f - c);
+        b1 = R.aRk * s;
+        b2 = R.aRk2 * c;
+    }
+    const float r2 = x * x + y * y;
+    Bx = -0.5f * x * b1 + R.hex_c * (2.0f * x * y);
+    By = -0.5f * y * b1 + R.hex_c * (x * x - y * y);
+    Bz = b0 - 0.25f * r2 * b2;
+}
+
+// one axis of the trilinear gather between cell centres, clamped at the faces
+__device__ __forceinline__ void tri_axis(float g, int n, int& i0, float& f)
+{
+    const float gc = g - 0.5f;
+    const float fl = floorf(gc);
+    int i = (int)fl;
+    if (i < 0) { i0 = 0; f = 0.0f; }
+    else if (i > n - 2) { i0 = n - 2; f = 1.0f; }
+    else { i0 = i; f = gc - fl; }
+}
+
+__device__ __forceinline__ void efield(const RunDev& R, float x, float y, float z,
+                                       float& Ex, float& Ey, float& Ez)
+{
+    int ix, iy, iz;
+    float fx, fy, fz;
+    tri_axis((x + R.R0) * R.inv_dx, R.nx, ix, fx);
+    tri_axis((y + R.R0) * R.inv_dy, R.ny, iy, fy);
+    tri_axis(z * R.inv_dz, R.nz, iz, fz);
+    const int sx = 1, sy = R.nx, sz = R.nx * R.ny;
+    const float4* e = R.E + ((iz * R.ny + iy) * R.nx + ix);
+    const float4 a000 = __ldg(e), a100 = __ldg(e + sx), a010 = __ldg(e + sy), a110 = __ldg(e + sy + sx);
+    const float4 a001 = __ldg(e + sz), a101 = __ldg(e + sz + sx), a011 = __ldg(e + sz + sy),
+                 a111 = __ldg(e + sz + sy + sx);
+    const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+    const float w000 = gx * gy * gz, w100 = fx * gy * gz, w010 = gx * fy * gz, w110 = fx * fy * gz;
+    const float w001 = gx * gy * fz, w101 = fx * gy * fz, w011 = gx * fy * fz, w111 = fx * fy * fz;
+    Ex = w000 * a000.x + w100 * a100.x + w010 * a010.x + w110 * a110.x +
+         w001 * a001.x + w101 * a101.x + w011 * a011.x + w111 * a111.x;
+    Ey = w000 * a000.y + w100 * a100.y + w010 * a010.y + w110 * a110.y +
+         w001 * a001.y + w101 * a101.y + w011 * a011.y + w111 * a111.y;
+    Ez = w000 * a000.z + w100 * a100.z + w010 * a010.z + w110 * a110.z +
+         w001 * a001.z + w101 * a101.z + w011 * a011.z + w111 * a111.z;
+}
+
+// nearest-grid-point cell of a position, clamped into the mesh
+__device__ __forceinline__ uint32_t ngp_cell(const RunDev& R, float x, float y, float z)
+{
+    int ix = __float2int_rd((x + R.R0) * R.inv_dx);
+    int iy = __float2int_rd((y + R.R0) * R.inv_dy);
+    int iz = __float2int_rd(z * R.inv_dz);
+    ix = min(max(ix, 0), R.nx - 1);
+    iy = min(max(iy, 0), R.ny - 1);
+    iz = min(max(iz, 0), R.nz - 1);
+    return (uint32_t)((iz * R.ny + iy) * R.nx + ix);
+}
+
+// ----------------------------------------------------------------------------
+// Launch wrappers (defined in step_kernel.cu / coulomb.cu)
+// ----------------------------------------------------------------------------
+// tiles[t] = (run index, first float4 group of the tile)
+cudaError_t launch_step(const RunDev* runs_dev, const uint2* tiles_dev, uint32_t ntiles,
+                        uint32_t nruns, unsigned int* ticket, int bump_step, int grid,
+                        cudaStream_t s);
+// Coulomb collisions of one run for the current step (after launch_step with
+// bump_step = 0): scan of the cell counts, scatter of the pairing keys, and
+// the per-cell sort / pair / collide kernel, whose last block advances the
+// step counter.  `kernels` receives the number of launches made.
+constexpr int kCoulombKernels = 5;   // kernels per launch_coulomb
+cudaError_t launch_coulomb(const RunDev* runs_dev, uint32_t run, uint32_t ncells, uint32_t n4,
+                           unsigned int* ticket, int grid, int* kernels, cudaStream_t s);
+int coulomb_scan_blocks(uint32_t ncells);
+
+// resident blocks per SM of the step kernel
+int step_blocks_per_sm();
+cudaError_t launch_fold(const RunDev* runs_dev, uint32_t run, uint32_t ncells,
+                        unsigned long long* count, unsigned long long* charge, cudaStream_t s);
+// validity limits and padding point for ecris_load_ions
+struct LoadCheck {
+    float R0sq, L;
+    uint32_t qmax;
+    float inlet_x, inlet_y, inlet_z;
+};
+// check particles [0, n), build their meta words from q8, fill pads [n, cap);
+// bad[0] counts invalid particles, bad[1] holds the lowest invalid index
+cudaError_t launch_load_init(const LoadCheck& lc, float* const soa[6], const uint8_t* q8, uint32_t* meta,
+                             uint32_t n, uint32_t cap, unsigned int* bad, cudaStream_t s);
+cudaError_t launch_census(const RunDev* runs_dev, uint32_t run, uint32_t n4,
+                          unsigned long long* census, cudaStream_t s);
+
+}  // namespace ecris

@@ -1,0 +1,399 @@
+// Fused per-macroparticle time step (push -> boundary test -> MCC -> wall and
+// aperture bookkeeping -> NGP deposition) of the ECRIS model of Mironov et
+// al. (arXiv:1507.03392, Sec. II), plus the deposit fold and the charge-state
+// census used by the diagnostics.
+//
+// Data layout: each run's particles are SoA float arrays x, y, z, vx, vy, vz
+// and a u32 meta word, padded to a multiple of 4 so that one thread moves four
+// particles with one 128-bit load and store per array (56 bytes per particle
+// per step, the whole HBM traffic of the step).  Per-cell data (n_e, zone,
+// delta) and the E grid are float4 records read through L1/L2; the rate table
+// is read through L1.  Tallies go to shared memory first and then to global
+// u64 counters once per tile; the deposit is one packed 64-bit reduction per
+// particle (count in the high word, charge in the low word).
+#include "ecris_internal.cuh"
+
+namespace ecris {
+
+namespace {
+
+struct BlockTally {
+    unsigned int ext[kQSlots];
+    unsigned int lost[kQSlots];
+    unsigned long long ke;
+};
+
+// Cosine-law re-emission at temperature T0 (full accommodation): normal speed
+// sigma sqrt(-2 ln U0) along the inward normal n, tangential components one
+// Box-Muller pair along e1, e2.
+__device__ __forceinline__ void emit(float sigma, float nx, float ny, float nz, float e1x, float e1y,
+                                     float e1z, float e2x, float e2y, float e2z, const Words& w,
+                                     float& vx, float& vy, float& vz)
+{
+    const float vn = sigma * sqrtf(-2.0f * logf(unit01(w.w0)));
+    const float rt = sigma * sqrtf(-2.0f * logf(unit01(w.w1)));
+    float s, c;
+    sincospif(2.0f * unit01(w.w2), &s, &c);
+    const float t1 = rt * c, t2 = rt * s;
+    vx = vn * nx + t1 * e1x + t2 * e2x;
+    vy = vn * ny + t1 * e1y + t2 * e2y;
+    vz = vn * nz + t1 * e1z + t2 * e2z;
+}
+
+__device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uint32_t step, float& x,
+                                              float& y, float& z, float& vx, float& vy, float& vz,
+                                              uint32_t& meta, BlockTally& T,
+                                              unsigned long long& ke_acc, uint32_t& ckey)
+{
+    ckey = kNoCell;
+    const uint32_t status = meta & 0xFFFF0000u;
+    if (status & (kStFrozen | kStPad)) {
+        meta = status | (meta & kQMask);   // events of a frozen particle are cleared
+        return;
+    }
+    uint32_t Q = meta & kQMask;
+    uint32_t ev = 0;
+    const float x0 = x, y0 = y, z0 = z;
+
+    // ---- push: Boris rotation for ions, straight line for atoms ----
+    if (R.flags & kFPush) {
+        if (Q > 0) {
+            float Bx, By, Bz, Ex, Ey, Ez;
+            bfield(R, x0, y0, z0, Bx, By, Bz);
+            efield(R, x0, y0, z0, Ex, Ey, Ez);
+            const float h = (float)Q * R.qm_unit * R.half_dt;
+            float mx = vx + h * Ex, my = vy + h * Ey, mz = vz + h * Ez;
+            const float tx = h * Bx, ty = h * By, tz = h * Bz;
+            const float sf = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
+            const float px = mx + (my * tz - mz * ty);
+            const float py = my + (mz * tx - mx * tz);
+            const float pz = mz + (mx * ty - my * tx);
+            mx += (py * tz - pz * ty) * sf;
+            my += (pz * tx - px * tz) * sf;
+            mz += (px * ty - py * tx) * sf;
+            vx = mx + h * Ex;
+            vy = my + h * Ey;
+            vz = mz + h * Ez;
+        }
+        x = x0 + vx * R.dt;
+        y = y0 + vy * R.dt;
+        z = z0 + vz * R.dt;
+    }
+
+    // ---- boundary test on the new position ----
+    const bool out_r = x * x + y * y > R.R0sq;
+    const bool out_0 = z < 0.0f;
+    const bool out_L = z > R.L;
+    uint32_t cell;
+    if (out_r | out_0 | out_L) {
+        // first crossing along the straight segment
+        const float dx = x - x0, dy = y - y0, dz = z - z0;
+        float fbest = 2.0f;
+        int kind = 0;
+        if (out_r) {
+            const float a = dx * dx + dy * dy, b = x0 * dx + y0 * dy;
+            const float c = x0 * x0 + y0 * y0 - R.R0sq;
+            const float disc = sqrtf(fmaxf(0.0f, b * b - a * c));
+            float f = (b + disc > 0.0f) ? -c / (b + disc) : 0.0f;
+            f = fmaxf(f, 0.0f);
+            fbest = f;
+            kind = 1;
+        }
+        if (out_0) {
+            const float f = z0 / (z0 - z);
+            if (f < fbest) { fbest = f; kind = 2; }
+        }
+        if (out_L) {
+            const float f = (R.L - z0) / (z - z0);
+            if (f < fbest) { fbest = f; kind = 3; }
+        }
+        float cx = x0 + fbest * dx, cy = y0 + fbest * dy, cz = z0 + fbest * dz;
+        if (kind == 3 && cx * cx + cy * cy < R.r_ap_sq) kind = 4;
+
+        // ---- wall / aperture bookkeeping ----
+        if (Q >= 1) ke_acc += __float2ull_rn(R.ke_scale * (vx * vx + vy * vy + vz * vz));
+        if (kind == 4) {
+            atomicAdd(&T.ext[Q], 1u);
+            ev |= kEvExtract;
+        } else {
+            atomicAdd(&T.lost[Q], 1u);
+            ev |= kEvWall;
+        }
+        Q = 0;
+        if (!(R.flags & kFRecycle)) {
+            meta = status | kStFrozen | ev;   // stays at its last position, never moves again
+            return;
+        }
+        const Words w = rng_words(R, pid, step, 2u);
+        if (kind == 4) {
+            cx = R.inlet_x; cy = R.inlet_y; cz = R.inlet_z;
+            emit(R.sig0, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, w, vx, vy, vz);
+        } else if (kind == 1) {
+            const float rc = sqrtf(cx * cx + cy * cy);
+            const float ux = cx / rc, uy = cy / rc;
+            const float sc = (R.R0 - R.eps_wall) / rc;
+            cx *= sc; cy *= sc;
+            emit(R.sig0, -ux, -uy, 0.f, -uy, ux, 0.f, 0.f, 0.f, 1.f, w, vx, vy, vz);
+        } else if (kind == 2) {
+            cz = R.eps_wall;
+            emit(R.sig0, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, w, vx, vy, vz);
+        } else {
+            cz = R.L - R.eps_wall;
+            emit(R.sig0, 0.f, 0.f, -1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, w, vx, vy, vz);
+        }
+        x = cx; y = cy; z = cz;
+        cell = ngp_cell(R, x, y, z);
+    } else {
+        // ---- MCC in the particle's cell ----
+        cell = ngp_cell(R, x, y, z);
+        const float4 cr = __ldg(R.cell + cell);   // n_e, zone, delta_x, delta_y
+        const int zone = cr.y > 0.5f ? 1 : 0;
+        const Words w = rng_words(R, pid, step, 0u);
+        if ((R.flags & kFIonize) && (int)Q < R.qmax) {
+            const float lam = cr.x * __ldg(R.kdt + zone * kQSlots + Q);
+            if (fires(w.w0, -expm1f(-lam))) { Q += 1; ev |= kEvIonize; }
+        }
+        if ((R.flags & kFCx) && R.n0s1 > 0.0f && Q >= 1 && Q != 2) {
+            const float vrel = sqrtf(vx * vx + vy * vy + vz * vz + R.vth2);
+            const float p = -expm1f(-R.n0s1 * (float)Q * vrel * R.dt);
+            if (fires(w.w1, p)) {
+                const Words u = rng_words(R, pid, step, 3u);
+                ev |= kEvCx;
+                if (Q == 1) {
+                    float s1, c1, s2, c2;
+                    const float r1 = R.sig0 * sqrtf(-2.0f * logf(unit01(u.w0)));
+                    sincospif(2.0f * unit01(u.w1), &s1, &c1);
+                    const float r2 = R.sig0 * sqrtf(-2.0f * logf(unit01(u.w2)));
+                    sincospif(2.0f * unit01(u.w3), &s2, &c2);
+                    vx = r1 * c1; vy = r1 * s1; vz = r2 * c2;
+                } else {
+                    const float ct = 2.0f * unit01(u.w0) - 1.0f;
+                    const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+                    float sp, cp;
+                    sincospif(2.0f * unit01(u.w1), &sp, &cp);
+                    vx += R.dv_cx * st * cp;
+                    vy += R.dv_cx * st * sp;
+                    vz += R.dv_cx * ct;
+                    Q -= 1;
+                }
+            }
+        }
+        if ((R.flags & kFEikick) && Q >= 1) {
+            const float qp = R.ei_pow == 1 ? (float)Q : (float)(Q * Q);
+            const float D = sqrtf(R.ei_coef[zone] * cr.x * qp);
+            const float ct = 2.0f * unit01(w.w2) - 1.0f;
+            const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+            float sp, cp;
+            sincospif(2.0f * unit01(w.w3), &sp, &cp);
+            const float dxv = st * cp + cr.z, dyv = st * sp + cr.w, dzv = ct;
+            const float m2 = dxv * dxv + dyv * dyv + dzv * dzv;
+            if (m2 > 0.0f) {
+                const float k = D * rsqrtf(m2);
+                vx += k * dxv;
+                vy += k * dyv;
+                vz += k * dzv;
+            }
+        }
+        if (Q >= 1 && (R.flags & kFCoulomb)) {
+            ckey = cell;
+            R.crank[pid] = atomicAdd(R.ccount + cell, 1u);
+        }
+    }
+
+    // ---- NGP deposition at the final position ----
+    atomicAdd(R.dep + cell, (1ull << 32) | (unsigned long long)Q);
+    meta = status | ev | Q;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_step(const RunDev* __restrict__ runs,
+                                                   const uint2* __restrict__ tiles, uint32_t ntiles,
+                                                   uint32_t nruns, unsigned int* ticket,
+                                                   int bump_step)
+{
+    __shared__ BlockTally T;
+    __shared__ int s_last;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint2 tile = tiles[t];
+        const RunDev& R = runs[tile.x];
+        for (int i = threadIdx.x; i < kQSlots; i += kThreads) { T.ext[i] = 0u; T.lost[i] = 0u; }
+        if (threadIdx.x == 0) T.ke = 0ull;
+        __syncthreads();
+        const uint32_t step = *R.step;
+        const uint32_t g = tile.y + threadIdx.x;
+        unsigned long long ke = 0ull;
+        if (g < R.n4) {
+            float4 X = reinterpret_cast<const float4*>(R.x)[g];
+            float4 Y = reinterpret_cast<const float4*>(R.y)[g];
+            float4 Z = reinterpret_cast<const float4*>(R.z)[g];
+            float4 VX = reinterpret_cast<const float4*>(R.vx)[g];
+            float4 VY = reinterpret_cast<const float4*>(R.vy)[g];
+            float4 VZ = reinterpret_cast<const float4*>(R.vz)[g];
+            uint4 M = reinterpret_cast<const uint4*>(R.meta)[g];
+            uint32_t ck[4];
+            const uint32_t p0 = 4u * g;
+            step_particle(R, p0 + 0, step, X.x, Y.x, Z.x, VX.x, VY.x, VZ.x, M.x, T, ke, ck[0]);
+            step_particle(R, p0 + 1, step, X.y, Y.y, Z.y, VX.y, VY.y, VZ.y, M.y, T, ke, ck[1]);
+            step_particle(R, p0 + 2, step, X.z, Y.z, Z.z, VX.z, VY.z, VZ.z, M.z, T, ke, ck[2]);
+            step_particle(R, p0 + 3, step, X.w, Y.w, Z.w, VX.w, VY.w, VZ.w, M.w, T, ke, ck[3]);
+            __stcs(reinterpret_cast<float4*>(R.x) + g, X);
+            __stcs(reinterpret_cast<float4*>(R.y) + g, Y);
+            __stcs(reinterpret_cast<float4*>(R.z) + g, Z);
+            __stcs(reinterpret_cast<float4*>(R.vx) + g, VX);
+            __stcs(reinterpret_cast<float4*>(R.vy) + g, VY);
+            __stcs(reinterpret_cast<float4*>(R.vz) + g, VZ);
+            __stcs(reinterpret_cast<uint4*>(R.meta) + g, M);
+            if (R.flags & kFCoulomb)
+                reinterpret_cast<uint4*>(R.ckey)[g] = make_uint4(ck[0], ck[1], ck[2], ck[3]);
+        }
+        ke = warp_sum(ke);
+        if ((threadIdx.x & 31) == 0 && ke) atomicAdd(&T.ke, ke);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kQSlots; i += kThreads) {
+            if (T.ext[i]) atomicAdd(R.tally + kTallyExtracted + i, (unsigned long long)T.ext[i]);
+            if (T.lost[i]) atomicAdd(R.tally + kTallyLost + i, (unsigned long long)T.lost[i]);
+        }
+        if (threadIdx.x == 0 && T.ke) atomicAdd(R.tally + kTallyKe, T.ke);
+        __syncthreads();
+    }
+    if (bump_step) {
+        // the last block to finish advances every run's step counter
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned int prev = atomicAdd(ticket, 1u);
+            s_last = (prev == gridDim.x - 1) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_last) {
+            for (uint32_t r = threadIdx.x; r < nruns; r += kThreads) *runs[r].step += 1u;
+            if (threadIdx.x == 0) *ticket = 0u;
+        }
+    }
+}
+
+// Fold the packed per-step deposit into the time-summed count and charge
+// grids and clear it.
+__global__ void k_fold(const RunDev* __restrict__ runs, uint32_t run, uint32_t ncells,
+                       unsigned long long* __restrict__ count, unsigned long long* __restrict__ charge)
+{
+    const RunDev& R = runs[run];
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        const unsigned long long v = R.dep[c];
+        if (v) {
+            count[c] += v >> 32;
+            charge[c] += v & 0xFFFFFFFFull;
+            R.dep[c] = 0ull;
+        }
+    }
+}
+
+// Number of particles in the chamber per charge state.
+__global__ void k_census(const RunDev* __restrict__ runs, uint32_t run, uint32_t n4,
+                         unsigned long long* __restrict__ census)
+{
+    __shared__ unsigned int h[kQSlots];
+    for (int i = threadIdx.x; i < kQSlots; i += blockDim.x) h[i] = 0u;
+    __syncthreads();
+    const RunDev& R = runs[run];
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
+        const uint4 m = reinterpret_cast<const uint4*>(R.meta)[g];
+        const uint32_t mm[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (!(mm[j] & (kStFrozen | kStPad))) atomicAdd(&h[mm[j] & kQMask], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kQSlots; i += blockDim.x)
+        if (h[i]) atomicAdd(census + i, (unsigned long long)h[i]);
+}
+
+struct SoaPtrs { float* p[6]; };
+
+__global__ void k_load_init(LoadCheck lc, SoaPtrs soa, const uint8_t* __restrict__ q8,
+                            uint32_t* __restrict__ meta, uint32_t n, uint32_t cap,
+                            unsigned int* __restrict__ bad)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            const float x = soa.p[0][i], y = soa.p[1][i], z = soa.p[2][i];
+            const float vx = soa.p[3][i], vy = soa.p[4][i], vz = soa.p[5][i];
+            const uint32_t q = q8[i];
+            const bool ok = (x * x + y * y <= lc.R0sq) && (z >= 0.0f) && (z <= lc.L) &&
+                            isfinite(vx) && isfinite(vy) && isfinite(vz) && q <= lc.qmax;
+            if (!ok) {
+                atomicAdd(bad, 1u);
+                atomicMin(bad + 1, i);
+            }
+            meta[i] = q;
+        } else {
+            soa.p[0][i] = lc.inlet_x;
+            soa.p[1][i] = lc.inlet_y;
+            soa.p[2][i] = lc.inlet_z;
+            soa.p[3][i] = 0.0f;
+            soa.p[4][i] = 0.0f;
+            soa.p[5][i] = 0.0f;
+            meta[i] = kStPad;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_load_init(const LoadCheck& lc, float* const soa[6], const uint8_t* q8, uint32_t* meta,
+                             uint32_t n, uint32_t cap, unsigned int* bad, cudaStream_t s)
+{
+    SoaPtrs p;
+    for (int k = 0; k < 6; ++k) p.p[k] = soa[k];
+    const int threads = 256;
+    int blocks = (int)((cap + threads - 1) / threads);
+    if (blocks > 8192) blocks = 8192;
+    k_load_init<<<blocks, threads, 0, s>>>(lc, p, q8, meta, n, cap, bad);
+    return cudaGetLastError();
+}
+
+int step_blocks_per_sm()
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step, kThreads, 0) != cudaSuccess || b < 1) b = 1;
+    return b;
+}
+
+cudaError_t launch_step(const RunDev* runs_dev, const uint2* tiles_dev, uint32_t ntiles,
+                        uint32_t nruns, unsigned int* ticket, int bump_step, int grid,
+                        cudaStream_t s)
+{
+    if (ntiles == 0) return cudaSuccess;
+    if (grid > (int)ntiles) grid = (int)ntiles;
+    k_step<<<grid, kThreads, 0, s>>>(runs_dev, tiles_dev, ntiles, nruns, ticket, bump_step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold(const RunDev* runs_dev, uint32_t run, uint32_t ncells,
+                        unsigned long long* count, unsigned long long* charge, cudaStream_t s)
+{
+    const int threads = 256;
+    int blocks = (int)((ncells + threads - 1) / threads);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_fold<<<blocks, threads, 0, s>>>(runs_dev, run, ncells, count, charge);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_census(const RunDev* runs_dev, uint32_t run, uint32_t n4,
+                          unsigned long long* census, cudaStream_t s)
+{
+    const int threads = 256;
+    int blocks = (int)((n4 + threads - 1) / threads);
+    if (blocks > 2048) blocks = 2048;
+    if (blocks < 1) blocks = 1;
+    k_census<<<blocks, threads, 0, s>>>(runs_dev, run, n4, census);
+    return cudaGetLastError();
+}
+
+}  // namespace ecris

@@ -1,0 +1,254 @@
+"""Python binding of the ECRIS C ABI (include/ecris.h).
+
+Argument marshalling only: every step of the time step runs in the CUDA
+library libecris.so, which this module loads from the package directory.  If
+the library is missing, importing this module raises; there is no fallback.
+
+The functions `ecris_create`, `ecris_destroy`, `ecris_last_error`,
+`ecris_init_fields`, `ecris_load_ions`, `ecris_step`, `ecris_diag` and
+`ecris_get_state` carry the C names and signatures.  `Run` wraps them for one
+run described by `inputs.RunParams`, taking numpy arrays (host) or torch CUDA
+tensors (device) for the particle state.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libecris.so")
+
+ECRIS_OK, ECRIS_EINVAL, ECRIS_ENOMEM, ECRIS_ECUDA, ECRIS_ETIMEOUT, ECRIS_ESTATE = range(6)
+STATUS_NAMES = {0: "ECRIS_OK", 1: "ECRIS_EINVAL", 2: "ECRIS_ENOMEM", 3: "ECRIS_ECUDA",
+                4: "ECRIS_ETIMEOUT", 5: "ECRIS_ESTATE"}
+EV_WALL, EV_EXTRACT, EV_IONIZE, EV_CX, EV_COULOMB = (1 << 8, 1 << 9, 1 << 10, 1 << 11, 1 << 12)
+ST_FROZEN = 1 << 16
+
+
+class EcrisError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("R0", ctypes.c_double), ("L", ctypes.c_double), ("r_ap", ctypes.c_double),
+                ("inlet", ctypes.c_double * 3)]
+
+
+class BField(ctypes.Structure):
+    _fields_ = [("B_inj", ctypes.c_double), ("B_min", ctypes.c_double), ("B_ext", ctypes.c_double),
+                ("B_hex", ctypes.c_double), ("B_ecr", ctypes.c_double)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("E", ctypes.c_void_p), ("ne_in_cm3", ctypes.c_double),
+                ("ne_in_cells", ctypes.c_void_p), ("ne_out_cm3", ctypes.c_double),
+                ("Te_warm_eV", ctypes.c_double), ("Te_cold_eV", ctypes.c_double)]
+
+
+class Species(ctypes.Structure):
+    _fields_ = [("mass_amu", ctypes.c_double), ("qmax", ctypes.c_int32),
+                ("ip_eV", ctypes.c_void_p), ("n_outer", ctypes.c_void_p)]
+
+
+class Mcc(ctypes.Structure):
+    _fields_ = [("n0_cm3", ctypes.c_double), ("T0_eV", ctypes.c_double),
+                ("sigma1_cm2", ctypes.c_double), ("E_cx_eV", ctypes.c_double),
+                ("lnL_ii", ctypes.c_double), ("lnL_ei", ctypes.c_double),
+                ("ei_charge_power", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class DiagOut(ctypes.Structure):
+    _fields_ = [("qmax", ctypes.c_int32), ("steps", ctypes.c_uint64), ("time_s", ctypes.c_double),
+                ("extracted", ctypes.c_void_p), ("lost", ctypes.c_void_p),
+                ("alive_by_q", ctypes.c_void_p), ("current_A", ctypes.c_void_p),
+                ("ke_lost_eV", ctypes.c_double), ("power_W", ctypes.c_double),
+                ("coulomb_collisions", ctypes.c_int64),
+                ("cell_count", ctypes.c_void_p), ("cell_charge", ctypes.c_void_p)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("step_launches", ctypes.c_int64), ("step_ms", ctypes.c_double),
+                ("coulomb_launches", ctypes.c_int64), ("coulomb_ms", ctypes.c_double),
+                ("other_launches", ctypes.c_int64), ("other_ms", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library {LIB_PATH} is not built; run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    st = ctypes.c_int
+    lib.ecris_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, P]
+    lib.ecris_create.restype = st
+    lib.ecris_destroy.argtypes = [P]
+    lib.ecris_destroy.restype = None
+    lib.ecris_last_error.argtypes = [P]
+    lib.ecris_last_error.restype = ctypes.c_char_p
+    lib.ecris_init_fields.argtypes = [P, ctypes.POINTER(Geometry), ctypes.POINTER(BField),
+                                      ctypes.POINTER(Grid), ctypes.POINTER(Species), ctypes.POINTER(Mcc)]
+    lib.ecris_init_fields.restype = st
+    lib.ecris_load_ions.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(P), P, ctypes.c_double,
+                                    ctypes.c_uint64, ctypes.c_int]
+    lib.ecris_load_ions.restype = st
+    lib.ecris_step.argtypes = [P, ctypes.c_uint32, ctypes.c_double]
+    lib.ecris_step.restype = st
+    lib.ecris_diag.argtypes = [P, ctypes.POINTER(DiagOut)]
+    lib.ecris_diag.restype = st
+    lib.ecris_get_state.argtypes = [P, ctypes.POINTER(P), P, ctypes.c_int]
+    lib.ecris_get_state.restype = st
+    lib.ecris_set_profiling.argtypes = [P, ctypes.c_int]
+    lib.ecris_set_profiling.restype = st
+    lib.ecris_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
+    lib.ecris_get_profile.restype = st
+    return lib
+
+
+LIB = _load()
+
+# ---- the C entry points under their own names --------------------------------
+ecris_create = LIB.ecris_create
+ecris_destroy = LIB.ecris_destroy
+ecris_last_error = LIB.ecris_last_error
+ecris_init_fields = LIB.ecris_init_fields
+ecris_load_ions = LIB.ecris_load_ions
+ecris_step = LIB.ecris_step
+ecris_diag = LIB.ecris_diag
+ecris_get_state = LIB.ecris_get_state
+ecris_set_profiling = LIB.ecris_set_profiling
+ecris_get_profile = LIB.ecris_get_profile
+
+
+def check(ctx, status):
+    if status != ECRIS_OK:
+        msg = ecris_last_error(ctx)
+        raise EcrisError(status, msg.decode() if msg else "")
+    return status
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _is_device(a):
+    return not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False)
+
+
+def current_stream_handle():
+    """cudaStream_t of torch's current stream on the current device."""
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Run:
+    """One ECRIS run on one GPU: fields, particles, steps and diagnostics."""
+
+    def __init__(self, rp, E=None, ne_cells=None, device=0, stream=None):
+        self.rp = rp
+        self.ctx = ctypes.c_void_p()
+        st = ecris_create(ctypes.byref(self.ctx), int(device), stream)
+        if st != ECRIS_OK:
+            raise EcrisError(st, ecris_last_error(None).decode())
+        self._keep = []
+        self.init_fields(rp, E, ne_cells)
+
+    def close(self):
+        if self.ctx:
+            ecris_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fields(self, rp, E=None, ne_cells=None):
+        geo = Geometry(rp.R0, rp.L, rp.r_ap, (ctypes.c_double * 3)(*rp.inlet))
+        bf = BField(rp.B_inj, rp.B_min, rp.B_ext, rp.B_hex, rp.B_ecr)
+        Eh = None if E is None else np.ascontiguousarray(E, dtype=np.float32).reshape(-1)
+        nh = None if ne_cells is None else np.ascontiguousarray(ne_cells, dtype=np.float32)
+        grid = Grid(rp.nx, rp.ny, rp.nz, _ptr(Eh), rp.ne_in_cm3, _ptr(nh), rp.ne_out_cm3,
+                    rp.Te_warm_eV, rp.Te_cold_eV)
+        ip, nout = rp.species.ladder()
+        ip = np.ascontiguousarray(ip, np.float64)
+        nout = np.ascontiguousarray(nout, np.int32)
+        sp = Species(rp.species.mass_amu, rp.species.qmax, _ptr(ip), _ptr(nout))
+        mcc = Mcc(rp.n0_cm3, rp.T0_eV, rp.sigma1_cm2, rp.E_cx_eV, rp.lnL_ii, rp.lnL_ei,
+                  rp.ei_charge_power, rp.flags)
+        check(self.ctx, ecris_init_fields(self.ctx, ctypes.byref(geo), ctypes.byref(bf),
+                                          ctypes.byref(grid), ctypes.byref(sp), ctypes.byref(mcc)))
+        self.ncells = rp.nx * rp.ny * rp.nz
+        self.qmax = rp.species.qmax
+
+    def load(self, state, weight=None, seed=None):
+        """state: dict of x,y,z,vx,vy,vz (float32) and q (uint8), numpy or torch CUDA."""
+        rp = self.rp
+        arrs = [state[k] for k in ("x", "y", "z", "vx", "vy", "vz")]
+        q = state["q"]
+        dev = _is_device(arrs[0])
+        if not dev:
+            arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in arrs]
+            q = np.ascontiguousarray(q, dtype=np.uint8)
+        self._keep = arrs + [q]
+        n = len(arrs[0])
+        ptrs = (ctypes.c_void_p * 6)(*[_ptr(a) for a in arrs])
+        check(self.ctx, ecris_load_ions(self.ctx, n, ptrs, _ptr(q),
+                                        rp.weight if weight is None else weight,
+                                        rp.seed if seed is None else seed, 1 if dev else 0))
+        self.n = n
+
+    def step(self, nsteps=1, dt=None):
+        check(self.ctx, ecris_step(self.ctx, int(nsteps), self.rp.dt if dt is None else dt))
+
+    def diag(self, grids=False):
+        q1 = self.qmax + 1
+        ext = np.zeros(q1, np.int64)
+        lost = np.zeros(q1, np.int64)
+        alive = np.zeros(q1, np.int64)
+        cur = np.zeros(q1, np.float64)
+        cc = np.zeros(self.ncells, np.uint64) if grids else None
+        cq = np.zeros(self.ncells, np.uint64) if grids else None
+        out = DiagOut(0, 0, 0.0, _ptr(ext), _ptr(lost), _ptr(alive), _ptr(cur), 0.0, 0.0, 0,
+                      _ptr(cc), _ptr(cq))
+        check(self.ctx, ecris_diag(self.ctx, ctypes.byref(out)))
+        d = {"steps": out.steps, "time_s": out.time_s, "extracted": ext, "lost": lost,
+             "alive_by_q": alive, "current_A": cur, "ke_lost_eV": out.ke_lost_eV,
+             "power_W": out.power_W, "coulomb_collisions": out.coulomb_collisions}
+        if grids:
+            d["cell_count"], d["cell_charge"] = cc, cq
+        return d
+
+    def state(self):
+        n = self.n
+        arrs = [np.zeros(n, np.float32) for _ in range(6)]
+        meta = np.zeros(n, np.uint32)
+        ptrs = (ctypes.c_void_p * 6)(*[_ptr(a) for a in arrs])
+        check(self.ctx, ecris_get_state(self.ctx, ptrs, _ptr(meta), 0))
+        d = dict(zip(("x", "y", "z", "vx", "vy", "vz"), arrs))
+        d["meta"] = meta
+        d["q"] = (meta & 0xFF).astype(np.int32)
+        return d
+
+    def set_profiling(self, on=True):
+        check(self.ctx, ecris_set_profiling(self.ctx, 1 if on else 0))
+
+    def profile(self):
+        p = Profile()
+        check(self.ctx, ecris_get_profile(self.ctx, ctypes.byref(p)))
+        return {f: getattr(p, f) for f, _ in Profile._fields_}
+
+    def state_to_device(self, out):
+        """Copy the state into torch CUDA tensors out[x..vz] (float32) and out['meta'] (int32)."""
+        ptrs = (ctypes.c_void_p * 6)(*[_ptr(out[k]) for k in ("x", "y", "z", "vx", "vy", "vz")])
+        check(self.ctx, ecris_get_state(self.ctx, ptrs, _ptr(out.get("meta")), 1))

@@ -1,0 +1,176 @@
+"""GPU parity of the fused CUDA time step with the FP64 oracle (lock-step and
+free-run), through the C ABI.
+
+Sizes span several 1024-particle tiles and a ragged tail; the busy case drives
+every event type (wall hits, extraction, ionisation, charge exchange, the
+heating kick) with a non-zero E grid.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1507_03392_gb300 import inputs as I
+from tests import parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def E():
+    from paper_1507_03392_gb300 import ecris
+    return ecris
+
+
+def busy_case(n=3001, seed=4):
+    rp = I.RunParams(nx=16, ny=16, nz=32, ne_in_cm3=3e12, ne_out_cm3=3e11, n0_cm3=3e11,
+                     dt=3e-8, Te_warm_eV=500.0, flags=I.F_ALL_NO_COULOMB, seed=seed)
+    wl = I.Workload("busy", rp, n=n, steps=0, atom_fraction=0.4, ion_qmax_init=8,
+                    ion_T_eV=60.0, atoms_fill_chamber=True, zone_box=(0.02, 0.05, 0.29))
+    st = I.make_particles(wl, seed=seed)
+    Ef = I.make_efield(rp, 4e3, -2e3)
+    return rp, st, Ef
+
+
+def assert_clean(t):
+    assert t["q"] == 0 and t["events"] == 0 and t["pos"] == 0 and t["vel"] == 0, t
+
+
+def test_lockstep_busy_case_every_event_type(E):
+    rp, st, Ef = busy_case()
+    run = E.Run(rp, E=Ef)
+    run.load(st)
+    t, orc = P.lockstep(run, rp, st, 60, E=Ef)
+    assert_clean(t)
+    wall, ext, ion, cx = t["events_seen"]
+    assert wall > 50 and ion > 50 and cx > 5, t["events_seen"]
+    # tallies agree up to guarded boundary outcomes
+    d = run.diag()
+    assert np.abs(d["lost"] - orc.lost()).sum() <= t["guarded"]
+    assert np.abs(d["extracted"] - orc.extracted()).sum() <= t["guarded"]
+    assert d["ke_lost_eV"] == pytest.approx(orc.tally.ke_lost_eV, rel=1e-4)
+    run.close()
+
+
+def test_lockstep_small_config_1000_steps(E):
+    wl = I.config_small(n=10_000, steps=1000)
+    st = I.make_particles(wl)
+    run = E.Run(wl.params)
+    run.load(st)
+    t, orc = P.lockstep(run, wl.params, st, wl.steps)
+    assert_clean(t)
+    run.close()
+
+
+def test_free_run_small_config_flags_and_positions(E):
+    # 1e3 steps without re-synchronisation: integer outcomes identical for every
+    # particle never flagged near a decision surface, positions within 1e-5
+    wl = I.config_small(n=10_000, steps=1000)
+    rp = wl.params
+    st = I.make_particles(wl)
+    run = E.Run(rp)
+    run.load(st)
+    run.step(wl.steps)
+    g = run.state()
+    orc = O.OracleRun(rp, st)
+    orc.step(wl.steps, accumulate_guard=True)
+    ok = orc.guard_acc == 0
+    assert ok.mean() > 0.95
+    assert np.array_equal(g["q"][ok], orc.q[ok])
+    for k, sc in (("x", rp.R0), ("y", rp.R0), ("z", rp.L)):
+        rel = np.abs(g[k][ok] - getattr(orc, k)[ok]) / sc
+        assert rel.max() < 1e-5, (k, rel.max())
+    d = run.diag()
+    assert np.array_equal(d["lost"], orc.lost()) or np.abs(d["lost"] - orc.lost()).sum() <= (~ok).sum()
+    run.close()
+
+
+@pytest.mark.parametrize("n", [1, 3, 5, 1023, 1025, 4099])
+def test_ragged_sizes_lockstep(E, n):
+    rp, st, Ef = busy_case(n=n, seed=11 + n)
+    run = E.Run(rp, E=Ef)
+    run.load(st)
+    t, _ = P.lockstep(run, rp, st, 5, E=Ef)
+    assert_clean(t)
+    run.close()
+
+
+def test_empty_run(E):
+    rp, st, Ef = busy_case(n=0)
+    run = E.Run(rp, E=Ef)
+    run.load({k: v[:0] for k, v in st.items()})
+    run.step(3)
+    d = run.diag()
+    assert d["steps"] == 3 and d["alive_by_q"].sum() == 0
+    run.close()
+
+
+def test_census_deposit_and_conservation(E):
+    rp, st, Ef = busy_case(n=5000)
+    run = E.Run(rp, E=Ef)
+    run.load(st)
+    orc = O.OracleRun(rp, st, E=Ef)
+    steps = 20
+    run.step(steps)
+    orc.step(steps)
+    d = run.diag(grids=True)
+    assert d["alive_by_q"].sum() == 5000                      # recycling keeps N
+    assert int(d["cell_count"].sum()) == 5000 * steps         # every particle deposits once a step
+    g = run.state()
+    assert np.array_equal(np.bincount(g["q"], minlength=rp.species.qmax + 1), d["alive_by_q"])
+    assert int(d["cell_charge"].sum()) > 0
+    # deposit equals a brute-force histogram of the oracle within the few
+    # particles whose trajectories split near a decision surface
+    diff = np.abs(d["cell_count"].astype(np.int64) - orc.dep_count).sum()
+    assert diff <= 0.01 * 5000 * steps
+
+
+def test_no_recycling_accounting(E):
+    rp, st, Ef = busy_case(n=4000)
+    rp.flags = I.F_ALL_NO_COULOMB & ~I.F_RECYCLE
+    run = E.Run(rp, E=Ef)
+    run.load(st)
+    run.step(50)
+    d = run.diag()
+    g = run.state()
+    frozen = (g["meta"] & E.ST_FROZEN) != 0
+    assert d["alive_by_q"].sum() + d["extracted"].sum() + d["lost"].sum() == 4000
+    assert frozen.sum() == d["extracted"].sum() + d["lost"].sum() > 0
+    run.close()
+
+
+def test_invalid_inputs_rejected(E):
+    rp, st, Ef = busy_case(n=64)
+    run = E.Run(rp, E=Ef)
+    bad = {k: v.copy() for k, v in st.items()}
+    bad["x"][7] = 1.0            # outside the chamber
+    with pytest.raises(E.EcrisError) as ei:
+        run.load(bad)
+    assert ei.value.status == E.ECRIS_EINVAL and "first index 7" in str(ei.value)
+    with pytest.raises(E.EcrisError) as ei:
+        run.step(1)               # nothing valid loaded
+    assert ei.value.status == E.ECRIS_ESTATE
+    run.load(st)
+    with pytest.raises(E.EcrisError):
+        run.step(1, dt=-1.0)
+    run.step(1)
+    run.close()
+
+
+def test_power_and_currents_follow_the_tallies(E):
+    rp, st, Ef = busy_case(n=6000)
+    run = E.Run(rp, E=Ef)
+    run.load(st)
+    run.step(40)
+    d = run.diag()
+    t = d["time_s"]
+    assert t == pytest.approx(40 * rp.dt)
+    q = np.arange(rp.species.qmax + 1)
+    assert np.allclose(d["current_A"], q * 1.602176634e-19 * rp.weight * d["extracted"] / t)
+    ip, _ = rp.species.ladder()
+    ipcum = np.concatenate([[0.0], np.cumsum(ip)])
+    left = d["extracted"] + d["lost"]
+    e_ev = d["ke_lost_eV"] + (left[1:] * (ipcum[1:] + 1.5 * q[1:] * rp.Te_warm_eV)).sum()
+    assert d["power_W"] == pytest.approx(rp.weight * e_ev * 1.602176634e-19 / t, rel=1e-9)
+    run.close()
