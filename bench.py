@@ -125,7 +125,6 @@ class ClockSampler:
 def make_workload(rank, n=None):
     from paper_1507_03392_gb300 import inputs as I
     wl = I.config_scaled(seed=2 + rank)
-    wl.params.flags = I.F_ALL_NO_COULOMB   # collisions kernel not built yet
     if n is not None:
         wl.n = n
     return wl

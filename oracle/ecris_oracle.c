@@ -65,6 +65,7 @@
 #define OR_G_BOUNDARY 2u
 #define OR_G_IONIZE 4u
 #define OR_G_CX 8u
+#define OR_G_CELLREC 16u   /* near a cell face whose other side has different electron data */
 
 typedef struct {
     double R0, L, r_ap, inlet[3];
@@ -205,6 +206,39 @@ static int64_t or_cell(const or_params *p, double x, double y, double z, uint32_
     int iy = or_clampi((int)floor(gy), 0, p->ny - 1);
     int iz = or_clampi((int)floor(gz), 0, p->nz - 1);
     return ((int64_t)iz * p->ny + iy) * p->nx + ix;
+}
+
+/* 1 if a flip of the particle's cell across a face it lies within the guard
+ * distance of could change its outcome this step: the ionisation decision
+ * (word w0 against the probability from the other cell's n_e and zone) or,
+ * for an ion, the heating kick (the other cell's n_e, zone or delta). */
+static int or_cell_record_guard(const or_params *p, double x, double y, double z, int64_t c,
+                                const double *ne, const int32_t *zone, const double *dlx,
+                                const double *dly, const double *rates, int q_before, int q_after,
+                                uint32_t w0)
+{
+    const double tol = 1e-4;
+    double g[3] = {(x + p->R0) / or_dx(p), (y + p->R0) / or_dy(p), z / or_dz(p)};
+    int n[3] = {p->nx, p->ny, p->nz};
+    int64_t stride[3] = {1, p->nx, (int64_t)p->nx * p->ny};
+    int idx[3] = {(int)(c % p->nx), (int)((c / p->nx) % p->ny), (int)(c / ((int64_t)p->nx * p->ny))};
+    for (int k = 0; k < 3; ++k) {
+        double r = g[k] - floor(g[k] + 0.5);
+        if (fabs(r) >= tol) continue;
+        /* the nearest face is below the cell when g sits just above an integer */
+        int other = (g[k] - idx[k] < 0.5) ? idx[k] - 1 : idx[k] + 1;
+        if (other < 0 || other >= n[k]) continue;
+        int64_t c2 = c + (other - idx[k]) * stride[k];
+        if ((p->flags & OR_F_IONIZE) && q_before < p->qmax) {
+            double t1 = floor(or_threshold(-expm1(-ne[c] * rates[zone[c] * p->qmax + q_before] * p->dt)));
+            double t2 = floor(or_threshold(-expm1(-ne[c2] * rates[zone[c2] * p->qmax + q_before] * p->dt)));
+            if (((double)w0 < t1) != ((double)w0 < t2)) return 1;
+        }
+        if ((p->flags & OR_F_EIKICK) && q_after >= 1 &&
+            (ne[c2] != ne[c] || zone[c2] != zone[c] || dlx[c2] != dlx[c] || dly[c2] != dly[c]))
+            return 1;
+    }
+    return 0;
 }
 
 /* E at a position: trilinear interpolation between cell centres of the
@@ -662,6 +696,9 @@ void or_step(const or_params *p, const double *rates, const double *ne, const in
             if (dm > 0.0)
                 for (int k = 0; k < 3; ++k) v[k] += D * d[k] / dm;
         }
+        if ((guard[i] & OR_G_CELL) &&
+            or_cell_record_guard(p, x1, y1, z1, c, ne, zone, dlx, dly, rates, q[i], Q, w[0]))
+            guard[i] |= OR_G_CELLREC;
         q[i] = Q;
         vx[i] = v[0]; vy[i] = v[1]; vz[i] = v[2];
         if (Q >= 1) part[i] = 1;

@@ -20,7 +20,9 @@ LIB = os.path.join(HERE, "libecris_oracle.so")
 
 F_PUSH, F_IONIZE, F_CX, F_EIKICK, F_COULOMB, F_RECYCLE = 1, 2, 4, 8, 16, 32
 EV_WALL, EV_EXTRACT, EV_IONIZE, EV_CX, EV_COULOMB = 1, 2, 4, 8, 16
-G_CELL, G_BOUNDARY, G_IONIZE, G_CX = 1, 2, 4, 8
+G_CELL, G_BOUNDARY, G_IONIZE, G_CX, G_CELLREC = 1, 2, 4, 8, 16
+# guards that can change a single-particle outcome (no Coulomb pairing)
+G_SINGLE = G_BOUNDARY | G_IONIZE | G_CX | G_CELLREC
 QMAX_SLOTS = 64
 
 

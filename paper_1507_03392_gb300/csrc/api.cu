@@ -151,7 +151,6 @@ struct ecris_ctx {
     bool loaded = false;        // a valid ensemble is loaded
     size_t cap = 0, cap_cells = 0;
     size_t n = 0, n4 = 0;
-    std::vector<uint2> tiles_h;
     uint8_t* d_q8 = nullptr;
     unsigned int* d_bad = nullptr;
     uint32_t* d_crank = nullptr;
@@ -172,10 +171,8 @@ struct ecris_ctx {
     unsigned long long* d_census = nullptr;
     uint32_t* d_step = nullptr;
     unsigned int* d_ticket = nullptr;
-    RunDev* d_run = nullptr;
-    uint2* d_tiles = nullptr;
     uint32_t ntiles = 0;
-    RunDev* h_run = nullptr;    // pinned staging copy of the parameter block
+    RunDev* h_run = nullptr;    // parameter block passed by value to every kernel
     float* h_kdt = nullptr;     // pinned staging copy of the rate table
     double weight = 0.0;
     uint64_t seed = 0;
@@ -280,8 +277,6 @@ void free_ions(ecris_ctx* ctx)
     free_async(ctx, ctx->d_census);
     free_async(ctx, ctx->d_step);
     free_async(ctx, ctx->d_ticket);
-    free_async(ctx, ctx->d_run);
-    free_async(ctx, ctx->d_tiles);
     free_async(ctx, ctx->d_q8);
     free_async(ctx, ctx->d_bad);
     free_async(ctx, ctx->d_crank);
@@ -401,7 +396,6 @@ ecris_status upload_dt(ecris_ctx* ctx, double dt)
     for (int zone = 0; zone < 2; ++zone)
         for (int q = 0; q < kQSlots; ++q)
             ctx->h_kdt[zone * kQSlots + q] = q < ctx->h.qmax ? (float)(ctx->h.rate[zone][q] * dt) : 0.0f;
-    CK(cudaMemcpyAsync(ctx->d_run, ctx->h_run, sizeof(RunDev), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_kdt, ctx->h_kdt, 2 * kQSlots * sizeof(float), cudaMemcpyHostToDevice,
                        ctx->stream));
     ctx->dt_loaded = dt;
@@ -646,8 +640,6 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         CK(cudaMallocAsync((void**)&ctx->d_step, sizeof(uint32_t), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_ticket, sizeof(unsigned int), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_bad, 2 * sizeof(unsigned int), ctx->stream));
-        CK(cudaMallocAsync((void**)&ctx->d_run, sizeof(RunDev), ctx->stream));
-        CK(cudaMallocAsync((void**)&ctx->d_tiles, (cap / kTile + 1) * sizeof(uint2), ctx->stream));
         if (h.mcc.flags & kFCoulomb) {
             CK(cudaMallocAsync((void**)&ctx->d_crank, cap * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_ckeys, cap * sizeof(unsigned long long), ctx->stream));
@@ -665,16 +657,12 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
     ctx->n = n;
     ctx->n4 = n4;
     ctx->ntiles = (uint32_t)((n4 + kThreads - 1) / kThreads);
-    ctx->tiles_h.resize(ctx->ntiles > 0 ? ctx->ntiles : 1);
-    for (uint32_t t = 0; t < ctx->ntiles; ++t) ctx->tiles_h[t] = make_uint2(0u, t * (uint32_t)kThreads);
     const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (n) {
         for (int k = 0; k < 6; ++k)
             CK(cudaMemcpyAsync(ctx->d_soa[k], xyzv[k], n * sizeof(float), kind, ctx->stream));
         CK(cudaMemcpyAsync(ctx->d_q8, q, n, kind, ctx->stream));
     }
-    CK(cudaMemcpyAsync(ctx->d_tiles, ctx->tiles_h.data(), ctx->tiles_h.size() * sizeof(uint2),
-                       cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_ckey, 0xFF, cap * sizeof(uint32_t), ctx->stream));
     if (ctx->d_ccount) CK(cudaMemsetAsync(ctx->d_ccount, 0, nc * sizeof(uint32_t), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_dep, 0, nc * sizeof(unsigned long long), ctx->stream));
@@ -738,18 +726,18 @@ ecris_status ecris_step(ecris_ctx* ctx, uint32_t nsteps, double dt)
     const uint32_t nc = (uint32_t)((size_t)ctx->h.nx * ctx->h.ny * ctx->h.nz);
     for (uint32_t s = 0; s < nsteps; ++s) {
         CK(timed(ctx, kKindStep, [&] {
-            return launch_step(ctx->d_run, ctx->d_tiles, ctx->ntiles, 1, ctx->d_ticket, coulomb ? 0 : 1,
-                               ctx->step_grid, ctx->stream);
+            return launch_step(*ctx->h_run, ctx->ntiles, ctx->d_ticket, coulomb ? 0 : 1, ctx->step_grid,
+                               ctx->stream);
         }));
         if (coulomb) {
             CK(timed(ctx, kKindCoulomb, [&] {
-                return launch_coulomb(ctx->d_run, 0, nc, (uint32_t)ctx->n4, ctx->d_ticket, ctx->collide_grid,
-                                      nullptr, ctx->stream);
+                return launch_coulomb(*ctx->h_run, nc, (uint32_t)ctx->n4, ctx->d_ticket, ctx->collide_grid,
+                                      ctx->stream);
             }, kCoulombKernels));
         }
         if (++ctx->since_fold >= ctx->fold_every) {
             CK(timed(ctx, kKindOther, [&] {
-                return launch_fold(ctx->d_run, 0, nc, ctx->d_count, ctx->d_charge, ctx->stream);
+                return launch_fold(*ctx->h_run, nc, ctx->d_count, ctx->d_charge, ctx->stream);
             }));
             ctx->since_fold = 0;
         }
@@ -772,10 +760,10 @@ ecris_status ecris_diag(ecris_ctx* ctx, ecris_diag_out* out)
         ecris_status st = upload_dt(ctx, 1e-9);   // parameter block for the census kernel
         if (st != ECRIS_OK) return st;
     }
-    CK(launch_fold(ctx->d_run, 0, (uint32_t)nc, ctx->d_count, ctx->d_charge, ctx->stream));
+    CK(launch_fold(*ctx->h_run, (uint32_t)nc, ctx->d_count, ctx->d_charge, ctx->stream));
     ctx->since_fold = 0;
     CK(cudaMemsetAsync(ctx->d_census, 0, kQSlots * sizeof(unsigned long long), ctx->stream));
-    CK(launch_census(ctx->d_run, 0, (uint32_t)ctx->n4, ctx->d_census, ctx->stream));
+    CK(launch_census(*ctx->h_run, (uint32_t)ctx->n4, ctx->d_census, ctx->stream));
     unsigned long long tally[kTallyWords], census[kQSlots];
     CK(cudaMemcpyAsync(tally, ctx->d_tally, sizeof tally, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(census, ctx->d_census, sizeof census, cudaMemcpyDeviceToHost, ctx->stream));

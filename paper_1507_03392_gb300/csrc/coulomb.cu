@@ -44,10 +44,8 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
 }
 
 // pass A: block-local exclusive scan of ccount into coff, block totals to cblk
-__global__ void __launch_bounds__(kScanThreads) k_scan_a(const RunDev* __restrict__ runs, uint32_t run,
-                                                         uint32_t ncells)
+__global__ void __launch_bounds__(kScanThreads) k_scan_a(const __grid_constant__ RunDev R, uint32_t ncells)
 {
-    const RunDev& R = runs[run];
     __shared__ uint32_t wsum[kScanThreads / 32];
     const uint32_t base = blockIdx.x * kScanBlock + threadIdx.x * kScanPerThread;
     uint32_t v[kScanPerThread];
@@ -79,10 +77,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_a(const RunDev* __restric
 }
 
 // pass B: one block scans the block totals in place; coff[ncells] = total
-__global__ void __launch_bounds__(1024) k_scan_b(const RunDev* __restrict__ runs, uint32_t run,
-                                                 uint32_t nblocks, uint32_t ncells)
+__global__ void __launch_bounds__(1024) k_scan_b(const __grid_constant__ RunDev R, uint32_t nblocks,
+                                                 uint32_t ncells)
 {
-    const RunDev& R = runs[run];
     __shared__ uint32_t wsum[32];
     const uint32_t per = (nblocks + 1023) / 1024;
     const uint32_t base = threadIdx.x * per;
@@ -114,10 +111,8 @@ __global__ void __launch_bounds__(1024) k_scan_b(const RunDev* __restrict__ runs
 }
 
 // pass C: add block offsets, clear the counts, list cells with >= 2 ions
-__global__ void __launch_bounds__(kScanThreads) k_scan_c(const RunDev* __restrict__ runs, uint32_t run,
-                                                         uint32_t ncells)
+__global__ void __launch_bounds__(kScanThreads) k_scan_c(const __grid_constant__ RunDev R, uint32_t ncells)
 {
-    const RunDev& R = runs[run];
     const uint32_t add = R.cblk[blockIdx.x];
     const uint32_t base = blockIdx.x * kScanBlock;
     for (uint32_t j = threadIdx.x; j < (uint32_t)kScanBlock; j += kScanThreads) {
@@ -133,9 +128,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_c(const RunDev* __restric
 }
 
 // scatter the pairing keys of the participants into their cell's segment
-__global__ void k_scatter(const RunDev* __restrict__ runs, uint32_t run, uint32_t n4)
+__global__ void k_scatter(const __grid_constant__ RunDev R, uint32_t n4)
 {
-    const RunDev& R = runs[run];
     const uint32_t step = *R.step;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
         const uint4 k4 = reinterpret_cast<const uint4*>(R.ckey)[g];
@@ -240,12 +234,11 @@ __device__ void warp_bitonic(unsigned long long* buf, uint32_t m)
     }
 }
 
-__global__ void __launch_bounds__(kCollideThreads) k_collide(const RunDev* __restrict__ runs, uint32_t run,
+__global__ void __launch_bounds__(kCollideThreads) k_collide(const __grid_constant__ RunDev R,
                                                              unsigned int* ticket)
 {
     __shared__ unsigned long long sk[kCollideWarps][kSmemKeys];
     __shared__ int s_last;
-    const RunDev& R = runs[run];
     const uint32_t step = *R.step;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint32_t nocc = *R.occ_n;
@@ -319,19 +312,18 @@ __global__ void __launch_bounds__(kCollideThreads) k_collide(const RunDev* __res
 
 int coulomb_scan_blocks(uint32_t ncells) { return (int)((ncells + kScanBlock - 1) / kScanBlock); }
 
-cudaError_t launch_coulomb(const RunDev* runs_dev, uint32_t run, uint32_t ncells, uint32_t n4,
-                           unsigned int* ticket, int grid, int* kernels, cudaStream_t s)
+cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t n4, unsigned int* ticket, int grid,
+                           cudaStream_t s)
 {
     const int nb = coulomb_scan_blocks(ncells);
-    k_scan_a<<<nb, kScanThreads, 0, s>>>(runs_dev, run, ncells);
-    k_scan_b<<<1, 1024, 0, s>>>(runs_dev, run, (uint32_t)nb, ncells);
-    k_scan_c<<<nb, kScanThreads, 0, s>>>(runs_dev, run, ncells);
+    k_scan_a<<<nb, kScanThreads, 0, s>>>(R, ncells);
+    k_scan_b<<<1, 1024, 0, s>>>(R, (uint32_t)nb, ncells);
+    k_scan_c<<<nb, kScanThreads, 0, s>>>(R, ncells);
     int sb = (int)((n4 + 255) / 256);
     if (sb > 8192) sb = 8192;
     if (sb < 1) sb = 1;
-    k_scatter<<<sb, 256, 0, s>>>(runs_dev, run, n4);
-    k_collide<<<grid, kCollideThreads, 0, s>>>(runs_dev, run, ticket);
-    if (kernels) *kernels = 5;
+    k_scatter<<<sb, 256, 0, s>>>(R, n4);
+    k_collide<<<grid, kCollideThreads, 0, s>>>(R, ticket);
     return cudaGetLastError();
 }
 

@@ -224,23 +224,12 @@ __device__ __forceinline__ uint32_t ngp_cell(const RunDev& R, float x, float y, 
 // ----------------------------------------------------------------------------
 // Launch wrappers (defined in step_kernel.cu / coulomb.cu)
 // ----------------------------------------------------------------------------
-// tiles[t] = (run index, first float4 group of the tile)
-cudaError_t launch_step(const RunDev* runs_dev, const uint2* tiles_dev, uint32_t ntiles,
-                        uint32_t nruns, unsigned int* ticket, int bump_step, int grid,
+// one pass of the fused step kernel over the run's ntiles tiles of kTile
+// particles; bump_step: the last block advances the run's step counter
+cudaError_t launch_step(const RunDev& R, uint32_t ntiles, unsigned int* ticket, int bump_step, int grid,
                         cudaStream_t s);
-// Coulomb collisions of one run for the current step (after launch_step with
-// bump_step = 0): scan of the cell counts, scatter of the pairing keys, and
-// the per-cell sort / pair / collide kernel, whose last block advances the
-// step counter.  `kernels` receives the number of launches made.
-constexpr int kCoulombKernels = 5;   // kernels per launch_coulomb
-cudaError_t launch_coulomb(const RunDev* runs_dev, uint32_t run, uint32_t ncells, uint32_t n4,
-                           unsigned int* ticket, int grid, int* kernels, cudaStream_t s);
-int coulomb_scan_blocks(uint32_t ncells);
-
-// resident blocks per SM of the step kernel
-int step_blocks_per_sm();
-cudaError_t launch_fold(const RunDev* runs_dev, uint32_t run, uint32_t ncells,
-                        unsigned long long* count, unsigned long long* charge, cudaStream_t s);
+cudaError_t launch_fold(const RunDev& R, uint32_t ncells, unsigned long long* count,
+                        unsigned long long* charge, cudaStream_t s);
 // validity limits and padding point for ecris_load_ions
 struct LoadCheck {
     float R0sq, L;
@@ -251,7 +240,17 @@ struct LoadCheck {
 // bad[0] counts invalid particles, bad[1] holds the lowest invalid index
 cudaError_t launch_load_init(const LoadCheck& lc, float* const soa[6], const uint8_t* q8, uint32_t* meta,
                              uint32_t n, uint32_t cap, unsigned int* bad, cudaStream_t s);
-cudaError_t launch_census(const RunDev* runs_dev, uint32_t run, uint32_t n4,
-                          unsigned long long* census, cudaStream_t s);
+cudaError_t launch_census(const RunDev& R, uint32_t n4, unsigned long long* census, cudaStream_t s);
+// resident blocks per SM of the step kernel
+int step_blocks_per_sm();
+
+// Coulomb collisions of one run for the current step (after launch_step with
+// bump_step = 0): scan of the cell counts, scatter of the pairing keys, and
+// the per-cell sort / pair / collide kernel, whose last block advances the
+// step counter.
+constexpr int kCoulombKernels = 5;   // kernels per launch_coulomb
+cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t n4, unsigned int* ticket, int grid,
+                           cudaStream_t s);
+int coulomb_scan_blocks(uint32_t ncells);
 
 }  // namespace ecris

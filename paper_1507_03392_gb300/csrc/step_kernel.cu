@@ -212,77 +212,142 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
     return v;
 }
 
-__global__ void __launch_bounds__(kThreads) k_step(const RunDev* __restrict__ runs,
-                                                   const uint2* __restrict__ tiles, uint32_t ntiles,
-                                                   uint32_t nruns, unsigned int* ticket,
-                                                   int bump_step)
+// Shared-memory stage of one tile: SoA copies of the tile's particles and the
+// processing order (ions first, then atoms), so that every warp runs one kind
+// of particle at a time instead of both paths for every lane.
+struct TileStage {
+    float4 x[kThreads], y[kThreads], z[kThreads], vx[kThreads], vy[kThreads], vz[kThreads];
+    uint4 meta[kThreads];
+    uint4 ckey[kThreads];
+    uint16_t order[kTile];
+    uint32_t warp_ions[kThreads / 32], warp_atoms[kThreads / 32];
+    BlockTally T;
+    int last;
+};
+
+__device__ __forceinline__ float& sf(float4* a, uint32_t i) { return reinterpret_cast<float*>(a)[i]; }
+__device__ __forceinline__ uint32_t& su(uint4* a, uint32_t i) { return reinterpret_cast<uint32_t*>(a)[i]; }
+
+// One pass over the tiles of a run.  Each tile of 1024 particles is loaded
+// with 128-bit coalesced loads into shared memory, the live particles are
+// ordered ions first (their push needs the field evaluation), each thread then
+// advances the particles at order[tid], order[tid + 256], ..., and the tile is
+// written back with 128-bit streaming stores.
+__global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ RunDev R, uint32_t ntiles,
+                                                      unsigned int* ticket, int bump_step)
 {
-    __shared__ BlockTally T;
-    __shared__ int s_last;
+    __shared__ TileStage S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool coulomb = (R.flags & kFCoulomb) != 0;
+    const uint32_t step = *R.step;
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint2 tile = tiles[t];
-        const RunDev& R = runs[tile.x];
-        for (int i = threadIdx.x; i < kQSlots; i += kThreads) { T.ext[i] = 0u; T.lost[i] = 0u; }
-        if (threadIdx.x == 0) T.ke = 0ull;
+        for (int i = tid; i < kQSlots; i += kThreads) { S.T.ext[i] = 0u; S.T.lost[i] = 0u; }
+        if (tid == 0) S.T.ke = 0ull;
+        const uint32_t g = t * kThreads + tid;
+        const bool valid = g < R.n4;
+        uint4 M = make_uint4(kStPad, kStPad, kStPad, kStPad);
+        if (valid) {
+            S.x[tid] = reinterpret_cast<const float4*>(R.x)[g];
+            S.y[tid] = reinterpret_cast<const float4*>(R.y)[g];
+            S.z[tid] = reinterpret_cast<const float4*>(R.z)[g];
+            S.vx[tid] = reinterpret_cast<const float4*>(R.vx)[g];
+            S.vy[tid] = reinterpret_cast<const float4*>(R.vy)[g];
+            S.vz[tid] = reinterpret_cast<const float4*>(R.vz)[g];
+            M = reinterpret_cast<const uint4*>(R.meta)[g];
+        }
+        S.meta[tid] = M;
+        S.ckey[tid] = make_uint4(kNoCell, kNoCell, kNoCell, kNoCell);
+        // classify: live ions, live atoms (frozen and padding slots are left alone)
+        const uint32_t mm[4] = {M.x, M.y, M.z, M.w};
+        uint32_t nion = 0, natom = 0;
+        bool is_ion[4], live[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            live[j] = !(mm[j] & (kStFrozen | kStPad));
+            is_ion[j] = live[j] && (mm[j] & kQMask) != 0u;
+            nion += is_ion[j];
+            natom += live[j] && !is_ion[j];
+        }
+        // warp-inclusive scans of the per-thread counts
+        uint32_t ion_incl = nion, atom_incl = natom;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t a = __shfl_up_sync(0xFFFFFFFFu, ion_incl, o);
+            const uint32_t b = __shfl_up_sync(0xFFFFFFFFu, atom_incl, o);
+            if (lane >= o) { ion_incl += a; atom_incl += b; }
+        }
+        if (lane == 31) { S.warp_ions[warp] = ion_incl; S.warp_atoms[warp] = atom_incl; }
         __syncthreads();
-        const uint32_t step = *R.step;
-        const uint32_t g = tile.y + threadIdx.x;
+        uint32_t ion_base = 0, atom_base = 0, ion_tot = 0, atom_tot = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const uint32_t wi = S.warp_ions[w], wa = S.warp_atoms[w];
+            if (w < warp) { ion_base += wi; atom_base += wa; }
+            ion_tot += wi;
+            atom_tot += wa;
+        }
+        uint32_t pi = ion_base + ion_incl - nion;
+        uint32_t pa = ion_tot + atom_base + atom_incl - natom;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (is_ion[j]) S.order[pi++] = (uint16_t)(4 * tid + j);
+            else if (live[j]) S.order[pa++] = (uint16_t)(4 * tid + j);
+        }
+        __syncthreads();
+        const uint32_t nlive = ion_tot + atom_tot;
+        const uint32_t pid0 = t * kTile;
         unsigned long long ke = 0ull;
-        if (g < R.n4) {
-            float4 X = reinterpret_cast<const float4*>(R.x)[g];
-            float4 Y = reinterpret_cast<const float4*>(R.y)[g];
-            float4 Z = reinterpret_cast<const float4*>(R.z)[g];
-            float4 VX = reinterpret_cast<const float4*>(R.vx)[g];
-            float4 VY = reinterpret_cast<const float4*>(R.vy)[g];
-            float4 VZ = reinterpret_cast<const float4*>(R.vz)[g];
-            uint4 M = reinterpret_cast<const uint4*>(R.meta)[g];
-            uint32_t ck[4];
-            const uint32_t p0 = 4u * g;
-            step_particle(R, p0 + 0, step, X.x, Y.x, Z.x, VX.x, VY.x, VZ.x, M.x, T, ke, ck[0]);
-            step_particle(R, p0 + 1, step, X.y, Y.y, Z.y, VX.y, VY.y, VZ.y, M.y, T, ke, ck[1]);
-            step_particle(R, p0 + 2, step, X.z, Y.z, Z.z, VX.z, VY.z, VZ.z, M.z, T, ke, ck[2]);
-            step_particle(R, p0 + 3, step, X.w, Y.w, Z.w, VX.w, VY.w, VZ.w, M.w, T, ke, ck[3]);
-            __stcs(reinterpret_cast<float4*>(R.x) + g, X);
-            __stcs(reinterpret_cast<float4*>(R.y) + g, Y);
-            __stcs(reinterpret_cast<float4*>(R.z) + g, Z);
-            __stcs(reinterpret_cast<float4*>(R.vx) + g, VX);
-            __stcs(reinterpret_cast<float4*>(R.vy) + g, VY);
-            __stcs(reinterpret_cast<float4*>(R.vz) + g, VZ);
-            __stcs(reinterpret_cast<uint4*>(R.meta) + g, M);
-            if (R.flags & kFCoulomb)
-                reinterpret_cast<uint4*>(R.ckey)[g] = make_uint4(ck[0], ck[1], ck[2], ck[3]);
+        for (uint32_t i = tid; i < nlive; i += kThreads) {
+            const uint32_t k = S.order[i];
+            float x = sf(S.x, k), y = sf(S.y, k), z = sf(S.z, k);
+            float vx = sf(S.vx, k), vy = sf(S.vy, k), vz = sf(S.vz, k);
+            uint32_t meta = su(S.meta, k), ck;
+            step_particle(R, pid0 + k, step, x, y, z, vx, vy, vz, meta, S.T, ke, ck);
+            sf(S.x, k) = x; sf(S.y, k) = y; sf(S.z, k) = z;
+            sf(S.vx, k) = vx; sf(S.vy, k) = vy; sf(S.vz, k) = vz;
+            su(S.meta, k) = meta;
+            if (coulomb) su(S.ckey, k) = ck;
         }
         ke = warp_sum(ke);
-        if ((threadIdx.x & 31) == 0 && ke) atomicAdd(&T.ke, ke);
+        if (lane == 0 && ke) atomicAdd(&S.T.ke, ke);
         __syncthreads();
-        for (int i = threadIdx.x; i < kQSlots; i += kThreads) {
-            if (T.ext[i]) atomicAdd(R.tally + kTallyExtracted + i, (unsigned long long)T.ext[i]);
-            if (T.lost[i]) atomicAdd(R.tally + kTallyLost + i, (unsigned long long)T.lost[i]);
+        if (valid) {
+            __stcs(reinterpret_cast<float4*>(R.x) + g, S.x[tid]);
+            __stcs(reinterpret_cast<float4*>(R.y) + g, S.y[tid]);
+            __stcs(reinterpret_cast<float4*>(R.z) + g, S.z[tid]);
+            __stcs(reinterpret_cast<float4*>(R.vx) + g, S.vx[tid]);
+            __stcs(reinterpret_cast<float4*>(R.vy) + g, S.vy[tid]);
+            __stcs(reinterpret_cast<float4*>(R.vz) + g, S.vz[tid]);
+            __stcs(reinterpret_cast<uint4*>(R.meta) + g, S.meta[tid]);
+            if (coulomb) reinterpret_cast<uint4*>(R.ckey)[g] = S.ckey[tid];
         }
-        if (threadIdx.x == 0 && T.ke) atomicAdd(R.tally + kTallyKe, T.ke);
+        for (int i = tid; i < kQSlots; i += kThreads) {
+            if (S.T.ext[i]) atomicAdd(R.tally + kTallyExtracted + i, (unsigned long long)S.T.ext[i]);
+            if (S.T.lost[i]) atomicAdd(R.tally + kTallyLost + i, (unsigned long long)S.T.lost[i]);
+        }
+        if (tid == 0 && S.T.ke) atomicAdd(R.tally + kTallyKe, S.T.ke);
         __syncthreads();
     }
     if (bump_step) {
-        // the last block to finish advances every run's step counter
-        if (threadIdx.x == 0) {
+        // the last block to finish advances the run's step counter
+        if (tid == 0) {
             __threadfence();
             const unsigned int prev = atomicAdd(ticket, 1u);
-            s_last = (prev == gridDim.x - 1) ? 1 : 0;
+            S.last = (prev == gridDim.x - 1) ? 1 : 0;
         }
         __syncthreads();
-        if (s_last) {
-            for (uint32_t r = threadIdx.x; r < nruns; r += kThreads) *runs[r].step += 1u;
-            if (threadIdx.x == 0) *ticket = 0u;
+        if (S.last && tid == 0) {
+            *R.step += 1u;
+            *ticket = 0u;
         }
     }
 }
 
 // Fold the packed per-step deposit into the time-summed count and charge
 // grids and clear it.
-__global__ void k_fold(const RunDev* __restrict__ runs, uint32_t run, uint32_t ncells,
+__global__ void k_fold(const __grid_constant__ RunDev R, uint32_t ncells,
                        unsigned long long* __restrict__ count, unsigned long long* __restrict__ charge)
 {
-    const RunDev& R = runs[run];
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
         const unsigned long long v = R.dep[c];
         if (v) {
@@ -294,13 +359,12 @@ __global__ void k_fold(const RunDev* __restrict__ runs, uint32_t run, uint32_t n
 }
 
 // Number of particles in the chamber per charge state.
-__global__ void k_census(const RunDev* __restrict__ runs, uint32_t run, uint32_t n4,
+__global__ void k_census(const __grid_constant__ RunDev R, uint32_t n4,
                          unsigned long long* __restrict__ census)
 {
     __shared__ unsigned int h[kQSlots];
     for (int i = threadIdx.x; i < kQSlots; i += blockDim.x) h[i] = 0u;
     __syncthreads();
-    const RunDev& R = runs[run];
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
         const uint4 m = reinterpret_cast<const uint4*>(R.meta)[g];
         const uint32_t mm[4] = {m.x, m.y, m.z, m.w};
@@ -364,35 +428,33 @@ int step_blocks_per_sm()
     return b;
 }
 
-cudaError_t launch_step(const RunDev* runs_dev, const uint2* tiles_dev, uint32_t ntiles,
-                        uint32_t nruns, unsigned int* ticket, int bump_step, int grid,
+cudaError_t launch_step(const RunDev& R, uint32_t ntiles, unsigned int* ticket, int bump_step, int grid,
                         cudaStream_t s)
 {
     if (ntiles == 0) return cudaSuccess;
     if (grid > (int)ntiles) grid = (int)ntiles;
-    k_step<<<grid, kThreads, 0, s>>>(runs_dev, tiles_dev, ntiles, nruns, ticket, bump_step);
+    k_step<<<grid, kThreads, 0, s>>>(R, ntiles, ticket, bump_step);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fold(const RunDev* runs_dev, uint32_t run, uint32_t ncells,
-                        unsigned long long* count, unsigned long long* charge, cudaStream_t s)
+cudaError_t launch_fold(const RunDev& R, uint32_t ncells, unsigned long long* count, unsigned long long* charge,
+                        cudaStream_t s)
 {
     const int threads = 256;
     int blocks = (int)((ncells + threads - 1) / threads);
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    k_fold<<<blocks, threads, 0, s>>>(runs_dev, run, ncells, count, charge);
+    k_fold<<<blocks, threads, 0, s>>>(R, ncells, count, charge);
     return cudaGetLastError();
 }
 
-cudaError_t launch_census(const RunDev* runs_dev, uint32_t run, uint32_t n4,
-                          unsigned long long* census, cudaStream_t s)
+cudaError_t launch_census(const RunDev& R, uint32_t n4, unsigned long long* census, cudaStream_t s)
 {
     const int threads = 256;
     int blocks = (int)((n4 + threads - 1) / threads);
     if (blocks > 2048) blocks = 2048;
     if (blocks < 1) blocks = 1;
-    k_census<<<blocks, threads, 0, s>>>(runs_dev, run, n4, census);
+    k_census<<<blocks, threads, 0, s>>>(R, n4, census);
     return cudaGetLastError();
 }
 

@@ -16,16 +16,37 @@ import numpy as np
 from oracle import oracle as O
 
 KEYS = ("x", "y", "z", "vx", "vy", "vz")
-EV_MASK = 0xF  # wall, extract, ionise, cx
+EV_MASK = 0x1F  # wall, extract, ionise, cx, coulomb
 
 
 class Mismatch(AssertionError):
     pass
 
 
-def compare_step(rp, g1, orc, pos_rel=1e-6, vel_rel=1e-5, v_floor=None):
-    """Compare one GPU step (g1 = state after) with the oracle that took the same step."""
-    ok = orc.guard == 0
+def coulomb_guard(rp, orc):
+    """Particles whose Coulomb partners may differ: every ion in a cell (or a
+    neighbouring cell) that holds an ion flagged near any decision surface."""
+    dx, dy, dz = 2 * rp.R0 / rp.nx, 2 * rp.R0 / rp.ny, rp.L / rp.nz
+    ix = np.clip(np.floor((orc.x + rp.R0) / dx).astype(np.int64), 0, rp.nx - 1)
+    iy = np.clip(np.floor((orc.y + rp.R0) / dy).astype(np.int64), 0, rp.ny - 1)
+    iz = np.clip(np.floor(orc.z / dz).astype(np.int64), 0, rp.nz - 1)
+    bad = np.zeros((rp.nz + 2, rp.ny + 2, rp.nx + 2), dtype=bool)
+    g = (orc.guard != 0) & (orc.q >= 1)
+    for ox in (0, 1, 2):
+        for oy in (0, 1, 2):
+            for oz in (0, 1, 2):
+                bad[iz[g] + oz, iy[g] + oy, ix[g] + ox] = True
+    return bad[iz + 1, iy + 1, ix + 1] & (orc.q >= 1)
+
+
+def compare_step(rp, g1, orc, pos_rel=1e-6, vel_rel=1e-5, v_floor=None, mask=O.G_SINGLE):
+    """Compare one GPU step (g1 = state after) with the oracle that took the same step.
+
+    `mask` selects the guard bits that excuse a particle; with Coulomb
+    collisions on, every ion near a flagged ion is excused as well."""
+    ok = (orc.guard & mask) == 0
+    if rp.flags & O.F_COULOMB:
+        ok &= (orc.guard == 0) & ~coulomb_guard(rp, orc)
     q_bad = (g1["q"] != orc.q) & ok
     ev_g = (g1["meta"] >> 8) & EV_MASK
     ev_bad = (ev_g != (orc.events & EV_MASK)) & ok
@@ -46,7 +67,7 @@ def compare_step(rp, g1, orc, pos_rel=1e-6, vel_rel=1e-5, v_floor=None):
             "bad_idx": np.nonzero(q_bad | ev_bad | pos_bad | vel_bad)[0][:10]}
 
 
-def lockstep(run, rp, state0, steps, E=None, ne_cells=None, pos_rel=1e-6, vel_rel=1e-5):
+def lockstep(run, rp, state0, steps, E=None, ne_cells=None, pos_rel=1e-6, vel_rel=1e-5, mask=O.G_SINGLE):
     """Drive the GPU run and the oracle step by step; returns totals and the oracle."""
     orc = O.OracleRun(rp, state0, E=E, ne_cells=ne_cells)
     totals = {"q": 0, "events": 0, "pos": 0, "vel": 0, "guarded": 0, "events_seen": 0}
@@ -60,7 +81,7 @@ def lockstep(run, rp, state0, steps, E=None, ne_cells=None, pos_rel=1e-6, vel_re
         orc.step(1)
         run.step(1)
         g1 = run.state()
-        r = compare_step(rp, g1, orc, pos_rel, vel_rel)
+        r = compare_step(rp, g1, orc, pos_rel, vel_rel, mask=mask)
         for k in ("q", "events", "pos", "vel", "guarded"):
             totals[k] += r[k]
         if first_bad is None and (r["q"] or r["events"] or r["pos"] or r["vel"]):

@@ -1,0 +1,108 @@
+"""GPU parity of the Coulomb collision kernels (Takizawa-Abe pairing, Nanbu
+angle) with the FP64 oracle, through the C ABI.
+
+Cells hold 1 to several thousand ions so that the register, shared-memory
+and global-memory sorting paths of the pairing kernel all run; every pairing
+must be identical to the oracle's (integer events and collision counts) and
+the velocities must agree to the FP32 rounding of the collision arithmetic.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1507_03392_gb300 import inputs as I
+from tests import parity as P
+
+pytestmark = pytest.mark.gpu
+QE = 1.602176634e-19
+AMU = 1.66053906660e-27
+
+
+@pytest.fixture(scope="module")
+def E():
+    from paper_1507_03392_gb300 import ecris
+    return ecris
+
+
+def cells_state(rp, sizes, seed, T_eV=0.5, qmax_init=10):
+    """ions grouped at the centres of distinct cells, len(sizes) cells"""
+    rng = np.random.default_rng(seed)
+    dx, dy, dz = 2 * rp.R0 / rp.nx, 2 * rp.R0 / rp.ny, rp.L / rp.nz
+    cells = rng.choice(np.arange(rp.nx * rp.ny * rp.nz), size=len(sizes), replace=False)
+    xs, ys, zs = [], [], []
+    for c, m in zip(cells, sizes):
+        ix, iy, iz = c % rp.nx, (c // rp.nx) % rp.ny, c // (rp.nx * rp.ny)
+        # spread inside the cell, away from its faces
+        xs.append(-rp.R0 + (ix + rng.uniform(0.2, 0.8, m)) * dx)
+        ys.append(-rp.R0 + (iy + rng.uniform(0.2, 0.8, m)) * dy)
+        zs.append((iz + rng.uniform(0.2, 0.8, m)) * dz)
+    x, y, z = (np.concatenate(a).astype(np.float32) for a in (xs, ys, zs))
+    inside = x.astype(np.float64) ** 2 + y.astype(np.float64) ** 2 < 0.98 * rp.R0 ** 2
+    n = len(x)
+    sig = math.sqrt(T_eV * QE / (rp.species.mass_amu * AMU))
+    v = rng.normal(0, sig, (3, n)).astype(np.float32)
+    q = rng.integers(1, qmax_init + 1, n).astype(np.uint8)
+    q[rng.random(n) < 0.1] = 0          # a few atoms take no part
+    keep = inside
+    return {"x": x[keep], "y": y[keep], "z": z[keep], "vx": v[0][keep], "vy": v[1][keep],
+            "vz": v[2][keep], "q": q[keep]}
+
+
+@pytest.mark.parametrize("sizes,seed", [([1, 2, 3, 7, 31, 32, 33], 1),
+                                        ([40, 100, 511, 1024, 1025], 2),
+                                        ([3000], 3)])
+def test_coulomb_only_lockstep_all_sort_paths(E, sizes, seed):
+    rp = I.RunParams(nx=8, ny=8, nz=16, flags=I.F_COULOMB, weight=5e7, dt=1e-8, seed=seed)
+    st = cells_state(rp, sizes, seed)
+    run = E.Run(rp)
+    run.load(st)
+    t, orc = P.lockstep(run, rp, st, 3, vel_rel=2e-4)
+    assert t["q"] == 0 and t["events"] == 0 and t["pos"] == 0 and t["vel"] == 0, t
+    d = run.diag()
+    assert d["coulomb_collisions"] == orc.tally.coulomb_pairs
+    run.close()
+
+
+def test_coulomb_conserves_momentum_and_energy_per_cell(E):
+    rp = I.RunParams(nx=8, ny=8, nz=16, flags=I.F_COULOMB, weight=2e8, dt=2e-8, seed=5)
+    sizes = [2, 5, 64, 300, 2000]
+    st = cells_state(rp, sizes, 5, T_eV=2.0)
+    run = E.Run(rp)
+    run.load(st)
+    g0 = run.state()
+    run.step(1)
+    g1 = run.state()
+    dx, dy, dz = 2 * rp.R0 / rp.nx, 2 * rp.R0 / rp.ny, rp.L / rp.nz
+    cell = ((np.floor(g0["z"] / dz) * rp.ny + np.floor((g0["y"] + rp.R0) / dy)) * rp.nx
+            + np.floor((g0["x"] + rp.R0) / dx)).astype(np.int64)
+    moved = 0
+    for c in np.unique(cell):
+        sel = (cell == c) & (g0["q"] >= 1)
+        v0 = np.stack([g0[k][sel] for k in ("vx", "vy", "vz")]).astype(np.float64)
+        v1 = np.stack([g1[k][sel] for k in ("vx", "vy", "vz")]).astype(np.float64)
+        scale = np.abs(v0).sum()
+        assert np.abs(v0.sum(axis=1) - v1.sum(axis=1)).max() <= 1e-5 * scale + 1e-3
+        assert (v1 ** 2).sum() == pytest.approx((v0 ** 2).sum(), rel=1e-5)
+        moved += int((np.abs(v1 - v0).max(axis=0) > 0).sum())
+    assert moved > 0.8 * int((g0["q"] >= 1).sum())
+    run.close()
+
+
+def test_full_step_with_coulomb_lockstep(E):
+    # every process on, ions dense enough for many multi-ion cells
+    rp = I.RunParams(nx=16, ny=16, nz=32, ne_in_cm3=2e12, ne_out_cm3=2e11, n0_cm3=2e11, dt=2e-8,
+                     flags=I.F_ALL, weight=1e8, seed=8)
+    wl = I.Workload("dense", rp, n=20000, steps=0, atom_fraction=0.3, ion_qmax_init=8, ion_T_eV=5.0,
+                    atoms_fill_chamber=True, zone_box=(0.01, 0.17, 0.2))
+    st = I.make_particles(wl, seed=8)
+    Ef = I.make_efield(rp, 2e3, -1e3)
+    run = E.Run(rp, E=Ef)
+    run.load(st)
+    t, orc = P.lockstep(run, rp, st, 8, E=Ef, vel_rel=2e-4)
+    assert t["q"] == 0 and t["events"] == 0 and t["pos"] == 0 and t["vel"] == 0, t
+    assert t["guarded"] < 0.7 * 8 * 20000     # a large share is compared exactly
+    d = run.diag()
+    assert d["coulomb_collisions"] > 1000
+    run.close()
