@@ -153,6 +153,7 @@ struct ecris_ctx {
     size_t n = 0, n4 = 0;
     uint8_t* d_q8 = nullptr;
     unsigned int* d_bad = nullptr;
+    uint32_t* d_err = nullptr;
     uint32_t* d_crank = nullptr;
     uint32_t* d_ccount = nullptr;
     uint32_t* d_coff = nullptr;
@@ -279,6 +280,7 @@ void free_ions(ecris_ctx* ctx)
     free_async(ctx, ctx->d_ticket);
     free_async(ctx, ctx->d_q8);
     free_async(ctx, ctx->d_bad);
+    free_async(ctx, ctx->d_err);
     free_async(ctx, ctx->d_crank);
     free_async(ctx, ctx->d_ccount);
     free_async(ctx, ctx->d_coff);
@@ -381,6 +383,7 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.nanbu_lnlo = (float)std::log(kNanbuSLo);
     R.nanbu_inv_dln = (float)((kNanbuN - 1) / std::log(kNanbuSHi / kNanbuSLo));
     R.step = ctx->d_step;
+    R.err = ctx->d_err;
     R.n = (uint32_t)ctx->n;
     R.n4 = (uint32_t)ctx->n4;
     R.ncells = (uint32_t)((size_t)h.nx * h.ny * h.nz);
@@ -446,7 +449,7 @@ ecris_status ecris_create(ecris_ctx** out, int device, void* cuda_stream)
         return ECRIS_ECUDA;
     }
     ctx->step_grid = ctx->sm_count * step_blocks_per_sm();   // one wave of resident blocks
-    ctx->collide_grid = ctx->sm_count * 8;
+    ctx->collide_grid = ctx->sm_count * collide_blocks_per_sm();
     *out = ctx;
     return ECRIS_OK;
 }
@@ -640,6 +643,7 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         CK(cudaMallocAsync((void**)&ctx->d_step, sizeof(uint32_t), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_ticket, sizeof(unsigned int), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_bad, 2 * sizeof(unsigned int), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_err, sizeof(uint32_t), ctx->stream));
         if (h.mcc.flags & kFCoulomb) {
             CK(cudaMallocAsync((void**)&ctx->d_crank, cap * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_ckeys, cap * sizeof(unsigned long long), ctx->stream));
@@ -671,6 +675,7 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
     CK(cudaMemsetAsync(ctx->d_tally, 0, kTallyWords * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(uint32_t), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_ticket, 0, sizeof(unsigned int), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_bad, 0, sizeof(unsigned int), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_bad + 1, 0xFF, sizeof(unsigned int), ctx->stream));
     // validate on the device, build the meta words and fill the padding slots
@@ -765,6 +770,8 @@ ecris_status ecris_diag(ecris_ctx* ctx, ecris_diag_out* out)
     CK(cudaMemsetAsync(ctx->d_census, 0, kQSlots * sizeof(unsigned long long), ctx->stream));
     CK(launch_census(*ctx->h_run, (uint32_t)ctx->n4, ctx->d_census, ctx->stream));
     unsigned long long tally[kTallyWords], census[kQSlots];
+    uint32_t err = 0;
+    CK(cudaMemcpyAsync(&err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(tally, ctx->d_tally, sizeof tally, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(census, ctx->d_census, sizeof census, cudaMemcpyDeviceToHost, ctx->stream));
     if (out->cell_count)
@@ -772,6 +779,10 @@ ecris_status ecris_diag(ecris_ctx* ctx, ecris_diag_out* out)
     if (out->cell_charge)
         CK(cudaMemcpyAsync(out->cell_charge, ctx->d_charge, nc * 8, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (err) {
+        ctx->failed = true;
+        return fail(ctx, ECRIS_ETIMEOUT, "diag: a kernel's bounded wait for its tile copies ran out; reload");
+    }
     const int Q1 = h.qmax + 1;
     out->qmax = h.qmax;
     out->steps = ctx->steps_done;

@@ -30,7 +30,7 @@ namespace {
 
 constexpr int kCollideThreads = 128;
 constexpr int kCollideWarps = kCollideThreads / 32;
-constexpr int kSmemKeys = 1024;   // keys per warp sorted in shared memory
+constexpr int kSmemKeys = 512;    // keys per warp sorted in shared memory (>= 64)
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
 {
@@ -205,23 +205,25 @@ __device__ void collide(const RunDev& R, uint32_t a, uint32_t b, float dtc, floa
 
 // ascending bitonic sort of buf[0, m) by one warp; every compare-exchange moves
 // the smaller key to the lower index, so positions >= m act as +infinity and
-// their exchanges are skipped
+// their exchanges are skipped.  Sub-network sizes are powers of two, so block
+// and offset come from shifts and masks.
 __device__ void warp_bitonic(unsigned long long* buf, uint32_t m)
 {
     const int lane = threadIdx.x & 31;
-    uint32_t P = 1;
-    while (P < m) P <<= 1;
-    for (uint32_t k = 2; k <= P; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+    uint32_t P = 1, lp = 0;
+    while (P < m) { P <<= 1; ++lp; }
+    for (uint32_t lk = 1; lk <= lp; ++lk) {
+        const uint32_t k = 1u << lk;
+        for (int lj = (int)lk - 1; lj >= 0; --lj) {
+            const uint32_t j = 1u << lj;
             for (uint32_t t = lane; t < P / 2; t += 32) {
+                const uint32_t blk = t >> lj, off = t & (j - 1);
                 uint32_t lo, hi;
-                if (j == (k >> 1)) {
-                    const uint32_t blk = t / j, off = t % j;
-                    lo = blk * k + off;
-                    hi = blk * k + k - 1 - off;
-                } else {
-                    const uint32_t blk = t / j, off = t % j;
-                    lo = blk * 2 * j + off;
+                if (lj == (int)lk - 1) {        // first sub-step: mirrored pairs
+                    lo = (blk << lk) + off;
+                    hi = (blk << lk) + k - 1 - off;
+                } else {                        // half-cleaner
+                    lo = (blk << (lj + 1)) + off;
                     hi = lo + j;
                 }
                 if (hi < m) {
@@ -234,7 +236,34 @@ __device__ void warp_bitonic(unsigned long long* buf, uint32_t m)
     }
 }
 
-__global__ void __launch_bounds__(kCollideThreads) k_collide(const __grid_constant__ RunDev R,
+// the same network on 32 keys held one per lane
+__device__ __forceinline__ unsigned long long lane_sort32(unsigned long long k, int lane)
+{
+#pragma unroll
+    for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            const int partner = (j == (kk >> 1)) ? (lane ^ (kk - 1)) : (lane ^ j);
+            const unsigned long long o = __shfl_sync(0xFFFFFFFFu, k, partner);
+            k = (lane < partner) ? (o < k ? o : k) : (o > k ? o : k);
+        }
+    }
+    return k;
+}
+
+// half-cleaners j = 16 .. 1 on 32 keys held one per lane
+__device__ __forceinline__ unsigned long long lane_clean32(unsigned long long k, int lane)
+{
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+        const int partner = lane ^ j;
+        const unsigned long long o = __shfl_sync(0xFFFFFFFFu, k, partner);
+        k = (lane < partner) ? (o < k ? o : k) : (o > k ? o : k);
+    }
+    return k;
+}
+
+__global__ void __launch_bounds__(kCollideThreads, 8) k_collide(const __grid_constant__ RunDev R,
                                                              unsigned int* ticket)
 {
     __shared__ unsigned long long sk[kCollideWarps][kSmemKeys];
@@ -251,18 +280,25 @@ __global__ void __launch_bounds__(kCollideThreads) k_collide(const __grid_consta
         const uint32_t m = R.coff[cell + 1] - off;
         unsigned long long* keys = R.ckeys + off;
         unsigned long long* buf;
-        if (m <= 32u) {
-            // registers: bitonic network over the 32 lanes
-            unsigned long long k = lane < (int)m ? keys[lane] : ~0ull;
-            for (int kk = 2; kk <= 32; kk <<= 1) {
-                for (int j = kk >> 1; j > 0; j >>= 1) {
-                    const int partner = (j == (kk >> 1)) ? (lane ^ (kk - 1)) : (lane ^ j);
-                    const unsigned long long o = __shfl_sync(0xFFFFFFFFu, k, partner);
-                    k = (lane < partner) ? (o < k ? o : k) : (o > k ? o : k);
-                }
+        if (m <= 64u) {
+            // registers: keys lane and lane + 32; each half is sorted by the
+            // 32-lane network, then one mirrored exchange across the halves and
+            // half-cleaners finish the 64-key network
+            unsigned long long k0 = lane < (int)m ? keys[lane] : ~0ull;
+            unsigned long long k1 = lane + 32 < (int)m ? keys[lane + 32] : ~0ull;
+            k0 = lane_sort32(k0, lane);
+            k1 = lane_sort32(k1, lane);
+            if (m > 32u) {
+                const unsigned long long o0 = __shfl_sync(0xFFFFFFFFu, k1, 31 - lane);
+                const unsigned long long o1 = __shfl_sync(0xFFFFFFFFu, k0, 31 - lane);
+                k0 = o0 < k0 ? o0 : k0;
+                k1 = o1 > k1 ? o1 : k1;
+                k0 = lane_clean32(k0, lane);
+                k1 = lane_clean32(k1, lane);
             }
             buf = sk[wib];
-            buf[lane] = k;
+            buf[lane] = k0;
+            buf[lane + 32] = k1;
             __syncwarp();
         } else if (m <= (uint32_t)kSmemKeys) {
             buf = sk[wib];
@@ -311,6 +347,14 @@ __global__ void __launch_bounds__(kCollideThreads) k_collide(const __grid_consta
 }  // namespace
 
 int coulomb_scan_blocks(uint32_t ncells) { return (int)((ncells + kScanBlock - 1) / kScanBlock); }
+
+int collide_blocks_per_sm()
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_collide, kCollideThreads, 0) != cudaSuccess || b < 1)
+        b = 1;
+    return b;
+}
 
 cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t n4, unsigned int* ticket, int grid,
                            cudaStream_t s)

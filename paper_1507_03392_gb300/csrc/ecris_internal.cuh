@@ -42,6 +42,11 @@ constexpr uint32_t kFRecycle = 1u << 5;
 
 constexpr uint32_t kNoCell = 0xFFFFFFFFu;
 
+// bounded waits: iterations of mbarrier.try_wait before a kernel gives up,
+// records ECRIS_ETIMEOUT (4) in the run's error word and stops its work
+constexpr uint32_t kWaitLimit = 1u << 20;
+constexpr uint32_t kErrTimeout = 4u;
+
 // Nanbu A(s) table: ln A tabulated on a uniform grid in ln s over [1e-3, 6]
 constexpr int kNanbuN = 2048;
 constexpr double kNanbuSLo = 1e-3;
@@ -102,6 +107,7 @@ struct RunDev {
     const float *nanbu;          // ln A at ln s = nanbu_lnlo + i / nanbu_inv_dln, i < kNanbuN
     float nanbu_lnlo, nanbu_inv_dln;
     uint32_t *step;              // device step counter of the run
+    uint32_t *err;               // device error word: 0, or ECRIS_ETIMEOUT after a bounded wait ran out
     uint32_t n;                  // particles
     uint32_t n4;                 // float4 groups = ceil(n/4)
     uint32_t ncells;
@@ -252,5 +258,6 @@ constexpr int kCoulombKernels = 5;   // kernels per launch_coulomb
 cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t n4, unsigned int* ticket, int grid,
                            cudaStream_t s);
 int coulomb_scan_blocks(uint32_t ncells);
+int collide_blocks_per_sm();
 
 }  // namespace ecris

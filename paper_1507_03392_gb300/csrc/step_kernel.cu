@@ -40,6 +40,14 @@ __device__ __forceinline__ void emit(float sigma, float nx, float ny, float nz, 
     vz = vn * nz + t1 * e1z + t2 * e2z;
 }
 
+// probability 1 - exp(-lam) of at least one event in a step; for small lam
+// the cubic Taylor polynomial is exact to FP32 rounding (error < lam^4 / 24)
+__device__ __forceinline__ float event_prob(float lam)
+{
+    if (lam < 1e-3f) return lam * (1.0f - lam * (0.5f - lam * (1.0f / 6.0f)));
+    return -expm1f(-lam);
+}
+
 __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uint32_t step, float& x,
                                               float& y, float& z, float& vx, float& vy, float& vz,
                                               uint32_t& meta, BlockTally& T,
@@ -64,7 +72,7 @@ __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uin
             const float h = (float)Q * R.qm_unit * R.half_dt;
             float mx = vx + h * Ex, my = vy + h * Ey, mz = vz + h * Ez;
             const float tx = h * Bx, ty = h * By, tz = h * Bz;
-            const float sf = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
+            const float sf = __fdividef(2.0f, 1.0f + tx * tx + ty * ty + tz * tz);
             const float px = mx + (my * tz - mz * ty);
             const float py = my + (mz * tx - mx * tz);
             const float pz = mz + (mx * ty - my * tx);
@@ -151,11 +159,11 @@ __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uin
         const Words w = rng_words(R, pid, step, 0u);
         if ((R.flags & kFIonize) && (int)Q < R.qmax) {
             const float lam = cr.x * __ldg(R.kdt + zone * kQSlots + Q);
-            if (fires(w.w0, -expm1f(-lam))) { Q += 1; ev |= kEvIonize; }
+            if (fires(w.w0, event_prob(lam))) { Q += 1; ev |= kEvIonize; }
         }
         if ((R.flags & kFCx) && R.n0s1 > 0.0f && Q >= 1 && Q != 2) {
             const float vrel = sqrtf(vx * vx + vy * vy + vz * vz + R.vth2);
-            const float p = -expm1f(-R.n0s1 * (float)Q * vrel * R.dt);
+            const float p = event_prob(R.n0s1 * (float)Q * vrel * R.dt);
             if (fires(w.w1, p)) {
                 const Words u = rng_words(R, pid, step, 3u);
                 ev |= kEvCx;
@@ -212,51 +220,139 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
     return v;
 }
 
-// Shared-memory stage of one tile: SoA copies of the tile's particles and the
-// processing order (ions first, then atoms), so that every warp runs one kind
-// of particle at a time instead of both paths for every lane.
-struct TileStage {
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA engine) between global and shared memory, and
+// the mbarrier that tracks the loads.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// bounded wait for phase `parity` of the barrier; false if the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    const uint32_t a = smem_addr(bar);
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// global -> shared, `bytes` a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// shared -> global, same alignment rules
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// One stage of the tile pipeline: SoA copies of a tile's particles.
+struct Stage {
     float4 x[kThreads], y[kThreads], z[kThreads], vx[kThreads], vy[kThreads], vz[kThreads];
     uint4 meta[kThreads];
+};
+
+struct StepShared {
+    Stage st[2];
     uint4 ckey[kThreads];
     uint16_t order[kTile];
     uint32_t warp_ions[kThreads / 32], warp_atoms[kThreads / 32];
     BlockTally T;
+    uint64_t bar[2];
     int last;
+    int failed;
 };
 
 __device__ __forceinline__ float& sf(float4* a, uint32_t i) { return reinterpret_cast<float*>(a)[i]; }
 __device__ __forceinline__ uint32_t& su(uint4* a, uint32_t i) { return reinterpret_cast<uint32_t*>(a)[i]; }
 
-// One pass over the tiles of a run.  Each tile of 1024 particles is loaded
-// with 128-bit coalesced loads into shared memory, the live particles are
-// ordered ions first (their push needs the field evaluation), each thread then
-// advances the particles at order[tid], order[tid + 256], ..., and the tile is
-// written back with 128-bit streaming stores.
+// issue the seven bulk loads of tile t into stage st (thread 0 only)
+__device__ __forceinline__ void load_tile(const RunDev& R, Stage& st, uint64_t* bar, uint32_t t)
+{
+    const uint32_t g0 = t * kThreads;
+    const uint32_t ng = min((uint32_t)kThreads, R.n4 - g0);
+    const uint32_t bytes = ng * 16u;
+    mbar_expect_tx(bar, 7u * bytes);
+    bulk_load(st.x, reinterpret_cast<const float4*>(R.x) + g0, bytes, bar);
+    bulk_load(st.y, reinterpret_cast<const float4*>(R.y) + g0, bytes, bar);
+    bulk_load(st.z, reinterpret_cast<const float4*>(R.z) + g0, bytes, bar);
+    bulk_load(st.vx, reinterpret_cast<const float4*>(R.vx) + g0, bytes, bar);
+    bulk_load(st.vy, reinterpret_cast<const float4*>(R.vy) + g0, bytes, bar);
+    bulk_load(st.vz, reinterpret_cast<const float4*>(R.vz) + g0, bytes, bar);
+    bulk_load(st.meta, reinterpret_cast<const uint4*>(R.meta) + g0, bytes, bar);
+}
+
+// Persistent pass over the tiles of a run, two tiles in flight per block: while
+// the block advances tile t in one stage, the TMA engine brings tile t + grid
+// into the other stage; results leave through bulk stores.  Inside a tile the
+// live particles are ordered ions first (their push needs the field
+// evaluation), so each warp runs one kind of particle at a time.
 __global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ RunDev R, uint32_t ntiles,
                                                       unsigned int* ticket, int bump_step)
 {
-    __shared__ TileStage S;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    StepShared& S = *reinterpret_cast<StepShared*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool coulomb = (R.flags & kFCoulomb) != 0;
     const uint32_t step = *R.step;
-    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (tid == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        S.failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t t = blockIdx.x;
+    if (tid == 0 && t < ntiles) load_tile(R, S.st[0], &S.bar[0], t);
+    for (uint32_t it = 0; t < ntiles; ++it, t += gridDim.x) {
+        const uint32_t s = it & 1u;
+        Stage& st = S.st[s];
+        const uint32_t tn = t + gridDim.x;
+        if (tid == 0 && tn < ntiles) {
+            bulk_wait_read_all();   // the other stage's previous stores have read their data
+            load_tile(R, S.st[s ^ 1u], &S.bar[s ^ 1u], tn);
+        }
         for (int i = tid; i < kQSlots; i += kThreads) { S.T.ext[i] = 0u; S.T.lost[i] = 0u; }
         if (tid == 0) S.T.ke = 0ull;
+        if (!mbar_wait(&S.bar[s], (it >> 1) & 1u)) S.failed = 1;
+        __syncthreads();
+        if (S.failed) break;
         const uint32_t g = t * kThreads + tid;
         const bool valid = g < R.n4;
-        uint4 M = make_uint4(kStPad, kStPad, kStPad, kStPad);
-        if (valid) {
-            S.x[tid] = reinterpret_cast<const float4*>(R.x)[g];
-            S.y[tid] = reinterpret_cast<const float4*>(R.y)[g];
-            S.z[tid] = reinterpret_cast<const float4*>(R.z)[g];
-            S.vx[tid] = reinterpret_cast<const float4*>(R.vx)[g];
-            S.vy[tid] = reinterpret_cast<const float4*>(R.vy)[g];
-            S.vz[tid] = reinterpret_cast<const float4*>(R.vz)[g];
-            M = reinterpret_cast<const uint4*>(R.meta)[g];
-        }
-        S.meta[tid] = M;
-        S.ckey[tid] = make_uint4(kNoCell, kNoCell, kNoCell, kNoCell);
+        const uint4 M = valid ? st.meta[tid] : make_uint4(kStPad, kStPad, kStPad, kStPad);
+        if (coulomb) S.ckey[tid] = make_uint4(kNoCell, kNoCell, kNoCell, kNoCell);
         // classify: live ions, live atoms (frozen and padding slots are left alone)
         const uint32_t mm[4] = {M.x, M.y, M.z, M.w};
         uint32_t nion = 0, natom = 0;
@@ -268,7 +364,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ Ru
             nion += is_ion[j];
             natom += live[j] && !is_ion[j];
         }
-        // warp-inclusive scans of the per-thread counts
         uint32_t ion_incl = nion, atom_incl = natom;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -299,34 +394,47 @@ __global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ Ru
         unsigned long long ke = 0ull;
         for (uint32_t i = tid; i < nlive; i += kThreads) {
             const uint32_t k = S.order[i];
-            float x = sf(S.x, k), y = sf(S.y, k), z = sf(S.z, k);
-            float vx = sf(S.vx, k), vy = sf(S.vy, k), vz = sf(S.vz, k);
-            uint32_t meta = su(S.meta, k), ck;
+            float x = sf(st.x, k), y = sf(st.y, k), z = sf(st.z, k);
+            float vx = sf(st.vx, k), vy = sf(st.vy, k), vz = sf(st.vz, k);
+            uint32_t meta = su(st.meta, k), ck;
             step_particle(R, pid0 + k, step, x, y, z, vx, vy, vz, meta, S.T, ke, ck);
-            sf(S.x, k) = x; sf(S.y, k) = y; sf(S.z, k) = z;
-            sf(S.vx, k) = vx; sf(S.vy, k) = vy; sf(S.vz, k) = vz;
-            su(S.meta, k) = meta;
+            sf(st.x, k) = x; sf(st.y, k) = y; sf(st.z, k) = z;
+            sf(st.vx, k) = vx; sf(st.vy, k) = vy; sf(st.vz, k) = vz;
+            su(st.meta, k) = meta;
             if (coulomb) su(S.ckey, k) = ck;
         }
         ke = warp_sum(ke);
         if (lane == 0 && ke) atomicAdd(&S.T.ke, ke);
+        fence_proxy_async();    // make this thread's stage writes visible to the bulk stores
         __syncthreads();
-        if (valid) {
-            __stcs(reinterpret_cast<float4*>(R.x) + g, S.x[tid]);
-            __stcs(reinterpret_cast<float4*>(R.y) + g, S.y[tid]);
-            __stcs(reinterpret_cast<float4*>(R.z) + g, S.z[tid]);
-            __stcs(reinterpret_cast<float4*>(R.vx) + g, S.vx[tid]);
-            __stcs(reinterpret_cast<float4*>(R.vy) + g, S.vy[tid]);
-            __stcs(reinterpret_cast<float4*>(R.vz) + g, S.vz[tid]);
-            __stcs(reinterpret_cast<uint4*>(R.meta) + g, S.meta[tid]);
-            if (coulomb) reinterpret_cast<uint4*>(R.ckey)[g] = S.ckey[tid];
+        if (tid == 0) {
+            const uint32_t g0 = t * kThreads;
+            const uint32_t bytes = min((uint32_t)kThreads, R.n4 - g0) * 16u;
+            bulk_store(reinterpret_cast<float4*>(R.x) + g0, st.x, bytes);
+            bulk_store(reinterpret_cast<float4*>(R.y) + g0, st.y, bytes);
+            bulk_store(reinterpret_cast<float4*>(R.z) + g0, st.z, bytes);
+            bulk_store(reinterpret_cast<float4*>(R.vx) + g0, st.vx, bytes);
+            bulk_store(reinterpret_cast<float4*>(R.vy) + g0, st.vy, bytes);
+            bulk_store(reinterpret_cast<float4*>(R.vz) + g0, st.vz, bytes);
+            bulk_store(reinterpret_cast<uint4*>(R.meta) + g0, st.meta, bytes);
+            bulk_commit();
         }
+        if (coulomb && valid) reinterpret_cast<uint4*>(R.ckey)[g] = S.ckey[tid];
         for (int i = tid; i < kQSlots; i += kThreads) {
             if (S.T.ext[i]) atomicAdd(R.tally + kTallyExtracted + i, (unsigned long long)S.T.ext[i]);
             if (S.T.lost[i]) atomicAdd(R.tally + kTallyLost + i, (unsigned long long)S.T.lost[i]);
         }
         if (tid == 0 && S.T.ke) atomicAdd(R.tally + kTallyKe, S.T.ke);
         __syncthreads();
+    }
+    if (tid == 0) {
+        bulk_wait_all();        // stores complete before the block retires
+        if (S.failed) {
+            atomicExch(R.err, kErrTimeout);
+            // the loads this block issued may still land: wait (bounded) for them
+            mbar_wait(&S.bar[0], 0u);
+            mbar_wait(&S.bar[1], 0u);
+        }
     }
     if (bump_step) {
         // the last block to finish advances the run's step counter
@@ -423,8 +531,10 @@ cudaError_t launch_load_init(const LoadCheck& lc, float* const soa[6], const uin
 
 int step_blocks_per_sm()
 {
+    const int smem = (int)sizeof(StepShared);
+    if (cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step, kThreads, 0) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step, kThreads, smem) != cudaSuccess || b < 1) b = 1;
     return b;
 }
 
@@ -433,7 +543,7 @@ cudaError_t launch_step(const RunDev& R, uint32_t ntiles, unsigned int* ticket, 
 {
     if (ntiles == 0) return cudaSuccess;
     if (grid > (int)ntiles) grid = (int)ntiles;
-    k_step<<<grid, kThreads, 0, s>>>(R, ntiles, ticket, bump_step);
+    k_step<<<grid, kThreads, sizeof(StepShared), s>>>(R, ntiles, ticket, bump_step);
     return cudaGetLastError();
 }
 
