@@ -604,7 +604,7 @@ void or_step(const or_params *p, const double *rates, const double *ne, const in
         int out_r = x1 * x1 + y1 * y1 > p->R0 * p->R0;
         int out_0 = z1 < 0.0, out_L = z1 > p->L;
         if (out_r || out_0 || out_L) {
-            double fbest = 2.0;
+            double fbest = 2.0, fr = 3.0, fz = 3.0;
             int kind = OR_LEAVE_NONE;
             double dx = x1 - x0, dy = y1 - y0, dz = z1 - z0;
             if (out_r) {
@@ -612,16 +612,21 @@ void or_step(const or_params *p, const double *rates, const double *ne, const in
                 double disc = sqrt(fmax(0.0, b * b - a * c));
                 double f = (b + disc > 0.0) ? -c / (b + disc) : 0.0;
                 if (f < 0.0) f = 0.0;
+                fr = f;
                 if (f < fbest) { fbest = f; kind = OR_LEAVE_RADIAL; }
             }
             if (out_0) {
                 double f = z0 / (z0 - z1);
+                fz = f;
                 if (f < fbest) { fbest = f; kind = OR_LEAVE_Z0; }
             }
             if (out_L) {
                 double f = (p->L - z0) / (z1 - z0);
+                fz = f;
                 if (f < fbest) { fbest = f; kind = OR_LEAVE_ZL; }
             }
+            /* a step through a corner: which wall comes first is a rounding tie */
+            if (fabs(fr - fz) < 1e-4) guard[i] |= OR_G_BOUNDARY;
             double cx = x0 + fbest * dx, cy = y0 + fbest * dy, cz = z0 + fbest * dz;
             if (kind == OR_LEAVE_ZL) {
                 double rc = sqrt(cx * cx + cy * cy);

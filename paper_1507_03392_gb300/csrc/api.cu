@@ -154,7 +154,10 @@ struct ecris_ctx {
     uint8_t* d_q8 = nullptr;
     unsigned int* d_bad = nullptr;
     uint32_t* d_err = nullptr;
-    uint32_t* d_crank = nullptr;
+    uint2* d_plist = nullptr;
+    float4* d_pvel = nullptr;
+    uint32_t* d_tcount = nullptr;
+    float4* d_crec = nullptr;
     uint32_t* d_ccount = nullptr;
     uint32_t* d_coff = nullptr;
     uint32_t* d_cblk = nullptr;
@@ -164,7 +167,6 @@ struct ecris_ctx {
     int collide_grid = 0;
     float* d_soa[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     uint32_t* d_meta = nullptr;
-    uint32_t* d_ckey = nullptr;
     unsigned long long* d_dep = nullptr;
     unsigned long long* d_count = nullptr;
     unsigned long long* d_charge = nullptr;
@@ -270,7 +272,6 @@ void free_ions(ecris_ctx* ctx)
 {
     for (auto& p : ctx->d_soa) free_async(ctx, p);
     free_async(ctx, ctx->d_meta);
-    free_async(ctx, ctx->d_ckey);
     free_async(ctx, ctx->d_dep);
     free_async(ctx, ctx->d_count);
     free_async(ctx, ctx->d_charge);
@@ -281,7 +282,10 @@ void free_ions(ecris_ctx* ctx)
     free_async(ctx, ctx->d_q8);
     free_async(ctx, ctx->d_bad);
     free_async(ctx, ctx->d_err);
-    free_async(ctx, ctx->d_crank);
+    free_async(ctx, ctx->d_plist);
+    free_async(ctx, ctx->d_pvel);
+    free_async(ctx, ctx->d_tcount);
+    free_async(ctx, ctx->d_crec);
     free_async(ctx, ctx->d_ccount);
     free_async(ctx, ctx->d_coff);
     free_async(ctx, ctx->d_cblk);
@@ -359,9 +363,24 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     }
     R.seed_lo = (uint32_t)ctx->seed;
     R.seed_hi = (uint32_t)(ctx->seed >> 32);
-    R.x = ctx->d_soa[0];
-    R.y = ctx->d_soa[1];
-    R.z = ctx->d_soa[2];
+    R.x = reinterpret_cast<int32_t*>(ctx->d_soa[0]);
+    R.y = reinterpret_cast<int32_t*>(ctx->d_soa[1]);
+    R.z = reinterpret_cast<int32_t*>(ctx->d_soa[2]);
+    R.sxy = (float)(h.geo.R0 / 2147483648.0);
+    R.inv_sxy = (float)(2147483648.0 / h.geo.R0);
+    R.sz = (float)(h.geo.L / 4294967296.0);
+    R.inv_sz = (float)(4294967296.0 / h.geo.L);
+    R.dt_sxy = (float)(dt * 2147483648.0 / h.geo.R0);
+    R.dt_sz = (float)(dt * 4294967296.0 / h.geo.L);
+    R.R0_d = h.geo.R0;
+    R.L_d = h.geo.L;
+    R.r_ap_d = h.geo.r_ap;
+    R.eps_wall_d = 1e-6 * h.geo.L;
+    R.sxy_d = h.geo.R0 / 2147483648.0;
+    R.sz_d = h.geo.L / 4294967296.0;
+    R.inlet_X = (int32_t)std::llrint(h.geo.inlet[0] / R.sxy_d);
+    R.inlet_Y = (int32_t)std::llrint(h.geo.inlet[1] / R.sxy_d);
+    R.inlet_Z = (int32_t)(std::llrint(h.geo.inlet[2] / R.sz_d) - 2147483648ll);
     R.vx = ctx->d_soa[3];
     R.vy = ctx->d_soa[4];
     R.vz = ctx->d_soa[5];
@@ -371,8 +390,10 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.kdt = ctx->d_kdt;
     R.dep = ctx->d_dep;
     R.tally = ctx->d_tally;
-    R.ckey = ctx->d_ckey;
-    R.crank = ctx->d_crank;
+    R.plist = ctx->d_plist;
+    R.pvel = ctx->d_pvel;
+    R.tcount = ctx->d_tcount;
+    R.crec = ctx->d_crec;
     R.ccount = ctx->d_ccount;
     R.coff = ctx->d_coff;
     R.cblk = ctx->d_cblk;
@@ -633,7 +654,6 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         for (int k = 0; k < 6; ++k)
             CK(cudaMallocAsync((void**)&ctx->d_soa[k], cap * sizeof(float), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_meta, cap * sizeof(uint32_t), ctx->stream));
-        CK(cudaMallocAsync((void**)&ctx->d_ckey, cap * sizeof(uint32_t), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_q8, cap, ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_dep, nc * sizeof(unsigned long long), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_count, nc * sizeof(unsigned long long), ctx->stream));
@@ -645,8 +665,12 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         CK(cudaMallocAsync((void**)&ctx->d_bad, 2 * sizeof(unsigned int), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_err, sizeof(uint32_t), ctx->stream));
         if (h.mcc.flags & kFCoulomb) {
-            CK(cudaMallocAsync((void**)&ctx->d_crank, cap * sizeof(uint32_t), ctx->stream));
+            const size_t slots = (cap / kTile + 1) * kTile;
+            CK(cudaMallocAsync((void**)&ctx->d_plist, slots * sizeof(uint2), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_pvel, slots * sizeof(float4), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_tcount, (cap / kTile + 1) * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_ckeys, cap * sizeof(unsigned long long), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_crec, cap * sizeof(float4), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_ccount, nc * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_coff, (nc + 1) * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_cblk, (size_t)coulomb_scan_blocks((uint32_t)nc) * sizeof(uint32_t),
@@ -667,7 +691,6 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
             CK(cudaMemcpyAsync(ctx->d_soa[k], xyzv[k], n * sizeof(float), kind, ctx->stream));
         CK(cudaMemcpyAsync(ctx->d_q8, q, n, kind, ctx->stream));
     }
-    CK(cudaMemsetAsync(ctx->d_ckey, 0xFF, cap * sizeof(uint32_t), ctx->stream));
     if (ctx->d_ccount) CK(cudaMemsetAsync(ctx->d_ccount, 0, nc * sizeof(uint32_t), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_dep, 0, nc * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_count, 0, nc * sizeof(unsigned long long), ctx->stream));
@@ -686,6 +709,8 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
     lc.inlet_x = (float)h.geo.inlet[0];
     lc.inlet_y = (float)h.geo.inlet[1];
     lc.inlet_z = (float)h.geo.inlet[2];
+    lc.inv_sxy = 2147483648.0 / h.geo.R0;
+    lc.inv_sz = 4294967296.0 / h.geo.L;
     CK(launch_load_init(lc, ctx->d_soa, ctx->d_q8, ctx->d_meta, (uint32_t)n, (uint32_t)cap, ctx->d_bad,
                         ctx->stream));
     unsigned int bad[2] = {0u, 0u};
@@ -736,7 +761,7 @@ ecris_status ecris_step(ecris_ctx* ctx, uint32_t nsteps, double dt)
         }));
         if (coulomb) {
             CK(timed(ctx, kKindCoulomb, [&] {
-                return launch_coulomb(*ctx->h_run, nc, (uint32_t)ctx->n4, ctx->d_ticket, ctx->collide_grid,
+                return launch_coulomb(*ctx->h_run, nc, ctx->ntiles, ctx->d_ticket, ctx->collide_grid,
                                       ctx->stream);
             }, kCoulombKernels));
         }
@@ -816,11 +841,32 @@ ecris_status ecris_get_state(ecris_ctx* ctx, float* const xyzv[6], uint32_t* met
     if (!ctx->loaded) return fail(ctx, ECRIS_ESTATE, "get_state: call ecris_load_ions first");
     CK(cudaSetDevice(ctx->device));
     const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (ctx->n) {
+    const double sxy = ctx->h.geo.R0 / 2147483648.0, sz = ctx->h.geo.L / 4294967296.0;
+    const size_t n = ctx->n;
+    if (n) {
         for (int k = 0; k < 6; ++k)
             if (xyzv && xyzv[k])
-                CK(cudaMemcpyAsync(xyzv[k], ctx->d_soa[k], ctx->n * sizeof(float), kind, ctx->stream));
-        if (meta) CK(cudaMemcpyAsync(meta, ctx->d_meta, ctx->n * sizeof(uint32_t), kind, ctx->stream));
+                CK(cudaMemcpyAsync(xyzv[k], ctx->d_soa[k], n * sizeof(float), kind, ctx->stream));
+        if (meta) CK(cudaMemcpyAsync(meta, ctx->d_meta, n * sizeof(uint32_t), kind, ctx->stream));
+        const bool pos = xyzv && xyzv[0] && xyzv[1] && xyzv[2];
+        if (dst_is_device && pos) {
+            // positions are held in fixed point: convert the copies in place
+            CK(launch_export(xyzv[0], xyzv[1], xyzv[2], (uint32_t)n, sxy, sz, ctx->stream));
+        } else if (dst_is_device && xyzv && (xyzv[0] || xyzv[1] || xyzv[2])) {
+            return fail(ctx, ECRIS_EINVAL, "get_state: device positions need all of x, y, z");
+        }
+        if (!dst_is_device) {
+            CK(cudaStreamSynchronize(ctx->stream));
+            for (int k = 0; k < 3; ++k) {
+                if (!xyzv || !xyzv[k]) continue;
+                float* f = xyzv[k];
+                for (size_t i = 0; i < n; ++i) {
+                    int32_t X;
+                    std::memcpy(&X, f + i, 4);
+                    f[i] = (float)(k < 2 ? (double)X * sxy : ((double)X + 2147483648.0) * sz);
+                }
+            }
+        }
     }
     if (!dst_is_device) CK(cudaStreamSynchronize(ctx->stream));
     return ECRIS_OK;

@@ -2,18 +2,22 @@
 // collision block): Takizawa-Abe pairing of the ions of each cell and Nanbu's
 // scattering angle, Coulomb logarithm lnL_ii.
 //
-// Per step, after the fused step kernel has given every ion that stayed inside
-// its cell (ckey) and its arrival rank in that cell (crank, from an atomic on
-// ccount):
+// Per step, after the fused step kernel has counted the ions that stayed inside
+// per cell (ccount) and published each one's (pid, cell) and (v, Q) record in
+// its tile's participant list:
 //   1. scan      exclusive scan of ccount -> coff (three small passes); the
-//                last pass clears ccount and lists the cells holding >= 2 ions;
-//   2. scatter   key = (pairing hash << 32 | pid) stored at coff[cell] + rank;
-//                the hash is word 0 of the particle's stream-1 Philox block;
+//                last pass lists the cells holding >= 2 ions;
+//   2. scatter   each listed participant takes slot coff[cell] + (ccount[cell]
+//                counted down by one), which leaves ccount at zero for the next
+//                step; the slot receives key = (pairing hash << 32 | pid), the
+//                hash being word 0 of the particle's stream-1 Philox block, and
+//                the (v, Q) record, so each cell's records become contiguous;
 //   3. collide   one warp per listed cell sorts its keys (bitonic network in
 //                registers, shared memory or global memory by size), so the
-//                pairing is independent of the atomic arrival order, then
-//                collides consecutive pairs; an odd count puts the first three
-//                in a triplet that collides (0,1), (1,2), (2,0) over dt/2 each.
+//                pairing is independent of the atomic arrival order, collides
+//                consecutive pairs on the contiguous records, and writes the new
+//                velocities back; an odd count puts the first three in a
+//                triplet that collides (0,1), (1,2), (2,0) over dt/2 each.
 // A collision of ions a, b (same mass M, charges Qa, Qb) over time dt_c uses
 //   s = lnL/(4 pi) (Qa Qb e^2 / (eps0 mu))^2 n g^-3 dt_c,  mu = M/2,
 // n = w m / V_cell for the cell's m ions; A(s) from coth A - 1/A = e^-s
@@ -30,7 +34,7 @@ namespace {
 
 constexpr int kCollideThreads = 128;
 constexpr int kCollideWarps = kCollideThreads / 32;
-constexpr int kSmemKeys = 512;    // keys per warp sorted in shared memory (>= 64)
+constexpr int kSmemKeys = 256;    // participants per warp handled in shared memory (>= 64)
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
 {
@@ -110,7 +114,7 @@ __global__ void __launch_bounds__(1024) k_scan_b(const __grid_constant__ RunDev 
     }
 }
 
-// pass C: add block offsets, clear the counts, list cells with >= 2 ions
+// pass C: add block offsets, list cells with >= 2 ions
 __global__ void __launch_bounds__(kScanThreads) k_scan_c(const __grid_constant__ RunDev R, uint32_t ncells)
 {
     const uint32_t add = R.cblk[blockIdx.x];
@@ -118,29 +122,25 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_c(const __grid_constant__
     for (uint32_t j = threadIdx.x; j < (uint32_t)kScanBlock; j += kScanThreads) {
         const uint32_t idx = base + j;
         if (idx >= ncells) break;
-        const uint32_t c = R.ccount[idx];
-        if (c) {
-            R.ccount[idx] = 0u;
-            if (c >= 2u) R.occ[atomicAdd(R.occ_n, 1u)] = idx;
-        }
+        if (R.ccount[idx] >= 2u) R.occ[atomicAdd(R.occ_n, 1u)] = idx;
         R.coff[idx] += add;
     }
 }
 
-// scatter the pairing keys of the participants into their cell's segment
-__global__ void k_scatter(const __grid_constant__ RunDev R, uint32_t n4)
+// scatter the participants of each tile into their cells' segments; counting
+// ccount back down gives each its slot and leaves ccount zero for the next step
+__global__ void k_scatter(const __grid_constant__ RunDev R, uint32_t ntiles)
 {
     const uint32_t step = *R.step;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
-        const uint4 k4 = reinterpret_cast<const uint4*>(R.ckey)[g];
-        const uint32_t cells[4] = {k4.x, k4.y, k4.z, k4.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (cells[j] == kNoCell) continue;
-            const uint32_t pid = 4u * g + j;
-            const uint32_t slot = R.coff[cells[j]] + R.crank[pid];
-            const Words w = rng_words(R, pid, step, 1u);
-            R.ckeys[slot] = ((unsigned long long)w.w0 << 32) | pid;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint32_t np = R.tcount[t];
+        for (uint32_t i = threadIdx.x; i < np; i += blockDim.x) {
+            const uint2 pc = R.plist[t * kTile + i];
+            const float4 v = R.pvel[t * kTile + i];
+            const uint32_t slot = R.coff[pc.y] + atomicSub(R.ccount + pc.y, 1u) - 1u;
+            const Words w = rng_words(R, pc.x, step, 1u);
+            R.ckeys[slot] = ((unsigned long long)w.w0 << 32) | pc.x;
+            R.crec[slot] = v;
         }
     }
 }
@@ -158,19 +158,16 @@ __device__ __forceinline__ float nanbu_A(const RunDev& R, float s)
     return expf(la);
 }
 
-__device__ void collide(const RunDev& R, uint32_t a, uint32_t b, float dtc, float m_cell, uint32_t first,
-                        uint32_t step)
+// One collision over time dtc of the records ra, rb (vx, vy, vz, Q bits),
+// using the stream-1 words of particle `first`; updates the records in place.
+__device__ __forceinline__ void collide(const RunDev& R, float4& ra, float4& rb, float dtc, float m_cell,
+                                        uint32_t first, uint32_t step)
 {
-    float vax = R.vx[a], vay = R.vy[a], vaz = R.vz[a];
-    float vbx = R.vx[b], vby = R.vy[b], vbz = R.vz[b];
-    const uint32_t ma = R.meta[a], mb = R.meta[b];
-    R.meta[a] = ma | kEvCoulomb;
-    R.meta[b] = mb | kEvCoulomb;
-    const float gx = vax - vbx, gy = vay - vby, gz = vaz - vbz;
+    const float gx = ra.x - rb.x, gy = ra.y - rb.y, gz = ra.z - rb.z;
     const float g2 = gx * gx + gy * gy + gz * gz;
     if (!(g2 > 0.0f)) return;
     const float g = sqrtf(g2);
-    const float qq = (float)((ma & kQMask) * (mb & kQMask));
+    const float qq = (float)(__float_as_uint(ra.w) * __float_as_uint(rb.w));
     const float s = R.lnl_ii_coef * (qq * qq) * m_cell * dtc / (g2 * g);
     const Words w = rng_words(R, first, step, 1u);
     const float U = unit01(w.w1);
@@ -199,24 +196,34 @@ __device__ void collide(const RunDev& R, uint32_t a, uint32_t b, float dtc, floa
     const float dgx = 0.5f * (gx * (cchi - 1.0f) + hx * schi);
     const float dgy = 0.5f * (gy * (cchi - 1.0f) + hy * schi);
     const float dgz = 0.5f * (gz * (cchi - 1.0f) + hz * schi);
-    R.vx[a] = vax + dgx; R.vy[a] = vay + dgy; R.vz[a] = vaz + dgz;
-    R.vx[b] = vbx - dgx; R.vy[b] = vby - dgy; R.vz[b] = vbz - dgz;
+    ra.x += dgx; ra.y += dgy; ra.z += dgz;
+    rb.x -= dgx; rb.y -= dgy; rb.z -= dgz;
 }
 
-// ascending bitonic sort of buf[0, m) by one warp; every compare-exchange moves
-// the smaller key to the lower index, so positions >= m act as +infinity and
-// their exchanges are skipped.  Sub-network sizes are powers of two, so block
-// and offset come from shifts and masks.
-__device__ void warp_bitonic(unsigned long long* buf, uint32_t m)
+__device__ __forceinline__ void write_back(const RunDev& R, uint32_t pid, const float4& r)
+{
+    R.vx[pid] = r.x;
+    R.vy[pid] = r.y;
+    R.vz[pid] = r.z;
+    atomicOr(R.meta + pid, kEvCoulomb);   // result unused: a fire-and-forget reduction
+}
+
+// Ascending bitonic sort of keys[0, m) by one warp, with a payload moved along
+// (shared-memory or global arrays).  Every compare-exchange moves the smaller
+// key to the lower index, so positions >= m act as +infinity and their
+// exchanges are skipped.  Sub-network sizes are powers of two, so block and
+// offset come from shifts and masks.
+template <class P>
+__device__ void warp_bitonic(unsigned long long* keys, P* pay, uint32_t m)
 {
     const int lane = threadIdx.x & 31;
-    uint32_t P = 1, lp = 0;
-    while (P < m) { P <<= 1; ++lp; }
+    uint32_t P2 = 1, lp = 0;
+    while (P2 < m) { P2 <<= 1; ++lp; }
     for (uint32_t lk = 1; lk <= lp; ++lk) {
         const uint32_t k = 1u << lk;
         for (int lj = (int)lk - 1; lj >= 0; --lj) {
             const uint32_t j = 1u << lj;
-            for (uint32_t t = lane; t < P / 2; t += 32) {
+            for (uint32_t t = lane; t < P2 / 2; t += 32) {
                 const uint32_t blk = t >> lj, off = t & (j - 1);
                 uint32_t lo, hi;
                 if (lj == (int)lk - 1) {        // first sub-step: mirrored pairs
@@ -227,8 +234,14 @@ __device__ void warp_bitonic(unsigned long long* buf, uint32_t m)
                     hi = lo + j;
                 }
                 if (hi < m) {
-                    const unsigned long long x = buf[lo], y = buf[hi];
-                    if (y < x) { buf[lo] = y; buf[hi] = x; }
+                    const unsigned long long x = keys[lo], y = keys[hi];
+                    if (y < x) {
+                        keys[lo] = y;
+                        keys[hi] = x;
+                        const P px = pay[lo];
+                        pay[lo] = pay[hi];
+                        pay[hi] = px;
+                    }
                 }
             }
             __syncwarp();
@@ -236,37 +249,44 @@ __device__ void warp_bitonic(unsigned long long* buf, uint32_t m)
     }
 }
 
-// the same network on 32 keys held one per lane
-__device__ __forceinline__ unsigned long long lane_sort32(unsigned long long k, int lane)
+// one compare-exchange stage across lanes for (key, index) held one per lane
+__device__ __forceinline__ void lane_cx(unsigned long long& k, uint32_t& i, int partner, bool low)
+{
+    const unsigned long long ok = __shfl_sync(0xFFFFFFFFu, k, partner);
+    const uint32_t oi = __shfl_sync(0xFFFFFFFFu, i, partner);
+    const bool take = low ? (ok < k) : (ok > k);
+    if (take) { k = ok; i = oi; }
+}
+
+// the bitonic network on 32 (key, index) pairs held one per lane
+__device__ __forceinline__ void lane_sort32(unsigned long long& k, uint32_t& i, int lane)
 {
 #pragma unroll
     for (int kk = 2; kk <= 32; kk <<= 1) {
 #pragma unroll
         for (int j = kk >> 1; j > 0; j >>= 1) {
             const int partner = (j == (kk >> 1)) ? (lane ^ (kk - 1)) : (lane ^ j);
-            const unsigned long long o = __shfl_sync(0xFFFFFFFFu, k, partner);
-            k = (lane < partner) ? (o < k ? o : k) : (o > k ? o : k);
+            lane_cx(k, i, partner, lane < partner);
         }
     }
-    return k;
 }
 
-// half-cleaners j = 16 .. 1 on 32 keys held one per lane
-__device__ __forceinline__ unsigned long long lane_clean32(unsigned long long k, int lane)
+// half-cleaners j = 16 .. 1 on 32 pairs held one per lane
+__device__ __forceinline__ void lane_clean32(unsigned long long& k, uint32_t& i, int lane)
 {
 #pragma unroll
     for (int j = 16; j > 0; j >>= 1) {
         const int partner = lane ^ j;
-        const unsigned long long o = __shfl_sync(0xFFFFFFFFu, k, partner);
-        k = (lane < partner) ? (o < k ? o : k) : (o > k ? o : k);
+        lane_cx(k, i, partner, lane < partner);
     }
-    return k;
 }
 
 __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(const __grid_constant__ RunDev R,
-                                                             unsigned int* ticket)
+                                                                unsigned int* ticket)
 {
     __shared__ unsigned long long sk[kCollideWarps][kSmemKeys];
+    __shared__ uint16_t si[kCollideWarps][kSmemKeys];
+    __shared__ float4 sr[kCollideWarps][kSmemKeys];
     __shared__ int s_last;
     const uint32_t step = *R.step;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -274,57 +294,94 @@ __global__ void __launch_bounds__(kCollideThreads, 8) k_collide(const __grid_con
     const uint32_t wstride = gridDim.x * kCollideWarps;
     unsigned long long ncoll = 0;
     const float dt = R.dt;
-    for (uint32_t i = blockIdx.x * kCollideWarps + wib; i < nocc; i += wstride) {
-        const uint32_t cell = R.occ[i];
+    for (uint32_t c = blockIdx.x * kCollideWarps + wib; c < nocc; c += wstride) {
+        const uint32_t cell = R.occ[c];
         const uint32_t off = R.coff[cell];
         const uint32_t m = R.coff[cell + 1] - off;
-        unsigned long long* keys = R.ckeys + off;
-        unsigned long long* buf;
-        if (m <= 64u) {
-            // registers: keys lane and lane + 32; each half is sorted by the
-            // 32-lane network, then one mirrored exchange across the halves and
-            // half-cleaners finish the 64-key network
-            unsigned long long k0 = lane < (int)m ? keys[lane] : ~0ull;
-            unsigned long long k1 = lane + 32 < (int)m ? keys[lane + 32] : ~0ull;
-            k0 = lane_sort32(k0, lane);
-            k1 = lane_sort32(k1, lane);
-            if (m > 32u) {
-                const unsigned long long o0 = __shfl_sync(0xFFFFFFFFu, k1, 31 - lane);
-                const unsigned long long o1 = __shfl_sync(0xFFFFFFFFu, k0, 31 - lane);
-                k0 = o0 < k0 ? o0 : k0;
-                k1 = o1 > k1 ? o1 : k1;
-                k0 = lane_clean32(k0, lane);
-                k1 = lane_clean32(k1, lane);
-            }
-            buf = sk[wib];
-            buf[lane] = k0;
-            buf[lane + 32] = k1;
-            __syncwarp();
-        } else if (m <= (uint32_t)kSmemKeys) {
-            buf = sk[wib];
-            for (uint32_t t = lane; t < m; t += 32) buf[t] = keys[t];
-            __syncwarp();
-            warp_bitonic(buf, m);
-        } else {
-            buf = keys;   // large cell: sort in place in global memory
-            warp_bitonic(buf, m);
-        }
+        unsigned long long* gk = R.ckeys + off;
+        float4* gr = R.crec + off;
         const float mc = (float)m;
-        uint32_t start = 0;
-        if (m & 1u) {
-            if (lane == 0) {
-                const uint32_t p0 = (uint32_t)buf[0], p1 = (uint32_t)buf[1], p2 = (uint32_t)buf[2];
-                collide(R, p0, p1, 0.5f * dt, mc, p0, step);
-                collide(R, p1, p2, 0.5f * dt, mc, p1, step);
-                collide(R, p2, p0, 0.5f * dt, mc, p2, step);
-            }
-            start = 3;
-            __syncwarp();
-        }
+        const uint32_t start = (m & 1u) ? 3u : 0u;
         const uint32_t npairs = (m - start) / 2;
-        for (uint32_t p = lane; p < npairs; p += 32) {
-            const uint32_t a = (uint32_t)buf[start + 2 * p], b = (uint32_t)buf[start + 2 * p + 1];
-            collide(R, a, b, dt, mc, a, step);
+        if (m <= (uint32_t)kSmemKeys) {
+            unsigned long long* K = sk[wib];
+            uint16_t* I = si[wib];
+            float4* Rc = sr[wib];
+            for (uint32_t t = lane; t < m; t += 32) Rc[t] = gr[t];
+            if (m <= 64u) {
+                // registers: pairs lane and lane + 32; each half is sorted by
+                // the 32-lane network, then one mirrored exchange across the
+                // halves and half-cleaners finish the 64-key network
+                unsigned long long k0 = lane < (int)m ? gk[lane] : ~0ull;
+                unsigned long long k1 = lane + 32 < (int)m ? gk[lane + 32] : ~0ull;
+                uint32_t i0 = lane, i1 = lane + 32;
+                lane_sort32(k0, i0, lane);
+                if (m > 32u) {
+                    lane_sort32(k1, i1, lane);
+                    const unsigned long long o0 = __shfl_sync(0xFFFFFFFFu, k1, 31 - lane);
+                    const uint32_t oi0 = __shfl_sync(0xFFFFFFFFu, i1, 31 - lane);
+                    const unsigned long long o1 = __shfl_sync(0xFFFFFFFFu, k0, 31 - lane);
+                    const uint32_t oi1 = __shfl_sync(0xFFFFFFFFu, i0, 31 - lane);
+                    if (o0 < k0) { k0 = o0; i0 = oi0; }
+                    if (o1 > k1) { k1 = o1; i1 = oi1; }
+                    lane_clean32(k0, i0, lane);
+                    lane_clean32(k1, i1, lane);
+                }
+                K[lane] = k0;
+                I[lane] = (uint16_t)i0;
+                K[lane + 32] = k1;
+                I[lane + 32] = (uint16_t)i1;
+                __syncwarp();
+            } else {
+                for (uint32_t t = lane; t < m; t += 32) {
+                    K[t] = gk[t];
+                    I[t] = (uint16_t)t;
+                }
+                __syncwarp();
+                warp_bitonic(K, I, m);
+            }
+            if (start) {
+                if (lane == 0) {
+                    const uint32_t p0 = (uint32_t)K[0], p1 = (uint32_t)K[1], p2 = (uint32_t)K[2];
+                    float4 r0 = Rc[I[0]], r1 = Rc[I[1]], r2 = Rc[I[2]];
+                    collide(R, r0, r1, 0.5f * dt, mc, p0, step);
+                    collide(R, r1, r2, 0.5f * dt, mc, p1, step);
+                    collide(R, r2, r0, 0.5f * dt, mc, p2, step);
+                    Rc[I[0]] = r0; Rc[I[1]] = r1; Rc[I[2]] = r2;
+                }
+                __syncwarp();
+            }
+            for (uint32_t p = lane; p < npairs; p += 32) {
+                const uint32_t a = start + 2 * p, b = a + 1;
+                float4 ra = Rc[I[a]], rb = Rc[I[b]];
+                collide(R, ra, rb, dt, mc, (uint32_t)K[a], step);
+                Rc[I[a]] = ra;
+                Rc[I[b]] = rb;
+            }
+            __syncwarp();
+            for (uint32_t t = lane; t < m; t += 32) write_back(R, (uint32_t)K[t], Rc[I[t]]);
+        } else {
+            // large cell: sort keys and records together in place in global memory
+            warp_bitonic(gk, gr, m);
+            if (start) {
+                if (lane == 0) {
+                    float4 r0 = gr[0], r1 = gr[1], r2 = gr[2];
+                    collide(R, r0, r1, 0.5f * dt, mc, (uint32_t)gk[0], step);
+                    collide(R, r1, r2, 0.5f * dt, mc, (uint32_t)gk[1], step);
+                    collide(R, r2, r0, 0.5f * dt, mc, (uint32_t)gk[2], step);
+                    gr[0] = r0; gr[1] = r1; gr[2] = r2;
+                }
+                __syncwarp();
+            }
+            for (uint32_t p = lane; p < npairs; p += 32) {
+                const uint32_t a = start + 2 * p, b = a + 1;
+                float4 ra = gr[a], rb = gr[b];
+                collide(R, ra, rb, dt, mc, (uint32_t)gk[a], step);
+                gr[a] = ra;
+                gr[b] = rb;
+            }
+            __syncwarp();
+            for (uint32_t t = lane; t < m; t += 32) write_back(R, (uint32_t)gk[t], gr[t]);
         }
         if (lane == 0) ncoll += npairs + (start ? 3u : 0u);
         __syncwarp();
@@ -356,17 +413,14 @@ int collide_blocks_per_sm()
     return b;
 }
 
-cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t n4, unsigned int* ticket, int grid,
+cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t ntiles, unsigned int* ticket, int grid,
                            cudaStream_t s)
 {
     const int nb = coulomb_scan_blocks(ncells);
     k_scan_a<<<nb, kScanThreads, 0, s>>>(R, ncells);
     k_scan_b<<<1, 1024, 0, s>>>(R, (uint32_t)nb, ncells);
     k_scan_c<<<nb, kScanThreads, 0, s>>>(R, ncells);
-    int sb = (int)((n4 + 255) / 256);
-    if (sb > 8192) sb = 8192;
-    if (sb < 1) sb = 1;
-    k_scatter<<<sb, 256, 0, s>>>(R, n4);
+    if (ntiles > 0) k_scatter<<<ntiles, 256, 0, s>>>(R, ntiles);
     k_collide<<<grid, kCollideThreads, 0, s>>>(R, ticket);
     return cudaGetLastError();
 }

@@ -63,7 +63,13 @@ struct RunDev {
     // geometry
     float R0, R0sq, L, r_ap_sq, eps_wall;
     float inlet_x, inlet_y, inlet_z;
-    float gband;                 // unused by kernels; kept for layout stability
+    // fixed-point positions: x = X sxy, y = Y sxy, z = (Z + 2^31) sz for int32
+    // X, Y, Z, a uniform grid of 2^32 points across [-R0, R0) and [0, L)
+    float sxy, inv_sxy, sz, inv_sz;
+    float dt_sxy, dt_sz;         // dt / sxy, dt / sz: displacement per unit velocity
+    int32_t inlet_X, inlet_Y, inlet_Z;   // gas inlet in fixed point
+    // FP64 geometry for the (rare) wall and aperture crossings
+    double R0_d, L_d, r_ap_d, eps_wall_d, sxy_d, sz_d;
     // synthetic mirror B0(z): raised-cosine halves around z_m
     float B_min, aL, aR;         // half amplitudes (B_inj-B_min)/2, (B_ext-B_min)/2
     float zm, inv_zm, inv_zr;    // z_m, 1/z_m, 1/(L-z_m)
@@ -89,19 +95,23 @@ struct RunDev {
     float lnl_ii_coef;           // Nanbu s prefactor lnL/(4 pi) (e^2/(eps0 mu))^2 w / V_cell
     uint32_t seed_lo, seed_hi;
     // arrays
-    float *x, *y, *z, *vx, *vy, *vz;
+    int32_t *x, *y, *z;          // fixed-point positions (see sxy, sz)
+    float *vx, *vy, *vz;
     uint32_t *meta;
     const float4 *cell;          // {n_e (m^-3), zone (0/1), delta_x, delta_y}
     const float4 *E;             // {E_x, E_y, E_z, 0} per cell centre
     const float *kdt;            // ionisation rate * dt, [zone * 64 + Q]
     unsigned long long *dep;     // packed deposit accumulator: count << 32 | charge
     unsigned long long *tally;   // kTallyWords
-    uint32_t *ckey;              // Coulomb cell key per particle (kNoCell if not taking part)
-    uint32_t *crank;             // arrival rank of a Coulomb participant in its cell
-    uint32_t *ccount;            // Coulomb participants per cell (zeroed by the scan)
+    uint2 *plist;                // Coulomb participants of each tile: (pid, cell), kTile slots a tile
+    float4 *pvel;                // their (vx, vy, vz, Q as bits), same slots
+    uint32_t *tcount;            // participants per tile
+    uint32_t *ccount;            // Coulomb participants per cell (counted up by the step kernel,
+                                 // counted back to zero by the scatter)
     uint32_t *coff;              // exclusive scan of ccount, Nc + 1 entries
     uint32_t *cblk;              // scan block totals
     unsigned long long *ckeys;   // (pairing hash << 32 | pid) per participant, grouped by cell
+    float4 *crec;                // (vx, vy, vz, Q as bits) per participant, grouped by cell
     uint32_t *occ;               // cells with >= 2 participants this step
     uint32_t *occ_n;             // number of entries in occ
     const float *nanbu;          // ln A at ln s = nanbu_lnlo + i / nanbu_inv_dln, i < kNanbuN
@@ -215,16 +225,23 @@ __device__ __forceinline__ void efield(const RunDev& R, float x, float y, float 
          w001 * a001.z + w101 * a101.z + w011 * a011.z + w111 * a111.z;
 }
 
-// nearest-grid-point cell of a position, clamped into the mesh
-__device__ __forceinline__ uint32_t ngp_cell(const RunDev& R, float x, float y, float z)
+// fixed point <-> metres
+__device__ __forceinline__ float fx_xy(const RunDev& R, int32_t X) { return (float)X * R.sxy; }
+__device__ __forceinline__ float fx_z(const RunDev& R, int32_t Z) { return ((float)Z + 2147483648.0f) * R.sz; }
+__device__ __forceinline__ int32_t to_fx_xy(const RunDev& R, float x) { return __float2int_rn(x * R.inv_sxy); }
+__device__ __forceinline__ int32_t to_fx_z(const RunDev& R, float z)
 {
-    int ix = __float2int_rd((x + R.R0) * R.inv_dx);
-    int iy = __float2int_rd((y + R.R0) * R.inv_dy);
-    int iz = __float2int_rd(z * R.inv_dz);
-    ix = min(max(ix, 0), R.nx - 1);
-    iy = min(max(iy, 0), R.ny - 1);
-    iz = min(max(iz, 0), R.nz - 1);
-    return (uint32_t)((iz * R.ny + iy) * R.nx + ix);
+    return (int32_t)(__float2uint_rn(z * R.inv_sz) ^ 0x80000000u);
+}
+
+// nearest-grid-point cell of a fixed-point position: with U = X + 2^31 the
+// cell is floor(U n / 2^32), the high word of a 32x32-bit product (exact)
+__device__ __forceinline__ uint32_t ngp_cell(const RunDev& R, int32_t X, int32_t Y, int32_t Z)
+{
+    const uint32_t ix = __umulhi((uint32_t)X ^ 0x80000000u, (uint32_t)R.nx);
+    const uint32_t iy = __umulhi((uint32_t)Y ^ 0x80000000u, (uint32_t)R.ny);
+    const uint32_t iz = __umulhi((uint32_t)Z ^ 0x80000000u, (uint32_t)R.nz);
+    return (iz * (uint32_t)R.ny + iy) * (uint32_t)R.nx + ix;
 }
 
 // ----------------------------------------------------------------------------
@@ -241,12 +258,16 @@ struct LoadCheck {
     float R0sq, L;
     uint32_t qmax;
     float inlet_x, inlet_y, inlet_z;
+    double inv_sxy, inv_sz;      // metres -> fixed point
 };
-// check particles [0, n), build their meta words from q8, fill pads [n, cap);
-// bad[0] counts invalid particles, bad[1] holds the lowest invalid index
+// check particles [0, n), convert their positions (metres, float) in place to
+// fixed point, build their meta words from q8, fill pads [n, cap); bad[0]
+// counts invalid particles, bad[1] holds the lowest invalid index
 cudaError_t launch_load_init(const LoadCheck& lc, float* const soa[6], const uint8_t* q8, uint32_t* meta,
                              uint32_t n, uint32_t cap, unsigned int* bad, cudaStream_t s);
 cudaError_t launch_census(const RunDev& R, uint32_t n4, unsigned long long* census, cudaStream_t s);
+// convert n fixed-point positions in place (device buffers) to metres (float)
+cudaError_t launch_export(void* x, void* y, void* z, uint32_t n, double sxy, double sz, cudaStream_t s);
 // resident blocks per SM of the step kernel
 int step_blocks_per_sm();
 
@@ -255,7 +276,7 @@ int step_blocks_per_sm();
 // the per-cell sort / pair / collide kernel, whose last block advances the
 // step counter.
 constexpr int kCoulombKernels = 5;   // kernels per launch_coulomb
-cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t n4, unsigned int* ticket, int grid,
+cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t ntiles, unsigned int* ticket, int grid,
                            cudaStream_t s);
 int coulomb_scan_blocks(uint32_t ncells);
 int collide_blocks_per_sm();

@@ -48,8 +48,8 @@ __device__ __forceinline__ float event_prob(float lam)
     return -expm1f(-lam);
 }
 
-__device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uint32_t step, float& x,
-                                              float& y, float& z, float& vx, float& vy, float& vz,
+__device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uint32_t step, int32_t& X,
+                                              int32_t& Y, int32_t& Z, float& vx, float& vy, float& vz,
                                               uint32_t& meta, BlockTally& T,
                                               unsigned long long& ke_acc, uint32_t& ckey)
 {
@@ -61,9 +61,10 @@ __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uin
     }
     uint32_t Q = meta & kQMask;
     uint32_t ev = 0;
-    const float x0 = x, y0 = y, z0 = z;
+    const float x0 = fx_xy(R, X), y0 = fx_xy(R, Y), z0 = fx_z(R, Z);
 
     // ---- push: Boris rotation for ions, straight line for atoms ----
+    long long xn = X, yn = Y, zn = Z;
     if (R.flags & kFPush) {
         if (Q > 0) {
             float Bx, By, Bz, Ex, Ey, Ez;
@@ -83,40 +84,56 @@ __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uin
             vy = my + h * Ey;
             vz = mz + h * Ez;
         }
-        x = x0 + vx * R.dt;
-        y = y0 + vy * R.dt;
-        z = z0 + vz * R.dt;
+        // displacement in fixed-point units, rounded to nearest; bounded so a
+        // runaway velocity cannot wrap the 64-bit sums
+        xn += __float2ll_rn(fminf(fmaxf(vx * R.dt_sxy, -1e12f), 1e12f));
+        yn += __float2ll_rn(fminf(fmaxf(vy * R.dt_sxy, -1e12f), 1e12f));
+        zn += __float2ll_rn(fminf(fmaxf(vz * R.dt_sz, -1e12f), 1e12f));
     }
 
-    // ---- boundary test on the new position ----
-    const bool out_r = x * x + y * y > R.R0sq;
-    const bool out_0 = z < 0.0f;
-    const bool out_L = z > R.L;
-    uint32_t cell;
+    // cell record and random words of the new position, fetched before the
+    // boundary test so their latency overlaps it (leavers discard them)
+    const long long lim = 2147483648ll;   // 2^31
+    const int32_t Xc = (int32_t)max(min(xn, lim - 1), -lim);
+    const int32_t Yc = (int32_t)max(min(yn, lim - 1), -lim);
+    const int32_t Zc = (int32_t)max(min(zn, lim - 1), -lim);
+    uint32_t cell = ngp_cell(R, Xc, Yc, Zc);
+    const float4 cr = __ldg(R.cell + cell);   // n_e, zone, delta_x, delta_y
+    const Words w = rng_words(R, pid, step, 0u);
+
+    // ---- boundary test on the new position, exact in fixed point ----
+    const bool out_r = xn < -lim || xn >= lim || yn < -lim || yn >= lim ||
+                       xn * xn + yn * yn > (1ll << 62);
+    const bool out_0 = zn < -lim;
+    const bool out_L = zn >= lim;
     if (out_r | out_0 | out_L) {
-        // first crossing along the straight segment
-        const float dx = x - x0, dy = y - y0, dz = z - z0;
-        float fbest = 2.0f;
+        // first crossing along the straight segment, in FP64 from the exact
+        // fixed-point coordinates (leavers are rare, so the cost is small)
+        const double sxy = R.sxy_d, szd = R.sz_d;
+        const double dx0 = (double)X * sxy, dy0 = (double)Y * sxy, dz0 = ((double)Z + 2147483648.0) * szd;
+        const double ddx = (double)(xn - X) * sxy, ddy = (double)(yn - Y) * sxy, ddz = (double)(zn - Z) * szd;
+        double fbest = 2.0;
         int kind = 0;
         if (out_r) {
-            const float a = dx * dx + dy * dy, b = x0 * dx + y0 * dy;
-            const float c = x0 * x0 + y0 * y0 - R.R0sq;
-            const float disc = sqrtf(fmaxf(0.0f, b * b - a * c));
-            float f = (b + disc > 0.0f) ? -c / (b + disc) : 0.0f;
-            f = fmaxf(f, 0.0f);
+            // |p0 + f d|^2 = R0^2 with c = |p0|^2 - R0^2 <= 0, taken exactly in fixed point
+            const double a = ddx * ddx + ddy * ddy, b = dx0 * ddx + dy0 * ddy;
+            const double c = (double)((long long)X * X + (long long)Y * Y - (1ll << 62)) * sxy * sxy;
+            const double disc = sqrt(fmax(0.0, b * b - a * c));
+            double f = (b + disc > 0.0) ? -c / (b + disc) : 0.0;
+            f = fmax(f, 0.0);
             fbest = f;
             kind = 1;
         }
         if (out_0) {
-            const float f = z0 / (z0 - z);
+            const double f = (double)((long long)Z + lim) / (double)((long long)Z - zn);
             if (f < fbest) { fbest = f; kind = 2; }
         }
         if (out_L) {
-            const float f = (R.L - z0) / (z - z0);
+            const double f = (double)(lim - (long long)Z) / (double)(zn - (long long)Z);
             if (f < fbest) { fbest = f; kind = 3; }
         }
-        float cx = x0 + fbest * dx, cy = y0 + fbest * dy, cz = z0 + fbest * dz;
-        if (kind == 3 && cx * cx + cy * cy < R.r_ap_sq) kind = 4;
+        double cxd = dx0 + fbest * ddx, cyd = dy0 + fbest * ddy, czd = dz0 + fbest * ddz;
+        if (kind == 3 && cxd * cxd + cyd * cyd < R.r_ap_d * R.r_ap_d) kind = 4;
 
         // ---- wall / aperture bookkeeping ----
         if (Q >= 1) ke_acc += __float2ull_rn(R.ke_scale * (vx * vx + vy * vy + vz * vz));
@@ -129,34 +146,43 @@ __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uin
         }
         Q = 0;
         if (!(R.flags & kFRecycle)) {
-            meta = status | kStFrozen | ev;   // stays at its last position, never moves again
+            // frozen at its last position, clamped into the fixed-point range
+            X = Xc;
+            Y = Yc;
+            Z = Zc;
+            meta = status | kStFrozen | ev;
             return;
         }
-        const Words w = rng_words(R, pid, step, 2u);
+        const Words u = rng_words(R, pid, step, 2u);
         if (kind == 4) {
-            cx = R.inlet_x; cy = R.inlet_y; cz = R.inlet_z;
-            emit(R.sig0, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, w, vx, vy, vz);
+            X = R.inlet_X; Y = R.inlet_Y; Z = R.inlet_Z;
+            emit(R.sig0, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, u, vx, vy, vz);
         } else if (kind == 1) {
-            const float rc = sqrtf(cx * cx + cy * cy);
-            const float ux = cx / rc, uy = cy / rc;
-            const float sc = (R.R0 - R.eps_wall) / rc;
-            cx *= sc; cy *= sc;
-            emit(R.sig0, -ux, -uy, 0.f, -uy, ux, 0.f, 0.f, 0.f, 1.f, w, vx, vy, vz);
+            const double rc = sqrt(cxd * cxd + cyd * cyd);
+            const float ux = (float)(cxd / rc), uy = (float)(cyd / rc);
+            const double sc = (R.R0_d - R.eps_wall_d) / rc;
+            X = (int32_t)rint(cxd * sc / sxy);
+            Y = (int32_t)rint(cyd * sc / sxy);
+            Z = (int32_t)(long long)rint(czd / szd - 2147483648.0);
+            emit(R.sig0, -ux, -uy, 0.f, -uy, ux, 0.f, 0.f, 0.f, 1.f, u, vx, vy, vz);
         } else if (kind == 2) {
-            cz = R.eps_wall;
-            emit(R.sig0, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, w, vx, vy, vz);
+            X = (int32_t)rint(cxd / sxy);
+            Y = (int32_t)rint(cyd / sxy);
+            Z = (int32_t)(long long)rint(R.eps_wall_d / szd - 2147483648.0);
+            emit(R.sig0, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, u, vx, vy, vz);
         } else {
-            cz = R.L - R.eps_wall;
-            emit(R.sig0, 0.f, 0.f, -1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, w, vx, vy, vz);
+            X = (int32_t)rint(cxd / sxy);
+            Y = (int32_t)rint(cyd / sxy);
+            Z = (int32_t)(long long)rint((R.L_d - R.eps_wall_d) / szd - 2147483648.0);
+            emit(R.sig0, 0.f, 0.f, -1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, u, vx, vy, vz);
         }
-        x = cx; y = cy; z = cz;
-        cell = ngp_cell(R, x, y, z);
+        cell = ngp_cell(R, X, Y, Z);
     } else {
         // ---- MCC in the particle's cell ----
-        cell = ngp_cell(R, x, y, z);
-        const float4 cr = __ldg(R.cell + cell);   // n_e, zone, delta_x, delta_y
+        X = Xc;
+        Y = Yc;
+        Z = Zc;
         const int zone = cr.y > 0.5f ? 1 : 0;
-        const Words w = rng_words(R, pid, step, 0u);
         if ((R.flags & kFIonize) && (int)Q < R.qmax) {
             const float lam = cr.x * __ldg(R.kdt + zone * kQSlots + Q);
             if (fires(w.w0, event_prob(lam))) { Q += 1; ev |= kEvIonize; }
@@ -204,7 +230,7 @@ __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uin
         }
         if (Q >= 1 && (R.flags & kFCoulomb)) {
             ckey = cell;
-            R.crank[pid] = atomicAdd(R.ccount + cell, 1u);
+            atomicAdd(R.ccount + cell, 1u);   // result unused: a fire-and-forget reduction
         }
     }
 
@@ -280,14 +306,15 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 
 // One stage of the tile pipeline: SoA copies of a tile's particles.
 struct Stage {
-    float4 x[kThreads], y[kThreads], z[kThreads], vx[kThreads], vy[kThreads], vz[kThreads];
+    int4 x[kThreads], y[kThreads], z[kThreads];
+    float4 vx[kThreads], vy[kThreads], vz[kThreads];
     uint4 meta[kThreads];
 };
 
 struct StepShared {
     Stage st[2];
-    uint4 ckey[kThreads];
     uint16_t order[kTile];
+    uint32_t npart;
     uint32_t warp_ions[kThreads / 32], warp_atoms[kThreads / 32];
     BlockTally T;
     uint64_t bar[2];
@@ -297,6 +324,7 @@ struct StepShared {
 
 __device__ __forceinline__ float& sf(float4* a, uint32_t i) { return reinterpret_cast<float*>(a)[i]; }
 __device__ __forceinline__ uint32_t& su(uint4* a, uint32_t i) { return reinterpret_cast<uint32_t*>(a)[i]; }
+__device__ __forceinline__ int32_t& si(int4* a, uint32_t i) { return reinterpret_cast<int32_t*>(a)[i]; }
 
 // issue the seven bulk loads of tile t into stage st (thread 0 only)
 __device__ __forceinline__ void load_tile(const RunDev& R, Stage& st, uint64_t* bar, uint32_t t)
@@ -305,9 +333,9 @@ __device__ __forceinline__ void load_tile(const RunDev& R, Stage& st, uint64_t* 
     const uint32_t ng = min((uint32_t)kThreads, R.n4 - g0);
     const uint32_t bytes = ng * 16u;
     mbar_expect_tx(bar, 7u * bytes);
-    bulk_load(st.x, reinterpret_cast<const float4*>(R.x) + g0, bytes, bar);
-    bulk_load(st.y, reinterpret_cast<const float4*>(R.y) + g0, bytes, bar);
-    bulk_load(st.z, reinterpret_cast<const float4*>(R.z) + g0, bytes, bar);
+    bulk_load(st.x, reinterpret_cast<const int4*>(R.x) + g0, bytes, bar);
+    bulk_load(st.y, reinterpret_cast<const int4*>(R.y) + g0, bytes, bar);
+    bulk_load(st.z, reinterpret_cast<const int4*>(R.z) + g0, bytes, bar);
     bulk_load(st.vx, reinterpret_cast<const float4*>(R.vx) + g0, bytes, bar);
     bulk_load(st.vy, reinterpret_cast<const float4*>(R.vy) + g0, bytes, bar);
     bulk_load(st.vz, reinterpret_cast<const float4*>(R.vz) + g0, bytes, bar);
@@ -352,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ Ru
         const uint32_t g = t * kThreads + tid;
         const bool valid = g < R.n4;
         const uint4 M = valid ? st.meta[tid] : make_uint4(kStPad, kStPad, kStPad, kStPad);
-        if (coulomb) S.ckey[tid] = make_uint4(kNoCell, kNoCell, kNoCell, kNoCell);
+        if (tid == 0) S.npart = 0u;
         // classify: live ions, live atoms (frozen and padding slots are left alone)
         const uint32_t mm[4] = {M.x, M.y, M.z, M.w};
         uint32_t nion = 0, natom = 0;
@@ -394,14 +422,19 @@ __global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ Ru
         unsigned long long ke = 0ull;
         for (uint32_t i = tid; i < nlive; i += kThreads) {
             const uint32_t k = S.order[i];
-            float x = sf(st.x, k), y = sf(st.y, k), z = sf(st.z, k);
+            int32_t x = si(st.x, k), y = si(st.y, k), z = si(st.z, k);
             float vx = sf(st.vx, k), vy = sf(st.vy, k), vz = sf(st.vz, k);
             uint32_t meta = su(st.meta, k), ck;
             step_particle(R, pid0 + k, step, x, y, z, vx, vy, vz, meta, S.T, ke, ck);
-            sf(st.x, k) = x; sf(st.y, k) = y; sf(st.z, k) = z;
+            si(st.x, k) = x; si(st.y, k) = y; si(st.z, k) = z;
             sf(st.vx, k) = vx; sf(st.vy, k) = vy; sf(st.vz, k) = vz;
             su(st.meta, k) = meta;
-            if (coulomb) su(S.ckey, k) = ck;
+            if (coulomb && ck != kNoCell) {
+                // publish the participant for the collision kernels
+                const uint32_t slot = t * kTile + atomicAdd(&S.npart, 1u);
+                R.plist[slot] = make_uint2(pid0 + k, ck);
+                R.pvel[slot] = make_float4(vx, vy, vz, __uint_as_float(meta & kQMask));
+            }
         }
         ke = warp_sum(ke);
         if (lane == 0 && ke) atomicAdd(&S.T.ke, ke);
@@ -410,16 +443,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ Ru
         if (tid == 0) {
             const uint32_t g0 = t * kThreads;
             const uint32_t bytes = min((uint32_t)kThreads, R.n4 - g0) * 16u;
-            bulk_store(reinterpret_cast<float4*>(R.x) + g0, st.x, bytes);
-            bulk_store(reinterpret_cast<float4*>(R.y) + g0, st.y, bytes);
-            bulk_store(reinterpret_cast<float4*>(R.z) + g0, st.z, bytes);
+            bulk_store(reinterpret_cast<int4*>(R.x) + g0, st.x, bytes);
+            bulk_store(reinterpret_cast<int4*>(R.y) + g0, st.y, bytes);
+            bulk_store(reinterpret_cast<int4*>(R.z) + g0, st.z, bytes);
             bulk_store(reinterpret_cast<float4*>(R.vx) + g0, st.vx, bytes);
             bulk_store(reinterpret_cast<float4*>(R.vy) + g0, st.vy, bytes);
             bulk_store(reinterpret_cast<float4*>(R.vz) + g0, st.vz, bytes);
             bulk_store(reinterpret_cast<uint4*>(R.meta) + g0, st.meta, bytes);
             bulk_commit();
         }
-        if (coulomb && valid) reinterpret_cast<uint4*>(R.ckey)[g] = S.ckey[tid];
+        if (coulomb && tid == 0) R.tcount[t] = S.npart;
         for (int i = tid; i < kQSlots; i += kThreads) {
             if (S.T.ext[i]) atomicAdd(R.tally + kTallyExtracted + i, (unsigned long long)S.T.ext[i]);
             if (S.T.lost[i]) atomicAdd(R.tally + kTallyLost + i, (unsigned long long)S.T.lost[i]);
@@ -487,6 +520,18 @@ __global__ void k_census(const __grid_constant__ RunDev R, uint32_t n4,
 
 struct SoaPtrs { float* p[6]; };
 
+// metres -> fixed point (FP64 products, rounded to nearest, saturated)
+__device__ __forceinline__ void store_fx(SoaPtrs soa, uint32_t i, float x, float y, float z, const LoadCheck& lc)
+{
+    const double lim = 2147483647.0;
+    const double X = fmin(fmax(rint((double)x * lc.inv_sxy), -lim - 1.0), lim);
+    const double Y = fmin(fmax(rint((double)y * lc.inv_sxy), -lim - 1.0), lim);
+    const double Z = fmin(fmax(rint((double)z * lc.inv_sz) - 2147483648.0, -lim - 1.0), lim);
+    reinterpret_cast<int32_t*>(soa.p[0])[i] = (int32_t)X;
+    reinterpret_cast<int32_t*>(soa.p[1])[i] = (int32_t)Y;
+    reinterpret_cast<int32_t*>(soa.p[2])[i] = (int32_t)Z;
+}
+
 __global__ void k_load_init(LoadCheck lc, SoaPtrs soa, const uint8_t* __restrict__ q8,
                             uint32_t* __restrict__ meta, uint32_t n, uint32_t cap,
                             unsigned int* __restrict__ bad)
@@ -503,10 +548,9 @@ __global__ void k_load_init(LoadCheck lc, SoaPtrs soa, const uint8_t* __restrict
                 atomicMin(bad + 1, i);
             }
             meta[i] = q;
+            store_fx(soa, i, x, y, z, lc);
         } else {
-            soa.p[0][i] = lc.inlet_x;
-            soa.p[1][i] = lc.inlet_y;
-            soa.p[2][i] = lc.inlet_z;
+            store_fx(soa, i, lc.inlet_x, lc.inlet_y, lc.inlet_z, lc);
             soa.p[3][i] = 0.0f;
             soa.p[4][i] = 0.0f;
             soa.p[5][i] = 0.0f;
@@ -515,7 +559,28 @@ __global__ void k_load_init(LoadCheck lc, SoaPtrs soa, const uint8_t* __restrict
     }
 }
 
+__global__ void k_export(int32_t* x, int32_t* y, int32_t* z, uint32_t n, double sxy, double sz)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float fx = (float)((double)x[i] * sxy);
+        const float fy = (float)((double)y[i] * sxy);
+        const float fz = (float)(((double)z[i] + 2147483648.0) * sz);
+        reinterpret_cast<float*>(x)[i] = fx;
+        reinterpret_cast<float*>(y)[i] = fy;
+        reinterpret_cast<float*>(z)[i] = fz;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_export(void* x, void* y, void* z, uint32_t n, double sxy, double sz, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    k_export<<<blocks, 256, 0, s>>>((int32_t*)x, (int32_t*)y, (int32_t*)z, n, sxy, sz);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_load_init(const LoadCheck& lc, float* const soa[6], const uint8_t* q8, uint32_t* meta,
                              uint32_t n, uint32_t cap, unsigned int* bad, cudaStream_t s)

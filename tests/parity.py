@@ -62,9 +62,15 @@ def compare_step(rp, g1, orc, pos_rel=1e-6, vel_rel=1e-5, v_floor=None, mask=O.G
     vel_bad = np.zeros_like(ok)
     for k in ("vx", "vy", "vz"):
         vel_bad |= same & (np.abs(g1[k].astype(np.float64) - getattr(orc, k)) > vel_rel * (vmag + v_floor))
+    bad = np.nonzero(q_bad | ev_bad | pos_bad | vel_bad)[0]
+    detail = None
+    if len(bad):
+        i = int(bad[0])
+        detail = {"i": i, "gpu": [float(g1[k][i]) for k in KEYS] + [int(g1["q"][i]), int(ev_g[i])],
+                  "oracle": [float(getattr(orc, k)[i]) for k in KEYS] + [int(orc.q[i]), int(orc.events[i])],
+                  "guard": int(orc.guard[i])}
     return {"q": int(q_bad.sum()), "events": int(ev_bad.sum()), "pos": int(pos_bad.sum()),
-            "vel": int(vel_bad.sum()), "guarded": int((~ok).sum()),
-            "bad_idx": np.nonzero(q_bad | ev_bad | pos_bad | vel_bad)[0][:10]}
+            "vel": int(vel_bad.sum()), "guarded": int((~ok).sum()), "detail": detail}
 
 
 def lockstep(run, rp, state0, steps, E=None, ne_cells=None, pos_rel=1e-6, vel_rel=1e-5, mask=O.G_SINGLE):
@@ -85,7 +91,8 @@ def lockstep(run, rp, state0, steps, E=None, ne_cells=None, pos_rel=1e-6, vel_re
         for k in ("q", "events", "pos", "vel", "guarded"):
             totals[k] += r[k]
         if first_bad is None and (r["q"] or r["events"] or r["pos"] or r["vel"]):
-            first_bad = (s, r)
+            first_bad = {"step": s, "before": {k: float(g0[k][r["detail"]["i"]]) for k in KEYS},
+                         **r["detail"]}
         for b in range(4):
             seen[b] += int(((orc.events >> b) & 1).sum())
     totals["events_seen"] = seen[:4].tolist()

@@ -34,7 +34,8 @@ def busy_case(n=3001, seed=4):
 
 
 def assert_clean(t):
-    assert t["q"] == 0 and t["events"] == 0 and t["pos"] == 0 and t["vel"] == 0, t
+    assert t["q"] == 0 and t["events"] == 0 and t["pos"] == 0 and t["vel"] == 0, \
+        (t["q"], t["events"], t["pos"], t["vel"], t["first_bad"])
 
 
 def test_lockstep_busy_case_every_event_type(E):
@@ -78,12 +79,10 @@ def test_free_run_small_config_flags_and_positions(E):
     ok = (orc.guard_acc & O.G_SINGLE) == 0
     assert ok.mean() > 0.95
     assert np.array_equal(g["q"][ok], orc.q[ok])
-    # positions within 1e-5 of the chamber size; FP32 rounding accumulated over
-    # 1e3 steps can carry a trajectory across a cell face a step apart from the
-    # oracle's, so a few in 1e3 may reach 1e-4
+    # positions (fixed point on the GPU) within 1e-5 of the chamber size
     for k, sc in (("x", rp.R0), ("y", rp.R0), ("z", rp.L)):
         rel = np.abs(g[k][ok] - getattr(orc, k)[ok]) / sc
-        assert (rel > 1e-5).mean() <= 1e-3 and rel.max() < 1e-4, (k, rel.max(), (rel > 1e-5).sum())
+        assert rel.max() < 1e-5, (k, rel.max(), (rel > 1e-5).sum())
     d = run.diag()
     assert np.array_equal(d["lost"], orc.lost()) or np.abs(d["lost"] - orc.lost()).sum() <= (~ok).sum()
     run.close()
