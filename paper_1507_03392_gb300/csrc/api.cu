@@ -95,6 +95,8 @@ struct HostRun {
     std::vector<double> ip;
     std::vector<int> nout;
     std::vector<double> rate[2];   // m^3/s per Q, zone 0 cold, 1 warm
+    std::vector<float> cell_ne;    // FP32 n_e per cell as the kernels see it (m^-3)
+    std::vector<unsigned char> cell_zone;
     ecris_mcc mcc;
     double zm;
 };
@@ -162,8 +164,8 @@ struct ecris_ctx {
     uint32_t* d_coff = nullptr;
     uint32_t* d_cblk = nullptr;
     unsigned long long* d_ckeys = nullptr;
-    uint32_t* d_occ = nullptr;
-    uint32_t* d_occ_n = nullptr;
+    unsigned long long* d_skeys = nullptr;
+    float4* d_srec = nullptr;
     int collide_grid = 0;
     float* d_soa[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     uint32_t* d_meta = nullptr;
@@ -290,8 +292,8 @@ void free_ions(ecris_ctx* ctx)
     free_async(ctx, ctx->d_coff);
     free_async(ctx, ctx->d_cblk);
     free_async(ctx, ctx->d_ckeys);
-    free_async(ctx, ctx->d_occ);
-    free_async(ctx, ctx->d_occ_n);
+    free_async(ctx, ctx->d_skeys);
+    free_async(ctx, ctx->d_srec);
     ctx->have_ions = false;
     ctx->loaded = false;
     ctx->cap = ctx->cap_cells = 0;
@@ -398,8 +400,8 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.coff = ctx->d_coff;
     R.cblk = ctx->d_cblk;
     R.ckeys = ctx->d_ckeys;
-    R.occ = ctx->d_occ;
-    R.occ_n = ctx->d_occ_n;
+    R.skeys = ctx->d_skeys;
+    R.srec = ctx->d_srec;
     R.nanbu = ctx->d_nanbu;
     R.nanbu_lnlo = (float)std::log(kNanbuSLo);
     R.nanbu_inv_dln = (float)((kNanbuN - 1) / std::log(kNanbuSHi / kNanbuSLo));
@@ -420,6 +422,14 @@ ecris_status upload_dt(ecris_ctx* ctx, double dt)
     for (int zone = 0; zone < 2; ++zone)
         for (int q = 0; q < kQSlots; ++q)
             ctx->h_kdt[zone * kQSlots + q] = q < ctx->h.qmax ? (float)(ctx->h.rate[zone][q] * dt) : 0.0f;
+    // the kernels' FP32 product n_e k_0 dt, maximised over the cells, with a
+    // relative margin that covers any rounding difference in the probability
+    float lam = 0.0f;
+    for (size_t c = 0; c < ctx->h.cell_ne.size(); ++c) {
+        const float v = ctx->h.cell_ne[c] * ctx->h_kdt[(ctx->h.cell_zone[c] ? 1 : 0) * kQSlots];
+        if (v > lam) lam = v;
+    }
+    ctx->h_run->lam0_max = lam * 1.0001f;
     CK(cudaMemcpyAsync(ctx->d_kdt, ctx->h_kdt, 2 * kQSlots * sizeof(float), cudaMemcpyHostToDevice,
                        ctx->stream));
     ctx->dt_loaded = dt;
@@ -521,6 +531,8 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
     if (!(grid->ne_in_cm3 >= 0.0) || !(grid->ne_out_cm3 >= 0.0) || !std::isfinite(grid->ne_in_cm3) ||
         !std::isfinite(grid->ne_out_cm3) || !finite_pos(grid->Te_warm_eV) || !finite_pos(grid->Te_cold_eV))
         return fail(ctx, ECRIS_EINVAL, "init_fields: need n_e >= 0 and T_e > 0");
+    if ((mcc->flags & kFCoulomb) && (double)grid->nx * grid->ny * grid->nz >= 67108864.0)
+        return fail(ctx, ECRIS_EINVAL, "init_fields: Coulomb collisions need Nc < 2^26 cells");
     if (!finite_pos(sp->mass_amu) || sp->qmax < 1 || sp->qmax > 63 || !sp->ip_eV || !sp->n_outer)
         return fail(ctx, ECRIS_EINVAL, "init_fields: need mass > 0, 1 <= qmax <= 63, ip and n_outer");
     for (int q = 0; q < sp->qmax; ++q)
@@ -576,6 +588,8 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
                 ne[c] = 1e6 * (zone[c] ? nin : grid->ne_out_cm3);
             }
     std::vector<float4> cell(nc);
+    h.cell_ne.assign(nc, 0.0f);
+    h.cell_zone.assign(nc, 0);
     auto NE = [&](int iz, int iy, int ix) {
         iy = iy < 0 ? 0 : (iy >= h.ny ? h.ny - 1 : iy);
         ix = ix < 0 ? 0 : (ix >= h.nx ? h.nx - 1 : ix);
@@ -600,6 +614,8 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
                     dly = -rl * sy;
                 }
                 cell[c] = make_float4((float)ne[c], zone[c] ? 1.0f : 0.0f, (float)dlx, (float)dly);
+                h.cell_ne[c] = (float)ne[c];
+                h.cell_zone[c] = zone[c];
             }
     std::vector<float4> E(nc, make_float4(0.f, 0.f, 0.f, 0.f));
     if (grid->E) {
@@ -675,8 +691,8 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
             CK(cudaMallocAsync((void**)&ctx->d_coff, (nc + 1) * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_cblk, (size_t)coulomb_scan_blocks((uint32_t)nc) * sizeof(uint32_t),
                                ctx->stream));
-            CK(cudaMallocAsync((void**)&ctx->d_occ, nc * sizeof(uint32_t), ctx->stream));
-            CK(cudaMallocAsync((void**)&ctx->d_occ_n, sizeof(uint32_t), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_skeys, cap * sizeof(unsigned long long), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_srec, cap * sizeof(float4), ctx->stream));
         }
         ctx->cap = cap;
         ctx->cap_cells = nc;
@@ -709,8 +725,13 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
     lc.inlet_x = (float)h.geo.inlet[0];
     lc.inlet_y = (float)h.geo.inlet[1];
     lc.inlet_z = (float)h.geo.inlet[2];
-    lc.inv_sxy = 2147483648.0 / h.geo.R0;
-    lc.inv_sz = 4294967296.0 / h.geo.L;
+    {
+        const double a = 2147483648.0 / h.geo.R0, b = 4294967296.0 / h.geo.L;
+        lc.inv_sxy_hi = (float)a;
+        lc.inv_sxy_lo = (float)(a - (double)lc.inv_sxy_hi);
+        lc.inv_sz_hi = (float)b;
+        lc.inv_sz_lo = (float)(b - (double)lc.inv_sz_hi);
+    }
     CK(launch_load_init(lc, ctx->d_soa, ctx->d_q8, ctx->d_meta, (uint32_t)n, (uint32_t)cap, ctx->d_bad,
                         ctx->stream));
     unsigned int bad[2] = {0u, 0u};

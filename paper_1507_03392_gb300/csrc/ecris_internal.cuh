@@ -92,6 +92,8 @@ struct RunDev {
     float ei_coef[2];            // D^2 = ei_coef[zone] * n_e * Q^p (zone 0 cold, 1 warm)
     int32_t ei_pow;
     float ke_scale;              // (M/2) / e * 1e6: micro-eV per (m/s)^2
+    float lam0_max;              // bound (with margin) on n_e k_0 dt over all cells: an atom
+                                 // whose word is above its threshold cannot ionise anywhere
     float lnl_ii_coef;           // Nanbu s prefactor lnL/(4 pi) (e^2/(eps0 mu))^2 w / V_cell
     uint32_t seed_lo, seed_hi;
     // arrays
@@ -111,9 +113,9 @@ struct RunDev {
     uint32_t *coff;              // exclusive scan of ccount, Nc + 1 entries
     uint32_t *cblk;              // scan block totals
     unsigned long long *ckeys;   // (pairing hash << 32 | pid) per participant, grouped by cell
-    float4 *crec;                // (vx, vy, vz, Q as bits) per participant, grouped by cell
-    uint32_t *occ;               // cells with >= 2 participants this step
-    uint32_t *occ_n;             // number of entries in occ
+    float4 *crec;                // (vx, vy, vz, cell << 6 | Q as bits) per participant, grouped by cell
+    unsigned long long *skeys;   // ckeys in pairing order within each cell
+    float4 *srec;                // crec in pairing order within each cell
     const float *nanbu;          // ln A at ln s = nanbu_lnlo + i / nanbu_inv_dln, i < kNanbuN
     float nanbu_lnlo, nanbu_inv_dln;
     uint32_t *step;              // device step counter of the run
@@ -258,7 +260,8 @@ struct LoadCheck {
     float R0sq, L;
     uint32_t qmax;
     float inlet_x, inlet_y, inlet_z;
-    double inv_sxy, inv_sz;      // metres -> fixed point
+    float inv_sxy_hi, inv_sxy_lo;   // metres -> fixed point, as an unevaluated FP32 sum
+    float inv_sz_hi, inv_sz_lo;
 };
 // check particles [0, n), convert their positions (metres, float) in place to
 // fixed point, build their meta words from q8, fill pads [n, cap); bad[0]
@@ -275,7 +278,7 @@ int step_blocks_per_sm();
 // bump_step = 0): scan of the cell counts, scatter of the pairing keys, and
 // the per-cell sort / pair / collide kernel, whose last block advances the
 // step counter.
-constexpr int kCoulombKernels = 5;   // kernels per launch_coulomb
+constexpr int kCoulombKernels = 6;   // kernels per launch_coulomb
 cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t ntiles, unsigned int* ticket, int grid,
                            cudaStream_t s);
 int coulomb_scan_blocks(uint32_t ncells);

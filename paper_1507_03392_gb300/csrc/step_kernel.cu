@@ -65,6 +65,15 @@ __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uin
 
     // ---- push: Boris rotation for ions, straight line for atoms ----
     long long xn = X, yn = Y, zn = Z;
+    // an ion's cell record is fetched with its field gather, at the old
+    // position; the push moves it far less than a cell, so it is reused
+    // unless the particle crossed into another cell
+    uint32_t cell_pre = kNoCell;
+    float4 cr = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (Q > 0) {
+        cell_pre = ngp_cell(R, X, Y, Z);
+        cr = __ldg(R.cell + cell_pre);
+    }
     if (R.flags & kFPush) {
         if (Q > 0) {
             float Bx, By, Bz, Ex, Ey, Ez;
@@ -98,7 +107,6 @@ __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uin
     const int32_t Yc = (int32_t)max(min(yn, lim - 1), -lim);
     const int32_t Zc = (int32_t)max(min(zn, lim - 1), -lim);
     uint32_t cell = ngp_cell(R, Xc, Yc, Zc);
-    const float4 cr = __ldg(R.cell + cell);   // n_e, zone, delta_x, delta_y
     const Words w = rng_words(R, pid, step, 0u);
 
     // ---- boundary test on the new position, exact in fixed point ----
@@ -182,8 +190,13 @@ __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uin
         X = Xc;
         Y = Yc;
         Z = Zc;
+        // an atom needs its cell only if its ionisation word could fire in
+        // the densest cell; otherwise no cell can ionise it this step
+        const bool ionize = (R.flags & kFIonize) && (int)Q < R.qmax;
+        const bool need = Q > 0 || (ionize && fires(w.w0, event_prob(R.lam0_max)));
+        if (need && cell != cell_pre) cr = __ldg(R.cell + cell);   // n_e, zone, delta_x, delta_y
         const int zone = cr.y > 0.5f ? 1 : 0;
-        if ((R.flags & kFIonize) && (int)Q < R.qmax) {
+        if (ionize && need) {
             const float lam = cr.x * __ldg(R.kdt + zone * kQSlots + Q);
             if (fires(w.w0, event_prob(lam))) { Q += 1; ev |= kEvIonize; }
         }
@@ -520,13 +533,23 @@ __global__ void k_census(const __grid_constant__ RunDev R, uint32_t n4,
 
 struct SoaPtrs { float* p[6]; };
 
-// metres -> fixed point (FP64 products, rounded to nearest, saturated)
+// v * (hi + lo) rounded to the nearest integer: the FP32 product p = v hi is
+// an integer once |p| >= 2^24, and its rounding error (exact by FMA) plus
+// v lo is added as a small correction
+__device__ __forceinline__ long long scale_round(float v, float hi, float lo)
+{
+    const float p = v * hi;
+    const float e = fmaf(v, hi, -p) + v * lo;
+    return (long long)rintf(p) + (long long)rintf(e + (p - rintf(p)));
+}
+
+// metres -> fixed point, rounded to nearest, saturated
 __device__ __forceinline__ void store_fx(SoaPtrs soa, uint32_t i, float x, float y, float z, const LoadCheck& lc)
 {
-    const double lim = 2147483647.0;
-    const double X = fmin(fmax(rint((double)x * lc.inv_sxy), -lim - 1.0), lim);
-    const double Y = fmin(fmax(rint((double)y * lc.inv_sxy), -lim - 1.0), lim);
-    const double Z = fmin(fmax(rint((double)z * lc.inv_sz) - 2147483648.0, -lim - 1.0), lim);
+    const long long lim = 2147483647ll;
+    const long long X = max(min(scale_round(x, lc.inv_sxy_hi, lc.inv_sxy_lo), lim), -lim - 1);
+    const long long Y = max(min(scale_round(y, lc.inv_sxy_hi, lc.inv_sxy_lo), lim), -lim - 1);
+    const long long Z = max(min(scale_round(z, lc.inv_sz_hi, lc.inv_sz_lo) - 2147483648ll, lim), -lim - 1);
     reinterpret_cast<int32_t*>(soa.p[0])[i] = (int32_t)X;
     reinterpret_cast<int32_t*>(soa.p[1])[i] = (int32_t)Y;
     reinterpret_cast<int32_t*>(soa.p[2])[i] = (int32_t)Z;
