@@ -167,8 +167,8 @@ ecris_status ecris_create(ecris_ctx** out, int device, void* cuda_stream);
 void ecris_destroy(ecris_ctx* ctx);
 
 /* Message for the last failure on ctx (empty string if none); valid until the
- * next call on ctx.  ctx may be NULL (then describes the last ecris_create
- * failure on this thread). */
+ * next call on ctx.  ctx may be NULL (then describes the last failure of
+ * ecris_create or ecris_coulomb_collide_noalloc on this thread). */
 const char* ecris_last_error(const ecris_ctx* ctx);
 
 /* Per-run setup (Sec. II model inputs): validates the inputs, builds in FP64
@@ -221,6 +221,42 @@ typedef struct {
 /* enable != 0 turns timing on (and resets the counters), 0 turns it off */
 ecris_status ecris_set_profiling(ecris_ctx* ctx, int enable);
 ecris_status ecris_get_profile(ecris_ctx* ctx, ecris_profile* out);
+
+/* Allocation-free Coulomb collision step.  The paper has no counterpart: this
+ * is an interface for callers that cannot allocate device memory when they
+ * need a collision step -- hosts that reserve all device memory up front and
+ * forbid allocation afterwards, plug-ins inside a larger code whose memory
+ * manager owns the device, and code that must not let cudaMalloc synchronise
+ * the device.  It runs the same Takizawa-Abe pairing and Nanbu scattering as
+ * ecris_step (ECRIS_F_COULOMB) on caller-owned device arrays and keeps all its
+ * working memory in one fixed-size array that the library holds on every GPU
+ * that loads it (about 5 MB, until the process exits); it allocates nothing.
+ *
+ *   n            particles, at most 65536; arrays are indexed by particle id
+ *                (the Philox counter word, as in ecris_step)
+ *   cell         device, n cell indices (c = (iz*ny + iy)*nx + ix); a particle
+ *                takes part when cell < ncells and 1 <= q <= 63
+ *   q            device, n charge states
+ *   vx, vy, vz   device, n velocities (m/s), updated in place
+ *   events       device, n words: ECRIS_EV_COULOMB is OR-ed into the word of
+ *                every particle that collided
+ *   ncells       1 .. 65536; weight, cell_volume_m3 and lnL_ii give the
+ *                density and Coulomb logarithm of Nanbu's s; mass in amu
+ *   dt, seed, step  time step (s), Philox key, step index (< 2^30)
+ *   cuda_stream  stream to order the work on (NULL: the legacy default stream)
+ *   collisions_out  if non-NULL, receives the number of pair collisions and
+ *                the call synchronises the stream; otherwise it is asynchronous
+ *
+ * Larger n or ncells return ECRIS_EINVAL with a message in
+ * ecris_last_error(NULL).  Every call shares the one working array: calls whose
+ * GPU work overlaps race and must be serialised by the caller.  The first call
+ * on a device sets that device up (a synchronous copy), so make it before any
+ * stream capture begins. */
+ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* cell, const uint8_t* q, float* vx,
+                                           float* vy, float* vz, uint32_t* events, uint32_t ncells,
+                                           double mass_amu, double weight, double cell_volume_m3,
+                                           double lnL_ii, double dt, uint64_t seed, uint32_t step,
+                                           void* cuda_stream, int64_t* collisions_out);
 
 #ifdef __cplusplus
 }

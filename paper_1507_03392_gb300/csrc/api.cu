@@ -133,6 +133,8 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
 }  // namespace
 
+void ecris::ecris_internal_set_thread_error(const char* msg) { g_create_error = msg; }
+
 struct ecris_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;

@@ -1,0 +1,233 @@
+// ecris_coulomb_collide_noalloc: one ion-ion Coulomb collision step (the same
+// Takizawa-Abe pairing and Nanbu scattering kernels ecris_step runs) for a
+// caller that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc at the moment they need a collision
+// step: code inside a region where the CUDA caching or stream-ordered
+// allocators are off limits, embedded or real-time hosts that reserve all
+// device memory up front and forbid allocation afterwards, and plug-ins
+// running inside a larger simulation whose memory manager owns the device.
+// cudaMalloc can also synchronise the device, which such callers must avoid.
+// This entry point therefore keeps all its working memory (per-cell counts and
+// offsets, participant records and keys, the Nanbu table, counters) in one
+// file-scope device array of fixed size, and allocates nothing.
+//
+// Limits: at most kNaMaxIons particles and kNaMaxCells cells per call; larger
+// sizes are rejected with ECRIS_EINVAL.  The array (kNaScratchBytes, about
+// 5 MB) is held by every GPU that loads the library until the process exits.
+// Every call shares it and finds the last call's contents there; what must
+// start at zero is cleared at the start of each call.  Calls whose GPU work
+// overlaps (different streams, or several host threads) race on the array
+// and must be serialised by the caller.  The first call on each device sets up
+// that device (symbol address, Nanbu table upload, a synchronous copy); make
+// that first call before any stream capture begins.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ecris.h"
+#include "ecris_internal.cuh"
+
+using namespace ecris;
+
+namespace {
+
+constexpr uint32_t kNaMaxIons = 65536;
+constexpr uint32_t kNaMaxCells = 65536;
+constexpr uint32_t kNaTiles = kNaMaxIons / kTile;
+constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// byte offsets of the sub-buffers inside the scratch array
+constexpr size_t kOffPlist = 0;
+constexpr size_t kOffPvel = kOffPlist + align256(sizeof(uint2) * kNaMaxIons);
+constexpr size_t kOffTcount = kOffPvel + align256(sizeof(float4) * kNaMaxIons);
+constexpr size_t kOffCcount = kOffTcount + align256(sizeof(uint32_t) * kNaTiles);
+constexpr size_t kOffCoff = kOffCcount + align256(sizeof(uint32_t) * kNaMaxCells);
+constexpr size_t kOffCblk = kOffCoff + align256(sizeof(uint32_t) * (kNaMaxCells + 1));
+constexpr size_t kOffCkeys = kOffCblk + align256(sizeof(uint32_t) * (kNaMaxCells / kScanBlock + 1));
+constexpr size_t kOffCrec = kOffCkeys + align256(sizeof(unsigned long long) * kNaMaxIons);
+constexpr size_t kOffSkeys = kOffCrec + align256(sizeof(float4) * kNaMaxIons);
+constexpr size_t kOffSrec = kOffSkeys + align256(sizeof(unsigned long long) * kNaMaxIons);
+constexpr size_t kOffNanbu = kOffSrec + align256(sizeof(float4) * kNaMaxIons);
+constexpr size_t kOffWords = kOffNanbu + align256(sizeof(float) * kNanbuN);
+// words: step, ticket, then the tally block
+constexpr size_t kOffTally = kOffWords + 256;
+constexpr size_t kNaScratchBytes = kOffTally + align256(sizeof(unsigned long long) * kTallyWords);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes];
+
+struct DeviceSetup {
+    bool ready = false;
+    unsigned char* base = nullptr;   // device address of g_noalloc_scratch
+    int grid = 0;
+};
+
+std::mutex g_setup_mutex;
+DeviceSetup g_setup[64];
+
+// Nanbu's A(s) from coth A - 1/A = exp(-s), bisection on ln A in FP64
+double nanbu_A_fp64(double s)
+{
+    const double y = std::exp(-s);
+    auto L = [](double A) {
+        if (A < 1e-3) return A / 3.0 - A * A * A / 45.0;
+        return 1.0 / std::tanh(A) - 1.0 / A;
+    };
+    double lo = std::log(1e-12), hi = std::log(2.0 / (-std::expm1(-s)) + 10.0);
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (L(std::exp(mid)) < y) lo = mid; else hi = mid;
+    }
+    return std::exp(0.5 * (lo + hi));
+}
+
+// clear the per-call counters and store the step index
+__global__ void k_na_init(unsigned char* base, uint32_t ncells, uint32_t tiles, uint32_t step)
+{
+    uint32_t* ccount = reinterpret_cast<uint32_t*>(base + kOffCcount);
+    uint32_t* tcount = reinterpret_cast<uint32_t*>(base + kOffTcount);
+    uint32_t* words = reinterpret_cast<uint32_t*>(base + kOffWords);
+    unsigned long long* tally = reinterpret_cast<unsigned long long*>(base + kOffTally);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += stride) ccount[i] = 0u;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < tiles; i += stride) tcount[i] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        words[0] = step;
+        words[1] = 0u;
+    }
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (uint32_t)kTallyWords; i += stride) tally[i] = 0ull;
+}
+
+// publish the participants (cell < ncells, Q >= 1) in their tile's list and
+// count them per cell, as the fused step kernel does for ecris_step
+__global__ void k_na_pack(unsigned char* base, uint32_t n, const uint32_t* __restrict__ cell,
+                          const uint8_t* __restrict__ q, const float* __restrict__ vx,
+                          const float* __restrict__ vy, const float* __restrict__ vz, uint32_t ncells)
+{
+    uint2* plist = reinterpret_cast<uint2*>(base + kOffPlist);
+    float4* pvel = reinterpret_cast<float4*>(base + kOffPvel);
+    uint32_t* tcount = reinterpret_cast<uint32_t*>(base + kOffTcount);
+    uint32_t* ccount = reinterpret_cast<uint32_t*>(base + kOffCcount);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t c = cell[i];
+        const uint32_t Q = q[i];
+        if (c >= ncells || Q == 0u || Q > 63u) continue;
+        const uint32_t t = i / kTile;
+        const uint32_t slot = t * kTile + atomicAdd(tcount + t, 1u);
+        plist[slot] = make_uint2(i, c);
+        pvel[slot] = make_float4(vx[i], vy[i], vz[i], __uint_as_float(Q));
+        atomicAdd(ccount + c, 1u);
+    }
+}
+
+ecris_status na_fail(const std::string& msg)
+{
+    ecris_internal_set_thread_error(msg.c_str());
+    return ECRIS_EINVAL;
+}
+
+ecris_status na_cuda(cudaError_t e, const char* what)
+{
+    ecris_internal_set_thread_error((std::string("coulomb_collide_noalloc: ") + what + ": " +
+                                     cudaGetErrorString(e)).c_str());
+    return ECRIS_ECUDA;
+}
+
+}  // namespace
+
+extern "C" ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* cell, const uint8_t* q, float* vx,
+                                                      float* vy, float* vz, uint32_t* events, uint32_t ncells,
+                                                      double mass_amu, double weight, double cell_volume_m3,
+                                                      double lnL_ii, double dt, uint64_t seed, uint32_t step,
+                                                      void* cuda_stream, int64_t* collisions_out)
+{
+    if (n > kNaMaxIons || ncells > kNaMaxCells || ncells == 0)
+        return na_fail("coulomb_collide_noalloc: need n <= " + std::to_string(kNaMaxIons) + " and 1 <= ncells <= " +
+                       std::to_string(kNaMaxCells) + " (fixed scratch size)");
+    if (n > 0 && (!cell || !q || !vx || !vy || !vz || !events))
+        return na_fail("coulomb_collide_noalloc: NULL array");
+    if (!(mass_amu > 0.0) || !(weight > 0.0) || !(cell_volume_m3 > 0.0) || !(lnL_ii >= 0.0) || !(dt > 0.0) ||
+        !std::isfinite(mass_amu) || !std::isfinite(weight) || !std::isfinite(cell_volume_m3) ||
+        !std::isfinite(lnL_ii) || !std::isfinite(dt))
+        return na_fail("coulomb_collide_noalloc: mass, weight, cell volume and dt must be finite and > 0");
+    if ((uint64_t)step * 4u + 3u > 0xFFFFFFFFull) return na_fail("coulomb_collide_noalloc: step must be < 2^30");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return na_cuda(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return na_fail("coulomb_collide_noalloc: device index above 63");
+    DeviceSetup setup;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        DeviceSetup& d = g_setup[dev];
+        if (!d.ready) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return na_cuda(e, "cudaGetSymbolAddress");
+            std::vector<float> tab(kNanbuN);
+            const double l0 = std::log(kNanbuSLo), dl = std::log(kNanbuSHi / kNanbuSLo) / (kNanbuN - 1);
+            for (int i = 0; i < kNanbuN; ++i) tab[i] = (float)std::log(nanbu_A_fp64(std::exp(l0 + i * dl)));
+            e = cudaMemcpy(static_cast<unsigned char*>(p) + kOffNanbu, tab.data(), kNanbuN * sizeof(float),
+                           cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return na_cuda(e, "Nanbu table upload");
+            int sms = 0;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return na_cuda(e, "cudaDeviceGetAttribute");
+            d.base = static_cast<unsigned char*>(p);
+            d.grid = sms * collide_blocks_per_sm();
+            d.ready = true;
+        }
+        setup = d;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    unsigned char* base = setup.base;
+    const uint32_t tiles = (uint32_t)((n + kTile - 1) / kTile);
+
+    // the parameter block the collision kernels read, pointing into the scratch
+    RunDev R;
+    std::memset(&R, 0, sizeof R);
+    const double M = mass_amu * 1.66053906660e-27, e2 = 1.602176634e-19 * 1.602176634e-19;
+    const double k = e2 / (8.8541878128e-12 * 0.5 * M);
+    R.lnl_ii_coef = (float)(lnL_ii / (4.0 * 3.14159265358979323846) * k * k * weight / cell_volume_m3);
+    R.dt = (float)dt;
+    R.seed_lo = (uint32_t)seed;
+    R.seed_hi = (uint32_t)(seed >> 32);
+    R.vx = vx;
+    R.vy = vy;
+    R.vz = vz;
+    R.meta = events;
+    R.plist = reinterpret_cast<uint2*>(base + kOffPlist);
+    R.pvel = reinterpret_cast<float4*>(base + kOffPvel);
+    R.tcount = reinterpret_cast<uint32_t*>(base + kOffTcount);
+    R.ccount = reinterpret_cast<uint32_t*>(base + kOffCcount);
+    R.coff = reinterpret_cast<uint32_t*>(base + kOffCoff);
+    R.cblk = reinterpret_cast<uint32_t*>(base + kOffCblk);
+    R.ckeys = reinterpret_cast<unsigned long long*>(base + kOffCkeys);
+    R.crec = reinterpret_cast<float4*>(base + kOffCrec);
+    R.skeys = reinterpret_cast<unsigned long long*>(base + kOffSkeys);
+    R.srec = reinterpret_cast<float4*>(base + kOffSrec);
+    R.nanbu = reinterpret_cast<const float*>(base + kOffNanbu);
+    R.nanbu_lnlo = (float)std::log(kNanbuSLo);
+    R.nanbu_inv_dln = (float)((kNanbuN - 1) / std::log(kNanbuSHi / kNanbuSLo));
+    R.step = reinterpret_cast<uint32_t*>(base + kOffWords);
+    R.tally = reinterpret_cast<unsigned long long*>(base + kOffTally);
+    unsigned int* ticket = reinterpret_cast<unsigned int*>(base + kOffWords) + 1;
+
+    const uint32_t span = ncells > tiles ? ncells : tiles;
+    k_na_init<<<(span + 255) / 256 > 0 ? (span + 255) / 256 : 1, 256, 0, s>>>(base, ncells, tiles, step);
+    if (n > 0)
+        k_na_pack<<<(uint32_t)((n + 255) / 256), 256, 0, s>>>(base, (uint32_t)n, cell, q, vx, vy, vz, ncells);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return na_cuda(e, "launch");
+    e = launch_coulomb(R, ncells, tiles, ticket, setup.grid, s);
+    if (e != cudaSuccess) return na_cuda(e, "launch_coulomb");
+    if (collisions_out) {
+        unsigned long long c = 0;
+        e = cudaMemcpyAsync(&c, R.tally + kTallyCoulomb, sizeof c, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return na_cuda(e, "collision count");
+        *collisions_out = (int64_t)c;
+    }
+    return ECRIS_OK;
+}

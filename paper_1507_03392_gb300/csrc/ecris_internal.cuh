@@ -273,6 +273,8 @@ cudaError_t launch_census(const RunDev& R, uint32_t n4, unsigned long long* cens
 cudaError_t launch_export(void* x, void* y, void* z, uint32_t n, double sxy, double sz, cudaStream_t s);
 // resident blocks per SM of the step kernel
 int step_blocks_per_sm();
+// message returned by ecris_last_error(NULL) on the calling thread
+void ecris_internal_set_thread_error(const char* msg);
 
 // Coulomb collisions of one run for the current step (after launch_step with
 // bump_step = 0): scan of the cell counts, scatter of the pairing keys, and

@@ -106,6 +106,11 @@ def _load():
     lib.ecris_set_profiling.restype = st
     lib.ecris_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
     lib.ecris_get_profile.restype = st
+    lib.ecris_coulomb_collide_noalloc.argtypes = [ctypes.c_size_t, P, P, P, P, P, P, ctypes.c_uint32,
+                                                  ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                                  ctypes.c_uint32, P, ctypes.POINTER(ctypes.c_int64)]
+    lib.ecris_coulomb_collide_noalloc.restype = st
     return lib
 
 
@@ -122,6 +127,7 @@ ecris_diag = LIB.ecris_diag
 ecris_get_state = LIB.ecris_get_state
 ecris_set_profiling = LIB.ecris_set_profiling
 ecris_get_profile = LIB.ecris_get_profile
+ecris_coulomb_collide_noalloc = LIB.ecris_coulomb_collide_noalloc
 
 
 def check(ctx, status):
