@@ -222,6 +222,16 @@ typedef struct {
 ecris_status ecris_set_profiling(ecris_ctx* ctx, int enable);
 ecris_status ecris_get_profile(ecris_ctx* ctx, ecris_profile* out);
 
+/* Performance knobs (not part of the paper's model; results do not depend on
+ * them).  The library keeps each run's particles grouped by (ion or atom,
+ * cell) in device memory and regroups them every sort_every steps (default
+ * 32; >= 1).  ecris_get_state always returns particles in load order. */
+typedef struct {
+    int32_t sort_every;
+    int32_t reserved[7];   /* set to 0 */
+} ecris_tuning;
+ecris_status ecris_set_tuning(ecris_ctx* ctx, const ecris_tuning* t);
+
 /* Allocation-free Coulomb collision step.  The paper has no counterpart: this
  * is an interface for callers that cannot allocate device memory when they
  * need a collision step -- hosts that reserve all device memory up front and
@@ -230,7 +240,7 @@ ecris_status ecris_get_profile(ecris_ctx* ctx, ecris_profile* out);
  * the device.  It runs the same Takizawa-Abe pairing and Nanbu scattering as
  * ecris_step (ECRIS_F_COULOMB) on caller-owned device arrays and keeps all its
  * working memory in one fixed-size array that the library holds on every GPU
- * that loads it (about 5 MB, until the process exits); it allocates nothing.
+ * that loads it (about 6 MB, until the process exits); it allocates nothing.
  *
  *   n            particles, at most 65536; arrays are indexed by particle id
  *                (the Philox counter word, as in ecris_step)

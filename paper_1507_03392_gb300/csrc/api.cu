@@ -158,7 +158,7 @@ struct ecris_ctx {
     uint8_t* d_q8 = nullptr;
     unsigned int* d_bad = nullptr;
     uint32_t* d_err = nullptr;
-    uint2* d_plist = nullptr;
+    uint4* d_plist = nullptr;
     float4* d_pvel = nullptr;
     uint32_t* d_tcount = nullptr;
     float4* d_crec = nullptr;
@@ -169,8 +169,27 @@ struct ecris_ctx {
     unsigned long long* d_skeys = nullptr;
     float4* d_srec = nullptr;
     int collide_grid = 0;
+    // two sets of particle arrays; the sort moves the particles from the
+    // current set (index cur) to the other
     float* d_soa[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     uint32_t* d_meta = nullptr;
+    uint32_t* d_id = nullptr;
+    float* d_soa2[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint32_t* d_meta2 = nullptr;
+    uint32_t* d_id2 = nullptr;
+    uint32_t* d_hist = nullptr;    // sort histogram (2 Nc + 1), kept zero between sorts
+    uint32_t* d_hoff = nullptr;    // its exclusive scan (2 Nc + 2)
+    uint32_t* d_hblk = nullptr;    // scan block totals
+    uint32_t sort_every = 32;      // steps between sorts
+    uint32_t since_sort = 0;
+    int parity = 0;                // which particle set is current (flips at each sort)
+    // captured per-step kernel sequences, by particle set and kind (0: the
+    // whole step, 1: the collision kernels only), valid for param_version
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    uint64_t gver[2][2] = {{0, 0}, {0, 0}};
+    uint64_t param_version = 1;
+    uint32_t* d_cslot = nullptr;
+    uint32_t* d_sslot = nullptr;
     unsigned long long* d_dep = nullptr;
     unsigned long long* d_count = nullptr;
     unsigned long long* d_charge = nullptr;
@@ -272,10 +291,29 @@ void free_async(ecris_ctx* ctx, T*& p)
     p = nullptr;
 }
 
+void free_graphs(ecris_ctx* ctx)
+{
+    for (auto& row : ctx->gexec)
+        for (auto& x : row) {
+            if (x) cudaGraphExecDestroy(x);
+            x = nullptr;
+        }
+}
+
 void free_ions(ecris_ctx* ctx)
 {
+    free_graphs(ctx);
     for (auto& p : ctx->d_soa) free_async(ctx, p);
     free_async(ctx, ctx->d_meta);
+    free_async(ctx, ctx->d_id);
+    for (auto& p : ctx->d_soa2) free_async(ctx, p);
+    free_async(ctx, ctx->d_meta2);
+    free_async(ctx, ctx->d_id2);
+    free_async(ctx, ctx->d_hist);
+    free_async(ctx, ctx->d_hoff);
+    free_async(ctx, ctx->d_hblk);
+    free_async(ctx, ctx->d_cslot);
+    free_async(ctx, ctx->d_sslot);
     free_async(ctx, ctx->d_dep);
     free_async(ctx, ctx->d_count);
     free_async(ctx, ctx->d_charge);
@@ -389,6 +427,7 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.vy = ctx->d_soa[4];
     R.vz = ctx->d_soa[5];
     R.meta = ctx->d_meta;
+    R.id = ctx->d_id;
     R.cell = ctx->d_cell;
     R.E = ctx->d_E;
     R.kdt = ctx->d_kdt;
@@ -404,6 +443,8 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.ckeys = ctx->d_ckeys;
     R.skeys = ctx->d_skeys;
     R.srec = ctx->d_srec;
+    R.cslot = ctx->d_cslot;
+    R.sslot = ctx->d_sslot;
     R.nanbu = ctx->d_nanbu;
     R.nanbu_lnlo = (float)std::log(kNanbuSLo);
     R.nanbu_inv_dln = (float)((kNanbuN - 1) / std::log(kNanbuSHi / kNanbuSLo));
@@ -435,6 +476,76 @@ ecris_status upload_dt(ecris_ctx* ctx, double dt)
     CK(cudaMemcpyAsync(ctx->d_kdt, ctx->h_kdt, 2 * kQSlots * sizeof(float), cudaMemcpyHostToDevice,
                        ctx->stream));
     ctx->dt_loaded = dt;
+    ++ctx->param_version;
+    return ECRIS_OK;
+}
+
+// the kernel sequence of one step, captured once per particle set and
+// parameter block and replayed as a CUDA graph
+ecris_status step_graph(ecris_ctx* ctx, int kind, cudaGraphExec_t* out)
+{
+    const int p = ctx->parity;
+    if (ctx->gexec[p][kind] && ctx->gver[p][kind] == ctx->param_version) {
+        *out = ctx->gexec[p][kind];
+        return ECRIS_OK;
+    }
+    if (ctx->gexec[p][kind]) {
+        cudaGraphExecDestroy(ctx->gexec[p][kind]);
+        ctx->gexec[p][kind] = nullptr;
+    }
+    const bool coulomb = (ctx->h.mcc.flags & kFCoulomb) != 0;
+    const uint32_t nc = (uint32_t)((size_t)ctx->h.nx * ctx->h.ny * ctx->h.nz);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    if (kind == 0)
+        e = launch_step(*ctx->h_run, ctx->ntiles, ctx->d_ticket, coulomb ? 0 : 1, ctx->step_grid, ctx->stream);
+    if (e == cudaSuccess && coulomb)
+        e = launch_coulomb(*ctx->h_run, nc, ctx->ntiles, ctx->d_ticket, ctx->collide_grid, ctx->stream);
+    const cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+    CK(e);
+    CK(e2);
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    ctx->gexec[p][kind] = x;
+    ctx->gver[p][kind] = ctx->param_version;
+    *out = x;
+    return ECRIS_OK;
+}
+
+// Regroup the particles by (ion/atom, cell) into the other set of arrays and
+// make that set current.  Needs the parameter block of the current set.
+ecris_status sort_particles(ecris_ctx* ctx)
+{
+    ParticleSet dst;
+    dst.x = reinterpret_cast<int32_t*>(ctx->d_soa2[0]);
+    dst.y = reinterpret_cast<int32_t*>(ctx->d_soa2[1]);
+    dst.z = reinterpret_cast<int32_t*>(ctx->d_soa2[2]);
+    dst.vx = ctx->d_soa2[3];
+    dst.vy = ctx->d_soa2[4];
+    dst.vz = ctx->d_soa2[5];
+    dst.meta = ctx->d_meta2;
+    dst.id = ctx->d_id2;
+    CK(timed(ctx, kKindOther, [&] {
+        return launch_sort(*ctx->h_run, (uint32_t)(4 * ctx->n4), dst, ctx->d_hist, ctx->d_hoff, ctx->d_hblk,
+                           ctx->stream);
+    }, 5));
+    for (int k = 0; k < 6; ++k) std::swap(ctx->d_soa[k], ctx->d_soa2[k]);
+    std::swap(ctx->d_meta, ctx->d_meta2);
+    std::swap(ctx->d_id, ctx->d_id2);
+    RunDev& R = *ctx->h_run;
+    R.x = reinterpret_cast<int32_t*>(ctx->d_soa[0]);
+    R.y = reinterpret_cast<int32_t*>(ctx->d_soa[1]);
+    R.z = reinterpret_cast<int32_t*>(ctx->d_soa[2]);
+    R.vx = ctx->d_soa[3];
+    R.vy = ctx->d_soa[4];
+    R.vz = ctx->d_soa[5];
+    R.meta = ctx->d_meta;
+    R.id = ctx->d_id;
+    ctx->since_sort = 0;
+    ctx->parity ^= 1;
     return ECRIS_OK;
 }
 
@@ -672,6 +783,16 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         for (int k = 0; k < 6; ++k)
             CK(cudaMallocAsync((void**)&ctx->d_soa[k], cap * sizeof(float), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_meta, cap * sizeof(uint32_t), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_id, cap * sizeof(uint32_t), ctx->stream));
+        for (int k = 0; k < 6; ++k)
+            CK(cudaMallocAsync((void**)&ctx->d_soa2[k], cap * sizeof(float), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_meta2, cap * sizeof(uint32_t), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_id2, cap * sizeof(uint32_t), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_hist, (2 * nc + 1) * sizeof(uint32_t), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_hoff, (2 * nc + 2) * sizeof(uint32_t), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_hblk, (size_t)sort_scan_blocks((uint32_t)(2 * nc + 1)) * sizeof(uint32_t),
+                           ctx->stream));
+        CK(cudaMemsetAsync(ctx->d_hist, 0, (2 * nc + 1) * sizeof(uint32_t), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_q8, cap, ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_dep, nc * sizeof(unsigned long long), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_count, nc * sizeof(unsigned long long), ctx->stream));
@@ -684,7 +805,9 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         CK(cudaMallocAsync((void**)&ctx->d_err, sizeof(uint32_t), ctx->stream));
         if (h.mcc.flags & kFCoulomb) {
             const size_t slots = (cap / kTile + 1) * kTile;
-            CK(cudaMallocAsync((void**)&ctx->d_plist, slots * sizeof(uint2), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_plist, slots * sizeof(uint4), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_cslot, cap * sizeof(uint32_t), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_sslot, cap * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_pvel, slots * sizeof(float4), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_tcount, (cap / kTile + 1) * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_ckeys, cap * sizeof(unsigned long long), ctx->stream));
@@ -734,7 +857,7 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         lc.inv_sz_hi = (float)b;
         lc.inv_sz_lo = (float)(b - (double)lc.inv_sz_hi);
     }
-    CK(launch_load_init(lc, ctx->d_soa, ctx->d_q8, ctx->d_meta, (uint32_t)n, (uint32_t)cap, ctx->d_bad,
+    CK(launch_load_init(lc, ctx->d_soa, ctx->d_q8, ctx->d_meta, ctx->d_id, (uint32_t)n, (uint32_t)cap, ctx->d_bad,
                         ctx->stream));
     unsigned int bad[2] = {0u, 0u};
     CK(cudaMemcpyAsync(bad, ctx->d_bad, sizeof bad, cudaMemcpyDeviceToHost, ctx->stream));
@@ -754,6 +877,8 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
     ctx->time_s = 0.0;
     ctx->dt_loaded = -1.0;
     ctx->since_fold = 0;
+    ctx->since_sort = ctx->sort_every;   // group the particles before the first step
+    ++ctx->param_version;
     // fold the packed deposit before its low word (charge) can carry
     const double per_step = (double)(n ? n : 1) * (h.qmax > 1 ? h.qmax : 1);
     const double k = std::floor(4294967295.0 / per_step);
@@ -778,15 +903,28 @@ ecris_status ecris_step(ecris_ctx* ctx, uint32_t nsteps, double dt)
     const bool coulomb = (ctx->h.mcc.flags & kFCoulomb) != 0;
     const uint32_t nc = (uint32_t)((size_t)ctx->h.nx * ctx->h.ny * ctx->h.nz);
     for (uint32_t s = 0; s < nsteps; ++s) {
-        CK(timed(ctx, kKindStep, [&] {
-            return launch_step(*ctx->h_run, ctx->ntiles, ctx->d_ticket, coulomb ? 0 : 1, ctx->step_grid,
-                               ctx->stream);
-        }));
-        if (coulomb) {
-            CK(timed(ctx, kKindCoulomb, [&] {
-                return launch_coulomb(*ctx->h_run, nc, ctx->ntiles, ctx->d_ticket, ctx->collide_grid,
-                                      ctx->stream);
-            }, kCoulombKernels));
+        if (ctx->since_sort >= ctx->sort_every && ctx->n4 > 0) {
+            st = sort_particles(ctx);
+            if (st != ECRIS_OK) return st;
+        }
+        if (!ctx->prof) {
+            // the whole step as one graph launch
+            cudaGraphExec_t x = nullptr;
+            st = step_graph(ctx, 0, &x);
+            if (st != ECRIS_OK) return st;
+            CK(cudaGraphLaunch(x, ctx->stream));
+        } else {
+            // timed: the step kernel on its own, the collision kernels as a graph
+            CK(timed(ctx, kKindStep, [&] {
+                return launch_step(*ctx->h_run, ctx->ntiles, ctx->d_ticket, coulomb ? 0 : 1, ctx->step_grid,
+                                   ctx->stream);
+            }));
+            if (coulomb) {
+                cudaGraphExec_t x = nullptr;
+                st = step_graph(ctx, 1, &x);
+                if (st != ECRIS_OK) return st;
+                CK(timed(ctx, kKindCoulomb, [&] { return cudaGraphLaunch(x, ctx->stream); }, kCoulombKernels));
+            }
         }
         if (++ctx->since_fold >= ctx->fold_every) {
             CK(timed(ctx, kKindOther, [&] {
@@ -794,6 +932,7 @@ ecris_status ecris_step(ecris_ctx* ctx, uint32_t nsteps, double dt)
             }));
             ctx->since_fold = 0;
         }
+        ++ctx->since_sort;
     }
     ctx->steps_done += nsteps;
     ctx->time_s += dt * nsteps;
@@ -863,35 +1002,41 @@ ecris_status ecris_get_state(ecris_ctx* ctx, float* const xyzv[6], uint32_t* met
     if (!ctx) return ECRIS_EINVAL;
     if (!ctx->loaded) return fail(ctx, ECRIS_ESTATE, "get_state: call ecris_load_ions first");
     CK(cudaSetDevice(ctx->device));
-    const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (ctx->dt_loaded < 0.0) {
+        ecris_status st = upload_dt(ctx, 1e-9);   // parameter block for the export kernel
+        if (st != ECRIS_OK) return st;
+    }
     const double sxy = ctx->h.geo.R0 / 2147483648.0, sz = ctx->h.geo.L / 4294967296.0;
     const size_t n = ctx->n;
     if (n) {
-        for (int k = 0; k < 6; ++k)
-            if (xyzv && xyzv[k])
-                CK(cudaMemcpyAsync(xyzv[k], ctx->d_soa[k], n * sizeof(float), kind, ctx->stream));
-        if (meta) CK(cudaMemcpyAsync(meta, ctx->d_meta, n * sizeof(uint32_t), kind, ctx->stream));
-        const bool pos = xyzv && xyzv[0] && xyzv[1] && xyzv[2];
-        if (dst_is_device && pos) {
-            // positions are held in fixed point: convert the copies in place
-            CK(launch_export(xyzv[0], xyzv[1], xyzv[2], (uint32_t)n, sxy, sz, ctx->stream));
-        } else if (dst_is_device && xyzv && (xyzv[0] || xyzv[1] || xyzv[2])) {
-            return fail(ctx, ECRIS_EINVAL, "get_state: device positions need all of x, y, z");
-        }
-        if (!dst_is_device) {
-            CK(cudaStreamSynchronize(ctx->stream));
-            for (int k = 0; k < 3; ++k) {
-                if (!xyzv || !xyzv[k]) continue;
-                float* f = xyzv[k];
-                for (size_t i = 0; i < n; ++i) {
-                    int32_t X;
-                    std::memcpy(&X, f + i, 4);
-                    f[i] = (float)(k < 2 ? (double)X * sxy : ((double)X + 2147483648.0) * sz);
-                }
-            }
+        // the particles sit in sorted order: scatter them back to load order
+        // by their ids (into the caller's device arrays, or via the spare set)
+        if (dst_is_device) {
+            CK(launch_export_ordered(*ctx->h_run, (uint32_t)n, (uint32_t)(4 * ctx->n4), xyzv, meta, sxy, sz,
+                                     ctx->stream));
+        } else {
+            float* spare[6];
+            for (int k = 0; k < 6; ++k) spare[k] = (xyzv && xyzv[k]) ? ctx->d_soa2[k] : nullptr;
+            CK(launch_export_ordered(*ctx->h_run, (uint32_t)n, (uint32_t)(4 * ctx->n4), spare,
+                                     meta ? ctx->d_meta2 : nullptr, sxy, sz, ctx->stream));
+            for (int k = 0; k < 6; ++k)
+                if (spare[k])
+                    CK(cudaMemcpyAsync(xyzv[k], spare[k], n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+            if (meta)
+                CK(cudaMemcpyAsync(meta, ctx->d_meta2, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
         }
     }
     if (!dst_is_device) CK(cudaStreamSynchronize(ctx->stream));
+    return ECRIS_OK;
+}
+
+ecris_status ecris_set_tuning(ecris_ctx* ctx, const ecris_tuning* t)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    if (!t) return fail(ctx, ECRIS_EINVAL, "set_tuning: NULL argument");
+    if (t->sort_every < 1) return fail(ctx, ECRIS_EINVAL, "set_tuning: sort_every must be >= 1");
+    ctx->sort_every = (uint32_t)t->sort_every;
+    if (ctx->since_sort > ctx->sort_every) ctx->since_sort = ctx->sort_every;
     return ECRIS_OK;
 }
 

@@ -129,12 +129,13 @@ __global__ void k_scatter(const __grid_constant__ RunDev R, uint32_t ntiles)
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const uint32_t np = R.tcount[t];
         for (uint32_t i = threadIdx.x; i < np; i += blockDim.x) {
-            const uint2 pc = R.plist[t * kTile + i];
+            const uint4 pc = R.plist[t * kTile + i];   // (array slot, cell, id, -)
             const float4 v = R.pvel[t * kTile + i];
             const uint32_t slot = R.coff[pc.y] + atomicSub(R.ccount + pc.y, 1u) - 1u;
-            const Words w = rng_words(R, pc.x, step, 1u);
-            R.ckeys[slot] = ((unsigned long long)w.w0 << 32) | pc.x;
+            const Words w = rng_words(R, pc.z, step, 1u);
+            R.ckeys[slot] = ((unsigned long long)w.w0 << 32) | pc.z;
             R.crec[slot] = make_float4(v.x, v.y, v.z, __uint_as_float((pc.y << 6) | __float_as_uint(v.w)));
+            R.cslot[slot] = pc.x;
         }
     }
 }
@@ -194,12 +195,12 @@ __device__ __forceinline__ void collide(const RunDev& R, float4& ra, float4& rb,
     rb.x -= dgx; rb.y -= dgy; rb.z -= dgz;
 }
 
-__device__ __forceinline__ void write_back(const RunDev& R, uint32_t pid, const float4& r)
+__device__ __forceinline__ void write_back(const RunDev& R, uint32_t slot, const float4& r)
 {
-    R.vx[pid] = r.x;
-    R.vy[pid] = r.y;
-    R.vz[pid] = r.z;
-    atomicOr(R.meta + pid, kEvCoulomb);   // result unused: a fire-and-forget reduction
+    R.vx[slot] = r.x;
+    R.vy[slot] = r.y;
+    R.vz[slot] = r.z;
+    atomicOr(R.meta + slot, kEvCoulomb);   // result unused: a fire-and-forget reduction
 }
 
 // place each participant at its rank within its cell's order
@@ -216,6 +217,7 @@ __global__ void k_rank(const __grid_constant__ RunDev R, uint32_t ncells)
         for (uint32_t i = 0; i < m; ++i) rank += (k[i] < key) ? 1u : 0u;
         R.skeys[seg + rank] = key;
         R.srec[seg + rank] = rec;
+        R.sslot[seg + rank] = R.cslot[j];
     }
 }
 
@@ -234,7 +236,7 @@ __global__ void k_pairs(const __grid_constant__ RunDev R, uint32_t ncells, unsig
         const uint32_t r = t - seg;
         if (m < 2u) continue;
         const float mc = (float)m;
-        const uint32_t pa = (uint32_t)R.skeys[t];
+        const uint32_t pa = (uint32_t)R.skeys[t];   // ids give the random words
         if ((m & 1u) && r == 0u) {
             // triplet of ranks 0, 1, 2: (0,1), (1,2), (2,0) over dt/2 each
             float4 rb = R.srec[t + 1], rc = R.srec[t + 2];
@@ -242,18 +244,17 @@ __global__ void k_pairs(const __grid_constant__ RunDev R, uint32_t ncells, unsig
             collide(R, ra, rb, 0.5f * dt, mc, pa, step);
             collide(R, rb, rc, 0.5f * dt, mc, pb, step);
             collide(R, rc, ra, 0.5f * dt, mc, pc, step);
-            write_back(R, pa, ra);
-            write_back(R, pb, rb);
-            write_back(R, pc, rc);
+            write_back(R, R.sslot[t], ra);
+            write_back(R, R.sslot[t + 1], rb);
+            write_back(R, R.sslot[t + 2], rc);
             ncoll += 3;
         } else {
             const uint32_t start = (m & 1u) ? 3u : 0u;
             if (r < start || ((r - start) & 1u)) continue;
             float4 rb = R.srec[t + 1];
-            const uint32_t pb = (uint32_t)R.skeys[t + 1];
             collide(R, ra, rb, dt, mc, pa, step);
-            write_back(R, pa, ra);
-            write_back(R, pb, rb);
+            write_back(R, R.sslot[t], ra);
+            write_back(R, R.sslot[t + 1], rb);
             ncoll += 1;
         }
     }

@@ -14,7 +14,7 @@
 //
 // Limits: at most kNaMaxIons particles and kNaMaxCells cells per call; larger
 // sizes are rejected with ECRIS_EINVAL.  The array (kNaScratchBytes, about
-// 5 MB) is held by every GPU that loads the library until the process exits.
+// 6 MB) is held by every GPU that loads the library until the process exits.
 // Every call shares it and finds the last call's contents there; what must
 // start at zero is cleared at the start of each call.  Calls whose GPU work
 // overlaps (different streams, or several host threads) race on the array
@@ -41,7 +41,7 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // byte offsets of the sub-buffers inside the scratch array
 constexpr size_t kOffPlist = 0;
-constexpr size_t kOffPvel = kOffPlist + align256(sizeof(uint2) * kNaMaxIons);
+constexpr size_t kOffPvel = kOffPlist + align256(sizeof(uint4) * kNaMaxIons);
 constexpr size_t kOffTcount = kOffPvel + align256(sizeof(float4) * kNaMaxIons);
 constexpr size_t kOffCcount = kOffTcount + align256(sizeof(uint32_t) * kNaTiles);
 constexpr size_t kOffCoff = kOffCcount + align256(sizeof(uint32_t) * kNaMaxCells);
@@ -50,7 +50,9 @@ constexpr size_t kOffCkeys = kOffCblk + align256(sizeof(uint32_t) * (kNaMaxCells
 constexpr size_t kOffCrec = kOffCkeys + align256(sizeof(unsigned long long) * kNaMaxIons);
 constexpr size_t kOffSkeys = kOffCrec + align256(sizeof(float4) * kNaMaxIons);
 constexpr size_t kOffSrec = kOffSkeys + align256(sizeof(unsigned long long) * kNaMaxIons);
-constexpr size_t kOffNanbu = kOffSrec + align256(sizeof(float4) * kNaMaxIons);
+constexpr size_t kOffCslot = kOffSrec + align256(sizeof(float4) * kNaMaxIons);
+constexpr size_t kOffSslot = kOffCslot + align256(sizeof(uint32_t) * kNaMaxIons);
+constexpr size_t kOffNanbu = kOffSslot + align256(sizeof(uint32_t) * kNaMaxIons);
 constexpr size_t kOffWords = kOffNanbu + align256(sizeof(float) * kNanbuN);
 // words: step, ticket, then the tally block
 constexpr size_t kOffTally = kOffWords + 256;
@@ -106,7 +108,7 @@ __global__ void k_na_pack(unsigned char* base, uint32_t n, const uint32_t* __res
                           const uint8_t* __restrict__ q, const float* __restrict__ vx,
                           const float* __restrict__ vy, const float* __restrict__ vz, uint32_t ncells)
 {
-    uint2* plist = reinterpret_cast<uint2*>(base + kOffPlist);
+    uint4* plist = reinterpret_cast<uint4*>(base + kOffPlist);
     float4* pvel = reinterpret_cast<float4*>(base + kOffPvel);
     uint32_t* tcount = reinterpret_cast<uint32_t*>(base + kOffTcount);
     uint32_t* ccount = reinterpret_cast<uint32_t*>(base + kOffCcount);
@@ -116,7 +118,7 @@ __global__ void k_na_pack(unsigned char* base, uint32_t n, const uint32_t* __res
         if (c >= ncells || Q == 0u || Q > 63u) continue;
         const uint32_t t = i / kTile;
         const uint32_t slot = t * kTile + atomicAdd(tcount + t, 1u);
-        plist[slot] = make_uint2(i, c);
+        plist[slot] = make_uint4(i, c, i, 0u);   // slot and id are both the array index
         pvel[slot] = make_float4(vx[i], vy[i], vz[i], __uint_as_float(Q));
         atomicAdd(ccount + c, 1u);
     }
@@ -197,7 +199,7 @@ extern "C" ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* 
     R.vy = vy;
     R.vz = vz;
     R.meta = events;
-    R.plist = reinterpret_cast<uint2*>(base + kOffPlist);
+    R.plist = reinterpret_cast<uint4*>(base + kOffPlist);
     R.pvel = reinterpret_cast<float4*>(base + kOffPvel);
     R.tcount = reinterpret_cast<uint32_t*>(base + kOffTcount);
     R.ccount = reinterpret_cast<uint32_t*>(base + kOffCcount);
@@ -207,6 +209,8 @@ extern "C" ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* 
     R.crec = reinterpret_cast<float4*>(base + kOffCrec);
     R.skeys = reinterpret_cast<unsigned long long*>(base + kOffSkeys);
     R.srec = reinterpret_cast<float4*>(base + kOffSrec);
+    R.cslot = reinterpret_cast<uint32_t*>(base + kOffCslot);
+    R.sslot = reinterpret_cast<uint32_t*>(base + kOffSslot);
     R.nanbu = reinterpret_cast<const float*>(base + kOffNanbu);
     R.nanbu_lnlo = (float)std::log(kNanbuSLo);
     R.nanbu_inv_dln = (float)((kNanbuN - 1) / std::log(kNanbuSHi / kNanbuSLo));

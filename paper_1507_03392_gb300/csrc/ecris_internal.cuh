@@ -100,12 +100,13 @@ struct RunDev {
     int32_t *x, *y, *z;          // fixed-point positions (see sxy, sz)
     float *vx, *vy, *vz;
     uint32_t *meta;
+    uint32_t *id;                // stable particle id (Philox counter word, output order)
     const float4 *cell;          // {n_e (m^-3), zone (0/1), delta_x, delta_y}
     const float4 *E;             // {E_x, E_y, E_z, 0} per cell centre
     const float *kdt;            // ionisation rate * dt, [zone * 64 + Q]
     unsigned long long *dep;     // packed deposit accumulator: count << 32 | charge
     unsigned long long *tally;   // kTallyWords
-    uint2 *plist;                // Coulomb participants of each tile: (pid, cell), kTile slots a tile
+    uint4 *plist;                // Coulomb participants of each tile: (slot, cell, id, 0), kTile slots a tile
     float4 *pvel;                // their (vx, vy, vz, Q as bits), same slots
     uint32_t *tcount;            // participants per tile
     uint32_t *ccount;            // Coulomb participants per cell (counted up by the step kernel,
@@ -114,8 +115,10 @@ struct RunDev {
     uint32_t *cblk;              // scan block totals
     unsigned long long *ckeys;   // (pairing hash << 32 | pid) per participant, grouped by cell
     float4 *crec;                // (vx, vy, vz, cell << 6 | Q as bits) per participant, grouped by cell
+    uint32_t *cslot;             // array slot of each participant, grouped by cell
     unsigned long long *skeys;   // ckeys in pairing order within each cell
     float4 *srec;                // crec in pairing order within each cell
+    uint32_t *sslot;             // cslot in pairing order within each cell
     const float *nanbu;          // ln A at ln s = nanbu_lnlo + i / nanbu_inv_dln, i < kNanbuN
     float nanbu_lnlo, nanbu_inv_dln;
     uint32_t *step;              // device step counter of the run
@@ -264,13 +267,30 @@ struct LoadCheck {
     float inv_sz_hi, inv_sz_lo;
 };
 // check particles [0, n), convert their positions (metres, float) in place to
-// fixed point, build their meta words from q8, fill pads [n, cap); bad[0]
-// counts invalid particles, bad[1] holds the lowest invalid index
+// fixed point, build their meta words from q8 and ids, fill pads [n, cap);
+// bad[0] counts invalid particles, bad[1] holds the lowest invalid index
 cudaError_t launch_load_init(const LoadCheck& lc, float* const soa[6], const uint8_t* q8, uint32_t* meta,
-                             uint32_t n, uint32_t cap, unsigned int* bad, cudaStream_t s);
+                             uint32_t* id, uint32_t n, uint32_t cap, unsigned int* bad, cudaStream_t s);
+
+// One set of particle arrays (the sort moves particles between two sets).
+struct ParticleSet {
+    int32_t *x, *y, *z;
+    float *vx, *vy, *vz;
+    uint32_t *meta, *id;
+};
+// Counting sort of the run's particles (in R) by (ion/atom, cell) into `dst`:
+// live ions first, then live atoms, each by cell; frozen and padding slots
+// last.  hist (2 Nc + 1 words) must be zero and is left zero; off (2 Nc + 2)
+// and blk (scan block totals) are scratch.
+cudaError_t launch_sort(const RunDev& R, uint32_t cap, const ParticleSet& dst, uint32_t* hist, uint32_t* off,
+                        uint32_t* blk, cudaStream_t s);
+int sort_scan_blocks(uint32_t nbins);
+// state in load order: out[id[slot]] = state[slot] for id < n (positions to
+// metres), into device arrays
+cudaError_t launch_export_ordered(const RunDev& R, uint32_t n, uint32_t cap, float* const out[6], uint32_t* meta_out,
+                                  double sxy, double sz, cudaStream_t s);
 cudaError_t launch_census(const RunDev& R, uint32_t n4, unsigned long long* census, cudaStream_t s);
-// convert n fixed-point positions in place (device buffers) to metres (float)
-cudaError_t launch_export(void* x, void* y, void* z, uint32_t n, double sxy, double sz, cudaStream_t s);
+
 // resident blocks per SM of the step kernel
 int step_blocks_per_sm();
 // message returned by ecris_last_error(NULL) on the calling thread

@@ -48,12 +48,18 @@ __device__ __forceinline__ float event_prob(float lam)
     return -expm1f(-lam);
 }
 
+// Advance one particle by one step.  pid is its stable id (the Philox counter
+// word).  On return dep_cell is the cell it deposits in (kNoCell if it does
+// not: frozen or padding) and ckey the cell where it takes part in Coulomb
+// collisions (kNoCell if it does not).
 __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uint32_t step, int32_t& X,
                                               int32_t& Y, int32_t& Z, float& vx, float& vy, float& vz,
                                               uint32_t& meta, BlockTally& T,
-                                              unsigned long long& ke_acc, uint32_t& ckey)
+                                              unsigned long long& ke_acc, uint32_t& ckey,
+                                              uint32_t& dep_cell)
 {
     ckey = kNoCell;
+    dep_cell = kNoCell;
     const uint32_t status = meta & 0xFFFF0000u;
     if (status & (kStFrozen | kStPad)) {
         meta = status | (meta & kQMask);   // events of a frozen particle are cleared
@@ -241,14 +247,10 @@ __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uin
                 vz += k * dzv;
             }
         }
-        if (Q >= 1 && (R.flags & kFCoulomb)) {
-            ckey = cell;
-            atomicAdd(R.ccount + cell, 1u);   // result unused: a fire-and-forget reduction
-        }
+        if (Q >= 1 && (R.flags & kFCoulomb)) ckey = cell;
     }
 
-    // ---- NGP deposition at the final position ----
-    atomicAdd(R.dep + cell, (1ull << 32) | (unsigned long long)Q);
+    dep_cell = cell;   // NGP deposition at the final position (warp-aggregated by the caller)
     meta = status | ev | Q;
 }
 
@@ -322,13 +324,12 @@ struct Stage {
     int4 x[kThreads], y[kThreads], z[kThreads];
     float4 vx[kThreads], vy[kThreads], vz[kThreads];
     uint4 meta[kThreads];
+    uint4 id[kThreads];
 };
 
 struct StepShared {
     Stage st[2];
-    uint16_t order[kTile];
     uint32_t npart;
-    uint32_t warp_ions[kThreads / 32], warp_atoms[kThreads / 32];
     BlockTally T;
     uint64_t bar[2];
     int last;
@@ -339,13 +340,13 @@ __device__ __forceinline__ float& sf(float4* a, uint32_t i) { return reinterpret
 __device__ __forceinline__ uint32_t& su(uint4* a, uint32_t i) { return reinterpret_cast<uint32_t*>(a)[i]; }
 __device__ __forceinline__ int32_t& si(int4* a, uint32_t i) { return reinterpret_cast<int32_t*>(a)[i]; }
 
-// issue the seven bulk loads of tile t into stage st (thread 0 only)
+// issue the eight bulk loads of tile t into stage st (thread 0 only)
 __device__ __forceinline__ void load_tile(const RunDev& R, Stage& st, uint64_t* bar, uint32_t t)
 {
     const uint32_t g0 = t * kThreads;
     const uint32_t ng = min((uint32_t)kThreads, R.n4 - g0);
     const uint32_t bytes = ng * 16u;
-    mbar_expect_tx(bar, 7u * bytes);
+    mbar_expect_tx(bar, 8u * bytes);
     bulk_load(st.x, reinterpret_cast<const int4*>(R.x) + g0, bytes, bar);
     bulk_load(st.y, reinterpret_cast<const int4*>(R.y) + g0, bytes, bar);
     bulk_load(st.z, reinterpret_cast<const int4*>(R.z) + g0, bytes, bar);
@@ -353,19 +354,53 @@ __device__ __forceinline__ void load_tile(const RunDev& R, Stage& st, uint64_t* 
     bulk_load(st.vy, reinterpret_cast<const float4*>(R.vy) + g0, bytes, bar);
     bulk_load(st.vz, reinterpret_cast<const float4*>(R.vz) + g0, bytes, bar);
     bulk_load(st.meta, reinterpret_cast<const uint4*>(R.meta) + g0, bytes, bar);
+    bulk_load(st.id, reinterpret_cast<const uint4*>(R.id) + g0, bytes, bar);
+}
+
+// NGP deposition of one particle per lane, aggregated over the lanes that hit
+// the same cell (particles are kept sorted by cell, so neighbours mostly do):
+// the lowest lane of each group adds count << 32 | charge for the group
+__device__ __forceinline__ void deposit_warp(const RunDev& R, uint32_t cell, uint32_t Q)
+{
+    const uint32_t live = __ballot_sync(0xFFFFFFFFu, cell != kNoCell);
+    if (cell == kNoCell) return;
+    const uint32_t grp = __match_any_sync(live, cell);
+    const uint32_t q = __reduce_add_sync(grp, Q);
+    if ((threadIdx.x & 31) == (uint32_t)(__ffs(grp) - 1))
+        atomicAdd(R.dep + cell, ((unsigned long long)__popc(grp) << 32) | (unsigned long long)q);
+}
+
+// Publish this lane's Coulomb participant (ck != kNoCell) for the collision
+// kernels: a slot in the tile's list (one shared-memory atomic per warp) and
+// a count in its cell (one global reduction per group of lanes in a cell)
+__device__ __forceinline__ void publish_warp(const RunDev& R, uint32_t& npart, uint32_t t, uint32_t slot_in_run,
+                                             uint32_t ck, uint32_t id, float vx, float vy, float vz, uint32_t Q)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t part = __ballot_sync(0xFFFFFFFFu, ck != kNoCell);
+    if (!part) return;
+    uint32_t base = 0;
+    if (lane == (uint32_t)(__ffs(part) - 1)) base = atomicAdd(&npart, (uint32_t)__popc(part));
+    base = __shfl_sync(0xFFFFFFFFu, base, __ffs(part) - 1);
+    if (ck == kNoCell) return;
+    const uint32_t slot = t * kTile + base + (uint32_t)__popc(part & ((1u << lane) - 1u));
+    R.plist[slot] = make_uint4(slot_in_run, ck, id, 0u);
+    R.pvel[slot] = make_float4(vx, vy, vz, __uint_as_float(Q));
+    const uint32_t grp = __match_any_sync(part, ck);
+    if (lane == (uint32_t)(__ffs(grp) - 1)) atomicAdd(R.ccount + ck, (uint32_t)__popc(grp));
 }
 
 // Persistent pass over the tiles of a run, two tiles in flight per block: while
 // the block advances tile t in one stage, the TMA engine brings tile t + grid
-// into the other stage; results leave through bulk stores.  Inside a tile the
-// live particles are ordered ions first (their push needs the field
-// evaluation), so each warp runs one kind of particle at a time.
+// into the other stage; results leave through bulk stores.  The particles are
+// kept sorted by (ion/atom, cell), so each thread takes its four consecutive
+// slots straight from the stage and the warps stay on one branch.
 __global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ RunDev R, uint32_t ntiles,
                                                       unsigned int* ticket, int bump_step)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     StepShared& S = *reinterpret_cast<StepShared*>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const bool coulomb = (R.flags & kFCoulomb) != 0;
     const uint32_t step = *R.step;
     if (tid == 0) {
@@ -386,68 +421,35 @@ __global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ Ru
             load_tile(R, S.st[s ^ 1u], &S.bar[s ^ 1u], tn);
         }
         for (int i = tid; i < kQSlots; i += kThreads) { S.T.ext[i] = 0u; S.T.lost[i] = 0u; }
-        if (tid == 0) S.T.ke = 0ull;
+        if (tid == 0) {
+            S.T.ke = 0ull;
+            S.npart = 0u;
+        }
         if (!mbar_wait(&S.bar[s], (it >> 1) & 1u)) S.failed = 1;
         __syncthreads();
         if (S.failed) break;
-        const uint32_t g = t * kThreads + tid;
-        const bool valid = g < R.n4;
-        const uint4 M = valid ? st.meta[tid] : make_uint4(kStPad, kStPad, kStPad, kStPad);
-        if (tid == 0) S.npart = 0u;
-        // classify: live ions, live atoms (frozen and padding slots are left alone)
-        const uint32_t mm[4] = {M.x, M.y, M.z, M.w};
-        uint32_t nion = 0, natom = 0;
-        bool is_ion[4], live[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            live[j] = !(mm[j] & (kStFrozen | kStPad));
-            is_ion[j] = live[j] && (mm[j] & kQMask) != 0u;
-            nion += is_ion[j];
-            natom += live[j] && !is_ion[j];
-        }
-        uint32_t ion_incl = nion, atom_incl = natom;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t a = __shfl_up_sync(0xFFFFFFFFu, ion_incl, o);
-            const uint32_t b = __shfl_up_sync(0xFFFFFFFFu, atom_incl, o);
-            if (lane >= o) { ion_incl += a; atom_incl += b; }
-        }
-        if (lane == 31) { S.warp_ions[warp] = ion_incl; S.warp_atoms[warp] = atom_incl; }
-        __syncthreads();
-        uint32_t ion_base = 0, atom_base = 0, ion_tot = 0, atom_tot = 0;
-#pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) {
-            const uint32_t wi = S.warp_ions[w], wa = S.warp_atoms[w];
-            if (w < warp) { ion_base += wi; atom_base += wa; }
-            ion_tot += wi;
-            atom_tot += wa;
-        }
-        uint32_t pi = ion_base + ion_incl - nion;
-        uint32_t pa = ion_tot + atom_base + atom_incl - natom;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (is_ion[j]) S.order[pi++] = (uint16_t)(4 * tid + j);
-            else if (live[j]) S.order[pa++] = (uint16_t)(4 * tid + j);
-        }
-        __syncthreads();
-        const uint32_t nlive = ion_tot + atom_tot;
-        const uint32_t pid0 = t * kTile;
+        const uint32_t nslot = min((uint32_t)kTile, 4u * (R.n4 - t * kThreads));
         unsigned long long ke = 0ull;
-        for (uint32_t i = tid; i < nlive; i += kThreads) {
-            const uint32_t k = S.order[i];
+        // thread tid takes slots tid, tid + 256, tid + 512, tid + 768 of the
+        // tile: a warp covers 32 consecutive slots (one kind of particle, few
+        // cells), the shared-memory accesses are free of bank conflicts, and
+        // every particle runs through the same single copy of the code
+#pragma unroll 1
+        for (uint32_t j = 0; j < (uint32_t)kVec; ++j) {
+            const uint32_t k = (uint32_t)tid + j * kThreads;
+            uint32_t meta = k < nslot ? su(st.meta, k) : kStPad;
             int32_t x = si(st.x, k), y = si(st.y, k), z = si(st.z, k);
             float vx = sf(st.vx, k), vy = sf(st.vy, k), vz = sf(st.vz, k);
-            uint32_t meta = su(st.meta, k), ck;
-            step_particle(R, pid0 + k, step, x, y, z, vx, vy, vz, meta, S.T, ke, ck);
-            si(st.x, k) = x; si(st.y, k) = y; si(st.z, k) = z;
-            sf(st.vx, k) = vx; sf(st.vy, k) = vy; sf(st.vz, k) = vz;
-            su(st.meta, k) = meta;
-            if (coulomb && ck != kNoCell) {
-                // publish the participant for the collision kernels
-                const uint32_t slot = t * kTile + atomicAdd(&S.npart, 1u);
-                R.plist[slot] = make_uint2(pid0 + k, ck);
-                R.pvel[slot] = make_float4(vx, vy, vz, __uint_as_float(meta & kQMask));
+            const uint32_t id = su(st.id, k);
+            uint32_t ck, dc;
+            step_particle(R, id, step, x, y, z, vx, vy, vz, meta, S.T, ke, ck, dc);
+            deposit_warp(R, dc, meta & kQMask);
+            if (k < nslot) {
+                si(st.x, k) = x; si(st.y, k) = y; si(st.z, k) = z;
+                sf(st.vx, k) = vx; sf(st.vy, k) = vy; sf(st.vz, k) = vz;
+                su(st.meta, k) = meta;
             }
+            if (coulomb) publish_warp(R, S.npart, t, t * kTile + k, ck, id, vx, vy, vz, meta & kQMask);
         }
         ke = warp_sum(ke);
         if (lane == 0 && ke) atomicAdd(&S.T.ke, ke);
@@ -464,8 +466,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ Ru
             bulk_store(reinterpret_cast<float4*>(R.vz) + g0, st.vz, bytes);
             bulk_store(reinterpret_cast<uint4*>(R.meta) + g0, st.meta, bytes);
             bulk_commit();
+            if (coulomb) R.tcount[t] = S.npart;
         }
-        if (coulomb && tid == 0) R.tcount[t] = S.npart;
         for (int i = tid; i < kQSlots; i += kThreads) {
             if (S.T.ext[i]) atomicAdd(R.tally + kTallyExtracted + i, (unsigned long long)S.T.ext[i]);
             if (S.T.lost[i]) atomicAdd(R.tally + kTallyLost + i, (unsigned long long)S.T.lost[i]);
@@ -556,10 +558,11 @@ __device__ __forceinline__ void store_fx(SoaPtrs soa, uint32_t i, float x, float
 }
 
 __global__ void k_load_init(LoadCheck lc, SoaPtrs soa, const uint8_t* __restrict__ q8,
-                            uint32_t* __restrict__ meta, uint32_t n, uint32_t cap,
+                            uint32_t* __restrict__ meta, uint32_t* __restrict__ id, uint32_t n, uint32_t cap,
                             unsigned int* __restrict__ bad)
 {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
+        id[i] = i;
         if (i < n) {
             const float x = soa.p[0][i], y = soa.p[1][i], z = soa.p[2][i];
             const float vx = soa.p[3][i], vy = soa.p[4][i], vz = soa.p[5][i];
@@ -582,38 +585,17 @@ __global__ void k_load_init(LoadCheck lc, SoaPtrs soa, const uint8_t* __restrict
     }
 }
 
-__global__ void k_export(int32_t* x, int32_t* y, int32_t* z, uint32_t n, double sxy, double sz)
-{
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float fx = (float)((double)x[i] * sxy);
-        const float fy = (float)((double)y[i] * sxy);
-        const float fz = (float)(((double)z[i] + 2147483648.0) * sz);
-        reinterpret_cast<float*>(x)[i] = fx;
-        reinterpret_cast<float*>(y)[i] = fy;
-        reinterpret_cast<float*>(z)[i] = fz;
-    }
-}
-
 }  // namespace
 
-cudaError_t launch_export(void* x, void* y, void* z, uint32_t n, double sxy, double sz, cudaStream_t s)
-{
-    if (n == 0) return cudaSuccess;
-    int blocks = (int)((n + 255) / 256);
-    if (blocks > 4096) blocks = 4096;
-    k_export<<<blocks, 256, 0, s>>>((int32_t*)x, (int32_t*)y, (int32_t*)z, n, sxy, sz);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_load_init(const LoadCheck& lc, float* const soa[6], const uint8_t* q8, uint32_t* meta,
-                             uint32_t n, uint32_t cap, unsigned int* bad, cudaStream_t s)
+                             uint32_t* id, uint32_t n, uint32_t cap, unsigned int* bad, cudaStream_t s)
 {
     SoaPtrs p;
     for (int k = 0; k < 6; ++k) p.p[k] = soa[k];
     const int threads = 256;
     int blocks = (int)((cap + threads - 1) / threads);
     if (blocks > 8192) blocks = 8192;
-    k_load_init<<<blocks, threads, 0, s>>>(lc, p, q8, meta, n, cap, bad);
+    k_load_init<<<blocks, threads, 0, s>>>(lc, p, q8, meta, id, n, cap, bad);
     return cudaGetLastError();
 }
 

@@ -71,6 +71,10 @@ class DiagOut(ctypes.Structure):
                 ("cell_count", ctypes.c_void_p), ("cell_charge", ctypes.c_void_p)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("sort_every", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("step_launches", ctypes.c_int64), ("step_ms", ctypes.c_double),
                 ("coulomb_launches", ctypes.c_int64), ("coulomb_ms", ctypes.c_double),
@@ -111,6 +115,8 @@ def _load():
                                                   ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                                   ctypes.c_uint32, P, ctypes.POINTER(ctypes.c_int64)]
     lib.ecris_coulomb_collide_noalloc.restype = st
+    lib.ecris_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
+    lib.ecris_set_tuning.restype = st
     return lib
 
 
@@ -128,6 +134,7 @@ ecris_get_state = LIB.ecris_get_state
 ecris_set_profiling = LIB.ecris_set_profiling
 ecris_get_profile = LIB.ecris_get_profile
 ecris_coulomb_collide_noalloc = LIB.ecris_coulomb_collide_noalloc
+ecris_set_tuning = LIB.ecris_set_tuning
 
 
 def check(ctx, status):
@@ -245,6 +252,11 @@ class Run:
         d["meta"] = meta
         d["q"] = (meta & 0xFF).astype(np.int32)
         return d
+
+    def set_tuning(self, sort_every=32):
+        t = Tuning()
+        t.sort_every = int(sort_every)
+        check(self.ctx, ecris_set_tuning(self.ctx, ctypes.byref(t)))
 
     def set_profiling(self, on=True):
         check(self.ctx, ecris_set_profiling(self.ctx, 1 if on else 0))
