@@ -28,8 +28,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-ALGO_BYTES_STEP_KERNEL = 56   # read + write of x,y,z,vx,vy,vz (f32) and meta (u32)
-ALGO_BYTES_CKEY = 4           # Coulomb cell key written by the step kernel when collisions are on
+# step kernel, per particle: reads x,y,z (fixed point), vx,vy,vz, meta and the
+# stable id (32 B), writes all but the id (28 B)
+ALGO_BYTES_STEP_KERNEL = 60
+# per Coulomb participant (an ion that stayed inside): its published record,
+# (slot, cell, id, -) and (v, Q), 32 B written
+ALGO_BYTES_PARTICIPANT = 32
 
 
 def env_int(name, default):
@@ -58,8 +62,9 @@ def kernel_source_hash():
 
 
 def ncu_traffic(n_particles):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    scaled to n particles; None if the kernel changed since it was measured."""
+    """DRAM bytes per launch of the step kernel from the committed ncu summary
+    (a capture on a smaller case, scaled by the particle count); None if the
+    kernel's sources changed since it was measured."""
     path = os.path.join(ROOT, "profiles", "k_step_traffic.json")
     try:
         with open(path) as f:
@@ -274,7 +279,8 @@ def main():
 
     # roofline of the dominant kernel (the fused step kernel)
     k_ms = prof["step_ms"] / max(1, prof["step_launches"])
-    algo = n * (ALGO_BYTES_STEP_KERNEL + (ALGO_BYTES_CKEY if coulomb else 0))
+    ions = int(run.diag()["alive_by_q"][1:].sum()) if coulomb else 0
+    algo = n * ALGO_BYTES_STEP_KERNEL + ions * ALGO_BYTES_PARTICIPANT
     achieved = algo / (k_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     roofline = {"bound": "hbm", "kernel": "k_step", "achieved": achieved, "peak": peak,

@@ -180,6 +180,7 @@ struct ecris_ctx {
     uint32_t* d_hist = nullptr;    // sort histogram (2 Nc + 1), kept zero between sorts
     uint32_t* d_hoff = nullptr;    // its exclusive scan (2 Nc + 2)
     uint32_t* d_hblk = nullptr;    // scan block totals
+    uint4* d_aos = nullptr;        // 32-byte particle records for the sort
     uint32_t sort_every = 32;      // steps between sorts
     uint32_t since_sort = 0;
     int parity = 0;                // which particle set is current (flips at each sort)
@@ -190,6 +191,9 @@ struct ecris_ctx {
     uint64_t param_version = 1;
     uint32_t* d_cslot = nullptr;
     uint32_t* d_sslot = nullptr;
+    uint2* d_pairs = nullptr;
+    uint2* d_trips = nullptr;
+    uint32_t* d_npt = nullptr;
     unsigned long long* d_dep = nullptr;
     unsigned long long* d_count = nullptr;
     unsigned long long* d_charge = nullptr;
@@ -312,8 +316,12 @@ void free_ions(ecris_ctx* ctx)
     free_async(ctx, ctx->d_hist);
     free_async(ctx, ctx->d_hoff);
     free_async(ctx, ctx->d_hblk);
+    free_async(ctx, ctx->d_aos);
     free_async(ctx, ctx->d_cslot);
     free_async(ctx, ctx->d_sslot);
+    free_async(ctx, ctx->d_pairs);
+    free_async(ctx, ctx->d_trips);
+    free_async(ctx, ctx->d_npt);
     free_async(ctx, ctx->d_dep);
     free_async(ctx, ctx->d_count);
     free_async(ctx, ctx->d_charge);
@@ -445,6 +453,9 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.srec = ctx->d_srec;
     R.cslot = ctx->d_cslot;
     R.sslot = ctx->d_sslot;
+    R.pairs = ctx->d_pairs;
+    R.trips = ctx->d_trips;
+    R.npt = ctx->d_npt;
     R.nanbu = ctx->d_nanbu;
     R.nanbu_lnlo = (float)std::log(kNanbuSLo);
     R.nanbu_inv_dln = (float)((kNanbuN - 1) / std::log(kNanbuSHi / kNanbuSLo));
@@ -530,8 +541,8 @@ ecris_status sort_particles(ecris_ctx* ctx)
     dst.id = ctx->d_id2;
     CK(timed(ctx, kKindOther, [&] {
         return launch_sort(*ctx->h_run, (uint32_t)(4 * ctx->n4), dst, ctx->d_hist, ctx->d_hoff, ctx->d_hblk,
-                           ctx->stream);
-    }, 5));
+                           ctx->d_aos, ctx->stream);
+    }, 6));
     for (int k = 0; k < 6; ++k) std::swap(ctx->d_soa[k], ctx->d_soa2[k]);
     std::swap(ctx->d_meta, ctx->d_meta2);
     std::swap(ctx->d_id, ctx->d_id2);
@@ -793,6 +804,7 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         CK(cudaMallocAsync((void**)&ctx->d_hblk, (size_t)sort_scan_blocks((uint32_t)(2 * nc + 1)) * sizeof(uint32_t),
                            ctx->stream));
         CK(cudaMemsetAsync(ctx->d_hist, 0, (2 * nc + 1) * sizeof(uint32_t), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_aos, 2 * cap * sizeof(uint4), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_q8, cap, ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_dep, nc * sizeof(unsigned long long), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_count, nc * sizeof(unsigned long long), ctx->stream));
@@ -808,6 +820,9 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
             CK(cudaMallocAsync((void**)&ctx->d_plist, slots * sizeof(uint4), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_cslot, cap * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_sslot, cap * sizeof(uint32_t), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_pairs, (cap / 2 + 1) * sizeof(uint2), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_trips, (cap / 3 + 1) * sizeof(uint2), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_npt, 2 * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_pvel, slots * sizeof(float4), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_tcount, (cap / kTile + 1) * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_ckeys, cap * sizeof(unsigned long long), ctx->stream));

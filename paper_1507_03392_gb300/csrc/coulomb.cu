@@ -15,10 +15,11 @@
 //                are smaller than its own; that rank is its place in the cell's
 //                order (by hash, then pid), independent of the atomic arrival
 //                order, and the record moves there;
-//   4. pairs     one thread per ordered slot: consecutive ranks pair up; a cell
-//                with an odd count puts ranks 0, 1, 2 in a triplet that collides
-//                (0,1), (1,2), (2,0) over dt/2 each; the thread collides its
-//                pair and writes both new velocities back.
+//                Consecutive ranks pair up; a cell with an odd count puts ranks
+//                0, 1, 2 in a triplet that collides (0,1), (1,2), (2,0) over
+//                dt/2 each; the first ion of every pair and triplet is listed;
+//   4. pairs     one thread per listed pair or triplet collides it and writes
+//                the new velocities back.
 // A collision of ions a, b (same mass M, charges Qa, Qb) over time dt_c uses
 //   s = lnL/(4 pi) (Qa Qb e^2 / (eps0 mu))^2 n g^-3 dt_c,  mu = M/2,
 // n = w m / V_cell for the cell's m ions; A(s) from coth A - 1/A = e^-s
@@ -96,7 +97,11 @@ __global__ void __launch_bounds__(1024) k_scan_b(const __grid_constant__ RunDev 
         const uint32_t w = wsum[lane];
         const uint32_t wi = warp_incl_scan(w);
         wsum[lane] = wi - w;
-        if (lane == 31) R.coff[ncells] = wi;
+        if (lane == 31) {
+            R.coff[ncells] = wi;
+            R.npt[0] = 0u;
+            R.npt[1] = 0u;
+        }
     }
     __syncthreads();
     uint32_t off = wsum[warp] + incl - sum;
@@ -203,44 +208,77 @@ __device__ __forceinline__ void write_back(const RunDev& R, uint32_t slot, const
     atomicOr(R.meta + slot, kEvCoulomb);   // result unused: a fire-and-forget reduction
 }
 
-// place each participant at its rank within its cell's order
+// place each participant at its rank within its cell's order, and list the
+// first ion of every pair (and of every triplet) for the collision kernel
 __global__ void k_rank(const __grid_constant__ RunDev R, uint32_t ncells)
 {
     const uint32_t total = R.coff[ncells];
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += gridDim.x * blockDim.x) {
-        const unsigned long long key = R.ckeys[j];
-        const float4 rec = R.crec[j];
-        const uint32_t cell = __float_as_uint(rec.w) >> 6;
-        const uint32_t seg = R.coff[cell], m = R.coff[cell + 1] - seg;
-        uint32_t rank = 0;
-        const unsigned long long* k = R.ckeys + seg;
-        for (uint32_t i = 0; i < m; ++i) rank += (k[i] < key) ? 1u : 0u;
-        R.skeys[seg + rank] = key;
-        R.srec[seg + rank] = rec;
-        R.sslot[seg + rank] = R.cslot[j];
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t end = (total + 31u) & ~31u;   // whole warps iterate together
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < end; j += gridDim.x * blockDim.x) {
+        uint32_t kind = 0, slot = 0, m = 0;      // kind 1: starts a pair, 2: starts a triplet
+        if (j < total) {
+            const unsigned long long key = R.ckeys[j];
+            const float4 rec = R.crec[j];
+            const uint32_t cell = __float_as_uint(rec.w) >> 6;
+            const uint32_t seg = R.coff[cell];
+            m = R.coff[cell + 1] - seg;
+            uint32_t rank = 0;
+            const unsigned long long* k = R.ckeys + seg;
+            for (uint32_t i = 0; i < m; ++i) rank += (k[i] < key) ? 1u : 0u;
+            slot = seg + rank;
+            R.skeys[slot] = key;
+            R.srec[slot] = rec;
+            R.sslot[slot] = R.cslot[j];
+            if (m >= 2u) {
+                const uint32_t start = (m & 1u) ? 3u : 0u;
+                if ((m & 1u) && rank == 0u) kind = 2;
+                else if (rank >= start && !((rank - start) & 1u)) kind = 1;
+            }
+        }
+        // warp-aggregated appends to the pair and triplet lists; the two
+        // counter updates are issued together so their latencies overlap
+        const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, kind == 1u);
+        const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, kind == 2u);
+        if (b1 | b2) {
+            uint32_t base1 = 0, base2 = 0;
+            if (lane == 0) {
+                if (b1) base1 = atomicAdd(R.npt, (uint32_t)__popc(b1));
+                if (b2) base2 = atomicAdd(R.npt + 1, (uint32_t)__popc(b2));
+            }
+            base1 = __shfl_sync(0xFFFFFFFFu, base1, 0);
+            base2 = __shfl_sync(0xFFFFFFFFu, base2, 0);
+            const uint32_t below = (1u << lane) - 1u;
+            if (kind == 1u) R.pairs[base1 + (uint32_t)__popc(b1 & below)] = make_uint2(slot, m);
+            if (kind == 2u) R.trips[base2 + (uint32_t)__popc(b2 & below)] = make_uint2(slot, m);
+        }
     }
 }
 
-// one thread per ordered slot: collide the pair (or the triplet) it starts
+// one thread per listed pair or triplet: collide it and write the velocities back
 __global__ void k_pairs(const __grid_constant__ RunDev R, uint32_t ncells, unsigned int* ticket)
 {
     __shared__ int s_last;
     const uint32_t step = *R.step;
-    const uint32_t total = R.coff[ncells];
+    const uint32_t np = R.npt[0], nt = R.npt[1];
     const float dt = R.dt;
     unsigned long long ncoll = 0;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        float4 ra = R.srec[t];
-        const uint32_t cell = __float_as_uint(ra.w) >> 6;
-        const uint32_t seg = R.coff[cell], m = R.coff[cell + 1] - seg;
-        const uint32_t r = t - seg;
-        if (m < 2u) continue;
-        const float mc = (float)m;
-        const uint32_t pa = (uint32_t)R.skeys[t];   // ids give the random words
-        if ((m & 1u) && r == 0u) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np + nt; i += gridDim.x * blockDim.x) {
+        if (i < np) {
+            const uint2 pr = R.pairs[i];
+            const uint32_t t = pr.x;
+            float4 ra = R.srec[t], rb = R.srec[t + 1];
+            collide(R, ra, rb, dt, (float)pr.y, (uint32_t)R.skeys[t], step);   // ids give the random words
+            write_back(R, R.sslot[t], ra);
+            write_back(R, R.sslot[t + 1], rb);
+            ncoll += 1;
+        } else {
             // triplet of ranks 0, 1, 2: (0,1), (1,2), (2,0) over dt/2 each
-            float4 rb = R.srec[t + 1], rc = R.srec[t + 2];
-            const uint32_t pb = (uint32_t)R.skeys[t + 1], pc = (uint32_t)R.skeys[t + 2];
+            const uint2 tr = R.trips[i - np];
+            const uint32_t t = tr.x;
+            const float mc = (float)tr.y;
+            float4 ra = R.srec[t], rb = R.srec[t + 1], rc = R.srec[t + 2];
+            const uint32_t pa = (uint32_t)R.skeys[t], pb = (uint32_t)R.skeys[t + 1], pc = (uint32_t)R.skeys[t + 2];
             collide(R, ra, rb, 0.5f * dt, mc, pa, step);
             collide(R, rb, rc, 0.5f * dt, mc, pb, step);
             collide(R, rc, ra, 0.5f * dt, mc, pc, step);
@@ -248,14 +286,6 @@ __global__ void k_pairs(const __grid_constant__ RunDev R, uint32_t ncells, unsig
             write_back(R, R.sslot[t + 1], rb);
             write_back(R, R.sslot[t + 2], rc);
             ncoll += 3;
-        } else {
-            const uint32_t start = (m & 1u) ? 3u : 0u;
-            if (r < start || ((r - start) & 1u)) continue;
-            float4 rb = R.srec[t + 1];
-            collide(R, ra, rb, dt, mc, pa, step);
-            write_back(R, R.sslot[t], ra);
-            write_back(R, R.sslot[t + 1], rb);
-            ncoll += 1;
         }
     }
 #pragma unroll

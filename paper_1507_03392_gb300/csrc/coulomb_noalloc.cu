@@ -14,7 +14,7 @@
 //
 // Limits: at most kNaMaxIons particles and kNaMaxCells cells per call; larger
 // sizes are rejected with ECRIS_EINVAL.  The array (kNaScratchBytes, about
-// 6 MB) is held by every GPU that loads the library until the process exits.
+// 7 MB) is held by every GPU that loads the library until the process exits.
 // Every call shares it and finds the last call's contents there; what must
 // start at zero is cleared at the start of each call.  Calls whose GPU work
 // overlaps (different streams, or several host threads) race on the array
@@ -52,9 +52,11 @@ constexpr size_t kOffSkeys = kOffCrec + align256(sizeof(float4) * kNaMaxIons);
 constexpr size_t kOffSrec = kOffSkeys + align256(sizeof(unsigned long long) * kNaMaxIons);
 constexpr size_t kOffCslot = kOffSrec + align256(sizeof(float4) * kNaMaxIons);
 constexpr size_t kOffSslot = kOffCslot + align256(sizeof(uint32_t) * kNaMaxIons);
-constexpr size_t kOffNanbu = kOffSslot + align256(sizeof(uint32_t) * kNaMaxIons);
+constexpr size_t kOffPairs = kOffSslot + align256(sizeof(uint32_t) * kNaMaxIons);
+constexpr size_t kOffTrips = kOffPairs + align256(sizeof(uint2) * (kNaMaxIons / 2 + 1));
+constexpr size_t kOffNanbu = kOffTrips + align256(sizeof(uint2) * (kNaMaxIons / 3 + 1));
 constexpr size_t kOffWords = kOffNanbu + align256(sizeof(float) * kNanbuN);
-// words: step, ticket, then the tally block
+// words: step, ticket, pair count, triplet count; then the tally block
 constexpr size_t kOffTally = kOffWords + 256;
 constexpr size_t kNaScratchBytes = kOffTally + align256(sizeof(unsigned long long) * kTallyWords);
 
@@ -211,6 +213,9 @@ extern "C" ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* 
     R.srec = reinterpret_cast<float4*>(base + kOffSrec);
     R.cslot = reinterpret_cast<uint32_t*>(base + kOffCslot);
     R.sslot = reinterpret_cast<uint32_t*>(base + kOffSslot);
+    R.pairs = reinterpret_cast<uint2*>(base + kOffPairs);
+    R.trips = reinterpret_cast<uint2*>(base + kOffTrips);
+    R.npt = reinterpret_cast<uint32_t*>(base + kOffWords) + 2;
     R.nanbu = reinterpret_cast<const float*>(base + kOffNanbu);
     R.nanbu_lnlo = (float)std::log(kNanbuSLo);
     R.nanbu_inv_dln = (float)((kNanbuN - 1) / std::log(kNanbuSHi / kNanbuSLo));
