@@ -228,9 +228,56 @@ ecris_status ecris_get_profile(ecris_ctx* ctx, ecris_profile* out);
  * 32; >= 1).  ecris_get_state always returns particles in load order. */
 typedef struct {
     int32_t sort_every;
-    int32_t reserved[7];   /* set to 0 */
+    int32_t blocks_per_sm;  /* batches: resident step-kernel blocks per SM (0: as many as fit) */
+    int32_t reserved[6];    /* set to 0 */
 } ecris_tuning;
 ecris_status ecris_set_tuning(ecris_ctx* ctx, const ecris_tuning* t);
+
+/* ------------------------------------------------------------------------ */
+/* Batched form: many runs advanced together (the paper's parameter scans of */
+/* Sec. III -- gas flow, microwave power via n_e and T_e -- run as one       */
+/* batch).  Every step of all active runs is one persistent launch of the     */
+/* step kernel over a work list of (run, tile) items, captured with the       */
+/* runs' collision kernels in one CUDA graph.  Each run keeps its particles   */
+/* resident on the device and gives exactly the results it gives alone.      */
+/* ------------------------------------------------------------------------ */
+typedef struct ecris_batch ecris_batch;
+
+/* Create a batch on `device`, ordering its work on `cuda_stream` (NULL: its
+ * own stream).  hbm_budget_bytes > 0 caps the device memory the batch's runs
+ * may hold (see ecris_run_bytes); 0 means no cap. */
+ecris_status ecris_batch_create(ecris_batch** out, int device, void* cuda_stream, size_t hbm_budget_bytes);
+void ecris_batch_destroy(ecris_batch* b);
+/* message for the last failure on the batch (empty if none) */
+const char* ecris_batch_last_error(const ecris_batch* b);
+
+/* Device bytes a run of n particles on an nx x ny x nz mesh holds in a batch
+ * (an upper estimate used for admission). */
+size_t ecris_run_bytes(size_t n, int32_t nx, int32_t ny, int32_t nz, int coulomb);
+
+/* Add a run: the arguments of ecris_init_fields and ecris_load_ions plus its
+ * time step dt (s).  On success *run_out receives the run's handle (>= 0).
+ * Returns ECRIS_ENOMEM without side effects when the run would exceed the
+ * batch's memory budget (the caller may retry after removing runs). */
+ecris_status ecris_batch_add_run(ecris_batch* b, const ecris_geometry* geo, const ecris_bfield* bf,
+                                 const ecris_grid* grid, const ecris_species* sp, const ecris_mcc* mcc,
+                                 size_t n, const float* const xyzv[6], const uint8_t* q, double weight,
+                                 uint64_t seed, double dt, int src_is_device, int32_t* run_out);
+/* Remove a run and release its device memory (synchronises the stream). */
+ecris_status ecris_batch_remove_run(ecris_batch* b, int32_t run);
+/* Advance every run of the batch by nsteps steps of its own dt. */
+ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps);
+/* Per-run diagnostics and state, as ecris_diag / ecris_get_state. */
+ecris_status ecris_batch_diag(ecris_batch* b, int32_t run, ecris_diag_out* out);
+ecris_status ecris_batch_get_state(ecris_batch* b, int32_t run, float* const xyzv[6], uint32_t* meta,
+                                   int dst_is_device);
+/* Bytes held by the batch's runs and its budget (0: none). */
+ecris_status ecris_batch_memory(const ecris_batch* b, size_t* used, size_t* budget);
+/* Launch-shape autotuner: times `trial_steps` steps of the batch for each
+ * candidate (resident step-kernel blocks per SM, steps between particle
+ * sorts), keeps the fastest and returns it in *chosen (may be NULL).  The
+ * trial steps are real steps of every run; no result depends on the choice. */
+ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tuning* chosen);
 
 /* Allocation-free Coulomb collision step.  The paper has no counterpart: this
  * is an interface for callers that cannot allocate device memory when they

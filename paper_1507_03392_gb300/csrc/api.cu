@@ -1084,3 +1084,397 @@ ecris_status ecris_get_profile(ecris_ctx* ctx, ecris_profile* out)
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Batched form
+// ============================================================================
+struct ecris_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sm_count = 0;
+    int blocks_per_sm = 0;          // 0: as many as fit
+    int max_blocks_per_sm = 1;
+    uint32_t sort_every = 32;
+    size_t budget = 0, used = 0;
+    std::string err;
+    std::vector<ecris_ctx*> runs;   // by handle; nullptr: free slot
+    std::vector<size_t> bytes;      // device bytes charged per run
+    std::vector<double> dt;         // time step per run
+    RunDev* d_runs = nullptr;       // parameter blocks by handle
+    RunDev* h_runs = nullptr;       // pinned staging of the same
+    cudaEvent_t staged = nullptr;   // the last upload from h_runs has finished
+    size_t runs_cap = 0;
+    uint2* d_items = nullptr;       // work list (handle, tile)
+    size_t items_cap = 0;
+    uint32_t nitems = 0;
+    bool layout_dirty = true;       // work list must be rebuilt
+    bool params_dirty = true;       // parameter blocks must be uploaded
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_dirty = true;
+};
+
+namespace {
+
+ecris_status bfail(ecris_batch* b, ecris_status st, const std::string& msg)
+{
+    b->err = msg;
+    return st;
+}
+
+#define BCK(call)                                                                      \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? ECRIS_ENOMEM : ECRIS_ECUDA, \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));           \
+    } while (0)
+
+bool run_live(const ecris_batch* b, int32_t r)
+{
+    return r >= 0 && (size_t)r < b->runs.size() && b->runs[r] != nullptr;
+}
+
+// upload the parameter blocks of all runs (free slots get a block whose step
+// pointer is NULL, which the kernels skip)
+ecris_status batch_upload(ecris_batch* b)
+{
+    const size_t nr = b->runs.size();
+    if (nr > b->runs_cap) {
+        BCK(cudaStreamSynchronize(b->stream));
+        if (b->d_runs) cudaFreeAsync(b->d_runs, b->stream);
+        if (b->h_runs) cudaFreeHost(b->h_runs);
+        b->runs_cap = nr + 16;
+        BCK(cudaMallocAsync((void**)&b->d_runs, b->runs_cap * sizeof(RunDev), b->stream));
+        BCK(cudaMallocHost((void**)&b->h_runs, b->runs_cap * sizeof(RunDev)));
+        b->graph_dirty = true;
+    } else {
+        BCK(cudaEventSynchronize(b->staged));   // the previous upload has read the staging copy
+    }
+    for (size_t r = 0; r < nr; ++r) {
+        if (b->runs[r]) b->h_runs[r] = *b->runs[r]->h_run;
+        else std::memset(&b->h_runs[r], 0, sizeof(RunDev));
+    }
+    if (nr) BCK(cudaMemcpyAsync(b->d_runs, b->h_runs, nr * sizeof(RunDev), cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaEventRecord(b->staged, b->stream));
+    b->params_dirty = false;
+    return ECRIS_OK;
+}
+
+ecris_status batch_items(ecris_batch* b)
+{
+    std::vector<uint2> items;
+    for (size_t r = 0; r < b->runs.size(); ++r)
+        if (b->runs[r])
+            for (uint32_t t = 0; t < b->runs[r]->ntiles; ++t) items.push_back(make_uint2((uint32_t)r, t));
+    if (items.size() > b->items_cap) {
+        BCK(cudaStreamSynchronize(b->stream));
+        if (b->d_items) cudaFreeAsync(b->d_items, b->stream);
+        b->items_cap = items.size() + 1024;
+        BCK(cudaMallocAsync((void**)&b->d_items, b->items_cap * sizeof(uint2), b->stream));
+    }
+    if (!items.empty()) {
+        BCK(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(uint2), cudaMemcpyHostToDevice,
+                            b->stream));
+        BCK(cudaStreamSynchronize(b->stream));   // the host vector dies here
+    }
+    b->nitems = (uint32_t)items.size();
+    b->layout_dirty = false;
+    b->graph_dirty = true;
+    return ECRIS_OK;
+}
+
+// one step of every run: the batched step kernel, the collision kernels of
+// the runs that have them, and the step counters of the others
+cudaError_t batch_launch(ecris_batch* b)
+{
+    const int bps = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, b->max_blocks_per_sm) : b->max_blocks_per_sm;
+    cudaError_t e = launch_step_batch(b->d_runs, b->d_items, b->nitems, b->sm_count * bps, b->stream);
+    for (size_t r = 0; e == cudaSuccess && r < b->runs.size(); ++r) {
+        ecris_ctx* c = b->runs[r];
+        if (!c || !(c->h.mcc.flags & kFCoulomb)) continue;
+        const uint32_t nc = (uint32_t)((size_t)c->h.nx * c->h.ny * c->h.nz);
+        e = launch_coulomb(*c->h_run, nc, c->ntiles, c->d_ticket, c->collide_grid, b->stream);
+    }
+    if (e == cudaSuccess) e = launch_bump_steps(b->d_runs, (uint32_t)b->runs.size(), b->stream);
+    return e;
+}
+
+ecris_status batch_graph(ecris_batch* b)
+{
+    if (!b->graph_dirty && b->gexec) return ECRIS_OK;
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t e = batch_launch(b);
+    const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    BCK(e);
+    BCK(e2);
+    const cudaError_t e3 = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    BCK(e3);
+    b->graph_dirty = false;
+    return ECRIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ecris_run_bytes(size_t n, int32_t nx, int32_t ny, int32_t nz, int coulomb)
+{
+    const size_t cap = 4 * ((n + 3) / 4) + 4;
+    const size_t nc = (size_t)(nx > 0 ? nx : 0) * (ny > 0 ? ny : 0) * (nz > 0 ? nz : 0);
+    // two particle sets with ids, the sort's records, load bytes, Coulomb lists
+    size_t per_p = 2 * 32 + 32 + 4 + 1;
+    if (coulomb) per_p += 16 + 16 + 8 + 16 + 4 + 8 + 16 + 4 + 4 + 3 + 16;
+    // cell records, E, deposit, time sums, sort histogram and scan, Coulomb counts
+    size_t per_c = 16 + 16 + 8 + 8 + 8 + 4 + 4 + (coulomb ? 12 : 0);
+    return cap * per_p + nc * per_c + (1u << 20);
+}
+
+ecris_status ecris_batch_create(ecris_batch** out, int device, void* cuda_stream, size_t hbm_budget_bytes)
+{
+    if (!out) {
+        g_create_error = "batch_create: out is NULL";
+        return ECRIS_EINVAL;
+    }
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        g_create_error = "batch_create: no such CUDA device";
+        return ECRIS_EINVAL;
+    }
+    ecris_batch* b = new (std::nothrow) ecris_batch();
+    if (!b) return ECRIS_ENOMEM;
+    b->device = device;
+    b->budget = hbm_budget_bytes;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            b->stream = (cudaStream_t)cuda_stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+            b->own_stream = e == cudaSuccess;
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("batch_create: ") + cudaGetErrorString(e);
+        if (b->own_stream) cudaStreamDestroy(b->stream);
+        delete b;
+        return ECRIS_ECUDA;
+    }
+    b->max_blocks_per_sm = step_batch_blocks_per_sm();
+    *out = b;
+    return ECRIS_OK;
+}
+
+void ecris_batch_destroy(ecris_batch* b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    for (auto* c : b->runs)
+        if (c) ecris_destroy(c);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->d_runs) cudaFreeAsync(b->d_runs, b->stream);
+    if (b->d_items) cudaFreeAsync(b->d_items, b->stream);
+    cudaStreamSynchronize(b->stream);
+    if (b->h_runs) cudaFreeHost(b->h_runs);
+    if (b->staged) cudaEventDestroy(b->staged);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+const char* ecris_batch_last_error(const ecris_batch* b)
+{
+    return b ? b->err.c_str() : g_create_error.c_str();
+}
+
+ecris_status ecris_batch_add_run(ecris_batch* b, const ecris_geometry* geo, const ecris_bfield* bf,
+                                 const ecris_grid* grid, const ecris_species* sp, const ecris_mcc* mcc,
+                                 size_t n, const float* const xyzv[6], const uint8_t* q, double weight,
+                                 uint64_t seed, double dt, int src_is_device, int32_t* run_out)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (!run_out || !grid || !mcc) return bfail(b, ECRIS_EINVAL, "batch_add_run: NULL argument");
+    if (!finite_pos(dt)) return bfail(b, ECRIS_EINVAL, "batch_add_run: dt must be finite and > 0");
+    const size_t need = ecris_run_bytes(n, grid->nx, grid->ny, grid->nz, (mcc->flags & kFCoulomb) != 0);
+    if (b->budget && b->used + need > b->budget)
+        return bfail(b, ECRIS_ENOMEM, "batch_add_run: the run (" + std::to_string(need) + " bytes) would exceed the "
+                     "memory budget (" + std::to_string(b->used) + " of " + std::to_string(b->budget) + " used)");
+    BCK(cudaSetDevice(b->device));
+    ecris_ctx* c = nullptr;
+    ecris_status st = ecris_create(&c, b->device, b->stream);
+    if (st != ECRIS_OK) return bfail(b, st, std::string("batch_add_run: ") + ecris_last_error(nullptr));
+    st = ecris_init_fields(c, geo, bf, grid, sp, mcc);
+    if (st == ECRIS_OK) st = ecris_load_ions(c, n, xyzv, q, weight, seed, src_is_device);
+    if (st == ECRIS_OK) st = upload_dt(c, dt);
+    if (st != ECRIS_OK) {
+        const std::string m = c->err;
+        ecris_destroy(c);
+        return bfail(b, st, "batch_add_run: " + m);
+    }
+    c->sort_every = b->sort_every;
+    int32_t h = -1;
+    for (size_t r = 0; r < b->runs.size(); ++r)
+        if (!b->runs[r]) {
+            h = (int32_t)r;
+            break;
+        }
+    if (h < 0) {
+        h = (int32_t)b->runs.size();
+        b->runs.push_back(nullptr);
+        b->bytes.push_back(0);
+        b->dt.push_back(0.0);
+    }
+    b->runs[h] = c;
+    b->bytes[h] = need;
+    b->dt[h] = dt;
+    b->used += need;
+    b->layout_dirty = b->params_dirty = true;
+    *run_out = h;
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_remove_run(ecris_batch* b, int32_t run)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (!run_live(b, run)) return bfail(b, ECRIS_EINVAL, "batch_remove_run: no such run");
+    BCK(cudaSetDevice(b->device));
+    BCK(cudaStreamSynchronize(b->stream));
+    ecris_destroy(b->runs[run]);
+    b->runs[run] = nullptr;
+    b->used -= b->bytes[run];
+    b->bytes[run] = 0;
+    b->layout_dirty = b->params_dirty = true;
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps)
+{
+    if (!b) return ECRIS_EINVAL;
+    BCK(cudaSetDevice(b->device));
+    for (auto* c : b->runs)
+        if (c && (c->failed || c->steps_done + nsteps >= kMaxSteps))
+            return bfail(b, ECRIS_ESTATE, "batch_step: a run failed earlier or would pass 2^30 steps");
+    if (b->layout_dirty) {
+        ecris_status st = batch_items(b);
+        if (st != ECRIS_OK) return st;
+    }
+    for (uint32_t s = 0; s < nsteps; ++s) {
+        // regroup the particles of the runs that are due; their parameter
+        // blocks change (the arrays swap), and so does the captured graph
+        // when a run's collision kernels take the block by value
+        for (auto* c : b->runs) {
+            if (!c || c->n4 == 0 || c->since_sort < c->sort_every) continue;
+            ecris_status st = sort_particles(c);
+            if (st != ECRIS_OK) return bfail(b, st, "batch_step: " + c->err);
+            b->params_dirty = true;
+            if (c->h.mcc.flags & kFCoulomb) b->graph_dirty = true;
+        }
+        if (b->params_dirty) {
+            ecris_status st = batch_upload(b);
+            if (st != ECRIS_OK) return st;
+        }
+        ecris_status st = batch_graph(b);
+        if (st != ECRIS_OK) return st;
+        BCK(cudaGraphLaunch(b->gexec, b->stream));
+        for (size_t r = 0; r < b->runs.size(); ++r) {
+            ecris_ctx* c = b->runs[r];
+            if (!c) continue;
+            c->steps_done += 1;
+            c->time_s += b->dt[r];
+            ++c->since_sort;
+            if (++c->since_fold >= c->fold_every) {
+                const uint32_t nc = (uint32_t)((size_t)c->h.nx * c->h.ny * c->h.nz);
+                BCK(launch_fold(*c->h_run, nc, c->d_count, c->d_charge, b->stream));
+                c->since_fold = 0;
+            }
+        }
+    }
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_diag(ecris_batch* b, int32_t run, ecris_diag_out* out)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (!run_live(b, run)) return bfail(b, ECRIS_EINVAL, "batch_diag: no such run");
+    ecris_status st = ecris_diag(b->runs[run], out);
+    if (st != ECRIS_OK) return bfail(b, st, "batch_diag: " + b->runs[run]->err);
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_get_state(ecris_batch* b, int32_t run, float* const xyzv[6], uint32_t* meta,
+                                   int dst_is_device)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (!run_live(b, run)) return bfail(b, ECRIS_EINVAL, "batch_get_state: no such run");
+    ecris_status st = ecris_get_state(b->runs[run], xyzv, meta, dst_is_device);
+    if (st != ECRIS_OK) return bfail(b, st, "batch_get_state: " + b->runs[run]->err);
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_memory(const ecris_batch* b, size_t* used, size_t* budget)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (used) *used = b->used;
+    if (budget) *budget = b->budget;
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tuning* chosen)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (trial_steps == 0) return bfail(b, ECRIS_EINVAL, "batch_autotune: trial_steps must be > 0");
+    BCK(cudaSetDevice(b->device));
+    cudaEvent_t t0, t1;
+    BCK(cudaEventCreate(&t0));
+    BCK(cudaEventCreate(&t1));
+    const int sorts[3] = {8, 32, 128};
+    float best = 1e30f;
+    int best_bps = b->max_blocks_per_sm, best_sort = (int)b->sort_every;
+    ecris_status st = ECRIS_OK;
+    for (int bps = 1; bps <= b->max_blocks_per_sm && st == ECRIS_OK; ++bps) {
+        for (int k = 0; k < 3 && st == ECRIS_OK; ++k) {
+            b->blocks_per_sm = bps;
+            b->sort_every = (uint32_t)sorts[k];
+            for (auto* c : b->runs)
+                if (c) c->sort_every = b->sort_every;
+            b->graph_dirty = true;
+            st = ecris_batch_step(b, 1);   // capture outside the timing
+            if (st != ECRIS_OK) break;
+            cudaEventRecord(t0, b->stream);
+            st = ecris_batch_step(b, trial_steps);
+            cudaEventRecord(t1, b->stream);
+            if (cudaEventSynchronize(t1) != cudaSuccess) st = ECRIS_ECUDA;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, t0, t1);
+            if (st == ECRIS_OK && ms < best) {
+                best = ms;
+                best_bps = bps;
+                best_sort = sorts[k];
+            }
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    b->blocks_per_sm = best_bps;
+    b->sort_every = (uint32_t)best_sort;
+    for (auto* c : b->runs)
+        if (c) c->sort_every = b->sort_every;
+    b->graph_dirty = true;
+    if (chosen) {
+        std::memset(chosen, 0, sizeof *chosen);
+        chosen->sort_every = best_sort;
+        chosen->blocks_per_sm = best_bps;
+    }
+    return st;
+}
+
+}  // extern "C"

@@ -296,6 +296,14 @@ cudaError_t launch_census(const RunDev& R, uint32_t n4, unsigned long long* cens
 
 // resident blocks per SM of the step kernel
 int step_blocks_per_sm();
+int step_batch_blocks_per_sm();
+// batch form: one persistent step-kernel launch over the work items (run,
+// tile) of many runs whose parameter blocks are in device memory (it leaves
+// the step counters alone); launch_bump_steps then advances the counters of
+// the runs without Coulomb collisions (the collision kernels of the others,
+// launched in between, advance theirs); entries with step == NULL are skipped
+cudaError_t launch_step_batch(const RunDev* runs, const uint2* items, uint32_t nitems, int grid, cudaStream_t s);
+cudaError_t launch_bump_steps(const RunDev* runs, uint32_t nruns, cudaStream_t s);
 // message returned by ecris_last_error(NULL) on the calling thread
 void ecris_internal_set_thread_error(const char* msg);
 

@@ -390,37 +390,69 @@ __device__ __forceinline__ void publish_warp(const RunDev& R, uint32_t& npart, u
     if (lane == (uint32_t)(__ffs(grp) - 1)) atomicAdd(R.ccount + ck, (uint32_t)__popc(grp));
 }
 
-// Persistent pass over the tiles of a run, two tiles in flight per block: while
-// the block advances tile t in one stage, the TMA engine brings tile t + grid
+// Where the tiles come from: one run (its parameter block a kernel argument)
+// or a batch of runs (parameter blocks in device memory and a work list of
+// (run, tile) items; the block stages the current item's block in shared
+// memory).
+struct SingleRun {
+    const RunDev& R;
+    uint32_t ntiles;
+    __device__ __forceinline__ uint32_t count() const { return ntiles; }
+    __device__ __forceinline__ uint2 item(uint32_t i) const { return make_uint2(0u, i); }
+    __device__ __forceinline__ const RunDev& global(uint32_t) const { return R; }
+};
+
+struct BatchRuns {
+    const RunDev* runs;
+    const uint2* items;
+    uint32_t nitems;
+    __device__ __forceinline__ uint32_t count() const { return nitems; }
+    __device__ __forceinline__ uint2 item(uint32_t i) const { return items[i]; }
+    __device__ __forceinline__ const RunDev& global(uint32_t r) const { return runs[r]; }
+};
+
+// Persistent pass over the work items, two tiles in flight per block: while
+// the block advances one tile in one stage, the TMA engine brings the next
 // into the other stage; results leave through bulk stores.  The particles are
-// kept sorted by (ion/atom, cell), so each thread takes its four consecutive
-// slots straight from the stage and the warps stay on one branch.
-__global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ RunDev R, uint32_t ntiles,
-                                                      unsigned int* ticket, int bump_step)
+// kept sorted by (ion/atom, cell), so each thread takes slots tid, tid + 256,
+// ... straight from the stage and the warps stay on one branch.
+template <bool kBatch, class Src>
+__device__ __forceinline__ void step_tiles(StepShared& S, RunDev* Rs, const Src& src, unsigned int* ticket,
+                                           int bump_step)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    StepShared& S = *reinterpret_cast<StepShared*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31;
-    const bool coulomb = (R.flags & kFCoulomb) != 0;
-    const uint32_t step = *R.step;
     if (tid == 0) {
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
         S.failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    uint32_t cur_run = 0xFFFFFFFFu;
     __syncthreads();
-    uint32_t t = blockIdx.x;
-    if (tid == 0 && t < ntiles) load_tile(R, S.st[0], &S.bar[0], t);
-    for (uint32_t it = 0; t < ntiles; ++it, t += gridDim.x) {
+    const uint32_t nitems = src.count();
+    uint32_t i = blockIdx.x;
+    if (tid == 0 && i < nitems) {
+        const uint2 it0 = src.item(i);
+        load_tile(src.global(it0.x), S.st[0], &S.bar[0], it0.y);
+    }
+    for (uint32_t it = 0; i < nitems; ++it, i += gridDim.x) {
         const uint32_t s = it & 1u;
         Stage& st = S.st[s];
-        const uint32_t tn = t + gridDim.x;
-        if (tid == 0 && tn < ntiles) {
+        const uint2 item = src.item(i);
+        const uint32_t in = i + gridDim.x;
+        if (tid == 0 && in < nitems) {
+            const uint2 itn = src.item(in);
             bulk_wait_read_all();   // the other stage's previous stores have read their data
-            load_tile(R, S.st[s ^ 1u], &S.bar[s ^ 1u], tn);
+            load_tile(src.global(itn.x), S.st[s ^ 1u], &S.bar[s ^ 1u], itn.y);
         }
-        for (int i = tid; i < kQSlots; i += kThreads) { S.T.ext[i] = 0u; S.T.lost[i] = 0u; }
+        if (kBatch && item.x != cur_run) {
+            // stage this run's parameter block (all threads, one word each)
+            const uint32_t* g = reinterpret_cast<const uint32_t*>(&src.global(item.x));
+            uint32_t* d = reinterpret_cast<uint32_t*>(Rs);
+            for (uint32_t w = tid; w < sizeof(RunDev) / 4; w += kThreads) d[w] = g[w];
+            cur_run = item.x;
+        }
+        for (int k = tid; k < kQSlots; k += kThreads) { S.T.ext[k] = 0u; S.T.lost[k] = 0u; }
         if (tid == 0) {
             S.T.ke = 0ull;
             S.npart = 0u;
@@ -428,6 +460,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ Ru
         if (!mbar_wait(&S.bar[s], (it >> 1) & 1u)) S.failed = 1;
         __syncthreads();
         if (S.failed) break;
+        const RunDev& R = kBatch ? *Rs : src.global(0);
+        const bool coulomb = (R.flags & kFCoulomb) != 0;
+        const uint32_t step = *R.step;
+        const uint32_t t = item.y;
         const uint32_t nslot = min((uint32_t)kTile, 4u * (R.n4 - t * kThreads));
         unsigned long long ke = 0ull;
         // thread tid takes slots tid, tid + 256, tid + 512, tid + 768 of the
@@ -468,9 +504,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ Ru
             bulk_commit();
             if (coulomb) R.tcount[t] = S.npart;
         }
-        for (int i = tid; i < kQSlots; i += kThreads) {
-            if (S.T.ext[i]) atomicAdd(R.tally + kTallyExtracted + i, (unsigned long long)S.T.ext[i]);
-            if (S.T.lost[i]) atomicAdd(R.tally + kTallyLost + i, (unsigned long long)S.T.lost[i]);
+        for (int k = tid; k < kQSlots; k += kThreads) {
+            if (S.T.ext[k]) atomicAdd(R.tally + kTallyExtracted + k, (unsigned long long)S.T.ext[k]);
+            if (S.T.lost[k]) atomicAdd(R.tally + kTallyLost + k, (unsigned long long)S.T.lost[k]);
         }
         if (tid == 0 && S.T.ke) atomicAdd(R.tally + kTallyKe, S.T.ke);
         __syncthreads();
@@ -478,13 +514,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ Ru
     if (tid == 0) {
         bulk_wait_all();        // stores complete before the block retires
         if (S.failed) {
-            atomicExch(R.err, kErrTimeout);
+            atomicExch((kBatch ? *Rs : src.global(0)).err, kErrTimeout);
             // the loads this block issued may still land: wait (bounded) for them
             mbar_wait(&S.bar[0], 0u);
             mbar_wait(&S.bar[1], 0u);
         }
     }
-    if (bump_step) {
+    if (!kBatch && bump_step) {
         // the last block to finish advances the run's step counter
         if (tid == 0) {
             __threadfence();
@@ -493,10 +529,36 @@ __global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ Ru
         }
         __syncthreads();
         if (S.last && tid == 0) {
-            *R.step += 1u;
+            *src.global(0).step += 1u;
             *ticket = 0u;
         }
     }
+}
+
+__global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ RunDev R, uint32_t ntiles,
+                                                      unsigned int* ticket, int bump_step)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    StepShared& S = *reinterpret_cast<StepShared*>(smem_raw);
+    step_tiles<false>(S, nullptr, SingleRun{R, ntiles}, ticket, bump_step);
+}
+
+// batch form: one persistent launch over the tiles of many runs
+__global__ void __launch_bounds__(kThreads, 3) k_step_batch(const RunDev* __restrict__ runs,
+                                                            const uint2* __restrict__ items, uint32_t nitems)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    StepShared& S = *reinterpret_cast<StepShared*>(smem_raw);
+    RunDev* Rs = reinterpret_cast<RunDev*>(smem_raw + ((sizeof(StepShared) + 15) & ~(size_t)15));
+    step_tiles<true>(S, Rs, BatchRuns{runs, items, nitems}, nullptr, 0);
+}
+
+// advance the step counter of every run of a batch without Coulomb
+// collisions (the collision kernels of the others advance their own)
+__global__ void k_bump_steps(const RunDev* __restrict__ runs, uint32_t nruns)
+{
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += gridDim.x * blockDim.x)
+        if (runs[r].step && !(runs[r].flags & kFCoulomb)) *runs[r].step += 1u;
 }
 
 // Fold the packed per-step deposit into the time-summed count and charge
@@ -606,6 +668,33 @@ int step_blocks_per_sm()
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step, kThreads, smem) != cudaSuccess || b < 1) b = 1;
     return b;
+}
+
+constexpr size_t kBatchSmem = ((sizeof(StepShared) + 15) & ~(size_t)15) + sizeof(RunDev);
+
+int step_batch_blocks_per_sm()
+{
+    if (cudaFuncSetAttribute(k_step_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess)
+        return 1;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_batch, kThreads, kBatchSmem) != cudaSuccess || b < 1)
+        b = 1;
+    return b;
+}
+
+cudaError_t launch_step_batch(const RunDev* runs, const uint2* items, uint32_t nitems, int grid, cudaStream_t s)
+{
+    if (nitems > 0) {
+        if (grid > (int)nitems) grid = (int)nitems;
+        k_step_batch<<<grid, kThreads, kBatchSmem, s>>>(runs, items, nitems);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bump_steps(const RunDev* runs, uint32_t nruns, cudaStream_t s)
+{
+    if (nruns > 0) k_bump_steps<<<(nruns + 127) / 128, 128, 0, s>>>(runs, nruns);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step(const RunDev& R, uint32_t ntiles, unsigned int* ticket, int bump_step, int grid,

@@ -72,7 +72,8 @@ class DiagOut(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("sort_every", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+    _fields_ = [("sort_every", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class Profile(ctypes.Structure):
@@ -117,6 +118,31 @@ def _load():
     lib.ecris_coulomb_collide_noalloc.restype = st
     lib.ecris_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
     lib.ecris_set_tuning.restype = st
+    lib.ecris_batch_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, P, ctypes.c_size_t]
+    lib.ecris_batch_create.restype = st
+    lib.ecris_batch_destroy.argtypes = [P]
+    lib.ecris_batch_destroy.restype = None
+    lib.ecris_batch_last_error.argtypes = [P]
+    lib.ecris_batch_last_error.restype = ctypes.c_char_p
+    lib.ecris_run_bytes.argtypes = [ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int]
+    lib.ecris_run_bytes.restype = ctypes.c_size_t
+    lib.ecris_batch_add_run.argtypes = [P, ctypes.POINTER(Geometry), ctypes.POINTER(BField), ctypes.POINTER(Grid),
+                                        ctypes.POINTER(Species), ctypes.POINTER(Mcc), ctypes.c_size_t,
+                                        ctypes.POINTER(P), P, ctypes.c_double, ctypes.c_uint64, ctypes.c_double,
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]
+    lib.ecris_batch_add_run.restype = st
+    lib.ecris_batch_remove_run.argtypes = [P, ctypes.c_int32]
+    lib.ecris_batch_remove_run.restype = st
+    lib.ecris_batch_step.argtypes = [P, ctypes.c_uint32]
+    lib.ecris_batch_step.restype = st
+    lib.ecris_batch_diag.argtypes = [P, ctypes.c_int32, ctypes.POINTER(DiagOut)]
+    lib.ecris_batch_diag.restype = st
+    lib.ecris_batch_get_state.argtypes = [P, ctypes.c_int32, ctypes.POINTER(P), P, ctypes.c_int]
+    lib.ecris_batch_get_state.restype = st
+    lib.ecris_batch_memory.argtypes = [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
+    lib.ecris_batch_memory.restype = st
+    lib.ecris_batch_autotune.argtypes = [P, ctypes.c_uint32, ctypes.POINTER(Tuning)]
+    lib.ecris_batch_autotune.restype = st
     return lib
 
 
@@ -135,6 +161,17 @@ ecris_set_profiling = LIB.ecris_set_profiling
 ecris_get_profile = LIB.ecris_get_profile
 ecris_coulomb_collide_noalloc = LIB.ecris_coulomb_collide_noalloc
 ecris_set_tuning = LIB.ecris_set_tuning
+ecris_batch_create = LIB.ecris_batch_create
+ecris_batch_destroy = LIB.ecris_batch_destroy
+ecris_batch_last_error = LIB.ecris_batch_last_error
+ecris_run_bytes = LIB.ecris_run_bytes
+ecris_batch_add_run = LIB.ecris_batch_add_run
+ecris_batch_remove_run = LIB.ecris_batch_remove_run
+ecris_batch_step = LIB.ecris_batch_step
+ecris_batch_diag = LIB.ecris_batch_diag
+ecris_batch_get_state = LIB.ecris_batch_get_state
+ecris_batch_memory = LIB.ecris_batch_memory
+ecris_batch_autotune = LIB.ecris_batch_autotune
 
 
 def check(ctx, status):
@@ -163,6 +200,126 @@ def current_stream_handle():
     return torch.cuda.current_stream().cuda_stream
 
 
+def field_structs(rp, E=None, ne_cells=None):
+    """ecris_init_fields arguments for an inputs.RunParams (plus the arrays they point to)."""
+    geo = Geometry(rp.R0, rp.L, rp.r_ap, (ctypes.c_double * 3)(*rp.inlet))
+    bf = BField(rp.B_inj, rp.B_min, rp.B_ext, rp.B_hex, rp.B_ecr)
+    Eh = None if E is None else np.ascontiguousarray(E, dtype=np.float32).reshape(-1)
+    nh = None if ne_cells is None else np.ascontiguousarray(ne_cells, dtype=np.float32)
+    grid = Grid(rp.nx, rp.ny, rp.nz, _ptr(Eh), rp.ne_in_cm3, _ptr(nh), rp.ne_out_cm3,
+                rp.Te_warm_eV, rp.Te_cold_eV)
+    ip, nout = rp.species.ladder()
+    ip = np.ascontiguousarray(ip, np.float64)
+    nout = np.ascontiguousarray(nout, np.int32)
+    sp = Species(rp.species.mass_amu, rp.species.qmax, _ptr(ip), _ptr(nout))
+    mcc = Mcc(rp.n0_cm3, rp.T0_eV, rp.sigma1_cm2, rp.E_cx_eV, rp.lnL_ii, rp.lnL_ei,
+              rp.ei_charge_power, rp.flags)
+    return geo, bf, grid, sp, mcc, (Eh, nh, ip, nout)
+
+
+def _state_arrays(state):
+    arrs = [state[k] for k in ("x", "y", "z", "vx", "vy", "vz")]
+    q = state["q"]
+    dev = _is_device(arrs[0])
+    if not dev:
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in arrs]
+        q = np.ascontiguousarray(q, dtype=np.uint8)
+    return arrs, q, dev
+
+
+def _diag(qmax, ncells, fn, grids=False):
+    q1 = qmax + 1
+    ext = np.zeros(q1, np.int64)
+    lost = np.zeros(q1, np.int64)
+    alive = np.zeros(q1, np.int64)
+    cur = np.zeros(q1, np.float64)
+    cc = np.zeros(ncells, np.uint64) if grids else None
+    cq = np.zeros(ncells, np.uint64) if grids else None
+    out = DiagOut(0, 0, 0.0, _ptr(ext), _ptr(lost), _ptr(alive), _ptr(cur), 0.0, 0.0, 0, _ptr(cc), _ptr(cq))
+    fn(ctypes.byref(out))
+    d = {"steps": out.steps, "time_s": out.time_s, "extracted": ext, "lost": lost,
+         "alive_by_q": alive, "current_A": cur, "ke_lost_eV": out.ke_lost_eV,
+         "power_W": out.power_W, "coulomb_collisions": out.coulomb_collisions}
+    if grids:
+        d["cell_count"], d["cell_charge"] = cc, cq
+    return d
+
+
+def _state(n, fn):
+    arrs = [np.zeros(n, np.float32) for _ in range(6)]
+    meta = np.zeros(n, np.uint32)
+    ptrs = (ctypes.c_void_p * 6)(*[_ptr(a) for a in arrs])
+    fn(ptrs, _ptr(meta))
+    d = dict(zip(("x", "y", "z", "vx", "vy", "vz"), arrs))
+    d["meta"] = meta
+    d["q"] = (meta & 0xFF).astype(np.int32)
+    return d
+
+
+class Batch:
+    """Many runs stepped together on one GPU (ecris_batch_*)."""
+
+    def __init__(self, device=0, stream=None, hbm_budget=0):
+        self.b = ctypes.c_void_p()
+        st = ecris_batch_create(ctypes.byref(self.b), int(device), stream, int(hbm_budget))
+        if st != ECRIS_OK:
+            raise EcrisError(st, ecris_batch_last_error(None).decode())
+        self.runs = {}
+
+    def _check(self, st):
+        if st != ECRIS_OK:
+            raise EcrisError(st, ecris_batch_last_error(self.b).decode())
+
+    def close(self):
+        if self.b:
+            ecris_batch_destroy(self.b)
+            self.b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, rp, state, E=None, ne_cells=None, weight=None, seed=None, dt=None):
+        """Add a run; returns its handle."""
+        f = field_structs(rp, E, ne_cells)
+        arrs, q, dev = _state_arrays(state)
+        ptrs = (ctypes.c_void_p * 6)(*[_ptr(a) for a in arrs])
+        h = ctypes.c_int32(-1)
+        self._check(ecris_batch_add_run(self.b, *[ctypes.byref(x) for x in f[:5]], len(arrs[0]), ptrs, _ptr(q),
+                                        rp.weight if weight is None else weight,
+                                        rp.seed if seed is None else seed, rp.dt if dt is None else dt,
+                                        1 if dev else 0, ctypes.byref(h)))
+        self.runs[h.value] = (rp, len(arrs[0]))
+        return h.value
+
+    def remove(self, h):
+        self._check(ecris_batch_remove_run(self.b, int(h)))
+        self.runs.pop(h, None)
+
+    def step(self, nsteps=1):
+        self._check(ecris_batch_step(self.b, int(nsteps)))
+
+    def diag(self, h, grids=False):
+        rp, n = self.runs[h]
+        return _diag(rp.species.qmax, rp.ncells, lambda o: self._check(ecris_batch_diag(self.b, int(h), o)), grids)
+
+    def state(self, h):
+        rp, n = self.runs[h]
+        return _state(n, lambda p, m: self._check(ecris_batch_get_state(self.b, int(h), p, m, 0)))
+
+    def memory(self):
+        u, b = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        self._check(ecris_batch_memory(self.b, ctypes.byref(u), ctypes.byref(b)))
+        return u.value, b.value
+
+    def autotune(self, trial_steps=4):
+        t = Tuning()
+        self._check(ecris_batch_autotune(self.b, int(trial_steps), ctypes.byref(t)))
+        return {"sort_every": t.sort_every, "blocks_per_sm": t.blocks_per_sm}
+
+
 class Run:
     """One ECRIS run on one GPU: fields, particles, steps and diagnostics."""
 
@@ -187,20 +344,8 @@ class Run:
             pass
 
     def init_fields(self, rp, E=None, ne_cells=None):
-        geo = Geometry(rp.R0, rp.L, rp.r_ap, (ctypes.c_double * 3)(*rp.inlet))
-        bf = BField(rp.B_inj, rp.B_min, rp.B_ext, rp.B_hex, rp.B_ecr)
-        Eh = None if E is None else np.ascontiguousarray(E, dtype=np.float32).reshape(-1)
-        nh = None if ne_cells is None else np.ascontiguousarray(ne_cells, dtype=np.float32)
-        grid = Grid(rp.nx, rp.ny, rp.nz, _ptr(Eh), rp.ne_in_cm3, _ptr(nh), rp.ne_out_cm3,
-                    rp.Te_warm_eV, rp.Te_cold_eV)
-        ip, nout = rp.species.ladder()
-        ip = np.ascontiguousarray(ip, np.float64)
-        nout = np.ascontiguousarray(nout, np.int32)
-        sp = Species(rp.species.mass_amu, rp.species.qmax, _ptr(ip), _ptr(nout))
-        mcc = Mcc(rp.n0_cm3, rp.T0_eV, rp.sigma1_cm2, rp.E_cx_eV, rp.lnL_ii, rp.lnL_ei,
-                  rp.ei_charge_power, rp.flags)
-        check(self.ctx, ecris_init_fields(self.ctx, ctypes.byref(geo), ctypes.byref(bf),
-                                          ctypes.byref(grid), ctypes.byref(sp), ctypes.byref(mcc)))
+        f = field_structs(rp, E, ne_cells)
+        check(self.ctx, ecris_init_fields(self.ctx, *[ctypes.byref(x) for x in f[:5]]))
         self.ncells = rp.nx * rp.ny * rp.nz
         self.qmax = rp.species.qmax
 
@@ -225,33 +370,10 @@ class Run:
         check(self.ctx, ecris_step(self.ctx, int(nsteps), self.rp.dt if dt is None else dt))
 
     def diag(self, grids=False):
-        q1 = self.qmax + 1
-        ext = np.zeros(q1, np.int64)
-        lost = np.zeros(q1, np.int64)
-        alive = np.zeros(q1, np.int64)
-        cur = np.zeros(q1, np.float64)
-        cc = np.zeros(self.ncells, np.uint64) if grids else None
-        cq = np.zeros(self.ncells, np.uint64) if grids else None
-        out = DiagOut(0, 0, 0.0, _ptr(ext), _ptr(lost), _ptr(alive), _ptr(cur), 0.0, 0.0, 0,
-                      _ptr(cc), _ptr(cq))
-        check(self.ctx, ecris_diag(self.ctx, ctypes.byref(out)))
-        d = {"steps": out.steps, "time_s": out.time_s, "extracted": ext, "lost": lost,
-             "alive_by_q": alive, "current_A": cur, "ke_lost_eV": out.ke_lost_eV,
-             "power_W": out.power_W, "coulomb_collisions": out.coulomb_collisions}
-        if grids:
-            d["cell_count"], d["cell_charge"] = cc, cq
-        return d
+        return _diag(self.qmax, self.ncells, lambda o: check(self.ctx, ecris_diag(self.ctx, o)), grids)
 
     def state(self):
-        n = self.n
-        arrs = [np.zeros(n, np.float32) for _ in range(6)]
-        meta = np.zeros(n, np.uint32)
-        ptrs = (ctypes.c_void_p * 6)(*[_ptr(a) for a in arrs])
-        check(self.ctx, ecris_get_state(self.ctx, ptrs, _ptr(meta), 0))
-        d = dict(zip(("x", "y", "z", "vx", "vy", "vz"), arrs))
-        d["meta"] = meta
-        d["q"] = (meta & 0xFF).astype(np.int32)
-        return d
+        return _state(self.n, lambda p, m: check(self.ctx, ecris_get_state(self.ctx, p, m, 0)))
 
     def set_tuning(self, sort_every=32):
         t = Tuning()
