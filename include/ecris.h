@@ -279,6 +279,75 @@ ecris_status ecris_batch_memory(const ecris_batch* b, size_t* used, size_t* budg
  * trial steps are real steps of every run; no result depends on the choice. */
 ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tuning* chosen);
 
+/* ------------------------------------------------------------------------ */
+/* Served form: a request loop (a library thread) that keeps a batch on the  */
+/* device and admits submitted runs as slots and memory free up (continuous  */
+/* batching).  A run is stepped until its extracted currents converge (Sec.  */
+/* II: the model's results hold for the stationary state of the source) or  */
+/* a step cap, then retired.  The rule is checked                            */
+/* at multiples of window_steps of the run's own steps, so a run's result    */
+/* does not depend on what else is being served.                             */
+/* ------------------------------------------------------------------------ */
+typedef struct ecris_server ecris_server;
+
+/* A run to serve: the arguments of ecris_init_fields / ecris_load_ions (host
+ * memory; everything is copied at submission) and the convergence rule.
+ * Converged: over two consecutive windows the total extracted current and
+ * the currents of the three strongest charge states each change by less
+ * than rel_tol times the larger of the two values, with at least
+ * min_events extractions in the window. */
+typedef struct {
+    ecris_geometry geo;
+    ecris_bfield bf;
+    ecris_grid grid;
+    ecris_species sp;
+    ecris_mcc mcc;
+    size_t n;
+    const float* xyzv[6];
+    const uint8_t* q;
+    double weight;
+    uint64_t seed;
+    double dt;
+    uint32_t window_steps;  /* must divide by the server's steps per tick */
+    double rel_tol;
+    int64_t min_events;
+    uint32_t max_steps;     /* a multiple of window_steps */
+} ecris_request;
+
+enum { ECRIS_REQ_QUEUED = 0, ECRIS_REQ_RUNNING = 1, ECRIS_REQ_DONE = 2, ECRIS_REQ_FAILED = 3 };
+
+typedef struct {
+    int32_t state;          /* ECRIS_REQ_* */
+    int32_t converged;      /* 1: rule met before max_steps */
+    uint64_t steps;
+    double t_submit, t_admit, t_done;   /* s, the server's monotonic clock */
+    int32_t qmax;
+    int64_t extracted[64];  /* cumulative, per Q */
+    int64_t lost[64];
+    double current_A[64];   /* over the last window */
+    double power_W;
+    double ke_lost_eV;
+    char error[128];
+} ecris_result;
+
+/* Start a server on `device`: memory budget for resident runs (0: none),
+ * steps per tick (the batch advances this many steps between admissions and
+ * checks), and the most runs served at once (0: no limit). */
+ecris_status ecris_server_create(ecris_server** out, int device, size_t hbm_budget_bytes, uint32_t steps_per_tick,
+                                 uint32_t max_active);
+/* Stop the loop (runs in flight are abandoned) and release everything. */
+void ecris_server_destroy(ecris_server* s);
+const char* ecris_server_last_error(const ecris_server* s);
+/* Queue a request (thread-safe); *ticket receives its handle.  A request that
+ * cannot fit the budget even alone is rejected with ECRIS_ENOMEM. */
+ecris_status ecris_server_submit(ecris_server* s, const ecris_request* req, int64_t* ticket);
+/* Current state and, once done, the result of a request (thread-safe). */
+ecris_status ecris_server_poll(ecris_server* s, int64_t ticket, ecris_result* out);
+/* Seconds on the server's clock, and counters: requests queued, running,
+ * done; ion-steps advanced since start. */
+ecris_status ecris_server_stats(ecris_server* s, double* now, int64_t* queued, int64_t* running, int64_t* done,
+                                double* ion_steps);
+
 /* Allocation-free Coulomb collision step.  The paper has no counterpart: this
  * is an interface for callers that cannot allocate device memory when they
  * need a collision step -- hosts that reserve all device memory up front and

@@ -192,7 +192,7 @@ static double or_dz(const or_params *p) { return p->L / p->nz; }
 
 static int or_clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-/* nearest-grid-point cell of a position ("in the given computational cell") */
+/* nearest-grid-point cell of a position: the cell whose plasma parameters act on the particle */
 static int64_t or_cell(const or_params *p, double x, double y, double z, uint32_t *guard)
 {
     double gx = (x + p->R0) / or_dx(p), gy = (y + p->R0) / or_dy(p), gz = z / or_dz(p);

@@ -1,0 +1,359 @@
+// Served form of the ECRIS ion time step: a request loop that keeps one batch
+// of runs resident on the device and admits queued runs as slots and memory
+// free up (continuous batching).  Host code only: it drives the batch through
+// the public C ABI.
+//
+// The loop, on its own thread:
+//   1. admit queued requests in arrival order while the batch's memory
+//      budget and the slot limit allow (a request that does not fit waits, and
+//      the ones behind it wait too, so arrival order is kept);
+//   2. advance the batch by steps_per_tick steps (one graph replay per step);
+//   3. for every run whose own step count reached a multiple of its window,
+//      read its diagnostics and apply the convergence rule (stationary
+//      extracted currents, Sec. II) or the step cap; retire finished runs,
+//      which frees their memory for the queue.
+// Because the rule only looks at a run's own counters at its own window
+// boundaries, and a run in a batch evolves exactly as it does alone, the
+// result of a request does not depend on what else is being served.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/ecris.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// a request with every pointer replaced by owned copies
+struct OwnedRequest {
+    ecris_request r;
+    std::vector<float> E, ne_cells, xyzv[6];
+    std::vector<double> ip;
+    std::vector<int32_t> nout;
+    std::vector<uint8_t> q;
+};
+
+struct Served {
+    int64_t ticket = 0;
+    std::unique_ptr<OwnedRequest> req;
+    ecris_result res;
+    int32_t run = -1;
+    std::vector<int64_t> last_ext;   // extracted counts at the previous window boundary
+    std::vector<double> last_cur;    // currents of the previous window
+    bool have_prev = false;
+};
+
+}  // namespace
+
+struct ecris_server {
+    int device = 0;
+    ecris_batch* batch = nullptr;
+    size_t budget = 0;
+    uint32_t steps_per_tick = 1;
+    uint32_t max_active = 0;
+    Clock::time_point t0;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stop = false;
+    std::string err;
+    std::deque<Served*> queue;
+    std::vector<Served*> active;
+    std::map<int64_t, std::unique_ptr<Served>> all;
+    int64_t next_ticket = 1;
+    int64_t n_done = 0;
+    double ion_steps = 0.0;
+    std::thread loop;
+};
+
+namespace {
+
+double now_s(const ecris_server* s)
+{
+    return std::chrono::duration<double>(Clock::now() - s->t0).count();
+}
+
+void finish(ecris_server* s, Served* v, int32_t state, const char* msg)
+{
+    v->res.state = state;
+    v->res.t_done = now_s(s);
+    if (msg) std::strncpy(v->res.error, msg, sizeof v->res.error - 1);
+}
+
+// read a run's diagnostics into its result; returns false on failure
+bool read_diag(ecris_server* s, Served* v, std::vector<int64_t>& ext)
+{
+    const int q1 = v->req->r.sp.qmax + 1;
+    ext.assign(q1, 0);
+    std::vector<int64_t> lost(q1, 0);
+    std::vector<double> cur(q1, 0.0);
+    ecris_diag_out d;
+    std::memset(&d, 0, sizeof d);
+    d.extracted = ext.data();
+    d.lost = lost.data();
+    d.current_A = cur.data();
+    if (ecris_batch_diag(s->batch, v->run, &d) != ECRIS_OK) return false;
+    v->res.steps = d.steps;
+    v->res.qmax = d.qmax;
+    v->res.power_W = d.power_W;
+    v->res.ke_lost_eV = d.ke_lost_eV;
+    for (int q = 0; q < q1 && q < 64; ++q) {
+        v->res.extracted[q] = ext[q];
+        v->res.lost[q] = lost[q];
+    }
+    return true;
+}
+
+// the convergence rule at a window boundary
+bool converged(Served* v, const std::vector<int64_t>& ext)
+{
+    const ecris_request& r = v->req->r;
+    const int q1 = r.sp.qmax + 1;
+    std::vector<double> cur(q1, 0.0);
+    int64_t events = 0;
+    const double window_s = r.window_steps * r.dt;
+    for (int q = 0; q < q1; ++q) {
+        const int64_t dn = ext[q] - (v->last_ext.empty() ? 0 : v->last_ext[q]);
+        events += dn;
+        cur[q] = q * 1.602176634e-19 * r.weight * (double)dn / window_s;
+    }
+    for (int q = 0; q < q1 && q < 64; ++q) v->res.current_A[q] = cur[q];
+    bool ok = false;
+    if (v->have_prev && events >= r.min_events) {
+        // relative change against the larger of the two (two zero currents agree)
+        auto rel = [&](double a, double b) { return std::abs(a - b) <= r.rel_tol * std::max(std::abs(a), std::abs(b)); };
+        double tot = 0.0, tot_prev = 0.0;
+        for (int q = 0; q < q1; ++q) {
+            tot += cur[q];
+            tot_prev += v->last_cur[q];
+        }
+        ok = rel(tot, tot_prev);
+        std::vector<int> order(q1);
+        for (int q = 0; q < q1; ++q) order[q] = q;
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return cur[a] > cur[b]; });
+        for (int k = 0; k < 3 && k < q1 && ok; ++k) ok = rel(cur[order[k]], v->last_cur[order[k]]);
+    }
+    v->last_ext = ext;
+    v->last_cur = cur;
+    v->have_prev = true;
+    return ok;
+}
+
+void serve_loop(ecris_server* s)
+{
+    cudaSetDevice(s->device);
+    std::vector<int64_t> ext;
+    for (;;) {
+        // 1. admission, in arrival order
+        std::vector<Served*> admit;
+        {
+            std::unique_lock<std::mutex> lock(s->mu);
+            if (s->stop) break;
+            if (s->active.empty() && s->queue.empty()) {
+                s->cv.wait_for(lock, std::chrono::milliseconds(20));
+                continue;
+            }
+            size_t used = 0, budget = 0;
+            ecris_batch_memory(s->batch, &used, &budget);
+            while (!s->queue.empty()) {
+                Served* v = s->queue.front();
+                const ecris_request& r = v->req->r;
+                const size_t need = ecris_run_bytes(r.n, r.grid.nx, r.grid.ny, r.grid.nz, (r.mcc.flags & ECRIS_F_COULOMB) != 0);
+                if (budget && used + need > budget) break;
+                if (s->max_active && s->active.size() + admit.size() >= s->max_active) break;
+                used += need;
+                admit.push_back(v);
+                s->queue.pop_front();
+            }
+        }
+        for (Served* v : admit) {
+            const ecris_request& r = v->req->r;
+            const ecris_status st = ecris_batch_add_run(s->batch, &r.geo, &r.bf, &r.grid, &r.sp, &r.mcc, r.n, r.xyzv,
+                                                        r.q, r.weight, r.seed, r.dt, 0, &v->run);
+            std::lock_guard<std::mutex> lock(s->mu);
+            if (st != ECRIS_OK) {
+                finish(s, v, ECRIS_REQ_FAILED, ecris_batch_last_error(s->batch));
+                ++s->n_done;
+                continue;
+            }
+            v->res.state = ECRIS_REQ_RUNNING;
+            v->res.t_admit = now_s(s);
+            s->active.push_back(v);
+        }
+        if (s->active.empty()) continue;
+        // 2. one tick of the whole batch
+        if (ecris_batch_step(s->batch, s->steps_per_tick) != ECRIS_OK) {
+            std::lock_guard<std::mutex> lock(s->mu);
+            s->err = ecris_batch_last_error(s->batch);
+            for (Served* v : s->active) finish(s, v, ECRIS_REQ_FAILED, s->err.c_str());
+            s->n_done += (int64_t)s->active.size();
+            s->active.clear();
+            continue;
+        }
+        // 3. window boundaries: convergence or cap; retire finished runs
+        std::vector<Served*> keep;
+        double advanced = 0.0;
+        for (Served* v : s->active) {
+            const ecris_request& r = v->req->r;
+            v->res.steps += s->steps_per_tick;
+            advanced += (double)r.n * s->steps_per_tick;
+            if (v->res.steps % r.window_steps != 0) {
+                keep.push_back(v);
+                continue;
+            }
+            const bool ok_diag = read_diag(s, v, ext);
+            const bool conv = ok_diag && converged(v, ext);
+            const bool cap = v->res.steps >= r.max_steps;
+            if (ok_diag && !conv && !cap) {
+                keep.push_back(v);
+                continue;
+            }
+            ecris_batch_remove_run(s->batch, v->run);
+            std::lock_guard<std::mutex> lock(s->mu);
+            v->res.converged = conv ? 1 : 0;
+            finish(s, v, ok_diag ? ECRIS_REQ_DONE : ECRIS_REQ_FAILED,
+                   ok_diag ? nullptr : ecris_batch_last_error(s->batch));
+            v->req.reset();   // the host copy of the inputs is no longer needed
+            ++s->n_done;
+        }
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->active.swap(keep);
+        s->ion_steps += advanced;
+    }
+}
+
+template <class T>
+void own(std::vector<T>& dst, const T* src, size_t n)
+{
+    if (src) dst.assign(src, src + n);
+    else dst.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+ecris_status ecris_server_create(ecris_server** out, int device, size_t hbm_budget_bytes, uint32_t steps_per_tick,
+                                 uint32_t max_active)
+{
+    if (!out || steps_per_tick == 0) return ECRIS_EINVAL;
+    *out = nullptr;
+    ecris_server* s = new (std::nothrow) ecris_server();
+    if (!s) return ECRIS_ENOMEM;
+    s->device = device;
+    s->budget = hbm_budget_bytes;
+    s->steps_per_tick = steps_per_tick;
+    s->max_active = max_active;
+    const ecris_status st = ecris_batch_create(&s->batch, device, nullptr, hbm_budget_bytes);
+    if (st != ECRIS_OK) {
+        delete s;
+        return st;
+    }
+    s->t0 = Clock::now();
+    s->loop = std::thread(serve_loop, s);
+    *out = s;
+    return ECRIS_OK;
+}
+
+void ecris_server_destroy(ecris_server* s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->loop.joinable()) s->loop.join();
+    ecris_batch_destroy(s->batch);
+    delete s;
+}
+
+const char* ecris_server_last_error(const ecris_server* s)
+{
+    return s ? s->err.c_str() : "";
+}
+
+ecris_status ecris_server_submit(ecris_server* s, const ecris_request* req, int64_t* ticket)
+{
+    if (!s) return ECRIS_EINVAL;
+    auto fail = [s](ecris_status st, const char* msg) {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->err = msg;
+        return st;
+    };
+    if (!req || !ticket) return fail(ECRIS_EINVAL, "server_submit: NULL argument");
+    const ecris_request& r = *req;
+    if (r.window_steps == 0 || r.window_steps % s->steps_per_tick != 0 || r.max_steps == 0 ||
+        r.max_steps % r.window_steps != 0 || !(r.dt > 0.0) || !(r.rel_tol > 0.0) || r.sp.qmax < 1 ||
+        r.sp.qmax > 63 || r.grid.nx < 2 || r.grid.ny < 2 || r.grid.nz < 2)
+        return fail(ECRIS_EINVAL, "server_submit: need window_steps a multiple of steps_per_tick, max_steps a "
+                                  "multiple of window_steps, dt > 0, rel_tol > 0 and a valid species and mesh");
+    if (r.n && (!r.q || !r.xyzv[0] || !r.xyzv[1] || !r.xyzv[2] || !r.xyzv[3] || !r.xyzv[4] || !r.xyzv[5]))
+        return fail(ECRIS_EINVAL, "server_submit: NULL particle array");
+    const size_t need = ecris_run_bytes(r.n, r.grid.nx, r.grid.ny, r.grid.nz, (r.mcc.flags & ECRIS_F_COULOMB) != 0);
+    if (s->budget && need > s->budget) return fail(ECRIS_ENOMEM, "server_submit: the run alone exceeds the memory budget");
+    auto v = std::make_unique<Served>();
+    auto o = std::make_unique<OwnedRequest>();
+    o->r = r;
+    const size_t nc = (size_t)r.grid.nx * r.grid.ny * r.grid.nz;
+    own(o->E, r.grid.E, 3 * nc);
+    own(o->ne_cells, r.grid.ne_in_cells, nc);
+    own(o->ip, r.sp.ip_eV, (size_t)r.sp.qmax);
+    own(o->nout, r.sp.n_outer, (size_t)r.sp.qmax);
+    own(o->q, r.q, r.n);
+    for (int k = 0; k < 6; ++k) own(o->xyzv[k], r.xyzv[k], r.n);
+    o->r.grid.E = r.grid.E ? o->E.data() : nullptr;
+    o->r.grid.ne_in_cells = r.grid.ne_in_cells ? o->ne_cells.data() : nullptr;
+    o->r.sp.ip_eV = o->ip.data();
+    o->r.sp.n_outer = o->nout.data();
+    o->r.q = o->q.data();
+    for (int k = 0; k < 6; ++k) o->r.xyzv[k] = o->xyzv[k].data();
+    v->req = std::move(o);
+    std::memset(&v->res, 0, sizeof v->res);
+    v->res.state = ECRIS_REQ_QUEUED;
+    std::lock_guard<std::mutex> lock(s->mu);
+    v->ticket = s->next_ticket++;
+    v->res.t_submit = now_s(s);
+    *ticket = v->ticket;
+    s->queue.push_back(v.get());
+    s->all[v->ticket] = std::move(v);
+    s->cv.notify_all();
+    return ECRIS_OK;
+}
+
+ecris_status ecris_server_poll(ecris_server* s, int64_t ticket, ecris_result* out)
+{
+    if (!s || !out) return ECRIS_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) {
+        s->err = "server_poll: unknown ticket";
+        return ECRIS_EINVAL;
+    }
+    *out = it->second->res;
+    return ECRIS_OK;
+}
+
+ecris_status ecris_server_stats(ecris_server* s, double* now, int64_t* queued, int64_t* running, int64_t* done,
+                                double* ion_steps)
+{
+    if (!s) return ECRIS_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (now) *now = now_s(s);
+    if (queued) *queued = (int64_t)s->queue.size();
+    if (running) *running = (int64_t)s->active.size();
+    if (done) *done = s->n_done;
+    if (ion_steps) *ion_steps = s->ion_steps;
+    return ECRIS_OK;
+}
+
+}  // extern "C"

@@ -76,6 +76,25 @@ class Tuning(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 6)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("geo", Geometry), ("bf", BField), ("grid", Grid), ("sp", Species), ("mcc", Mcc),
+                ("n", ctypes.c_size_t), ("xyzv", ctypes.c_void_p * 6), ("q", ctypes.c_void_p),
+                ("weight", ctypes.c_double), ("seed", ctypes.c_uint64), ("dt", ctypes.c_double),
+                ("window_steps", ctypes.c_uint32), ("rel_tol", ctypes.c_double),
+                ("min_events", ctypes.c_int64), ("max_steps", ctypes.c_uint32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("converged", ctypes.c_int32), ("steps", ctypes.c_uint64),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("qmax", ctypes.c_int32), ("extracted", ctypes.c_int64 * 64), ("lost", ctypes.c_int64 * 64),
+                ("current_A", ctypes.c_double * 64), ("power_W", ctypes.c_double),
+                ("ke_lost_eV", ctypes.c_double), ("error", ctypes.c_char * 128)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("step_launches", ctypes.c_int64), ("step_ms", ctypes.c_double),
                 ("coulomb_launches", ctypes.c_int64), ("coulomb_ms", ctypes.c_double),
@@ -143,6 +162,21 @@ def _load():
     lib.ecris_batch_memory.restype = st
     lib.ecris_batch_autotune.argtypes = [P, ctypes.c_uint32, ctypes.POINTER(Tuning)]
     lib.ecris_batch_autotune.restype = st
+    lib.ecris_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_size_t, ctypes.c_uint32,
+                                        ctypes.c_uint32]
+    lib.ecris_server_create.restype = st
+    lib.ecris_server_destroy.argtypes = [P]
+    lib.ecris_server_destroy.restype = None
+    lib.ecris_server_last_error.argtypes = [P]
+    lib.ecris_server_last_error.restype = ctypes.c_char_p
+    lib.ecris_server_submit.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int64)]
+    lib.ecris_server_submit.restype = st
+    lib.ecris_server_poll.argtypes = [P, ctypes.c_int64, ctypes.POINTER(Result)]
+    lib.ecris_server_poll.restype = st
+    d = ctypes.POINTER(ctypes.c_double)
+    i64 = ctypes.POINTER(ctypes.c_int64)
+    lib.ecris_server_stats.argtypes = [P, d, i64, i64, i64, d]
+    lib.ecris_server_stats.restype = st
     return lib
 
 
@@ -172,6 +206,12 @@ ecris_batch_diag = LIB.ecris_batch_diag
 ecris_batch_get_state = LIB.ecris_batch_get_state
 ecris_batch_memory = LIB.ecris_batch_memory
 ecris_batch_autotune = LIB.ecris_batch_autotune
+ecris_server_create = LIB.ecris_server_create
+ecris_server_destroy = LIB.ecris_server_destroy
+ecris_server_last_error = LIB.ecris_server_last_error
+ecris_server_submit = LIB.ecris_server_submit
+ecris_server_poll = LIB.ecris_server_poll
+ecris_server_stats = LIB.ecris_server_stats
 
 
 def check(ctx, status):
@@ -318,6 +358,71 @@ class Batch:
         t = Tuning()
         self._check(ecris_batch_autotune(self.b, int(trial_steps), ctypes.byref(t)))
         return {"sort_every": t.sort_every, "blocks_per_sm": t.blocks_per_sm}
+
+
+class Server:
+    """The served form (ecris_server_*): submit runs, poll their results."""
+
+    def __init__(self, device=0, hbm_budget=0, steps_per_tick=32, max_active=0):
+        self.s = ctypes.c_void_p()
+        st = ecris_server_create(ctypes.byref(self.s), int(device), int(hbm_budget), int(steps_per_tick),
+                                 int(max_active))
+        if st != ECRIS_OK:
+            raise EcrisError(st, "server_create failed")
+
+    def close(self):
+        if self.s:
+            ecris_server_destroy(self.s)
+            self.s = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, rp, state, E=None, ne_cells=None, window_steps=256, rel_tol=0.02, min_events=400,
+               max_steps=4096, weight=None, seed=None, dt=None):
+        f = field_structs(rp, E, ne_cells)
+        arrs, q, dev = _state_arrays(state)
+        if dev:
+            raise ValueError("the server copies host arrays; pass numpy arrays")
+        r = Request()
+        r.geo, r.bf, r.grid, r.sp, r.mcc = f[:5]
+        r.n = len(arrs[0])
+        for k in range(6):
+            r.xyzv[k] = _ptr(arrs[k])
+        r.q = _ptr(q)
+        r.weight = rp.weight if weight is None else weight
+        r.seed = rp.seed if seed is None else seed
+        r.dt = rp.dt if dt is None else dt
+        r.window_steps, r.rel_tol, r.min_events, r.max_steps = window_steps, rel_tol, min_events, max_steps
+        t = ctypes.c_int64(0)
+        st = ecris_server_submit(self.s, ctypes.byref(r), ctypes.byref(t))
+        if st != ECRIS_OK:
+            raise EcrisError(st, ecris_server_last_error(self.s).decode())
+        return t.value
+
+    def poll(self, ticket):
+        res = Result()
+        st = ecris_server_poll(self.s, int(ticket), ctypes.byref(res))
+        if st != ECRIS_OK:
+            raise EcrisError(st, ecris_server_last_error(self.s).decode())
+        q1 = res.qmax + 1
+        return {"state": res.state, "converged": bool(res.converged), "steps": res.steps,
+                "t_submit": res.t_submit, "t_admit": res.t_admit, "t_done": res.t_done,
+                "extracted": np.array(res.extracted[:q1]), "lost": np.array(res.lost[:q1]),
+                "current_A": np.array(res.current_A[:q1]), "power_W": res.power_W,
+                "ke_lost_eV": res.ke_lost_eV, "error": res.error.decode()}
+
+    def stats(self):
+        now = ctypes.c_double()
+        qd, rn, dn = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        ist = ctypes.c_double()
+        ecris_server_stats(self.s, ctypes.byref(now), ctypes.byref(qd), ctypes.byref(rn), ctypes.byref(dn),
+                           ctypes.byref(ist))
+        return {"now": now.value, "queued": qd.value, "running": rn.value, "done": dn.value,
+                "ion_steps": ist.value}
 
 
 class Run:
