@@ -6,6 +6,11 @@ density 1e10 cm^-3, every process of the step on.  Inputs are synthetic
 (seeded generators); a "step" is one time step of the whole hot path over all
 particles.  L2 is flushed (a 512 MB write) between timed steps.
 
+On one GPU the line also carries the batched form (a 64-run oxygen gas-flow
+scan in one persistent kernel and graph, beside the same runs stepped one at a
+time) and the served form (a Poisson request stream of O/Ar/Kr runs: scans/s,
+p50/p99 time to converged currents).
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 With N > 1 (launched by torch.distributed.run) every rank runs an independent
@@ -194,6 +199,157 @@ def run_reference(args, rank, world):
     return 0
 
 
+def _percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q
+    lo = int(math.floor(k))
+    hi = min(lo + 1, len(xs) - 1)
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+def bench_batched(E, I, args, local, stream, flush, peak, peak_kind):
+    """The batched gas-flow scan: oxygen runs (n0 log-spaced 3e9-3e11 cm^-3, N
+    log-uniform 2e5-2e6) advanced together by the persistent batched step
+    kernel, replayed as one CUDA graph per step, launch shape autotuned.
+    Reported beside the plain single-run form of the same runs."""
+    import torch
+    wls = [I.config_oxygen_scan(i) for i in range(args.batch_runs)]
+    states = [I.make_particles(wl) for wl in wls]
+    total = sum(wl.n for wl in wls)
+    b = E.Batch(device=local, stream=stream.cuda_stream)
+    for wl, st in zip(wls, states):
+        b.add(wl.params, st)
+    tune = b.autotune(trial_steps=4)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.batch_steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.batch_steps)]
+    for k in range(args.batch_steps):
+        flush.zero_()
+        starts[k].record(stream)
+        b.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    value = total * args.batch_steps / (ms * 1e-3)
+    # the batched step kernel alone (profiling launches the step's kernels one by one)
+    b.set_profiling(True)
+    nprof = min(args.batch_steps, 20)
+    for _ in range(nprof):
+        flush.zero_()
+        b.step(1)
+    prof = b.profile()
+    b.set_profiling(False)
+    b.close()
+    k_ms = prof["step_ms"] / max(1, prof["step_launches"])
+    algo = total * ALGO_BYTES_STEP_KERNEL
+    achieved = algo / (k_ms * 1e-3) / 1e9
+    # the plain single-run form: the first runs of the scan, one at a time
+    plain_ion_steps, plain_ms = 0, 0.0
+    for wl, st in list(zip(wls, states))[: args.plain_runs]:
+        run = E.Run(wl.params, device=local, stream=stream.cuda_stream)
+        run.load(st)
+        run.step(args.warmup)
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t = 0.0
+        for _ in range(20):
+            flush.zero_()
+            a.record(stream)
+            run.step(1)
+            z.record(stream)
+            z.synchronize()
+            t += a.elapsed_time(z)
+        plain_ion_steps += wl.n * 20
+        plain_ms += t
+        run.close()
+    plain = plain_ion_steps / (plain_ms * 1e-3) if plain_ms > 0 else None
+    return {
+        "workload": f"oxygen gas-flow scan, {len(wls)} runs, N log-uniform 2e5-2e6, n0 3e9-3e11 cm^-3, "
+                    "32x32x64 mesh, collisions between ions off",
+        "runs": len(wls), "particles": total, "steps": args.batch_steps,
+        "value": value, "unit": "ion-steps/s", "ms_per_step": ms / args.batch_steps,
+        "tuning": tune,
+        "roofline": {"bound": "hbm", "kernel": "k_step_batch", "achieved": achieved, "peak": peak,
+                     "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "algorithmic_bytes_per_launch": algo, "kernel_ms": k_ms, "traffic": None,
+                     "share_of_step": prof["step_ms"] / max(1e-9, prof["step_ms"] + prof["coulomb_ms"]
+                                                            + prof["other_ms"])},
+        "plain_single_run": {"value": plain, "unit": "ion-steps/s",
+                             "runs": min(args.plain_runs, len(wls)),
+                             "note": "the first runs of the scan stepped one at a time through ecris_step"},
+        "gpu_launches_per_step": (prof["step_launches"] + prof["coulomb_launches"] + prof["other_launches"])
+                                 / nprof,
+        "l2": "flushed between timed steps (512 MB write)",
+    }
+
+
+def bench_served(E, I, args, local):
+    """The served request stream: Poisson arrivals of O/Ar/Kr scan runs
+    submitted from host memory to the request loop, which keeps every admitted
+    run resident and steps them together; latency is submission to converged
+    currents (or the step cap)."""
+    import numpy as np
+    stream_reqs = I.served_stream(seed=5, rate_per_s=args.serve_rate, duration_s=args.serve_seconds)
+    if not stream_reqs:
+        return None
+    # one pool of initial states per species; a request takes a prefix of it
+    pools = {}
+    for _, wl in stream_reqs:
+        sp = wl.params.species.name
+        if sp not in pools or pools[sp].n < wl.n:
+            pools[sp] = wl
+    pool_states = {}
+    for sp, wl in pools.items():
+        pool_states[sp] = I.make_particles(I.Workload(wl.name, wl.params, n=wl.n, steps=0, atom_fraction=0.75,
+                                                      ion_qmax_init=wl.ion_qmax_init, atoms_fill_chamber=True),
+                                           seed=5)
+    srv = E.Server(device=local, hbm_budget=int(args.serve_budget_gb * 2**30), steps_per_tick=32)
+    tickets = []
+    t0 = time.perf_counter()
+    for at, wl in stream_reqs:
+        st = {k: v[: wl.n] for k, v in pool_states[wl.params.species.name].items()}
+        delay = at - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append((srv.submit(wl.params, st, window_steps=256, rel_tol=0.02, min_events=400,
+                                   max_steps=4096), wl))
+    limit = time.perf_counter() + args.serve_limit_s
+    while True:
+        res = [(srv.poll(t), wl) for t, wl in tickets]
+        if all(r["state"] >= 2 for r, _ in res):
+            break
+        if time.perf_counter() > limit:
+            srv.close()
+            return {"error": f"served stream not finished within {args.serve_limit_s} s"}
+        time.sleep(0.02)
+    stats = srv.stats()
+    srv.close()
+    done = [(r, wl) for r, wl in res if r["state"] == 2]
+    lat = [r["t_done"] - r["t_submit"] for r, _ in done]
+    first = min(r["t_submit"] for r, _ in res)
+    last = max(r["t_done"] for r, _ in res)
+    span = max(1e-9, last - first)
+    ion_steps = sum(wl.n * r["steps"] for r, wl in done)
+    offered = ion_steps / args.serve_seconds
+    return {
+        "workload": f"Poisson arrivals at {args.serve_rate}/s for {args.serve_seconds} s; O/Ar/Kr; "
+                    "N log-uniform 1e4-8e6; meshes 32x32x64/64x64x128/96x96x192; every process on",
+        "requests": len(res), "done": len(done), "failed": len(res) - len(done),
+        "converged": sum(1 for r, _ in done if r["converged"]),
+        "scans_per_s": len(done) / span, "p50_s": _percentile(lat, 0.5), "p99_s": _percentile(lat, 0.99),
+        "ion_steps_per_s": ion_steps / span, "makespan_s": span,
+        "offered_ion_steps_per_s": offered, "load_factor": offered / max(1e-9, ion_steps / span),
+        "server_ion_steps": stats["ion_steps"],
+        "rule": "2 % change of total and top-3 Q currents between 256-step windows with >= 400 extractions, "
+                "cap 4096 steps",
+        "hbm_budget_gb": args.serve_budget_gb,
+    }
+
+
 def workload_config(wl, coulomb):
     p = wl.params
     return {"workload": wl.name, "species": p.species.name, "particles": wl.n,
@@ -212,6 +368,15 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=50_000)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-runs", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=100)
+    ap.add_argument("--plain-runs", type=int, default=8)
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--serve-limit-s", type=float, default=300.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -331,9 +496,15 @@ def main():
         "clocks": clocks,
         "step_ms_median": statistics.median(step_ms),
     }
+    run.close()
+    del pinned
+    # the batched and served forms on one GPU (replica runs at N > 1 time the plain form only)
+    if not args.no_batched and world == 1:
+        line["batched"] = bench_batched(E, I, args, local, stream, flush, peak, peak_kind)
+    if not args.no_served and world == 1:
+        line["served"] = bench_served(E, I, args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
-    run.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -273,6 +273,12 @@ ecris_status ecris_batch_get_state(ecris_batch* b, int32_t run, float* const xyz
                                    int dst_is_device);
 /* Bytes held by the batch's runs and its budget (0: none). */
 ecris_status ecris_batch_memory(const ecris_batch* b, size_t* used, size_t* budget);
+/* Kernel timing for a batch, as ecris_set_profiling / ecris_get_profile:
+ * with profiling on, every step launches its kernels one by one (no graph)
+ * between events; step_* is the batched step kernel, coulomb_* the collision
+ * kernels of all runs, other_* sorts, deposit folds and step counters. */
+ecris_status ecris_batch_set_profiling(ecris_batch* b, int enable);
+ecris_status ecris_batch_get_profile(ecris_batch* b, ecris_profile* out);
 /* Launch-shape autotuner: times `trial_steps` steps of the batch for each
  * candidate (resident step-kernel blocks per SM, steps between particle
  * sorts), keeps the fastest and returns it in *chosen (may be NULL).  The

@@ -135,6 +135,95 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
 void ecris::ecris_internal_set_thread_error(const char* msg) { g_create_error = msg; }
 
+namespace {
+
+enum { kKindStep = 0, kKindCoulomb = 1, kKindOther = 2 };
+
+// kernel timing (ecris_set_profiling / ecris_batch_set_profiling): launches
+// bracketed by events on the launching stream, read back when collected
+struct KernelTimer {
+    bool on = false;
+    struct Timed { int kind; int kernels; cudaEvent_t a, b; };
+    std::vector<Timed> pending;
+    std::vector<cudaEvent_t> pool;
+    int64_t launches[3] = {0, 0, 0};
+    double ms[3] = {0.0, 0.0, 0.0};
+
+    cudaEvent_t take()
+    {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+
+    template <class F>
+    cudaError_t run(int kind, cudaStream_t s, F fn, int kernels = 1)
+    {
+        if (!on) return fn();
+        cudaEvent_t a = take(), b = take();
+        if (!a || !b) return cudaErrorMemoryAllocation;
+        cudaError_t e = cudaEventRecord(a, s);
+        if (e == cudaSuccess) e = fn();
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        pending.push_back({kind, kernels, a, b});
+        return e;
+    }
+
+    cudaError_t collect(cudaStream_t s)
+    {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        for (auto& t : pending) {
+            float m = 0.0f;
+            e = cudaEventElapsedTime(&m, t.a, t.b);
+            if (e != cudaSuccess) return e;
+            launches[t.kind] += t.kernels;
+            ms[t.kind] += m;
+            pool.push_back(t.a);
+            pool.push_back(t.b);
+        }
+        pending.clear();
+        return cudaSuccess;
+    }
+
+    void reset(bool enable)
+    {
+        on = enable;
+        for (int k = 0; k < 3; ++k) {
+            launches[k] = 0;
+            ms[k] = 0.0;
+        }
+    }
+
+    void fill(ecris_profile* out) const
+    {
+        out->step_launches = launches[kKindStep];
+        out->step_ms = ms[kKindStep];
+        out->coulomb_launches = launches[kKindCoulomb];
+        out->coulomb_ms = ms[kKindCoulomb];
+        out->other_launches = launches[kKindOther];
+        out->other_ms = ms[kKindOther];
+    }
+
+    void release()
+    {
+        for (auto& t : pending) {
+            cudaEventDestroy(t.a);
+            cudaEventDestroy(t.b);
+        }
+        pending.clear();
+        for (auto e : pool) cudaEventDestroy(e);
+        pool.clear();
+    }
+};
+
+}  // namespace
+
 struct ecris_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -211,13 +300,7 @@ struct ecris_ctx {
     double dt_loaded = -1.0;
     uint32_t fold_every = 1, since_fold = 0;
 
-    // kernel timing (ecris_set_profiling)
-    bool prof = false;
-    struct Timed { int kind; int kernels; cudaEvent_t a, b; };
-    std::vector<Timed> pending;
-    std::vector<cudaEvent_t> event_pool;
-    int64_t launches[3] = {0, 0, 0};
-    double ms[3] = {0.0, 0.0, 0.0};
+    KernelTimer timer;          // ecris_set_profiling
 };
 
 namespace {
@@ -243,49 +326,11 @@ ecris_status fail(ecris_ctx* c, ecris_status st, const char* fmt, ...)
         }                                                                                 \
     } while (0)
 
-enum { kKindStep = 0, kKindCoulomb = 1, kKindOther = 2 };
-
-cudaEvent_t take_event(ecris_ctx* ctx)
-{
-    if (!ctx->event_pool.empty()) {
-        cudaEvent_t e = ctx->event_pool.back();
-        ctx->event_pool.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-    return e;
-}
-
 // launch `fn` on the context stream; with profiling on, bracket it by events
 template <class F>
 cudaError_t timed(ecris_ctx* ctx, int kind, F fn, int kernels = 1)
 {
-    if (!ctx->prof) return fn();
-    cudaEvent_t a = take_event(ctx), b = take_event(ctx);
-    if (!a || !b) return cudaErrorMemoryAllocation;
-    cudaError_t e = cudaEventRecord(a, ctx->stream);
-    if (e == cudaSuccess) e = fn();
-    if (e == cudaSuccess) e = cudaEventRecord(b, ctx->stream);
-    ctx->pending.push_back({kind, kernels, a, b});
-    return e;
-}
-
-cudaError_t collect_profile(ecris_ctx* ctx)
-{
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return e;
-    for (auto& t : ctx->pending) {
-        float ms = 0.0f;
-        e = cudaEventElapsedTime(&ms, t.a, t.b);
-        if (e != cudaSuccess) return e;
-        ctx->launches[t.kind] += t.kernels;
-        ctx->ms[t.kind] += ms;
-        ctx->event_pool.push_back(t.a);
-        ctx->event_pool.push_back(t.b);
-    }
-    ctx->pending.clear();
-    return cudaSuccess;
+    return ctx->timer.run(kind, ctx->stream, fn, kernels);
 }
 
 template <class T>
@@ -616,11 +661,7 @@ void ecris_destroy(ecris_ctx* ctx)
     free_ions(ctx);
     free_fields(ctx);
     cudaStreamSynchronize(ctx->stream);
-    for (auto& t : ctx->pending) {
-        cudaEventDestroy(t.a);
-        cudaEventDestroy(t.b);
-    }
-    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    ctx->timer.release();
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     if (ctx->h_run) cudaFreeHost(ctx->h_run);
     if (ctx->h_kdt) cudaFreeHost(ctx->h_kdt);
@@ -922,7 +963,7 @@ ecris_status ecris_step(ecris_ctx* ctx, uint32_t nsteps, double dt)
             st = sort_particles(ctx);
             if (st != ECRIS_OK) return st;
         }
-        if (!ctx->prof) {
+        if (!ctx->timer.on) {
             // the whole step as one graph launch
             cudaGraphExec_t x = nullptr;
             st = step_graph(ctx, 0, &x);
@@ -1059,12 +1100,8 @@ ecris_status ecris_set_profiling(ecris_ctx* ctx, int enable)
 {
     if (!ctx) return ECRIS_EINVAL;
     CK(cudaSetDevice(ctx->device));
-    CK(collect_profile(ctx));
-    ctx->prof = enable != 0;
-    for (int k = 0; k < 3; ++k) {
-        ctx->launches[k] = 0;
-        ctx->ms[k] = 0.0;
-    }
+    CK(ctx->timer.collect(ctx->stream));
+    ctx->timer.reset(enable != 0);
     return ECRIS_OK;
 }
 
@@ -1073,13 +1110,8 @@ ecris_status ecris_get_profile(ecris_ctx* ctx, ecris_profile* out)
     if (!ctx) return ECRIS_EINVAL;
     if (!out) return fail(ctx, ECRIS_EINVAL, "get_profile: out is NULL");
     CK(cudaSetDevice(ctx->device));
-    CK(collect_profile(ctx));
-    out->step_launches = ctx->launches[kKindStep];
-    out->step_ms = ctx->ms[kKindStep];
-    out->coulomb_launches = ctx->launches[kKindCoulomb];
-    out->coulomb_ms = ctx->ms[kKindCoulomb];
-    out->other_launches = ctx->launches[kKindOther];
-    out->other_ms = ctx->ms[kKindOther];
+    CK(ctx->timer.collect(ctx->stream));
+    ctx->timer.fill(out);
     return ECRIS_OK;
 }
 
@@ -1112,6 +1144,7 @@ struct ecris_batch {
     bool params_dirty = true;       // parameter blocks must be uploaded
     cudaGraphExec_t gexec = nullptr;
     bool graph_dirty = true;
+    KernelTimer timer;              // ecris_batch_set_profiling
 };
 
 namespace {
@@ -1186,10 +1219,14 @@ ecris_status batch_items(ecris_batch* b)
 
 // one step of every run: the batched step kernel, the collision kernels of
 // the runs that have them, and the step counters of the others
+int batch_bps(const ecris_batch* b)
+{
+    return b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, b->max_blocks_per_sm) : b->max_blocks_per_sm;
+}
+
 cudaError_t batch_launch(ecris_batch* b)
 {
-    const int bps = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, b->max_blocks_per_sm) : b->max_blocks_per_sm;
-    cudaError_t e = launch_step_batch(b->d_runs, b->d_items, b->nitems, b->sm_count * bps, b->stream);
+    cudaError_t e = launch_step_batch(b->d_runs, b->d_items, b->nitems, b->sm_count * batch_bps(b), b->stream);
     for (size_t r = 0; e == cudaSuccess && r < b->runs.size(); ++r) {
         ecris_ctx* c = b->runs[r];
         if (!c || !(c->h.mcc.flags & kFCoulomb)) continue;
@@ -1287,6 +1324,7 @@ void ecris_batch_destroy(ecris_batch* b)
     cudaStreamSynchronize(b->stream);
     if (b->h_runs) cudaFreeHost(b->h_runs);
     if (b->staged) cudaEventDestroy(b->staged);
+    b->timer.release();
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -1373,7 +1411,11 @@ ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps)
         // when a run's collision kernels take the block by value
         for (auto* c : b->runs) {
             if (!c || c->n4 == 0 || c->since_sort < c->sort_every) continue;
-            ecris_status st = sort_particles(c);
+            ecris_status st = ECRIS_OK;
+            BCK(b->timer.run(kKindOther, b->stream, [&] {
+                st = sort_particles(c);
+                return cudaSuccess;
+            }, 6));
             if (st != ECRIS_OK) return bfail(b, st, "batch_step: " + c->err);
             b->params_dirty = true;
             if (c->h.mcc.flags & kFCoulomb) b->graph_dirty = true;
@@ -1382,9 +1424,26 @@ ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps)
             ecris_status st = batch_upload(b);
             if (st != ECRIS_OK) return st;
         }
-        ecris_status st = batch_graph(b);
-        if (st != ECRIS_OK) return st;
-        BCK(cudaGraphLaunch(b->gexec, b->stream));
+        if (!b->timer.on) {
+            ecris_status st = batch_graph(b);
+            if (st != ECRIS_OK) return st;
+            BCK(cudaGraphLaunch(b->gexec, b->stream));
+        } else {
+            // timed: the same launches as the graph, one by one
+            BCK(b->timer.run(kKindStep, b->stream, [&] {
+                return launch_step_batch(b->d_runs, b->d_items, b->nitems, b->sm_count * batch_bps(b), b->stream);
+            }));
+            for (auto* c : b->runs) {
+                if (!c || !(c->h.mcc.flags & kFCoulomb)) continue;
+                const uint32_t nc = (uint32_t)((size_t)c->h.nx * c->h.ny * c->h.nz);
+                BCK(b->timer.run(kKindCoulomb, b->stream, [&] {
+                    return launch_coulomb(*c->h_run, nc, c->ntiles, c->d_ticket, c->collide_grid, b->stream);
+                }, kCoulombKernels));
+            }
+            BCK(b->timer.run(kKindOther, b->stream, [&] {
+                return launch_bump_steps(b->d_runs, (uint32_t)b->runs.size(), b->stream);
+            }));
+        }
         for (size_t r = 0; r < b->runs.size(); ++r) {
             ecris_ctx* c = b->runs[r];
             if (!c) continue;
@@ -1393,7 +1452,9 @@ ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps)
             ++c->since_sort;
             if (++c->since_fold >= c->fold_every) {
                 const uint32_t nc = (uint32_t)((size_t)c->h.nx * c->h.ny * c->h.nz);
-                BCK(launch_fold(*c->h_run, nc, c->d_count, c->d_charge, b->stream));
+                BCK(b->timer.run(kKindOther, b->stream, [&] {
+                    return launch_fold(*c->h_run, nc, c->d_count, c->d_charge, b->stream);
+                }));
                 c->since_fold = 0;
             }
         }
@@ -1425,6 +1486,25 @@ ecris_status ecris_batch_memory(const ecris_batch* b, size_t* used, size_t* budg
     if (!b) return ECRIS_EINVAL;
     if (used) *used = b->used;
     if (budget) *budget = b->budget;
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_set_profiling(ecris_batch* b, int enable)
+{
+    if (!b) return ECRIS_EINVAL;
+    BCK(cudaSetDevice(b->device));
+    BCK(b->timer.collect(b->stream));
+    b->timer.reset(enable != 0);
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_get_profile(ecris_batch* b, ecris_profile* out)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (!out) return bfail(b, ECRIS_EINVAL, "batch_get_profile: out is NULL");
+    BCK(cudaSetDevice(b->device));
+    BCK(b->timer.collect(b->stream));
+    b->timer.fill(out);
     return ECRIS_OK;
 }
 

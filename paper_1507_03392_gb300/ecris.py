@@ -162,6 +162,10 @@ def _load():
     lib.ecris_batch_memory.restype = st
     lib.ecris_batch_autotune.argtypes = [P, ctypes.c_uint32, ctypes.POINTER(Tuning)]
     lib.ecris_batch_autotune.restype = st
+    lib.ecris_batch_set_profiling.argtypes = [P, ctypes.c_int]
+    lib.ecris_batch_set_profiling.restype = st
+    lib.ecris_batch_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
+    lib.ecris_batch_get_profile.restype = st
     lib.ecris_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_size_t, ctypes.c_uint32,
                                         ctypes.c_uint32]
     lib.ecris_server_create.restype = st
@@ -206,6 +210,8 @@ ecris_batch_diag = LIB.ecris_batch_diag
 ecris_batch_get_state = LIB.ecris_batch_get_state
 ecris_batch_memory = LIB.ecris_batch_memory
 ecris_batch_autotune = LIB.ecris_batch_autotune
+ecris_batch_set_profiling = LIB.ecris_batch_set_profiling
+ecris_batch_get_profile = LIB.ecris_batch_get_profile
 ecris_server_create = LIB.ecris_server_create
 ecris_server_destroy = LIB.ecris_server_destroy
 ecris_server_last_error = LIB.ecris_server_last_error
@@ -358,6 +364,14 @@ class Batch:
         t = Tuning()
         self._check(ecris_batch_autotune(self.b, int(trial_steps), ctypes.byref(t)))
         return {"sort_every": t.sort_every, "blocks_per_sm": t.blocks_per_sm}
+
+    def set_profiling(self, on=True):
+        self._check(ecris_batch_set_profiling(self.b, 1 if on else 0))
+
+    def profile(self):
+        p = Profile()
+        self._check(ecris_batch_get_profile(self.b, ctypes.byref(p)))
+        return {f: getattr(p, f) for f, _ in Profile._fields_}
 
 
 class Server:

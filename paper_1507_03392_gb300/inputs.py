@@ -179,6 +179,50 @@ def config_oxygen_scan(i: int, n: Optional[int] = None) -> Workload:
                     ion_qmax_init=6, atoms_fill_chamber=True)
 
 
+def config_power_scan(i: int, n: Optional[int] = None) -> Workload:
+    """One run of the batched microwave-power scan: Ar, electron density in the
+    zone log-uniform 5e10-2e12 cm^-3 and warm-electron temperature log-uniform
+    0.3-3 keV (the coupled power sets both, Sec. II), N log-uniform 1e5-4e6."""
+    rng = np.random.default_rng(2000 + i)
+    lu = lambda lo, hi: math.exp(rng.uniform(math.log(lo), math.log(hi)))
+    ne, te = lu(5e10, 2e12), lu(300.0, 3000.0)
+    n_draw = int(round(lu(1e5, 4e6)))
+    p = RunParams(seed=2000 + i, ne_in_cm3=ne, Te_warm_eV=te, n0_cm3=1e10, flags=F_ALL)
+    return Workload(f"ar_power_scan_{i}", p, n=n_draw if n is None else n, steps=10_000,
+                    atom_fraction=0.75, ion_qmax_init=8, atoms_fill_chamber=True)
+
+
+SERVED_MESHES = ((32, 32, 64), (64, 64, 128), (96, 96, 192))
+
+
+def served_stream(seed: int = 5, rate_per_s: float = 20.0, duration_s: float = 2.0,
+                  n_range: tuple = (1e4, 8e6)):
+    """A served request stream: Poisson arrivals (rate_per_s) over duration_s.
+
+    Each request is a parameter-scan run: species uniform over O, Ar, Kr;
+    N log-uniform in n_range; mesh uniform over SERVED_MESHES; neutral density
+    (gas flow) log-uniform 3e9-3e11 cm^-3; zone electron density log-uniform
+    5e10-2e12 cm^-3 and warm-electron temperature 0.3-3 keV (microwave power);
+    every process of the step on.  Returns a list of (arrival time s, Workload).
+    """
+    rng = np.random.default_rng(seed)
+    lu = lambda lo, hi: math.exp(rng.uniform(math.log(lo), math.log(hi)))
+    out, t, i = [], 0.0, 0
+    species = (OXYGEN, ARGON, KRYPTON)
+    while True:
+        t += rng.exponential(1.0 / rate_per_s)
+        if t > duration_s:
+            return out
+        sp = species[int(rng.integers(3))]
+        nx, ny, nz = SERVED_MESHES[int(rng.integers(len(SERVED_MESHES)))]
+        n = int(round(lu(*n_range)))
+        p = RunParams(species=sp, nx=nx, ny=ny, nz=nz, n0_cm3=lu(3e9, 3e11), ne_in_cm3=lu(5e10, 2e12),
+                      Te_warm_eV=lu(300.0, 3000.0), flags=F_ALL, seed=5000 + i)
+        out.append((t, Workload(f"served_{i}_{sp.name}", p, n=n, steps=4096, atom_fraction=0.75,
+                                ion_qmax_init=min(8, sp.qmax - 1), atoms_fill_chamber=True)))
+        i += 1
+
+
 def _mb_velocities(rng, n, T_eV, mass_amu):
     sigma = math.sqrt(T_eV * E_CHARGE / (mass_amu * AMU))
     return rng.normal(0.0, sigma, size=(3, n))

@@ -113,3 +113,22 @@ def test_autotune_keeps_results(E):
     for h, (rp, st, Ef) in zip(hs, specs):
         same((b.state(h), b.diag(h, grids=True)), alone(E, rp, st, Ef, total))
     b.close()
+
+
+def test_profiled_steps_keep_results(E):
+    """With timing on, the batch launches its kernels one by one instead of
+    replaying the graph; results must not change."""
+    specs = run_specs()
+    b = E.Batch()
+    hs = [b.add(rp, st, E=Ef) for rp, st, Ef in specs]
+    b.step(3)
+    b.set_profiling(True)
+    b.step(4)
+    p = b.profile()
+    b.set_profiling(False)
+    b.step(2)
+    assert p["step_launches"] == 4 and p["step_ms"] > 0
+    assert p["coulomb_launches"] == 4 * 6      # one run has collisions: six kernels a step
+    for h, (rp, st, Ef) in zip(hs, specs):
+        same((b.state(h), b.diag(h, grids=True)), alone(E, rp, st, Ef, 9))
+    b.close()
