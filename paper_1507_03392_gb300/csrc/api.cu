@@ -529,6 +529,11 @@ ecris_status upload_dt(ecris_ctx* ctx, double dt)
         if (v > lam) lam = v;
     }
     ctx->h_run->lam0_max = lam * 1.0001f;
+    // the same bound as an integer gate on the ionisation word: the kernels'
+    // threshold floor(p 2^32) for any cell is at most ceil(p(lam0_max) 2^32)
+    const double pmax = -std::expm1(-(double)ctx->h_run->lam0_max);
+    const double gate = std::ceil(pmax * 4294967296.0);
+    ctx->h_run->atom_gate = gate >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)gate;
     CK(cudaMemcpyAsync(ctx->d_kdt, ctx->h_kdt, 2 * kQSlots * sizeof(float), cudaMemcpyHostToDevice,
                        ctx->stream));
     ctx->dt_loaded = dt;

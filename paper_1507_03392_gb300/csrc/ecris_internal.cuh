@@ -92,8 +92,9 @@ struct RunDev {
     float ei_coef[2];            // D^2 = ei_coef[zone] * n_e * Q^p (zone 0 cold, 1 warm)
     int32_t ei_pow;
     float ke_scale;              // (M/2) / e * 1e6: micro-eV per (m/s)^2
-    float lam0_max;              // bound (with margin) on n_e k_0 dt over all cells: an atom
-                                 // whose word is above its threshold cannot ionise anywhere
+    float lam0_max;              // bound (with margin) on n_e k_0 dt over all cells
+    uint32_t atom_gate;          // an atom whose ionisation word is >= atom_gate cannot ionise
+                                 // in any cell (0xFFFFFFFF: no such bound)
     float lnl_ii_coef;           // Nanbu s prefactor lnL/(4 pi) (e^2/(eps0 mu))^2 w / V_cell
     uint32_t seed_lo, seed_hi;
     // arrays
@@ -129,7 +130,6 @@ struct RunDev {
     uint32_t n;                  // particles
     uint32_t n4;                 // float4 groups = ceil(n/4)
     uint32_t ncells;
-    uint32_t pad_;
 };
 
 // ----------------------------------------------------------------------------

@@ -48,6 +48,16 @@ __device__ __forceinline__ float event_prob(float lam)
     return -expm1f(-lam);
 }
 
+// 64-bit displacement for the rare step longer than 2^30 fixed-point units
+// (kept out of line: the common path converts in 32 bits)
+struct Disp { long long x, y, z; };
+
+__device__ __noinline__ Disp far_displacement(float dx, float dy, float dz)
+{
+    return Disp{__float2ll_rn(fminf(fmaxf(dx, -1e12f), 1e12f)), __float2ll_rn(fminf(fmaxf(dy, -1e12f), 1e12f)),
+                __float2ll_rn(fminf(fmaxf(dz, -1e12f), 1e12f))};
+}
+
 // Advance one particle by one step.  pid is its stable id (the Philox counter
 // word).  On return dep_cell is the cell it deposits in (kNoCell if it does
 // not: frozen or padding) and ckey the cell where it takes part in Coulomb
@@ -99,11 +109,21 @@ __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uin
             vy = my + h * Ey;
             vz = mz + h * Ez;
         }
-        // displacement in fixed-point units, rounded to nearest; bounded so a
+        // displacement in fixed-point units, rounded to nearest.  Below 2^30
+        // units a 32-bit conversion gives the same integer; larger (or
+        // non-finite) displacements take the 64-bit conversion, bounded so a
         // runaway velocity cannot wrap the 64-bit sums
-        xn += __float2ll_rn(fminf(fmaxf(vx * R.dt_sxy, -1e12f), 1e12f));
-        yn += __float2ll_rn(fminf(fmaxf(vy * R.dt_sxy, -1e12f), 1e12f));
-        zn += __float2ll_rn(fminf(fmaxf(vz * R.dt_sz, -1e12f), 1e12f));
+        const float dx = vx * R.dt_sxy, dy = vy * R.dt_sxy, dz = vz * R.dt_sz;
+        if (fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))) < 1.0e9f) {
+            xn += __float2int_rn(dx);
+            yn += __float2int_rn(dy);
+            zn += __float2int_rn(dz);
+        } else {
+            const Disp d = far_displacement(dx, dy, dz);
+            xn += d.x;
+            yn += d.y;
+            zn += d.z;
+        }
     }
 
     // cell record and random words of the new position, fetched before the
@@ -116,8 +136,9 @@ __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uin
     const Words w = rng_words(R, pid, step, 0u);
 
     // ---- boundary test on the new position, exact in fixed point ----
-    const bool out_r = xn < -lim || xn >= lim || yn < -lim || yn >= lim ||
-                       xn * xn + yn * yn > (1ll << 62);
+    const bool out_xy = xn < -lim || xn >= lim || yn < -lim || yn >= lim;
+    const bool out_r = out_xy || (long long)(int32_t)xn * (int32_t)xn + (long long)(int32_t)yn * (int32_t)yn >
+                                     (1ll << 62);
     const bool out_0 = zn < -lim;
     const bool out_L = zn >= lim;
     if (out_r | out_0 | out_L) {
@@ -199,7 +220,7 @@ __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uin
         // an atom needs its cell only if its ionisation word could fire in
         // the densest cell; otherwise no cell can ionise it this step
         const bool ionize = (R.flags & kFIonize) && (int)Q < R.qmax;
-        const bool need = Q > 0 || (ionize && fires(w.w0, event_prob(R.lam0_max)));
+        const bool need = Q > 0 || (ionize && (w.w0 < R.atom_gate || R.atom_gate == 0xFFFFFFFFu));
         if (need && cell != cell_pre) cr = __ldg(R.cell + cell);   // n_e, zone, delta_x, delta_y
         const int zone = cr.y > 0.5f ? 1 : 0;
         if (ionize && need) {
@@ -357,17 +378,31 @@ __device__ __forceinline__ void load_tile(const RunDev& R, Stage& st, uint64_t* 
     bulk_load(st.id, reinterpret_cast<const uint4*>(R.id) + g0, bytes, bar);
 }
 
-// NGP deposition of one particle per lane, aggregated over the lanes that hit
-// the same cell (particles are kept sorted by cell, so neighbours mostly do):
-// the lowest lane of each group adds count << 32 | charge for the group
+// NGP deposition of one particle per lane (the whole warp calls it), summed
+// over runs of neighbouring lanes in the same cell (particles are kept sorted
+// by cell, so neighbours mostly are): the last lane of each run adds
+// count << 32 | charge for the run.  The sums come from one warp prefix sum of
+// (1 << 16 | Q) per lane: at most 32 lanes of Q <= 63 fit 16 bits of charge.
 __device__ __forceinline__ void deposit_warp(const RunDev& R, uint32_t cell, uint32_t Q)
 {
-    const uint32_t live = __ballot_sync(0xFFFFFFFFu, cell != kNoCell);
-    if (cell == kNoCell) return;
-    const uint32_t grp = __match_any_sync(live, cell);
-    const uint32_t q = __reduce_add_sync(grp, Q);
-    if ((threadIdx.x & 31) == (uint32_t)(__ffs(grp) - 1))
-        atomicAdd(R.dep + cell, ((unsigned long long)__popc(grp) << 32) | (unsigned long long)q);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, cell, 1);
+    const uint32_t heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || prev != cell);
+    const uint32_t v = cell != kNoCell ? (65536u | Q) : 0u;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += t;
+    }
+    // first lane of this lane's run, and the prefix just before it
+    const uint32_t h = 31u - (uint32_t)__clz(heads & (0xFFFFFFFFu >> (31u - lane)));
+    const uint32_t before = __shfl_sync(0xFFFFFFFFu, incl, h == 0 ? 0 : h - 1);
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (tail && cell != kNoCell) {
+        const uint32_t sum = incl - (h == 0 ? 0u : before);
+        atomicAdd(R.dep + cell, ((unsigned long long)(sum >> 16) << 32) | (unsigned long long)(sum & 0xFFFFu));
+    }
 }
 
 // Publish this lane's Coulomb participant (ck != kNoCell) for the collision
