@@ -362,7 +362,7 @@ ecris_status ecris_server_stats(ecris_server* s, double* now, int64_t* queued, i
  * the device.  It runs the same Takizawa-Abe pairing and Nanbu scattering as
  * ecris_step (ECRIS_F_COULOMB) on caller-owned device arrays and keeps all its
  * working memory in one fixed-size array that the library holds on every GPU
- * that loads it (about 7 MB, until the process exits); it allocates nothing.
+ * that loads it (about 4.5 MB, until the process exits); it allocates nothing.
  *
  *   n            particles, at most 65536; arrays are indexed by particle id
  *                (the Philox counter word, as in ecris_step)

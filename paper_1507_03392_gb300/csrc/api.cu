@@ -252,11 +252,10 @@ struct ecris_ctx {
     uint32_t* d_tcount = nullptr;
     float4* d_crec = nullptr;
     uint32_t* d_ccount = nullptr;
+    uint32_t* d_cstart = nullptr;
     uint32_t* d_coff = nullptr;
     uint32_t* d_cblk = nullptr;
     unsigned long long* d_ckeys = nullptr;
-    unsigned long long* d_skeys = nullptr;
-    float4* d_srec = nullptr;
     int collide_grid = 0;
     // two sets of particle arrays; the sort moves the particles from the
     // current set (index cur) to the other
@@ -280,15 +279,14 @@ struct ecris_ctx {
     uint64_t param_version = 1;
     uint32_t* d_cslot = nullptr;
     uint32_t* d_sslot = nullptr;
-    uint2* d_pairs = nullptr;
-    uint2* d_trips = nullptr;
-    uint32_t* d_npt = nullptr;
     unsigned long long* d_dep = nullptr;
     unsigned long long* d_count = nullptr;
     unsigned long long* d_charge = nullptr;
     unsigned long long* d_tally = nullptr;
     unsigned long long* d_census = nullptr;
     uint32_t* d_step = nullptr;
+    uint32_t* d_leave = nullptr;    // leaver list (cap) and its count
+    uint32_t* d_nleave = nullptr;
     unsigned int* d_ticket = nullptr;
     uint32_t ntiles = 0;
     RunDev* h_run = nullptr;    // parameter block passed by value to every kernel
@@ -364,15 +362,14 @@ void free_ions(ecris_ctx* ctx)
     free_async(ctx, ctx->d_aos);
     free_async(ctx, ctx->d_cslot);
     free_async(ctx, ctx->d_sslot);
-    free_async(ctx, ctx->d_pairs);
-    free_async(ctx, ctx->d_trips);
-    free_async(ctx, ctx->d_npt);
     free_async(ctx, ctx->d_dep);
     free_async(ctx, ctx->d_count);
     free_async(ctx, ctx->d_charge);
     free_async(ctx, ctx->d_tally);
     free_async(ctx, ctx->d_census);
     free_async(ctx, ctx->d_step);
+    free_async(ctx, ctx->d_leave);
+    free_async(ctx, ctx->d_nleave);
     free_async(ctx, ctx->d_ticket);
     free_async(ctx, ctx->d_q8);
     free_async(ctx, ctx->d_bad);
@@ -382,11 +379,10 @@ void free_ions(ecris_ctx* ctx)
     free_async(ctx, ctx->d_tcount);
     free_async(ctx, ctx->d_crec);
     free_async(ctx, ctx->d_ccount);
+    free_async(ctx, ctx->d_cstart);
     free_async(ctx, ctx->d_coff);
     free_async(ctx, ctx->d_cblk);
     free_async(ctx, ctx->d_ckeys);
-    free_async(ctx, ctx->d_skeys);
-    free_async(ctx, ctx->d_srec);
     ctx->have_ions = false;
     ctx->loaded = false;
     ctx->cap = ctx->cap_cells = 0;
@@ -491,21 +487,19 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.tcount = ctx->d_tcount;
     R.crec = ctx->d_crec;
     R.ccount = ctx->d_ccount;
+    R.cstart = ctx->d_cstart;
     R.coff = ctx->d_coff;
     R.cblk = ctx->d_cblk;
     R.ckeys = ctx->d_ckeys;
-    R.skeys = ctx->d_skeys;
-    R.srec = ctx->d_srec;
     R.cslot = ctx->d_cslot;
     R.sslot = ctx->d_sslot;
-    R.pairs = ctx->d_pairs;
-    R.trips = ctx->d_trips;
-    R.npt = ctx->d_npt;
     R.nanbu = ctx->d_nanbu;
     R.nanbu_lnlo = (float)std::log(kNanbuSLo);
     R.nanbu_inv_dln = (float)((kNanbuN - 1) / std::log(kNanbuSHi / kNanbuSLo));
     R.step = ctx->d_step;
     R.err = ctx->d_err;
+    R.leave = ctx->d_leave;
+    R.nleave = ctx->d_nleave;
     R.n = (uint32_t)ctx->n;
     R.n4 = (uint32_t)ctx->n4;
     R.ncells = (uint32_t)((size_t)h.nx * h.ny * h.nz);
@@ -559,8 +553,10 @@ ecris_status step_graph(ecris_ctx* ctx, int kind, cudaGraphExec_t* out)
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    if (kind == 0)
-        e = launch_step(*ctx->h_run, ctx->ntiles, ctx->d_ticket, coulomb ? 0 : 1, ctx->step_grid, ctx->stream);
+    if (kind == 0) {
+        e = launch_step(*ctx->h_run, ctx->ntiles, ctx->step_grid, ctx->stream);
+        if (e == cudaSuccess) e = launch_leave(*ctx->h_run, ctx->d_ticket, coulomb ? 0 : 1, ctx->stream);
+    }
     if (e == cudaSuccess && coulomb)
         e = launch_coulomb(*ctx->h_run, nc, ctx->ntiles, ctx->d_ticket, ctx->collide_grid, ctx->stream);
     const cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
@@ -858,6 +854,8 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         CK(cudaMallocAsync((void**)&ctx->d_tally, kTallyWords * sizeof(unsigned long long), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_census, kQSlots * sizeof(unsigned long long), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_step, sizeof(uint32_t), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_leave, cap * sizeof(uint32_t), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_nleave, sizeof(uint32_t), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_ticket, sizeof(unsigned int), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_bad, 2 * sizeof(unsigned int), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_err, sizeof(uint32_t), ctx->stream));
@@ -866,19 +864,15 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
             CK(cudaMallocAsync((void**)&ctx->d_plist, slots * sizeof(uint4), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_cslot, cap * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_sslot, cap * sizeof(uint32_t), ctx->stream));
-            CK(cudaMallocAsync((void**)&ctx->d_pairs, (cap / 2 + 1) * sizeof(uint2), ctx->stream));
-            CK(cudaMallocAsync((void**)&ctx->d_trips, (cap / 3 + 1) * sizeof(uint2), ctx->stream));
-            CK(cudaMallocAsync((void**)&ctx->d_npt, 2 * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_pvel, slots * sizeof(float4), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_tcount, (cap / kTile + 1) * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_ckeys, cap * sizeof(unsigned long long), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_crec, cap * sizeof(float4), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_ccount, nc * sizeof(uint32_t), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_cstart, (cap / kCellIons + 2) * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_coff, (nc + 1) * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_cblk, (size_t)coulomb_scan_blocks((uint32_t)nc) * sizeof(uint32_t),
                                ctx->stream));
-            CK(cudaMallocAsync((void**)&ctx->d_skeys, cap * sizeof(unsigned long long), ctx->stream));
-            CK(cudaMallocAsync((void**)&ctx->d_srec, cap * sizeof(float4), ctx->stream));
         }
         ctx->cap = cap;
         ctx->cap_cells = nc;
@@ -886,7 +880,7 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
     }
     ctx->n = n;
     ctx->n4 = n4;
-    ctx->ntiles = (uint32_t)((n4 + kThreads - 1) / kThreads);
+    ctx->ntiles = (uint32_t)((n4 + kTileGroups - 1) / kTileGroups);
     const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (n) {
         for (int k = 0; k < 6; ++k)
@@ -899,6 +893,7 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
     CK(cudaMemsetAsync(ctx->d_charge, 0, nc * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_tally, 0, kTallyWords * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(uint32_t), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_nleave, 0, sizeof(uint32_t), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_ticket, 0, sizeof(unsigned int), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_bad, 0, sizeof(unsigned int), ctx->stream));
@@ -977,8 +972,10 @@ ecris_status ecris_step(ecris_ctx* ctx, uint32_t nsteps, double dt)
         } else {
             // timed: the step kernel on its own, the collision kernels as a graph
             CK(timed(ctx, kKindStep, [&] {
-                return launch_step(*ctx->h_run, ctx->ntiles, ctx->d_ticket, coulomb ? 0 : 1, ctx->step_grid,
-                                   ctx->stream);
+                return launch_step(*ctx->h_run, ctx->ntiles, ctx->step_grid, ctx->stream);
+            }));
+            CK(timed(ctx, kKindOther, [&] {
+                return launch_leave(*ctx->h_run, ctx->d_ticket, coulomb ? 0 : 1, ctx->stream);
             }));
             if (coulomb) {
                 cudaGraphExec_t x = nullptr;
@@ -1149,6 +1146,7 @@ struct ecris_batch {
     bool params_dirty = true;       // parameter blocks must be uploaded
     cudaGraphExec_t gexec = nullptr;
     bool graph_dirty = true;
+    unsigned int* d_ticket = nullptr;   // last-block ticket of the leaver pass
     KernelTimer timer;              // ecris_batch_set_profiling
 };
 
@@ -1232,6 +1230,7 @@ int batch_bps(const ecris_batch* b)
 cudaError_t batch_launch(ecris_batch* b)
 {
     cudaError_t e = launch_step_batch(b->d_runs, b->d_items, b->nitems, b->sm_count * batch_bps(b), b->stream);
+    if (e == cudaSuccess) e = launch_leave_batch(b->d_runs, (uint32_t)b->runs.size(), b->d_ticket, b->stream);
     for (size_t r = 0; e == cudaSuccess && r < b->runs.size(); ++r) {
         ecris_ctx* c = b->runs[r];
         if (!c || !(c->h.mcc.flags & kFCoulomb)) continue;
@@ -1271,8 +1270,8 @@ size_t ecris_run_bytes(size_t n, int32_t nx, int32_t ny, int32_t nz, int coulomb
     const size_t cap = 4 * ((n + 3) / 4) + 4;
     const size_t nc = (size_t)(nx > 0 ? nx : 0) * (ny > 0 ? ny : 0) * (nz > 0 ? nz : 0);
     // two particle sets with ids, the sort's records, load bytes, Coulomb lists
-    size_t per_p = 2 * 32 + 32 + 4 + 1;
-    if (coulomb) per_p += 16 + 16 + 8 + 16 + 4 + 8 + 16 + 4 + 4 + 3 + 16;
+    size_t per_p = 2 * 32 + 32 + 4 + 4 + 1;
+    if (coulomb) per_p += 16 + 16 + 8 + 16 + 4 + 4 + 1;
     // cell records, E, deposit, time sums, sort histogram and scan, Coulomb counts
     size_t per_c = 16 + 16 + 8 + 8 + 8 + 4 + 4 + (coulomb ? 12 : 0);
     return cap * per_p + nc * per_c + (1u << 20);
@@ -1305,8 +1304,12 @@ ecris_status ecris_batch_create(ecris_batch** out, int device, void* cuda_stream
         }
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&b->d_ticket, sizeof(unsigned int), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned int), b->stream);
     if (e != cudaSuccess) {
         g_create_error = std::string("batch_create: ") + cudaGetErrorString(e);
+        if (b->d_ticket) cudaFreeAsync(b->d_ticket, b->stream);
+        if (b->staged) cudaEventDestroy(b->staged);
         if (b->own_stream) cudaStreamDestroy(b->stream);
         delete b;
         return ECRIS_ECUDA;
@@ -1326,6 +1329,7 @@ void ecris_batch_destroy(ecris_batch* b)
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->d_runs) cudaFreeAsync(b->d_runs, b->stream);
     if (b->d_items) cudaFreeAsync(b->d_items, b->stream);
+    if (b->d_ticket) cudaFreeAsync(b->d_ticket, b->stream);
     cudaStreamSynchronize(b->stream);
     if (b->h_runs) cudaFreeHost(b->h_runs);
     if (b->staged) cudaEventDestroy(b->staged);
@@ -1437,6 +1441,9 @@ ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps)
             // timed: the same launches as the graph, one by one
             BCK(b->timer.run(kKindStep, b->stream, [&] {
                 return launch_step_batch(b->d_runs, b->d_items, b->nitems, b->sm_count * batch_bps(b), b->stream);
+            }));
+            BCK(b->timer.run(kKindOther, b->stream, [&] {
+                return launch_leave_batch(b->d_runs, (uint32_t)b->runs.size(), b->d_ticket, b->stream);
             }));
             for (auto* c : b->runs) {
                 if (!c || !(c->h.mcc.flags & kFCoulomb)) continue;

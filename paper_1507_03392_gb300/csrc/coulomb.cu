@@ -11,15 +11,18 @@
 //                the slot receives key = (pairing hash << 32 | pid), the hash
 //                being word 0 of the particle's stream-1 Philox block, and the
 //                record (v, cell << 6 | Q), so each cell's records are contiguous;
-//   3. rank      one thread per participant counts the keys of its cell that
-//                are smaller than its own; that rank is its place in the cell's
-//                order (by hash, then pid), independent of the atomic arrival
-//                order, and the record moves there;
-//                Consecutive ranks pair up; a cell with an odd count puts ranks
-//                0, 1, 2 in a triplet that collides (0,1), (1,2), (2,0) over
-//                dt/2 each; the first ion of every pair and triplet is listed;
-//   4. pairs     one thread per listed pair or triplet collides it and writes
-//                the new velocities back.
+//   3. cells     each block takes the cells whose segments start in its
+//                range of about kCellIons participants and copies their keys,
+//                records and array slots to shared memory; one thread per
+//                participant counts the keys of its cell that are smaller than
+//                its own, which is its place in the cell's order (by hash, then
+//                pid), independent of the atomic arrival order.  Consecutive
+//                ranks pair up; a cell with an odd count puts ranks 0, 1, 2 in a
+//                triplet that collides (0,1), (1,2), (2,0) over dt/2 each.  The
+//                first ion of every pair and triplet is listed in shared memory
+//                and one thread per listed entry collides it and writes the
+//                velocities back.  A range too large for shared memory (a cell
+//                with thousands of ions) is done the same way in global memory.
 // A collision of ions a, b (same mass M, charges Qa, Qb) over time dt_c uses
 //   s = lnL/(4 pi) (Qa Qb e^2 / (eps0 mu))^2 n g^-3 dt_c,  mu = M/2,
 // n = w m / V_cell for the cell's m ions; A(s) from coth A - 1/A = e^-s
@@ -97,11 +100,7 @@ __global__ void __launch_bounds__(1024) k_scan_b(const __grid_constant__ RunDev 
         const uint32_t w = wsum[lane];
         const uint32_t wi = warp_incl_scan(w);
         wsum[lane] = wi - w;
-        if (lane == 31) {
-            R.coff[ncells] = wi;
-            R.npt[0] = 0u;
-            R.npt[1] = 0u;
-        }
+        if (lane == 31) R.coff[ncells] = wi;
     }
     __syncthreads();
     uint32_t off = wsum[warp] + incl - sum;
@@ -114,7 +113,17 @@ __global__ void __launch_bounds__(1024) k_scan_b(const __grid_constant__ RunDev 
     }
 }
 
-// pass C: add block offsets
+// range b of the collision kernel starts at the first cell c with
+// coff[c] >= b kCellIons: cell c starts the ranges b with
+// coff[c - 1] < b kCellIons <= coff[c]
+__device__ __forceinline__ void mark_ranges(const RunDev& R, uint32_t c, uint32_t prev, uint32_t cur)
+{
+    const uint32_t b0 = c == 0 ? 0u : prev / (uint32_t)kCellIons + 1u;
+    for (uint32_t b = b0; b <= cur / (uint32_t)kCellIons; ++b) R.cstart[b] = c;
+}
+
+// pass C: add block offsets, and mark where the collision kernel's ranges
+// start (the previous cell's offset is this one's minus its count)
 __global__ void __launch_bounds__(kScanThreads) k_scan_c(const __grid_constant__ RunDev R, uint32_t ncells)
 {
     const uint32_t add = R.cblk[blockIdx.x];
@@ -122,7 +131,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_c(const __grid_constant__
     for (uint32_t j = threadIdx.x; j < (uint32_t)kScanBlock; j += kScanThreads) {
         const uint32_t idx = base + j;
         if (idx >= ncells) break;
-        R.coff[idx] += add;
+        const uint32_t cur = R.coff[idx] + add;
+        R.coff[idx] = cur;
+        mark_ranges(R, idx, idx ? cur - R.ccount[idx - 1] : 0u, cur);
+        if (idx == ncells - 1) mark_ranges(R, ncells, cur, R.coff[ncells]);
     }
 }
 
@@ -208,98 +220,164 @@ __device__ __forceinline__ void write_back(const RunDev& R, uint32_t slot, const
     atomicOr(R.meta + slot, kEvCoulomb);   // result unused: a fire-and-forget reduction
 }
 
-// place each participant at its rank within its cell's order, and list the
-// first ion of every pair (and of every triplet) for the collision kernel
-__global__ void k_rank(const __grid_constant__ RunDev R, uint32_t ncells)
+// Shared-memory image of one range of cells (see the header).
+struct CellSmem {
+    unsigned long long key[kCellCap];
+    float4 rec[kCellCap];
+    uint32_t slot[kCellCap];
+    uint32_t sidx[kCellCap];          // sorted position -> index in the range
+    uint2 start[kCellCap / 2 + 1];    // (sorted position | triplet << 31, cell count)
+    uint32_t nstart;
+    uint32_t s0, s1;
+    unsigned long long ncoll;
+};
+
+// collide the pair (kind 0) or triplet (kind 1) starting at sorted position p
+// of a range (key / rec / slot indexed through sidx), m ions in the cell
+template <class K, class V, class S, class I>
+__device__ __forceinline__ uint32_t collide_entry(const RunDev& R, const K& key, const V& rec, const S& slot,
+                                                  const I& sidx, uint32_t p, uint32_t m, bool triplet,
+                                                  uint32_t step)
 {
-    const uint32_t total = R.coff[ncells];
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t end = (total + 31u) & ~31u;   // whole warps iterate together
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < end; j += gridDim.x * blockDim.x) {
-        uint32_t kind = 0, slot = 0, m = 0;      // kind 1: starts a pair, 2: starts a triplet
-        if (j < total) {
-            const unsigned long long key = R.ckeys[j];
-            const float4 rec = R.crec[j];
-            const uint32_t cell = __float_as_uint(rec.w) >> 6;
-            const uint32_t seg = R.coff[cell];
-            m = R.coff[cell + 1] - seg;
-            uint32_t rank = 0;
-            const unsigned long long* k = R.ckeys + seg;
-            for (uint32_t i = 0; i < m; ++i) rank += (k[i] < key) ? 1u : 0u;
-            slot = seg + rank;
-            R.skeys[slot] = key;
-            R.srec[slot] = rec;
-            R.sslot[slot] = R.cslot[j];
-            if (m >= 2u) {
-                const uint32_t start = (m & 1u) ? 3u : 0u;
-                if ((m & 1u) && rank == 0u) kind = 2;
-                else if (rank >= start && !((rank - start) & 1u)) kind = 1;
-            }
-        }
-        // warp-aggregated appends to the pair and triplet lists; the two
-        // counter updates are issued together so their latencies overlap
-        const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, kind == 1u);
-        const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, kind == 2u);
-        if (b1 | b2) {
-            uint32_t base1 = 0, base2 = 0;
-            if (lane == 0) {
-                if (b1) base1 = atomicAdd(R.npt, (uint32_t)__popc(b1));
-                if (b2) base2 = atomicAdd(R.npt + 1, (uint32_t)__popc(b2));
-            }
-            base1 = __shfl_sync(0xFFFFFFFFu, base1, 0);
-            base2 = __shfl_sync(0xFFFFFFFFu, base2, 0);
-            const uint32_t below = (1u << lane) - 1u;
-            if (kind == 1u) R.pairs[base1 + (uint32_t)__popc(b1 & below)] = make_uint2(slot, m);
-            if (kind == 2u) R.trips[base2 + (uint32_t)__popc(b2 & below)] = make_uint2(slot, m);
-        }
+    const float dt = R.dt;
+    const uint32_t ia = sidx[p], ib = sidx[p + 1];
+    float4 ra = rec[ia], rb = rec[ib];
+    if (!triplet) {
+        collide(R, ra, rb, dt, (float)m, (uint32_t)key[ia], step);   // ids give the random words
+        write_back(R, slot[ia], ra);
+        write_back(R, slot[ib], rb);
+        return 1u;
     }
+    // ranks 0, 1, 2: (0,1), (1,2), (2,0) over dt/2 each
+    const uint32_t ic = sidx[p + 2];
+    float4 rc = rec[ic];
+    const float mc = (float)m;
+    collide(R, ra, rb, 0.5f * dt, mc, (uint32_t)key[ia], step);
+    collide(R, rb, rc, 0.5f * dt, mc, (uint32_t)key[ib], step);
+    collide(R, rc, ra, 0.5f * dt, mc, (uint32_t)key[ic], step);
+    write_back(R, slot[ia], ra);
+    write_back(R, slot[ib], rb);
+    write_back(R, slot[ic], rc);
+    return 3u;
 }
 
-// one thread per listed pair or triplet: collide it and write the velocities back
-__global__ void k_pairs(const __grid_constant__ RunDev R, uint32_t ncells, unsigned int* ticket)
+// rank of participant j (index in the range) within its cell: the number of
+// smaller keys among the cell's m; seg = the cell's first index in the range
+template <class K>
+__device__ __forceinline__ uint32_t rank_in_cell(const K& key, uint32_t seg, uint32_t m, unsigned long long mine)
 {
-    __shared__ int s_last;
+    uint32_t r0 = 0, r1 = 0;
+    uint32_t i = 0;
+    for (; i + 2 <= m; i += 2) {
+        r0 += key[seg + i] < mine ? 1u : 0u;
+        r1 += key[seg + i + 1] < mine ? 1u : 0u;
+    }
+    if (i < m) r0 += key[seg + i] < mine ? 1u : 0u;
+    return r0 + r1;
+}
+
+// kind of sorted place r in a cell of m: 1 starts a pair, 2 starts a triplet
+__device__ __forceinline__ uint32_t start_kind(uint32_t r, uint32_t m)
+{
+    if (m < 2u) return 0u;
+    if (m & 1u) {
+        if (r == 0u) return 2u;
+        return (r >= 3u && !((r - 3u) & 1u)) ? 1u : 0u;
+    }
+    return (r & 1u) ? 0u : 1u;
+}
+
+__global__ void __launch_bounds__(256) k_cells(const __grid_constant__ RunDev R, uint32_t ncells, unsigned int* ticket)
+{
+    extern __shared__ __align__(16) unsigned char cell_smem_raw[];
+    CellSmem& S = *reinterpret_cast<CellSmem*>(cell_smem_raw);
+    const uint32_t total = R.coff[ncells];
     const uint32_t step = *R.step;
-    const uint32_t np = R.npt[0], nt = R.npt[1];
-    const float dt = R.dt;
-    unsigned long long ncoll = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np + nt; i += gridDim.x * blockDim.x) {
-        if (i < np) {
-            const uint2 pr = R.pairs[i];
-            const uint32_t t = pr.x;
-            float4 ra = R.srec[t], rb = R.srec[t + 1];
-            collide(R, ra, rb, dt, (float)pr.y, (uint32_t)R.skeys[t], step);   // ids give the random words
-            write_back(R, R.sslot[t], ra);
-            write_back(R, R.sslot[t + 1], rb);
-            ncoll += 1;
-        } else {
-            // triplet of ranks 0, 1, 2: (0,1), (1,2), (2,0) over dt/2 each
-            const uint2 tr = R.trips[i - np];
-            const uint32_t t = tr.x;
-            const float mc = (float)tr.y;
-            float4 ra = R.srec[t], rb = R.srec[t + 1], rc = R.srec[t + 2];
-            const uint32_t pa = (uint32_t)R.skeys[t], pb = (uint32_t)R.skeys[t + 1], pc = (uint32_t)R.skeys[t + 2];
-            collide(R, ra, rb, 0.5f * dt, mc, pa, step);
-            collide(R, rb, rc, 0.5f * dt, mc, pb, step);
-            collide(R, rc, ra, 0.5f * dt, mc, pc, step);
-            write_back(R, R.sslot[t], ra);
-            write_back(R, R.sslot[t + 1], rb);
-            write_back(R, R.sslot[t + 2], rc);
-            ncoll += 3;
+    const uint32_t tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) S.ncoll = 0ull;
+    uint32_t ncoll = 0;
+    for (uint32_t b = blockIdx.x; b * (uint32_t)kCellIons < total; b += gridDim.x) {
+        if (tid == 0) {
+            const uint32_t hi = (b + 1u) * (uint32_t)kCellIons;
+            const uint32_t c1 = hi >= total ? ncells : R.cstart[b + 1];
+            S.s0 = R.coff[R.cstart[b]];
+            S.s1 = R.coff[c1];
+            S.nstart = 0u;
         }
+        __syncthreads();
+        const uint32_t s0 = S.s0, n = S.s1 - S.s0;
+        if (n <= (uint32_t)kCellCap) {
+            for (uint32_t j = tid; j < n; j += blockDim.x) {
+                S.key[j] = R.ckeys[s0 + j];
+                S.rec[j] = R.crec[s0 + j];
+                S.slot[j] = R.cslot[s0 + j];
+            }
+            __syncthreads();
+            // ranks, and the list of pair / triplet starters
+            const uint32_t end = (n + 31u) & ~31u;
+            for (uint32_t j = tid; j < end; j += blockDim.x) {
+                uint32_t kind = 0u, pos = 0u, m = 0u;
+                if (j < n) {
+                    const uint32_t cell = __float_as_uint(S.rec[j].w) >> 6;
+                    const uint32_t seg = R.coff[cell] - s0;
+                    m = R.coff[cell + 1] - R.coff[cell];
+                    const uint32_t r = rank_in_cell(S.key, seg, m, S.key[j]);
+                    pos = seg + r;
+                    S.sidx[pos] = j;
+                    kind = start_kind(r, m);
+                }
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, kind != 0u);
+                if (bal) {
+                    uint32_t base = 0;
+                    if (lane == 0) base = atomicAdd(&S.nstart, (uint32_t)__popc(bal));
+                    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                    if (kind) S.start[base + (uint32_t)__popc(bal & ((1u << lane) - 1u))] =
+                        make_uint2(pos | (kind == 2u ? 0x80000000u : 0u), m);
+                }
+            }
+            __syncthreads();
+            const uint32_t ns = S.nstart;
+            for (uint32_t e = tid; e < ns; e += blockDim.x) {
+                const uint2 st = S.start[e];
+                ncoll += collide_entry(R, S.key, S.rec, S.slot, S.sidx, st.x & 0x7FFFFFFFu, st.y,
+                                       (st.x >> 31) != 0u, step);
+            }
+        } else {
+            // the same in global memory: sorted positions in sslot
+            const unsigned long long* key = R.ckeys + s0;
+            const float4* rec = R.crec + s0;
+            const uint32_t* slot = R.cslot + s0;
+            uint32_t* sidx = R.sslot + s0;
+            for (uint32_t j = tid; j < n; j += blockDim.x) {
+                const uint32_t cell = __float_as_uint(rec[j].w) >> 6;
+                const uint32_t seg = R.coff[cell] - s0;
+                const uint32_t m = R.coff[cell + 1] - R.coff[cell];
+                sidx[seg + rank_in_cell(key, seg, m, key[j])] = j;
+            }
+            __syncthreads();
+            for (uint32_t p = tid; p < n; p += blockDim.x) {
+                const uint32_t cell = __float_as_uint(rec[sidx[p]].w) >> 6;
+                const uint32_t seg = R.coff[cell] - s0;
+                const uint32_t m = R.coff[cell + 1] - R.coff[cell];
+                const uint32_t kind = start_kind(p - seg, m);
+                if (kind) ncoll += collide_entry(R, key, rec, slot, sidx, p, m, kind == 2u, step);
+            }
+        }
+        __syncthreads();   // the range's shared memory is reused by the next one
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ncoll += __shfl_down_sync(0xFFFFFFFFu, ncoll, o);
-    if ((threadIdx.x & 31) == 0 && ncoll) atomicAdd(R.tally + kTallyCoulomb, ncoll);
-    // the last block to finish advances the run's step counter
+    if (lane == 0 && ncoll) atomicAdd(&S.ncoll, (unsigned long long)ncoll);
+    __shared__ int s_last;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
+        if (S.ncoll) atomicAdd(R.tally + kTallyCoulomb, S.ncoll);
+        // the last block to finish advances the run's step counter
         __threadfence();
-        const unsigned int prev = atomicAdd(ticket, 1u);
-        s_last = (prev == gridDim.x - 1) ? 1 : 0;
+        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1 : 0;
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
+    if (s_last && tid == 0) {
         *R.step += 1u;
         *ticket = 0u;
     }
@@ -311,8 +389,10 @@ int coulomb_scan_blocks(uint32_t ncells) { return (int)((ncells + kScanBlock - 1
 
 int collide_blocks_per_sm()
 {
+    const int smem = (int)sizeof(CellSmem);
+    if (cudaFuncSetAttribute(k_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs, 256, 0) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cells, 256, smem) != cudaSuccess || b < 1) b = 1;
     return b;
 }
 
@@ -324,8 +404,7 @@ cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t ntiles, un
     k_scan_b<<<1, 1024, 0, s>>>(R, (uint32_t)nb, ncells);
     k_scan_c<<<nb, kScanThreads, 0, s>>>(R, ncells);
     if (ntiles > 0) k_scatter<<<ntiles, 256, 0, s>>>(R, ntiles);
-    k_rank<<<grid, 256, 0, s>>>(R, ncells);
-    k_pairs<<<grid, 256, 0, s>>>(R, ncells, ticket);
+    k_cells<<<grid, 256, sizeof(CellSmem), s>>>(R, ncells, ticket);
     return cudaGetLastError();
 }
 

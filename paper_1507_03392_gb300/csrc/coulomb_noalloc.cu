@@ -14,7 +14,7 @@
 //
 // Limits: at most kNaMaxIons particles and kNaMaxCells cells per call; larger
 // sizes are rejected with ECRIS_EINVAL.  The array (kNaScratchBytes, about
-// 7 MB) is held by every GPU that loads the library until the process exits.
+// 4.5 MB) is held by every GPU that loads the library until the process exits.
 // Every call shares it and finds the last call's contents there; what must
 // start at zero is cleared at the start of each call.  Calls whose GPU work
 // overlaps (different streams, or several host threads) race on the array
@@ -48,15 +48,12 @@ constexpr size_t kOffCoff = kOffCcount + align256(sizeof(uint32_t) * kNaMaxCells
 constexpr size_t kOffCblk = kOffCoff + align256(sizeof(uint32_t) * (kNaMaxCells + 1));
 constexpr size_t kOffCkeys = kOffCblk + align256(sizeof(uint32_t) * (kNaMaxCells / kScanBlock + 1));
 constexpr size_t kOffCrec = kOffCkeys + align256(sizeof(unsigned long long) * kNaMaxIons);
-constexpr size_t kOffSkeys = kOffCrec + align256(sizeof(float4) * kNaMaxIons);
-constexpr size_t kOffSrec = kOffSkeys + align256(sizeof(unsigned long long) * kNaMaxIons);
-constexpr size_t kOffCslot = kOffSrec + align256(sizeof(float4) * kNaMaxIons);
+constexpr size_t kOffCslot = kOffCrec + align256(sizeof(float4) * kNaMaxIons);
 constexpr size_t kOffSslot = kOffCslot + align256(sizeof(uint32_t) * kNaMaxIons);
-constexpr size_t kOffPairs = kOffSslot + align256(sizeof(uint32_t) * kNaMaxIons);
-constexpr size_t kOffTrips = kOffPairs + align256(sizeof(uint2) * (kNaMaxIons / 2 + 1));
-constexpr size_t kOffNanbu = kOffTrips + align256(sizeof(uint2) * (kNaMaxIons / 3 + 1));
+constexpr size_t kOffCstart = kOffSslot + align256(sizeof(uint32_t) * kNaMaxIons);
+constexpr size_t kOffNanbu = kOffCstart + align256(sizeof(uint32_t) * (kNaMaxIons / kCellIons + 2));
 constexpr size_t kOffWords = kOffNanbu + align256(sizeof(float) * kNanbuN);
-// words: step, ticket, pair count, triplet count; then the tally block
+// words: step, ticket; then the tally block
 constexpr size_t kOffTally = kOffWords + 256;
 constexpr size_t kNaScratchBytes = kOffTally + align256(sizeof(unsigned long long) * kTallyWords);
 
@@ -207,15 +204,11 @@ extern "C" ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* 
     R.ccount = reinterpret_cast<uint32_t*>(base + kOffCcount);
     R.coff = reinterpret_cast<uint32_t*>(base + kOffCoff);
     R.cblk = reinterpret_cast<uint32_t*>(base + kOffCblk);
+    R.cstart = reinterpret_cast<uint32_t*>(base + kOffCstart);
     R.ckeys = reinterpret_cast<unsigned long long*>(base + kOffCkeys);
     R.crec = reinterpret_cast<float4*>(base + kOffCrec);
-    R.skeys = reinterpret_cast<unsigned long long*>(base + kOffSkeys);
-    R.srec = reinterpret_cast<float4*>(base + kOffSrec);
     R.cslot = reinterpret_cast<uint32_t*>(base + kOffCslot);
     R.sslot = reinterpret_cast<uint32_t*>(base + kOffSslot);
-    R.pairs = reinterpret_cast<uint2*>(base + kOffPairs);
-    R.trips = reinterpret_cast<uint2*>(base + kOffTrips);
-    R.npt = reinterpret_cast<uint32_t*>(base + kOffWords) + 2;
     R.nanbu = reinterpret_cast<const float*>(base + kOffNanbu);
     R.nanbu_lnlo = (float)std::log(kNanbuSLo);
     R.nanbu_inv_dln = (float)((kNanbuN - 1) / std::log(kNanbuSHi / kNanbuSLo));

@@ -10,9 +10,17 @@
 namespace ecris {
 
 constexpr int kQSlots = 64;            // charge-state slots per tally array
-constexpr int kThreads = 256;          // threads per block of the step kernel
-constexpr int kVec = 4;                // particles per thread (one float4 per SoA array)
-constexpr int kTile = kThreads * kVec; // particles per tile
+#ifndef ECRIS_TILE_VEC
+#define ECRIS_TILE_VEC 4
+#endif
+#ifndef ECRIS_STEP_MIN_BLOCKS
+#define ECRIS_STEP_MIN_BLOCKS 3
+#endif
+constexpr int kThreads = 256;                 // threads per block of the step kernel
+constexpr int kVec = ECRIS_TILE_VEC;          // particles per thread per tile
+constexpr int kTile = kThreads * kVec;        // particles per tile
+constexpr int kTileGroups = kTile / 4;        // float4 groups per tile
+constexpr int kStepMinBlocks = ECRIS_STEP_MIN_BLOCKS;   // resident step-kernel blocks per SM asked of ptxas
 
 // Tally words per run (u64): extracted[64], lost[64], kinetic energy of ions
 // that left (micro-eV), Coulomb pair collisions.
@@ -114,18 +122,16 @@ struct RunDev {
                                  // counted back to zero by the scatter)
     uint32_t *coff;              // exclusive scan of ccount, Nc + 1 entries
     uint32_t *cblk;              // scan block totals
+    uint32_t *cstart;            // first cell of each range of kCellIons participants (collision kernel)
     unsigned long long *ckeys;   // (pairing hash << 32 | pid) per participant, grouped by cell
     float4 *crec;                // (vx, vy, vz, cell << 6 | Q as bits) per participant, grouped by cell
     uint32_t *cslot;             // array slot of each participant, grouped by cell
-    unsigned long long *skeys;   // ckeys in pairing order within each cell
-    float4 *srec;                // crec in pairing order within each cell
-    uint32_t *sslot;             // cslot in pairing order within each cell
-    uint2 *pairs;                // (ordered slot of a pair's first ion, cell count m)
-    uint2 *trips;                // (ordered slot of a triplet's first ion, m) for odd cells
-    uint32_t *npt;               // [0] pairs, [1] triplets listed this step
+    uint32_t *sslot;             // scratch: pairing order of a range of cells too large for shared memory
     const float *nanbu;          // ln A at ln s = nanbu_lnlo + i / nanbu_inv_dln, i < kNanbuN
     float nanbu_lnlo, nanbu_inv_dln;
     uint32_t *step;              // device step counter of the run
+    uint32_t *leave;             // slots of the particles that left the chamber this step
+    uint32_t *nleave;            // their number (zero between steps)
     uint32_t *err;               // device error word: 0, or ECRIS_ETIMEOUT after a bounded wait ran out
     uint32_t n;                  // particles
     uint32_t n4;                 // float4 groups = ceil(n/4)
@@ -256,9 +262,15 @@ __device__ __forceinline__ uint32_t ngp_cell(const RunDev& R, int32_t X, int32_t
 // Launch wrappers (defined in step_kernel.cu / coulomb.cu)
 // ----------------------------------------------------------------------------
 // one pass of the fused step kernel over the run's ntiles tiles of kTile
-// particles; bump_step: the last block advances the run's step counter
-cudaError_t launch_step(const RunDev& R, uint32_t ntiles, unsigned int* ticket, int bump_step, int grid,
-                        cudaStream_t s);
+// particles; the particles that left the chamber are listed in R.leave
+cudaError_t launch_step(const RunDev& R, uint32_t ntiles, int grid, cudaStream_t s);
+// the leaver pass after it: crossing, tallies, re-emission and deposit of the
+// listed particles; the list is cleared; bump_step: advance the step counter
+// (ticket: a zeroed device word, left zero)
+constexpr int kLeaveBlocks = 64;
+cudaError_t launch_leave(const RunDev& R, unsigned int* ticket, int bump_step, cudaStream_t s);
+// the same for every run of a batch (step counters untouched)
+cudaError_t launch_leave_batch(const RunDev* runs, uint32_t nruns, unsigned int* ticket, cudaStream_t s);
 cudaError_t launch_fold(const RunDev& R, uint32_t ncells, unsigned long long* count,
                         unsigned long long* charge, cudaStream_t s);
 // validity limits and padding point for ecris_load_ions
@@ -311,7 +323,9 @@ void ecris_internal_set_thread_error(const char* msg);
 // bump_step = 0): scan of the cell counts, scatter of the pairing keys, and
 // the per-cell sort / pair / collide kernel, whose last block advances the
 // step counter.
-constexpr int kCoulombKernels = 6;   // kernels per launch_coulomb
+constexpr int kCoulombKernels = 5;   // kernels per launch_coulomb
+constexpr int kCellIons = 512;       // participants per range of cells of the collision kernel
+constexpr int kCellCap = 1024;       // participants of a range held in shared memory
 cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t ntiles, unsigned int* ticket, int grid,
                            cudaStream_t s);
 int coulomb_scan_blocks(uint32_t ncells);

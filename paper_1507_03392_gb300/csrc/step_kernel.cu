@@ -1,27 +1,24 @@
-// Fused per-macroparticle time step (push -> boundary test -> MCC -> wall and
-// aperture bookkeeping -> NGP deposition) of the ECRIS model of Mironov et
-// al. (arXiv:1507.03392, Sec. II), plus the deposit fold and the charge-state
-// census used by the diagnostics.
+// Fused per-macroparticle time step (push -> boundary test -> MCC -> NGP
+// deposition) of the ECRIS model of Mironov et al. (arXiv:1507.03392, Sec.
+// II), the wall and aperture bookkeeping of the particles that left the
+// chamber in the step, the deposit fold and the charge-state census used by
+// the diagnostics.
 //
-// Data layout: each run's particles are SoA float arrays x, y, z, vx, vy, vz
-// and a u32 meta word, padded to a multiple of 4 so that one thread moves four
-// particles with one 128-bit load and store per array (56 bytes per particle
-// per step, the whole HBM traffic of the step).  Per-cell data (n_e, zone,
-// delta) and the E grid are float4 records read through L1/L2; the rate table
-// is read through L1.  Tallies go to shared memory first and then to global
-// u64 counters once per tile; the deposit is one packed 64-bit reduction per
-// particle (count in the high word, charge in the low word).
+// Data layout: each run's particles are SoA arrays x, y, z (fixed point), vx,
+// vy, vz, a u32 meta word and a u32 stable id, padded to a multiple of 4.
+// The step kernel streams tiles of them through shared memory with the bulk
+// copy engine.  Per-cell data (n_e, zone, delta) and the E grid are float4
+// records read through L1/L2; the rate table is read through L1.  The deposit
+// is one packed 64-bit reduction per run of lanes in the same cell (count in
+// the high word, charge in the low word).  A particle that leaves the chamber
+// is only listed by the step kernel; a second, small kernel does its crossing
+// geometry (FP64), tallies and re-emission, so the step kernel carries no
+// FP64 code and no per-tile tally traffic.
 #include "ecris_internal.cuh"
 
 namespace ecris {
 
 namespace {
-
-struct BlockTally {
-    unsigned int ext[kQSlots];
-    unsigned int lost[kQSlots];
-    unsigned long long ke;
-};
 
 // Cosine-law re-emission at temperature T0 (full accommodation): normal speed
 // sigma sqrt(-2 ln U0) along the inward normal n, tangential components one
@@ -58,29 +55,67 @@ __device__ __noinline__ Disp far_displacement(float dx, float dy, float dz)
                 __float2ll_rn(fminf(fmaxf(dz, -1e12f), 1e12f))};
 }
 
+// Position after the step's straight move with the (already pushed)
+// velocity, in 64-bit fixed point.  The step kernel and the leaver pass both
+// call this, so they get the same integers.  The displacement is rounded to
+// nearest; below 2^30 units a 32-bit conversion gives the same integer,
+// larger (or non-finite) ones take the bounded 64-bit conversion.
+__device__ __forceinline__ void displace(const RunDev& R, int32_t X, int32_t Y, int32_t Z, float vx, float vy,
+                                         float vz, long long& xn, long long& yn, long long& zn)
+{
+    xn = X;
+    yn = Y;
+    zn = Z;
+    if (!(R.flags & kFPush)) return;
+    const float dx = vx * R.dt_sxy, dy = vy * R.dt_sxy, dz = vz * R.dt_sz;
+    if (fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))) < 1.0e9f) {
+        xn += __float2int_rn(dx);
+        yn += __float2int_rn(dy);
+        zn += __float2int_rn(dz);
+    } else {
+        const Disp d = far_displacement(dx, dy, dz);
+        xn += d.x;
+        yn += d.y;
+        zn += d.z;
+    }
+}
+
+constexpr long long kLim = 2147483648ll;   // 2^31: the fixed-point range
+
+// Boundary test on the new position, exact in fixed point: outside the
+// cylinder wall (r > R0), behind the injection plane (z < 0), past the
+// extraction plane (z >= L).
+__device__ __forceinline__ void outside(long long xn, long long yn, long long zn, bool& out_r, bool& out_0,
+                                        bool& out_L)
+{
+    const bool out_xy = xn < -kLim || xn >= kLim || yn < -kLim || yn >= kLim;
+    out_r = out_xy || (long long)(int32_t)xn * (int32_t)xn + (long long)(int32_t)yn * (int32_t)yn > (1ll << 62);
+    out_0 = zn < -kLim;
+    out_L = zn >= kLim;
+}
+
+__device__ __forceinline__ int32_t clamp_fx(long long v) { return (int32_t)max(min(v, kLim - 1), -kLim); }
+
 // Advance one particle by one step.  pid is its stable id (the Philox counter
-// word).  On return dep_cell is the cell it deposits in (kNoCell if it does
-// not: frozen or padding) and ckey the cell where it takes part in Coulomb
-// collisions (kNoCell if it does not).
-__device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uint32_t step, int32_t& X,
+// word).  On return dep_cell is the cell it deposits in and ckey the cell
+// where it takes part in Coulomb collisions (kNoCell if it does not).  A
+// particle that left the chamber keeps its old position and returns true
+// with its pushed velocity: the leaver pass finishes its step.
+__device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uint32_t step, int32_t& X,
                                               int32_t& Y, int32_t& Z, float& vx, float& vy, float& vz,
-                                              uint32_t& meta, BlockTally& T,
-                                              unsigned long long& ke_acc, uint32_t& ckey,
-                                              uint32_t& dep_cell)
+                                              uint32_t& meta, uint32_t& ckey, uint32_t& dep_cell)
 {
     ckey = kNoCell;
     dep_cell = kNoCell;
     const uint32_t status = meta & 0xFFFF0000u;
     if (status & (kStFrozen | kStPad)) {
         meta = status | (meta & kQMask);   // events of a frozen particle are cleared
-        return;
+        return false;
     }
     uint32_t Q = meta & kQMask;
     uint32_t ev = 0;
-    const float x0 = fx_xy(R, X), y0 = fx_xy(R, Y), z0 = fx_z(R, Z);
 
     // ---- push: Boris rotation for ions, straight line for atoms ----
-    long long xn = X, yn = Y, zn = Z;
     // an ion's cell record is fetched with its field gather, at the old
     // position; the push moves it far less than a cell, so it is reused
     // unless the particle crossed into another cell
@@ -90,196 +125,189 @@ __device__ __forceinline__ void step_particle(const RunDev& R, uint32_t pid, uin
         cell_pre = ngp_cell(R, X, Y, Z);
         cr = __ldg(R.cell + cell_pre);
     }
-    if (R.flags & kFPush) {
-        if (Q > 0) {
-            float Bx, By, Bz, Ex, Ey, Ez;
-            bfield(R, x0, y0, z0, Bx, By, Bz);
-            efield(R, x0, y0, z0, Ex, Ey, Ez);
-            const float h = (float)Q * R.qm_unit * R.half_dt;
-            float mx = vx + h * Ex, my = vy + h * Ey, mz = vz + h * Ez;
-            const float tx = h * Bx, ty = h * By, tz = h * Bz;
-            const float sf = __fdividef(2.0f, 1.0f + tx * tx + ty * ty + tz * tz);
-            const float px = mx + (my * tz - mz * ty);
-            const float py = my + (mz * tx - mx * tz);
-            const float pz = mz + (mx * ty - my * tx);
-            mx += (py * tz - pz * ty) * sf;
-            my += (pz * tx - px * tz) * sf;
-            mz += (px * ty - py * tx) * sf;
-            vx = mx + h * Ex;
-            vy = my + h * Ey;
-            vz = mz + h * Ez;
-        }
-        // displacement in fixed-point units, rounded to nearest.  Below 2^30
-        // units a 32-bit conversion gives the same integer; larger (or
-        // non-finite) displacements take the 64-bit conversion, bounded so a
-        // runaway velocity cannot wrap the 64-bit sums
-        const float dx = vx * R.dt_sxy, dy = vy * R.dt_sxy, dz = vz * R.dt_sz;
-        if (fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))) < 1.0e9f) {
-            xn += __float2int_rn(dx);
-            yn += __float2int_rn(dy);
-            zn += __float2int_rn(dz);
-        } else {
-            const Disp d = far_displacement(dx, dy, dz);
-            xn += d.x;
-            yn += d.y;
-            zn += d.z;
-        }
+    if ((R.flags & kFPush) && Q > 0) {
+        const float x0 = fx_xy(R, X), y0 = fx_xy(R, Y), z0 = fx_z(R, Z);
+        float Bx, By, Bz, Ex, Ey, Ez;
+        bfield(R, x0, y0, z0, Bx, By, Bz);
+        efield(R, x0, y0, z0, Ex, Ey, Ez);
+        const float h = (float)Q * R.qm_unit * R.half_dt;
+        float mx = vx + h * Ex, my = vy + h * Ey, mz = vz + h * Ez;
+        const float tx = h * Bx, ty = h * By, tz = h * Bz;
+        const float sf = __fdividef(2.0f, 1.0f + tx * tx + ty * ty + tz * tz);
+        const float px = mx + (my * tz - mz * ty);
+        const float py = my + (mz * tx - mx * tz);
+        const float pz = mz + (mx * ty - my * tx);
+        mx += (py * tz - pz * ty) * sf;
+        my += (pz * tx - px * tz) * sf;
+        mz += (px * ty - py * tx) * sf;
+        vx = mx + h * Ex;
+        vy = my + h * Ey;
+        vz = mz + h * Ez;
     }
+    long long xn, yn, zn;
+    displace(R, X, Y, Z, vx, vy, vz, xn, yn, zn);
 
     // cell record and random words of the new position, fetched before the
     // boundary test so their latency overlaps it (leavers discard them)
-    const long long lim = 2147483648ll;   // 2^31
-    const int32_t Xc = (int32_t)max(min(xn, lim - 1), -lim);
-    const int32_t Yc = (int32_t)max(min(yn, lim - 1), -lim);
-    const int32_t Zc = (int32_t)max(min(zn, lim - 1), -lim);
-    uint32_t cell = ngp_cell(R, Xc, Yc, Zc);
+    const int32_t Xc = clamp_fx(xn), Yc = clamp_fx(yn), Zc = clamp_fx(zn);
+    const uint32_t cell = ngp_cell(R, Xc, Yc, Zc);
     const Words w = rng_words(R, pid, step, 0u);
 
-    // ---- boundary test on the new position, exact in fixed point ----
-    const bool out_xy = xn < -lim || xn >= lim || yn < -lim || yn >= lim;
-    const bool out_r = out_xy || (long long)(int32_t)xn * (int32_t)xn + (long long)(int32_t)yn * (int32_t)yn >
-                                     (1ll << 62);
-    const bool out_0 = zn < -lim;
-    const bool out_L = zn >= lim;
+    bool out_r, out_0, out_L;
+    outside(xn, yn, zn, out_r, out_0, out_L);
     if (out_r | out_0 | out_L) {
-        // first crossing along the straight segment, in FP64 from the exact
-        // fixed-point coordinates (leavers are rare, so the cost is small)
-        const double sxy = R.sxy_d, szd = R.sz_d;
-        const double dx0 = (double)X * sxy, dy0 = (double)Y * sxy, dz0 = ((double)Z + 2147483648.0) * szd;
-        const double ddx = (double)(xn - X) * sxy, ddy = (double)(yn - Y) * sxy, ddz = (double)(zn - Z) * szd;
-        double fbest = 2.0;
-        int kind = 0;
-        if (out_r) {
-            // |p0 + f d|^2 = R0^2 with c = |p0|^2 - R0^2 <= 0, taken exactly in fixed point
-            const double a = ddx * ddx + ddy * ddy, b = dx0 * ddx + dy0 * ddy;
-            const double c = (double)((long long)X * X + (long long)Y * Y - (1ll << 62)) * sxy * sxy;
-            const double disc = sqrt(fmax(0.0, b * b - a * c));
-            double f = (b + disc > 0.0) ? -c / (b + disc) : 0.0;
-            f = fmax(f, 0.0);
-            fbest = f;
-            kind = 1;
-        }
-        if (out_0) {
-            const double f = (double)((long long)Z + lim) / (double)((long long)Z - zn);
-            if (f < fbest) { fbest = f; kind = 2; }
-        }
-        if (out_L) {
-            const double f = (double)(lim - (long long)Z) / (double)(zn - (long long)Z);
-            if (f < fbest) { fbest = f; kind = 3; }
-        }
-        double cxd = dx0 + fbest * ddx, cyd = dy0 + fbest * ddy, czd = dz0 + fbest * ddz;
-        if (kind == 3 && cxd * cxd + cyd * cyd < R.r_ap_d * R.r_ap_d) kind = 4;
-
-        // ---- wall / aperture bookkeeping ----
-        if (Q >= 1) ke_acc += __float2ull_rn(R.ke_scale * (vx * vx + vy * vy + vz * vz));
-        if (kind == 4) {
-            atomicAdd(&T.ext[Q], 1u);
-            ev |= kEvExtract;
-        } else {
-            atomicAdd(&T.lost[Q], 1u);
-            ev |= kEvWall;
-        }
-        Q = 0;
-        if (!(R.flags & kFRecycle)) {
-            // frozen at its last position, clamped into the fixed-point range
-            X = Xc;
-            Y = Yc;
-            Z = Zc;
-            meta = status | kStFrozen | ev;
-            return;
-        }
-        const Words u = rng_words(R, pid, step, 2u);
-        if (kind == 4) {
-            X = R.inlet_X; Y = R.inlet_Y; Z = R.inlet_Z;
-            emit(R.sig0, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, u, vx, vy, vz);
-        } else if (kind == 1) {
-            const double rc = sqrt(cxd * cxd + cyd * cyd);
-            const float ux = (float)(cxd / rc), uy = (float)(cyd / rc);
-            const double sc = (R.R0_d - R.eps_wall_d) / rc;
-            X = (int32_t)rint(cxd * sc / sxy);
-            Y = (int32_t)rint(cyd * sc / sxy);
-            Z = (int32_t)(long long)rint(czd / szd - 2147483648.0);
-            emit(R.sig0, -ux, -uy, 0.f, -uy, ux, 0.f, 0.f, 0.f, 1.f, u, vx, vy, vz);
-        } else if (kind == 2) {
-            X = (int32_t)rint(cxd / sxy);
-            Y = (int32_t)rint(cyd / sxy);
-            Z = (int32_t)(long long)rint(R.eps_wall_d / szd - 2147483648.0);
-            emit(R.sig0, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, u, vx, vy, vz);
-        } else {
-            X = (int32_t)rint(cxd / sxy);
-            Y = (int32_t)rint(cyd / sxy);
-            Z = (int32_t)(long long)rint((R.L_d - R.eps_wall_d) / szd - 2147483648.0);
-            emit(R.sig0, 0.f, 0.f, -1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, u, vx, vy, vz);
-        }
-        cell = ngp_cell(R, X, Y, Z);
-    } else {
-        // ---- MCC in the particle's cell ----
-        X = Xc;
-        Y = Yc;
-        Z = Zc;
-        // an atom needs its cell only if its ionisation word could fire in
-        // the densest cell; otherwise no cell can ionise it this step
-        const bool ionize = (R.flags & kFIonize) && (int)Q < R.qmax;
-        const bool need = Q > 0 || (ionize && (w.w0 < R.atom_gate || R.atom_gate == 0xFFFFFFFFu));
-        if (need && cell != cell_pre) cr = __ldg(R.cell + cell);   // n_e, zone, delta_x, delta_y
-        const int zone = cr.y > 0.5f ? 1 : 0;
-        if (ionize && need) {
-            const float lam = cr.x * __ldg(R.kdt + zone * kQSlots + Q);
-            if (fires(w.w0, event_prob(lam))) { Q += 1; ev |= kEvIonize; }
-        }
-        if ((R.flags & kFCx) && R.n0s1 > 0.0f && Q >= 1 && Q != 2) {
-            const float vrel = sqrtf(vx * vx + vy * vy + vz * vz + R.vth2);
-            const float p = event_prob(R.n0s1 * (float)Q * vrel * R.dt);
-            if (fires(w.w1, p)) {
-                const Words u = rng_words(R, pid, step, 3u);
-                ev |= kEvCx;
-                if (Q == 1) {
-                    float s1, c1, s2, c2;
-                    const float r1 = R.sig0 * sqrtf(-2.0f * logf(unit01(u.w0)));
-                    sincospif(2.0f * unit01(u.w1), &s1, &c1);
-                    const float r2 = R.sig0 * sqrtf(-2.0f * logf(unit01(u.w2)));
-                    sincospif(2.0f * unit01(u.w3), &s2, &c2);
-                    vx = r1 * c1; vy = r1 * s1; vz = r2 * c2;
-                } else {
-                    const float ct = 2.0f * unit01(u.w0) - 1.0f;
-                    const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
-                    float sp, cp;
-                    sincospif(2.0f * unit01(u.w1), &sp, &cp);
-                    vx += R.dv_cx * st * cp;
-                    vy += R.dv_cx * st * sp;
-                    vz += R.dv_cx * ct;
-                    Q -= 1;
-                }
-            }
-        }
-        if ((R.flags & kFEikick) && Q >= 1) {
-            const float qp = R.ei_pow == 1 ? (float)Q : (float)(Q * Q);
-            const float D = sqrtf(R.ei_coef[zone] * cr.x * qp);
-            const float ct = 2.0f * unit01(w.w2) - 1.0f;
-            const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
-            float sp, cp;
-            sincospif(2.0f * unit01(w.w3), &sp, &cp);
-            const float dxv = st * cp + cr.z, dyv = st * sp + cr.w, dzv = ct;
-            const float m2 = dxv * dxv + dyv * dyv + dzv * dzv;
-            if (m2 > 0.0f) {
-                const float k = D * rsqrtf(m2);
-                vx += k * dxv;
-                vy += k * dyv;
-                vz += k * dzv;
-            }
-        }
-        if (Q >= 1 && (R.flags & kFCoulomb)) ckey = cell;
+        meta = status | Q;
+        return true;
     }
 
-    dep_cell = cell;   // NGP deposition at the final position (warp-aggregated by the caller)
+    // ---- MCC in the particle's cell ----
+    X = Xc;
+    Y = Yc;
+    Z = Zc;
+    // an atom needs its cell only if its ionisation word could fire in
+    // the densest cell; otherwise no cell can ionise it this step
+    const bool ionize = (R.flags & kFIonize) && (int)Q < R.qmax;
+    const bool need = Q > 0 || (ionize && (w.w0 < R.atom_gate || R.atom_gate == 0xFFFFFFFFu));
+    if (need && cell != cell_pre) cr = __ldg(R.cell + cell);   // n_e, zone, delta_x, delta_y
+    const int zone = cr.y > 0.5f ? 1 : 0;
+    if (ionize && need) {
+        const float lam = cr.x * __ldg(R.kdt + zone * kQSlots + Q);
+        if (fires(w.w0, event_prob(lam))) { Q += 1; ev |= kEvIonize; }
+    }
+    if ((R.flags & kFCx) && R.n0s1 > 0.0f && Q >= 1 && Q != 2) {
+        const float vrel = sqrtf(vx * vx + vy * vy + vz * vz + R.vth2);
+        const float p = event_prob(R.n0s1 * (float)Q * vrel * R.dt);
+        if (fires(w.w1, p)) {
+            const Words u = rng_words(R, pid, step, 3u);
+            ev |= kEvCx;
+            if (Q == 1) {
+                float s1, c1, s2, c2;
+                const float r1 = R.sig0 * sqrtf(-2.0f * logf(unit01(u.w0)));
+                sincospif(2.0f * unit01(u.w1), &s1, &c1);
+                const float r2 = R.sig0 * sqrtf(-2.0f * logf(unit01(u.w2)));
+                sincospif(2.0f * unit01(u.w3), &s2, &c2);
+                vx = r1 * c1; vy = r1 * s1; vz = r2 * c2;
+            } else {
+                const float ct = 2.0f * unit01(u.w0) - 1.0f;
+                const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+                float sp, cp;
+                sincospif(2.0f * unit01(u.w1), &sp, &cp);
+                vx += R.dv_cx * st * cp;
+                vy += R.dv_cx * st * sp;
+                vz += R.dv_cx * ct;
+                Q -= 1;
+            }
+        }
+    }
+    if ((R.flags & kFEikick) && Q >= 1) {
+        const float qp = R.ei_pow == 1 ? (float)Q : (float)(Q * Q);
+        const float D = sqrtf(R.ei_coef[zone] * cr.x * qp);
+        const float ct = 2.0f * unit01(w.w2) - 1.0f;
+        const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+        float sp, cp;
+        sincospif(2.0f * unit01(w.w3), &sp, &cp);
+        const float dxv = st * cp + cr.z, dyv = st * sp + cr.w, dzv = ct;
+        const float m2 = dxv * dxv + dyv * dyv + dzv * dzv;
+        if (m2 > 0.0f) {
+            const float k = D * rsqrtf(m2);
+            vx += k * dxv;
+            vy += k * dyv;
+            vz += k * dzv;
+        }
+    }
+    if (Q >= 1 && (R.flags & kFCoulomb)) ckey = cell;
+    dep_cell = cell;   // NGP deposition at the final position (aggregated over the warp by the caller)
     meta = status | ev | Q;
+    return false;
 }
 
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+// Finish the step of a particle that left the chamber (the step kernel kept
+// its old position X, Y, Z and its pushed velocity): the first crossing of
+// the straight segment with the wall, the injection plane or the extraction
+// plane, in FP64 from the exact fixed-point coordinates; the extracted / lost
+// tallies and the energy carried to the wall; then re-emission (cosine law at
+// T0 from the crossing point, or from the inlet after extraction) or, without
+// recycling, freezing.  Returns the cell it deposits in (kNoCell if frozen).
+__device__ __forceinline__ uint32_t leave_particle(const RunDev& R, uint32_t pid, uint32_t step, int32_t& X,
+                                                   int32_t& Y, int32_t& Z, float& vx, float& vy, float& vz,
+                                                   uint32_t& meta)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-    return v;
+    const uint32_t status = meta & 0xFFFF0000u;
+    const uint32_t Q = meta & kQMask;
+    long long xn, yn, zn;
+    displace(R, X, Y, Z, vx, vy, vz, xn, yn, zn);
+    bool out_r, out_0, out_L;
+    outside(xn, yn, zn, out_r, out_0, out_L);
+
+    const double sxy = R.sxy_d, szd = R.sz_d;
+    const double dx0 = (double)X * sxy, dy0 = (double)Y * sxy, dz0 = ((double)Z + 2147483648.0) * szd;
+    const double ddx = (double)(xn - X) * sxy, ddy = (double)(yn - Y) * sxy, ddz = (double)(zn - Z) * szd;
+    double fbest = 2.0;
+    int kind = 0;
+    if (out_r) {
+        // |p0 + f d|^2 = R0^2 with c = |p0|^2 - R0^2 <= 0, taken exactly in fixed point
+        const double a = ddx * ddx + ddy * ddy, b = dx0 * ddx + dy0 * ddy;
+        const double c = (double)((long long)X * X + (long long)Y * Y - (1ll << 62)) * sxy * sxy;
+        const double disc = sqrt(fmax(0.0, b * b - a * c));
+        double f = (b + disc > 0.0) ? -c / (b + disc) : 0.0;
+        f = fmax(f, 0.0);
+        fbest = f;
+        kind = 1;
+    }
+    if (out_0) {
+        const double f = (double)((long long)Z + kLim) / (double)((long long)Z - zn);
+        if (f < fbest) { fbest = f; kind = 2; }
+    }
+    if (out_L) {
+        const double f = (double)(kLim - (long long)Z) / (double)(zn - (long long)Z);
+        if (f < fbest) { fbest = f; kind = 3; }
+    }
+    const double cxd = dx0 + fbest * ddx, cyd = dy0 + fbest * ddy, czd = dz0 + fbest * ddz;
+    if (kind == 3 && cxd * cxd + cyd * cyd < R.r_ap_d * R.r_ap_d) kind = 4;
+
+    // ---- wall / aperture bookkeeping ----
+    if (Q >= 1) atomicAdd(R.tally + kTallyKe, __float2ull_rn(R.ke_scale * (vx * vx + vy * vy + vz * vz)));
+    uint32_t ev;
+    if (kind == 4) {
+        atomicAdd(R.tally + kTallyExtracted + Q, 1ull);
+        ev = kEvExtract;
+    } else {
+        atomicAdd(R.tally + kTallyLost + Q, 1ull);
+        ev = kEvWall;
+    }
+    if (!(R.flags & kFRecycle)) {
+        // frozen at its last position, clamped into the fixed-point range
+        X = clamp_fx(xn);
+        Y = clamp_fx(yn);
+        Z = clamp_fx(zn);
+        meta = status | kStFrozen | ev;
+        return kNoCell;
+    }
+    const Words u = rng_words(R, pid, step, 2u);
+    if (kind == 4) {
+        X = R.inlet_X; Y = R.inlet_Y; Z = R.inlet_Z;
+        emit(R.sig0, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, u, vx, vy, vz);
+    } else if (kind == 1) {
+        const double rc = sqrt(cxd * cxd + cyd * cyd);
+        const float ux = (float)(cxd / rc), uy = (float)(cyd / rc);
+        const double sc = (R.R0_d - R.eps_wall_d) / rc;
+        X = (int32_t)rint(cxd * sc / sxy);
+        Y = (int32_t)rint(cyd * sc / sxy);
+        Z = (int32_t)(long long)rint(czd / szd - 2147483648.0);
+        emit(R.sig0, -ux, -uy, 0.f, -uy, ux, 0.f, 0.f, 0.f, 1.f, u, vx, vy, vz);
+    } else if (kind == 2) {
+        X = (int32_t)rint(cxd / sxy);
+        Y = (int32_t)rint(cyd / sxy);
+        Z = (int32_t)(long long)rint(R.eps_wall_d / szd - 2147483648.0);
+        emit(R.sig0, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, u, vx, vy, vz);
+    } else {
+        X = (int32_t)rint(cxd / sxy);
+        Y = (int32_t)rint(cyd / sxy);
+        Z = (int32_t)(long long)rint((R.L_d - R.eps_wall_d) / szd - 2147483648.0);
+        emit(R.sig0, 0.f, 0.f, -1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, u, vx, vy, vz);
+    }
+    meta = status | ev;   // Q = 0: the particle comes back as an atom
+    return ngp_cell(R, X, Y, Z);
 }
 
 // ---------------------------------------------------------------------------
@@ -342,18 +370,16 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 
 // One stage of the tile pipeline: SoA copies of a tile's particles.
 struct Stage {
-    int4 x[kThreads], y[kThreads], z[kThreads];
-    float4 vx[kThreads], vy[kThreads], vz[kThreads];
-    uint4 meta[kThreads];
-    uint4 id[kThreads];
+    int4 x[kTileGroups], y[kTileGroups], z[kTileGroups];
+    float4 vx[kTileGroups], vy[kTileGroups], vz[kTileGroups];
+    uint4 meta[kTileGroups];
+    uint4 id[kTileGroups];
 };
 
 struct StepShared {
     Stage st[2];
     uint32_t npart;
-    BlockTally T;
     uint64_t bar[2];
-    int last;
     int failed;
 };
 
@@ -364,8 +390,8 @@ __device__ __forceinline__ int32_t& si(int4* a, uint32_t i) { return reinterpret
 // issue the eight bulk loads of tile t into stage st (thread 0 only)
 __device__ __forceinline__ void load_tile(const RunDev& R, Stage& st, uint64_t* bar, uint32_t t)
 {
-    const uint32_t g0 = t * kThreads;
-    const uint32_t ng = min((uint32_t)kThreads, R.n4 - g0);
+    const uint32_t g0 = t * kTileGroups;
+    const uint32_t ng = min((uint32_t)kTileGroups, R.n4 - g0);
     const uint32_t bytes = ng * 16u;
     mbar_expect_tx(bar, 8u * bytes);
     bulk_load(st.x, reinterpret_cast<const int4*>(R.x) + g0, bytes, bar);
@@ -407,7 +433,8 @@ __device__ __forceinline__ void deposit_warp(const RunDev& R, uint32_t cell, uin
 
 // Publish this lane's Coulomb participant (ck != kNoCell) for the collision
 // kernels: a slot in the tile's list (one shared-memory atomic per warp) and
-// a count in its cell (one global reduction per group of lanes in a cell)
+// a count in its cell (one global reduction per run of neighbouring lanes in
+// the same cell; the whole warp calls this)
 __device__ __forceinline__ void publish_warp(const RunDev& R, uint32_t& npart, uint32_t t, uint32_t slot_in_run,
                                              uint32_t ck, uint32_t id, float vx, float vy, float vz, uint32_t Q)
 {
@@ -417,12 +444,17 @@ __device__ __forceinline__ void publish_warp(const RunDev& R, uint32_t& npart, u
     uint32_t base = 0;
     if (lane == (uint32_t)(__ffs(part) - 1)) base = atomicAdd(&npart, (uint32_t)__popc(part));
     base = __shfl_sync(0xFFFFFFFFu, base, __ffs(part) - 1);
+    const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, ck, 1);
+    const uint32_t heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || prev != ck);
     if (ck == kNoCell) return;
     const uint32_t slot = t * kTile + base + (uint32_t)__popc(part & ((1u << lane) - 1u));
     R.plist[slot] = make_uint4(slot_in_run, ck, id, 0u);
     R.pvel[slot] = make_float4(vx, vy, vz, __uint_as_float(Q));
-    const uint32_t grp = __match_any_sync(part, ck);
-    if (lane == (uint32_t)(__ffs(grp) - 1)) atomicAdd(R.ccount + ck, (uint32_t)__popc(grp));
+    // every lane of a run shares ck, so all of them take part
+    if (lane == 31 || ((heads >> (lane + 1)) & 1u)) {
+        const uint32_t h = 31u - (uint32_t)__clz(heads & (0xFFFFFFFFu >> (31u - lane)));
+        atomicAdd(R.ccount + ck, lane - h + 1u);
+    }
 }
 
 // Where the tiles come from: one run (its parameter block a kernel argument)
@@ -451,9 +483,21 @@ struct BatchRuns {
 // into the other stage; results leave through bulk stores.  The particles are
 // kept sorted by (ion/atom, cell), so each thread takes slots tid, tid + 256,
 // ... straight from the stage and the warps stay on one branch.
+// List the particles of this lane that left the chamber (leave) for the
+// leaver pass: one global atomic per warp.
+__device__ __forceinline__ void list_leavers(const RunDev& R, bool leave, uint32_t slot)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, leave);
+    if (!m) return;
+    uint32_t base = 0;
+    if (lane == (uint32_t)(__ffs(m) - 1)) base = atomicAdd(R.nleave, (uint32_t)__popc(m));
+    base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m) - 1);
+    if (leave) R.leave[base + (uint32_t)__popc(m & ((1u << lane) - 1u))] = slot;
+}
+
 template <bool kBatch, class Src>
-__device__ __forceinline__ void step_tiles(StepShared& S, RunDev* Rs, const Src& src, unsigned int* ticket,
-                                           int bump_step)
+__device__ __forceinline__ void step_tiles(StepShared& S, RunDev* Rs, const Src& src)
 {
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) {
@@ -487,11 +531,7 @@ __device__ __forceinline__ void step_tiles(StepShared& S, RunDev* Rs, const Src&
             for (uint32_t w = tid; w < sizeof(RunDev) / 4; w += kThreads) d[w] = g[w];
             cur_run = item.x;
         }
-        for (int k = tid; k < kQSlots; k += kThreads) { S.T.ext[k] = 0u; S.T.lost[k] = 0u; }
-        if (tid == 0) {
-            S.T.ke = 0ull;
-            S.npart = 0u;
-        }
+        if (tid == 0) S.npart = 0u;
         if (!mbar_wait(&S.bar[s], (it >> 1) & 1u)) S.failed = 1;
         __syncthreads();
         if (S.failed) break;
@@ -499,9 +539,8 @@ __device__ __forceinline__ void step_tiles(StepShared& S, RunDev* Rs, const Src&
         const bool coulomb = (R.flags & kFCoulomb) != 0;
         const uint32_t step = *R.step;
         const uint32_t t = item.y;
-        const uint32_t nslot = min((uint32_t)kTile, 4u * (R.n4 - t * kThreads));
-        unsigned long long ke = 0ull;
-        // thread tid takes slots tid, tid + 256, tid + 512, tid + 768 of the
+        const uint32_t nslot = min((uint32_t)kTile, 4u * (R.n4 - t * kTileGroups));
+        // thread tid takes slots tid, tid + 256, ... (kVec of them) of the
         // tile: a warp covers 32 consecutive slots (one kind of particle, few
         // cells), the shared-memory accesses are free of bank conflicts, and
         // every particle runs through the same single copy of the code
@@ -513,8 +552,9 @@ __device__ __forceinline__ void step_tiles(StepShared& S, RunDev* Rs, const Src&
             float vx = sf(st.vx, k), vy = sf(st.vy, k), vz = sf(st.vz, k);
             const uint32_t id = su(st.id, k);
             uint32_t ck, dc;
-            step_particle(R, id, step, x, y, z, vx, vy, vz, meta, S.T, ke, ck, dc);
+            const bool leave = step_particle(R, id, step, x, y, z, vx, vy, vz, meta, ck, dc);
             deposit_warp(R, dc, meta & kQMask);
+            list_leavers(R, leave, t * kTile + k);
             if (k < nslot) {
                 si(st.x, k) = x; si(st.y, k) = y; si(st.z, k) = z;
                 sf(st.vx, k) = vx; sf(st.vy, k) = vy; sf(st.vz, k) = vz;
@@ -522,13 +562,11 @@ __device__ __forceinline__ void step_tiles(StepShared& S, RunDev* Rs, const Src&
             }
             if (coulomb) publish_warp(R, S.npart, t, t * kTile + k, ck, id, vx, vy, vz, meta & kQMask);
         }
-        ke = warp_sum(ke);
-        if (lane == 0 && ke) atomicAdd(&S.T.ke, ke);
         fence_proxy_async();    // make this thread's stage writes visible to the bulk stores
         __syncthreads();
         if (tid == 0) {
-            const uint32_t g0 = t * kThreads;
-            const uint32_t bytes = min((uint32_t)kThreads, R.n4 - g0) * 16u;
+            const uint32_t g0 = t * kTileGroups;
+            const uint32_t bytes = min((uint32_t)kTileGroups, R.n4 - g0) * 16u;
             bulk_store(reinterpret_cast<int4*>(R.x) + g0, st.x, bytes);
             bulk_store(reinterpret_cast<int4*>(R.y) + g0, st.y, bytes);
             bulk_store(reinterpret_cast<int4*>(R.z) + g0, st.z, bytes);
@@ -539,11 +577,6 @@ __device__ __forceinline__ void step_tiles(StepShared& S, RunDev* Rs, const Src&
             bulk_commit();
             if (coulomb) R.tcount[t] = S.npart;
         }
-        for (int k = tid; k < kQSlots; k += kThreads) {
-            if (S.T.ext[k]) atomicAdd(R.tally + kTallyExtracted + k, (unsigned long long)S.T.ext[k]);
-            if (S.T.lost[k]) atomicAdd(R.tally + kTallyLost + k, (unsigned long long)S.T.lost[k]);
-        }
-        if (tid == 0 && S.T.ke) atomicAdd(R.tally + kTallyKe, S.T.ke);
         __syncthreads();
     }
     if (tid == 0) {
@@ -555,37 +588,89 @@ __device__ __forceinline__ void step_tiles(StepShared& S, RunDev* Rs, const Src&
             mbar_wait(&S.bar[1], 0u);
         }
     }
-    if (!kBatch && bump_step) {
-        // the last block to finish advances the run's step counter
-        if (tid == 0) {
-            __threadfence();
-            const unsigned int prev = atomicAdd(ticket, 1u);
-            S.last = (prev == gridDim.x - 1) ? 1 : 0;
-        }
-        __syncthreads();
-        if (S.last && tid == 0) {
-            *src.global(0).step += 1u;
-            *ticket = 0u;
-        }
-    }
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_step(const __grid_constant__ RunDev R, uint32_t ntiles,
-                                                      unsigned int* ticket, int bump_step)
+__global__ void __launch_bounds__(kThreads, kStepMinBlocks) k_step(const __grid_constant__ RunDev R, uint32_t ntiles)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     StepShared& S = *reinterpret_cast<StepShared*>(smem_raw);
-    step_tiles<false>(S, nullptr, SingleRun{R, ntiles}, ticket, bump_step);
+    step_tiles<false>(S, nullptr, SingleRun{R, ntiles});
 }
 
 // batch form: one persistent launch over the tiles of many runs
-__global__ void __launch_bounds__(kThreads, 3) k_step_batch(const RunDev* __restrict__ runs,
+__global__ void __launch_bounds__(kThreads, kStepMinBlocks) k_step_batch(const RunDev* __restrict__ runs,
                                                             const uint2* __restrict__ items, uint32_t nitems)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     StepShared& S = *reinterpret_cast<StepShared*>(smem_raw);
     RunDev* Rs = reinterpret_cast<RunDev*>(smem_raw + ((sizeof(StepShared) + 15) & ~(size_t)15));
-    step_tiles<true>(S, Rs, BatchRuns{runs, items, nitems}, nullptr, 0);
+    step_tiles<true>(S, Rs, BatchRuns{runs, items, nitems});
+}
+
+// The leaver pass of one run: finish the step of every listed particle, add
+// its deposit, and clear the list.  Threads [tid0, tid0 + nthr) of the grid
+// share the work.
+__device__ __forceinline__ void leave_run(const RunDev& R, uint32_t n, uint32_t tid0, uint32_t nthr)
+{
+    const uint32_t step = *R.step;
+    for (uint32_t e = tid0; e < n; e += nthr) {
+        const uint32_t i = R.leave[e];
+        int32_t X = R.x[i], Y = R.y[i], Z = R.z[i];
+        float vx = R.vx[i], vy = R.vy[i], vz = R.vz[i];
+        uint32_t meta = R.meta[i];
+        const uint32_t cell = leave_particle(R, R.id[i], step, X, Y, Z, vx, vy, vz, meta);
+        if (cell != kNoCell) atomicAdd(R.dep + cell, 1ull << 32);   // Q = 0: count only
+        R.x[i] = X;
+        R.y[i] = Y;
+        R.z[i] = Z;
+        R.vx[i] = vx;
+        R.vy[i] = vy;
+        R.vz[i] = vz;
+        R.meta[i] = meta;
+    }
+}
+
+// last block of a grid (after every block's work is visible): ticket reset
+__device__ __forceinline__ bool last_block(unsigned int* ticket)
+{
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1 : 0;
+        if (last) *ticket = 0u;
+    }
+    __syncthreads();
+    return last != 0;
+}
+
+// one run; the last block clears the list and, with bump_step, advances the
+// run's step counter (runs with Coulomb collisions advance it in the
+// collision kernels)
+__global__ void __launch_bounds__(256) k_leave(const __grid_constant__ RunDev R, unsigned int* ticket, int bump_step)
+{
+    const uint32_t n = *R.nleave;
+    leave_run(R, n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    if (last_block(ticket) && threadIdx.x == 0) {
+        *R.nleave = 0u;
+        if (bump_step) *R.step += 1u;
+    }
+}
+
+// every run of a batch: block b takes runs b, b + grid, ...; the last block
+// clears the lists (step counters are left to k_bump_steps and the collision
+// kernels)
+__global__ void __launch_bounds__(256) k_leave_batch(const RunDev* __restrict__ runs, uint32_t nruns,
+                                                     unsigned int* ticket)
+{
+    for (uint32_t r = blockIdx.x; r < nruns; r += gridDim.x) {
+        const RunDev& R = runs[r];
+        if (!R.step) continue;
+        leave_run(R, *R.nleave, threadIdx.x, blockDim.x);
+    }
+    if (last_block(ticket))
+        for (uint32_t r = threadIdx.x; r < nruns; r += blockDim.x)
+            if (runs[r].step) *runs[r].nleave = 0u;
 }
 
 // advance the step counter of every run of a batch without Coulomb
@@ -732,12 +817,25 @@ cudaError_t launch_bump_steps(const RunDev* runs, uint32_t nruns, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(const RunDev& R, uint32_t ntiles, unsigned int* ticket, int bump_step, int grid,
-                        cudaStream_t s)
+cudaError_t launch_step(const RunDev& R, uint32_t ntiles, int grid, cudaStream_t s)
 {
     if (ntiles == 0) return cudaSuccess;
     if (grid > (int)ntiles) grid = (int)ntiles;
-    k_step<<<grid, kThreads, sizeof(StepShared), s>>>(R, ntiles, ticket, bump_step);
+    k_step<<<grid, kThreads, sizeof(StepShared), s>>>(R, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leave(const RunDev& R, unsigned int* ticket, int bump_step, cudaStream_t s)
+{
+    k_leave<<<kLeaveBlocks, 256, 0, s>>>(R, ticket, bump_step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leave_batch(const RunDev* runs, uint32_t nruns, unsigned int* ticket, cudaStream_t s)
+{
+    if (nruns == 0) return cudaSuccess;
+    k_leave_batch<<<nruns < (uint32_t)kLeaveBlocks ? nruns : (uint32_t)kLeaveBlocks, 256, 0, s>>>(runs, nruns,
+                                                                                                     ticket);
     return cudaGetLastError();
 }
 

@@ -1,8 +1,9 @@
 """GPU parity of the Coulomb collision kernels (Takizawa-Abe pairing, Nanbu
 angle) with the FP64 oracle, through the C ABI.
 
-Cells hold 1 to several thousand ions so that the register, shared-memory
-and global-memory sorting paths of the pairing kernel all run; every pairing
+Cells hold 1 to several thousand ions so that both the shared-memory path of
+the collision kernel and its global-memory path (a range of cells larger than
+shared memory holds) run, with ranges that split anywhere; every pairing
 must be identical to the oracle's (integer events and collision counts) and
 the velocities must agree to the FP32 rounding of the collision arithmetic.
 """
