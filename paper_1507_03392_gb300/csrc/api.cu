@@ -254,7 +254,7 @@ struct ecris_ctx {
     uint32_t* d_ccount = nullptr;
     uint32_t* d_cstart = nullptr;
     uint32_t* d_coff = nullptr;
-    uint32_t* d_cblk = nullptr;
+    unsigned long long* d_cstat = nullptr;   // scan tile status words and ticket counter
     unsigned long long* d_ckeys = nullptr;
     int collide_grid = 0;
     // two sets of particle arrays; the sort moves the particles from the
@@ -381,7 +381,7 @@ void free_ions(ecris_ctx* ctx)
     free_async(ctx, ctx->d_ccount);
     free_async(ctx, ctx->d_cstart);
     free_async(ctx, ctx->d_coff);
-    free_async(ctx, ctx->d_cblk);
+    free_async(ctx, ctx->d_cstat);
     free_async(ctx, ctx->d_ckeys);
     ctx->have_ions = false;
     ctx->loaded = false;
@@ -489,7 +489,8 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.ccount = ctx->d_ccount;
     R.cstart = ctx->d_cstart;
     R.coff = ctx->d_coff;
-    R.cblk = ctx->d_cblk;
+    R.cstat = ctx->d_cstat;
+    R.cctr = ctx->d_cstat ? ctx->d_cstat + coulomb_scan_blocks((uint32_t)ctx->cap_cells) : nullptr;
     R.ckeys = ctx->d_ckeys;
     R.cslot = ctx->d_cslot;
     R.sslot = ctx->d_sslot;
@@ -871,7 +872,7 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
             CK(cudaMallocAsync((void**)&ctx->d_ccount, nc * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_cstart, (cap / kCellIons + 2) * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_coff, (nc + 1) * sizeof(uint32_t), ctx->stream));
-            CK(cudaMallocAsync((void**)&ctx->d_cblk, (size_t)coulomb_scan_blocks((uint32_t)nc) * sizeof(uint32_t),
+            CK(cudaMallocAsync((void**)&ctx->d_cstat, (size_t)(coulomb_scan_blocks((uint32_t)nc) + 1) * sizeof(unsigned long long),
                                ctx->stream));
         }
         ctx->cap = cap;
@@ -888,6 +889,9 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         CK(cudaMemcpyAsync(ctx->d_q8, q, n, kind, ctx->stream));
     }
     if (ctx->d_ccount) CK(cudaMemsetAsync(ctx->d_ccount, 0, nc * sizeof(uint32_t), ctx->stream));
+    if (ctx->d_cstat)
+        CK(cudaMemsetAsync(ctx->d_cstat, 0, (size_t)(coulomb_scan_blocks((uint32_t)nc) + 1) * sizeof(unsigned long long),
+                           ctx->stream));
     CK(cudaMemsetAsync(ctx->d_dep, 0, nc * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_count, 0, nc * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_charge, 0, nc * sizeof(unsigned long long), ctx->stream));

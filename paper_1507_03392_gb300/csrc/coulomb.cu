@@ -5,7 +5,7 @@
 // Per step, after the fused step kernel has counted the ions that stayed inside
 // per cell (ccount) and published each one's (pid, cell) and (v, Q) record in
 // its tile's participant list:
-//   1. scan      exclusive scan of ccount -> coff (three small passes);
+//   1. scan      exclusive scan of ccount -> coff (one pass, decoupled look-back);
 //   2. scatter   each participant takes slot coff[cell] + (ccount[cell] counted
 //                down by one), which leaves ccount at zero for the next step;
 //                the slot receives key = (pairing hash << 32 | pid), the hash
@@ -49,11 +49,49 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
     return v;
 }
 
-// pass A: block-local exclusive scan of ccount into coff, block totals to cblk
-__global__ void __launch_bounds__(kScanThreads) k_scan_a(const __grid_constant__ RunDev R, uint32_t ncells)
+// range b of the collision kernel starts at the first cell c with
+// coff[c] >= b kCellIons: cell c starts the ranges b with
+// coff[c - 1] < b kCellIons <= coff[c]
+__device__ __forceinline__ void mark_ranges(const RunDev& R, uint32_t c, uint32_t prev, uint32_t cur)
+{
+    const uint32_t b0 = c == 0 ? 0u : prev / (uint32_t)kCellIons + 1u;
+    for (uint32_t b = b0; b <= cur / (uint32_t)kCellIons; ++b) R.cstart[b] = c;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// One-pass exclusive scan of ccount into coff (coff[ncells] = total) with
+// decoupled look-back: each block takes the next scan tile in ticket order,
+// scans its kScanBlock counts, publishes the tile's total, then adds up the
+// totals (or the first inclusive prefix) of the tiles before it.  A status
+// word is epoch << 33 | inclusive << 32 | value; the epoch (launch number,
+// from the ticket) tells this launch's words from stale ones.  A wait that
+// runs out of its bounded spin sets the run's error word.  The kernel also
+// marks where the collision kernel's ranges start.
+__global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ RunDev R, uint32_t ncells,
+                                                      uint32_t ntile)
 {
     __shared__ uint32_t wsum[kScanThreads / 32];
-    const uint32_t base = blockIdx.x * kScanBlock + threadIdx.x * kScanPerThread;
+    __shared__ uint32_t s_tile, s_epoch, s_prefix;
+    if (threadIdx.x == 0) {
+        const unsigned long long t = atomicAdd(R.cctr, 1ull);
+        s_tile = (uint32_t)(t % ntile);
+        s_epoch = (uint32_t)(t / ntile) + 1u;
+    }
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const unsigned long long ep = (unsigned long long)s_epoch << 33;
+    const uint32_t base = tile * kScanBlock + threadIdx.x * kScanPerThread;
     uint32_t v[kScanPerThread];
     uint32_t sum = 0;
 #pragma unroll
@@ -67,88 +105,91 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_a(const __grid_constant__
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = lane < kScanThreads / 32 ? wsum[lane] : 0u;
+        const uint32_t w = lane < kScanThreads / 32 ? wsum[lane] : 0u;
         const uint32_t wi = warp_incl_scan(w);
         if (lane < kScanThreads / 32) wsum[lane] = wi - w;
-        if (lane == kScanThreads / 32 - 1) R.cblk[blockIdx.x] = wi;
+        // the tile's total: publish it, look back over up to 32 earlier tiles
+        // at a time (lane k reads tile p - k), publish the inclusive prefix
+        const uint32_t agg = __shfl_sync(0xFFFFFFFFu, wi, kScanThreads / 32 - 1);
+        uint32_t prefix = 0;
+        if (tile == 0) {
+            if (lane == 0) st_release(R.cstat, ep | (1ull << 32) | agg);
+        } else {
+            if (lane == 0) st_release(R.cstat + tile, ep | agg);
+            bool ok = true;
+            for (int p = (int)tile - 1; p >= 0; p -= 32) {
+                const int q = p - (int)lane;
+                unsigned long long st = 0;
+                if (q >= 0) {
+                    uint32_t it = 0;
+                    do {
+                        st = ld_acquire(R.cstat + q);
+                    } while ((st >> 33) != (ep >> 33) && ++it < kWaitLimit);
+                    if ((st >> 33) != (ep >> 33)) ok = false;
+                }
+                // sum up to and including the nearest inclusive prefix
+                const uint32_t incl_mask = __ballot_sync(0xFFFFFFFFu, q >= 0 && (st & (1ull << 32)));
+                const uint32_t first = incl_mask ? (uint32_t)(__ffs(incl_mask) - 1) : 31u;
+                uint32_t val = (q >= 0 && lane <= first) ? (uint32_t)st : 0u;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xFFFFFFFFu, val, o);
+                prefix += val;
+                if (incl_mask) break;
+            }
+            if (__any_sync(0xFFFFFFFFu, !ok) && lane == 0) atomicExch(R.err, kErrTimeout);
+            if (lane == 0) st_release(R.cstat + tile, ep | (1ull << 32) | (prefix + agg));
+        }
+        if (lane == 0) s_prefix = prefix;
     }
     __syncthreads();
-    uint32_t run_off = wsum[warp] + incl - sum;
+    uint32_t cur = s_prefix + wsum[warp] + incl - sum;
 #pragma unroll
     for (int j = 0; j < kScanPerThread; ++j) {
         const uint32_t idx = base + j;
-        if (idx < ncells) R.coff[idx] = run_off;
-        run_off += v[j];
-    }
-}
-
-// pass B: one block scans the block totals in place; coff[ncells] = total
-__global__ void __launch_bounds__(1024) k_scan_b(const __grid_constant__ RunDev R, uint32_t nblocks,
-                                                 uint32_t ncells)
-{
-    __shared__ uint32_t wsum[32];
-    const uint32_t per = (nblocks + 1023) / 1024;
-    const uint32_t base = threadIdx.x * per;
-    uint32_t sum = 0;
-    for (uint32_t j = 0; j < per; ++j)
-        if (base + j < nblocks) sum += R.cblk[base + j];
-    const uint32_t incl = warp_incl_scan(sum);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t w = wsum[lane];
-        const uint32_t wi = warp_incl_scan(w);
-        wsum[lane] = wi - w;
-        if (lane == 31) R.coff[ncells] = wi;
-    }
-    __syncthreads();
-    uint32_t off = wsum[warp] + incl - sum;
-    for (uint32_t j = 0; j < per; ++j) {
-        if (base + j < nblocks) {
-            const uint32_t t = R.cblk[base + j];
-            R.cblk[base + j] = off;
-            off += t;
+        if (idx < ncells) {
+            R.coff[idx] = cur;
+            const uint32_t prev = idx == 0 ? 0u : (j > 0 ? cur - v[j - 1] : cur - R.ccount[idx - 1]);
+            mark_ranges(R, idx, prev, cur);
+            if (idx == ncells - 1) {
+                R.coff[ncells] = cur + v[j];
+                mark_ranges(R, ncells, cur, cur + v[j]);
+            }
         }
-    }
-}
-
-// range b of the collision kernel starts at the first cell c with
-// coff[c] >= b kCellIons: cell c starts the ranges b with
-// coff[c - 1] < b kCellIons <= coff[c]
-__device__ __forceinline__ void mark_ranges(const RunDev& R, uint32_t c, uint32_t prev, uint32_t cur)
-{
-    const uint32_t b0 = c == 0 ? 0u : prev / (uint32_t)kCellIons + 1u;
-    for (uint32_t b = b0; b <= cur / (uint32_t)kCellIons; ++b) R.cstart[b] = c;
-}
-
-// pass C: add block offsets, and mark where the collision kernel's ranges
-// start (the previous cell's offset is this one's minus its count)
-__global__ void __launch_bounds__(kScanThreads) k_scan_c(const __grid_constant__ RunDev R, uint32_t ncells)
-{
-    const uint32_t add = R.cblk[blockIdx.x];
-    const uint32_t base = blockIdx.x * kScanBlock;
-    for (uint32_t j = threadIdx.x; j < (uint32_t)kScanBlock; j += kScanThreads) {
-        const uint32_t idx = base + j;
-        if (idx >= ncells) break;
-        const uint32_t cur = R.coff[idx] + add;
-        R.coff[idx] = cur;
-        mark_ranges(R, idx, idx ? cur - R.ccount[idx - 1] : 0u, cur);
-        if (idx == ncells - 1) mark_ranges(R, ncells, cur, R.coff[ncells]);
+        cur += v[j];
     }
 }
 
 // scatter the participants of each tile into their cells' segments; counting
-// ccount back down gives each its slot and leaves ccount zero for the next step
+// ccount back down gives each its slot and leaves ccount zero for the next step.
+// Neighbouring list entries mostly share a cell (the step kernel sees the
+// particles sorted by cell), so each run of equal cells within a warp takes
+// its slots with one atomic.
 __global__ void k_scatter(const __grid_constant__ RunDev R, uint32_t ntiles)
 {
     const uint32_t step = *R.step;
+    const uint32_t lane = threadIdx.x & 31;
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const uint32_t np = R.tcount[t];
-        for (uint32_t i = threadIdx.x; i < np; i += blockDim.x) {
-            const uint4 pc = R.plist[t * kTile + i];   // (array slot, cell, id, -)
-            const float4 v = R.pvel[t * kTile + i];
-            const uint32_t slot = R.coff[pc.y] + atomicSub(R.ccount + pc.y, 1u) - 1u;
+        const uint32_t end = (np + 31u) & ~31u;   // whole warps iterate together
+        for (uint32_t i = threadIdx.x; i < end; i += blockDim.x) {
+            const bool in = i < np;
+            uint4 pc = make_uint4(0u, kNoCell, 0u, 0u);   // (array slot, cell, id, -)
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (in) {
+                pc = R.plist[t * kTile + i];
+                v = R.pvel[t * kTile + i];
+            }
+            const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, pc.y, 1);
+            const uint32_t heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || prev != pc.y);
+            const uint32_t upto = 0xFFFFFFFFu >> (31u - lane);             // lanes 0..lane
+            const uint32_t after = heads & ~upto;                           // run heads above this lane
+            const uint32_t tl = after ? (uint32_t)(__ffs(after) - 2) : 31u; // last lane of this lane's run
+            const uint32_t h = 31u - (uint32_t)__clz(heads & upto);          // first lane of this lane's run
+            uint32_t top = 0;
+            if (in && lane == tl) top = atomicSub(R.ccount + pc.y, tl - h + 1u);
+            top = __shfl_sync(0xFFFFFFFFu, top, tl);
+            if (!in) continue;
+            const uint32_t slot = R.coff[pc.y] + top - 1u - (tl - lane);
             const Words w = rng_words(R, pc.z, step, 1u);
             R.ckeys[slot] = ((unsigned long long)w.w0 << 32) | pc.z;
             R.crec[slot] = make_float4(v.x, v.y, v.z, __uint_as_float((pc.y << 6) | __float_as_uint(v.w)));
@@ -226,8 +267,9 @@ struct CellSmem {
     float4 rec[kCellCap];
     uint32_t slot[kCellCap];
     uint32_t sidx[kCellCap];          // sorted position -> index in the range
-    uint2 start[kCellCap / 2 + 1];    // (sorted position | triplet << 31, cell count)
-    uint32_t nstart;
+    uint2 start[kCellCap / 2 + 1];    // (sorted position, cell count): pairs from the front,
+                                      // triplets from the back, so a warp runs one kind
+    uint32_t npair, ntrip;
     uint32_t s0, s1;
     unsigned long long ncoll;
 };
@@ -302,7 +344,8 @@ __global__ void __launch_bounds__(256) k_cells(const __grid_constant__ RunDev R,
             const uint32_t c1 = hi >= total ? ncells : R.cstart[b + 1];
             S.s0 = R.coff[R.cstart[b]];
             S.s1 = R.coff[c1];
-            S.nstart = 0u;
+            S.npair = 0u;
+            S.ntrip = 0u;
         }
         __syncthreads();
         const uint32_t s0 = S.s0, n = S.s1 - S.s0;
@@ -326,21 +369,30 @@ __global__ void __launch_bounds__(256) k_cells(const __grid_constant__ RunDev R,
                     S.sidx[pos] = j;
                     kind = start_kind(r, m);
                 }
-                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, kind != 0u);
-                if (bal) {
-                    uint32_t base = 0;
-                    if (lane == 0) base = atomicAdd(&S.nstart, (uint32_t)__popc(bal));
-                    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-                    if (kind) S.start[base + (uint32_t)__popc(bal & ((1u << lane) - 1u))] =
-                        make_uint2(pos | (kind == 2u ? 0x80000000u : 0u), m);
+                const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, kind == 1u);
+                const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, kind == 2u);
+                if (b1 | b2) {
+                    uint32_t base1 = 0, base2 = 0;
+                    if (lane == 0) {
+                        if (b1) base1 = atomicAdd(&S.npair, (uint32_t)__popc(b1));
+                        if (b2) base2 = atomicAdd(&S.ntrip, (uint32_t)__popc(b2));
+                    }
+                    base1 = __shfl_sync(0xFFFFFFFFu, base1, 0);
+                    base2 = __shfl_sync(0xFFFFFFFFu, base2, 0);
+                    const uint32_t below = (1u << lane) - 1u;
+                    if (kind == 1u) S.start[base1 + (uint32_t)__popc(b1 & below)] = make_uint2(pos, m);
+                    if (kind == 2u) S.start[kCellCap / 2 - (base2 + (uint32_t)__popc(b2 & below))] = make_uint2(pos, m);
                 }
             }
             __syncthreads();
-            const uint32_t ns = S.nstart;
-            for (uint32_t e = tid; e < ns; e += blockDim.x) {
+            const uint32_t np = S.npair, nt = S.ntrip;
+            for (uint32_t e = tid; e < np; e += blockDim.x) {
                 const uint2 st = S.start[e];
-                ncoll += collide_entry(R, S.key, S.rec, S.slot, S.sidx, st.x & 0x7FFFFFFFu, st.y,
-                                       (st.x >> 31) != 0u, step);
+                ncoll += collide_entry(R, S.key, S.rec, S.slot, S.sidx, st.x, st.y, false, step);
+            }
+            for (uint32_t e = tid; e < nt; e += blockDim.x) {
+                const uint2 st = S.start[kCellCap / 2 - e];
+                ncoll += collide_entry(R, S.key, S.rec, S.slot, S.sidx, st.x, st.y, true, step);
             }
         } else {
             // the same in global memory: sorted positions in sslot
@@ -400,9 +452,7 @@ cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t ntiles, un
                            cudaStream_t s)
 {
     const int nb = coulomb_scan_blocks(ncells);
-    k_scan_a<<<nb, kScanThreads, 0, s>>>(R, ncells);
-    k_scan_b<<<1, 1024, 0, s>>>(R, (uint32_t)nb, ncells);
-    k_scan_c<<<nb, kScanThreads, 0, s>>>(R, ncells);
+    k_scan<<<nb, kScanThreads, 0, s>>>(R, ncells, (uint32_t)nb);
     if (ntiles > 0) k_scatter<<<ntiles, 256, 0, s>>>(R, ntiles);
     k_cells<<<grid, 256, sizeof(CellSmem), s>>>(R, ncells, ticket);
     return cudaGetLastError();

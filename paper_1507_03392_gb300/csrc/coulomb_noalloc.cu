@@ -45,8 +45,9 @@ constexpr size_t kOffPvel = kOffPlist + align256(sizeof(uint4) * kNaMaxIons);
 constexpr size_t kOffTcount = kOffPvel + align256(sizeof(float4) * kNaMaxIons);
 constexpr size_t kOffCcount = kOffTcount + align256(sizeof(uint32_t) * kNaTiles);
 constexpr size_t kOffCoff = kOffCcount + align256(sizeof(uint32_t) * kNaMaxCells);
-constexpr size_t kOffCblk = kOffCoff + align256(sizeof(uint32_t) * (kNaMaxCells + 1));
-constexpr size_t kOffCkeys = kOffCblk + align256(sizeof(uint32_t) * (kNaMaxCells / kScanBlock + 1));
+constexpr uint32_t kNaScanTiles = kNaMaxCells / kScanBlock + 1;
+constexpr size_t kOffCstat = kOffCoff + align256(sizeof(uint32_t) * (kNaMaxCells + 1));
+constexpr size_t kOffCkeys = kOffCstat + align256(sizeof(unsigned long long) * (kNaScanTiles + 1));
 constexpr size_t kOffCrec = kOffCkeys + align256(sizeof(unsigned long long) * kNaMaxIons);
 constexpr size_t kOffCslot = kOffCrec + align256(sizeof(float4) * kNaMaxIons);
 constexpr size_t kOffSslot = kOffCslot + align256(sizeof(uint32_t) * kNaMaxIons);
@@ -91,7 +92,11 @@ __global__ void k_na_init(unsigned char* base, uint32_t ncells, uint32_t tiles, 
     uint32_t* tcount = reinterpret_cast<uint32_t*>(base + kOffTcount);
     uint32_t* words = reinterpret_cast<uint32_t*>(base + kOffWords);
     unsigned long long* tally = reinterpret_cast<unsigned long long*>(base + kOffTally);
+    unsigned long long* cstat = reinterpret_cast<unsigned long long*>(base + kOffCstat);
     const uint32_t stride = gridDim.x * blockDim.x;
+    // scan status words and their ticket counter (the scan's tile count
+    // changes with ncells from call to call)
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= kNaScanTiles; i += stride) cstat[i] = 0ull;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += stride) ccount[i] = 0u;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < tiles; i += stride) tcount[i] = 0u;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -203,7 +208,8 @@ extern "C" ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* 
     R.tcount = reinterpret_cast<uint32_t*>(base + kOffTcount);
     R.ccount = reinterpret_cast<uint32_t*>(base + kOffCcount);
     R.coff = reinterpret_cast<uint32_t*>(base + kOffCoff);
-    R.cblk = reinterpret_cast<uint32_t*>(base + kOffCblk);
+    R.cstat = reinterpret_cast<unsigned long long*>(base + kOffCstat);
+    R.cctr = R.cstat + kNaScanTiles;
     R.cstart = reinterpret_cast<uint32_t*>(base + kOffCstart);
     R.ckeys = reinterpret_cast<unsigned long long*>(base + kOffCkeys);
     R.crec = reinterpret_cast<float4*>(base + kOffCrec);

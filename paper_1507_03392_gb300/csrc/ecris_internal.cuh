@@ -60,7 +60,7 @@ constexpr int kNanbuN = 2048;
 constexpr double kNanbuSLo = 1e-3;
 constexpr double kNanbuSHi = 6.0;
 
-// scan of the per-cell participant counts: cells per block of the first pass
+// scan of the per-cell participant counts: cells per scan tile (one block)
 constexpr int kScanThreads = 256;
 constexpr int kScanPerThread = 8;
 constexpr int kScanBlock = kScanThreads * kScanPerThread;
@@ -121,7 +121,8 @@ struct RunDev {
     uint32_t *ccount;            // Coulomb participants per cell (counted up by the step kernel,
                                  // counted back to zero by the scatter)
     uint32_t *coff;              // exclusive scan of ccount, Nc + 1 entries
-    uint32_t *cblk;              // scan block totals
+    unsigned long long *cstat;   // scan tile status words (decoupled look-back), one per scan tile
+    unsigned long long *cctr;    // scan tile tickets handed out so far
     uint32_t *cstart;            // first cell of each range of kCellIons participants (collision kernel)
     unsigned long long *ckeys;   // (pairing hash << 32 | pid) per participant, grouped by cell
     float4 *crec;                // (vx, vy, vz, cell << 6 | Q as bits) per participant, grouped by cell
@@ -323,7 +324,7 @@ void ecris_internal_set_thread_error(const char* msg);
 // bump_step = 0): scan of the cell counts, scatter of the pairing keys, and
 // the per-cell sort / pair / collide kernel, whose last block advances the
 // step counter.
-constexpr int kCoulombKernels = 5;   // kernels per launch_coulomb
+constexpr int kCoulombKernels = 3;   // kernels per launch_coulomb
 constexpr int kCellIons = 512;       // participants per range of cells of the collision kernel
 constexpr int kCellCap = 1024;       // participants of a range held in shared memory
 cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t ntiles, unsigned int* ticket, int grid,
