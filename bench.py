@@ -199,6 +199,19 @@ def run_reference(args, rank, world):
     return 0
 
 
+def replica_throughput(units, seconds, dist=None, device="cpu"):
+    """Whole-job rate of independent replicas: the units all ranks processed
+    divided by the slowest rank's time (one rank: units / seconds)."""
+    if dist is None:
+        return units / seconds, seconds
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
 def _percentile(xs, q):
     xs = sorted(xs)
     if not xs:
@@ -434,12 +447,8 @@ def main():
     prof = run.profile()
     run.set_profiling(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    total_ms = float(tmax.item())
-    value = world * n * args.steps / (total_ms * 1e-3)
+    value, total_s = replica_throughput(n * args.steps, 1e-3 * sum(step_ms), dist, "cuda")
+    total_ms = 1e3 * total_s
     launches = prof["step_launches"] + prof["coulomb_launches"] + prof["other_launches"]
 
     # roofline of the dominant kernel (the fused step kernel)
@@ -475,10 +484,7 @@ def main():
         t1 = time.perf_counter()
         if i >= 2:
             e2e_times.append(t1 - t0)
-    e2e_t = torch.tensor([sum(e2e_times)], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * n * len(e2e_times) / float(e2e_t.item())
+    e2e_value, _ = replica_throughput(n * len(e2e_times), sum(e2e_times), dist, "cuda")
     h2d = n * (6 * 4 + 1)
     d2h = (132 + 64) * 8
 
