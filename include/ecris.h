@@ -279,10 +279,12 @@ ecris_status ecris_batch_memory(const ecris_batch* b, size_t* used, size_t* budg
  * kernels of all runs, other_* sorts, deposit folds and step counters. */
 ecris_status ecris_batch_set_profiling(ecris_batch* b, int enable);
 ecris_status ecris_batch_get_profile(ecris_batch* b, ecris_profile* out);
-/* Launch-shape autotuner: times `trial_steps` steps of the batch for each
- * candidate (resident step-kernel blocks per SM, steps between particle
- * sorts), keeps the fastest and returns it in *chosen (may be NULL).  The
- * trial steps are real steps of every run; no result depends on the choice. */
+/* Launch-shape autotuner: for each candidate (resident step-kernel blocks
+ * per SM, steps between particle sorts) times at least `trial_steps` steps of
+ * the batch, in whole sort periods that each start with a sort, keeps the
+ * candidate with the least time per step and returns it in *chosen (may be
+ * NULL).  The trial steps are real steps of every run; no result depends on
+ * the choice. */
 ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tuning* chosen);
 
 /* ------------------------------------------------------------------------ */

@@ -1545,12 +1545,18 @@ ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tu
             b->graph_dirty = true;
             st = ecris_batch_step(b, 1);   // capture outside the timing
             if (st != ECRIS_OK) break;
+            // time whole sort periods, each starting with a sort, so every
+            // candidate pays its own share of sorting
+            for (auto* c : b->runs)
+                if (c) c->since_sort = c->sort_every;
+            const uint32_t steps = ((trial_steps + sorts[k] - 1) / sorts[k]) * sorts[k];
             cudaEventRecord(t0, b->stream);
-            st = ecris_batch_step(b, trial_steps);
+            st = ecris_batch_step(b, steps);
             cudaEventRecord(t1, b->stream);
             if (cudaEventSynchronize(t1) != cudaSuccess) st = ECRIS_ECUDA;
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, t0, t1);
+            ms /= (float)steps;
             if (st == ECRIS_OK && ms < best) {
                 best = ms;
                 best_bps = bps;

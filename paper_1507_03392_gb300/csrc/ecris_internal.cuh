@@ -11,10 +11,10 @@ namespace ecris {
 
 constexpr int kQSlots = 64;            // charge-state slots per tally array
 #ifndef ECRIS_TILE_VEC
-#define ECRIS_TILE_VEC 4
+#define ECRIS_TILE_VEC 2
 #endif
 #ifndef ECRIS_STEP_MIN_BLOCKS
-#define ECRIS_STEP_MIN_BLOCKS 3
+#define ECRIS_STEP_MIN_BLOCKS 5
 #endif
 constexpr int kThreads = 256;                 // threads per block of the step kernel
 constexpr int kVec = ECRIS_TILE_VEC;          // particles per thread per tile

@@ -96,6 +96,50 @@ __device__ __forceinline__ void outside(long long xn, long long yn, long long zn
 
 __device__ __forceinline__ int32_t clamp_fx(long long v) { return (int32_t)max(min(v, kLim - 1), -kLim); }
 
+// a + b in 32 bits, and whether the exact sum left the 32-bit range
+__device__ __forceinline__ int32_t add_wrap(int32_t a, int32_t b, bool& over)
+{
+    const int32_t s = (int32_t)((uint32_t)a + (uint32_t)b);
+    over = ((a ^ s) & (b ^ s)) < 0;
+    return s;
+}
+
+// The straight move of the step and the boundary test, as displace() and
+// outside() give them, but in 32-bit arithmetic for the common step shorter
+// than 2^30 units: the fixed-point range is the chamber's bounding box, so a
+// sum that leaves the 32-bit range has left the chamber.  On return X, Y, Z
+// hold the new position (clamped into the range for a leaver); true if the
+// particle left.
+__device__ __forceinline__ bool move(const RunDev& R, int32_t& X, int32_t& Y, int32_t& Z, float vx, float vy,
+                                     float vz)
+{
+    const bool push = (R.flags & kFPush) != 0;
+    const float dx = push ? vx * R.dt_sxy : 0.0f, dy = push ? vy * R.dt_sxy : 0.0f, dz = push ? vz * R.dt_sz : 0.0f;
+    if (fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))) < 1.0e9f) {
+        bool ox, oy, oz;
+        const int32_t xn = add_wrap(X, __float2int_rn(dx), ox);
+        const int32_t yn = add_wrap(Y, __float2int_rn(dy), oy);
+        const int32_t zn = add_wrap(Z, __float2int_rn(dz), oz);
+        const bool leave = ox | oy | oz ||
+                           (long long)xn * xn + (long long)yn * yn > (1ll << 62);
+        if (!leave) {
+            X = xn;
+            Y = yn;
+            Z = zn;
+        }
+        return leave;
+    }
+    long long xn, yn, zn;
+    displace(R, X, Y, Z, vx, vy, vz, xn, yn, zn);
+    bool out_r, out_0, out_L;
+    outside(xn, yn, zn, out_r, out_0, out_L);
+    if (out_r | out_0 | out_L) return true;
+    X = clamp_fx(xn);
+    Y = clamp_fx(yn);
+    Z = clamp_fx(zn);
+    return false;
+}
+
 // Advance one particle by one step.  pid is its stable id (the Philox counter
 // word).  On return dep_cell is the cell it deposits in and ckey the cell
 // where it takes part in Coulomb collisions (kNoCell if it does not).  A
@@ -144,26 +188,18 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
         vy = my + h * Ey;
         vz = mz + h * Ez;
     }
-    long long xn, yn, zn;
-    displace(R, X, Y, Z, vx, vy, vz, xn, yn, zn);
-
-    // cell record and random words of the new position, fetched before the
-    // boundary test so their latency overlaps it (leavers discard them)
-    const int32_t Xc = clamp_fx(xn), Yc = clamp_fx(yn), Zc = clamp_fx(zn);
-    const uint32_t cell = ngp_cell(R, Xc, Yc, Zc);
-    const Words w = rng_words(R, pid, step, 0u);
-
-    bool out_r, out_0, out_L;
-    outside(xn, yn, zn, out_r, out_0, out_L);
-    if (out_r | out_0 | out_L) {
+    const int32_t X0 = X, Y0 = Y, Z0 = Z;
+    if (move(R, X, Y, Z, vx, vy, vz)) {
+        X = X0;   // the leaver pass redoes the move from the old position
+        Y = Y0;
+        Z = Z0;
         meta = status | Q;
         return true;
     }
 
     // ---- MCC in the particle's cell ----
-    X = Xc;
-    Y = Yc;
-    Z = Zc;
+    const uint32_t cell = ngp_cell(R, X, Y, Z);
+    const Words w = rng_words(R, pid, step, 0u);
     // an atom needs its cell only if its ionisation word could fire in
     // the densest cell; otherwise no cell can ionise it this step
     const bool ionize = (R.flags & kFIonize) && (int)Q < R.qmax;
@@ -406,29 +442,21 @@ __device__ __forceinline__ void load_tile(const RunDev& R, Stage& st, uint64_t* 
 
 // NGP deposition of one particle per lane (the whole warp calls it), summed
 // over runs of neighbouring lanes in the same cell (particles are kept sorted
-// by cell, so neighbours mostly are): the last lane of each run adds
-// count << 32 | charge for the run.  The sums come from one warp prefix sum of
-// (1 << 16 | Q) per lane: at most 32 lanes of Q <= 63 fit 16 bits of charge.
+// by cell, so neighbours mostly are): one reduction over each run's lanes, and
+// the last lane of the run adds count << 32 | charge for it.
 __device__ __forceinline__ void deposit_warp(const RunDev& R, uint32_t cell, uint32_t Q)
 {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, cell, 1);
     const uint32_t heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || prev != cell);
-    const uint32_t v = cell != kNoCell ? (65536u | Q) : 0u;
-    uint32_t incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= (uint32_t)o) incl += t;
-    }
-    // first lane of this lane's run, and the prefix just before it
-    const uint32_t h = 31u - (uint32_t)__clz(heads & (0xFFFFFFFFu >> (31u - lane)));
-    const uint32_t before = __shfl_sync(0xFFFFFFFFu, incl, h == 0 ? 0 : h - 1);
-    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-    if (tail && cell != kNoCell) {
-        const uint32_t sum = incl - (h == 0 ? 0u : before);
-        atomicAdd(R.dep + cell, ((unsigned long long)(sum >> 16) << 32) | (unsigned long long)(sum & 0xFFFFu));
-    }
+    const uint32_t upto = 0xFFFFFFFFu >> (31u - lane);                // lanes 0..lane
+    const uint32_t h = 31u - (uint32_t)__clz(heads & upto);           // first lane of the run
+    const uint32_t after = heads & ~upto;
+    const uint32_t tl = after ? (uint32_t)(__ffs(after) - 2) : 31u;    // last lane of the run
+    const uint32_t run = (0xFFFFFFFFu >> (31u - tl)) & (0xFFFFFFFFu << h);
+    const uint32_t q = __reduce_add_sync(run, Q);
+    if (lane == tl && cell != kNoCell)
+        atomicAdd(R.dep + cell, ((unsigned long long)(tl - h + 1u) << 32) | (unsigned long long)q);
 }
 
 // Publish this lane's Coulomb participant (ck != kNoCell) for the collision
