@@ -16,6 +16,12 @@ LIB = os.path.join(HERE, "libecris.so")
 SOURCES = ["api.cu", "step_kernel.cu", "coulomb.cu", "coulomb_noalloc.cu", "sort.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--cudart", "shared"]
+# The step kernels for one run and for a batch inline the same per-particle
+# code; without contraction of separate multiplies and adds into FMAs (an
+# optimiser's choice that may differ between the two kernels) both round
+# every operation the same way, so a run gives identical results alone and in
+# a batch.  Explicit fmaf() calls in that code still compile to FMAs.
+FILE_FLAGS = {"step_kernel.cu": ["-fmad=false"]}
 
 
 def _nvcc():
@@ -36,6 +42,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(HERE, "..", "include", "ecris.h"))
+    headers.append(os.path.abspath(__file__))   # flag changes rebuild everything
     nvcc = _nvcc()
     jobs = []
     objs = []
@@ -44,7 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o]
+            cmd = [nvcc, *ARCH, *FLAGS, *FILE_FLAGS.get(src, []), "-c", s, "-o", o]
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append(cmd)

@@ -99,6 +99,7 @@ struct HostRun {
     std::vector<unsigned char> cell_zone;
     ecris_mcc mcc;
     double zm;
+    bool has_e = false;            // some cell of the E grid is nonzero
 };
 
 // synthetic on-axis mirror and its first two derivatives
@@ -436,7 +437,7 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.qm_unit = (float)(kE / M);
     R.dt = (float)dt;
     R.half_dt = (float)(0.5 * dt);
-    R.flags = h.mcc.flags;
+    R.flags = (h.mcc.flags & ~kFHasE) | (h.has_e ? kFHasE : 0u);
     R.sig0 = (float)std::sqrt(h.mcc.T0_eV * kE / M);
     R.n0s1 = (float)(h.mcc.n0_cm3 * 1e6 * h.mcc.sigma1_cm2 * 1e-4);
     R.vth2 = (float)(8.0 * h.mcc.T0_eV * kE / (kPi * M));
@@ -715,6 +716,7 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
     free_ions(ctx);
     free_fields(ctx);
     HostRun& h = ctx->h;
+    h.has_e = false;
     h.geo = *geo;
     h.bf = *bf;
     h.nx = grid->nx;
@@ -791,6 +793,7 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
             if (!std::isfinite(ex) || !std::isfinite(ey) || !std::isfinite(ez))
                 return fail(ctx, ECRIS_EINVAL, "init_fields: E[%zu] is not finite", c);
             E[c] = make_float4(ex, ey, ez, 0.f);
+            if (ex != 0.0f || ey != 0.0f || ez != 0.0f) h.has_e = true;
         }
     }
     CK(cudaMallocAsync((void**)&ctx->d_cell, nc * sizeof(float4), ctx->stream));

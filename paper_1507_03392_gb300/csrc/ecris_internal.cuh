@@ -47,6 +47,7 @@ constexpr uint32_t kFCx = 1u << 2;
 constexpr uint32_t kFEikick = 1u << 3;
 constexpr uint32_t kFCoulomb = 1u << 4;
 constexpr uint32_t kFRecycle = 1u << 5;
+constexpr uint32_t kFHasE = 1u << 16;   // internal: the run has a nonzero E grid (the push gathers it)
 
 constexpr uint32_t kNoCell = 0xFFFFFFFFu;
 

@@ -173,20 +173,27 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
         const float x0 = fx_xy(R, X), y0 = fx_xy(R, Y), z0 = fx_z(R, Z);
         float Bx, By, Bz, Ex, Ey, Ez;
         bfield(R, x0, y0, z0, Bx, By, Bz);
-        efield(R, x0, y0, z0, Ex, Ey, Ez);
+        if (R.flags & kFHasE) {
+            efield(R, x0, y0, z0, Ex, Ey, Ez);
+        } else {
+            Ex = 0.0f;   // no E grid: the gather would return zeros
+            Ey = 0.0f;
+            Ez = 0.0f;
+        }
+        // (FMAs written out: this file is compiled without contraction)
         const float h = (float)Q * R.qm_unit * R.half_dt;
-        float mx = vx + h * Ex, my = vy + h * Ey, mz = vz + h * Ez;
+        float mx = fmaf(h, Ex, vx), my = fmaf(h, Ey, vy), mz = fmaf(h, Ez, vz);
         const float tx = h * Bx, ty = h * By, tz = h * Bz;
-        const float sf = __fdividef(2.0f, 1.0f + tx * tx + ty * ty + tz * tz);
-        const float px = mx + (my * tz - mz * ty);
-        const float py = my + (mz * tx - mx * tz);
-        const float pz = mz + (mx * ty - my * tx);
-        mx += (py * tz - pz * ty) * sf;
-        my += (pz * tx - px * tz) * sf;
-        mz += (px * ty - py * tx) * sf;
-        vx = mx + h * Ex;
-        vy = my + h * Ey;
-        vz = mz + h * Ez;
+        const float sf = __fdividef(2.0f, fmaf(tx, tx, fmaf(ty, ty, fmaf(tz, tz, 1.0f))));
+        const float px = mx + fmaf(my, tz, -mz * ty);
+        const float py = my + fmaf(mz, tx, -mx * tz);
+        const float pz = mz + fmaf(mx, ty, -my * tx);
+        mx = fmaf(fmaf(py, tz, -pz * ty), sf, mx);
+        my = fmaf(fmaf(pz, tx, -px * tz), sf, my);
+        mz = fmaf(fmaf(px, ty, -py * tx), sf, mz);
+        vx = fmaf(h, Ex, mx);
+        vy = fmaf(h, Ey, my);
+        vz = fmaf(h, Ez, mz);
     }
     const int32_t X0 = X, Y0 = Y, Z0 = Z;
     if (move(R, X, Y, Z, vx, vy, vz)) {
