@@ -1129,6 +1129,8 @@ ecris_status ecris_get_profile(ecris_ctx* ctx, ecris_profile* out)
 // ============================================================================
 // Batched form
 // ============================================================================
+constexpr int kBatchSideStreams = 8;
+
 struct ecris_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -1155,6 +1157,11 @@ struct ecris_batch {
     bool graph_dirty = true;
     unsigned int* d_ticket = nullptr;   // last-block ticket of the leaver pass
     KernelTimer timer;              // ecris_batch_set_profiling
+    // side streams on which the captured graph runs the collision kernels of
+    // different runs side by side (small runs do not fill the GPU alone)
+    cudaStream_t side[kBatchSideStreams] = {};
+    cudaEvent_t side_join[kBatchSideStreams] = {};
+    cudaEvent_t side_fork = nullptr;
 };
 
 namespace {
@@ -1234,15 +1241,40 @@ int batch_bps(const ecris_batch* b)
     return b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, b->max_blocks_per_sm) : b->max_blocks_per_sm;
 }
 
+cudaError_t batch_side_streams(ecris_batch* b)
+{
+    if (b->side_fork) return cudaSuccess;
+    cudaError_t e = cudaEventCreateWithFlags(&b->side_fork, cudaEventDisableTiming);
+    for (int k = 0; e == cudaSuccess && k < kBatchSideStreams; ++k) {
+        e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side_join[k], cudaEventDisableTiming);
+    }
+    return e;
+}
+
+// The step of every run (captured into the batch graph): the batched step
+// kernel and leaver pass on the batch stream; the collision kernels of the
+// runs that have them forked onto the side streams, so different runs'
+// collision kernels overlap; then the step counters of the others.
 cudaError_t batch_launch(ecris_batch* b)
 {
     cudaError_t e = launch_step_batch(b->d_runs, b->d_items, b->nitems, b->sm_count * batch_bps(b), b->stream);
     if (e == cudaSuccess) e = launch_leave_batch(b->d_runs, (uint32_t)b->runs.size(), b->d_ticket, b->stream);
+    if (e == cudaSuccess) e = batch_side_streams(b);
+    if (e == cudaSuccess) e = cudaEventRecord(b->side_fork, b->stream);
+    int used = 0;
     for (size_t r = 0; e == cudaSuccess && r < b->runs.size(); ++r) {
         ecris_ctx* c = b->runs[r];
         if (!c || !(c->h.mcc.flags & kFCoulomb)) continue;
+        const int k = used % kBatchSideStreams;
+        if (used < kBatchSideStreams) e = cudaStreamWaitEvent(b->side[k], b->side_fork, 0);
+        ++used;
         const uint32_t nc = (uint32_t)((size_t)c->h.nx * c->h.ny * c->h.nz);
-        e = launch_coulomb(*c->h_run, nc, c->ntiles, c->d_ticket, c->collide_grid, b->stream);
+        if (e == cudaSuccess) e = launch_coulomb(*c->h_run, nc, c->ntiles, c->d_ticket, c->collide_grid, b->side[k]);
+    }
+    for (int k = 0; e == cudaSuccess && k < used && k < kBatchSideStreams; ++k) {
+        e = cudaEventRecord(b->side_join[k], b->side[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->side_join[k], 0);
     }
     if (e == cudaSuccess) e = launch_bump_steps(b->d_runs, (uint32_t)b->runs.size(), b->stream);
     return e;
@@ -1338,6 +1370,11 @@ void ecris_batch_destroy(ecris_batch* b)
     if (b->d_items) cudaFreeAsync(b->d_items, b->stream);
     if (b->d_ticket) cudaFreeAsync(b->d_ticket, b->stream);
     cudaStreamSynchronize(b->stream);
+    for (int k = 0; k < kBatchSideStreams; ++k) {
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+        if (b->side_join[k]) cudaEventDestroy(b->side_join[k]);
+    }
+    if (b->side_fork) cudaEventDestroy(b->side_fork);
     if (b->h_runs) cudaFreeHost(b->h_runs);
     if (b->staged) cudaEventDestroy(b->staged);
     b->timer.release();
