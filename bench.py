@@ -8,8 +8,9 @@ particles.  L2 is flushed (a 512 MB write) between timed steps.
 
 On one GPU the line also carries the batched form (a 64-run oxygen gas-flow
 scan in one persistent kernel and graph, beside the same runs stepped one at a
-time) and the served form (a Poisson request stream of O/Ar/Kr runs: scans/s,
-p50/p99 time to converged currents).
+time), the served form (a Poisson request stream of O/Ar/Kr runs: scans/s,
+p50/p99 time to converged currents) and a 128-run argon power scan admitted
+under an HBM budget of a third of its total.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -363,6 +364,45 @@ def bench_served(E, I, args, local):
     }
 
 
+def bench_power_scan(E, I, args, local):
+    """The batched microwave-power scan: Ar runs with n_e in the zone 5e10-2e12
+    cm^-3, T_ew 0.3-3 keV and N log-uniform 1e5-4e6, every process on,
+    submitted together to the request loop with an HBM budget of about a third
+    of their total, so runs are admitted as others finish.  Each run takes a
+    fixed number of steps; the leg reports the makespan and ion-steps/s."""
+    wls = [I.config_power_scan(i) for i in range(args.power_runs)]
+    # one initial state, a prefix of it per run
+    big = max(wls, key=lambda w: w.n)
+    pool = I.make_particles(I.Workload("ar_pool", big.params, n=big.n, steps=0, atom_fraction=0.75,
+                                       ion_qmax_init=8, atoms_fill_chamber=True), seed=2000)
+    need = [E.ecris_run_bytes(w.n, w.params.nx, w.params.ny, w.params.nz, 1) for w in wls]
+    budget = max(max(need), sum(need) // 3)
+    srv = E.Server(device=local, hbm_budget=budget, steps_per_tick=32)
+    t0 = time.perf_counter()
+    tickets = [(srv.submit(w.params, {k: v[: w.n] for k, v in pool.items()}, window_steps=args.power_steps,
+                           rel_tol=1e-3, min_events=10**15, max_steps=args.power_steps), w) for w in wls]
+    limit = time.perf_counter() + args.serve_limit_s
+    while True:
+        res = [(srv.poll(t), w) for t, w in tickets]
+        if all(r["state"] >= 2 for r, _ in res) or time.perf_counter() > limit:
+            break
+        time.sleep(0.02)
+    wall = time.perf_counter() - t0
+    srv.close()
+    done = [(r, w) for r, w in res if r["state"] == 2]
+    first = min(r["t_submit"] for r, _ in res)
+    last = max(r["t_done"] for r, _ in done) if done else first
+    ion_steps = sum(w.n * r["steps"] for r, w in done)
+    return {
+        "workload": f"Ar power scan, {len(wls)} runs, N log-uniform 1e5-4e6, n_e 5e10-2e12 cm^-3, "
+                    f"T_ew 0.3-3 keV, every process on, {args.power_steps} steps each",
+        "runs": len(wls), "done": len(done), "particles": sum(w.n for w in wls),
+        "hbm_budget_bytes": budget, "bytes_all_runs": sum(need),
+        "makespan_s": last - first, "value": ion_steps / max(1e-9, last - first), "unit": "ion-steps/s",
+        "wall_s_incl_submission": wall,
+    }
+
+
 def workload_config(wl, coulomb):
     p = wl.params
     return {"workload": wl.name, "species": p.species.name, "particles": wl.n,
@@ -386,6 +426,9 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--plain-runs", type=int, default=8)
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-power-scan", action="store_true")
+    ap.add_argument("--power-runs", type=int, default=128)
+    ap.add_argument("--power-steps", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
@@ -509,6 +552,8 @@ def main():
         line["batched"] = bench_batched(E, I, args, local, stream, flush, peak, peak_kind)
     if not args.no_served and world == 1:
         line["served"] = bench_served(E, I, args, local)
+    if not args.no_power_scan and world == 1:
+        line["batched_power_scan"] = bench_power_scan(E, I, args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     if dist:
