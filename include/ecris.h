@@ -8,7 +8,7 @@
  *   push        Boris push of ions in the static minimum-B field (solenoid
  *               mirror plus the printed analytic hexapole) and the electric
  *               field interpolated from a cell-centred 3-D grid; atoms move in
- *               straight lines (Sec. II, "standard particle-in-cell technique");
+ *               straight lines (Sec. II, particle-in-cell tracing);
  *   MCC         step-wise electron-impact ionisation Q -> Q+1 from the cell's
  *               electron density and temperature, charge exchange with the
  *               neutral background, the electron-ion heating kick (equation for
@@ -352,7 +352,9 @@ ecris_status ecris_server_submit(ecris_server* s, const ecris_request* req, int6
 /* Current state and, once done, the result of a request (thread-safe). */
 ecris_status ecris_server_poll(ecris_server* s, int64_t ticket, ecris_result* out);
 /* Seconds on the server's clock, and counters: requests queued, running,
- * done; ion-steps advanced since start. */
+ * done; ion-steps advanced since start.  The loop reads a run's tallies one
+ * tick after a window boundary while the batch keeps stepping, so a retired
+ * run has advanced one tick past the boundary its result belongs to. */
 ecris_status ecris_server_stats(ecris_server* s, double* now, int64_t* queued, int64_t* running, int64_t* done,
                                 double* ion_steps);
 

@@ -799,11 +799,13 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
     CK(cudaMallocAsync((void**)&ctx->d_cell, nc * sizeof(float4), ctx->stream));
     CK(cudaMallocAsync((void**)&ctx->d_E, nc * sizeof(float4), ctx->stream));
     CK(cudaMallocAsync((void**)&ctx->d_kdt, 2 * kQSlots * sizeof(float), ctx->stream));
-    std::vector<float> nanbu(kNanbuN);
-    {
+    // the same for every run: built once per process
+    static const std::vector<float> nanbu = [] {
+        std::vector<float> t(kNanbuN);
         const double l0 = std::log(kNanbuSLo), dl = std::log(kNanbuSHi / kNanbuSLo) / (kNanbuN - 1);
-        for (int i = 0; i < kNanbuN; ++i) nanbu[i] = (float)std::log(nanbu_A_host(std::exp(l0 + i * dl)));
-    }
+        for (int i = 0; i < kNanbuN; ++i) t[i] = (float)std::log(nanbu_A_host(std::exp(l0 + i * dl)));
+        return t;
+    }();
     CK(cudaMallocAsync((void**)&ctx->d_nanbu, kNanbuN * sizeof(float), ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_nanbu, nanbu.data(), kNanbuN * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_cell, cell.data(), nc * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
@@ -1004,6 +1006,39 @@ ecris_status ecris_step(ecris_ctx* ctx, uint32_t nsteps, double dt)
     return ECRIS_OK;
 }
 
+namespace {
+
+// the diagnostics of a run from its tally words (and census, if any) after
+// `steps` steps lasting time_s
+void fill_diag(const HostRun& h, double weight, const unsigned long long* tally, const unsigned long long* census,
+               uint64_t steps, double time_s, ecris_diag_out* out)
+{
+    const int Q1 = h.qmax + 1;
+    out->qmax = h.qmax;
+    out->steps = steps;
+    out->time_s = time_s;
+    for (int q = 0; q < Q1; ++q) {
+        if (out->extracted) out->extracted[q] = (int64_t)tally[kTallyExtracted + q];
+        if (out->lost) out->lost[q] = (int64_t)tally[kTallyLost + q];
+        if (out->alive_by_q && census) out->alive_by_q[q] = (int64_t)census[q];
+        if (out->current_A)
+            out->current_A[q] = time_s > 0.0 ? q * kE * weight * (double)tally[kTallyExtracted + q] / time_s : 0.0;
+    }
+    out->ke_lost_eV = 1e-6 * (double)tally[kTallyKe];
+    out->coulomb_collisions = (int64_t)tally[kTallyCoulomb];
+    // power balance: kinetic + potential energy of the ions that left plus
+    // 3/2 T_ew per electron that left with them
+    double e_eV = out->ke_lost_eV, ipcum = 0.0;
+    for (int q = 1; q < Q1; ++q) {
+        ipcum += h.ip[q - 1];
+        const double nleft = (double)tally[kTallyExtracted + q] + (double)tally[kTallyLost + q];
+        e_eV += nleft * (ipcum + 1.5 * q * h.Te_w);
+    }
+    out->power_W = time_s > 0.0 ? weight * e_eV * kE / time_s : 0.0;
+}
+
+}  // namespace
+
 ecris_status ecris_diag(ecris_ctx* ctx, ecris_diag_out* out)
 {
     if (!ctx) return ECRIS_EINVAL;
@@ -1035,30 +1070,7 @@ ecris_status ecris_diag(ecris_ctx* ctx, ecris_diag_out* out)
         ctx->failed = true;
         return fail(ctx, ECRIS_ETIMEOUT, "diag: a kernel's bounded wait for its tile copies ran out; reload");
     }
-    const int Q1 = h.qmax + 1;
-    out->qmax = h.qmax;
-    out->steps = ctx->steps_done;
-    out->time_s = ctx->time_s;
-    for (int q = 0; q < Q1; ++q) {
-        if (out->extracted) out->extracted[q] = (int64_t)tally[kTallyExtracted + q];
-        if (out->lost) out->lost[q] = (int64_t)tally[kTallyLost + q];
-        if (out->alive_by_q) out->alive_by_q[q] = (int64_t)census[q];
-        if (out->current_A)
-            out->current_A[q] = ctx->time_s > 0.0
-                                    ? q * kE * ctx->weight * (double)tally[kTallyExtracted + q] / ctx->time_s
-                                    : 0.0;
-    }
-    out->ke_lost_eV = 1e-6 * (double)tally[kTallyKe];
-    out->coulomb_collisions = (int64_t)tally[kTallyCoulomb];
-    // power balance: kinetic + potential energy of the ions that left plus
-    // 3/2 T_ew per electron that left with them
-    double e_eV = out->ke_lost_eV, ipcum = 0.0;
-    for (int q = 1; q < Q1; ++q) {
-        ipcum += h.ip[q - 1];
-        const double nleft = (double)tally[kTallyExtracted + q] + (double)tally[kTallyLost + q];
-        e_eV += nleft * (ipcum + 1.5 * q * h.Te_w);
-    }
-    out->power_W = ctx->time_s > 0.0 ? ctx->weight * e_eV * kE / ctx->time_s : 0.0;
+    fill_diag(h, ctx->weight, tally, census, ctx->steps_done, ctx->time_s, out);
     return ECRIS_OK;
 }
 
@@ -1162,6 +1174,19 @@ struct ecris_batch {
     cudaStream_t side[kBatchSideStreams] = {};
     cudaEvent_t side_join[kBatchSideStreams] = {};
     cudaEvent_t side_fork = nullptr;
+    // added runs are set up on their own stream, so the batch's queued steps
+    // keep running meanwhile
+    cudaStream_t setup = nullptr;
+    // pinned staging of the work list, and the event after its last upload
+    uint2* h_items = nullptr;
+    size_t h_items_cap = 0;
+    cudaEvent_t items_staged = nullptr;
+    // graphs replaced while launches of them may still be queued, each with an
+    // event recorded after its last launch; destroyed once that has passed
+    std::vector<std::pair<cudaEvent_t, cudaGraphExec_t>> old_graphs;
+    // pinned host blocks of removed runs (freed with the batch: freeing pinned
+    // memory may synchronise the device)
+    std::vector<void*> old_host;
 };
 
 namespace {
@@ -1187,13 +1212,43 @@ bool run_live(const ecris_batch* b, int32_t r)
 
 // upload the parameter blocks of all runs (free slots get a block whose step
 // pointer is NULL, which the kernels skip)
+// destroy the replaced graphs whose last launch has passed
+void batch_reap(ecris_batch* b)
+{
+    size_t k = 0;
+    for (auto& g : b->old_graphs) {
+        if (cudaEventQuery(g.first) == cudaSuccess) {
+            cudaGraphExecDestroy(g.second);
+            cudaEventDestroy(g.first);
+        } else {
+            b->old_graphs[k++] = g;
+        }
+    }
+    b->old_graphs.resize(k);
+}
+
+// Release a removed run without waiting for the batch's queued steps: its
+// device memory is freed in stream order after them (no launch enqueued later
+// reads it), its pinned blocks are kept until the batch goes.
+void batch_release_run(ecris_batch* b, ecris_ctx* c)
+{
+    c->stream = b->stream;
+    free_ions(c);
+    free_fields(c);
+    c->timer.release();
+    if (c->h_run) b->old_host.push_back(c->h_run);
+    if (c->h_kdt) b->old_host.push_back(c->h_kdt);
+    delete c;
+}
+
 ecris_status batch_upload(ecris_batch* b)
 {
     const size_t nr = b->runs.size();
     if (nr > b->runs_cap) {
-        BCK(cudaStreamSynchronize(b->stream));
+        // queued launches may still read the old blocks: free them in stream order
+        BCK(cudaEventSynchronize(b->staged));   // the last upload has read the old staging copy
         if (b->d_runs) cudaFreeAsync(b->d_runs, b->stream);
-        if (b->h_runs) cudaFreeHost(b->h_runs);
+        if (b->h_runs) b->old_host.push_back(b->h_runs);
         b->runs_cap = nr + 16;
         BCK(cudaMallocAsync((void**)&b->d_runs, b->runs_cap * sizeof(RunDev), b->stream));
         BCK(cudaMallocHost((void**)&b->h_runs, b->runs_cap * sizeof(RunDev)));
@@ -1217,16 +1272,24 @@ ecris_status batch_items(ecris_batch* b)
     for (size_t r = 0; r < b->runs.size(); ++r)
         if (b->runs[r])
             for (uint32_t t = 0; t < b->runs[r]->ntiles; ++t) items.push_back(make_uint2((uint32_t)r, t));
+    // the last upload must have read the staging copy before it is rewritten;
+    // queued launches may still read the old device list, freed in stream order
+    if (b->items_staged) BCK(cudaEventSynchronize(b->items_staged));
     if (items.size() > b->items_cap) {
-        BCK(cudaStreamSynchronize(b->stream));
         if (b->d_items) cudaFreeAsync(b->d_items, b->stream);
         b->items_cap = items.size() + 1024;
         BCK(cudaMallocAsync((void**)&b->d_items, b->items_cap * sizeof(uint2), b->stream));
     }
+    if (items.size() > b->h_items_cap) {
+        if (b->h_items) b->old_host.push_back(b->h_items);
+        b->h_items_cap = items.size() + 1024;
+        BCK(cudaMallocHost((void**)&b->h_items, b->h_items_cap * sizeof(uint2)));
+    }
     if (!items.empty()) {
-        BCK(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(uint2), cudaMemcpyHostToDevice,
+        std::memcpy(b->h_items, items.data(), items.size() * sizeof(uint2));
+        BCK(cudaMemcpyAsync(b->d_items, b->h_items, items.size() * sizeof(uint2), cudaMemcpyHostToDevice,
                             b->stream));
-        BCK(cudaStreamSynchronize(b->stream));   // the host vector dies here
+        BCK(cudaEventRecord(b->items_staged, b->stream));
     }
     b->nitems = (uint32_t)items.size();
     b->layout_dirty = false;
@@ -1284,7 +1347,11 @@ ecris_status batch_graph(ecris_batch* b)
 {
     if (!b->graph_dirty && b->gexec) return ECRIS_OK;
     if (b->gexec) {
-        cudaGraphExecDestroy(b->gexec);
+        // launches of the old graph may still be queued: destroy it later
+        cudaEvent_t ev = nullptr;
+        BCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        BCK(cudaEventRecord(ev, b->stream));
+        b->old_graphs.emplace_back(ev, b->gexec);
         b->gexec = nullptr;
     }
     cudaGraph_t g = nullptr;
@@ -1343,12 +1410,16 @@ ecris_status ecris_batch_create(ecris_batch** out, int device, void* cuda_stream
         }
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->items_staged, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->setup, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&b->d_ticket, sizeof(unsigned int), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned int), b->stream);
     if (e != cudaSuccess) {
         g_create_error = std::string("batch_create: ") + cudaGetErrorString(e);
         if (b->d_ticket) cudaFreeAsync(b->d_ticket, b->stream);
         if (b->staged) cudaEventDestroy(b->staged);
+        if (b->items_staged) cudaEventDestroy(b->items_staged);
+        if (b->setup) cudaStreamDestroy(b->setup);
         if (b->own_stream) cudaStreamDestroy(b->stream);
         delete b;
         return ECRIS_ECUDA;
@@ -1375,6 +1446,14 @@ void ecris_batch_destroy(ecris_batch* b)
         if (b->side_join[k]) cudaEventDestroy(b->side_join[k]);
     }
     if (b->side_fork) cudaEventDestroy(b->side_fork);
+    for (auto& g : b->old_graphs) {
+        cudaGraphExecDestroy(g.second);
+        cudaEventDestroy(g.first);
+    }
+    for (void* p : b->old_host) cudaFreeHost(p);
+    if (b->h_items) cudaFreeHost(b->h_items);
+    if (b->items_staged) cudaEventDestroy(b->items_staged);
+    if (b->setup) cudaStreamDestroy(b->setup);
     if (b->h_runs) cudaFreeHost(b->h_runs);
     if (b->staged) cudaEventDestroy(b->staged);
     b->timer.release();
@@ -1400,17 +1479,25 @@ ecris_status ecris_batch_add_run(ecris_batch* b, const ecris_geometry* geo, cons
         return bfail(b, ECRIS_ENOMEM, "batch_add_run: the run (" + std::to_string(need) + " bytes) would exceed the "
                      "memory budget (" + std::to_string(b->used) + " of " + std::to_string(b->budget) + " used)");
     BCK(cudaSetDevice(b->device));
+    batch_reap(b);
+    // set the run up on the setup stream (its waits then cover only its own
+    // copies), then hand it to the batch stream
     ecris_ctx* c = nullptr;
-    ecris_status st = ecris_create(&c, b->device, b->stream);
+    ecris_status st = ecris_create(&c, b->device, b->setup);
     if (st != ECRIS_OK) return bfail(b, st, std::string("batch_add_run: ") + ecris_last_error(nullptr));
     st = ecris_init_fields(c, geo, bf, grid, sp, mcc);
     if (st == ECRIS_OK) st = ecris_load_ions(c, n, xyzv, q, weight, seed, src_is_device);
     if (st == ECRIS_OK) st = upload_dt(c, dt);
+    if (st == ECRIS_OK && cudaStreamSynchronize(b->setup) != cudaSuccess) {
+        st = ECRIS_ECUDA;
+        c->err = "setup stream failed";
+    }
     if (st != ECRIS_OK) {
         const std::string m = c->err;
         ecris_destroy(c);
         return bfail(b, st, "batch_add_run: " + m);
     }
+    c->stream = b->stream;
     c->sort_every = b->sort_every;
     int32_t h = -1;
     for (size_t r = 0; r < b->runs.size(); ++r)
@@ -1438,8 +1525,7 @@ ecris_status ecris_batch_remove_run(ecris_batch* b, int32_t run)
     if (!b) return ECRIS_EINVAL;
     if (!run_live(b, run)) return bfail(b, ECRIS_EINVAL, "batch_remove_run: no such run");
     BCK(cudaSetDevice(b->device));
-    BCK(cudaStreamSynchronize(b->stream));
-    ecris_destroy(b->runs[run]);
+    batch_release_run(b, b->runs[run]);
     b->runs[run] = nullptr;
     b->used -= b->bytes[run];
     b->bytes[run] = 0;
@@ -1451,6 +1537,7 @@ ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps)
 {
     if (!b) return ECRIS_EINVAL;
     BCK(cudaSetDevice(b->device));
+    batch_reap(b);
     for (auto* c : b->runs)
         if (c && (c->failed || c->steps_done + nsteps >= kMaxSteps))
             return bfail(b, ECRIS_ESTATE, "batch_step: a run failed earlier or would pass 2^30 steps");
@@ -1620,3 +1707,28 @@ ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tu
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Hooks of the served form
+// ---------------------------------------------------------------------------
+namespace ecris {
+
+ecris_status batch_snapshot(ecris_batch* b, int32_t run, TallySnapshot* dst)
+{
+    if (!run_live(b, run)) return bfail(b, ECRIS_EINVAL, "batch_snapshot: no such run");
+    const ecris_ctx* c = b->runs[run];
+    BCK(cudaMemcpyAsync(dst->tally, c->d_tally, sizeof dst->tally, cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaMemcpyAsync(&dst->err, c->d_err, sizeof dst->err, cudaMemcpyDeviceToHost, b->stream));
+    return ECRIS_OK;
+}
+
+cudaStream_t batch_stream(const ecris_batch* b) { return b->stream; }
+
+void batch_snapshot_diag(const ecris_batch* b, int32_t run, const TallySnapshot& snap, uint64_t steps,
+                         ecris_diag_out* out)
+{
+    const ecris_ctx* c = b->runs[run];
+    fill_diag(c->h, c->weight, snap.tally, nullptr, steps, (double)steps * b->dt[run], out);
+}
+
+}  // namespace ecris

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/ecris.h"
+
 namespace ecris {
 
 constexpr int kQSlots = 64;            // charge-state slots per tally array
@@ -320,6 +322,22 @@ cudaError_t launch_step_batch(const RunDev* runs, const uint2* items, uint32_t n
 cudaError_t launch_bump_steps(const RunDev* runs, uint32_t nruns, cudaStream_t s);
 // message returned by ecris_last_error(NULL) on the calling thread
 void ecris_internal_set_thread_error(const char* msg);
+
+// Hooks of the served form (defined in api.cu, used by server.cu).  A tally
+// snapshot is a run's tally words and device error word, copied in stream
+// order into pinned host memory at a step boundary; the served loop reads it
+// a tick later, while the batch keeps stepping.
+struct TallySnapshot {
+    unsigned long long tally[kTallyWords];
+    uint32_t err, pad;
+};
+// enqueue the copies of run `run`'s tallies into *dst (pinned) on the batch stream
+ecris_status batch_snapshot(ecris_batch* b, int32_t run, TallySnapshot* dst);
+cudaStream_t batch_stream(const ecris_batch* b);
+// fill out (extracted, lost, currents, power, wall energy, collisions) from a
+// snapshot taken after `steps` steps of the run (time steps * dt)
+void batch_snapshot_diag(const ecris_batch* b, int32_t run, const TallySnapshot& snap, uint64_t steps,
+                         ecris_diag_out* out);
 
 // Coulomb collisions of one run for the current step (after launch_step with
 // bump_step = 0): scan of the cell counts, scatter of the pairing keys, and

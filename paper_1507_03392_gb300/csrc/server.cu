@@ -1,20 +1,24 @@
 // Served form of the ECRIS ion time step: a request loop that keeps one batch
 // of runs resident on the device and admits queued runs as slots and memory
-// free up (continuous batching).  Host code only: it drives the batch through
-// the public C ABI.
+// free up (continuous batching).
 //
-// The loop, on its own thread:
+// The loop, on its own thread, per tick:
 //   1. admit queued requests in arrival order while the batch's memory
 //      budget and the slot limit allow (a request that does not fit waits, and
-//      the ones behind it wait too, so arrival order is kept);
-//   2. advance the batch by steps_per_tick steps (one graph replay per step);
-//   3. for every run whose own step count reached a multiple of its window,
-//      read its diagnostics and apply the convergence rule (stationary
-//      extracted currents, Sec. II) or the step cap; retire finished runs,
-//      which frees their memory for the queue.
-// Because the rule only looks at a run's own counters at its own window
-// boundaries, and a run in a batch evolves exactly as it does alone, the
-// result of a request does not depend on what else is being served.
+//      the ones behind it wait too, so arrival order is kept); a new run is
+//      set up on its own stream while the batch's queued steps run;
+//   2. enqueue steps_per_tick steps of the batch (one graph replay per step)
+//      and, for every run whose own step count reaches a multiple of its
+//      window, a copy of its tallies into pinned memory (a snapshot);
+//   3. while those steps run, read the snapshots of the previous tick and
+//      apply the convergence rule (stationary extracted currents, Sec. II) or
+//      the step cap; retire finished runs, which frees their memory for the
+//      queue in stream order.
+// A run retired at a boundary has run one tick past it; its result is the
+// snapshot at the boundary.  Because the rule only looks at a run's own
+// counters at its own window boundaries, and a run in a batch evolves exactly
+// as it does alone, the result of a request does not depend on what else is
+// being served.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -29,6 +33,7 @@
 #include <vector>
 
 #include "../../include/ecris.h"
+#include "ecris_internal.cuh"
 
 namespace {
 
@@ -51,6 +56,10 @@ struct Served {
     std::vector<int64_t> last_ext;   // extracted counts at the previous window boundary
     std::vector<double> last_cur;    // currents of the previous window
     bool have_prev = false;
+    uint64_t issued = 0;             // steps enqueued for the run
+    uint64_t snap_steps = 0;         // steps at its latest snapshot
+    ecris::TallySnapshot* snap = nullptr;   // pinned
+    cudaEvent_t ev = nullptr;        // the snapshot has landed
 };
 
 }  // namespace
@@ -73,6 +82,9 @@ struct ecris_server {
     int64_t n_done = 0;
     double ion_steps = 0.0;
     std::thread loop;
+    // recycled pinned snapshot slots and events (only the loop thread uses them)
+    std::vector<ecris::TallySnapshot*> free_snaps;
+    std::vector<cudaEvent_t> free_events;
 };
 
 namespace {
@@ -89,32 +101,60 @@ void finish(ecris_server* s, Served* v, int32_t state, const char* msg)
     if (msg) std::strncpy(v->res.error, msg, sizeof v->res.error - 1);
 }
 
-// read a run's diagnostics into its result; returns false on failure
-bool read_diag(ecris_server* s, Served* v, std::vector<int64_t>& ext)
+// a pinned snapshot slot and an event for a newly admitted run
+bool take_slot(ecris_server* s, Served* v)
+{
+    if (s->free_snaps.empty()) {
+        ecris::TallySnapshot* p = nullptr;
+        if (cudaMallocHost((void**)&p, sizeof(ecris::TallySnapshot)) != cudaSuccess) return false;
+        s->free_snaps.push_back(p);
+    }
+    if (s->free_events.empty()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+        s->free_events.push_back(e);
+    }
+    v->snap = s->free_snaps.back();
+    s->free_snaps.pop_back();
+    v->ev = s->free_events.back();
+    s->free_events.pop_back();
+    return true;
+}
+
+void give_slot(ecris_server* s, Served* v)
+{
+    if (v->snap) s->free_snaps.push_back(v->snap);
+    if (v->ev) s->free_events.push_back(v->ev);
+    v->snap = nullptr;
+    v->ev = nullptr;
+}
+
+// the run's result at its latest snapshot (landed) into res; false on a
+// device error
+bool read_snapshot(ecris_server* s, Served* v, std::vector<int64_t>& ext, ecris_result& res)
 {
     const int q1 = v->req->r.sp.qmax + 1;
     ext.assign(q1, 0);
     std::vector<int64_t> lost(q1, 0);
-    std::vector<double> cur(q1, 0.0);
+    if (v->snap->err) return false;
     ecris_diag_out d;
     std::memset(&d, 0, sizeof d);
     d.extracted = ext.data();
     d.lost = lost.data();
-    d.current_A = cur.data();
-    if (ecris_batch_diag(s->batch, v->run, &d) != ECRIS_OK) return false;
-    v->res.steps = d.steps;
-    v->res.qmax = d.qmax;
-    v->res.power_W = d.power_W;
-    v->res.ke_lost_eV = d.ke_lost_eV;
+    ecris::batch_snapshot_diag(s->batch, v->run, *v->snap, v->snap_steps, &d);
+    res.steps = d.steps;
+    res.qmax = d.qmax;
+    res.power_W = d.power_W;
+    res.ke_lost_eV = d.ke_lost_eV;
     for (int q = 0; q < q1 && q < 64; ++q) {
-        v->res.extracted[q] = ext[q];
-        v->res.lost[q] = lost[q];
+        res.extracted[q] = ext[q];
+        res.lost[q] = lost[q];
     }
     return true;
 }
 
-// the convergence rule at a window boundary
-bool converged(Served* v, const std::vector<int64_t>& ext)
+// the convergence rule at a window boundary (currents into res)
+bool converged(Served* v, const std::vector<int64_t>& ext, ecris_result& res)
 {
     const ecris_request& r = v->req->r;
     const int q1 = r.sp.qmax + 1;
@@ -126,7 +166,7 @@ bool converged(Served* v, const std::vector<int64_t>& ext)
         events += dn;
         cur[q] = q * 1.602176634e-19 * r.weight * (double)dn / window_s;
     }
-    for (int q = 0; q < q1 && q < 64; ++q) v->res.current_A[q] = cur[q];
+    for (int q = 0; q < q1 && q < 64; ++q) res.current_A[q] = cur[q];
     bool ok = false;
     if (v->have_prev && events >= r.min_events) {
         // relative change against the larger of the two (two zero currents agree)
@@ -151,14 +191,16 @@ bool converged(Served* v, const std::vector<int64_t>& ext)
 void serve_loop(ecris_server* s)
 {
     cudaSetDevice(s->device);
+    const cudaStream_t bs = ecris::batch_stream(s->batch);
     std::vector<int64_t> ext;
+    std::vector<Served*> waiting;   // runs with a snapshot enqueued in the previous tick
     for (;;) {
         // 1. admission, in arrival order
         std::vector<Served*> admit;
         {
             std::unique_lock<std::mutex> lock(s->mu);
             if (s->stop) break;
-            if (s->active.empty() && s->queue.empty()) {
+            if (s->active.empty() && s->queue.empty() && waiting.empty()) {
                 s->cv.wait_for(lock, std::chrono::milliseconds(20));
                 continue;
             }
@@ -177,10 +219,13 @@ void serve_loop(ecris_server* s)
         }
         for (Served* v : admit) {
             const ecris_request& r = v->req->r;
-            const ecris_status st = ecris_batch_add_run(s->batch, &r.geo, &r.bf, &r.grid, &r.sp, &r.mcc, r.n, r.xyzv,
-                                                        r.q, r.weight, r.seed, r.dt, 0, &v->run);
+            ecris_status st = take_slot(s, v) ? ECRIS_OK : ECRIS_ENOMEM;
+            if (st == ECRIS_OK)
+                st = ecris_batch_add_run(s->batch, &r.geo, &r.bf, &r.grid, &r.sp, &r.mcc, r.n, r.xyzv, r.q, r.weight,
+                                         r.seed, r.dt, 0, &v->run);
             std::lock_guard<std::mutex> lock(s->mu);
             if (st != ECRIS_OK) {
+                give_slot(s, v);
                 finish(s, v, ECRIS_REQ_FAILED, ecris_batch_last_error(s->batch));
                 ++s->n_done;
                 continue;
@@ -189,45 +234,71 @@ void serve_loop(ecris_server* s)
             v->res.t_admit = now_s(s);
             s->active.push_back(v);
         }
-        if (s->active.empty()) continue;
-        // 2. one tick of the whole batch
-        if (ecris_batch_step(s->batch, s->steps_per_tick) != ECRIS_OK) {
-            std::lock_guard<std::mutex> lock(s->mu);
-            s->err = ecris_batch_last_error(s->batch);
-            for (Served* v : s->active) finish(s, v, ECRIS_REQ_FAILED, s->err.c_str());
-            s->n_done += (int64_t)s->active.size();
-            s->active.clear();
-            continue;
-        }
-        // 3. window boundaries: convergence or cap; retire finished runs
-        std::vector<Served*> keep;
-        double advanced = 0.0;
-        for (Served* v : s->active) {
-            const ecris_request& r = v->req->r;
-            v->res.steps += s->steps_per_tick;
-            advanced += (double)r.n * s->steps_per_tick;
-            if (v->res.steps % r.window_steps != 0) {
-                keep.push_back(v);
+        // 2. one tick of the whole batch, and the snapshots at window boundaries
+        std::vector<Served*> taken;
+        if (!s->active.empty()) {
+            if (ecris_batch_step(s->batch, s->steps_per_tick) != ECRIS_OK) {
+                std::lock_guard<std::mutex> lock(s->mu);
+                s->err = ecris_batch_last_error(s->batch);
+                for (Served* v : s->active) finish(s, v, ECRIS_REQ_FAILED, s->err.c_str());
+                s->n_done += (int64_t)s->active.size();
+                s->active.clear();
+                waiting.clear();
                 continue;
             }
-            const bool ok_diag = read_diag(s, v, ext);
-            const bool conv = ok_diag && converged(v, ext);
-            const bool cap = v->res.steps >= r.max_steps;
-            if (ok_diag && !conv && !cap) {
-                keep.push_back(v);
-                continue;
+            double advanced = 0.0;
+            for (Served* v : s->active) {
+                const ecris_request& r = v->req->r;
+                v->issued += s->steps_per_tick;
+                advanced += (double)r.n * s->steps_per_tick;
+                if (v->issued % r.window_steps == 0 &&
+                    ecris::batch_snapshot(s->batch, v->run, v->snap) == ECRIS_OK &&
+                    cudaEventRecord(v->ev, bs) == cudaSuccess) {
+                    v->snap_steps = v->issued;
+                    taken.push_back(v);
+                }
+            }
+            std::lock_guard<std::mutex> lock(s->mu);
+            s->ion_steps += advanced;
+        }
+        // 3. the previous tick's snapshots, read while this tick runs
+        std::vector<std::pair<Served*, int32_t>> retire;
+        for (Served* v : waiting) {
+            const bool landed = cudaEventSynchronize(v->ev) == cudaSuccess;
+            const ecris_request& r = v->req->r;
+            ecris_result res;
+            {
+                std::lock_guard<std::mutex> lock(s->mu);
+                res = v->res;
+            }
+            const bool ok_diag = landed && read_snapshot(s, v, ext, res);
+            const bool conv = ok_diag && converged(v, ext, res);
+            const bool cap = v->snap_steps >= r.max_steps;
+            res.converged = conv ? 1 : 0;
+            {
+                std::lock_guard<std::mutex> lock(s->mu);
+                v->res = res;   // the result at this boundary, visible to poll
+            }
+            if (ok_diag && !conv && !cap) continue;
+            retire.push_back({v, ok_diag ? ECRIS_REQ_DONE : ECRIS_REQ_FAILED});
+        }
+        for (auto& rv : retire) {
+            Served* v = rv.first;
+            // a snapshot of the run enqueued this tick must land before its slot is reused
+            auto it = std::find(taken.begin(), taken.end(), v);
+            if (it != taken.end()) {
+                cudaEventSynchronize(v->ev);
+                taken.erase(it);
             }
             ecris_batch_remove_run(s->batch, v->run);
+            give_slot(s, v);
             std::lock_guard<std::mutex> lock(s->mu);
-            v->res.converged = conv ? 1 : 0;
-            finish(s, v, ok_diag ? ECRIS_REQ_DONE : ECRIS_REQ_FAILED,
-                   ok_diag ? nullptr : ecris_batch_last_error(s->batch));
+            finish(s, v, rv.second, rv.second == ECRIS_REQ_DONE ? nullptr : "device error word set (bounded wait ran out)");
             v->req.reset();   // the host copy of the inputs is no longer needed
+            s->active.erase(std::find(s->active.begin(), s->active.end(), v));
             ++s->n_done;
         }
-        std::lock_guard<std::mutex> lock(s->mu);
-        s->active.swap(keep);
-        s->ion_steps += advanced;
+        waiting.swap(taken);
     }
 }
 
@@ -274,6 +345,9 @@ void ecris_server_destroy(ecris_server* s)
     s->cv.notify_all();
     if (s->loop.joinable()) s->loop.join();
     ecris_batch_destroy(s->batch);
+    for (auto& kv : s->all) give_slot(s, kv.second.get());
+    for (auto* p : s->free_snaps) cudaFreeHost(p);
+    for (auto e : s->free_events) cudaEventDestroy(e);
     delete s;
 }
 

@@ -85,7 +85,9 @@ def test_served_results_equal_runs_alone(E):
         assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
     s = srv.stats()
     assert s["done"] == 3 and s["queued"] == 0 and s["running"] == 0
-    assert s["ion_steps"] == sum(len(st["x"]) * r["steps"] for r, (_, st, _) in zip(res, sp))
+    # each run is stepped up to one tick (4 steps) past the boundary it retired at
+    used = sum(len(st["x"]) * r["steps"] for r, (_, st, _) in zip(res, sp))
+    assert used <= s["ion_steps"] <= used + sum(len(st["x"]) * 4 for _, st, _ in sp)
     srv.close()
 
 
