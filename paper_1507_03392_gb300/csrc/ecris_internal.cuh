@@ -195,12 +195,12 @@ __device__ __forceinline__ void bfield(const RunDev& R, float x, float y, float 
 {
     float b0, b1, b2, s, c;
     if (z <= R.zm) {
-        sincospif(z * R.inv_zm, &s, &c);
+        __sincosf(3.14159265358979f * (z * R.inv_zm), &s, &c);   // argument in [0, pi]
         b0 = R.B_min + R.aL * (1.0f + c);
         b1 = -R.aLk * s;
         b2 = -R.aLk2 * c;
     } else {
-        sincospif((z - R.zm) * R.inv_zr, &s, &c);
+        __sincosf(3.14159265358979f * ((z - R.zm) * R.inv_zr), &s, &c);
         b0 = R.B_min + R.aR * (1.0f - c);
         b1 = R.aRk * s;
         b2 = R.aRk2 * c;

@@ -247,8 +247,13 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
         const float D = sqrtf(R.ei_coef[zone] * cr.x * qp);
         const float ct = 2.0f * unit01(w.w2) - 1.0f;
         const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+        // azimuth 2 pi u through the fast intrinsic, kept inside [-pi, pi]
+        // where its absolute error is below 2^-21: (cos, sin)(2 pi u) =
+        // -(cos, sin)(pi (2u - 1))
         float sp, cp;
-        sincospif(2.0f * unit01(w.w3), &sp, &cp);
+        __sincosf(3.14159265358979f * (2.0f * unit01(w.w3) - 1.0f), &sp, &cp);
+        sp = -sp;
+        cp = -cp;
         const float dxv = st * cp + cr.z, dyv = st * sp + cr.w, dzv = ct;
         const float m2 = dxv * dxv + dyv * dyv + dzv * dzv;
         if (m2 > 0.0f) {
