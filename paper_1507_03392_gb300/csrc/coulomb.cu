@@ -329,7 +329,7 @@ __device__ __forceinline__ uint32_t start_kind(uint32_t r, uint32_t m)
     return (r & 1u) ? 0u : 1u;
 }
 
-__global__ void __launch_bounds__(256) k_cells(const __grid_constant__ RunDev R, uint32_t ncells, unsigned int* ticket)
+__global__ void __launch_bounds__(256, 5) k_cells(const __grid_constant__ RunDev R, uint32_t ncells, unsigned int* ticket)
 {
     extern __shared__ __align__(16) unsigned char cell_smem_raw[];
     CellSmem& S = *reinterpret_cast<CellSmem*>(cell_smem_raw);
