@@ -70,7 +70,7 @@ constexpr int kScanBlock = kScanThreads * kScanPerThread;
 
 // Device parameter block of one run: FP32 constants of the kernels (built in
 // FP64 on the host) and the run's device arrays.
-struct RunDev {
+struct alignas(16) RunDev {
     // geometry
     float R0, R0sq, L, r_ap_sq, eps_wall;
     float inlet_x, inlet_y, inlet_z;

@@ -426,7 +426,8 @@ struct Stage {
 
 struct StepShared {
     Stage st[2];
-    uint32_t npart;
+    RunDev rs[2];          // batch form: the stage's run parameter block (copied with the tile)
+    uint32_t npart[2];     // Coulomb participants of the stage's tile
     uint64_t bar[2];
     int failed;
 };
@@ -435,13 +436,15 @@ __device__ __forceinline__ float& sf(float4* a, uint32_t i) { return reinterpret
 __device__ __forceinline__ uint32_t& su(uint4* a, uint32_t i) { return reinterpret_cast<uint32_t*>(a)[i]; }
 __device__ __forceinline__ int32_t& si(int4* a, uint32_t i) { return reinterpret_cast<int32_t*>(a)[i]; }
 
-// issue the eight bulk loads of tile t into stage st (thread 0 only)
-__device__ __forceinline__ void load_tile(const RunDev& R, Stage& st, uint64_t* bar, uint32_t t)
+// issue the eight bulk loads of tile t into stage st (thread 0 only); in the
+// batch form also the run's parameter block into *rs, on the same barrier
+__device__ __forceinline__ void load_tile(const RunDev& R, Stage& st, uint64_t* bar, uint32_t t, RunDev* rs)
 {
     const uint32_t g0 = t * kTileGroups;
     const uint32_t ng = min((uint32_t)kTileGroups, R.n4 - g0);
     const uint32_t bytes = ng * 16u;
-    mbar_expect_tx(bar, 8u * bytes);
+    mbar_expect_tx(bar, 8u * bytes + (rs ? (uint32_t)sizeof(RunDev) : 0u));
+    if (rs) bulk_load(rs, &R, (uint32_t)sizeof(RunDev), bar);
     bulk_load(st.x, reinterpret_cast<const int4*>(R.x) + g0, bytes, bar);
     bulk_load(st.y, reinterpret_cast<const int4*>(R.y) + g0, bytes, bar);
     bulk_load(st.z, reinterpret_cast<const int4*>(R.z) + g0, bytes, bar);
@@ -518,11 +521,6 @@ struct BatchRuns {
     __device__ __forceinline__ const RunDev& global(uint32_t r) const { return runs[r]; }
 };
 
-// Persistent pass over the work items, two tiles in flight per block: while
-// the block advances one tile in one stage, the TMA engine brings the next
-// into the other stage; results leave through bulk stores.  The particles are
-// kept sorted by (ion/atom, cell), so each thread takes slots tid, tid + 256,
-// ... straight from the stage and the warps stay on one branch.
 // List the particles of this lane that left the chamber (leave) for the
 // leaver pass: one global atomic per warp.
 __device__ __forceinline__ void list_leavers(const RunDev& R, bool leave, uint32_t slot)
@@ -536,24 +534,34 @@ __device__ __forceinline__ void list_leavers(const RunDev& R, bool leave, uint32
     if (leave) R.leave[base + (uint32_t)__popc(m & ((1u << lane) - 1u))] = slot;
 }
 
+// Persistent pass over the work items, two tiles in flight per block: while
+// the block advances one tile in one stage, the TMA engine brings the next
+// into the other stage; results leave through bulk stores.  The particles are
+// kept sorted by (ion/atom, cell), so each thread takes slots tid, tid + 256,
+// ... straight from the stage and the warps stay on one branch.
 template <bool kBatch, class Src>
-__device__ __forceinline__ void step_tiles(StepShared& S, RunDev* Rs, const Src& src)
+__device__ __forceinline__ void step_tiles(StepShared& S, const Src& src)
 {
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
+        S.npart[0] = 0u;
+        S.npart[1] = 0u;
         S.failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    uint32_t cur_run = 0xFFFFFFFFu;
     __syncthreads();
     const uint32_t nitems = src.count();
     uint32_t i = blockIdx.x;
     if (tid == 0 && i < nitems) {
         const uint2 it0 = src.item(i);
-        load_tile(src.global(it0.x), S.st[0], &S.bar[0], it0.y);
+        load_tile(src.global(it0.x), S.st[0], &S.bar[0], it0.y, kBatch ? &S.rs[0] : nullptr);
     }
+    // Two block barriers per tile: after the copies land, and before the
+    // stores.  Stage s ^ 1 is free when a tile starts: every thread stopped
+    // reading or writing it before the previous tile's second barrier, and
+    // thread 0 waits for its bulk stores to have read it.
     for (uint32_t it = 0; i < nitems; ++it, i += gridDim.x) {
         const uint32_t s = it & 1u;
         Stage& st = S.st[s];
@@ -562,20 +570,18 @@ __device__ __forceinline__ void step_tiles(StepShared& S, RunDev* Rs, const Src&
         if (tid == 0 && in < nitems) {
             const uint2 itn = src.item(in);
             bulk_wait_read_all();   // the other stage's previous stores have read their data
-            load_tile(src.global(itn.x), S.st[s ^ 1u], &S.bar[s ^ 1u], itn.y);
+            load_tile(src.global(itn.x), S.st[s ^ 1u], &S.bar[s ^ 1u], itn.y, kBatch ? &S.rs[s ^ 1u] : nullptr);
         }
-        if (kBatch && item.x != cur_run) {
-            // stage this run's parameter block (all threads, one word each)
-            const uint32_t* g = reinterpret_cast<const uint32_t*>(&src.global(item.x));
-            uint32_t* d = reinterpret_cast<uint32_t*>(Rs);
-            for (uint32_t w = tid; w < sizeof(RunDev) / 4; w += kThreads) d[w] = g[w];
-            cur_run = item.x;
+        // the block stops together if any thread's wait ran out
+        const bool ok = mbar_wait(&S.bar[s], (it >> 1) & 1u);
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            if (tid == 0) {
+                S.failed = 1;
+                atomicExch(src.global(item.x).err, kErrTimeout);
+            }
+            break;
         }
-        if (tid == 0) S.npart = 0u;
-        if (!mbar_wait(&S.bar[s], (it >> 1) & 1u)) S.failed = 1;
-        __syncthreads();
-        if (S.failed) break;
-        const RunDev& R = kBatch ? *Rs : src.global(0);
+        const RunDev& R = kBatch ? S.rs[s] : src.global(0);
         const bool coulomb = (R.flags & kFCoulomb) != 0;
         const uint32_t step = *R.step;
         const uint32_t t = item.y;
@@ -600,7 +606,7 @@ __device__ __forceinline__ void step_tiles(StepShared& S, RunDev* Rs, const Src&
                 sf(st.vx, k) = vx; sf(st.vy, k) = vy; sf(st.vz, k) = vz;
                 su(st.meta, k) = meta;
             }
-            if (coulomb) publish_warp(R, S.npart, t, t * kTile + k, ck, id, vx, vy, vz, meta & kQMask);
+            if (coulomb) publish_warp(R, S.npart[s], t, t * kTile + k, ck, id, vx, vy, vz, meta & kQMask);
         }
         fence_proxy_async();    // make this thread's stage writes visible to the bulk stores
         __syncthreads();
@@ -615,14 +621,14 @@ __device__ __forceinline__ void step_tiles(StepShared& S, RunDev* Rs, const Src&
             bulk_store(reinterpret_cast<float4*>(R.vz) + g0, st.vz, bytes);
             bulk_store(reinterpret_cast<uint4*>(R.meta) + g0, st.meta, bytes);
             bulk_commit();
-            if (coulomb) R.tcount[t] = S.npart;
+            // the stage's count is next used two tiles on, past the next barrier
+            if (coulomb) R.tcount[t] = S.npart[s];
+            S.npart[s] = 0u;
         }
-        __syncthreads();
     }
     if (tid == 0) {
         bulk_wait_all();        // stores complete before the block retires
         if (S.failed) {
-            atomicExch((kBatch ? *Rs : src.global(0)).err, kErrTimeout);
             // the loads this block issued may still land: wait (bounded) for them
             mbar_wait(&S.bar[0], 0u);
             mbar_wait(&S.bar[1], 0u);
@@ -634,7 +640,7 @@ __global__ void __launch_bounds__(kThreads, kStepMinBlocks) k_step(const __grid_
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     StepShared& S = *reinterpret_cast<StepShared*>(smem_raw);
-    step_tiles<false>(S, nullptr, SingleRun{R, ntiles});
+    step_tiles<false>(S, SingleRun{R, ntiles});
 }
 
 // batch form: one persistent launch over the tiles of many runs
@@ -643,8 +649,7 @@ __global__ void __launch_bounds__(kThreads, kStepMinBlocks) k_step_batch(const R
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     StepShared& S = *reinterpret_cast<StepShared*>(smem_raw);
-    RunDev* Rs = reinterpret_cast<RunDev*>(smem_raw + ((sizeof(StepShared) + 15) & ~(size_t)15));
-    step_tiles<true>(S, Rs, BatchRuns{runs, items, nitems});
+    step_tiles<true>(S, BatchRuns{runs, items, nitems});
 }
 
 // The leaver pass of one run: finish the step of every listed particle, add
@@ -830,7 +835,7 @@ int step_blocks_per_sm()
     return b;
 }
 
-constexpr size_t kBatchSmem = ((sizeof(StepShared) + 15) & ~(size_t)15) + sizeof(RunDev);
+constexpr size_t kBatchSmem = sizeof(StepShared);
 
 int step_batch_blocks_per_sm()
 {
