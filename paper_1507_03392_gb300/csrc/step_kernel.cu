@@ -558,10 +558,11 @@ __device__ __forceinline__ void step_tiles(StepShared& S, const Src& src)
         const uint2 it0 = src.item(i);
         load_tile(src.global(it0.x), S.st[0], &S.bar[0], it0.y, kBatch ? &S.rs[0] : nullptr);
     }
-    // Two block barriers per tile: after the copies land, and before the
-    // stores.  Stage s ^ 1 is free when a tile starts: every thread stopped
-    // reading or writing it before the previous tile's second barrier, and
-    // thread 0 waits for its bulk stores to have read it.
+    // One block barrier per tile, before the stores.  Stage s ^ 1 is free
+    // when a tile starts: every thread stopped reading or writing it before
+    // the previous tile's barrier, and thread 0 waits for its bulk stores to
+    // have read it.  A stage's participant count is reset by thread 0 after
+    // the barrier and used again two tiles on, past the next barrier.
     for (uint32_t it = 0; i < nitems; ++it, i += gridDim.x) {
         const uint32_t s = it & 1u;
         Stage& st = S.st[s];
@@ -572,8 +573,39 @@ __device__ __forceinline__ void step_tiles(StepShared& S, const Src& src)
             bulk_wait_read_all();   // the other stage's previous stores have read their data
             load_tile(src.global(itn.x), S.st[s ^ 1u], &S.bar[s ^ 1u], itn.y, kBatch ? &S.rs[s ^ 1u] : nullptr);
         }
-        // the block stops together if any thread's wait ran out
-        const bool ok = mbar_wait(&S.bar[s], (it >> 1) & 1u);
+        // a warp whose wait ran out (in any lane) leaves the tile alone; the
+        // block learns of it at the barrier and stops there
+        const bool ok = __all_sync(0xFFFFFFFFu, mbar_wait(&S.bar[s], (it >> 1) & 1u));
+        const uint32_t t = item.y;
+        if (ok) {
+            const RunDev& R = kBatch ? S.rs[s] : src.global(0);
+            const bool coulomb = (R.flags & kFCoulomb) != 0;
+            const uint32_t step = *R.step;
+            const uint32_t nslot = min((uint32_t)kTile, 4u * (R.n4 - t * kTileGroups));
+            // thread tid takes slots tid, tid + 256, ... (kVec of them) of the
+            // tile: a warp covers 32 consecutive slots (one kind of particle, few
+            // cells), the shared-memory accesses are free of bank conflicts, and
+            // every particle runs through the same single copy of the code
+#pragma unroll 1
+            for (uint32_t j = 0; j < (uint32_t)kVec; ++j) {
+                const uint32_t k = (uint32_t)tid + j * kThreads;
+                uint32_t meta = k < nslot ? su(st.meta, k) : kStPad;
+                int32_t x = si(st.x, k), y = si(st.y, k), z = si(st.z, k);
+                float vx = sf(st.vx, k), vy = sf(st.vy, k), vz = sf(st.vz, k);
+                const uint32_t id = su(st.id, k);
+                uint32_t ck, dc;
+                const bool leave = step_particle(R, id, step, x, y, z, vx, vy, vz, meta, ck, dc);
+                deposit_warp(R, dc, meta & kQMask);
+                list_leavers(R, leave, t * kTile + k);
+                if (k < nslot) {
+                    si(st.x, k) = x; si(st.y, k) = y; si(st.z, k) = z;
+                    sf(st.vx, k) = vx; sf(st.vy, k) = vy; sf(st.vz, k) = vz;
+                    su(st.meta, k) = meta;
+                }
+                if (coulomb) publish_warp(R, S.npart[s], t, t * kTile + k, ck, id, vx, vy, vz, meta & kQMask);
+            }
+        }
+        fence_proxy_async();    // make this thread's stage writes visible to the bulk stores
         if (__syncthreads_or(ok ? 0 : 1)) {
             if (tid == 0) {
                 S.failed = 1;
@@ -581,36 +613,9 @@ __device__ __forceinline__ void step_tiles(StepShared& S, const Src& src)
             }
             break;
         }
-        const RunDev& R = kBatch ? S.rs[s] : src.global(0);
-        const bool coulomb = (R.flags & kFCoulomb) != 0;
-        const uint32_t step = *R.step;
-        const uint32_t t = item.y;
-        const uint32_t nslot = min((uint32_t)kTile, 4u * (R.n4 - t * kTileGroups));
-        // thread tid takes slots tid, tid + 256, ... (kVec of them) of the
-        // tile: a warp covers 32 consecutive slots (one kind of particle, few
-        // cells), the shared-memory accesses are free of bank conflicts, and
-        // every particle runs through the same single copy of the code
-#pragma unroll 1
-        for (uint32_t j = 0; j < (uint32_t)kVec; ++j) {
-            const uint32_t k = (uint32_t)tid + j * kThreads;
-            uint32_t meta = k < nslot ? su(st.meta, k) : kStPad;
-            int32_t x = si(st.x, k), y = si(st.y, k), z = si(st.z, k);
-            float vx = sf(st.vx, k), vy = sf(st.vy, k), vz = sf(st.vz, k);
-            const uint32_t id = su(st.id, k);
-            uint32_t ck, dc;
-            const bool leave = step_particle(R, id, step, x, y, z, vx, vy, vz, meta, ck, dc);
-            deposit_warp(R, dc, meta & kQMask);
-            list_leavers(R, leave, t * kTile + k);
-            if (k < nslot) {
-                si(st.x, k) = x; si(st.y, k) = y; si(st.z, k) = z;
-                sf(st.vx, k) = vx; sf(st.vy, k) = vy; sf(st.vz, k) = vz;
-                su(st.meta, k) = meta;
-            }
-            if (coulomb) publish_warp(R, S.npart[s], t, t * kTile + k, ck, id, vx, vy, vz, meta & kQMask);
-        }
-        fence_proxy_async();    // make this thread's stage writes visible to the bulk stores
-        __syncthreads();
         if (tid == 0) {
+            const RunDev& R = kBatch ? S.rs[s] : src.global(0);
+            const bool coulomb = (R.flags & kFCoulomb) != 0;
             const uint32_t g0 = t * kTileGroups;
             const uint32_t bytes = min((uint32_t)kTileGroups, R.n4 - g0) * 16u;
             bulk_store(reinterpret_cast<int4*>(R.x) + g0, st.x, bytes);
