@@ -225,6 +225,8 @@ struct KernelTimer {
 
 }  // namespace
 
+constexpr uint32_t kSortAfterLoad = 8;   // steps of one ecris_step call that sort a fresh load first
+
 struct ecris_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -272,6 +274,8 @@ struct ecris_ctx {
     uint4* d_aos = nullptr;        // 32-byte particle records for the sort
     uint32_t sort_every = 32;      // steps between sorts
     uint32_t since_sort = 0;
+    bool fresh = false;         // loaded, not yet sorted
+    uint32_t calls_since_load = 0;
     int parity = 0;                // which particle set is current (flips at each sort)
     // captured per-step kernel sequences, by particle set and kind (0: the
     // whole step, 1: the collision kernels only), valid for param_version
@@ -604,6 +608,7 @@ ecris_status sort_particles(ecris_ctx* ctx)
     R.meta = ctx->d_meta;
     R.id = ctx->d_id;
     ctx->since_sort = 0;
+    ctx->fresh = false;
     ctx->parity ^= 1;
     return ECRIS_OK;
 }
@@ -942,7 +947,14 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
     ctx->time_s = 0.0;
     ctx->dt_loaded = -1.0;
     ctx->since_fold = 0;
-    ctx->since_sort = ctx->sort_every;   // group the particles before the first step
+    // a load leaves the particles in load order.  The first ecris_step call
+    // after it groups them first only if it runs kSortAfterLoad or more
+    // steps; a shorter first call (a load, a step and a read-back, say) steps
+    // them as they are, and the next call sorts (the sort costs several
+    // steps' time)
+    ctx->since_sort = 0;
+    ctx->fresh = true;
+    ctx->calls_since_load = 0;
     ++ctx->param_version;
     // fold the packed deposit before its low word (charge) can carry
     const double per_step = (double)(n ? n : 1) * (h.qmax > 1 ? h.qmax : 1);
@@ -968,7 +980,9 @@ ecris_status ecris_step(ecris_ctx* ctx, uint32_t nsteps, double dt)
     const bool coulomb = (ctx->h.mcc.flags & kFCoulomb) != 0;
     const uint32_t nc = (uint32_t)((size_t)ctx->h.nx * ctx->h.ny * ctx->h.nz);
     for (uint32_t s = 0; s < nsteps; ++s) {
-        if (ctx->since_sort >= ctx->sort_every && ctx->n4 > 0) {
+        const bool due = ctx->since_sort >= ctx->sort_every ||
+                         (ctx->fresh && s == 0 && (nsteps >= kSortAfterLoad || ctx->calls_since_load > 0));
+        if (due && ctx->n4 > 0) {
             st = sort_particles(ctx);
             if (st != ECRIS_OK) return st;
         }
@@ -1002,6 +1016,7 @@ ecris_status ecris_step(ecris_ctx* ctx, uint32_t nsteps, double dt)
         ++ctx->since_sort;
     }
     ctx->steps_done += nsteps;
+    ++ctx->calls_since_load;
     ctx->time_s += dt * nsteps;
     return ECRIS_OK;
 }
@@ -1499,6 +1514,7 @@ ecris_status ecris_batch_add_run(ecris_batch* b, const ecris_geometry* geo, cons
     }
     c->stream = b->stream;
     c->sort_every = b->sort_every;
+    c->since_sort = c->sort_every;   // a batch run is grouped before its first step
     int32_t h = -1;
     for (size_t r = 0; r < b->runs.size(); ++r)
         if (!b->runs[r]) {
