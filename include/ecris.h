@@ -199,6 +199,25 @@ ecris_status ecris_step(ecris_ctx* ctx, uint32_t nsteps, double dt);
 /* Copy the diagnostics of the run to caller memory (synchronises). */
 ecris_status ecris_diag(ecris_ctx* ctx, ecris_diag_out* out);
 
+/* Self-consistent electron density (Sec. II: the electron density equals the
+ * ion charge density, by charge neutrality).  Replaces the prescribed n_e of
+ * every cell by the time-averaged ion charge density since the load or the
+ * previous call:
+ *     n_e(c) = w * sum over steps and particles in c of Q / (steps * V_cell),
+ * with w the load's weight, V_cell = (2 R0/nx)(2 R0/ny)(L/nz) and the
+ * deposit that ecris_diag reports as cell_charge (ions after each step's
+ * move, NGP), and rebuilds each cell's delta from it (the 3x3 stencil and
+ * R_L of the heating kick, Sec. II).  The zones (warm / cold electrons) stay
+ * as |B| gave them.  Cells without ions get n_e = 0 (no ionisation, no
+ * heating).  Synchronises the context's stream.  ECRIS_ESTATE when no step
+ * ran since the load or the previous call; the run is unchanged then. */
+ecris_status ecris_update_ne(ecris_ctx* ctx);
+
+/* Copy the per-cell electron data the kernels read to host memory: n_e in
+ * m^-3 and the two delta components, nx*ny*nz floats each in cell order
+ * (ix fastest); any pointer may be NULL.  Synchronises. */
+ecris_status ecris_get_cells(ecris_ctx* ctx, float* ne, float* delta_x, float* delta_y);
+
 /* Copy the particle state out: xyzv[0..5] n floats each, meta n words (see
  * ECRIS_META_Q / ECRIS_EV_* / ECRIS_ST_*), any pointer may be NULL.  Host
  * pointers when dst_is_device == 0 (synchronises), device pointers otherwise
@@ -271,6 +290,10 @@ ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps);
 ecris_status ecris_batch_diag(ecris_batch* b, int32_t run, ecris_diag_out* out);
 ecris_status ecris_batch_get_state(ecris_batch* b, int32_t run, float* const xyzv[6], uint32_t* meta,
                                    int dst_is_device);
+/* ecris_update_ne / ecris_get_cells for one run of the batch (ordered after
+ * its queued steps; synchronises the batch stream). */
+ecris_status ecris_batch_update_ne(ecris_batch* b, int32_t run);
+ecris_status ecris_batch_get_cells(ecris_batch* b, int32_t run, float* ne, float* delta_x, float* delta_y);
 /* Bytes held by the batch's runs and its budget (0: none). */
 ecris_status ecris_batch_memory(const ecris_batch* b, size_t* used, size_t* budget);
 /* Kernel timing for a batch, as ecris_set_profiling / ecris_get_profile:

@@ -27,8 +27,9 @@
  *
  * Functions whose result is pinned by the CPU tests: or_philox (library
  * Philox), or_b0/or_bfield (closed forms, div/curl), or_efield (exact for
- * linear fields), or_lotz_rate (E1 closed form), or_setup_cells (delta on a
- * linear ramp), or_step (Boris closed forms, mirror invariant, 0-D Markov
+ * linear fields), or_lotz_rate (E1 closed form), or_setup_cells and
+ * or_cell_delta (delta on a linear ramp, via a prescribed n_e and via the
+ * self-consistent n_e of resting ions), or_step (Boris closed forms, mirror invariant, 0-D Markov
  * chains for ionisation and charge exchange, kick moments, wall sampler
  * moments, conservation laws, brute-force deposit), or_nanbu_* (mean cos chi,
  * pair conservation).
@@ -317,6 +318,9 @@ void or_build_rates(const or_params *p, const double *ip_eV, const int32_t *n_ou
 /* R_L = 2.38e-6 sqrt(T_e) / (B dX); neighbours outside the mesh take the    */
 /* edge cell's value and a cell with n_e = 0 gets delta = 0.                 */
 /* ------------------------------------------------------------------------ */
+void or_cell_delta(const or_params *p, const double *ne, const int32_t *zone, const double *Bmag,
+                   double *dlx, double *dly);
+
 void or_setup_cells(const or_params *p, const float *ne_in_cells, double ne_in_cm3,
                     double ne_out_cm3, double *ne, int32_t *zone, double *Bmag,
                     double *dlx, double *dly)
@@ -335,6 +339,17 @@ void or_setup_cells(const or_params *p, const float *ne_in_cells, double ne_in_c
                 double nin = ne_in_cells ? (double)ne_in_cells[c] : ne_in_cm3;
                 ne[c] = (zone[c] ? nin : ne_out_cm3) * 1e6;
             }
+    or_cell_delta(p, ne, zone, Bmag, dlx, dly);
+}
+
+/* delta of every cell from n_e (m^-3), the zone flags and |B|: the stencil   */
+/* and R_L above.  Called at setup and again whenever n_e is replaced by the */
+/* ions' charge density (Sec. II, charge neutrality).                         */
+void or_cell_delta(const or_params *p, const double *ne, const int32_t *zone, const double *Bmag,
+                   double *dlx, double *dly)
+{
+    int nx = p->nx, ny = p->ny, nz = p->nz;
+    double dx = or_dx(p);
     for (int iz = 0; iz < nz; ++iz)
         for (int iy = 0; iy < ny; ++iy)
             for (int ix = 0; ix < nx; ++ix) {

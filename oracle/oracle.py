@@ -81,6 +81,7 @@ def lib():
         _lib.or_lotz_rate.restype = d
         _lib.or_build_rates.argtypes = [pp, p, p, p]
         _lib.or_setup_cells.argtypes = [pp, p, d, d, p, p, p, p, p]
+        _lib.or_cell_delta.argtypes = [pp, p, p, p, p, p]
         _lib.or_boris.argtypes = [d, p, p, d, p]
         _lib.or_emit.argtypes = [d, p, p, p, p, p]
         _lib.or_nanbu_A.argtypes = [d]
@@ -184,6 +185,8 @@ class OracleRun:
         self.events = np.zeros(self.n, dtype=np.uint8)
         self.guard = np.zeros(self.n, dtype=np.uint8)
         self.step_index = 0
+        self.ne_mark_charge = None if self.dep_charge is None else self.dep_charge.copy()
+        self.ne_mark_step = 0
 
     def set_state(self, s):
         for k in ("x", "y", "z", "vx", "vy", "vz"):
@@ -210,6 +213,26 @@ class OracleRun:
         if accumulate_guard:
             self.events_acc, self.guard_acc = acc_ev, acc_g
         return self
+
+    def update_ne(self):
+        """Self-consistent electron density (Sec. II, charge neutrality): n_e
+        of each cell becomes the ion charge density, w times the charge the
+        cell collected since the previous update (or the start), averaged over
+        the steps in between and divided by the cell volume; delta is then
+        rebuilt from the new n_e."""
+        if self.dep_charge is None:
+            raise ValueError("update_ne needs the deposit")
+        steps = self.step_index - self.ne_mark_step
+        if steps <= 0:
+            raise ValueError("update_ne: no step since the previous update")
+        rp = self.rp
+        vol = (2.0 * rp.R0 / rp.nx) * (2.0 * rp.R0 / rp.ny) * (rp.L / rp.nz)
+        dq = (self.dep_charge - self.ne_mark_charge).astype(np.float64)
+        self.ne = np.ascontiguousarray(rp.weight * dq / (steps * vol))
+        lib().or_cell_delta(ctypes.byref(self.p), _ptr(self.ne), _ptr(self.zone), _ptr(self.Bmag),
+                            _ptr(self.dlx), _ptr(self.dly))
+        self.ne_mark_charge = self.dep_charge.copy()
+        self.ne_mark_step = self.step_index
 
     def extracted(self):
         return np.array(self.tally.extracted[: self.rp.species.qmax + 1], dtype=np.int64)

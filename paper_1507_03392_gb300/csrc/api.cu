@@ -100,6 +100,9 @@ struct HostRun {
     ecris_mcc mcc;
     double zm;
     bool has_e = false;            // some cell of the E grid is nonzero
+    std::vector<double> bmag;      // |B| at the cell centres (T)
+    std::vector<unsigned long long> charge_mark;   // time-summed charge deposit at the last n_e update
+    uint64_t steps_mark = 0;       // steps at the last n_e update (or load)
 };
 
 // synthetic on-axis mirror and its first two derivatives
@@ -511,6 +514,47 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.ncells = (uint32_t)((size_t)h.nx * h.ny * h.nz);
 }
 
+// The per-cell records the kernels read, {n_e, zone, delta_x, delta_y}, from
+// n_e (m^-3) and the zone flags, in FP64: delta follows the printed stencil
+// (y-differences for delta_x, x-differences for delta_y) scaled by
+// R_L = 2.38e-6 sqrt(T_e) / (B dX) / n_e; neighbours outside the mesh take the
+// edge value and a cell with n_e = 0 gets delta = 0 (Sec. II).
+void cell_records(HostRun& h, const std::vector<double>& ne, const std::vector<unsigned char>& zone,
+                  std::vector<float4>& cell)
+{
+    const size_t nc = (size_t)h.nx * h.ny * h.nz;
+    const double dx = 2.0 * h.geo.R0 / h.nx;
+    cell.assign(nc, make_float4(0.f, 0.f, 0.f, 0.f));
+    h.cell_ne.assign(nc, 0.0f);
+    h.cell_zone.assign(nc, 0);
+    auto NE = [&](int iz, int iy, int ix) {
+        iy = iy < 0 ? 0 : (iy >= h.ny ? h.ny - 1 : iy);
+        ix = ix < 0 ? 0 : (ix >= h.nx ? h.nx - 1 : ix);
+        return ne[((size_t)iz * h.ny + iy) * h.nx + ix];
+    };
+    for (int iz = 0; iz < h.nz; ++iz)
+        for (int iy = 0; iy < h.ny; ++iy)
+            for (int ix = 0; ix < h.nx; ++ix) {
+                const size_t c = ((size_t)iz * h.ny + iy) * h.nx + ix;
+                double dlx = 0.0, dly = 0.0;
+                if (ne[c] > 0.0) {
+                    const double Te = zone[c] ? h.Te_w : h.Te_c;
+                    const double rl = 2.38e-6 * std::sqrt(Te) / (h.bmag[c] * dx) / ne[c];
+                    const double sx = NE(iz, iy - 1, ix) - NE(iz, iy + 1, ix) +
+                                      0.5 * (NE(iz, iy - 1, ix + 1) + NE(iz, iy - 1, ix - 1) -
+                                             NE(iz, iy + 1, ix - 1) - NE(iz, iy + 1, ix + 1));
+                    const double sy = NE(iz, iy, ix + 1) - NE(iz, iy, ix - 1) +
+                                      0.5 * (NE(iz, iy + 1, ix + 1) + NE(iz, iy - 1, ix + 1) -
+                                             NE(iz, iy + 1, ix - 1) - NE(iz, iy - 1, ix - 1));
+                    dlx = -rl * sx;
+                    dly = -rl * sy;
+                }
+                cell[c] = make_float4((float)ne[c], zone[c] ? 1.0f : 0.0f, (float)dlx, (float)dly);
+                h.cell_ne[c] = (float)ne[c];
+                h.cell_zone[c] = zone[c];
+            }
+}
+
 // upload the parameter block and rate table for step length dt
 ecris_status upload_dt(ecris_ctx* ctx, double dt)
 {
@@ -538,6 +582,61 @@ ecris_status upload_dt(ecris_ctx* ctx, double dt)
                        ctx->stream));
     ctx->dt_loaded = dt;
     ++ctx->param_version;
+    return ECRIS_OK;
+}
+
+// Self-consistent electron density (Sec. II: n_e equals the ion charge
+// density, by charge neutrality).  Folds the deposit, takes the charge each
+// cell received since the last update (or the load), time-averages it over
+// the steps in between, n_e = w sum(Q) / (steps V_cell), and rebuilds every
+// cell's {n_e, zone, delta} record from it (Sec. II, the delta stencil and
+// R_L of the heating kick).  The zones stay (they
+// follow |B|).  The parameter block, whose atom gate bounds n_e k_0 dt over
+// the cells, is rebuilt before the next step.
+ecris_status update_ne(ecris_ctx* ctx)
+{
+    HostRun& h = ctx->h;
+    if (ctx->steps_done <= h.steps_mark)
+        return fail(ctx, ECRIS_ESTATE, "update_ne: no step since the load or the last update");
+    const size_t nc = (size_t)h.nx * h.ny * h.nz;
+    CK(launch_fold(*ctx->h_run, (uint32_t)nc, ctx->d_count, ctx->d_charge, ctx->stream));
+    ctx->since_fold = 0;
+    std::vector<unsigned long long> charge(nc);
+    uint32_t err = 0;
+    CK(cudaMemcpyAsync(&err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(charge.data(), ctx->d_charge, nc * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (err) {
+        ctx->failed = true;
+        return fail(ctx, ECRIS_ETIMEOUT, "update_ne: a kernel's bounded wait for its tile copies ran out; reload");
+    }
+    const double vol = (2.0 * h.geo.R0 / h.nx) * (2.0 * h.geo.R0 / h.ny) * (h.geo.L / h.nz);
+    const double steps = (double)(ctx->steps_done - h.steps_mark);
+    std::vector<double> ne(nc);
+    for (size_t c = 0; c < nc; ++c)
+        ne[c] = ctx->weight * (double)(charge[c] - h.charge_mark[c]) / (steps * vol);
+    const std::vector<unsigned char> zone = h.cell_zone;
+    std::vector<float4> cell;
+    cell_records(h, ne, zone, cell);
+    CK(cudaMemcpyAsync(ctx->d_cell, cell.data(), nc * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));   // the host records die at return
+    h.charge_mark.swap(charge);
+    h.steps_mark = ctx->steps_done;
+    ctx->dt_loaded = -1.0;
+    return ECRIS_OK;
+}
+
+ecris_status get_cells(ecris_ctx* ctx, float* ne, float* delta_x, float* delta_y)
+{
+    const size_t nc = (size_t)ctx->h.nx * ctx->h.ny * ctx->h.nz;
+    std::vector<float4> cell(nc);
+    CK(cudaMemcpyAsync(cell.data(), ctx->d_cell, nc * sizeof(float4), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t c = 0; c < nc; ++c) {
+        if (ne) ne[c] = cell[c].x;
+        if (delta_x) delta_x[c] = cell[c].z;
+        if (delta_y) delta_y[c] = cell[c].w;
+    }
     return ECRIS_OK;
 }
 
@@ -761,36 +860,9 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
                     return fail(ctx, ECRIS_EINVAL, "init_fields: ne_in_cells[%zu] must be finite and >= 0", c);
                 ne[c] = 1e6 * (zone[c] ? nin : grid->ne_out_cm3);
             }
-    std::vector<float4> cell(nc);
-    h.cell_ne.assign(nc, 0.0f);
-    h.cell_zone.assign(nc, 0);
-    auto NE = [&](int iz, int iy, int ix) {
-        iy = iy < 0 ? 0 : (iy >= h.ny ? h.ny - 1 : iy);
-        ix = ix < 0 ? 0 : (ix >= h.nx ? h.nx - 1 : ix);
-        return ne[((size_t)iz * h.ny + iy) * h.nx + ix];
-    };
-    for (int iz = 0; iz < h.nz; ++iz)
-        for (int iy = 0; iy < h.ny; ++iy)
-            for (int ix = 0; ix < h.nx; ++ix) {
-                const size_t c = ((size_t)iz * h.ny + iy) * h.nx + ix;
-                double dlx = 0.0, dly = 0.0;
-                if (ne[c] > 0.0) {
-                    const double Te = zone[c] ? h.Te_w : h.Te_c;
-                    const double rl = 2.38e-6 * std::sqrt(Te) / (bm[c] * dx) / ne[c];
-                    // printed stencil: y-differences for delta_x, x-differences for delta_y
-                    const double sx = NE(iz, iy - 1, ix) - NE(iz, iy + 1, ix) +
-                                      0.5 * (NE(iz, iy - 1, ix + 1) + NE(iz, iy - 1, ix - 1) -
-                                             NE(iz, iy + 1, ix - 1) - NE(iz, iy + 1, ix + 1));
-                    const double sy = NE(iz, iy, ix + 1) - NE(iz, iy, ix - 1) +
-                                      0.5 * (NE(iz, iy + 1, ix + 1) + NE(iz, iy - 1, ix + 1) -
-                                             NE(iz, iy + 1, ix - 1) - NE(iz, iy - 1, ix - 1));
-                    dlx = -rl * sx;
-                    dly = -rl * sy;
-                }
-                cell[c] = make_float4((float)ne[c], zone[c] ? 1.0f : 0.0f, (float)dlx, (float)dly);
-                h.cell_ne[c] = (float)ne[c];
-                h.cell_zone[c] = zone[c];
-            }
+    h.bmag = bm;
+    std::vector<float4> cell;
+    cell_records(h, ne, zone, cell);
     std::vector<float4> E(nc, make_float4(0.f, 0.f, 0.f, 0.f));
     if (grid->E) {
         for (size_t c = 0; c < nc; ++c) {
@@ -944,6 +1016,8 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
     ctx->weight = weight;
     ctx->seed = seed;
     ctx->steps_done = 0;
+    ctx->h.charge_mark.assign(nc, 0ull);
+    ctx->h.steps_mark = 0;
     ctx->time_s = 0.0;
     ctx->dt_loaded = -1.0;
     ctx->since_fold = 0;
@@ -1087,6 +1161,23 @@ ecris_status ecris_diag(ecris_ctx* ctx, ecris_diag_out* out)
     }
     fill_diag(h, ctx->weight, tally, census, ctx->steps_done, ctx->time_s, out);
     return ECRIS_OK;
+}
+
+ecris_status ecris_update_ne(ecris_ctx* ctx)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    if (!ctx->loaded) return fail(ctx, ECRIS_ESTATE, "update_ne: call ecris_load_ions first");
+    if (ctx->failed) return fail(ctx, ECRIS_ESTATE, "update_ne: context failed earlier (%s)", ctx->err.c_str());
+    CK(cudaSetDevice(ctx->device));
+    return update_ne(ctx);
+}
+
+ecris_status ecris_get_cells(ecris_ctx* ctx, float* ne, float* delta_x, float* delta_y)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    if (!ctx->have_fields) return fail(ctx, ECRIS_ESTATE, "get_cells: call ecris_init_fields first");
+    CK(cudaSetDevice(ctx->device));
+    return get_cells(ctx, ne, delta_x, delta_y);
 }
 
 ecris_status ecris_get_state(ecris_ctx* ctx, float* const xyzv[6], uint32_t* meta, int dst_is_device)
@@ -1627,6 +1718,32 @@ ecris_status ecris_batch_diag(ecris_batch* b, int32_t run, ecris_diag_out* out)
     if (!run_live(b, run)) return bfail(b, ECRIS_EINVAL, "batch_diag: no such run");
     ecris_status st = ecris_diag(b->runs[run], out);
     if (st != ECRIS_OK) return bfail(b, st, "batch_diag: " + b->runs[run]->err);
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_update_ne(ecris_batch* b, int32_t run)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (!run_live(b, run)) return bfail(b, ECRIS_EINVAL, "batch_update_ne: no such run");
+    BCK(cudaSetDevice(b->device));
+    ecris_ctx* c = b->runs[run];
+    if (c->failed) return bfail(b, ECRIS_ESTATE, "batch_update_ne: the run failed earlier");
+    // the run's stream is the batch stream: the fold follows the queued steps
+    ecris_status st = update_ne(c);
+    if (st == ECRIS_OK) st = upload_dt(c, b->dt[run]);
+    if (st != ECRIS_OK) return bfail(b, st, "batch_update_ne: " + c->err);
+    b->params_dirty = true;
+    if (c->h.mcc.flags & kFCoulomb) b->graph_dirty = true;
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_get_cells(ecris_batch* b, int32_t run, float* ne, float* delta_x, float* delta_y)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (!run_live(b, run)) return bfail(b, ECRIS_EINVAL, "batch_get_cells: no such run");
+    BCK(cudaSetDevice(b->device));
+    ecris_status st = get_cells(b->runs[run], ne, delta_x, delta_y);
+    if (st != ECRIS_OK) return bfail(b, st, "batch_get_cells: " + b->runs[run]->err);
     return ECRIS_OK;
 }
 

@@ -126,6 +126,10 @@ def _load():
     lib.ecris_diag.restype = st
     lib.ecris_get_state.argtypes = [P, ctypes.POINTER(P), P, ctypes.c_int]
     lib.ecris_get_state.restype = st
+    lib.ecris_update_ne.argtypes = [P]
+    lib.ecris_update_ne.restype = st
+    lib.ecris_get_cells.argtypes = [P, P, P, P]
+    lib.ecris_get_cells.restype = st
     lib.ecris_set_profiling.argtypes = [P, ctypes.c_int]
     lib.ecris_set_profiling.restype = st
     lib.ecris_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
@@ -158,6 +162,10 @@ def _load():
     lib.ecris_batch_diag.restype = st
     lib.ecris_batch_get_state.argtypes = [P, ctypes.c_int32, ctypes.POINTER(P), P, ctypes.c_int]
     lib.ecris_batch_get_state.restype = st
+    lib.ecris_batch_update_ne.argtypes = [P, ctypes.c_int32]
+    lib.ecris_batch_update_ne.restype = st
+    lib.ecris_batch_get_cells.argtypes = [P, ctypes.c_int32, P, P, P]
+    lib.ecris_batch_get_cells.restype = st
     lib.ecris_batch_memory.argtypes = [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
     lib.ecris_batch_memory.restype = st
     lib.ecris_batch_autotune.argtypes = [P, ctypes.c_uint32, ctypes.POINTER(Tuning)]
@@ -195,6 +203,8 @@ ecris_load_ions = LIB.ecris_load_ions
 ecris_step = LIB.ecris_step
 ecris_diag = LIB.ecris_diag
 ecris_get_state = LIB.ecris_get_state
+ecris_update_ne = LIB.ecris_update_ne
+ecris_get_cells = LIB.ecris_get_cells
 ecris_set_profiling = LIB.ecris_set_profiling
 ecris_get_profile = LIB.ecris_get_profile
 ecris_coulomb_collide_noalloc = LIB.ecris_coulomb_collide_noalloc
@@ -208,6 +218,8 @@ ecris_batch_remove_run = LIB.ecris_batch_remove_run
 ecris_batch_step = LIB.ecris_batch_step
 ecris_batch_diag = LIB.ecris_batch_diag
 ecris_batch_get_state = LIB.ecris_batch_get_state
+ecris_batch_update_ne = LIB.ecris_batch_update_ne
+ecris_batch_get_cells = LIB.ecris_batch_get_cells
 ecris_batch_memory = LIB.ecris_batch_memory
 ecris_batch_autotune = LIB.ecris_batch_autotune
 ecris_batch_set_profiling = LIB.ecris_batch_set_profiling
@@ -355,6 +367,13 @@ class Batch:
         rp, n = self.runs[h]
         return _state(n, lambda p, m: self._check(ecris_batch_get_state(self.b, int(h), p, m, 0)))
 
+    def update_ne(self, h):
+        self._check(ecris_batch_update_ne(self.b, int(h)))
+
+    def cells(self, h):
+        rp, _ = self.runs[h]
+        return _cells(rp.ncells, lambda a, b, c: self._check(ecris_batch_get_cells(self.b, int(h), a, b, c)))
+
     def memory(self):
         u, b = ctypes.c_size_t(0), ctypes.c_size_t(0)
         self._check(ecris_batch_memory(self.b, ctypes.byref(u), ctypes.byref(b)))
@@ -439,6 +458,12 @@ class Server:
                 "ion_steps": ist.value}
 
 
+def _cells(nc, call):
+    out = {k: np.zeros(nc, dtype=np.float32) for k in ("ne", "delta_x", "delta_y")}
+    call(_ptr(out["ne"]), _ptr(out["delta_x"]), _ptr(out["delta_y"]))
+    return out
+
+
 class Run:
     """One ECRIS run on one GPU: fields, particles, steps and diagnostics."""
 
@@ -493,6 +518,15 @@ class Run:
 
     def state(self):
         return _state(self.n, lambda p, m: check(self.ctx, ecris_get_state(self.ctx, p, m, 0)))
+
+    def update_ne(self):
+        """n_e of every cell := the time-averaged ion charge density since the
+        load or the previous call; delta rebuilt from it."""
+        check(self.ctx, ecris_update_ne(self.ctx))
+
+    def cells(self):
+        """The per-cell electron data the kernels read: n_e (m^-3), delta_x, delta_y."""
+        return _cells(self.ncells, lambda a, b, c: check(self.ctx, ecris_get_cells(self.ctx, a, b, c)))
 
     def set_tuning(self, sort_every=32):
         t = Tuning()
