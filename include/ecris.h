@@ -213,6 +213,23 @@ ecris_status ecris_diag(ecris_ctx* ctx, ecris_diag_out* out);
  * ran since the load or the previous call; the run is unchanged then. */
 ecris_status ecris_update_ne(ecris_ctx* ctx);
 
+/* First-passage time distribution (Sec. III.D): for every ion extracted
+ * through the aperture, its age in steps since the particle was last
+ * ionised from Q = 0 (an ion loaded as an ion, whose birth is unknown, is not
+ * counted; a particle neutralised at a wall or by charge exchange starts a
+ * new age at its next ionisation).  Ages a >= 1 are binned by
+ *     e = floor(log2 a),  m = the two bits of a below its leading one
+ *     (a << (2 - e) & 3 for e < 2),  bin = 4 e + m,
+ * so bin 4e + m starts at a = 2^e (1 + m/4) for e >= 2.  Multiply by dt for
+ * seconds. */
+#define ECRIS_FPTD_BINS 120
+
+/* Copy the distribution out: hist[(qmax + 1) * ECRIS_FPTD_BINS] counts by
+ * (Q, bin), row Q = 0 empty; age_sum[qmax + 1] the summed ages (steps) by Q,
+ * for the mean.  Either pointer may be NULL.  Host memory; synchronises.
+ * Counts since the load. */
+ecris_status ecris_get_fptd(ecris_ctx* ctx, uint64_t* hist, uint64_t* age_sum);
+
 /* Copy the per-cell electron data the kernels read to host memory: n_e in
  * m^-3 and the two delta components, nx*ny*nz floats each in cell order
  * (ix fastest); any pointer may be NULL.  Synchronises. */
@@ -293,6 +310,7 @@ ecris_status ecris_batch_get_state(ecris_batch* b, int32_t run, float* const xyz
 /* ecris_update_ne / ecris_get_cells for one run of the batch (ordered after
  * its queued steps; synchronises the batch stream). */
 ecris_status ecris_batch_update_ne(ecris_batch* b, int32_t run);
+ecris_status ecris_batch_get_fptd(ecris_batch* b, int32_t run, uint64_t* hist, uint64_t* age_sum);
 ecris_status ecris_batch_get_cells(ecris_batch* b, int32_t run, float* ne, float* delta_x, float* delta_y);
 /* Bytes held by the batch's runs and its budget (0: none). */
 ecris_status ecris_batch_memory(const ecris_batch* b, size_t* used, size_t* budget);

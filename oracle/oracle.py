@@ -24,6 +24,15 @@ G_CELL, G_BOUNDARY, G_IONIZE, G_CX, G_CELLREC = 1, 2, 4, 8, 16
 # guards that can change a single-particle outcome (no Coulomb pairing)
 G_SINGLE = G_BOUNDARY | G_IONIZE | G_CX | G_CELLREC
 QMAX_SLOTS = 64
+FPTD_BINS = 120
+
+
+def fptd_bin(age: int) -> int:
+    """Log bin of a first-passage age in steps (>= 1): e = floor(log2 age),
+    m = the two bits below the leading one, bin = 4 e + m."""
+    e = int(age).bit_length() - 1
+    m = (age >> (e - 2)) & 3 if e >= 2 else (age << (2 - e)) & 3
+    return 4 * e + m
 
 
 def build(force: bool = False) -> str:
@@ -187,6 +196,12 @@ class OracleRun:
         self.step_index = 0
         self.ne_mark_charge = None if self.dep_charge is None else self.dep_charge.copy()
         self.ne_mark_step = 0
+        # first-passage times (Sec. III.D): step of each particle's last
+        # ionisation from Q = 0 (-1: unknown, e.g. loaded as an ion), and the
+        # ages of extracted ions by charge state
+        self.birth = np.full(self.n, -1, dtype=np.int64)
+        self.fptd_hist = np.zeros((qmax + 1, FPTD_BINS), dtype=np.int64)
+        self.fptd_sum = np.zeros(qmax + 1, dtype=np.int64)
 
     def set_state(self, s):
         for k in ("x", "y", "z", "vx", "vy", "vz"):
@@ -201,18 +216,33 @@ class OracleRun:
         acc_ev = np.zeros(self.n, dtype=np.uint8)
         acc_g = np.zeros(self.n, dtype=np.uint8)
         for _ in range(nsteps):
+            q_before = self.q.copy()
             lib().or_step(ctypes.byref(self.p), _ptr(self.rates), _ptr(self.ne), _ptr(self.zone),
                           _ptr(self.dlx), _ptr(self.dly), _ptr(self.E), self.n,
                           _ptr(self.x), _ptr(self.y), _ptr(self.z), _ptr(self.vx), _ptr(self.vy),
                           _ptr(self.vz), _ptr(self.q), _ptr(self.status), self.step_index,
                           _ptr(self.events), _ptr(self.guard), ctypes.byref(self.tally),
                           _ptr(self.dep_count), _ptr(self.dep_charge))
+            self._first_passage(q_before)
             self.step_index += 1
             acc_ev |= self.events
             acc_g |= self.guard
         if accumulate_guard:
             self.events_acc, self.guard_acc = acc_ev, acc_g
         return self
+
+    def _first_passage(self, q_before):
+        """After a step: an extracted ion (it leaves with its charge state from
+        before the step) adds its age since its birth; an atom ionised in this
+        step is born now."""
+        s = self.step_index
+        ext = ((self.events & EV_EXTRACT) != 0) & (q_before >= 1) & (self.birth >= 0)
+        for i in np.nonzero(ext)[0]:
+            age = s - int(self.birth[i])
+            self.fptd_hist[q_before[i], fptd_bin(age)] += 1
+            self.fptd_sum[q_before[i]] += age
+        born = (q_before == 0) & ((self.events & EV_IONIZE) != 0)
+        self.birth[born] = s
 
     def update_ne(self):
         """Self-consistent electron density (Sec. II, charge neutrality): n_e

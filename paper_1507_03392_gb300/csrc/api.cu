@@ -294,6 +294,8 @@ struct ecris_ctx {
     unsigned long long* d_census = nullptr;
     uint32_t* d_step = nullptr;
     uint32_t* d_leave = nullptr;    // leaver list (cap) and its count
+    uint32_t* d_birth = nullptr;    // ionisation step by particle id (cap)
+    unsigned long long* d_fptd = nullptr;   // first-passage histogram and age sums
     uint32_t* d_nleave = nullptr;
     unsigned int* d_ticket = nullptr;
     uint32_t ntiles = 0;
@@ -377,6 +379,8 @@ void free_ions(ecris_ctx* ctx)
     free_async(ctx, ctx->d_census);
     free_async(ctx, ctx->d_step);
     free_async(ctx, ctx->d_leave);
+    free_async(ctx, ctx->d_birth);
+    free_async(ctx, ctx->d_fptd);
     free_async(ctx, ctx->d_nleave);
     free_async(ctx, ctx->d_ticket);
     free_async(ctx, ctx->d_q8);
@@ -508,6 +512,8 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.step = ctx->d_step;
     R.err = ctx->d_err;
     R.leave = ctx->d_leave;
+    R.birth = ctx->d_birth;
+    R.fptd = ctx->d_fptd;
     R.nleave = ctx->d_nleave;
     R.n = (uint32_t)ctx->n;
     R.n4 = (uint32_t)ctx->n4;
@@ -623,6 +629,20 @@ ecris_status update_ne(ecris_ctx* ctx)
     h.charge_mark.swap(charge);
     h.steps_mark = ctx->steps_done;
     ctx->dt_loaded = -1.0;
+    return ECRIS_OK;
+}
+
+ecris_status get_fptd(ecris_ctx* ctx, uint64_t* hist, uint64_t* age_sum)
+{
+    std::vector<unsigned long long> f(kFptdWords);
+    CK(cudaMemcpyAsync(f.data(), ctx->d_fptd, kFptdWords * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int q = 0; q <= ctx->h.qmax; ++q) {
+        if (hist)
+            for (int b = 0; b < kFptdBins; ++b) hist[(size_t)q * kFptdBins + b] = f[(size_t)q * kFptdBins + b];
+        if (age_sum) age_sum[q] = f[(size_t)kQSlots * kFptdBins + q];
+    }
     return ECRIS_OK;
 }
 
@@ -938,6 +958,8 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         CK(cudaMallocAsync((void**)&ctx->d_census, kQSlots * sizeof(unsigned long long), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_step, sizeof(uint32_t), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_leave, cap * sizeof(uint32_t), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_birth, cap * sizeof(uint32_t), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_fptd, kFptdWords * sizeof(unsigned long long), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_nleave, sizeof(uint32_t), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_ticket, sizeof(unsigned int), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_bad, 2 * sizeof(unsigned int), ctx->stream));
@@ -978,6 +1000,8 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
     CK(cudaMemsetAsync(ctx->d_count, 0, nc * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_charge, 0, nc * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_tally, 0, kTallyWords * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_birth, 0xFF, ctx->cap * sizeof(uint32_t), ctx->stream));   // births unknown
+    CK(cudaMemsetAsync(ctx->d_fptd, 0, kFptdWords * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(uint32_t), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_nleave, 0, sizeof(uint32_t), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_ticket, 0, sizeof(unsigned int), ctx->stream));
@@ -1170,6 +1194,14 @@ ecris_status ecris_update_ne(ecris_ctx* ctx)
     if (ctx->failed) return fail(ctx, ECRIS_ESTATE, "update_ne: context failed earlier (%s)", ctx->err.c_str());
     CK(cudaSetDevice(ctx->device));
     return update_ne(ctx);
+}
+
+ecris_status ecris_get_fptd(ecris_ctx* ctx, uint64_t* hist, uint64_t* age_sum)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    if (!ctx->loaded) return fail(ctx, ECRIS_ESTATE, "get_fptd: call ecris_load_ions first");
+    CK(cudaSetDevice(ctx->device));
+    return get_fptd(ctx, hist, age_sum);
 }
 
 ecris_status ecris_get_cells(ecris_ctx* ctx, float* ne, float* delta_x, float* delta_y)
@@ -1481,8 +1513,8 @@ size_t ecris_run_bytes(size_t n, int32_t nx, int32_t ny, int32_t nz, int coulomb
 {
     const size_t cap = 4 * ((n + 3) / 4) + 4;
     const size_t nc = (size_t)(nx > 0 ? nx : 0) * (ny > 0 ? ny : 0) * (nz > 0 ? nz : 0);
-    // two particle sets with ids, the sort's records, load bytes, Coulomb lists
-    size_t per_p = 2 * 32 + 32 + 4 + 4 + 1;
+    // two particle sets with ids, the sort's records, leaver list, births, load bytes, Coulomb lists
+    size_t per_p = 2 * 32 + 32 + 4 + 4 + 4 + 1;
     if (coulomb) per_p += 16 + 16 + 8 + 16 + 4 + 4 + 1;
     // cell records, E, deposit, time sums, sort histogram and scan, Coulomb counts
     size_t per_c = 16 + 16 + 8 + 8 + 8 + 4 + 4 + (coulomb ? 12 : 0);
@@ -1734,6 +1766,16 @@ ecris_status ecris_batch_update_ne(ecris_batch* b, int32_t run)
     if (st != ECRIS_OK) return bfail(b, st, "batch_update_ne: " + c->err);
     b->params_dirty = true;
     if (c->h.mcc.flags & kFCoulomb) b->graph_dirty = true;
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_get_fptd(ecris_batch* b, int32_t run, uint64_t* hist, uint64_t* age_sum)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (!run_live(b, run)) return bfail(b, ECRIS_EINVAL, "batch_get_fptd: no such run");
+    BCK(cudaSetDevice(b->device));
+    ecris_status st = get_fptd(b->runs[run], hist, age_sum);
+    if (st != ECRIS_OK) return bfail(b, st, "batch_get_fptd: " + b->runs[run]->err);
     return ECRIS_OK;
 }
 

@@ -31,6 +31,9 @@ constexpr int kTallyLost = 64;
 constexpr int kTallyKe = 128;
 constexpr int kTallyCoulomb = 129;
 constexpr int kTallyWords = 132;
+// first-passage times: 4 bins per octave of the age in steps (ages < 2^30)
+constexpr int kFptdBins = ECRIS_FPTD_BINS;
+constexpr int kFptdWords = kQSlots * (kFptdBins + 1);
 
 // meta word layout (matches the public header)
 constexpr uint32_t kQMask = 0xFFu;
@@ -137,6 +140,8 @@ struct alignas(16) RunDev {
     uint32_t *leave;             // slots of the particles that left the chamber this step
     uint32_t *nleave;            // their number (zero between steps)
     uint32_t *err;               // device error word: 0, or ECRIS_ETIMEOUT after a bounded wait ran out
+    uint32_t *birth;             // by particle id: step of the last ionisation from Q = 0 (~0: unknown)
+    unsigned long long *fptd;    // [Q][kFptdBins] extraction counts by age bin, then [Q] summed ages (steps)
     uint32_t n;                  // particles
     uint32_t n4;                 // float4 groups = ceil(n/4)
     uint32_t ncells;

@@ -215,7 +215,11 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
     const int zone = cr.y > 0.5f ? 1 : 0;
     if (ionize && need) {
         const float lam = cr.x * __ldg(R.kdt + zone * kQSlots + Q);
-        if (fires(w.w0, event_prob(lam))) { Q += 1; ev |= kEvIonize; }
+        if (fires(w.w0, event_prob(lam))) {
+            if (Q == 0) R.birth[pid] = step;   // an ion is born (first-passage clock)
+            Q += 1;
+            ev |= kEvIonize;
+        }
     }
     if ((R.flags & kFCx) && R.n0s1 > 0.0f && Q >= 1 && Q != 2) {
         const float vrel = sqrtf(vx * vx + vy * vy + vz * vz + R.vth2);
@@ -269,6 +273,17 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
     return false;
 }
 
+// first-passage time of an extracted ion, age in steps (>= 1 for an ion born
+// in an earlier step): 4 log bins per octave, and the age summed by Q
+__device__ __forceinline__ void fptd_record(const RunDev& R, uint32_t Q, uint32_t age)
+{
+    if (age == 0u) return;
+    const int e = 31 - __clz(age);
+    const uint32_t m = e >= 2 ? (age >> (e - 2)) & 3u : (age << (2 - e)) & 3u;
+    atomicAdd(R.fptd + Q * kFptdBins + 4 * e + m, 1ull);
+    atomicAdd(R.fptd + kQSlots * kFptdBins + Q, (unsigned long long)age);
+}
+
 // Finish the step of a particle that left the chamber (the step kernel kept
 // its old position X, Y, Z and its pushed velocity): the first crossing of
 // the straight segment with the wall, the injection plane or the extraction
@@ -319,6 +334,8 @@ __device__ __forceinline__ uint32_t leave_particle(const RunDev& R, uint32_t pid
     if (kind == 4) {
         atomicAdd(R.tally + kTallyExtracted + Q, 1ull);
         ev = kEvExtract;
+        const uint32_t born = Q >= 1 ? R.birth[pid] : 0xFFFFFFFFu;
+        if (born <= step) fptd_record(R, Q, step - born);
     } else {
         atomicAdd(R.tally + kTallyLost + Q, 1ull);
         ev = kEvWall;

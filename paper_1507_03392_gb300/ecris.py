@@ -130,6 +130,8 @@ def _load():
     lib.ecris_update_ne.restype = st
     lib.ecris_get_cells.argtypes = [P, P, P, P]
     lib.ecris_get_cells.restype = st
+    lib.ecris_get_fptd.argtypes = [P, P, P]
+    lib.ecris_get_fptd.restype = st
     lib.ecris_set_profiling.argtypes = [P, ctypes.c_int]
     lib.ecris_set_profiling.restype = st
     lib.ecris_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
@@ -166,6 +168,8 @@ def _load():
     lib.ecris_batch_update_ne.restype = st
     lib.ecris_batch_get_cells.argtypes = [P, ctypes.c_int32, P, P, P]
     lib.ecris_batch_get_cells.restype = st
+    lib.ecris_batch_get_fptd.argtypes = [P, ctypes.c_int32, P, P]
+    lib.ecris_batch_get_fptd.restype = st
     lib.ecris_batch_memory.argtypes = [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
     lib.ecris_batch_memory.restype = st
     lib.ecris_batch_autotune.argtypes = [P, ctypes.c_uint32, ctypes.POINTER(Tuning)]
@@ -205,6 +209,7 @@ ecris_diag = LIB.ecris_diag
 ecris_get_state = LIB.ecris_get_state
 ecris_update_ne = LIB.ecris_update_ne
 ecris_get_cells = LIB.ecris_get_cells
+ecris_get_fptd = LIB.ecris_get_fptd
 ecris_set_profiling = LIB.ecris_set_profiling
 ecris_get_profile = LIB.ecris_get_profile
 ecris_coulomb_collide_noalloc = LIB.ecris_coulomb_collide_noalloc
@@ -220,6 +225,7 @@ ecris_batch_diag = LIB.ecris_batch_diag
 ecris_batch_get_state = LIB.ecris_batch_get_state
 ecris_batch_update_ne = LIB.ecris_batch_update_ne
 ecris_batch_get_cells = LIB.ecris_batch_get_cells
+ecris_batch_get_fptd = LIB.ecris_batch_get_fptd
 ecris_batch_memory = LIB.ecris_batch_memory
 ecris_batch_autotune = LIB.ecris_batch_autotune
 ecris_batch_set_profiling = LIB.ecris_batch_set_profiling
@@ -370,6 +376,10 @@ class Batch:
     def update_ne(self, h):
         self._check(ecris_batch_update_ne(self.b, int(h)))
 
+    def fptd(self, h):
+        rp, _ = self.runs[h]
+        return _fptd(rp.species.qmax, lambda a, b: self._check(ecris_batch_get_fptd(self.b, int(h), a, b)))
+
     def cells(self, h):
         rp, _ = self.runs[h]
         return _cells(rp.ncells, lambda a, b, c: self._check(ecris_batch_get_cells(self.b, int(h), a, b, c)))
@@ -458,6 +468,16 @@ class Server:
                 "ion_steps": ist.value}
 
 
+FPTD_BINS = 120   # ECRIS_FPTD_BINS
+
+
+def _fptd(qmax, call):
+    hist = np.zeros((qmax + 1, FPTD_BINS), dtype=np.uint64)
+    age_sum = np.zeros(qmax + 1, dtype=np.uint64)
+    call(_ptr(hist), _ptr(age_sum))
+    return {"hist": hist, "age_sum": age_sum}
+
+
 def _cells(nc, call):
     out = {k: np.zeros(nc, dtype=np.float32) for k in ("ne", "delta_x", "delta_y")}
     call(_ptr(out["ne"]), _ptr(out["delta_x"]), _ptr(out["delta_y"]))
@@ -523,6 +543,12 @@ class Run:
         """n_e of every cell := the time-averaged ion charge density since the
         load or the previous call; delta rebuilt from it."""
         check(self.ctx, ecris_update_ne(self.ctx))
+
+    def fptd(self):
+        """First-passage times of the extracted ions since the load: hist
+        [Q, bin] (bins of ECRIS_FPTD_BINS, 4 per octave of the age in steps)
+        and age_sum [Q] (steps)."""
+        return _fptd(self.qmax, lambda a, b: check(self.ctx, ecris_get_fptd(self.ctx, a, b)))
 
     def cells(self):
         """The per-cell electron data the kernels read: n_e (m^-3), delta_x, delta_y."""
