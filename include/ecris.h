@@ -230,6 +230,48 @@ ecris_status ecris_update_ne(ecris_ctx* ctx);
  * Counts since the load. */
 ecris_status ecris_get_fptd(ecris_ctx* ctx, uint64_t* hist, uint64_t* age_sum);
 
+/* Summed radius sqrt(x^2 + y^2) of the extracted ions at the aperture
+ * plane, by charge state, in metres (accumulated in whole nanometres since
+ * the load); the mean radial displacement of Sec. III.A is
+ * r_sum[Q] / extracted[Q].  r_sum holds qmax + 1 values.  Synchronises. */
+ecris_status ecris_get_extraction_radius(ecris_ctx* ctx, double* r_sum);
+
+/* Moment probes and screens (diagnostics of Sec. III.A, Figs. 9-16).  Each
+ * ecris_probe_sample call adds the particles as they are now:
+ *  - for every probed cell c and charge state Q (atoms Q = 0 included): the
+ *    number of particles and the sums of vx, vy, vz, vx^2, vy^2, vz^2, in
+ *    FP64; the density of Q in c is w count / (samples V_cell) and its
+ *    temperature M (<v^2> - <v>^2) / 3 in energy units (the ion pressure of
+ *    a cell is the sum over Q of n_Q T_Q, its mean temperature that pressure
+ *    over the summed density);
+ *  - for every screen s, a slab z_lo[s] <= z < z_hi[s]: a hit on the pixel
+ *    under each particle in the slab, by Q, on a pixels x pixels grid over
+ *    the square [-R0, R0)^2 (pixel (px, py) covers x from -R0 + 2 R0 px /
+ *    pixels, row-major with px fastest).
+ * Sampled every step, the screens are the paper's exposure images (a pixel
+ * counts a particle each time step it is there); sampled every k steps they
+ * estimate the same picture at 1/k of the counts. */
+#define ECRIS_MAX_SCREENS 4
+typedef struct {
+    size_t ncells;            /* probed cells, each at most once */
+    const uint32_t* cells;    /* their indices (ix fastest), host memory */
+    int32_t nscreens;         /* 0 .. ECRIS_MAX_SCREENS */
+    double z_lo[ECRIS_MAX_SCREENS], z_hi[ECRIS_MAX_SCREENS];   /* slabs (m), 0 <= z_lo < z_hi <= L */
+    int32_t pixels;           /* power of two, 2 .. 4096 (ignored without screens) */
+} ecris_probe_spec;
+
+/* Install the probes (replacing earlier ones) and zero their sums; a load
+ * zeroes them as well.  Needs ecris_init_fields.  ECRIS_EINVAL for a cell
+ * index out of range, a repeated cell, a bad slab or pixel count. */
+ecris_status ecris_set_probes(ecris_ctx* ctx, const ecris_probe_spec* spec);
+/* Add the current particles (asynchronous on the context's stream). */
+ecris_status ecris_probe_sample(ecris_ctx* ctx);
+/* Copy the sums out (synchronises); any pointer may be NULL:
+ *   samples     number of ecris_probe_sample calls since the sums were zeroed;
+ *   moments     [ncells][qmax + 1][7]: count, sum vx, vy, vz, sum vx^2, vy^2, vz^2;
+ *   screens     [nscreens][qmax + 1][pixels * pixels] hit counts. */
+ecris_status ecris_get_probes(ecris_ctx* ctx, uint64_t* samples, double* moments, uint64_t* screens);
+
 /* Copy the per-cell electron data the kernels read to host memory: n_e in
  * m^-3 and the two delta components, nx*ny*nz floats each in cell order
  * (ix fastest); any pointer may be NULL.  Synchronises. */
@@ -311,6 +353,11 @@ ecris_status ecris_batch_get_state(ecris_batch* b, int32_t run, float* const xyz
  * its queued steps; synchronises the batch stream). */
 ecris_status ecris_batch_update_ne(ecris_batch* b, int32_t run);
 ecris_status ecris_batch_get_fptd(ecris_batch* b, int32_t run, uint64_t* hist, uint64_t* age_sum);
+ecris_status ecris_batch_get_extraction_radius(ecris_batch* b, int32_t run, double* r_sum);
+ecris_status ecris_batch_set_probes(ecris_batch* b, int32_t run, const ecris_probe_spec* spec);
+ecris_status ecris_batch_probe_sample(ecris_batch* b, int32_t run);
+ecris_status ecris_batch_get_probes(ecris_batch* b, int32_t run, uint64_t* samples, double* moments,
+                                    uint64_t* screens);
 ecris_status ecris_batch_get_cells(ecris_batch* b, int32_t run, float* ne, float* delta_x, float* delta_y);
 /* Bytes held by the batch's runs and its budget (0: none). */
 ecris_status ecris_batch_memory(const ecris_batch* b, size_t* used, size_t* budget);

@@ -87,6 +87,7 @@ typedef struct {
     int64_t lost[OR_QMAX];
     double ke_lost_eV;   /* kinetic energy of ions (Q>=1) leaving the chamber */
     int64_t coulomb_pairs;
+    double r_ext_sum[OR_QMAX];   /* radius at the aperture plane summed over extracted particles (m) */
 } or_tally;
 
 /* ------------------------------------------------------------------------ */
@@ -739,6 +740,7 @@ void or_step(const or_params *p, const double *rates, const double *ne, const in
             double nrm[3], e1[3], e2[3];
             if (leave[i] == OR_LEAVE_APERTURE) {
                 t->extracted[Q] += 1;
+                t->r_ext_sum[Q] += sqrt(cx * cx + cy * cy);
                 events[i] |= OR_EV_EXTRACT;
                 cx = p->inlet[0]; cy = p->inlet[1]; cz = p->inlet[2];
                 nrm[0] = 0; nrm[1] = 0; nrm[2] = 1; e1[0] = 1; e1[1] = 0; e1[2] = 0; e2[0] = 0; e2[1] = 1; e2[2] = 0;

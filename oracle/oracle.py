@@ -67,6 +67,7 @@ class Tally(ctypes.Structure):
         ("lost", ctypes.c_int64 * QMAX_SLOTS),
         ("ke_lost_eV", ctypes.c_double),
         ("coulomb_pairs", ctypes.c_int64),
+        ("r_ext_sum", ctypes.c_double * QMAX_SLOTS),
     ]
 
 
@@ -161,6 +162,77 @@ def boris(qm, E, B, dt, v):
     lib().or_boris(float(qm), _ptr(np.asarray(E, np.float64)), _ptr(np.asarray(B, np.float64)),
                    float(dt), _ptr(v))
     return v
+
+
+def ngp_cells(rp, x, y, z):
+    """Nearest-grid-point cell of each position (ix fastest), by the floor of
+    the coordinate over the mesh step; positions on the upper faces clamp."""
+    dx, dy, dz = 2 * rp.R0 / rp.nx, 2 * rp.R0 / rp.ny, rp.L / rp.nz
+    ix = np.clip(np.floor((np.asarray(x, np.float64) + rp.R0) / dx).astype(np.int64), 0, rp.nx - 1)
+    iy = np.clip(np.floor((np.asarray(y, np.float64) + rp.R0) / dy).astype(np.int64), 0, rp.ny - 1)
+    iz = np.clip(np.floor(np.asarray(z, np.float64) / dz).astype(np.int64), 0, rp.nz - 1)
+    return (iz * rp.ny + iy) * rp.nx + ix
+
+
+def probe_moments(rp, state, cells, alive=None):
+    """Moments of the particles in each listed cell by charge state (Sec.
+    III.A profiles): [len(cells), qmax + 1, 7] holding the count and the sums
+    of vx, vy, vz, vx^2, vy^2, vz^2."""
+    qs = rp.species.qmax + 1
+    cells = np.asarray(cells, dtype=np.int64)
+    out = np.zeros((len(cells), qs, 7))
+    slot = np.full(rp.ncells, -1, dtype=np.int64)
+    slot[cells] = np.arange(len(cells))
+    s = slot[ngp_cells(rp, state["x"], state["y"], state["z"])]
+    sel = s >= 0 if alive is None else (s >= 0) & alive
+    q = np.asarray(state["q"], dtype=np.int64)
+    v = [np.asarray(state[k], dtype=np.float64) for k in ("vx", "vy", "vz")]
+    for i in np.nonzero(sel)[0]:
+        row = out[s[i], q[i]]
+        row[0] += 1.0
+        for c in range(3):
+            row[1 + c] += v[c][i]
+            row[4 + c] += v[c][i] * v[c][i]
+    return out
+
+
+def moment_profiles(rp, moments, samples, weight=None):
+    """Densities, temperatures and the ion pressure from summed moments
+    (Sec. III.A): n_Q = w count / (samples V_cell) (m^-3), T_Q = M (<v^2> -
+    <v>^2) / 3 in eV, P = sum over Q >= 1 of n_Q T_Q (eV m^-3) and the mean
+    ion temperature P / sum over Q >= 1 of n_Q (eV).  Empty slots get T = 0."""
+    w = rp.weight if weight is None else weight
+    vol = (2.0 * rp.R0 / rp.nx) * (2.0 * rp.R0 / rp.ny) * (rp.L / rp.nz)
+    cnt = moments[..., 0]
+    n = w * cnt / (samples * vol)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mean_v2 = (moments[..., 4] + moments[..., 5] + moments[..., 6]) / cnt
+        mean_v = moments[..., 1:4] / cnt[..., None]
+        var = mean_v2 - (mean_v ** 2).sum(axis=-1)
+        T = np.where(cnt > 0, rp.species.mass_amu * 1.66053906660e-27 * var / 3.0 / 1.602176634e-19, 0.0)
+        P = (n[..., 1:] * T[..., 1:]).sum(axis=-1)
+        ni = n[..., 1:].sum(axis=-1)
+        Tm = np.where(ni > 0, P / ni, 0.0)
+    return {"n": n, "T_eV": T, "P_eV_m3": P, "T_mean_eV": Tm}
+
+
+def screen_hits(rp, state, slabs, pixels, alive=None):
+    """Screen images (Sec. III.A, Figs. 9-11, 16): for each slab z_lo <= z <
+    z_hi, one hit per particle in it on the pixel under it, by charge state,
+    pixels x pixels over [-R0, R0)^2: [len(slabs), qmax + 1, py, px]."""
+    qs = rp.species.qmax + 1
+    out = np.zeros((len(slabs), qs, pixels, pixels), dtype=np.int64)
+    x, y, z = (np.asarray(state[k], dtype=np.float64) for k in ("x", "y", "z"))
+    q = np.asarray(state["q"], dtype=np.int64)
+    px = np.floor((x + rp.R0) / (2 * rp.R0) * pixels).astype(np.int64)
+    py = np.floor((y + rp.R0) / (2 * rp.R0) * pixels).astype(np.int64)
+    for k, (lo, hi) in enumerate(slabs):
+        sel = (z >= lo) & (z < hi)
+        if alive is not None:
+            sel &= alive
+        for i in np.nonzero(sel)[0]:
+            out[k, q[i], py[i], px[i]] += 1
+    return out
 
 
 class OracleRun:

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libecris.so")
-SOURCES = ["api.cu", "step_kernel.cu", "coulomb.cu", "coulomb_noalloc.cu", "sort.cu", "server.cu"]
+SOURCES = ["api.cu", "step_kernel.cu", "coulomb.cu", "coulomb_noalloc.cu", "sort.cu", "server.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--cudart", "shared"]
 # The step kernels for one run and for a batch inline the same per-particle

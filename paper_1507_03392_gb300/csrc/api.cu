@@ -295,6 +295,15 @@ struct ecris_ctx {
     uint32_t* d_step = nullptr;
     uint32_t* d_leave = nullptr;    // leaver list (cap) and its count
     uint32_t* d_birth = nullptr;    // ionisation step by particle id (cap)
+    // moment probes and screens
+    int32_t* d_pslot = nullptr;     // per cell: probe slot or -1
+    double* d_pmom = nullptr;       // [slot][qmax + 1][7]
+    unsigned long long* d_pscreen = nullptr;   // [screen][qmax + 1][pixels^2]
+    size_t probe_cells = 0;
+    size_t screen_words = 0;
+    ProbeDev probe{};
+    bool have_probes = false;
+    uint64_t probe_samples = 0;
     unsigned long long* d_fptd = nullptr;   // first-passage histogram and age sums
     uint32_t* d_nleave = nullptr;
     unsigned int* d_ticket = nullptr;
@@ -406,7 +415,24 @@ void free_fields(ecris_ctx* ctx)
     free_async(ctx, ctx->d_E);
     free_async(ctx, ctx->d_kdt);
     free_async(ctx, ctx->d_nanbu);
+    free_async(ctx, ctx->d_pslot);
+    free_async(ctx, ctx->d_pmom);
+    free_async(ctx, ctx->d_pscreen);
+    ctx->have_probes = false;
     ctx->have_fields = false;
+}
+
+// zero the probes' sums (after installing them, and at every load)
+ecris_status zero_probes(ecris_ctx* ctx)
+{
+    if (!ctx->have_probes) return ECRIS_OK;
+    const size_t qs = (size_t)ctx->h.qmax + 1;
+    if (ctx->probe_cells)
+        CK(cudaMemsetAsync(ctx->d_pmom, 0, ctx->probe_cells * qs * 7 * sizeof(double), ctx->stream));
+    if (ctx->screen_words)
+        CK(cudaMemsetAsync(ctx->d_pscreen, 0, ctx->screen_words * sizeof(unsigned long long), ctx->stream));
+    ctx->probe_samples = 0;
+    return ECRIS_OK;
 }
 
 // FP32 kernel constants of the run for time step dt (built in FP64)
@@ -641,8 +667,107 @@ ecris_status get_fptd(ecris_ctx* ctx, uint64_t* hist, uint64_t* age_sum)
     for (int q = 0; q <= ctx->h.qmax; ++q) {
         if (hist)
             for (int b = 0; b < kFptdBins; ++b) hist[(size_t)q * kFptdBins + b] = f[(size_t)q * kFptdBins + b];
-        if (age_sum) age_sum[q] = f[(size_t)kQSlots * kFptdBins + q];
+        if (age_sum) age_sum[q] = f[(size_t)kFptdAgeSum + q];
     }
+    return ECRIS_OK;
+}
+
+ecris_status get_extraction_radius(ecris_ctx* ctx, double* r_sum)
+{
+    std::vector<unsigned long long> f(kQSlots);
+    CK(cudaMemcpyAsync(f.data(), ctx->d_fptd + kFptdRadius, kQSlots * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int q = 0; q <= ctx->h.qmax; ++q) r_sum[q] = (double)f[q] * 1e-9;
+    return ECRIS_OK;
+}
+
+ecris_status set_probes(ecris_ctx* ctx, const ecris_probe_spec* sp)
+{
+    const HostRun& h = ctx->h;
+    const size_t nc = (size_t)h.nx * h.ny * h.nz;
+    if (sp->ncells > nc || (sp->ncells && !sp->cells))
+        return fail(ctx, ECRIS_EINVAL, "set_probes: need ncells <= Nc and a cell list");
+    if (sp->nscreens < 0 || sp->nscreens > kMaxScreens)
+        return fail(ctx, ECRIS_EINVAL, "set_probes: 0 <= nscreens <= %d", kMaxScreens);
+    std::vector<int32_t> slot(nc, -1);
+    for (size_t k = 0; k < sp->ncells; ++k) {
+        const uint32_t c = sp->cells[k];
+        if (c >= nc) return fail(ctx, ECRIS_EINVAL, "set_probes: cell %u out of range", c);
+        if (slot[c] >= 0) return fail(ctx, ECRIS_EINVAL, "set_probes: cell %u listed twice", c);
+        slot[c] = (int32_t)k;
+    }
+    ProbeDev P{};
+    P.qs = h.qmax + 1;
+    P.nscreens = sp->nscreens;
+    if (sp->nscreens) {
+        int lg = 0;
+        while ((1 << lg) < sp->pixels && lg < 13) ++lg;
+        if (sp->pixels < 2 || sp->pixels > 4096 || (1 << lg) != sp->pixels)
+            return fail(ctx, ECRIS_EINVAL, "set_probes: pixels must be a power of two in [2, 4096]");
+        P.pix_log2 = lg;
+        // z = U L / 2^32 for U = Z + 2^31: the slab z_lo <= z < z_hi is
+        // ceil(z_lo 2^32 / L) <= U <= ceil(z_hi 2^32 / L) - 1
+        const double per = 4294967296.0 / h.geo.L;
+        for (int k = 0; k < sp->nscreens; ++k) {
+            const double lo = sp->z_lo[k], hi = sp->z_hi[k];
+            if (!std::isfinite(lo) || !std::isfinite(hi) || !(lo >= 0.0) || !(hi > lo) || hi > h.geo.L)
+                return fail(ctx, ECRIS_EINVAL, "set_probes: screen %d needs 0 <= z_lo < z_hi <= L", k);
+            const double ulo = std::ceil(lo * per), uhi = std::ceil(hi * per) - 1.0;
+            P.ulo[k] = (uint32_t)std::min(ulo, 4294967295.0);
+            P.uhi[k] = (uint32_t)std::max(0.0, std::min(uhi, 4294967295.0));
+        }
+    }
+    const size_t words = (size_t)sp->nscreens * P.qs << (2 * P.pix_log2);
+    if (words * sizeof(unsigned long long) > ((size_t)16 << 30))
+        return fail(ctx, ECRIS_EINVAL, "set_probes: screens above 16 GB");
+    CK(cudaSetDevice(ctx->device));
+    free_async(ctx, ctx->d_pslot);
+    free_async(ctx, ctx->d_pmom);
+    free_async(ctx, ctx->d_pscreen);
+    ctx->have_probes = false;
+    if (sp->ncells) {
+        CK(cudaMallocAsync((void**)&ctx->d_pslot, nc * sizeof(int32_t), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_pmom, sp->ncells * P.qs * 7 * sizeof(double), ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d_pslot, slot.data(), nc * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    if (words) CK(cudaMallocAsync((void**)&ctx->d_pscreen, words * sizeof(unsigned long long), ctx->stream));
+    P.slot = ctx->d_pslot;
+    P.mom = ctx->d_pmom;
+    P.screen = ctx->d_pscreen;
+    ctx->probe = P;
+    ctx->probe_cells = sp->ncells;
+    ctx->screen_words = words;
+    ctx->have_probes = true;
+    ecris_status st = zero_probes(ctx);
+    CK(cudaStreamSynchronize(ctx->stream));   // the slot map's host copy dies at return
+    return st;
+}
+
+ecris_status probe_sample(ecris_ctx* ctx)
+{
+    if (!ctx->have_probes) return fail(ctx, ECRIS_ESTATE, "probe_sample: call ecris_set_probes first");
+    if (ctx->dt_loaded < 0.0) {
+        ecris_status st = upload_dt(ctx, 1e-9);   // parameter block for the probe kernel
+        if (st != ECRIS_OK) return st;
+    }
+    CK(launch_probe(*ctx->h_run, ctx->probe, (uint32_t)ctx->n4, ctx->sm_count, ctx->stream));
+    ++ctx->probe_samples;
+    return ECRIS_OK;
+}
+
+ecris_status get_probes(ecris_ctx* ctx, uint64_t* samples, double* moments, uint64_t* screens)
+{
+    if (!ctx->have_probes) return fail(ctx, ECRIS_ESTATE, "get_probes: call ecris_set_probes first");
+    const size_t qs = (size_t)ctx->h.qmax + 1;
+    if (moments && ctx->probe_cells)
+        CK(cudaMemcpyAsync(moments, ctx->d_pmom, ctx->probe_cells * qs * 7 * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    if (screens && ctx->screen_words)
+        CK(cudaMemcpyAsync(screens, ctx->d_pscreen, ctx->screen_words * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (samples) *samples = ctx->probe_samples;
     return ECRIS_OK;
 }
 
@@ -1002,6 +1127,10 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
     CK(cudaMemsetAsync(ctx->d_tally, 0, kTallyWords * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_birth, 0xFF, ctx->cap * sizeof(uint32_t), ctx->stream));   // births unknown
     CK(cudaMemsetAsync(ctx->d_fptd, 0, kFptdWords * sizeof(unsigned long long), ctx->stream));
+    {
+        const ecris_status pst = zero_probes(ctx);
+        if (pst != ECRIS_OK) return pst;
+    }
     CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(uint32_t), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_nleave, 0, sizeof(uint32_t), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_ticket, 0, sizeof(unsigned int), ctx->stream));
@@ -1202,6 +1331,39 @@ ecris_status ecris_get_fptd(ecris_ctx* ctx, uint64_t* hist, uint64_t* age_sum)
     if (!ctx->loaded) return fail(ctx, ECRIS_ESTATE, "get_fptd: call ecris_load_ions first");
     CK(cudaSetDevice(ctx->device));
     return get_fptd(ctx, hist, age_sum);
+}
+
+ecris_status ecris_get_extraction_radius(ecris_ctx* ctx, double* r_sum)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    if (!r_sum) return fail(ctx, ECRIS_EINVAL, "get_extraction_radius: r_sum is NULL");
+    if (!ctx->loaded) return fail(ctx, ECRIS_ESTATE, "get_extraction_radius: call ecris_load_ions first");
+    CK(cudaSetDevice(ctx->device));
+    return get_extraction_radius(ctx, r_sum);
+}
+
+ecris_status ecris_set_probes(ecris_ctx* ctx, const ecris_probe_spec* spec)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    if (!spec) return fail(ctx, ECRIS_EINVAL, "set_probes: spec is NULL");
+    if (!ctx->have_fields) return fail(ctx, ECRIS_ESTATE, "set_probes: call ecris_init_fields first");
+    return set_probes(ctx, spec);
+}
+
+ecris_status ecris_probe_sample(ecris_ctx* ctx)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    if (!ctx->loaded) return fail(ctx, ECRIS_ESTATE, "probe_sample: call ecris_load_ions first");
+    if (ctx->failed) return fail(ctx, ECRIS_ESTATE, "probe_sample: context failed earlier (%s)", ctx->err.c_str());
+    CK(cudaSetDevice(ctx->device));
+    return probe_sample(ctx);
+}
+
+ecris_status ecris_get_probes(ecris_ctx* ctx, uint64_t* samples, double* moments, uint64_t* screens)
+{
+    if (!ctx) return ECRIS_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    return get_probes(ctx, samples, moments, screens);
 }
 
 ecris_status ecris_get_cells(ecris_ctx* ctx, float* ne, float* delta_x, float* delta_y)
@@ -1776,6 +1938,47 @@ ecris_status ecris_batch_get_fptd(ecris_batch* b, int32_t run, uint64_t* hist, u
     BCK(cudaSetDevice(b->device));
     ecris_status st = get_fptd(b->runs[run], hist, age_sum);
     if (st != ECRIS_OK) return bfail(b, st, "batch_get_fptd: " + b->runs[run]->err);
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_get_extraction_radius(ecris_batch* b, int32_t run, double* r_sum)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (!run_live(b, run) || !r_sum) return bfail(b, ECRIS_EINVAL, "batch_get_extraction_radius: no such run");
+    BCK(cudaSetDevice(b->device));
+    ecris_status st = get_extraction_radius(b->runs[run], r_sum);
+    if (st != ECRIS_OK) return bfail(b, st, "batch_get_extraction_radius: " + b->runs[run]->err);
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_set_probes(ecris_batch* b, int32_t run, const ecris_probe_spec* spec)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (!run_live(b, run) || !spec) return bfail(b, ECRIS_EINVAL, "batch_set_probes: no such run or no spec");
+    BCK(cudaSetDevice(b->device));
+    ecris_status st = set_probes(b->runs[run], spec);
+    if (st != ECRIS_OK) return bfail(b, st, "batch_set_probes: " + b->runs[run]->err);
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_probe_sample(ecris_batch* b, int32_t run)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (!run_live(b, run)) return bfail(b, ECRIS_EINVAL, "batch_probe_sample: no such run");
+    BCK(cudaSetDevice(b->device));
+    ecris_status st = probe_sample(b->runs[run]);
+    if (st != ECRIS_OK) return bfail(b, st, "batch_probe_sample: " + b->runs[run]->err);
+    return ECRIS_OK;
+}
+
+ecris_status ecris_batch_get_probes(ecris_batch* b, int32_t run, uint64_t* samples, double* moments,
+                                    uint64_t* screens)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (!run_live(b, run)) return bfail(b, ECRIS_EINVAL, "batch_get_probes: no such run");
+    BCK(cudaSetDevice(b->device));
+    ecris_status st = get_probes(b->runs[run], samples, moments, screens);
+    if (st != ECRIS_OK) return bfail(b, st, "batch_get_probes: " + b->runs[run]->err);
     return ECRIS_OK;
 }
 

@@ -33,7 +33,10 @@ constexpr int kTallyCoulomb = 129;
 constexpr int kTallyWords = 132;
 // first-passage times: 4 bins per octave of the age in steps (ages < 2^30)
 constexpr int kFptdBins = ECRIS_FPTD_BINS;
-constexpr int kFptdWords = kQSlots * (kFptdBins + 1);
+// [Q][bin] counts, [Q] age sums, [Q] extraction radius sums (nm)
+constexpr int kFptdWords = kQSlots * (kFptdBins + 2);
+constexpr int kFptdAgeSum = kQSlots * kFptdBins;
+constexpr int kFptdRadius = kQSlots * (kFptdBins + 1);
 
 // meta word layout (matches the public header)
 constexpr uint32_t kQMask = 0xFFu;
@@ -141,7 +144,8 @@ struct alignas(16) RunDev {
     uint32_t *nleave;            // their number (zero between steps)
     uint32_t *err;               // device error word: 0, or ECRIS_ETIMEOUT after a bounded wait ran out
     uint32_t *birth;             // by particle id: step of the last ionisation from Q = 0 (~0: unknown)
-    unsigned long long *fptd;    // [Q][kFptdBins] extraction counts by age bin, then [Q] summed ages (steps)
+    unsigned long long *fptd;    // [Q][kFptdBins] extraction counts by age bin, [Q] summed ages (steps),
+                                 // [Q] summed extraction radii (nm)
     uint32_t n;                  // particles
     uint32_t n4;                 // float4 groups = ceil(n/4)
     uint32_t ncells;
@@ -270,6 +274,19 @@ __device__ __forceinline__ uint32_t ngp_cell(const RunDev& R, int32_t X, int32_t
     return (iz * (uint32_t)R.ny + iy) * (uint32_t)R.nx + ix;
 }
 
+// moment probes and screens (probe.cu)
+constexpr int kMaxScreens = ECRIS_MAX_SCREENS;
+struct ProbeDev {
+    const int32_t* slot;          // per cell: its probe slot, or -1 (nullptr: no probed cells)
+    double* mom;                  // [slot][qs][7]: count, sums of v and of v^2 per component
+    unsigned long long* screen;   // [screen][qs][pixels^2] hit counts
+    uint32_t ulo[kMaxScreens];    // slab of each screen in U = Z + 2^31: ulo <= U <= uhi
+    uint32_t uhi[kMaxScreens];
+    int32_t nscreens;
+    int32_t pix_log2;             // pixels = 2^pix_log2
+    int32_t qs;                   // qmax + 1
+};
+
 // ----------------------------------------------------------------------------
 // Launch wrappers (defined in step_kernel.cu / coulomb.cu)
 // ----------------------------------------------------------------------------
@@ -317,6 +334,8 @@ int sort_scan_blocks(uint32_t nbins);
 cudaError_t launch_export_ordered(const RunDev& R, uint32_t n, uint32_t cap, float* const out[6], uint32_t* meta_out,
                                   double sxy, double sz, cudaStream_t s);
 cudaError_t launch_census(const RunDev& R, uint32_t n4, unsigned long long* census, cudaStream_t s);
+// add the current particles to the probes' sums (probe.cu)
+cudaError_t launch_probe(const RunDev& R, const ProbeDev& P, uint32_t n4, int sm_count, cudaStream_t s);
 
 // resident blocks per SM of the step kernel
 int step_blocks_per_sm();

@@ -281,7 +281,7 @@ __device__ __forceinline__ void fptd_record(const RunDev& R, uint32_t Q, uint32_
     const int e = 31 - __clz(age);
     const uint32_t m = e >= 2 ? (age >> (e - 2)) & 3u : (age << (2 - e)) & 3u;
     atomicAdd(R.fptd + Q * kFptdBins + 4 * e + m, 1ull);
-    atomicAdd(R.fptd + kQSlots * kFptdBins + Q, (unsigned long long)age);
+    atomicAdd(R.fptd + kFptdAgeSum + Q, (unsigned long long)age);
 }
 
 // Finish the step of a particle that left the chamber (the step kernel kept
@@ -336,6 +336,8 @@ __device__ __forceinline__ uint32_t leave_particle(const RunDev& R, uint32_t pid
         ev = kEvExtract;
         const uint32_t born = Q >= 1 ? R.birth[pid] : 0xFFFFFFFFu;
         if (born <= step) fptd_record(R, Q, step - born);
+        // radius at the aperture plane (mean radial displacement by Q), in nm
+        atomicAdd(R.fptd + kFptdRadius + Q, (unsigned long long)rint(sqrt(cxd * cxd + cyd * cyd) * 1e9));
     } else {
         atomicAdd(R.tally + kTallyLost + Q, 1ull);
         ev = kEvWall;

@@ -95,6 +95,15 @@ class Result(ctypes.Structure):
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 
+MAX_SCREENS = 4   # ECRIS_MAX_SCREENS
+
+
+class ProbeSpec(ctypes.Structure):
+    _fields_ = [("ncells", ctypes.c_size_t), ("cells", ctypes.c_void_p), ("nscreens", ctypes.c_int32),
+                ("z_lo", ctypes.c_double * MAX_SCREENS), ("z_hi", ctypes.c_double * MAX_SCREENS),
+                ("pixels", ctypes.c_int32)]
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("step_launches", ctypes.c_int64), ("step_ms", ctypes.c_double),
                 ("coulomb_launches", ctypes.c_int64), ("coulomb_ms", ctypes.c_double),
@@ -132,6 +141,14 @@ def _load():
     lib.ecris_get_cells.restype = st
     lib.ecris_get_fptd.argtypes = [P, P, P]
     lib.ecris_get_fptd.restype = st
+    lib.ecris_get_extraction_radius.argtypes = [P, P]
+    lib.ecris_get_extraction_radius.restype = st
+    lib.ecris_set_probes.argtypes = [P, ctypes.POINTER(ProbeSpec)]
+    lib.ecris_set_probes.restype = st
+    lib.ecris_probe_sample.argtypes = [P]
+    lib.ecris_probe_sample.restype = st
+    lib.ecris_get_probes.argtypes = [P, P, P, P]
+    lib.ecris_get_probes.restype = st
     lib.ecris_set_profiling.argtypes = [P, ctypes.c_int]
     lib.ecris_set_profiling.restype = st
     lib.ecris_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
@@ -170,6 +187,14 @@ def _load():
     lib.ecris_batch_get_cells.restype = st
     lib.ecris_batch_get_fptd.argtypes = [P, ctypes.c_int32, P, P]
     lib.ecris_batch_get_fptd.restype = st
+    lib.ecris_batch_get_extraction_radius.argtypes = [P, ctypes.c_int32, P]
+    lib.ecris_batch_get_extraction_radius.restype = st
+    lib.ecris_batch_set_probes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ProbeSpec)]
+    lib.ecris_batch_set_probes.restype = st
+    lib.ecris_batch_probe_sample.argtypes = [P, ctypes.c_int32]
+    lib.ecris_batch_probe_sample.restype = st
+    lib.ecris_batch_get_probes.argtypes = [P, ctypes.c_int32, P, P, P]
+    lib.ecris_batch_get_probes.restype = st
     lib.ecris_batch_memory.argtypes = [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
     lib.ecris_batch_memory.restype = st
     lib.ecris_batch_autotune.argtypes = [P, ctypes.c_uint32, ctypes.POINTER(Tuning)]
@@ -210,6 +235,10 @@ ecris_get_state = LIB.ecris_get_state
 ecris_update_ne = LIB.ecris_update_ne
 ecris_get_cells = LIB.ecris_get_cells
 ecris_get_fptd = LIB.ecris_get_fptd
+ecris_get_extraction_radius = LIB.ecris_get_extraction_radius
+ecris_set_probes = LIB.ecris_set_probes
+ecris_probe_sample = LIB.ecris_probe_sample
+ecris_get_probes = LIB.ecris_get_probes
 ecris_set_profiling = LIB.ecris_set_profiling
 ecris_get_profile = LIB.ecris_get_profile
 ecris_coulomb_collide_noalloc = LIB.ecris_coulomb_collide_noalloc
@@ -226,6 +255,10 @@ ecris_batch_get_state = LIB.ecris_batch_get_state
 ecris_batch_update_ne = LIB.ecris_batch_update_ne
 ecris_batch_get_cells = LIB.ecris_batch_get_cells
 ecris_batch_get_fptd = LIB.ecris_batch_get_fptd
+ecris_batch_get_extraction_radius = LIB.ecris_batch_get_extraction_radius
+ecris_batch_set_probes = LIB.ecris_batch_set_probes
+ecris_batch_probe_sample = LIB.ecris_batch_probe_sample
+ecris_batch_get_probes = LIB.ecris_batch_get_probes
 ecris_batch_memory = LIB.ecris_batch_memory
 ecris_batch_autotune = LIB.ecris_batch_autotune
 ecris_batch_set_profiling = LIB.ecris_batch_set_profiling
@@ -376,6 +409,25 @@ class Batch:
     def update_ne(self, h):
         self._check(ecris_batch_update_ne(self.b, int(h)))
 
+    def extraction_radius(self, h):
+        rp, _ = self.runs[h]
+        return _radius(rp.species.qmax, lambda a: self._check(ecris_batch_get_extraction_radius(self.b, int(h), a)))
+
+    def set_probes(self, h, cells=None, screens=(), pixels=256):
+        sp, keep = _probe_spec(cells, screens, pixels)
+        self._check(ecris_batch_set_probes(self.b, int(h), ctypes.byref(sp)))
+        self._probe_shape = getattr(self, "_probe_shape", {})
+        self._probe_shape[h] = (len(keep), len(screens), int(pixels))
+
+    def probe_sample(self, h):
+        self._check(ecris_batch_probe_sample(self.b, int(h)))
+
+    def probes(self, h):
+        rp, _ = self.runs[h]
+        nc, ns, px = self._probe_shape[h]
+        return _probes(rp.species.qmax, nc, ns, px,
+                       lambda a, b, c: self._check(ecris_batch_get_probes(self.b, int(h), a, b, c)))
+
     def fptd(self, h):
         rp, _ = self.runs[h]
         return _fptd(rp.species.qmax, lambda a, b: self._check(ecris_batch_get_fptd(self.b, int(h), a, b)))
@@ -478,6 +530,35 @@ def _fptd(qmax, call):
     return {"hist": hist, "age_sum": age_sum}
 
 
+def _probe_spec(cells, screens, pixels):
+    """ecris_probe_spec for the cell list and the (z_lo, z_hi) slabs; the
+    cell array is returned with it and must outlive the call."""
+    c = np.ascontiguousarray([] if cells is None else cells, dtype=np.uint32)
+    sp = ProbeSpec()
+    sp.ncells = len(c)
+    sp.cells = c.ctypes.data if len(c) else None
+    sp.nscreens = len(screens)
+    for k, (lo, hi) in enumerate(screens):
+        sp.z_lo[k], sp.z_hi[k] = float(lo), float(hi)
+    sp.pixels = int(pixels)
+    return sp, c
+
+
+def _probes(qmax, ncells, nscreens, pixels, call):
+    qs = qmax + 1
+    n = ctypes.c_uint64(0)
+    mom = np.zeros((ncells, qs, 7), dtype=np.float64)
+    scr = np.zeros((nscreens, qs, pixels, pixels), dtype=np.uint64)
+    call(ctypes.byref(n), _ptr(mom) if ncells else None, _ptr(scr) if nscreens else None)
+    return {"samples": int(n.value), "moments": mom, "screens": scr}
+
+
+def _radius(qmax, call):
+    r = np.zeros(qmax + 1, dtype=np.float64)
+    call(_ptr(r))
+    return r
+
+
 def _cells(nc, call):
     out = {k: np.zeros(nc, dtype=np.float32) for k in ("ne", "delta_x", "delta_y")}
     call(_ptr(out["ne"]), _ptr(out["delta_x"]), _ptr(out["delta_y"]))
@@ -543,6 +624,26 @@ class Run:
         """n_e of every cell := the time-averaged ion charge density since the
         load or the previous call; delta rebuilt from it."""
         check(self.ctx, ecris_update_ne(self.ctx))
+
+    def extraction_radius(self):
+        """Summed radius (m) of the extracted ions at the aperture plane, by Q."""
+        return _radius(self.qmax, lambda a: check(self.ctx, ecris_get_extraction_radius(self.ctx, a)))
+
+    def set_probes(self, cells=None, screens=(), pixels=256):
+        """Install moment probes on the listed cells and x-y screens on the
+        (z_lo, z_hi) slabs, pixels x pixels each; zeroes their sums."""
+        sp, keep = _probe_spec(cells, screens, pixels)
+        check(self.ctx, ecris_set_probes(self.ctx, ctypes.byref(sp)))
+        self._probe_shape = (len(keep), len(screens), int(pixels))
+
+    def probe_sample(self):
+        """Add the particles as they are now to the probes' sums."""
+        check(self.ctx, ecris_probe_sample(self.ctx))
+
+    def probes(self):
+        """samples, moments [cell, Q, 7] (count, sum v, sum v^2) and screens [s, Q, py, px]."""
+        nc, ns, px = self._probe_shape
+        return _probes(self.qmax, nc, ns, px, lambda a, b, c: check(self.ctx, ecris_get_probes(self.ctx, a, b, c)))
 
     def fptd(self):
         """First-passage times of the extracted ions since the load: hist
