@@ -45,7 +45,9 @@ def test_lockstep_busy_case_every_event_type(E):
     t, orc = P.lockstep(run, rp, st, 60, E=Ef)
     assert_clean(t)
     wall, ext, ion, cx = t["events_seen"]
-    assert wall > 50 and ion > 50 and cx > 5, t["events_seen"]
+    # every event type occurs (the oracle alone over seeds 4-8 sees 140-170
+    # wall hits, 34-47 ionisations and 15-26 charge exchanges in these steps)
+    assert wall > 50 and ion > 15 and cx > 5, t["events_seen"]
     # tallies agree up to guarded boundary outcomes
     d = run.diag()
     assert np.abs(d["lost"] - orc.lost()).sum() <= t["guarded"]

@@ -120,9 +120,19 @@ def test_coulomb_step_conserves_per_cell_and_pairs_as_stated():
 
 @pytest.mark.slow
 def test_two_temperature_relaxation_matches_spitzer_rate():
-    rp = _cell_params(weight=2e6, dt=2e-6)
+    # Two Maxwellian groups of one species (T 3 and 0.5 eV, equal densities)
+    # exchange energy at the Spitzer rate, dT_a/dt = nu (T_b - T_a) with
+    # nu = (8 sqrt(2 pi)/3) n_b e^4 lnL / ((4 pi eps0)^2 M^2) (M/(T_a+T_b))^1.5,
+    # as long as both stay Maxwellian.  For equal masses the groups' own
+    # collisions are no faster than the exchange, so the distributions change
+    # shape as they relax and the two-Maxwellian rate holds for the initial
+    # rate only: measured here over a 2 % decay with 1e6 ions.  A pair
+    # exchanges energy in proportion to 1 - exp(-s) = 1 - <cos chi>, not s:
+    # slow pairs (s ~ 1) saturate.  That factor, computed below by sampling
+    # the initial Maxwellians, is 0.97 at this dt.
+    n = 1_000_000
+    rp = _cell_params(weight=2e6 * 20000 / n, dt=2e-6)
     rng = np.random.default_rng(7)
-    n = 20000
     c0 = 4 * 64 + 4 * 8 + 4
     st = _grouped_state(rp, [c0], [n], np.ones(n), rng, T_eV=1.0)
     M = rp.species.mass_amu * AMU
@@ -138,11 +148,27 @@ def test_two_temperature_relaxation_matches_spitzer_rate():
     Ta, Tb = temp(hot), temp(~hot)
     rate = (8 * math.sqrt(2 * math.pi) / 3) * n_b * QE ** 4 * rp.lnL_ii / ((4 * math.pi * EPS0) ** 2 * M ** 2) \
         * (M / ((Ta + Tb) * QE)) ** 1.5
+    # saturation factor E[(1 - e^-s) (va^2 - vb^2)] / E[s (va^2 - vb^2)] over
+    # hot-cold pairs, s = s1 g^-3 with s1 = (lnL/4pi) (e^2/(eps0 M/2))^2 n dt.
+    # With va^2 - vb^2 = g.(va + vb) and va + vb = alpha g + (a part
+    # independent of g), both averages reduce to alpha E[f(g) g^2] over the
+    # Maxwellian |g| of variance sigma^2 = (T_a + T_b)/M per component; the
+    # denominator is s1 sigma^2 (times the same constant)
+    from scipy.integrate import quad
+    n_all = rp.weight * n / vcell
+    s1 = rp.lnL_ii / (4 * math.pi) * (QE * QE / (EPS0 * 0.5 * M)) ** 2 * n_all * rp.dt
+    sig2 = (Ta + Tb) * QE / M
+    num = quad(lambda g: -math.expm1(-s1 / g ** 3) * g ** 4 * math.exp(-g * g / (2 * sig2)), 0.0, 60 * math.sqrt(sig2),
+               limit=400, points=[s1 ** (1 / 3)])[0]
+    sat = num / (s1 * sig2)
+    assert 0.95 < sat < 0.99
     # dT_a/dt = rate (T_b - T_a) and symmetrically, so T_a - T_b decays at 2 rate
-    steps = int(0.3 / (2 * rate * rp.dt))
+    steps = int(0.02 / (2 * rate * rp.dt))
     d0 = Ta - Tb
     r.step(steps)
     d1 = temp(hot) - temp(~hot)
     got = -math.log(d1 / d0) / (steps * rp.dt)
-    assert got == pytest.approx(2 * rate, rel=0.12)
+    # sampling error about 0.8 %; the groups' change of shape over 2 % of the
+    # decay lowers the mean rate by about 0.6 %
+    assert got == pytest.approx(2 * rate * sat, rel=0.03)
     assert temp(hot) + temp(~hot) == pytest.approx(Ta + Tb, rel=1e-9)
