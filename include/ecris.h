@@ -67,6 +67,19 @@ typedef enum {
 #define ECRIS_F_COULOMB (1u << 4) /* ion-ion Coulomb collisions */
 #define ECRIS_F_RECYCLE (1u << 5) /* re-emit at walls, reinject extracted particles;
                                      off: leavers are frozen and counted once */
+/* Opt-in processes and variants (Sec. II collision block; Secs. III.C, IV). */
+#define ECRIS_F_ISOHEAT (1u << 6) /* isotropic heating: the kick without the drift
+                                     bias, delta = 0 (the paper's diffusion-off run) */
+#define ECRIS_F_DOUBLE (1u << 7)  /* double ionisation Q -> Q+2: rate k2_factor times
+                                     the Lotz-Maxwellian rate with threshold
+                                     P_Q + P_{Q+1}; one word decides, single below
+                                     p k1/(k1+k2), double up to p = 1 - exp(-n_e
+                                     (k1+k2) dt) */
+#define ECRIS_F_ELASTIC (1u << 8) /* elastic ion-atom scattering on the background,
+                                     cross section sigma_el1_cm2 * Q, isotropic in
+                                     the centre-of-mass frame with an atom drawn at
+                                     T0; shares its word with charge exchange in
+                                     proportion to the cross sections */
 
 /* Per-particle state word (ecris_get_state meta): bits 0-7 charge state Q,
  * bits 8-15 events of the last step, bits 16-23 status. */
@@ -76,6 +89,7 @@ typedef enum {
 #define ECRIS_EV_IONIZE (1u << 10)  /* ionised this step */
 #define ECRIS_EV_CX (1u << 11)      /* charge exchange this step */
 #define ECRIS_EV_COULOMB (1u << 12) /* took part in a Coulomb collision */
+#define ECRIS_EV_ELASTIC (1u << 13) /* elastic ion-atom scattering this step */
 #define ECRIS_ST_FROZEN (1u << 16)  /* left the chamber with recycling off */
 
 /* Chamber geometry (Sec. II, Table I shapes). */
@@ -136,6 +150,10 @@ typedef struct {
     int32_t ei_charge_power;/* 1 or 2: power of Q in the kick's D^2 (2 = the text's
                                quadratic dependence) */
     uint32_t flags;         /* ECRIS_F_* */
+    double T_refl_eV;       /* re-emission temperature of ions neutralised at a wall
+                               (Sec. III.C warm atoms, 0.15 eV); 0: T0 */
+    double sigma_el1_cm2;   /* elastic ion-atom cross section of Q=1, cm^2 (ECRIS_F_ELASTIC) */
+    double k2_factor;       /* double-ionisation rate factor (ECRIS_F_DOUBLE), >= 0 */
 } ecris_mcc;
 
 /* Diagnostics filled by ecris_diag.  Arrays are caller-owned; each array

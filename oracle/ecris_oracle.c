@@ -53,6 +53,9 @@
 #define OR_F_EIKICK 8u
 #define OR_F_COULOMB 16u
 #define OR_F_RECYCLE 32u
+#define OR_F_ISOHEAT 64u    /* heating kick without the drift bias: delta = 0 */
+#define OR_F_DOUBLE 128u    /* double ionisation Q -> Q+2 beside Q -> Q+1 */
+#define OR_F_ELASTIC 256u   /* elastic ion-atom scattering, isotropic in the CM frame */
 
 /* per-particle event bits of one step */
 #define OR_EV_WALL 1u
@@ -60,6 +63,7 @@
 #define OR_EV_IONIZE 4u
 #define OR_EV_CX 8u
 #define OR_EV_COULOMB 16u
+#define OR_EV_ELASTIC 32u
 
 /* guard bits: outcomes within rounding distance of a decision surface */
 #define OR_G_CELL 1u
@@ -80,6 +84,9 @@ typedef struct {
     double weight;
     uint64_t seed;
     double dt;
+    double T_refl_eV;                /* re-emission temperature of ions neutralised at a wall (0: T0) */
+    double sigma_el_m2;              /* elastic ion-atom cross section of Q = 1 (scaled by Q) */
+    double k2_factor;                /* double-ionisation rate factor */
 } or_params;
 
 typedef struct {
@@ -214,10 +221,13 @@ static int64_t or_cell(const or_params *p, double x, double y, double z, uint32_
  * distance of could change its outcome this step: the ionisation decision
  * (word w0 against the probability from the other cell's n_e and zone) or,
  * for an ion, the heating kick (the other cell's n_e, zone or delta). */
+static int or_ion_outcome(const or_params *p, double ne_c, int zc, const double *rates, const double *rates2,
+                          int Q, uint32_t w0, int *near);
+
 static int or_cell_record_guard(const or_params *p, double x, double y, double z, int64_t c,
                                 const double *ne, const int32_t *zone, const double *dlx,
-                                const double *dly, const double *rates, int q_before, int q_after,
-                                uint32_t w0)
+                                const double *dly, const double *rates, const double *rates2, int q_before,
+                                int q_after, uint32_t w0)
 {
     const double tol = 1e-4;
     double g[3] = {(x + p->R0) / or_dx(p), (y + p->R0) / or_dy(p), z / or_dz(p)};
@@ -231,11 +241,10 @@ static int or_cell_record_guard(const or_params *p, double x, double y, double z
         int other = (g[k] - idx[k] < 0.5) ? idx[k] - 1 : idx[k] + 1;
         if (other < 0 || other >= n[k]) continue;
         int64_t c2 = c + (other - idx[k]) * stride[k];
-        if ((p->flags & OR_F_IONIZE) && q_before < p->qmax) {
-            double t1 = floor(or_threshold(-expm1(-ne[c] * rates[zone[c] * p->qmax + q_before] * p->dt)));
-            double t2 = floor(or_threshold(-expm1(-ne[c2] * rates[zone[c2] * p->qmax + q_before] * p->dt)));
-            if (((double)w0 < t1) != ((double)w0 < t2)) return 1;
-        }
+        if ((p->flags & OR_F_IONIZE) && q_before < p->qmax &&
+            or_ion_outcome(p, ne[c], zone[c], rates, rates2, q_before, w0, NULL) !=
+                or_ion_outcome(p, ne[c2], zone[c2], rates, rates2, q_before, w0, NULL))
+            return 1;
         if ((p->flags & OR_F_EIKICK) && q_after >= 1 &&
             (ne[c2] != ne[c] || zone[c2] != zone[c] || dlx[c2] != dlx[c] || dly[c2] != dly[c]))
             return 1;
@@ -311,6 +320,44 @@ void or_build_rates(const or_params *p, const double *ip_eV, const int32_t *n_ou
     }
 }
 
+/* Double ionisation Q -> Q+2 (Sec. II; the fit of [22] is not available):
+ * k2_factor times the Lotz-Maxwellian rate with the threshold P_Q + P_{Q+1}
+ * (both electrons removed) and q_Q outer electrons; rates2[zone*qmax + Q],
+ * zero for Q = qmax - 1.  Removal of three or more electrons is left out
+ * (the paper finds it a minor contributor). */
+void or_build_rates2(const or_params *p, const double *ip_eV, const int32_t *n_outer, double *rates2)
+{
+    for (int zone = 0; zone < 2; ++zone) {
+        double Te = zone ? p->Te_warm : p->Te_cold;
+        for (int q = 0; q < p->qmax; ++q)
+            rates2[zone * p->qmax + q] =
+                q + 1 < p->qmax ? p->k2_factor * or_lotz_rate(ip_eV[q] + ip_eV[q + 1], n_outer[q], Te) : 0.0;
+    }
+}
+
+/* Outcome of the ionisation word w0 in a cell: 0 none, 1 single, 2 double.
+ * One step's probability of any ionisation is 1 - exp(-n_e (k1 + k2) dt); it
+ * is shared between the two in proportion to k1 and k2, so w0 below the
+ * single threshold ionises once and w0 between the two thresholds twice.
+ * *near is set when w0 lies within rounding distance of either threshold. */
+static int or_ion_outcome(const or_params *p, double ne_c, int zc, const double *rates, const double *rates2,
+                          int Q, uint32_t w0, int *near)
+{
+    double k1 = rates[zc * p->qmax + Q];
+    double k2 = (rates2 && (p->flags & OR_F_DOUBLE)) ? rates2[zc * p->qmax + Q] : 0.0;
+    if (k2 <= 0.0) {
+        double thr = or_threshold(-expm1(-ne_c * k1 * p->dt));
+        if (near && fabs((double)w0 - thr) < 1e-5 * thr + 2.0) *near = 1;
+        return (double)w0 < floor(thr) ? 1 : 0;
+    }
+    double pt = -expm1(-ne_c * (k1 + k2) * p->dt);
+    double thr = or_threshold(pt), thr1 = or_threshold(pt * (k1 / (k1 + k2)));
+    if (near && (fabs((double)w0 - thr) < 1e-5 * thr + 2.0 || fabs((double)w0 - thr1) < 1e-5 * thr1 + 2.0))
+        *near = 1;
+    if ((double)w0 < floor(thr1)) return 1;
+    return (double)w0 < floor(thr) ? 2 : 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Per-cell electron data.  A cell is in the ECR zone (warm electrons) when */
 /* |B| at its centre is below B_ECR.  n_e there is the per-cell input (or   */
@@ -351,6 +398,11 @@ void or_cell_delta(const or_params *p, const double *ne, const int32_t *zone, co
 {
     int nx = p->nx, ny = p->ny, nz = p->nz;
     double dx = or_dx(p);
+    if (p->flags & OR_F_ISOHEAT) {
+        /* isotropic heating (Sec. IV): the kick without the drift bias */
+        for (int64_t c = 0; c < (int64_t)nx * ny * nz; ++c) { dlx[c] = 0.0; dly[c] = 0.0; }
+        return;
+    }
     for (int iz = 0; iz < nz; ++iz)
         for (int iy = 0; iy < ny; ++iy)
             for (int ix = 0; ix < nx; ++ix) {
@@ -575,7 +627,7 @@ static void or_coulomb(const or_params *p, int64_t n, const int64_t *cell, const
 #define OR_LEAVE_ZL 3
 #define OR_LEAVE_APERTURE 4
 
-void or_step(const or_params *p, const double *rates, const double *ne, const int32_t *zone,
+void or_step(const or_params *p, const double *rates, const double *rates2, const double *ne, const int32_t *zone,
              const double *dlx, const double *dly, const double *E, int64_t n, double *x,
              double *y, double *z, double *vx, double *vy, double *vz, int32_t *q,
              uint32_t *status, uint32_t step, uint8_t *events, uint8_t *guard, or_tally *t,
@@ -586,6 +638,9 @@ void or_step(const or_params *p, const double *rates, const double *ne, const in
     const double gband = 1e-4 * fmin(or_dx(p), or_dz(p)); /* metres */
     const double eps_wall = 1e-6 * p->L;
     const double sig0 = sqrt(p->T0_eV * OR_QE / M);
+    /* ions neutralised at a wall come back at T_refl (Sec. III.C, warm
+     * reflected atoms); atoms hitting a wall and reinjected gas at T0 */
+    const double sig_refl = p->T_refl_eV > 0.0 ? sqrt(p->T_refl_eV * OR_QE / M) : sig0;
     int64_t *cell = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
     uint8_t *leave = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
     uint8_t *part = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
@@ -664,20 +719,63 @@ void or_step(const or_params *p, const double *rates, const double *ne, const in
         double ne_c = ne[c];
         int zc = zone[c];
         int Q = q[i];
-        /* step-wise ionisation Q -> Q+1, probability 1 - exp(-n_e k_Q(T_e) dt) */
+        /* step-wise ionisation Q -> Q+1, probability 1 - exp(-n_e k_Q(T_e) dt);
+         * with double ionisation, Q -> Q+1 or Q+2 (or_ion_outcome) */
         if ((p->flags & OR_F_IONIZE) && Q < p->qmax) {
-            double pr = -expm1(-ne_c * rates[zc * p->qmax + Q] * dt);
-            double thr = or_threshold(pr);
-            if (fabs((double)w[0] - thr) < 1e-5 * thr + 2.0) guard[i] |= OR_G_IONIZE;
-            if ((double)w[0] < floor(thr)) { Q += 1; events[i] |= OR_EV_IONIZE; }
+            int near = 0;
+            int up = or_ion_outcome(p, ne_c, zc, rates, rates2, Q, w[0], &near);
+            if (near) guard[i] |= OR_G_IONIZE;
+            if (up) { Q += up; events[i] |= OR_EV_IONIZE; }
         }
         /* charge exchange with the neutral background: sigma_Q = Q sigma_1,
          * rate n0 sigma_Q v_rel, v_rel^2 = |v|^2 + 8 kT0/(pi M); Q = 2 is
          * forbidden; Q = 1 (resonant) gives a thermal ion; Q >= 3 -> Q-1 with
          * half of the release energy as an isotropic kick */
-        if ((p->flags & OR_F_CX) && p->n0_m3 > 0.0 && Q >= 1 && Q != 2) {
+        /* with elastic scattering, charge exchange and elastic scattering
+         * compete: one step's probability of either is 1 - exp(-n0 (sigma_cx +
+         * sigma_el) v_rel dt), shared in proportion to the cross sections; the
+         * word w1 below the charge-exchange threshold exchanges, between the
+         * two thresholds it scatters elastically */
+        int elastic = 0;
+        if ((p->flags & OR_F_ELASTIC) && p->n0_m3 > 0.0 && Q >= 1 && p->sigma_el_m2 > 0.0) {
+            double scx = ((p->flags & OR_F_CX) && Q != 2) ? p->sigma1_m2 * Q : 0.0;
+            double sel = p->sigma_el_m2 * Q;
+            double vrel = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + 8.0 * p->T0_eV * OR_QE / (OR_PI * M));
+            double pt = -expm1(-p->n0_m3 * (scx + sel) * vrel * dt);
+            double thr = or_threshold(pt), thr1 = or_threshold(pt * (scx / (scx + sel)));
+            if (fabs((double)w[1] - thr) < 1e-5 * thr + 2.0 || fabs((double)w[1] - thr1) < 1e-5 * thr1 + 2.0)
+                guard[i] |= OR_G_CX;
+            if ((double)w[1] >= floor(thr1) && (double)w[1] < floor(thr)) elastic = 1;
+        }
+        if (elastic) {
+            /* isotropic in the centre-of-mass frame with a background atom
+             * drawn from the Maxwellian at T0 (stream-3 words); the new
+             * direction of the relative velocity from the stream-2 words (the
+             * wall stream, unused by a particle that stayed inside) */
+            uint32_t u[4], d[4];
+            or_words(p->seed, (uint32_t)i, step, 3, u);
+            or_words(p->seed, (uint32_t)i, step, 2, d);
+            double r1g = sig0 * sqrt(-2.0 * log(or_unit(u[0])));
+            double t1 = 2.0 * OR_PI * or_unit(u[1]);
+            double r2g = sig0 * sqrt(-2.0 * log(or_unit(u[2])));
+            double t2 = 2.0 * OR_PI * or_unit(u[3]);
+            double va[3] = {r1g * cos(t1), r1g * sin(t1), r2g * cos(t2)};
+            double gx = v[0] - va[0], gy = v[1] - va[1], gz = v[2] - va[2];
+            double gm = sqrt(gx * gx + gy * gy + gz * gz);
+            double ct = 2.0 * or_unit(d[0]) - 1.0;
+            double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+            double ph = 2.0 * OR_PI * or_unit(d[1]);
+            double n[3] = {st * cos(ph), st * sin(ph), ct};
+            for (int k = 0; k < 3; ++k) v[k] = 0.5 * (v[k] + va[k]) + 0.5 * gm * n[k];
+            events[i] |= OR_EV_ELASTIC;
+        } else if ((p->flags & OR_F_CX) && p->n0_m3 > 0.0 && Q >= 1 && Q != 2) {
             double vrel = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + 8.0 * p->T0_eV * OR_QE / (OR_PI * M));
             double pr = -expm1(-p->n0_m3 * p->sigma1_m2 * Q * vrel * dt);
+            if ((p->flags & OR_F_ELASTIC) && p->sigma_el_m2 > 0.0) {
+                /* the exchange threshold of the shared word, as above */
+                double sel = p->sigma_el_m2 * Q, scx = p->sigma1_m2 * Q;
+                pr = -expm1(-p->n0_m3 * (scx + sel) * vrel * dt) * (scx / (scx + sel));
+            }
             double thr = or_threshold(pr);
             if (fabs((double)w[1] - thr) < 1e-5 * thr + 2.0) guard[i] |= OR_G_CX;
             if ((double)w[1] < floor(thr)) {
@@ -718,7 +816,7 @@ void or_step(const or_params *p, const double *rates, const double *ne, const in
                 for (int k = 0; k < 3; ++k) v[k] += D * d[k] / dm;
         }
         if ((guard[i] & OR_G_CELL) &&
-            or_cell_record_guard(p, x1, y1, z1, c, ne, zone, dlx, dly, rates, q[i], Q, w[0]))
+            or_cell_record_guard(p, x1, y1, z1, c, ne, zone, dlx, dly, rates, rates2, q[i], Q, w[0]))
             guard[i] |= OR_G_CELLREC;
         q[i] = Q;
         vx[i] = v[0]; vy[i] = v[1]; vz[i] = v[2];
@@ -768,7 +866,7 @@ void or_step(const or_params *p, const double *rates, const double *ne, const in
                 uint32_t w[4];
                 double v[3];
                 or_words(p->seed, (uint32_t)i, step, 2, w);
-                or_emit(sig0, nrm, e1, e2, w, v);
+                or_emit(Q >= 1 && leave[i] != OR_LEAVE_APERTURE ? sig_refl : sig0, nrm, e1, e2, w, v);
                 x[i] = cx; y[i] = cy; z[i] = cz;
                 vx[i] = v[0]; vy[i] = v[1]; vz[i] = v[2];
             } else {

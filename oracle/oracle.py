@@ -19,7 +19,8 @@ SRC = os.path.join(HERE, "ecris_oracle.c")
 LIB = os.path.join(HERE, "libecris_oracle.so")
 
 F_PUSH, F_IONIZE, F_CX, F_EIKICK, F_COULOMB, F_RECYCLE = 1, 2, 4, 8, 16, 32
-EV_WALL, EV_EXTRACT, EV_IONIZE, EV_CX, EV_COULOMB = 1, 2, 4, 8, 16
+F_ISOHEAT, F_DOUBLE, F_ELASTIC = 64, 128, 256
+EV_WALL, EV_EXTRACT, EV_IONIZE, EV_CX, EV_COULOMB, EV_ELASTIC = 1, 2, 4, 8, 16, 32
 G_CELL, G_BOUNDARY, G_IONIZE, G_CX, G_CELLREC = 1, 2, 4, 8, 16
 # guards that can change a single-particle outcome (no Coulomb pairing)
 G_SINGLE = G_BOUNDARY | G_IONIZE | G_CX | G_CELLREC
@@ -58,6 +59,7 @@ class Params(ctypes.Structure):
         ("E_cx_eV", ctypes.c_double), ("lnL_ii", ctypes.c_double), ("lnL_ei", ctypes.c_double),
         ("ei_charge_power", ctypes.c_int32), ("flags", ctypes.c_uint32),
         ("weight", ctypes.c_double), ("seed", ctypes.c_uint64), ("dt", ctypes.c_double),
+        ("T_refl_eV", ctypes.c_double), ("sigma_el_m2", ctypes.c_double), ("k2_factor", ctypes.c_double),
     ]
 
 
@@ -90,6 +92,7 @@ def lib():
         _lib.or_lotz_rate.argtypes = [d, ctypes.c_int, d]
         _lib.or_lotz_rate.restype = d
         _lib.or_build_rates.argtypes = [pp, p, p, p]
+        _lib.or_build_rates2.argtypes = [pp, p, p, p]
         _lib.or_setup_cells.argtypes = [pp, p, d, d, p, p, p, p, p]
         _lib.or_cell_delta.argtypes = [pp, p, p, p, p, p]
         _lib.or_boris.argtypes = [d, p, p, d, p]
@@ -101,7 +104,7 @@ def lib():
         _lib.or_nanbu_s.argtypes = [d, d, d, d, d, d, d]
         _lib.or_nanbu_s.restype = d
         _lib.or_scatter_pair.argtypes = [p, p, d, d]
-        _lib.or_step.argtypes = [pp, p, p, p, p, p, p, i64, p, p, p, p, p, p, p, p, u32, p, p,
+        _lib.or_step.argtypes = [pp, p, p, p, p, p, p, p, i64, p, p, p, p, p, p, p, p, u32, p, p,
                                  ctypes.POINTER(Tally), p, p]
     return _lib
 
@@ -138,6 +141,9 @@ def make_params(rp, dt=None) -> Params:
     p.weight = rp.weight
     p.seed = rp.seed
     p.dt = rp.dt if dt is None else dt
+    p.T_refl_eV = rp.T_refl_eV
+    p.sigma_el_m2 = rp.sigma_el1_cm2 * 1e-4
+    p.k2_factor = rp.k2_factor
     return p
 
 
@@ -247,6 +253,10 @@ class OracleRun:
         self.rates = np.zeros(2 * qmax)
         lib().or_build_rates(ctypes.byref(self.p), _ptr(np.ascontiguousarray(ip, np.float64)),
                              _ptr(np.ascontiguousarray(nout, np.int32)), _ptr(self.rates))
+        self.rates2 = np.zeros(2 * qmax)
+        if rp.flags & F_DOUBLE:
+            lib().or_build_rates2(ctypes.byref(self.p), _ptr(np.ascontiguousarray(ip, np.float64)),
+                                  _ptr(np.ascontiguousarray(nout, np.int32)), _ptr(self.rates2))
         self.ne = np.zeros(nc)
         self.zone = np.zeros(nc, dtype=np.int32)
         self.Bmag = np.zeros(nc)
@@ -289,7 +299,7 @@ class OracleRun:
         acc_g = np.zeros(self.n, dtype=np.uint8)
         for _ in range(nsteps):
             q_before = self.q.copy()
-            lib().or_step(ctypes.byref(self.p), _ptr(self.rates), _ptr(self.ne), _ptr(self.zone),
+            lib().or_step(ctypes.byref(self.p), _ptr(self.rates), _ptr(self.rates2), _ptr(self.ne), _ptr(self.zone),
                           _ptr(self.dlx), _ptr(self.dly), _ptr(self.E), self.n,
                           _ptr(self.x), _ptr(self.y), _ptr(self.z), _ptr(self.vx), _ptr(self.vy),
                           _ptr(self.vz), _ptr(self.q), _ptr(self.status), self.step_index,

@@ -95,6 +95,7 @@ struct HostRun {
     std::vector<double> ip;
     std::vector<int> nout;
     std::vector<double> rate[2];   // m^3/s per Q, zone 0 cold, 1 warm
+    std::vector<double> rate2[2];  // double ionisation Q -> Q+2 (m^3/s), same layout
     std::vector<float> cell_ne;    // FP32 n_e per cell as the kernels see it (m^-3)
     std::vector<unsigned char> cell_zone;
     ecris_mcc mcc;
@@ -479,6 +480,8 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.n0s1 = (float)(h.mcc.n0_cm3 * 1e6 * h.mcc.sigma1_cm2 * 1e-4);
     R.vth2 = (float)(8.0 * h.mcc.T0_eV * kE / (kPi * M));
     R.dv_cx = (float)std::sqrt(2.0 * 0.5 * h.mcc.E_cx_eV * kE / M);
+    R.n0sel = (h.mcc.flags & kFElastic) ? (float)(h.mcc.n0_cm3 * 1e6 * h.mcc.sigma_el1_cm2 * 1e-4) : 0.0f;
+    R.sig_refl = h.mcc.T_refl_eV > 0.0 ? (float)std::sqrt(h.mcc.T_refl_eV * kE / M) : R.sig0;
     for (int zone = 0; zone < 2; ++zone) {
         const double Te = zone ? h.Te_w : h.Te_c;
         R.ei_coef[zone] = (float)(3.715e-6 * h.mcc.lnL_ei * dt / (h.mass_amu * h.mass_amu * std::sqrt(Te)));
@@ -569,7 +572,8 @@ void cell_records(HostRun& h, const std::vector<double>& ne, const std::vector<u
             for (int ix = 0; ix < h.nx; ++ix) {
                 const size_t c = ((size_t)iz * h.ny + iy) * h.nx + ix;
                 double dlx = 0.0, dly = 0.0;
-                if (ne[c] > 0.0) {
+                // isotropic heating (Sec. IV): no drift bias
+                if (ne[c] > 0.0 && !(h.mcc.flags & kFIsoheat)) {
                     const double Te = zone[c] ? h.Te_w : h.Te_c;
                     const double rl = 2.38e-6 * std::sqrt(Te) / (h.bmag[c] * dx) / ne[c];
                     const double sx = NE(iz, iy - 1, ix) - NE(iz, iy + 1, ix) +
@@ -594,9 +598,16 @@ ecris_status upload_dt(ecris_ctx* ctx, double dt)
     // the pinned staging buffers may still feed an earlier copy
     CK(cudaStreamSynchronize(ctx->stream));
     fill_rundev(ctx, dt, *ctx->h_run);
+    // k1 dt, or (k1 + k2) dt with double ionisation, and the single share
+    // k1 / (k1 + k2)
+    const bool dbl = (ctx->h.mcc.flags & kFDouble) != 0;
     for (int zone = 0; zone < 2; ++zone)
-        for (int q = 0; q < kQSlots; ++q)
-            ctx->h_kdt[zone * kQSlots + q] = q < ctx->h.qmax ? (float)(ctx->h.rate[zone][q] * dt) : 0.0f;
+        for (int q = 0; q < kQSlots; ++q) {
+            const double k1 = q < ctx->h.qmax ? ctx->h.rate[zone][q] : 0.0;
+            const double k2 = (dbl && q < ctx->h.qmax) ? ctx->h.rate2[zone][q] : 0.0;
+            ctx->h_kdt[zone * kQSlots + q] = (float)((k1 + k2) * dt);
+            ctx->h_kdt[2 * kQSlots + zone * kQSlots + q] = k1 + k2 > 0.0 ? (float)(k1 / (k1 + k2)) : 1.0f;
+        }
     // the kernels' FP32 product n_e k_0 dt, maximised over the cells, with a
     // relative margin that covers any rounding difference in the probability
     float lam = 0.0f;
@@ -610,7 +621,7 @@ ecris_status upload_dt(ecris_ctx* ctx, double dt)
     const double pmax = -std::expm1(-(double)ctx->h_run->lam0_max);
     const double gate = std::ceil(pmax * 4294967296.0);
     ctx->h_run->atom_gate = gate >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)gate;
-    CK(cudaMemcpyAsync(ctx->d_kdt, ctx->h_kdt, 2 * kQSlots * sizeof(float), cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync(ctx->d_kdt, ctx->h_kdt, 4 * kQSlots * sizeof(float), cudaMemcpyHostToDevice,
                        ctx->stream));
     ctx->dt_loaded = dt;
     ++ctx->param_version;
@@ -892,7 +903,7 @@ ecris_status ecris_create(ecris_ctx** out, int device, void* cuda_stream)
         }
     }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_run, sizeof(RunDev));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_kdt, 2 * kQSlots * sizeof(float));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_kdt, 4 * kQSlots * sizeof(float));
     if (e != cudaSuccess) {
         g_create_error = std::string("ecris_create: ") + cudaGetErrorString(e);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -958,7 +969,9 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
     if (!(mcc->n0_cm3 >= 0.0) || !std::isfinite(mcc->n0_cm3) || !finite_pos(mcc->T0_eV) ||
         !(mcc->sigma1_cm2 >= 0.0) || !(mcc->E_cx_eV >= 0.0) || !(mcc->lnL_ii >= 0.0) ||
         !(mcc->lnL_ei >= 0.0) || (mcc->ei_charge_power != 1 && mcc->ei_charge_power != 2) ||
-        (mcc->flags & ~0x3Fu))
+        (mcc->flags & ~kFlagMask) || !(mcc->T_refl_eV >= 0.0) || !std::isfinite(mcc->T_refl_eV) ||
+        !(mcc->sigma_el1_cm2 >= 0.0) || !std::isfinite(mcc->sigma_el1_cm2) || !(mcc->k2_factor >= 0.0) ||
+        !std::isfinite(mcc->k2_factor))
         return fail(ctx, ECRIS_EINVAL, "init_fields: invalid collision parameters");
 
     CK(cudaSetDevice(ctx->device));
@@ -985,6 +998,12 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
         h.rate[zone].resize(sp->qmax);
         const double Te = zone ? h.Te_w : h.Te_c;
         for (int q = 0; q < sp->qmax; ++q) h.rate[zone][q] = lotz_rate(h.ip[q], h.nout[q], Te);
+        // double ionisation (the fit of [22] is not available): k2_factor
+        // times the Lotz-Maxwellian rate with threshold P_Q + P_{Q+1}
+        h.rate2[zone].assign(sp->qmax, 0.0);
+        if (mcc->flags & kFDouble)
+            for (int q = 0; q + 1 < sp->qmax; ++q)
+                h.rate2[zone][q] = mcc->k2_factor * lotz_rate(h.ip[q] + h.ip[q + 1], h.nout[q], Te);
     }
 
     // per-cell electron data in FP64: zone by |B| at the centre, n_e, delta
@@ -1020,7 +1039,7 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
     }
     CK(cudaMallocAsync((void**)&ctx->d_cell, nc * sizeof(float4), ctx->stream));
     CK(cudaMallocAsync((void**)&ctx->d_E, nc * sizeof(float4), ctx->stream));
-    CK(cudaMallocAsync((void**)&ctx->d_kdt, 2 * kQSlots * sizeof(float), ctx->stream));
+    CK(cudaMallocAsync((void**)&ctx->d_kdt, 4 * kQSlots * sizeof(float), ctx->stream));
     // the same for every run: built once per process
     static const std::vector<float> nanbu = [] {
         std::vector<float> t(kNanbuN);
@@ -1463,6 +1482,7 @@ struct ecris_batch {
     uint2* d_items = nullptr;       // work list (handle, tile)
     size_t items_cap = 0;
     uint32_t nitems = 0;
+    bool variants = false;          // some run has an opt-in process of kFVariants
     bool layout_dirty = true;       // work list must be rebuilt
     bool params_dirty = true;       // parameter blocks must be uploaded
     cudaGraphExec_t gexec = nullptr;
@@ -1592,6 +1612,9 @@ ecris_status batch_items(ecris_batch* b)
         BCK(cudaEventRecord(b->items_staged, b->stream));
     }
     b->nitems = (uint32_t)items.size();
+    b->variants = false;
+    for (auto* c : b->runs)
+        if (c && (c->h.mcc.flags & kFVariants)) b->variants = true;
     b->layout_dirty = false;
     b->graph_dirty = true;
     return ECRIS_OK;
@@ -1621,7 +1644,8 @@ cudaError_t batch_side_streams(ecris_batch* b)
 // collision kernels overlap; then the step counters of the others.
 cudaError_t batch_launch(ecris_batch* b)
 {
-    cudaError_t e = launch_step_batch(b->d_runs, b->d_items, b->nitems, b->sm_count * batch_bps(b), b->stream);
+    cudaError_t e = launch_step_batch(b->d_runs, b->d_items, b->nitems, b->sm_count * batch_bps(b), b->variants,
+                                      b->stream);
     if (e == cudaSuccess) e = launch_leave_batch(b->d_runs, (uint32_t)b->runs.size(), b->d_ticket, b->stream);
     if (e == cudaSuccess) e = batch_side_streams(b);
     if (e == cudaSuccess) e = cudaEventRecord(b->side_fork, b->stream);
@@ -1872,7 +1896,8 @@ ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps)
         } else {
             // timed: the same launches as the graph, one by one
             BCK(b->timer.run(kKindStep, b->stream, [&] {
-                return launch_step_batch(b->d_runs, b->d_items, b->nitems, b->sm_count * batch_bps(b), b->stream);
+                return launch_step_batch(b->d_runs, b->d_items, b->nitems, b->sm_count * batch_bps(b),
+                                         b->variants, b->stream);
             }));
             BCK(b->timer.run(kKindOther, b->stream, [&] {
                 return launch_leave_batch(b->d_runs, (uint32_t)b->runs.size(), b->d_ticket, b->stream);

@@ -45,6 +45,7 @@ constexpr uint32_t kEvExtract = 1u << 9;
 constexpr uint32_t kEvIonize = 1u << 10;
 constexpr uint32_t kEvCx = 1u << 11;
 constexpr uint32_t kEvCoulomb = 1u << 12;
+constexpr uint32_t kEvElastic = 1u << 13;
 constexpr uint32_t kStFrozen = 1u << 16;
 constexpr uint32_t kStPad = 1u << 17;   // padding slot, never processed
 
@@ -55,6 +56,12 @@ constexpr uint32_t kFCx = 1u << 2;
 constexpr uint32_t kFEikick = 1u << 3;
 constexpr uint32_t kFCoulomb = 1u << 4;
 constexpr uint32_t kFRecycle = 1u << 5;
+constexpr uint32_t kFIsoheat = 1u << 6;
+constexpr uint32_t kFDouble = 1u << 7;
+constexpr uint32_t kFElastic = 1u << 8;
+constexpr uint32_t kFlagMask = 0x1FFu;
+// processes whose code only the variant step kernels carry
+constexpr uint32_t kFVariants = kFDouble | kFElastic;
 constexpr uint32_t kFHasE = 1u << 16;   // internal: the run has a nonzero E grid (the push gathers it)
 
 constexpr uint32_t kNoCell = 0xFFFFFFFFu;
@@ -106,6 +113,8 @@ struct alignas(16) RunDev {
     float n0s1;                  // n0 * sigma_1 (1/m)
     float vth2;                  // 8 kT0 / (pi M)
     float dv_cx;                 // kick of a Q>=3 charge exchange: sqrt(2 (E_cx/2) / M)
+    float n0sel;                 // n0 * sigma_el1 (1/m): elastic ion-atom scattering
+    float sig_refl;              // thermal speed of ions re-emitted after neutralisation at a wall
     float ei_coef[2];            // D^2 = ei_coef[zone] * n_e * Q^p (zone 0 cold, 1 warm)
     int32_t ei_pow;
     float ke_scale;              // (M/2) / e * 1e6: micro-eV per (m/s)^2
@@ -121,7 +130,8 @@ struct alignas(16) RunDev {
     uint32_t *id;                // stable particle id (Philox counter word, output order)
     const float4 *cell;          // {n_e (m^-3), zone (0/1), delta_x, delta_y}
     const float4 *E;             // {E_x, E_y, E_z, 0} per cell centre
-    const float *kdt;            // ionisation rate * dt, [zone * 64 + Q]
+    const float *kdt;            // ionisation rate * dt, [zone * 64 + Q] ((k1 + k2) dt with double
+                                 // ionisation), then [2 * 64 + zone * 64 + Q] the single share k1/(k1+k2)
     unsigned long long *dep;     // packed deposit accumulator: count << 32 | charge
     unsigned long long *tally;   // kTallyWords
     uint4 *plist;                // Coulomb participants of each tile: (slot, cell, id, 0), kTile slots a tile
@@ -345,7 +355,10 @@ int step_batch_blocks_per_sm();
 // the step counters alone); launch_bump_steps then advances the counters of
 // the runs without Coulomb collisions (the collision kernels of the others,
 // launched in between, advance theirs); entries with step == NULL are skipped
-cudaError_t launch_step_batch(const RunDev* runs, const uint2* items, uint32_t nitems, int grid, cudaStream_t s);
+// variants: launch the kernel with the opt-in processes' code (some run has
+// one of kFVariants)
+cudaError_t launch_step_batch(const RunDev* runs, const uint2* items, uint32_t nitems, int grid, bool variants,
+                              cudaStream_t s);
 cudaError_t launch_bump_steps(const RunDev* runs, uint32_t nruns, cudaStream_t s);
 // message returned by ecris_last_error(NULL) on the calling thread
 void ecris_internal_set_thread_error(const char* msg);

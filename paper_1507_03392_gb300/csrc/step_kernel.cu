@@ -140,11 +140,40 @@ __device__ __forceinline__ bool move(const RunDev& R, int32_t& X, int32_t& Y, in
     return false;
 }
 
+// Elastic ion-atom scattering (a rare event, kept out of line so that the
+// per-particle code's registers do not carry it): isotropic in the
+// centre-of-mass frame with a background atom drawn at T0 from the stream-3
+// words u; the new direction of the relative velocity from the wall stream,
+// unused by a particle that stays inside
+__device__ __noinline__ void elastic_scatter(const RunDev& R, const Words& u, uint32_t pid, uint32_t step, float& vx,
+                                             float& vy, float& vz)
+{
+    const Words d = rng_words(R, pid, step, 2u);
+    float s1, c1, s2, c2;
+    const float r1 = R.sig0 * sqrtf(-2.0f * logf(unit01(u.w0)));
+    sincospif(2.0f * unit01(u.w1), &s1, &c1);
+    const float r2 = R.sig0 * sqrtf(-2.0f * logf(unit01(u.w2)));
+    sincospif(2.0f * unit01(u.w3), &s2, &c2);
+    const float ax = r1 * c1, ay = r1 * s1, az = r2 * c2;
+    const float gx = vx - ax, gy = vy - ay, gz = vz - az;
+    const float gm = sqrtf(gx * gx + gy * gy + gz * gz);
+    const float ct = 2.0f * unit01(d.w0) - 1.0f;
+    const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+    float sp, cp;
+    sincospif(2.0f * unit01(d.w1), &sp, &cp);
+    vx = 0.5f * (vx + ax) + 0.5f * gm * (st * cp);
+    vy = 0.5f * (vy + ay) + 0.5f * gm * (st * sp);
+    vz = 0.5f * (vz + az) + 0.5f * gm * ct;
+}
+
 // Advance one particle by one step.  pid is its stable id (the Philox counter
 // word).  On return dep_cell is the cell it deposits in and ckey the cell
 // where it takes part in Coulomb collisions (kNoCell if it does not).  A
 // particle that left the chamber keeps its old position and returns true
 // with its pushed velocity: the leaver pass finishes its step.
+// kVar: with the code of the opt-in processes (double ionisation, elastic
+// ion-atom scattering); without it the kernels carry none of their branches
+template <bool kVar>
 __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uint32_t step, int32_t& X,
                                               int32_t& Y, int32_t& Z, float& vx, float& vy, float& vz,
                                               uint32_t& meta, uint32_t& ckey, uint32_t& dep_cell)
@@ -215,17 +244,47 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
     const int zone = cr.y > 0.5f ? 1 : 0;
     if (ionize && need) {
         const float lam = cr.x * __ldg(R.kdt + zone * kQSlots + Q);
-        if (fires(w.w0, event_prob(lam))) {
+        if constexpr (kVar) {
+            const float p = event_prob(lam);
+            if (fires(w.w0, p)) {
+                // with double ionisation the word below p k1/(k1+k2) removes
+                // one electron, the rest of [0, p) two
+                uint32_t up = 1u;
+                if ((R.flags & kFDouble) && !fires(w.w0, p * __ldg(R.kdt + 2 * kQSlots + zone * kQSlots + Q)))
+                    up = 2u;
+                if (Q == 0) R.birth[pid] = step;   // an ion is born (first-passage clock)
+                Q += up;
+                ev |= kEvIonize;
+            }
+        } else if (fires(w.w0, event_prob(lam))) {
             if (Q == 0) R.birth[pid] = step;   // an ion is born (first-passage clock)
             Q += 1;
             ev |= kEvIonize;
         }
     }
-    if ((R.flags & kFCx) && R.n0s1 > 0.0f && Q >= 1 && Q != 2) {
+    // collisions with the neutral background: 1 charge exchange, 2 elastic
+    uint32_t coll = 0u;
+    if (kVar && (R.flags & kFElastic) && R.n0sel > 0.0f) {
+        if (Q >= 1) {
+            // either process with probability 1 - exp(-n0 (sigma_cx + sigma_el)
+            // v_rel dt), shared in proportion to the cross sections
+            const float vrel = sqrtf(vx * vx + vy * vy + vz * vz + R.vth2);
+            const float scx = ((R.flags & kFCx) && Q != 2) ? R.n0s1 * (float)Q : 0.0f;
+            const float sel = R.n0sel * (float)Q;
+            const float pt = event_prob((scx + sel) * vrel * R.dt);
+            if (fires(w.w1, pt)) coll = fires(w.w1, pt * (scx / (scx + sel))) ? 1u : 2u;
+        }
+    } else if ((R.flags & kFCx) && R.n0s1 > 0.0f && Q >= 1 && Q != 2) {
         const float vrel = sqrtf(vx * vx + vy * vy + vz * vz + R.vth2);
         const float p = event_prob(R.n0s1 * (float)Q * vrel * R.dt);
-        if (fires(w.w1, p)) {
-            const Words u = rng_words(R, pid, step, 3u);
+        if (fires(w.w1, p)) coll = 1u;
+    }
+    if (coll) {
+        const Words u = rng_words(R, pid, step, 3u);
+        if (kVar && coll == 2u) {
+            elastic_scatter(R, u, pid, step, vx, vy, vz);
+            ev |= kEvElastic;
+        } else {
             ev |= kEvCx;
             if (Q == 1) {
                 float s1, c1, s2, c2;
@@ -351,6 +410,9 @@ __device__ __forceinline__ uint32_t leave_particle(const RunDev& R, uint32_t pid
         return kNoCell;
     }
     const Words u = rng_words(R, pid, step, 2u);
+    // an ion neutralised at a wall comes back at T_refl; atoms and the gas
+    // reinjected at the inlet at T0
+    const float sig = Q >= 1 ? R.sig_refl : R.sig0;
     if (kind == 4) {
         X = R.inlet_X; Y = R.inlet_Y; Z = R.inlet_Z;
         emit(R.sig0, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, u, vx, vy, vz);
@@ -361,17 +423,17 @@ __device__ __forceinline__ uint32_t leave_particle(const RunDev& R, uint32_t pid
         X = (int32_t)rint(cxd * sc / sxy);
         Y = (int32_t)rint(cyd * sc / sxy);
         Z = (int32_t)(long long)rint(czd / szd - 2147483648.0);
-        emit(R.sig0, -ux, -uy, 0.f, -uy, ux, 0.f, 0.f, 0.f, 1.f, u, vx, vy, vz);
+        emit(sig, -ux, -uy, 0.f, -uy, ux, 0.f, 0.f, 0.f, 1.f, u, vx, vy, vz);
     } else if (kind == 2) {
         X = (int32_t)rint(cxd / sxy);
         Y = (int32_t)rint(cyd / sxy);
         Z = (int32_t)(long long)rint(R.eps_wall_d / szd - 2147483648.0);
-        emit(R.sig0, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, u, vx, vy, vz);
+        emit(sig, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, u, vx, vy, vz);
     } else {
         X = (int32_t)rint(cxd / sxy);
         Y = (int32_t)rint(cyd / sxy);
         Z = (int32_t)(long long)rint((R.L_d - R.eps_wall_d) / szd - 2147483648.0);
-        emit(R.sig0, 0.f, 0.f, -1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, u, vx, vy, vz);
+        emit(sig, 0.f, 0.f, -1.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, u, vx, vy, vz);
     }
     meta = status | ev;   // Q = 0: the particle comes back as an atom
     return ngp_cell(R, X, Y, Z);
@@ -558,7 +620,7 @@ __device__ __forceinline__ void list_leavers(const RunDev& R, bool leave, uint32
 // into the other stage; results leave through bulk stores.  The particles are
 // kept sorted by (ion/atom, cell), so each thread takes slots tid, tid + 256,
 // ... straight from the stage and the warps stay on one branch.
-template <bool kBatch, class Src>
+template <bool kBatch, bool kVar, class Src>
 __device__ __forceinline__ void step_tiles(StepShared& S, const Src& src)
 {
     const int tid = threadIdx.x;
@@ -613,7 +675,7 @@ __device__ __forceinline__ void step_tiles(StepShared& S, const Src& src)
                 float vx = sf(st.vx, k), vy = sf(st.vy, k), vz = sf(st.vz, k);
                 const uint32_t id = su(st.id, k);
                 uint32_t ck, dc;
-                const bool leave = step_particle(R, id, step, x, y, z, vx, vy, vz, meta, ck, dc);
+                const bool leave = step_particle<kVar>(R, id, step, x, y, z, vx, vy, vz, meta, ck, dc);
                 deposit_warp(R, dc, meta & kQMask);
                 list_leavers(R, leave, t * kTile + k);
                 if (k < nslot) {
@@ -660,20 +722,22 @@ __device__ __forceinline__ void step_tiles(StepShared& S, const Src& src)
     }
 }
 
+template <bool kVar>
 __global__ void __launch_bounds__(kThreads, kStepMinBlocks) k_step(const __grid_constant__ RunDev R, uint32_t ntiles)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     StepShared& S = *reinterpret_cast<StepShared*>(smem_raw);
-    step_tiles<false>(S, SingleRun{R, ntiles});
+    step_tiles<false, kVar>(S, SingleRun{R, ntiles});
 }
 
 // batch form: one persistent launch over the tiles of many runs
+template <bool kVar>
 __global__ void __launch_bounds__(kThreads, kStepMinBlocks) k_step_batch(const RunDev* __restrict__ runs,
                                                             const uint2* __restrict__ items, uint32_t nitems)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     StepShared& S = *reinterpret_cast<StepShared*>(smem_raw);
-    step_tiles<true>(S, BatchRuns{runs, items, nitems});
+    step_tiles<true, kVar>(S, BatchRuns{runs, items, nitems});
 }
 
 // The leaver pass of one run: finish the step of every listed particle, add
@@ -853,29 +917,42 @@ cudaError_t launch_load_init(const LoadCheck& lc, float* const soa[6], const uin
 int step_blocks_per_sm()
 {
     const int smem = (int)sizeof(StepShared);
-    if (cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step, kThreads, smem) != cudaSuccess || b < 1) b = 1;
-    return b;
+    if (cudaFuncSetAttribute(k_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return 1;
+    int b = 0, bv = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<false>, kThreads, smem) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bv, k_step<true>, kThreads, smem) != cudaSuccess || bv < 1)
+        bv = 1;
+    return b < bv ? b : bv;
 }
 
 constexpr size_t kBatchSmem = sizeof(StepShared);
 
 int step_batch_blocks_per_sm()
 {
-    if (cudaFuncSetAttribute(k_step_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_step_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_step_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) !=
+            cudaSuccess)
         return 1;
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_batch, kThreads, kBatchSmem) != cudaSuccess || b < 1)
+    int b = 0, bv = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_batch<false>, kThreads, kBatchSmem) != cudaSuccess ||
+        b < 1)
         b = 1;
-    return b;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bv, k_step_batch<true>, kThreads, kBatchSmem) != cudaSuccess ||
+        bv < 1)
+        bv = 1;
+    return b < bv ? b : bv;
 }
 
-cudaError_t launch_step_batch(const RunDev* runs, const uint2* items, uint32_t nitems, int grid, cudaStream_t s)
+cudaError_t launch_step_batch(const RunDev* runs, const uint2* items, uint32_t nitems, int grid, bool variants,
+                              cudaStream_t s)
 {
     if (nitems > 0) {
         if (grid > (int)nitems) grid = (int)nitems;
-        k_step_batch<<<grid, kThreads, kBatchSmem, s>>>(runs, items, nitems);
+        if (variants) k_step_batch<true><<<grid, kThreads, kBatchSmem, s>>>(runs, items, nitems);
+        else k_step_batch<false><<<grid, kThreads, kBatchSmem, s>>>(runs, items, nitems);
     }
     return cudaGetLastError();
 }
@@ -890,7 +967,8 @@ cudaError_t launch_step(const RunDev& R, uint32_t ntiles, int grid, cudaStream_t
 {
     if (ntiles == 0) return cudaSuccess;
     if (grid > (int)ntiles) grid = (int)ntiles;
-    k_step<<<grid, kThreads, sizeof(StepShared), s>>>(R, ntiles);
+    if (R.flags & kFVariants) k_step<true><<<grid, kThreads, sizeof(StepShared), s>>>(R, ntiles);
+    else k_step<false><<<grid, kThreads, sizeof(StepShared), s>>>(R, ntiles);
     return cudaGetLastError();
 }
 

@@ -37,6 +37,9 @@ F_CX = 1 << 2
 F_EIKICK = 1 << 3
 F_COULOMB = 1 << 4
 F_RECYCLE = 1 << 5
+F_ISOHEAT = 1 << 6   # heating kick without the drift bias (delta = 0)
+F_DOUBLE = 1 << 7    # double ionisation Q -> Q+2
+F_ELASTIC = 1 << 8   # elastic ion-atom scattering
 F_ALL_NO_COULOMB = F_PUSH | F_IONIZE | F_CX | F_EIKICK | F_RECYCLE
 F_ALL = F_ALL_NO_COULOMB | F_COULOMB
 
@@ -121,6 +124,12 @@ class RunParams:
     lnL_ii: float = 10.0
     lnL_ei: float = 17.0
     ei_charge_power: int = 2
+    # opt-in processes: re-emission temperature of ions neutralised at a wall
+    # (0: T0), synthetic elastic ion-atom cross section of Q = 1 (cm^2),
+    # double-ionisation rate factor
+    T_refl_eV: float = 0.0
+    sigma_el1_cm2: float = 4e-15
+    k2_factor: float = 0.1
     flags: int = F_ALL_NO_COULOMB
     # macroparticle weight and RNG key
     weight: float = 1e8

@@ -16,7 +16,7 @@ import numpy as np
 from oracle import oracle as O
 
 KEYS = ("x", "y", "z", "vx", "vy", "vz")
-EV_MASK = 0x1F  # wall, extract, ionise, cx, coulomb
+EV_MASK = 0x3F  # wall, extract, ionise, cx, coulomb, elastic
 
 
 class Mismatch(AssertionError):
