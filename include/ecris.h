@@ -111,6 +111,15 @@ typedef struct {
     double B_inj, B_min, B_ext; /* T; B_inj > B_min >= 0, B_ext > B_min */
     double B_hex;               /* hexapole field at r = R0, T */
     double B_ecr;               /* resonance field, T (0.5 T at 14 GHz) */
+    /* Optional on-axis table replacing the synthetic mirror (a computed
+     * solenoid map, the flat or middle-coil profiles of Sec. IV): B0 at
+     * n_axial points z_k = k L / (n_axial - 1), host memory, copied.  The
+     * library takes the natural cubic spline through the samples for B0, B0'
+     * and B0'' and extends it off axis as above.  n_axial = 0: the mirror
+     * (B_inj, B_min, B_ext are then required); otherwise 4 <= n_axial <= 65537
+     * finite samples >= 0. */
+    int32_t n_axial;
+    const double* B_axial;
 } ecris_bfield;
 
 /* Mesh and electron background (Sec. II: 3-D Cartesian mesh; warm electrons

@@ -87,6 +87,9 @@ typedef struct {
     double T_refl_eV;                /* re-emission temperature of ions neutralised at a wall (0: T0) */
     double sigma_el_m2;              /* elastic ion-atom cross section of Q = 1 (scaled by Q) */
     double k2_factor;                /* double-ionisation rate factor */
+    int32_t ax_n;                    /* on-axis B0 table: samples at z_k = k L/(ax_n - 1); 0: mirror */
+    const double *ax_y;              /* B0(z_k), T */
+    const double *ax_M;              /* the natural cubic spline's B0''(z_k) (or_axial_setup) */
 } or_params;
 
 typedef struct {
@@ -155,8 +158,52 @@ double or_zmin(const or_params *p)
     return p->L / (1.0 + ratio);
 }
 
+/* Natural cubic spline through n samples y_k at z_k = k h (h = L/(n-1)):
+ * its second derivatives M_k solve M_0 = M_{n-1} = 0 and
+ * M_{k-1} + 4 M_k + M_{k+1} = 6 (y_{k+1} - 2 y_k + y_{k-1}) / h^2, by
+ * forward elimination and back substitution (Thomas algorithm). */
+void or_axial_setup(int32_t n, double L, const double *y, double *M)
+{
+    double h = L / (n - 1);
+    double *c = (double *)malloc((size_t)n * sizeof(double));
+    double *d = (double *)malloc((size_t)n * sizeof(double));
+    M[0] = 0.0;
+    M[n - 1] = 0.0;
+    /* unknowns M_1 .. M_{n-2}: diagonal 4, off-diagonals 1 */
+    for (int k = 1; k <= n - 2; ++k) {
+        double rhs = 6.0 * (y[k + 1] - 2.0 * y[k] + y[k - 1]) / (h * h);
+        double diag = 4.0 - (k > 1 ? c[k - 1] : 0.0);
+        c[k] = 1.0 / diag;
+        d[k] = (rhs - (k > 1 ? d[k - 1] : 0.0)) / diag;
+    }
+    for (int k = n - 2; k >= 1; --k) M[k] = d[k] - c[k] * (k < n - 2 ? M[k + 1] : 0.0);
+    free(c);
+    free(d);
+}
+
+/* B0, B0', B0'' of the spline on the segment holding z (clamped to the ends):
+ * with t = (z - z_k)/h, B0 = (1-t) y_k + t y_{k+1} + h^2/6 [((1-t)^3 - (1-t)) M_k
+ * + (t^3 - t) M_{k+1}] and its derivatives in z. */
+static void or_b0_axial(const or_params *p, double z, double out[3])
+{
+    int n = p->ax_n;
+    double h = p->L / (n - 1);
+    int k = (int)floor(z / h);
+    if (k < 0) k = 0;
+    if (k > n - 2) k = n - 2;
+    double t = (z - k * h) / h, u = 1.0 - t;
+    const double *y = p->ax_y, *M = p->ax_M;
+    out[0] = u * y[k] + t * y[k + 1] + h * h / 6.0 * ((u * u * u - u) * M[k] + (t * t * t - t) * M[k + 1]);
+    out[1] = (y[k + 1] - y[k]) / h + h / 6.0 * (-(3.0 * u * u - 1.0) * M[k] + (3.0 * t * t - 1.0) * M[k + 1]);
+    out[2] = u * M[k] + t * M[k + 1];
+}
+
 void or_b0(const or_params *p, double z, double out[3])
 {
+    if (p->ax_n > 0) {
+        or_b0_axial(p, z, out);
+        return;
+    }
     double zm = or_zmin(p);
     if (z <= zm) {
         double a = 0.5 * (p->B_inj - p->B_min), k = OR_PI / zm;

@@ -60,6 +60,7 @@ class Params(ctypes.Structure):
         ("ei_charge_power", ctypes.c_int32), ("flags", ctypes.c_uint32),
         ("weight", ctypes.c_double), ("seed", ctypes.c_uint64), ("dt", ctypes.c_double),
         ("T_refl_eV", ctypes.c_double), ("sigma_el_m2", ctypes.c_double), ("k2_factor", ctypes.c_double),
+        ("ax_n", ctypes.c_int32), ("ax_y", ctypes.c_void_p), ("ax_M", ctypes.c_void_p),
     ]
 
 
@@ -93,6 +94,7 @@ def lib():
         _lib.or_lotz_rate.restype = d
         _lib.or_build_rates.argtypes = [pp, p, p, p]
         _lib.or_build_rates2.argtypes = [pp, p, p, p]
+        _lib.or_axial_setup.argtypes = [ctypes.c_int32, d, p, p]
         _lib.or_setup_cells.argtypes = [pp, p, d, d, p, p, p, p, p]
         _lib.or_cell_delta.argtypes = [pp, p, p, p, p, p]
         _lib.or_boris.argtypes = [d, p, p, d, p]
@@ -144,6 +146,13 @@ def make_params(rp, dt=None) -> Params:
     p.T_refl_eV = rp.T_refl_eV
     p.sigma_el_m2 = rp.sigma_el1_cm2 * 1e-4
     p.k2_factor = rp.k2_factor
+    if rp.B_axial is not None:
+        # on-axis table: the spline's second derivatives, kept alive with p
+        y = np.ascontiguousarray(rp.B_axial, dtype=np.float64)
+        M = np.zeros_like(y)
+        lib().or_axial_setup(len(y), rp.L, _ptr(y), _ptr(M))
+        p.ax_n, p.ax_y, p.ax_M = len(y), y.ctypes.data, M.ctypes.data
+        p._keep = (y, M)
     return p
 
 

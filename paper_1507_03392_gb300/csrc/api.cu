@@ -102,13 +102,48 @@ struct HostRun {
     double zm;
     bool has_e = false;            // some cell of the E grid is nonzero
     std::vector<double> bmag;      // |B| at the cell centres (T)
+    std::vector<double> ax_y, ax_M;   // on-axis table and its spline's second derivatives (empty: mirror)
     std::vector<unsigned long long> charge_mark;   // time-summed charge deposit at the last n_e update
     uint64_t steps_mark = 0;       // steps at the last n_e update (or load)
 };
 
-// synthetic on-axis mirror and its first two derivatives
+// Natural cubic spline through n samples at z_k = k h: second derivatives
+// M_0 = M_{n-1} = 0 and M_{k-1} + 4 M_k + M_{k+1} = 6 (y_{k+1} - 2 y_k +
+// y_{k-1}) / h^2 for the inner points (tridiagonal elimination)
+void axial_spline(const std::vector<double>& y, double L, std::vector<double>& M)
+{
+    const size_t n = y.size();
+    const double h = L / (double)(n - 1);
+    M.assign(n, 0.0);
+    std::vector<double> cp(n, 0.0), dp(n, 0.0);
+    for (size_t k = 1; k + 1 < n; ++k) {
+        const double r = 6.0 * (y[k + 1] - 2.0 * y[k] + y[k - 1]) / (h * h);
+        const double m = 4.0 - cp[k - 1];
+        cp[k] = 1.0 / m;
+        dp[k] = (r - dp[k - 1]) / m;
+    }
+    for (size_t k = n - 2; k >= 1; --k) {
+        M[k] = dp[k] - cp[k] * M[k + 1];
+        if (k == 1) break;
+    }
+}
+
+// on-axis B0 and its first two derivatives: the table's spline, or the
+// synthetic mirror
 void b0_host(const HostRun& h, double z, double& b0, double& b1, double& b2)
 {
+    if (!h.ax_y.empty()) {
+        const size_t n = h.ax_y.size();
+        const double hz = h.geo.L / (double)(n - 1);
+        long k = (long)std::floor(z / hz);
+        k = k < 0 ? 0 : (k > (long)n - 2 ? (long)n - 2 : k);
+        const double t = z / hz - (double)k, u = 1.0 - t;
+        const double y0 = h.ax_y[k], y1 = h.ax_y[k + 1], m0 = h.ax_M[k], m1 = h.ax_M[k + 1];
+        b0 = u * y0 + t * y1 + hz * hz / 6.0 * ((u * u * u - u) * m0 + (t * t * t - t) * m1);
+        b1 = (y1 - y0) / hz + hz / 6.0 * ((3.0 * t * t - 1.0) * m1 - (3.0 * u * u - 1.0) * m0);
+        b2 = u * m0 + t * m1;
+        return;
+    }
     const double bmin = h.bf.B_min;
     if (z <= h.zm) {
         const double a = 0.5 * (h.bf.B_inj - bmin), k = kPi / h.zm;
@@ -245,6 +280,7 @@ struct ecris_ctx {
     float4* d_cell = nullptr;
     float4* d_E = nullptr;
     float* d_kdt = nullptr;
+    float4* d_btab = nullptr;       // on-axis table, one cubic per segment
     float* d_nanbu = nullptr;
 
     bool have_ions = false;     // device buffers allocated
@@ -415,6 +451,7 @@ void free_fields(ecris_ctx* ctx)
     free_async(ctx, ctx->d_cell);
     free_async(ctx, ctx->d_E);
     free_async(ctx, ctx->d_kdt);
+    free_async(ctx, ctx->d_btab);
     free_async(ctx, ctx->d_nanbu);
     free_async(ctx, ctx->d_pslot);
     free_async(ctx, ctx->d_pmom);
@@ -521,6 +558,9 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.cell = ctx->d_cell;
     R.E = ctx->d_E;
     R.kdt = ctx->d_kdt;
+    R.btab = ctx->d_btab;
+    R.nseg = ctx->h.ax_y.empty() ? 0 : (int32_t)ctx->h.ax_y.size() - 1;
+    R.inv_h = ctx->h.ax_y.empty() ? 0.0f : (float)((double)R.nseg / ctx->h.geo.L);
     R.dep = ctx->d_dep;
     R.tally = ctx->d_tally;
     R.plist = ctx->d_plist;
@@ -949,10 +989,18 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
         if (!(ix * ix + iy * iy < geo->R0 * geo->R0) || !(iz > 0.0) || !(iz < geo->L))
             return fail(ctx, ECRIS_EINVAL, "init_fields: gas inlet must lie inside the chamber");
     }
-    if (!(std::isfinite(bf->B_min) && bf->B_min >= 0.0) || !(bf->B_inj > bf->B_min) ||
-        !(bf->B_ext > bf->B_min) || !std::isfinite(bf->B_inj) || !std::isfinite(bf->B_ext) ||
-        !std::isfinite(bf->B_hex) || !std::isfinite(bf->B_ecr))
+    if (bf->n_axial != 0) {
+        if (bf->n_axial < 4 || bf->n_axial > 65537 || !bf->B_axial)
+            return fail(ctx, ECRIS_EINVAL, "init_fields: the axial table needs 4 <= n_axial <= 65537 samples");
+        for (int32_t k = 0; k < bf->n_axial; ++k)
+            if (!(std::isfinite(bf->B_axial[k]) && bf->B_axial[k] >= 0.0))
+                return fail(ctx, ECRIS_EINVAL, "init_fields: axial sample %d must be finite and >= 0", (int)k);
+    } else if (!(std::isfinite(bf->B_min) && bf->B_min >= 0.0) || !(bf->B_inj > bf->B_min) ||
+               !(bf->B_ext > bf->B_min) || !std::isfinite(bf->B_inj) || !std::isfinite(bf->B_ext)) {
         return fail(ctx, ECRIS_EINVAL, "init_fields: need B_inj > B_min >= 0 and B_ext > B_min");
+    }
+    if (!std::isfinite(bf->B_hex) || !std::isfinite(bf->B_ecr))
+        return fail(ctx, ECRIS_EINVAL, "init_fields: B_hex and B_ecr must be finite");
     if (grid->nx < 2 || grid->ny < 2 || grid->nz < 2 ||
         (double)grid->nx * grid->ny * grid->nz > 4.0e8)
         return fail(ctx, ECRIS_EINVAL, "init_fields: mesh sizes must be >= 2 and Nc <= 4e8");
@@ -993,7 +1041,17 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
     h.ip.assign(sp->ip_eV, sp->ip_eV + sp->qmax);
     h.nout.assign(sp->n_outer, sp->n_outer + sp->qmax);
     h.mcc = *mcc;
-    h.zm = geo->L / (1.0 + std::sqrt((bf->B_ext - bf->B_min) / (bf->B_inj - bf->B_min)));
+    h.ax_y.clear();
+    h.ax_M.clear();
+    if (bf->n_axial) {
+        h.ax_y.assign(bf->B_axial, bf->B_axial + bf->n_axial);
+        axial_spline(h.ax_y, geo->L, h.ax_M);
+        h.bf.n_axial = 0;          // the copy above owns the samples
+        h.bf.B_axial = nullptr;
+        h.zm = 0.5 * geo->L;       // (mirror constants unused with a table)
+    } else {
+        h.zm = geo->L / (1.0 + std::sqrt((bf->B_ext - bf->B_min) / (bf->B_inj - bf->B_min)));
+    }
     for (int zone = 0; zone < 2; ++zone) {
         h.rate[zone].resize(sp->qmax);
         const double Te = zone ? h.Te_w : h.Te_c;
@@ -1040,6 +1098,22 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
     CK(cudaMallocAsync((void**)&ctx->d_cell, nc * sizeof(float4), ctx->stream));
     CK(cudaMallocAsync((void**)&ctx->d_E, nc * sizeof(float4), ctx->stream));
     CK(cudaMallocAsync((void**)&ctx->d_kdt, 4 * kQSlots * sizeof(float), ctx->stream));
+    // the table's cubics in t per segment, from the FP64 spline:
+    // a = y_k, b = y_{k+1} - y_k - h^2 (2 M_k + M_{k+1})/6, c = h^2 M_k/2,
+    // d = h^2 (M_{k+1} - M_k)/6
+    std::vector<float4> btab;
+    if (!h.ax_y.empty()) {
+        const size_t nseg = h.ax_y.size() - 1;
+        const double hz = geo->L / (double)nseg;
+        btab.resize(nseg);
+        for (size_t k = 0; k < nseg; ++k) {
+            const double y0 = h.ax_y[k], y1 = h.ax_y[k + 1], m0 = h.ax_M[k], m1 = h.ax_M[k + 1];
+            btab[k] = make_float4((float)y0, (float)(y1 - y0 - hz * hz * (2.0 * m0 + m1) / 6.0),
+                                  (float)(hz * hz * m0 / 2.0), (float)(hz * hz * (m1 - m0) / 6.0));
+        }
+        CK(cudaMallocAsync((void**)&ctx->d_btab, nseg * sizeof(float4), ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d_btab, btab.data(), nseg * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
+    }
     // the same for every run: built once per process
     static const std::vector<float> nanbu = [] {
         std::vector<float> t(kNanbuN);
@@ -1614,7 +1688,7 @@ ecris_status batch_items(ecris_batch* b)
     b->nitems = (uint32_t)items.size();
     b->variants = false;
     for (auto* c : b->runs)
-        if (c && (c->h.mcc.flags & kFVariants)) b->variants = true;
+        if (c && ((c->h.mcc.flags & kFVariants) || !c->h.ax_y.empty())) b->variants = true;
     b->layout_dirty = false;
     b->graph_dirty = true;
     return ECRIS_OK;

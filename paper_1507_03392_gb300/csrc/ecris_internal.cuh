@@ -60,7 +60,8 @@ constexpr uint32_t kFIsoheat = 1u << 6;
 constexpr uint32_t kFDouble = 1u << 7;
 constexpr uint32_t kFElastic = 1u << 8;
 constexpr uint32_t kFlagMask = 0x1FFu;
-// processes whose code only the variant step kernels carry
+// processes whose code only the variant step kernels carry (with the
+// on-axis field table)
 constexpr uint32_t kFVariants = kFDouble | kFElastic;
 constexpr uint32_t kFHasE = 1u << 16;   // internal: the run has a nonzero E grid (the push gathers it)
 
@@ -99,6 +100,11 @@ struct alignas(16) RunDev {
     float zm, inv_zm, inv_zr;    // z_m, 1/z_m, 1/(L-z_m)
     float aLk, aLk2, aRk, aRk2;  // a k and a k^2 of each half (k = pi/z_m, pi/(L-z_m))
     float hex_c;                 // B_hex / R0^2
+    // on-axis table instead of the mirror: per segment k of length h the cubic
+    // B0 = a + t (b + t (c + t d)), t = z/h - k (nullptr: the mirror)
+    const float4 *btab;
+    int32_t nseg;
+    float inv_h;
     float B_ecr;
     // mesh
     int32_t nx, ny, nz;
@@ -224,6 +230,25 @@ __device__ __forceinline__ void bfield(const RunDev& R, float x, float y, float 
         b1 = R.aRk * s;
         b2 = R.aRk2 * c;
     }
+    const float r2 = x * x + y * y;
+    Bx = -0.5f * x * b1 + R.hex_c * (2.0f * x * y);
+    By = -0.5f * y * b1 + R.hex_c * (x * x - y * y);
+    Bz = b0 - 0.25f * r2 * b2;
+}
+
+// the same from the on-axis table: the segment's cubic in t and its
+// derivatives in z
+__device__ __forceinline__ void bfield_table(const RunDev& R, float x, float y, float z,
+                                             float& Bx, float& By, float& Bz)
+{
+    const float u = z * R.inv_h;
+    int k = (int)u;
+    k = k < 0 ? 0 : (k > R.nseg - 1 ? R.nseg - 1 : k);
+    const float t = u - (float)k;
+    const float4 cf = __ldg(R.btab + k);
+    const float b0 = cf.x + t * (cf.y + t * (cf.z + t * cf.w));
+    const float b1 = (cf.y + t * (2.0f * cf.z + 3.0f * t * cf.w)) * R.inv_h;
+    const float b2 = (2.0f * cf.z + 6.0f * t * cf.w) * (R.inv_h * R.inv_h);
     const float r2 = x * x + y * y;
     Bx = -0.5f * x * b1 + R.hex_c * (2.0f * x * y);
     By = -0.5f * y * b1 + R.hex_c * (x * x - y * y);

@@ -43,7 +43,7 @@ using Clock = std::chrono::steady_clock;
 struct OwnedRequest {
     ecris_request r;
     std::vector<float> E, ne_cells, xyzv[6];
-    std::vector<double> ip;
+    std::vector<double> ip, axial;
     std::vector<int32_t> nout;
     std::vector<uint8_t> q;
 };
@@ -382,12 +382,14 @@ ecris_status ecris_server_submit(ecris_server* s, const ecris_request* req, int6
     own(o->E, r.grid.E, 3 * nc);
     own(o->ne_cells, r.grid.ne_in_cells, nc);
     own(o->ip, r.sp.ip_eV, (size_t)r.sp.qmax);
+    own(o->axial, r.bf.B_axial, r.bf.n_axial > 0 ? (size_t)r.bf.n_axial : 0);
     own(o->nout, r.sp.n_outer, (size_t)r.sp.qmax);
     own(o->q, r.q, r.n);
     for (int k = 0; k < 6; ++k) own(o->xyzv[k], r.xyzv[k], r.n);
     o->r.grid.E = r.grid.E ? o->E.data() : nullptr;
     o->r.grid.ne_in_cells = r.grid.ne_in_cells ? o->ne_cells.data() : nullptr;
     o->r.sp.ip_eV = o->ip.data();
+    o->r.bf.B_axial = r.bf.B_axial ? o->axial.data() : nullptr;
     o->r.sp.n_outer = o->nout.data();
     o->r.q = o->q.data();
     for (int k = 0; k < 6; ++k) o->r.xyzv[k] = o->xyzv[k].data();

@@ -201,7 +201,8 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
     if ((R.flags & kFPush) && Q > 0) {
         const float x0 = fx_xy(R, X), y0 = fx_xy(R, Y), z0 = fx_z(R, Z);
         float Bx, By, Bz, Ex, Ey, Ez;
-        bfield(R, x0, y0, z0, Bx, By, Bz);
+        if (kVar && R.btab) bfield_table(R, x0, y0, z0, Bx, By, Bz);
+        else bfield(R, x0, y0, z0, Bx, By, Bz);
         if (R.flags & kFHasE) {
             efield(R, x0, y0, z0, Ex, Ey, Ez);
         } else {
@@ -967,7 +968,7 @@ cudaError_t launch_step(const RunDev& R, uint32_t ntiles, int grid, cudaStream_t
 {
     if (ntiles == 0) return cudaSuccess;
     if (grid > (int)ntiles) grid = (int)ntiles;
-    if (R.flags & kFVariants) k_step<true><<<grid, kThreads, sizeof(StepShared), s>>>(R, ntiles);
+    if ((R.flags & kFVariants) || R.btab) k_step<true><<<grid, kThreads, sizeof(StepShared), s>>>(R, ntiles);
     else k_step<false><<<grid, kThreads, sizeof(StepShared), s>>>(R, ntiles);
     return cudaGetLastError();
 }

@@ -40,7 +40,8 @@ class Geometry(ctypes.Structure):
 
 class BField(ctypes.Structure):
     _fields_ = [("B_inj", ctypes.c_double), ("B_min", ctypes.c_double), ("B_ext", ctypes.c_double),
-                ("B_hex", ctypes.c_double), ("B_ecr", ctypes.c_double)]
+                ("B_hex", ctypes.c_double), ("B_ecr", ctypes.c_double),
+                ("n_axial", ctypes.c_int32), ("B_axial", ctypes.c_void_p)]
 
 
 class Grid(ctypes.Structure):
@@ -301,7 +302,8 @@ def current_stream_handle():
 def field_structs(rp, E=None, ne_cells=None):
     """ecris_init_fields arguments for an inputs.RunParams (plus the arrays they point to)."""
     geo = Geometry(rp.R0, rp.L, rp.r_ap, (ctypes.c_double * 3)(*rp.inlet))
-    bf = BField(rp.B_inj, rp.B_min, rp.B_ext, rp.B_hex, rp.B_ecr)
+    bax = None if rp.B_axial is None else np.ascontiguousarray(rp.B_axial, dtype=np.float64)
+    bf = BField(rp.B_inj, rp.B_min, rp.B_ext, rp.B_hex, rp.B_ecr, 0 if bax is None else len(bax), _ptr(bax))
     Eh = None if E is None else np.ascontiguousarray(E, dtype=np.float32).reshape(-1)
     nh = None if ne_cells is None else np.ascontiguousarray(ne_cells, dtype=np.float32)
     grid = Grid(rp.nx, rp.ny, rp.nz, _ptr(Eh), rp.ne_in_cm3, _ptr(nh), rp.ne_out_cm3,
@@ -312,7 +314,7 @@ def field_structs(rp, E=None, ne_cells=None):
     sp = Species(rp.species.mass_amu, rp.species.qmax, _ptr(ip), _ptr(nout))
     mcc = Mcc(rp.n0_cm3, rp.T0_eV, rp.sigma1_cm2, rp.E_cx_eV, rp.lnL_ii, rp.lnL_ei,
               rp.ei_charge_power, rp.flags, rp.T_refl_eV, rp.sigma_el1_cm2, rp.k2_factor)
-    return geo, bf, grid, sp, mcc, (Eh, nh, ip, nout)
+    return geo, bf, grid, sp, mcc, (Eh, nh, ip, nout, bax)
 
 
 def _state_arrays(state):

@@ -124,6 +124,9 @@ class RunParams:
     lnL_ii: float = 10.0
     lnL_ei: float = 17.0
     ei_charge_power: int = 2
+    # optional on-axis field table: B0 (T) at z_k = k L/(n-1), n >= 4; None:
+    # the synthetic mirror through B_inj, B_min, B_ext
+    B_axial: Optional[tuple] = None
     # opt-in processes: re-emission temperature of ions neutralised at a wall
     # (0: T0), synthetic elastic ion-atom cross section of Q = 1 (cm^2),
     # double-ionisation rate factor
@@ -235,6 +238,21 @@ def served_stream(seed: int = 5, rate_per_s: float = 20.0, duration_s: float = 2
 def _mb_velocities(rng, n, T_eV, mass_amu):
     sigma = math.sqrt(T_eV * E_CHARGE / (mass_amu * AMU))
     return rng.normal(0.0, sigma, size=(3, n))
+
+
+def flat_axial_profile(rp: RunParams, n: int = 513, flat: float = 0.06):
+    """Samples of a synthetic flat on-axis profile (the paper's flat
+    configuration, Sec. IV, Fig. 34): the mirror's two raised-cosine halves
+    moved apart by a plateau of length `flat` at B_min, centred where the
+    plain mirror has its minimum.  B0 at z_k = k L/(n-1) as a tuple."""
+    zm = rp.L / (1.0 + np.sqrt((rp.B_ext - rp.B_min) / (rp.B_inj - rp.B_min)))
+    z1, z2 = zm - 0.5 * flat, zm + 0.5 * flat
+    z = np.linspace(0.0, rp.L, n)
+    b = np.full(n, rp.B_min)
+    lo, hi = z < z1, z > z2
+    b[lo] = rp.B_min + 0.5 * (rp.B_inj - rp.B_min) * (1.0 + np.cos(np.pi * z[lo] / z1))
+    b[hi] = rp.B_min + 0.5 * (rp.B_ext - rp.B_min) * (1.0 - np.cos(np.pi * (z[hi] - z2) / (rp.L - z2)))
+    return tuple(float(v) for v in b)
 
 
 def make_particles(wl: Workload, seed: Optional[int] = None):
