@@ -80,6 +80,9 @@ typedef enum {
                                      the centre-of-mass frame with an atom drawn at
                                      T0; shares its word with charge exchange in
                                      proportion to the cross sections */
+#define ECRIS_F_RECOMB (1u << 9)  /* radiative recombination Q -> Q-1 at Seaton's
+                                     hydrogenic rate for charge Q and T_e; shares
+                                     the ionisation word in proportion to the rates */
 
 /* Per-particle state word (ecris_get_state meta): bits 0-7 charge state Q,
  * bits 8-15 events of the last step, bits 16-23 status. */
@@ -90,6 +93,7 @@ typedef enum {
 #define ECRIS_EV_CX (1u << 11)      /* charge exchange this step */
 #define ECRIS_EV_COULOMB (1u << 12) /* took part in a Coulomb collision */
 #define ECRIS_EV_ELASTIC (1u << 13) /* elastic ion-atom scattering this step */
+#define ECRIS_EV_RECOMB (1u << 14)  /* recombined this step */
 #define ECRIS_ST_FROZEN (1u << 16)  /* left the chamber with recycling off */
 
 /* Chamber geometry (Sec. II, Table I shapes). */

@@ -56,6 +56,7 @@
 #define OR_F_ISOHEAT 64u    /* heating kick without the drift bias: delta = 0 */
 #define OR_F_DOUBLE 128u    /* double ionisation Q -> Q+2 beside Q -> Q+1 */
 #define OR_F_ELASTIC 256u   /* elastic ion-atom scattering, isotropic in the CM frame */
+#define OR_F_RECOMB 512u    /* radiative recombination Q -> Q-1 */
 
 /* per-particle event bits of one step */
 #define OR_EV_WALL 1u
@@ -64,6 +65,7 @@
 #define OR_EV_CX 8u
 #define OR_EV_COULOMB 16u
 #define OR_EV_ELASTIC 32u
+#define OR_EV_RECOMB 64u
 
 /* guard bits: outcomes within rounding distance of a decision surface */
 #define OR_G_CELL 1u
@@ -269,12 +271,12 @@ static int64_t or_cell(const or_params *p, double x, double y, double z, uint32_
  * (word w0 against the probability from the other cell's n_e and zone) or,
  * for an ion, the heating kick (the other cell's n_e, zone or delta). */
 static int or_ion_outcome(const or_params *p, double ne_c, int zc, const double *rates, const double *rates2,
-                          int Q, uint32_t w0, int *near);
+                          const double *ratesr, int Q, uint32_t w0, int *near);
 
 static int or_cell_record_guard(const or_params *p, double x, double y, double z, int64_t c,
                                 const double *ne, const int32_t *zone, const double *dlx,
-                                const double *dly, const double *rates, const double *rates2, int q_before,
-                                int q_after, uint32_t w0)
+                                const double *dly, const double *rates, const double *rates2,
+                                const double *ratesr, int q_before, int q_after, uint32_t w0)
 {
     const double tol = 1e-4;
     double g[3] = {(x + p->R0) / or_dx(p), (y + p->R0) / or_dy(p), z / or_dz(p)};
@@ -288,9 +290,9 @@ static int or_cell_record_guard(const or_params *p, double x, double y, double z
         int other = (g[k] - idx[k] < 0.5) ? idx[k] - 1 : idx[k] + 1;
         if (other < 0 || other >= n[k]) continue;
         int64_t c2 = c + (other - idx[k]) * stride[k];
-        if ((p->flags & OR_F_IONIZE) && q_before < p->qmax &&
-            or_ion_outcome(p, ne[c], zone[c], rates, rates2, q_before, w0, NULL) !=
-                or_ion_outcome(p, ne[c2], zone[c2], rates, rates2, q_before, w0, NULL))
+        if ((((p->flags & OR_F_IONIZE) && q_before < p->qmax) || ((p->flags & OR_F_RECOMB) && q_before >= 1)) &&
+            or_ion_outcome(p, ne[c], zone[c], rates, rates2, ratesr, q_before, w0, NULL) !=
+                or_ion_outcome(p, ne[c2], zone[c2], rates, rates2, ratesr, q_before, w0, NULL))
             return 1;
         if ((p->flags & OR_F_EIKICK) && q_after >= 1 &&
             (ne[c2] != ne[c] || zone[c2] != zone[c] || dlx[c2] != dlx[c] || dly[c2] != dly[c]))
@@ -382,14 +384,55 @@ void or_build_rates2(const or_params *p, const double *ip_eV, const int32_t *n_o
     }
 }
 
-/* Outcome of the ionisation word w0 in a cell: 0 none, 1 single, 2 double.
+/* Radiative recombination Q -> Q-1 (Sec. II; the datasets [21] are not
+ * available): Seaton's hydrogenic rate for an ion of charge Z = Q,
+ * alpha = 5.197e-14 Z lambda^1/2 (0.4288 + 0.5 ln lambda + 0.469 lambda^-1/3)
+ * cm^3/s with lambda = 157890 Z^2 / T(K), T = T_e.  ratesr[zone*(qmax+1) + Q],
+ * zero for atoms. */
+double or_recomb_rate(int Z, double Te_eV)
+{
+    double TK = Te_eV * 11604.518;
+    double lam = 157890.0 * Z * Z / TK;
+    return 5.197e-14 * Z * sqrt(lam) * (0.4288 + 0.5 * log(lam) + 0.469 * pow(lam, -1.0 / 3.0)) * 1e-6;
+}
+
+void or_build_rates_rec(const or_params *p, double *ratesr)
+{
+    for (int zone = 0; zone < 2; ++zone) {
+        double Te = zone ? p->Te_warm : p->Te_cold;
+        for (int q = 0; q <= p->qmax; ++q)
+            ratesr[zone * (p->qmax + 1) + q] = q >= 1 ? or_recomb_rate(q, Te) : 0.0;
+    }
+}
+
+/* Outcome of the ionisation word w0 in a cell: 0 none, 1 single, 2 double,
+ * -1 recombination.
  * One step's probability of any ionisation is 1 - exp(-n_e (k1 + k2) dt); it
  * is shared between the two in proportion to k1 and k2, so w0 below the
  * single threshold ionises once and w0 between the two thresholds twice.
  * *near is set when w0 lies within rounding distance of either threshold. */
 static int or_ion_outcome(const or_params *p, double ne_c, int zc, const double *rates, const double *rates2,
-                          int Q, uint32_t w0, int *near)
+                          const double *ratesr, int Q, uint32_t w0, int *near)
 {
+    if (ratesr && (p->flags & OR_F_RECOMB)) {
+        /* single, double and recombination share the word in proportion to
+         * their rates: w0 below p k1/k, then below p (k1+k2)/k, then below p,
+         * with k = k1 + k2 + kr and p = 1 - exp(-n_e k dt) */
+        int ion = (p->flags & OR_F_IONIZE) && Q < p->qmax;
+        double k1 = ion ? rates[zc * p->qmax + Q] : 0.0;
+        double k2 = (ion && rates2 && (p->flags & OR_F_DOUBLE)) ? rates2[zc * p->qmax + Q] : 0.0;
+        double kr = ratesr[zc * (p->qmax + 1) + Q];
+        double k = k1 + k2 + kr;
+        if (k <= 0.0) return 0;
+        double pt = -expm1(-ne_c * k * p->dt);
+        double t = or_threshold(pt), t1 = or_threshold(pt * (k1 / k)), t2 = or_threshold(pt * ((k1 + k2) / k));
+        if (near && (fabs((double)w0 - t) < 1e-5 * t + 2.0 || fabs((double)w0 - t1) < 1e-5 * t1 + 2.0 ||
+                     fabs((double)w0 - t2) < 1e-5 * t2 + 2.0))
+            *near = 1;
+        if ((double)w0 < floor(t1)) return 1;
+        if ((double)w0 < floor(t2)) return 2;
+        return (double)w0 < floor(t) ? -1 : 0;
+    }
     double k1 = rates[zc * p->qmax + Q];
     double k2 = (rates2 && (p->flags & OR_F_DOUBLE)) ? rates2[zc * p->qmax + Q] : 0.0;
     if (k2 <= 0.0) {
@@ -674,7 +717,8 @@ static void or_coulomb(const or_params *p, int64_t n, const int64_t *cell, const
 #define OR_LEAVE_ZL 3
 #define OR_LEAVE_APERTURE 4
 
-void or_step(const or_params *p, const double *rates, const double *rates2, const double *ne, const int32_t *zone,
+void or_step(const or_params *p, const double *rates, const double *rates2, const double *ratesr,
+             const double *ne, const int32_t *zone,
              const double *dlx, const double *dly, const double *E, int64_t n, double *x,
              double *y, double *z, double *vx, double *vy, double *vz, int32_t *q,
              uint32_t *status, uint32_t step, uint8_t *events, uint8_t *guard, or_tally *t,
@@ -768,11 +812,12 @@ void or_step(const or_params *p, const double *rates, const double *rates2, cons
         int Q = q[i];
         /* step-wise ionisation Q -> Q+1, probability 1 - exp(-n_e k_Q(T_e) dt);
          * with double ionisation, Q -> Q+1 or Q+2 (or_ion_outcome) */
-        if ((p->flags & OR_F_IONIZE) && Q < p->qmax) {
+        if (((p->flags & OR_F_IONIZE) && Q < p->qmax) || ((p->flags & OR_F_RECOMB) && Q >= 1)) {
             int near = 0;
-            int up = or_ion_outcome(p, ne_c, zc, rates, rates2, Q, w[0], &near);
+            int up = or_ion_outcome(p, ne_c, zc, rates, rates2, ratesr, Q, w[0], &near);
             if (near) guard[i] |= OR_G_IONIZE;
-            if (up) { Q += up; events[i] |= OR_EV_IONIZE; }
+            if (up > 0) { Q += up; events[i] |= OR_EV_IONIZE; }
+            if (up < 0) { Q -= 1; events[i] |= OR_EV_RECOMB; }
         }
         /* charge exchange with the neutral background: sigma_Q = Q sigma_1,
          * rate n0 sigma_Q v_rel, v_rel^2 = |v|^2 + 8 kT0/(pi M); Q = 2 is
@@ -863,7 +908,7 @@ void or_step(const or_params *p, const double *rates, const double *rates2, cons
                 for (int k = 0; k < 3; ++k) v[k] += D * d[k] / dm;
         }
         if ((guard[i] & OR_G_CELL) &&
-            or_cell_record_guard(p, x1, y1, z1, c, ne, zone, dlx, dly, rates, rates2, q[i], Q, w[0]))
+            or_cell_record_guard(p, x1, y1, z1, c, ne, zone, dlx, dly, rates, rates2, ratesr, q[i], Q, w[0]))
             guard[i] |= OR_G_CELLREC;
         q[i] = Q;
         vx[i] = v[0]; vy[i] = v[1]; vz[i] = v[2];

@@ -19,8 +19,8 @@ SRC = os.path.join(HERE, "ecris_oracle.c")
 LIB = os.path.join(HERE, "libecris_oracle.so")
 
 F_PUSH, F_IONIZE, F_CX, F_EIKICK, F_COULOMB, F_RECYCLE = 1, 2, 4, 8, 16, 32
-F_ISOHEAT, F_DOUBLE, F_ELASTIC = 64, 128, 256
-EV_WALL, EV_EXTRACT, EV_IONIZE, EV_CX, EV_COULOMB, EV_ELASTIC = 1, 2, 4, 8, 16, 32
+F_ISOHEAT, F_DOUBLE, F_ELASTIC, F_RECOMB = 64, 128, 256, 512
+EV_WALL, EV_EXTRACT, EV_IONIZE, EV_CX, EV_COULOMB, EV_ELASTIC, EV_RECOMB = 1, 2, 4, 8, 16, 32, 64
 G_CELL, G_BOUNDARY, G_IONIZE, G_CX, G_CELLREC = 1, 2, 4, 8, 16
 # guards that can change a single-particle outcome (no Coulomb pairing)
 G_SINGLE = G_BOUNDARY | G_IONIZE | G_CX | G_CELLREC
@@ -95,6 +95,9 @@ def lib():
         _lib.or_build_rates.argtypes = [pp, p, p, p]
         _lib.or_build_rates2.argtypes = [pp, p, p, p]
         _lib.or_axial_setup.argtypes = [ctypes.c_int32, d, p, p]
+        _lib.or_build_rates_rec.argtypes = [pp, p]
+        _lib.or_recomb_rate.argtypes = [ctypes.c_int, d]
+        _lib.or_recomb_rate.restype = d
         _lib.or_setup_cells.argtypes = [pp, p, d, d, p, p, p, p, p]
         _lib.or_cell_delta.argtypes = [pp, p, p, p, p, p]
         _lib.or_boris.argtypes = [d, p, p, d, p]
@@ -106,7 +109,7 @@ def lib():
         _lib.or_nanbu_s.argtypes = [d, d, d, d, d, d, d]
         _lib.or_nanbu_s.restype = d
         _lib.or_scatter_pair.argtypes = [p, p, d, d]
-        _lib.or_step.argtypes = [pp, p, p, p, p, p, p, p, i64, p, p, p, p, p, p, p, p, u32, p, p,
+        _lib.or_step.argtypes = [pp, p, p, p, p, p, p, p, p, i64, p, p, p, p, p, p, p, p, u32, p, p,
                                  ctypes.POINTER(Tally), p, p]
     return _lib
 
@@ -262,6 +265,9 @@ class OracleRun:
         self.rates = np.zeros(2 * qmax)
         lib().or_build_rates(ctypes.byref(self.p), _ptr(np.ascontiguousarray(ip, np.float64)),
                              _ptr(np.ascontiguousarray(nout, np.int32)), _ptr(self.rates))
+        self.ratesr = np.zeros(2 * (qmax + 1))
+        if rp.flags & F_RECOMB:
+            lib().or_build_rates_rec(ctypes.byref(self.p), _ptr(self.ratesr))
         self.rates2 = np.zeros(2 * qmax)
         if rp.flags & F_DOUBLE:
             lib().or_build_rates2(ctypes.byref(self.p), _ptr(np.ascontiguousarray(ip, np.float64)),
@@ -308,7 +314,8 @@ class OracleRun:
         acc_g = np.zeros(self.n, dtype=np.uint8)
         for _ in range(nsteps):
             q_before = self.q.copy()
-            lib().or_step(ctypes.byref(self.p), _ptr(self.rates), _ptr(self.rates2), _ptr(self.ne), _ptr(self.zone),
+            lib().or_step(ctypes.byref(self.p), _ptr(self.rates), _ptr(self.rates2), _ptr(self.ratesr),
+                          _ptr(self.ne), _ptr(self.zone),
                           _ptr(self.dlx), _ptr(self.dly), _ptr(self.E), self.n,
                           _ptr(self.x), _ptr(self.y), _ptr(self.z), _ptr(self.vx), _ptr(self.vy),
                           _ptr(self.vz), _ptr(self.q), _ptr(self.status), self.step_index,

@@ -96,6 +96,7 @@ struct HostRun {
     std::vector<int> nout;
     std::vector<double> rate[2];   // m^3/s per Q, zone 0 cold, 1 warm
     std::vector<double> rate2[2];  // double ionisation Q -> Q+2 (m^3/s), same layout
+    std::vector<double> rate_r[2]; // recombination Q -> Q-1 (m^3/s), Q = 0..qmax
     std::vector<float> cell_ne;    // FP32 n_e per cell as the kernels see it (m^-3)
     std::vector<unsigned char> cell_zone;
     ecris_mcc mcc;
@@ -638,15 +639,22 @@ ecris_status upload_dt(ecris_ctx* ctx, double dt)
     // the pinned staging buffers may still feed an earlier copy
     CK(cudaStreamSynchronize(ctx->stream));
     fill_rundev(ctx, dt, *ctx->h_run);
-    // k1 dt, or (k1 + k2) dt with double ionisation, and the single share
-    // k1 / (k1 + k2)
-    const bool dbl = (ctx->h.mcc.flags & kFDouble) != 0;
+    // k dt with k = k1 (+ k2 with double ionisation, + kr with
+    // recombination), and the shares k1 / k and (k1 + k2) / k
+    const uint32_t fl = ctx->h.mcc.flags;
+    const bool dbl = (fl & kFDouble) != 0, rec = (fl & kFRecomb) != 0;
     for (int zone = 0; zone < 2; ++zone)
         for (int q = 0; q < kQSlots; ++q) {
-            const double k1 = q < ctx->h.qmax ? ctx->h.rate[zone][q] : 0.0;
-            const double k2 = (dbl && q < ctx->h.qmax) ? ctx->h.rate2[zone][q] : 0.0;
-            ctx->h_kdt[zone * kQSlots + q] = (float)((k1 + k2) * dt);
-            ctx->h_kdt[2 * kQSlots + zone * kQSlots + q] = k1 + k2 > 0.0 ? (float)(k1 / (k1 + k2)) : 1.0f;
+            // with recombination on the variant kernel reads these for every
+            // ion, so ionisation enters only where it is switched on
+            const bool ion = q < ctx->h.qmax && (!rec || (fl & kFIonize));
+            const double k1 = ion ? ctx->h.rate[zone][q] : 0.0;
+            const double k2 = (dbl && ion) ? ctx->h.rate2[zone][q] : 0.0;
+            const double kr = (rec && q <= ctx->h.qmax) ? ctx->h.rate_r[zone][q] : 0.0;
+            const double k = k1 + k2 + kr;
+            ctx->h_kdt[zone * kQSlots + q] = (float)(k * dt);
+            ctx->h_kdt[2 * kQSlots + zone * kQSlots + q] = k > 0.0 ? (float)(k1 / k) : 1.0f;
+            ctx->h_kdt[4 * kQSlots + zone * kQSlots + q] = k > 0.0 ? (float)((k1 + k2) / k) : 1.0f;
         }
     // the kernels' FP32 product n_e k_0 dt, maximised over the cells, with a
     // relative margin that covers any rounding difference in the probability
@@ -661,7 +669,7 @@ ecris_status upload_dt(ecris_ctx* ctx, double dt)
     const double pmax = -std::expm1(-(double)ctx->h_run->lam0_max);
     const double gate = std::ceil(pmax * 4294967296.0);
     ctx->h_run->atom_gate = gate >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)gate;
-    CK(cudaMemcpyAsync(ctx->d_kdt, ctx->h_kdt, 4 * kQSlots * sizeof(float), cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync(ctx->d_kdt, ctx->h_kdt, 6 * kQSlots * sizeof(float), cudaMemcpyHostToDevice,
                        ctx->stream));
     ctx->dt_loaded = dt;
     ++ctx->param_version;
@@ -943,7 +951,7 @@ ecris_status ecris_create(ecris_ctx** out, int device, void* cuda_stream)
         }
     }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_run, sizeof(RunDev));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_kdt, 4 * kQSlots * sizeof(float));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_kdt, 6 * kQSlots * sizeof(float));
     if (e != cudaSuccess) {
         g_create_error = std::string("ecris_create: ") + cudaGetErrorString(e);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -1062,6 +1070,14 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
         if (mcc->flags & kFDouble)
             for (int q = 0; q + 1 < sp->qmax; ++q)
                 h.rate2[zone][q] = mcc->k2_factor * lotz_rate(h.ip[q] + h.ip[q + 1], h.nout[q], Te);
+        // radiative recombination (the datasets [21] are not available):
+        // Seaton's hydrogenic rate for charge Z = Q, lambda = 157890 Z^2 / T(K)
+        h.rate_r[zone].assign(sp->qmax + 1, 0.0);
+        for (int q = 1; q <= sp->qmax; ++q) {
+            const double lam = 157890.0 * q * q / (Te * 11604.518);
+            h.rate_r[zone][q] = 5.197e-14 * q * std::sqrt(lam) *
+                                (0.4288 + 0.5 * std::log(lam) + 0.469 * std::pow(lam, -1.0 / 3.0)) * 1e-6;
+        }
     }
 
     // per-cell electron data in FP64: zone by |B| at the centre, n_e, delta
@@ -1097,7 +1113,7 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
     }
     CK(cudaMallocAsync((void**)&ctx->d_cell, nc * sizeof(float4), ctx->stream));
     CK(cudaMallocAsync((void**)&ctx->d_E, nc * sizeof(float4), ctx->stream));
-    CK(cudaMallocAsync((void**)&ctx->d_kdt, 4 * kQSlots * sizeof(float), ctx->stream));
+    CK(cudaMallocAsync((void**)&ctx->d_kdt, 6 * kQSlots * sizeof(float), ctx->stream));
     // the table's cubics in t per segment, from the FP64 spline:
     // a = y_k, b = y_{k+1} - y_k - h^2 (2 M_k + M_{k+1})/6, c = h^2 M_k/2,
     // d = h^2 (M_{k+1} - M_k)/6

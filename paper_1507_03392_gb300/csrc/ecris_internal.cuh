@@ -46,6 +46,7 @@ constexpr uint32_t kEvIonize = 1u << 10;
 constexpr uint32_t kEvCx = 1u << 11;
 constexpr uint32_t kEvCoulomb = 1u << 12;
 constexpr uint32_t kEvElastic = 1u << 13;
+constexpr uint32_t kEvRecomb = 1u << 14;
 constexpr uint32_t kStFrozen = 1u << 16;
 constexpr uint32_t kStPad = 1u << 17;   // padding slot, never processed
 
@@ -59,10 +60,11 @@ constexpr uint32_t kFRecycle = 1u << 5;
 constexpr uint32_t kFIsoheat = 1u << 6;
 constexpr uint32_t kFDouble = 1u << 7;
 constexpr uint32_t kFElastic = 1u << 8;
-constexpr uint32_t kFlagMask = 0x1FFu;
+constexpr uint32_t kFRecomb = 1u << 9;
+constexpr uint32_t kFlagMask = 0x3FFu;
 // processes whose code only the variant step kernels carry (with the
 // on-axis field table)
-constexpr uint32_t kFVariants = kFDouble | kFElastic;
+constexpr uint32_t kFVariants = kFDouble | kFElastic | kFRecomb;
 constexpr uint32_t kFHasE = 1u << 16;   // internal: the run has a nonzero E grid (the push gathers it)
 
 constexpr uint32_t kNoCell = 0xFFFFFFFFu;
@@ -136,8 +138,9 @@ struct alignas(16) RunDev {
     uint32_t *id;                // stable particle id (Philox counter word, output order)
     const float4 *cell;          // {n_e (m^-3), zone (0/1), delta_x, delta_y}
     const float4 *E;             // {E_x, E_y, E_z, 0} per cell centre
-    const float *kdt;            // ionisation rate * dt, [zone * 64 + Q] ((k1 + k2) dt with double
-                                 // ionisation), then [2 * 64 + zone * 64 + Q] the single share k1/(k1+k2)
+    const float *kdt;            // [zone * 64 + Q]: k dt with k = k1 (single ionisation) + k2 (double)
+                                 // + kr (recombination) as switched on; then [2 * 64 + ...] the share
+                                 // k1 / k and [4 * 64 + ...] the share (k1 + k2) / k
     unsigned long long *dep;     // packed deposit accumulator: count << 32 | charge
     unsigned long long *tally;   // kTallyWords
     uint4 *plist;                // Coulomb participants of each tile: (slot, cell, id, 0), kTile slots a tile

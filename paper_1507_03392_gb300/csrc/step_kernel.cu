@@ -243,19 +243,28 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
     const bool need = Q > 0 || (ionize && (w.w0 < R.atom_gate || R.atom_gate == 0xFFFFFFFFu));
     if (need && cell != cell_pre) cr = __ldg(R.cell + cell);   // n_e, zone, delta_x, delta_y
     const int zone = cr.y > 0.5f ? 1 : 0;
-    if (ionize && need) {
+    const bool recomb = kVar && (R.flags & kFRecomb) && Q >= 1;
+    if ((ionize && need) || recomb) {
         const float lam = cr.x * __ldg(R.kdt + zone * kQSlots + Q);
         if constexpr (kVar) {
             const float p = event_prob(lam);
             if (fires(w.w0, p)) {
-                // with double ionisation the word below p k1/(k1+k2) removes
-                // one electron, the rest of [0, p) two
-                uint32_t up = 1u;
-                if ((R.flags & kFDouble) && !fires(w.w0, p * __ldg(R.kdt + 2 * kQSlots + zone * kQSlots + Q)))
-                    up = 2u;
-                if (Q == 0) R.birth[pid] = step;   // an ion is born (first-passage clock)
-                Q += up;
-                ev |= kEvIonize;
+                // single, double and recombination share [0, p) in proportion
+                // to their rates: below p k1/k one electron goes, below
+                // p (k1+k2)/k two, above that one is captured
+                int up = 1;
+                if (R.flags & (kFDouble | kFRecomb)) {
+                    if (!fires(w.w0, p * __ldg(R.kdt + 2 * kQSlots + zone * kQSlots + Q)))
+                        up = fires(w.w0, p * __ldg(R.kdt + 4 * kQSlots + zone * kQSlots + Q)) ? 2 : -1;
+                }
+                if (up > 0) {
+                    if (Q == 0) R.birth[pid] = step;   // an ion is born (first-passage clock)
+                    Q += (uint32_t)up;
+                    ev |= kEvIonize;
+                } else {
+                    Q -= 1u;
+                    ev |= kEvRecomb;
+                }
             }
         } else if (fires(w.w0, event_prob(lam))) {
             if (Q == 0) R.birth[pid] = step;   // an ion is born (first-passage clock)

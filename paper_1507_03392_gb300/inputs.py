@@ -40,6 +40,7 @@ F_RECYCLE = 1 << 5
 F_ISOHEAT = 1 << 6   # heating kick without the drift bias (delta = 0)
 F_DOUBLE = 1 << 7    # double ionisation Q -> Q+2
 F_ELASTIC = 1 << 8   # elastic ion-atom scattering
+F_RECOMB = 1 << 9    # radiative recombination Q -> Q-1
 F_ALL_NO_COULOMB = F_PUSH | F_IONIZE | F_CX | F_EIKICK | F_RECYCLE
 F_ALL = F_ALL_NO_COULOMB | F_COULOMB
 

@@ -1,7 +1,7 @@
 """GPU parity of the opt-in processes and variants (Sec. II collision block;
 Secs. III.C, IV) through the C ABI: double ionisation, elastic ion-atom
-scattering, warm reflected atoms and isotropic heating, in lock-step with
-the oracle, and a batch run against the same run alone."""
+scattering, recombination, warm reflected atoms and isotropic heating, in
+lock-step with the oracle, and a batch run against the same run alone."""
 import dataclasses
 
 import numpy as np
@@ -24,7 +24,7 @@ def E():
 
 def _variant_case(seed=4):
     rp, st, Ef = G.busy_case(seed=seed)
-    rp = dataclasses.replace(rp, flags=rp.flags | I.F_DOUBLE | I.F_ELASTIC, T_refl_eV=0.15, k2_factor=0.5,
+    rp = dataclasses.replace(rp, flags=rp.flags | I.F_DOUBLE | I.F_ELASTIC | I.F_RECOMB, T_refl_eV=0.15, k2_factor=0.5,
                              sigma_el1_cm2=2e-14)
     return rp, st, Ef
 
@@ -52,6 +52,23 @@ def test_lockstep_double_elastic_warm_reflection(E):
         doubles += int(((g1["q"].astype(np.int64) - g0["q"]) >= 2).sum())
     wall, ext, ion, cx, _, el = seen
     assert wall > 50 and ion > 15 and cx > 5 and el > 50 and doubles > 0, (seen, doubles)
+    run.close()
+
+
+def test_lockstep_recombination(E):
+    # ions at rest in cold, dense electrons: recombination competes with
+    # ionisation for the same word
+    rp = V._uniform_params(flags=I.F_RECOMB | I.F_IONIZE, Te_warm_eV=8.0, Te_cold_eV=8.0, ne_in_cm3=1e14,
+                           ne_out_cm3=1e14, dt=3e-5)
+    st = V._static(4001, 6, rp)
+    st32 = {k: np.asarray(v, np.float32) for k, v in st.items() if k != "q"}
+    st32["q"] = st["q"].astype(np.uint8)
+    run = E.Run(rp)
+    run.load(st32)
+    t, orc = P.lockstep(run, rp, st32, 12)
+    assert t["q"] == 0 and t["events"] == 0 and t["pos"] == 0 and t["vel"] == 0, t["first_bad"]
+    g = run.state()
+    assert (g["q"] < 6).sum() > 500 and (g["q"] > 6).sum() > 0
     run.close()
 
 
@@ -123,6 +140,6 @@ def test_invalid_variant_parameters(E):
     rp = dataclasses.replace(G.busy_case()[0], T_refl_eV=float("nan"))
     with pytest.raises(E.EcrisError):
         E.Run(rp)
-    rp = dataclasses.replace(G.busy_case()[0], flags=1 << 9)
+    rp = dataclasses.replace(G.busy_case()[0], flags=1 << 10)
     with pytest.raises(E.EcrisError):
         E.Run(rp)

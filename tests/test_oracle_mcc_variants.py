@@ -176,3 +176,59 @@ def test_isotropic_heating_drops_delta():
                      deposit=False)
     c = O.ngp_cells(rp, st["x"][:1], st["y"][:1], st["z"][:1])[0]
     assert r2.dlx[c] > 0
+
+
+def test_recombination_rate_anchor_and_scaling():
+    # Seaton's hydrogenic radiative-recombination rate: hydrogen at 1e4 K
+    # has the textbook case-A coefficient 4.18e-13 cm^3/s (Seaton's
+    # approximation lies within 2 % of it); the rate scales as
+    # alpha(Z, T) = Z alpha(1, T / Z^2)
+    lib = O.lib()
+    a_h = lib.or_recomb_rate(1, 1e4 / 11604.518) * 1e6
+    assert a_h == pytest.approx(4.18e-13, rel=0.03)
+    for Z in (2, 5, 8, 18):
+        for T in (5.0, 300.0, 3000.0):
+            assert lib.or_recomb_rate(Z, T) == pytest.approx(Z * lib.or_recomb_rate(1, T / Z ** 2), rel=1e-12)
+    # recombination is slow next to ionisation in the warm zone, faster in the cold periphery
+    assert lib.or_recomb_rate(8, 1000.0) < lib.or_recomb_rate(8, 5.0)
+
+
+def test_recombination_markov_chain():
+    # ions at rest in cold, dense electrons: only Q -> Q-1, with per-step
+    # probability 1 - exp(-n_e alpha_Q dt)
+    rp = _uniform_params(flags=I.F_RECOMB, Te_warm_eV=5.0, Te_cold_eV=5.0, ne_in_cm3=1e14, ne_out_cm3=1e14,
+                         dt=5e-5)
+    n, S, q0 = 30000, 40, 8
+    r = O.OracleRun(rp, _static(n, q0, rp), deposit=False)
+    lib = O.lib()
+    T = np.eye(q0 + 1)
+    for q in range(1, q0 + 1):
+        pr = 1 - math.exp(-1e20 * lib.or_recomb_rate(q, 5.0) * rp.dt)
+        T[q, q], T[q, q - 1] = 1 - pr, pr
+    r.step(S)
+    got = np.bincount(r.q, minlength=q0 + 1)[: q0 + 1] / n
+    want = np.linalg.matrix_power(T, S)[q0]
+    sig = np.sqrt(want * (1 - want) / n) + 1e-12
+    assert np.all(np.abs(got - want) < 5 * sig + 1e-4)
+    assert want[q0] < 0.7          # the chain moved
+    ev = (r.events & O.EV_RECOMB) != 0
+    assert ev.sum() > 0
+
+
+def test_recombination_and_ionisation_share_the_word():
+    # both on: per step any change with p = 1 - exp(-n_e (k1 + kr) dt), up
+    # with p k1/(k1+kr), down with p kr/(k1+kr)
+    rp = _uniform_params(flags=I.F_RECOMB | I.F_IONIZE, Te_warm_eV=40.0, Te_cold_eV=40.0, ne_in_cm3=1e14,
+                         ne_out_cm3=1e14, dt=2e-6)
+    n, q0 = 60000, 3
+    r = O.OracleRun(rp, _static(n, q0, rp), deposit=False)
+    lib = O.lib()
+    ip, nout = rp.species.ladder()
+    k1 = closed_form(ip[q0], nout[q0], 40.0)
+    kr = lib.or_recomb_rate(q0, 40.0)
+    r.step(1)
+    pt = 1 - math.exp(-1e20 * (k1 + kr) * rp.dt)
+    for qq, frac in ((q0 + 1, k1 / (k1 + kr)), (q0 - 1, kr / (k1 + kr))):
+        k = int((r.q == qq).sum())
+        pr = pt * frac
+        assert abs(k - n * pr) < 5 * math.sqrt(n * pr * (1 - pr)) + 1
