@@ -455,6 +455,9 @@ typedef struct {
     double power_W;
     double ke_lost_eV;
     char error[128];
+    double flow_per_s;      /* gas flow over the last window: particles (ions and
+                               atoms) out through the aperture per second, times w */
+    double power_window_W;  /* power losses (as power_W) over the last window */
 } ecris_result;
 
 /* Start a server on `device`: memory budget for resident runs (0: none),
@@ -476,6 +479,47 @@ ecris_status ecris_server_poll(ecris_server* s, int64_t ticket, ecris_result* ou
  * run has advanced one tick past the boundary its result belongs to. */
 ecris_status ecris_server_stats(ecris_server* s, double* now, int64_t* queued, int64_t* running, int64_t* done,
                                 double* ion_steps);
+
+/* Calibration as a served workload (Sec. II: for a given field the model
+ * needs two inputs, the macroparticle weight w and the warm-electron
+ * temperature T_ew, which are adjusted until the converged plasma's two
+ * outputs, the gas flow out of the chamber and the coupled power, meet
+ * targets).  A job serves a sequence of runs of `base`, each with the current
+ * (w, T_ew) and stepped to convergence (or max_steps) like a request; from
+ * the flow F and power P of its last window, with targets Ft and Pt, the
+ * next inputs are
+ *     w' = w Ft / F,   T_ew' = T_ew (Pt / Ft) / (P / F)
+ * (each changed by at most a factor of 4), until both outputs are within
+ * tol of the targets or max_iter runs were served.  The first run uses
+ * base.weight and base.grid.Te_warm_eV.  At fixed T_ew both outputs are
+ * proportional to w; T_ew sets the energy carried out per particle. */
+#define ECRIS_CALIB_HISTORY 32
+typedef struct {
+    ecris_request base;
+    double flow_target;     /* particles per second through the aperture */
+    double power_target_W;
+    double tol;             /* relative, > 0 */
+    int32_t max_iter;       /* 1 .. ECRIS_CALIB_HISTORY */
+} ecris_calib_request;
+
+typedef struct {
+    int32_t state;          /* ECRIS_REQ_*: done when met or after max_iter runs */
+    int32_t met;            /* 1: the last run met both targets within tol */
+    int32_t iterations;     /* runs finished */
+    double weight[ECRIS_CALIB_HISTORY];      /* inputs of run k */
+    double Te_warm_eV[ECRIS_CALIB_HISTORY];
+    double flow_per_s[ECRIS_CALIB_HISTORY];  /* outputs of run k (last window) */
+    double power_W[ECRIS_CALIB_HISTORY];
+    uint64_t steps[ECRIS_CALIB_HISTORY];
+    char error[128];
+} ecris_calib_result;
+
+/* Queue a calibration job (thread-safe; everything is copied); *job receives
+ * its handle.  ECRIS_EINVAL for targets <= 0, tol <= 0, max_iter out of
+ * range, or a base request ecris_server_submit would reject. */
+ecris_status ecris_server_calibrate(ecris_server* s, const ecris_calib_request* req, int64_t* job);
+/* State and history of a calibration job (thread-safe). */
+ecris_status ecris_server_calib_poll(ecris_server* s, int64_t job, ecris_calib_result* out);
 
 /* Allocation-free Coulomb collision step.  The paper has no counterpart: this
  * is an interface for callers that cannot allocate device memory when they

@@ -19,6 +19,11 @@
 // counters at its own window boundaries, and a run in a batch evolves exactly
 // as it does alone, the result of a request does not depend on what else is
 // being served.
+//
+// Calibration jobs ride on the same loop: a job is a sequence of requests of
+// one base run with the weight and warm-electron temperature it adjusts; when
+// one of its runs retires, the loop records the run's last-window flow and
+// power and queues the next run, until both meet their targets.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -48,18 +53,32 @@ struct OwnedRequest {
     std::vector<uint8_t> q;
 };
 
+struct CalibJob;
+
 struct Served {
     int64_t ticket = 0;
+    CalibJob* job = nullptr;         // the calibration job this run belongs to, if any
     std::unique_ptr<OwnedRequest> req;
     ecris_result res;
     int32_t run = -1;
     std::vector<int64_t> last_ext;   // extracted counts at the previous window boundary
     std::vector<double> last_cur;    // currents of the previous window
+    double last_energy_J = 0.0;      // energy carried out up to the previous window boundary
     bool have_prev = false;
     uint64_t issued = 0;             // steps enqueued for the run
     uint64_t snap_steps = 0;         // steps at its latest snapshot
     ecris::TallySnapshot* snap = nullptr;   // pinned
     cudaEvent_t ev = nullptr;        // the snapshot has landed
+};
+
+// a calibration job: its base request (owned), targets and history
+struct CalibJob {
+    int64_t id = 0;
+    std::unique_ptr<OwnedRequest> base;
+    double flow_target = 0.0, power_target = 0.0, tol = 0.0;
+    int32_t max_iter = 1;
+    double w = 0.0, Te = 0.0;        // inputs of the run in flight
+    ecris_calib_result res;
 };
 
 }  // namespace
@@ -78,7 +97,9 @@ struct ecris_server {
     std::deque<Served*> queue;
     std::vector<Served*> active;
     std::map<int64_t, std::unique_ptr<Served>> all;
+    std::map<int64_t, std::unique_ptr<CalibJob>> calibs;
     int64_t next_ticket = 1;
+    int64_t next_job = 1;
     int64_t n_done = 0;
     double ion_steps = 0.0;
     std::thread loop;
@@ -167,6 +188,12 @@ bool converged(Served* v, const std::vector<int64_t>& ext, ecris_result& res)
         cur[q] = q * 1.602176634e-19 * r.weight * (double)dn / window_s;
     }
     for (int q = 0; q < q1 && q < 64; ++q) res.current_A[q] = cur[q];
+    // gas flow and power losses over the window (the power from the
+    // cumulative energy carried out, power_W times the run's time)
+    res.flow_per_s = r.weight * (double)events / window_s;
+    const double energy = res.power_W * (double)res.steps * r.dt;
+    res.power_window_W = (energy - v->last_energy_J) / window_s;
+    v->last_energy_J = energy;
     bool ok = false;
     if (v->have_prev && events >= r.min_events) {
         // relative change against the larger of the two (two zero currents agree)
@@ -186,6 +213,66 @@ bool converged(Served* v, const std::vector<int64_t>& ext, ecris_result& res)
     v->last_cur = cur;
     v->have_prev = true;
     return ok;
+}
+
+// a run of a calibration job: the base request with weight w and warm
+// electron temperature Te, pointing into the job's owned arrays
+std::unique_ptr<Served> calib_run(ecris_server* s, CalibJob* j)
+{
+    auto v = std::make_unique<Served>();
+    auto o = std::make_unique<OwnedRequest>();
+    o->r = j->base->r;
+    o->r.weight = j->w;
+    o->r.grid.Te_warm_eV = j->Te;
+    v->req = std::move(o);
+    v->job = j;
+    std::memset(&v->res, 0, sizeof v->res);
+    v->res.state = ECRIS_REQ_QUEUED;
+    v->ticket = s->next_ticket++;
+    v->res.t_submit = now_s(s);
+    return v;
+}
+
+// a calibration run retired (s->mu held): record it and queue the next one,
+// or finish the job
+void calib_advance(ecris_server* s, Served* v, bool ok)
+{
+    CalibJob* j = v->job;
+    ecris_calib_result& jr = j->res;
+    if (!ok) {
+        jr.state = ECRIS_REQ_FAILED;
+        std::strncpy(jr.error, v->res.error, sizeof jr.error - 1);
+        return;
+    }
+    const int k = jr.iterations;
+    jr.weight[k] = j->w;
+    jr.Te_warm_eV[k] = j->Te;
+    jr.flow_per_s[k] = v->res.flow_per_s;
+    jr.power_W[k] = v->res.power_window_W;
+    jr.steps[k] = v->res.steps;
+    jr.iterations = k + 1;
+    const double F = v->res.flow_per_s, P = v->res.power_window_W;
+    const bool met = F > 0.0 && P > 0.0 && std::abs(F / j->flow_target - 1.0) <= j->tol &&
+                     std::abs(P / j->power_target - 1.0) <= j->tol;
+    if (met || jr.iterations >= j->max_iter) {
+        jr.met = met ? 1 : 0;
+        jr.state = ECRIS_REQ_DONE;
+        return;
+    }
+    // next inputs: flow and power scale with w; T_ew sets the energy per
+    // particle carried out; each moves by at most a factor of 4
+    auto clamp4 = [](double f) { return f < 0.25 ? 0.25 : (f > 4.0 ? 4.0 : f); };
+    if (F > 0.0 && P > 0.0) {
+        j->w *= clamp4(j->flow_target / F);
+        j->Te *= clamp4((j->power_target / j->flow_target) / (P / F));
+    } else {
+        j->w *= 4.0;   // nothing left through the aperture in the window: more particles
+    }
+    auto n = calib_run(s, j);
+    Served* raw = n.get();
+    s->all[raw->ticket] = std::move(n);
+    s->queue.push_back(raw);
+    s->cv.notify_one();
 }
 
 void serve_loop(ecris_server* s)
@@ -227,6 +314,7 @@ void serve_loop(ecris_server* s)
             if (st != ECRIS_OK) {
                 give_slot(s, v);
                 finish(s, v, ECRIS_REQ_FAILED, ecris_batch_last_error(s->batch));
+                if (v->job) calib_advance(s, v, false);
                 ++s->n_done;
                 continue;
             }
@@ -240,7 +328,10 @@ void serve_loop(ecris_server* s)
             if (ecris_batch_step(s->batch, s->steps_per_tick) != ECRIS_OK) {
                 std::lock_guard<std::mutex> lock(s->mu);
                 s->err = ecris_batch_last_error(s->batch);
-                for (Served* v : s->active) finish(s, v, ECRIS_REQ_FAILED, s->err.c_str());
+                for (Served* v : s->active) {
+                    finish(s, v, ECRIS_REQ_FAILED, s->err.c_str());
+                    if (v->job) calib_advance(s, v, false);
+                }
                 s->n_done += (int64_t)s->active.size();
                 s->active.clear();
                 waiting.clear();
@@ -294,6 +385,7 @@ void serve_loop(ecris_server* s)
             give_slot(s, v);
             std::lock_guard<std::mutex> lock(s->mu);
             finish(s, v, rv.second, rv.second == ECRIS_REQ_DONE ? nullptr : "device error word set (bounded wait ran out)");
+            if (v->job) calib_advance(s, v, rv.second == ECRIS_REQ_DONE);
             v->req.reset();   // the host copy of the inputs is no longer needed
             s->active.erase(std::find(s->active.begin(), s->active.end(), v));
             ++s->n_done;
@@ -307,6 +399,51 @@ void own(std::vector<T>& dst, const T* src, size_t n)
 {
     if (src) dst.assign(src, src + n);
     else dst.clear();
+}
+
+// the checks of ecris_server_submit
+ecris_status check_request(const ecris_server* s, const ecris_request& r, const char** why)
+{
+    if (r.window_steps == 0 || r.window_steps % s->steps_per_tick != 0 || r.max_steps == 0 ||
+        r.max_steps % r.window_steps != 0 || !(r.dt > 0.0) || !(r.rel_tol > 0.0) || r.sp.qmax < 1 ||
+        r.sp.qmax > 63 || r.grid.nx < 2 || r.grid.ny < 2 || r.grid.nz < 2) {
+        *why = "server_submit: need window_steps a multiple of steps_per_tick, max_steps a multiple of "
+               "window_steps, dt > 0, rel_tol > 0 and a valid species and mesh";
+        return ECRIS_EINVAL;
+    }
+    if (r.n && (!r.q || !r.xyzv[0] || !r.xyzv[1] || !r.xyzv[2] || !r.xyzv[3] || !r.xyzv[4] || !r.xyzv[5])) {
+        *why = "server_submit: NULL particle array";
+        return ECRIS_EINVAL;
+    }
+    const size_t need = ecris_run_bytes(r.n, r.grid.nx, r.grid.ny, r.grid.nz, (r.mcc.flags & ECRIS_F_COULOMB) != 0);
+    if (s->budget && need > s->budget) {
+        *why = "server_submit: the run alone exceeds the memory budget";
+        return ECRIS_ENOMEM;
+    }
+    return ECRIS_OK;
+}
+
+// a copy of the request with every array owned
+std::unique_ptr<OwnedRequest> own_request(const ecris_request& r)
+{
+    auto o = std::make_unique<OwnedRequest>();
+    o->r = r;
+    const size_t nc = (size_t)r.grid.nx * r.grid.ny * r.grid.nz;
+    own(o->E, r.grid.E, 3 * nc);
+    own(o->ne_cells, r.grid.ne_in_cells, nc);
+    own(o->ip, r.sp.ip_eV, (size_t)r.sp.qmax);
+    own(o->axial, r.bf.B_axial, r.bf.n_axial > 0 ? (size_t)r.bf.n_axial : 0);
+    own(o->nout, r.sp.n_outer, (size_t)r.sp.qmax);
+    own(o->q, r.q, r.n);
+    for (int k = 0; k < 6; ++k) own(o->xyzv[k], r.xyzv[k], r.n);
+    o->r.grid.E = r.grid.E ? o->E.data() : nullptr;
+    o->r.grid.ne_in_cells = r.grid.ne_in_cells ? o->ne_cells.data() : nullptr;
+    o->r.sp.ip_eV = o->ip.data();
+    o->r.bf.B_axial = r.bf.B_axial ? o->axial.data() : nullptr;
+    o->r.sp.n_outer = o->nout.data();
+    o->r.q = o->q.data();
+    for (int k = 0; k < 6; ++k) o->r.xyzv[k] = o->xyzv[k].data();
+    return o;
 }
 
 }  // namespace
@@ -365,34 +502,11 @@ ecris_status ecris_server_submit(ecris_server* s, const ecris_request* req, int6
         return st;
     };
     if (!req || !ticket) return fail(ECRIS_EINVAL, "server_submit: NULL argument");
-    const ecris_request& r = *req;
-    if (r.window_steps == 0 || r.window_steps % s->steps_per_tick != 0 || r.max_steps == 0 ||
-        r.max_steps % r.window_steps != 0 || !(r.dt > 0.0) || !(r.rel_tol > 0.0) || r.sp.qmax < 1 ||
-        r.sp.qmax > 63 || r.grid.nx < 2 || r.grid.ny < 2 || r.grid.nz < 2)
-        return fail(ECRIS_EINVAL, "server_submit: need window_steps a multiple of steps_per_tick, max_steps a "
-                                  "multiple of window_steps, dt > 0, rel_tol > 0 and a valid species and mesh");
-    if (r.n && (!r.q || !r.xyzv[0] || !r.xyzv[1] || !r.xyzv[2] || !r.xyzv[3] || !r.xyzv[4] || !r.xyzv[5]))
-        return fail(ECRIS_EINVAL, "server_submit: NULL particle array");
-    const size_t need = ecris_run_bytes(r.n, r.grid.nx, r.grid.ny, r.grid.nz, (r.mcc.flags & ECRIS_F_COULOMB) != 0);
-    if (s->budget && need > s->budget) return fail(ECRIS_ENOMEM, "server_submit: the run alone exceeds the memory budget");
+    const char* why = nullptr;
+    const ecris_status cst = check_request(s, *req, &why);
+    if (cst != ECRIS_OK) return fail(cst, why);
     auto v = std::make_unique<Served>();
-    auto o = std::make_unique<OwnedRequest>();
-    o->r = r;
-    const size_t nc = (size_t)r.grid.nx * r.grid.ny * r.grid.nz;
-    own(o->E, r.grid.E, 3 * nc);
-    own(o->ne_cells, r.grid.ne_in_cells, nc);
-    own(o->ip, r.sp.ip_eV, (size_t)r.sp.qmax);
-    own(o->axial, r.bf.B_axial, r.bf.n_axial > 0 ? (size_t)r.bf.n_axial : 0);
-    own(o->nout, r.sp.n_outer, (size_t)r.sp.qmax);
-    own(o->q, r.q, r.n);
-    for (int k = 0; k < 6; ++k) own(o->xyzv[k], r.xyzv[k], r.n);
-    o->r.grid.E = r.grid.E ? o->E.data() : nullptr;
-    o->r.grid.ne_in_cells = r.grid.ne_in_cells ? o->ne_cells.data() : nullptr;
-    o->r.sp.ip_eV = o->ip.data();
-    o->r.bf.B_axial = r.bf.B_axial ? o->axial.data() : nullptr;
-    o->r.sp.n_outer = o->nout.data();
-    o->r.q = o->q.data();
-    for (int k = 0; k < 6; ++k) o->r.xyzv[k] = o->xyzv[k].data();
+    auto o = own_request(*req);
     v->req = std::move(o);
     std::memset(&v->res, 0, sizeof v->res);
     v->res.state = ECRIS_REQ_QUEUED;
@@ -429,6 +543,57 @@ ecris_status ecris_server_stats(ecris_server* s, double* now, int64_t* queued, i
     if (running) *running = (int64_t)s->active.size();
     if (done) *done = s->n_done;
     if (ion_steps) *ion_steps = s->ion_steps;
+    return ECRIS_OK;
+}
+
+ecris_status ecris_server_calibrate(ecris_server* s, const ecris_calib_request* req, int64_t* job)
+{
+    if (!s) return ECRIS_EINVAL;
+    auto fail = [s](ecris_status st, const char* msg) {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->err = msg;
+        return st;
+    };
+    if (!req || !job) return fail(ECRIS_EINVAL, "server_calibrate: NULL argument");
+    if (!(req->flow_target > 0.0) || !(req->power_target_W > 0.0) || !(req->tol > 0.0) ||
+        !std::isfinite(req->flow_target) || !std::isfinite(req->power_target_W) || req->max_iter < 1 ||
+        req->max_iter > ECRIS_CALIB_HISTORY || !(req->base.weight > 0.0) || !(req->base.grid.Te_warm_eV > 0.0))
+        return fail(ECRIS_EINVAL, "server_calibrate: need targets > 0, tol > 0, 1 <= max_iter <= "
+                                  "ECRIS_CALIB_HISTORY, weight > 0 and T_ew > 0");
+    const char* why = nullptr;
+    const ecris_status cst = check_request(s, req->base, &why);
+    if (cst != ECRIS_OK) return fail(cst, why);
+    auto j = std::make_unique<CalibJob>();
+    j->base = own_request(req->base);
+    j->flow_target = req->flow_target;
+    j->power_target = req->power_target_W;
+    j->tol = req->tol;
+    j->max_iter = req->max_iter;
+    j->w = req->base.weight;
+    j->Te = req->base.grid.Te_warm_eV;
+    std::memset(&j->res, 0, sizeof j->res);
+    j->res.state = ECRIS_REQ_RUNNING;
+    std::lock_guard<std::mutex> lock(s->mu);
+    j->id = s->next_job++;
+    *job = j->id;
+    auto v = calib_run(s, j.get());
+    s->queue.push_back(v.get());
+    s->all[v->ticket] = std::move(v);
+    s->calibs[j->id] = std::move(j);
+    s->cv.notify_all();
+    return ECRIS_OK;
+}
+
+ecris_status ecris_server_calib_poll(ecris_server* s, int64_t job, ecris_calib_result* out)
+{
+    if (!s || !out) return ECRIS_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->calibs.find(job);
+    if (it == s->calibs.end()) {
+        s->err = "server_calib_poll: unknown job";
+        return ECRIS_EINVAL;
+    }
+    *out = it->second->res;
     return ECRIS_OK;
 }
 

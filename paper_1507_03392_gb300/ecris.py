@@ -91,10 +91,24 @@ class Result(ctypes.Structure):
                 ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
                 ("qmax", ctypes.c_int32), ("extracted", ctypes.c_int64 * 64), ("lost", ctypes.c_int64 * 64),
                 ("current_A", ctypes.c_double * 64), ("power_W", ctypes.c_double),
-                ("ke_lost_eV", ctypes.c_double), ("error", ctypes.c_char * 128)]
+                ("ke_lost_eV", ctypes.c_double), ("error", ctypes.c_char * 128),
+                ("flow_per_s", ctypes.c_double), ("power_window_W", ctypes.c_double)]
 
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+CALIB_HISTORY = 32   # ECRIS_CALIB_HISTORY
+
+
+class CalibRequest(ctypes.Structure):
+    _fields_ = [("base", Request), ("flow_target", ctypes.c_double), ("power_target_W", ctypes.c_double),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32)]
+
+
+class CalibResult(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("met", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("weight", ctypes.c_double * CALIB_HISTORY), ("Te_warm_eV", ctypes.c_double * CALIB_HISTORY),
+                ("flow_per_s", ctypes.c_double * CALIB_HISTORY), ("power_W", ctypes.c_double * CALIB_HISTORY),
+                ("steps", ctypes.c_uint64 * CALIB_HISTORY), ("error", ctypes.c_char * 128)]
 
 
 MAX_SCREENS = 4   # ECRIS_MAX_SCREENS
@@ -220,6 +234,10 @@ def _load():
     i64 = ctypes.POINTER(ctypes.c_int64)
     lib.ecris_server_stats.argtypes = [P, d, i64, i64, i64, d]
     lib.ecris_server_stats.restype = st
+    lib.ecris_server_calibrate.argtypes = [P, ctypes.POINTER(CalibRequest), i64]
+    lib.ecris_server_calibrate.restype = st
+    lib.ecris_server_calib_poll.argtypes = [P, ctypes.c_int64, ctypes.POINTER(CalibResult)]
+    lib.ecris_server_calib_poll.restype = st
     return lib
 
 
@@ -271,6 +289,8 @@ ecris_server_last_error = LIB.ecris_server_last_error
 ecris_server_submit = LIB.ecris_server_submit
 ecris_server_poll = LIB.ecris_server_poll
 ecris_server_stats = LIB.ecris_server_stats
+ecris_server_calibrate = LIB.ecris_server_calibrate
+ecris_server_calib_poll = LIB.ecris_server_calib_poll
 
 
 def check(ctx, status):
@@ -479,8 +499,8 @@ class Server:
         except Exception:
             pass
 
-    def submit(self, rp, state, E=None, ne_cells=None, window_steps=256, rel_tol=0.02, min_events=400,
-               max_steps=4096, weight=None, seed=None, dt=None):
+    def _request(self, rp, state, E, ne_cells, window_steps, rel_tol, min_events, max_steps, weight, seed, dt):
+        """ecris_request for rp and state, with the arrays it points to."""
         f = field_structs(rp, E, ne_cells)
         arrs, q, dev = _state_arrays(state)
         if dev:
@@ -495,6 +515,39 @@ class Server:
         r.seed = rp.seed if seed is None else seed
         r.dt = rp.dt if dt is None else dt
         r.window_steps, r.rel_tol, r.min_events, r.max_steps = window_steps, rel_tol, min_events, max_steps
+        return r, (f, arrs, q)
+
+    def calibrate(self, rp, state, flow_target, power_target_W, tol=0.1, max_iter=8, E=None, ne_cells=None,
+                  window_steps=256, rel_tol=0.02, min_events=400, max_steps=4096, weight=None, seed=None, dt=None):
+        """Queue a calibration job (ecris_server_calibrate): runs of rp with
+        the weight and rp.Te_warm_eV adjusted until the last window's flow and
+        power meet the targets within tol.  Returns the job handle."""
+        r, keep = self._request(rp, state, E, ne_cells, window_steps, rel_tol, min_events, max_steps, weight, seed,
+                                dt)
+        c = CalibRequest()
+        c.base = r
+        c.flow_target, c.power_target_W, c.tol, c.max_iter = flow_target, power_target_W, tol, max_iter
+        j = ctypes.c_int64(0)
+        st = ecris_server_calibrate(self.s, ctypes.byref(c), ctypes.byref(j))
+        if st != ECRIS_OK:
+            raise EcrisError(st, ecris_server_last_error(self.s).decode())
+        return j.value
+
+    def calib_poll(self, job):
+        res = CalibResult()
+        st = ecris_server_calib_poll(self.s, int(job), ctypes.byref(res))
+        if st != ECRIS_OK:
+            raise EcrisError(st, ecris_server_last_error(self.s).decode())
+        k = res.iterations
+        return {"state": res.state, "met": bool(res.met), "iterations": k,
+                "weight": np.array(res.weight[:k]), "Te_warm_eV": np.array(res.Te_warm_eV[:k]),
+                "flow_per_s": np.array(res.flow_per_s[:k]), "power_W": np.array(res.power_W[:k]),
+                "steps": np.array(res.steps[:k]), "error": res.error.decode()}
+
+    def submit(self, rp, state, E=None, ne_cells=None, window_steps=256, rel_tol=0.02, min_events=400,
+               max_steps=4096, weight=None, seed=None, dt=None):
+        r, keep = self._request(rp, state, E, ne_cells, window_steps, rel_tol, min_events, max_steps, weight, seed,
+                                dt)
         t = ctypes.c_int64(0)
         st = ecris_server_submit(self.s, ctypes.byref(r), ctypes.byref(t))
         if st != ECRIS_OK:
@@ -511,7 +564,8 @@ class Server:
                 "t_submit": res.t_submit, "t_admit": res.t_admit, "t_done": res.t_done,
                 "extracted": np.array(res.extracted[:q1]), "lost": np.array(res.lost[:q1]),
                 "current_A": np.array(res.current_A[:q1]), "power_W": res.power_W,
-                "ke_lost_eV": res.ke_lost_eV, "error": res.error.decode()}
+                "ke_lost_eV": res.ke_lost_eV, "error": res.error.decode(), "flow_per_s": res.flow_per_s,
+                "power_window_W": res.power_window_W}
 
     def stats(self):
         now = ctypes.c_double()
