@@ -142,25 +142,39 @@ def make_workload(rank, n=None):
 
 
 def cpu_baseline(wl, target_s=12.0, sample=200_000):
-    """The oracle as it stands, on the host cores, over a bounded sample."""
+    """The oracle as it stands, on the host cores, over a bounded sample: the
+    benchmark workload on all cores and on one, and the small plain run."""
     ncores = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
     from oracle import oracle as O
     from paper_1507_03392_gb300 import inputs as I
-    st = I.make_particles(wl)
-    m = min(sample, wl.n)
-    sub = {k: v[:m] for k, v in st.items()}
-    orc = O.OracleRun(wl.params, sub, ne_cells=I.make_ne_cells(wl))
-    t0 = time.perf_counter()
-    orc.step(1)
-    one = time.perf_counter() - t0
-    steps = max(1, min(200, int(target_s / max(one, 1e-6))))
-    t0 = time.perf_counter()
-    orc.step(steps)
-    el = time.perf_counter() - t0
-    return {"value": m * steps / el, "unit": "ion-steps/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
-            "kind": "oracle",
-            "sample": f"first {m} of the {wl.n} particles of the workload, {steps} steps, FP64 C oracle"}
+
+    def timed(w, m, budget_s):
+        st = I.make_particles(w)
+        m = min(m, w.n)
+        sub = {k: v[:m] for k, v in st.items()}
+        orc = O.OracleRun(w.params, sub, ne_cells=I.make_ne_cells(w))
+        t0 = time.perf_counter()
+        orc.step(1)
+        one = time.perf_counter() - t0
+        steps = max(1, min(200, int(budget_s / max(one, 1e-6))))
+        t0 = time.perf_counter()
+        orc.step(steps)
+        return m, steps, m * steps / (time.perf_counter() - t0)
+
+    cores = O.lib().or_set_threads(int(os.environ["OMP_NUM_THREADS"]))
+    m, steps, value = timed(wl, sample, target_s)
+    O.lib().or_set_threads(1)
+    m1, steps1, value1 = timed(wl, sample // 4, target_s / 3)
+    small = I.config_small()
+    ms, steps_s, value_s = timed(small, small.n, target_s / 3)
+    O.lib().or_set_threads(cores)
+    return {"value": value, "unit": "ion-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {m} of the {wl.n} particles of the workload, {steps} steps, FP64 C oracle",
+            "one_core": {"value": value1, "cores": 1,
+                         "sample": f"first {m1} of the {wl.n} particles, {steps1} steps"},
+            "small_run": {"value": value_s, "cores": 1, "workload": small.name,
+                          "sample": f"all {ms} particles, {steps_s} steps"}}
 
 
 def run_reference(args, rank, world):

@@ -36,6 +36,9 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -512,6 +515,19 @@ void or_cell_delta(const or_params *p, const double *ne, const int32_t *zone, co
                 dlx[c] = -RL / n0 * sx;
                 dly[c] = -RL / n0 * sy;
             }
+}
+
+/* Threads of the particle loop (the timed CPU baseline runs on all cores and
+ * on one); returns the count in effect. */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------------ */

@@ -96,6 +96,8 @@ def lib():
         _lib.or_build_rates2.argtypes = [pp, p, p, p]
         _lib.or_axial_setup.argtypes = [ctypes.c_int32, d, p, p]
         _lib.or_build_rates_rec.argtypes = [pp, p]
+        _lib.or_set_threads.argtypes = [ctypes.c_int]
+        _lib.or_set_threads.restype = ctypes.c_int
         _lib.or_recomb_rate.argtypes = [ctypes.c_int, d]
         _lib.or_recomb_rate.restype = d
         _lib.or_setup_cells.argtypes = [pp, p, d, d, p, p, p, p, p]

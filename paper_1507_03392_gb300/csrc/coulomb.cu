@@ -94,12 +94,20 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ R
     const uint32_t base = tile * kScanBlock + threadIdx.x * kScanPerThread;
     uint32_t v[kScanPerThread];
     uint32_t sum = 0;
+    // four counts per load where the group lies inside the mesh
 #pragma unroll
-    for (int j = 0; j < kScanPerThread; ++j) {
+    for (int j = 0; j < kScanPerThread; j += 4) {
         const uint32_t idx = base + j;
-        v[j] = idx < ncells ? R.ccount[idx] : 0u;
-        sum += v[j];
+        if (idx + 3u < ncells) {
+            const uint4 c4 = *reinterpret_cast<const uint4*>(R.ccount + idx);
+            v[j] = c4.x; v[j + 1] = c4.y; v[j + 2] = c4.z; v[j + 3] = c4.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[j + k] = idx + k < ncells ? R.ccount[idx + k] : 0u;
+        }
     }
+#pragma unroll
+    for (int j = 0; j < kScanPerThread; ++j) sum += v[j];
     const uint32_t incl = warp_incl_scan(sum);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 31) wsum[warp] = incl;

@@ -81,7 +81,7 @@ constexpr double kNanbuSHi = 6.0;
 
 // scan of the per-cell participant counts: cells per scan tile (one block)
 constexpr int kScanThreads = 256;
-constexpr int kScanPerThread = 8;
+constexpr int kScanPerThread = 8;     // a multiple of 4 (vector loads)
 constexpr int kScanBlock = kScanThreads * kScanPerThread;
 
 // Device parameter block of one run: FP32 constants of the kernels (built in
