@@ -28,7 +28,8 @@
 // n = w m / V_cell for the cell's m ions; A(s) from coth A - 1/A = e^-s
 // (tabulated in FP64 on the host, s >= 1e-3; 1/(1 - e^-s) below, where coth A
 // is 1 to working precision; isotropic for s > 6);
-//   cos chi = 1 + ln(U + (1-U) e^-2A) / A,  eps = 2 pi U';
+//   cos chi = 1 + ln(U + (1-U) e^-2A) / A,  eps = 2 pi U'
+// (the logarithm's argument formed without cancellation in FP32, see collide);
 // the relative velocity g is turned by (chi, eps) and the change is shared
 // equally, which conserves momentum and energy of the pair.
 #include "ecris_internal.cuh"
@@ -237,7 +238,13 @@ __device__ __forceinline__ void collide(const RunDev& R, float4& ra, float4& rb,
         cchi = 2.0f * U - 1.0f;
     } else {
         const float A = nanbu_A(R, s);
-        cchi = 1.0f + log1pf((1.0f - U) * expm1f(-2.0f * A)) / A;
+        // ln(U + (1-U) e^-2A): for small A the sum is close to 1 and log1p of
+        // (1-U)(e^-2A - 1) keeps its precision; for larger A the two positive
+        // terms are formed directly, since e^-2A can lie below the FP32
+        // spacing of expm1 near -1 while U is small as well
+        const float lnarg = A < 0.5f ? log1pf((1.0f - U) * expm1f(-2.0f * A))
+                                     : logf(U + (1.0f - U) * expf(-2.0f * A));
+        cchi = 1.0f + lnarg / A;
         cchi = fminf(fmaxf(cchi, -1.0f), 1.0f);
     }
     const float schi = sqrtf(fmaxf(0.0f, 1.0f - cchi * cchi));
