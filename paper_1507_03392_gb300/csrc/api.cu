@@ -7,6 +7,7 @@
 // closed form of the Maxwellian-averaged single-term Lotz cross section,
 //   k = sqrt(8 e / (pi m_e)) a q E1(P/T) / ((P/T) T^1.5),  a = 4.5e-14 cm^2 eV^2,
 // with E1 from its power series (x <= 1) and continued fraction (x > 1).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -97,7 +98,7 @@ struct HostRun {
     std::vector<double> rate[2];   // m^3/s per Q, zone 0 cold, 1 warm
     std::vector<double> rate2[2];  // double ionisation Q -> Q+2 (m^3/s), same layout
     std::vector<double> rate_r[2]; // recombination Q -> Q-1 (m^3/s), Q = 0..qmax
-    std::vector<float> cell_ne;    // FP32 n_e per cell as the kernels see it (m^-3)
+    float ne_max[2] = {0.f, 0.f};  // largest FP32 n_e (as the kernels see it) of the cold and warm cells
     std::vector<unsigned char> cell_zone;
     ecris_mcc mcc;
     double zm;
@@ -267,6 +268,14 @@ struct KernelTimer {
 
 constexpr uint32_t kSortAfterLoad = 8;   // steps of one ecris_step call that sort a fresh load first
 
+// what a captured step graph bakes in: the parameter block (by value) and
+// the launch shapes
+struct GraphKey {
+    RunDev R;
+    uint32_t ntiles;
+    int step_grid, collide_grid;
+};
+
 struct ecris_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -319,10 +328,12 @@ struct ecris_ctx {
     uint32_t calls_since_load = 0;
     int parity = 0;                // which particle set is current (flips at each sort)
     // captured per-step kernel sequences, by particle set and kind (0: the
-    // whole step, 1: the collision kernels only), valid for param_version
+    // whole step, 1: the collision kernels only), each valid for the launch
+    // arguments it was captured with (a reload into the same buffers with
+    // the same step length keeps them, so a load-step-read cycle does not
+    // re-instantiate its graph)
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-    uint64_t gver[2][2] = {{0, 0}, {0, 0}};
-    uint64_t param_version = 1;
+    GraphKey gkey[2][2];
     uint32_t* d_cslot = nullptr;
     uint32_t* d_sslot = nullptr;
     unsigned long long* d_dep = nullptr;
@@ -601,7 +612,7 @@ void cell_records(HostRun& h, const std::vector<double>& ne, const std::vector<u
     const size_t nc = (size_t)h.nx * h.ny * h.nz;
     const double dx = 2.0 * h.geo.R0 / h.nx;
     cell.assign(nc, make_float4(0.f, 0.f, 0.f, 0.f));
-    h.cell_ne.assign(nc, 0.0f);
+    h.ne_max[0] = h.ne_max[1] = 0.0f;
     h.cell_zone.assign(nc, 0);
     auto NE = [&](int iz, int iy, int ix) {
         iy = iy < 0 ? 0 : (iy >= h.ny ? h.ny - 1 : iy);
@@ -627,7 +638,8 @@ void cell_records(HostRun& h, const std::vector<double>& ne, const std::vector<u
                     dly = -rl * sy;
                 }
                 cell[c] = make_float4((float)ne[c], zone[c] ? 1.0f : 0.0f, (float)dlx, (float)dly);
-                h.cell_ne[c] = (float)ne[c];
+                float& m = h.ne_max[zone[c] ? 1 : 0];
+                if (cell[c].x > m) m = cell[c].x;
                 h.cell_zone[c] = zone[c];
             }
 }
@@ -657,12 +669,10 @@ ecris_status upload_dt(ecris_ctx* ctx, double dt)
             ctx->h_kdt[4 * kQSlots + zone * kQSlots + q] = k > 0.0 ? (float)((k1 + k2) / k) : 1.0f;
         }
     // the kernels' FP32 product n_e k_0 dt, maximised over the cells, with a
-    // relative margin that covers any rounding difference in the probability
-    float lam = 0.0f;
-    for (size_t c = 0; c < ctx->h.cell_ne.size(); ++c) {
-        const float v = ctx->h.cell_ne[c] * ctx->h_kdt[(ctx->h.cell_zone[c] ? 1 : 0) * kQSlots];
-        if (v > lam) lam = v;
-    }
+    // relative margin that covers any rounding difference in the probability.
+    // Rounding to nearest is monotone, so over the cells of one zone the
+    // largest product is the product of the largest n_e
+    const float lam = std::max(ctx->h.ne_max[0] * ctx->h_kdt[0], ctx->h.ne_max[1] * ctx->h_kdt[kQSlots]);
     ctx->h_run->lam0_max = lam * 1.0001f;
     // the same bound as an integer gate on the ionisation word: the kernels'
     // threshold floor(p 2^32) for any cell is at most ceil(p(lam0_max) 2^32)
@@ -672,7 +682,6 @@ ecris_status upload_dt(ecris_ctx* ctx, double dt)
     CK(cudaMemcpyAsync(ctx->d_kdt, ctx->h_kdt, 6 * kQSlots * sizeof(float), cudaMemcpyHostToDevice,
                        ctx->stream));
     ctx->dt_loaded = dt;
-    ++ctx->param_version;
     return ECRIS_OK;
 }
 
@@ -849,7 +858,13 @@ ecris_status get_cells(ecris_ctx* ctx, float* ne, float* delta_x, float* delta_y
 ecris_status step_graph(ecris_ctx* ctx, int kind, cudaGraphExec_t* out)
 {
     const int p = ctx->parity;
-    if (ctx->gexec[p][kind] && ctx->gver[p][kind] == ctx->param_version) {
+    GraphKey key;
+    std::memset(&key, 0, sizeof key);
+    std::memcpy(&key.R, ctx->h_run, sizeof(RunDev));   // the block was zeroed before it was filled
+    key.ntiles = ctx->ntiles;
+    key.step_grid = ctx->step_grid;
+    key.collide_grid = ctx->collide_grid;
+    if (ctx->gexec[p][kind] && std::memcmp(&ctx->gkey[p][kind], &key, sizeof key) == 0) {
         *out = ctx->gexec[p][kind];
         return ECRIS_OK;
     }
@@ -876,7 +891,7 @@ ecris_status step_graph(ecris_ctx* ctx, int kind, cudaGraphExec_t* out)
     cudaGraphDestroy(g);
     CK(e);
     ctx->gexec[p][kind] = x;
-    ctx->gver[p][kind] = ctx->param_version;
+    ctx->gkey[p][kind] = key;
     *out = x;
     return ECRIS_OK;
 }
@@ -1291,7 +1306,6 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
     ctx->since_sort = 0;
     ctx->fresh = true;
     ctx->calls_since_load = 0;
-    ++ctx->param_version;
     // fold the packed deposit before its low word (charge) can carry
     const double per_step = (double)(n ? n : 1) * (h.qmax > 1 ? h.qmax : 1);
     const double k = std::floor(4294967295.0 / per_step);
