@@ -240,7 +240,8 @@ ecris_status ecris_diag(ecris_ctx* ctx, ecris_diag_out* out);
  * move, NGP), and rebuilds each cell's delta from it (the 3x3 stencil and
  * R_L of the heating kick, Sec. II).  The zones (warm / cold electrons) stay
  * as |B| gave them.  Cells without ions get n_e = 0 (no ionisation, no
- * heating).  Synchronises the context's stream.  ECRIS_ESTATE when no step
+ * heating).  Runs on the device in stream order after the queued steps and
+ * returns without waiting (nothing is read back).  ECRIS_ESTATE when no step
  * ran since the load or the previous call; the run is unchanged then. */
 ecris_status ecris_update_ne(ecris_ctx* ctx);
 
@@ -380,8 +381,9 @@ ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps);
 ecris_status ecris_batch_diag(ecris_batch* b, int32_t run, ecris_diag_out* out);
 ecris_status ecris_batch_get_state(ecris_batch* b, int32_t run, float* const xyzv[6], uint32_t* meta,
                                    int dst_is_device);
-/* ecris_update_ne / ecris_get_cells for one run of the batch (ordered after
- * its queued steps; synchronises the batch stream). */
+/* ecris_update_ne / ecris_get_cells for one run of the batch, ordered after
+ * its queued steps on the batch stream (the update does not wait; reading
+ * the cells does). */
 ecris_status ecris_batch_update_ne(ecris_batch* b, int32_t run);
 ecris_status ecris_batch_get_fptd(ecris_batch* b, int32_t run, uint64_t* hist, uint64_t* age_sum);
 ecris_status ecris_batch_get_extraction_radius(ecris_batch* b, int32_t run, double* r_sum);
@@ -439,6 +441,8 @@ typedef struct {
     double rel_tol;
     int64_t min_events;
     uint32_t max_steps;     /* a multiple of window_steps */
+    uint32_t ne_windows;    /* 0: the prescribed n_e throughout; k > 0: self-consistent n_e,
+                               ecris_update_ne after every k windows of the run's steps */
 } ecris_request;
 
 enum { ECRIS_REQ_QUEUED = 0, ECRIS_REQ_RUNNING = 1, ECRIS_REQ_DONE = 2, ECRIS_REQ_FAILED = 3 };

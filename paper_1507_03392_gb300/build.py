@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libecris.so")
-SOURCES = ["api.cu", "step_kernel.cu", "coulomb.cu", "coulomb_noalloc.cu", "sort.cu", "server.cu", "probe.cu"]
+SOURCES = ["api.cu", "step_kernel.cu", "coulomb.cu", "coulomb_noalloc.cu", "sort.cu", "server.cu", "probe.cu",
+           "ne_update.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--cudart", "shared"]
 # The step kernels for one run and for a batch inline the same per-particle
@@ -21,7 +22,9 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--cudart", "s
 # optimiser's choice that may differ between the two kernels) both round
 # every operation the same way, so a run gives identical results alone and in
 # a batch.  Explicit fmaf() calls in that code still compile to FMAs.
-FILE_FLAGS = {"step_kernel.cu": ["-fmad=false"]}
+# The device update of n_e builds the cell records in FP64 as the host does,
+# operation by operation, so it is compiled without contraction too.
+FILE_FLAGS = {"step_kernel.cu": ["-fmad=false"], "ne_update.cu": ["-fmad=false"]}
 
 
 def _nvcc():

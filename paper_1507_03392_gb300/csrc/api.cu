@@ -105,7 +105,6 @@ struct HostRun {
     bool has_e = false;            // some cell of the E grid is nonzero
     std::vector<double> bmag;      // |B| at the cell centres (T)
     std::vector<double> ax_y, ax_M;   // on-axis table and its spline's second derivatives (empty: mirror)
-    std::vector<unsigned long long> charge_mark;   // time-summed charge deposit at the last n_e update
     uint64_t steps_mark = 0;       // steps at the last n_e update (or load)
 };
 
@@ -158,6 +157,28 @@ void b0_host(const HostRun& h, double z, double& b0, double& b1, double& b2)
         b1 = a * k * std::sin(k * (z - h.zm));
         b2 = a * k * k * std::cos(k * (z - h.zm));
     }
+}
+
+uint32_t float_bits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, sizeof u);
+    return u;
+}
+
+// The ionisation word above which no cell can ionise an atom: the kernels'
+// FP32 product n_e k_0 dt, largest over the cells (the largest n_e of each
+// zone times its k_0 dt), with a relative margin of 1e-4 that covers any
+// rounding difference in the probability, as ceil((1 - exp(-lambda)) 2^32);
+// never 0, which the kernels read as "take the device's word"
+uint32_t atom_gate_host(const float ne_max[2], const float* kdt)
+{
+    const float lam = std::max(ne_max[0] * kdt[0], ne_max[1] * kdt[kQSlots]);
+    const float lam_max = lam * 1.0001f;
+    const double pmax = -std::expm1(-(double)lam_max);
+    const double gate = std::ceil(pmax * 4294967296.0);
+    if (gate >= 4294967295.0) return 0xFFFFFFFFu;
+    return gate < 1.0 ? 1u : (uint32_t)gate;
 }
 
 double bmag_host(const HostRun& h, double x, double y, double z)
@@ -288,6 +309,8 @@ struct ecris_ctx {
     bool have_fields = false;
     HostRun h;
     float4* d_cell = nullptr;
+    double* d_rlc = nullptr;        // 2.38e-6 sqrt(T_e)/(B dX) per cell: R_L n_e of the delta stencil
+    bool ne_device = false;         // n_e was updated on the device: the host no longer knows its maxima
     float4* d_E = nullptr;
     float* d_kdt = nullptr;
     float4* d_btab = nullptr;       // on-axis table, one cubic per segment
@@ -339,6 +362,8 @@ struct ecris_ctx {
     unsigned long long* d_dep = nullptr;
     unsigned long long* d_count = nullptr;
     unsigned long long* d_charge = nullptr;
+    unsigned long long* d_mark = nullptr;   // d_charge at the last n_e update (or load)
+    double* d_ne64 = nullptr;               // scratch of the n_e update: FP64 n_e per cell
     unsigned long long* d_tally = nullptr;
     unsigned long long* d_census = nullptr;
     uint32_t* d_step = nullptr;
@@ -433,6 +458,8 @@ void free_ions(ecris_ctx* ctx)
     free_async(ctx, ctx->d_dep);
     free_async(ctx, ctx->d_count);
     free_async(ctx, ctx->d_charge);
+    free_async(ctx, ctx->d_mark);
+    free_async(ctx, ctx->d_ne64);
     free_async(ctx, ctx->d_tally);
     free_async(ctx, ctx->d_census);
     free_async(ctx, ctx->d_step);
@@ -461,6 +488,7 @@ void free_ions(ecris_ctx* ctx)
 void free_fields(ecris_ctx* ctx)
 {
     free_async(ctx, ctx->d_cell);
+    free_async(ctx, ctx->d_rlc);
     free_async(ctx, ctx->d_E);
     free_async(ctx, ctx->d_kdt);
     free_async(ctx, ctx->d_btab);
@@ -668,19 +696,15 @@ ecris_status upload_dt(ecris_ctx* ctx, double dt)
             ctx->h_kdt[2 * kQSlots + zone * kQSlots + q] = k > 0.0 ? (float)(k1 / k) : 1.0f;
             ctx->h_kdt[4 * kQSlots + zone * kQSlots + q] = k > 0.0 ? (float)((k1 + k2) / k) : 1.0f;
         }
-    // the kernels' FP32 product n_e k_0 dt, maximised over the cells, with a
-    // relative margin that covers any rounding difference in the probability.
-    // Rounding to nearest is monotone, so over the cells of one zone the
-    // largest product is the product of the largest n_e
-    const float lam = std::max(ctx->h.ne_max[0] * ctx->h_kdt[0], ctx->h.ne_max[1] * ctx->h_kdt[kQSlots]);
-    ctx->h_run->lam0_max = lam * 1.0001f;
-    // the same bound as an integer gate on the ionisation word: the kernels'
-    // threshold floor(p 2^32) for any cell is at most ceil(p(lam0_max) 2^32)
-    const double pmax = -std::expm1(-(double)ctx->h_run->lam0_max);
-    const double gate = std::ceil(pmax * 4294967296.0);
-    ctx->h_run->atom_gate = gate >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)gate;
     CK(cudaMemcpyAsync(ctx->d_kdt, ctx->h_kdt, 6 * kQSlots * sizeof(float), cudaMemcpyHostToDevice,
                        ctx->stream));
+    // the atom gate on the device, from the new k_0 dt and the largest n_e of
+    // each zone that the device keeps (a device update of n_e changes them),
+    // and by value in the parameter block while the host knows those maxima.
+    // Rounding to nearest is monotone, so over the cells of one zone the
+    // largest FP32 product n_e k_0 dt is the product of the largest n_e
+    CK(launch_atom_gate(ctx->d_kdt, ctx->stream));
+    ctx->h_run->atom_gate = ctx->ne_device ? 0u : atom_gate_host(ctx->h.ne_max, ctx->h_kdt);
     ctx->dt_loaded = dt;
     return ECRIS_OK;
 }
@@ -689,40 +713,30 @@ ecris_status upload_dt(ecris_ctx* ctx, double dt)
 // density, by charge neutrality).  Folds the deposit, takes the charge each
 // cell received since the last update (or the load), time-averages it over
 // the steps in between, n_e = w sum(Q) / (steps V_cell), and rebuilds every
-// cell's {n_e, zone, delta} record from it (Sec. II, the delta stencil and
-// R_L of the heating kick).  The zones stay (they
-// follow |B|).  The parameter block, whose atom gate bounds n_e k_0 dt over
-// the cells, is rebuilt before the next step.
+// cell's {n_e, zone, delta} record and the atom gate from it (Sec. II, the
+// delta stencil and R_L of the heating kick).  The zones stay (they follow
+// |B|).  All of it runs on the device in stream order after the queued
+// steps: nothing is read back and the host does not wait.
 ecris_status update_ne(ecris_ctx* ctx)
 {
     HostRun& h = ctx->h;
     if (ctx->steps_done <= h.steps_mark)
         return fail(ctx, ECRIS_ESTATE, "update_ne: no step since the load or the last update");
-    const size_t nc = (size_t)h.nx * h.ny * h.nz;
-    CK(launch_fold(*ctx->h_run, (uint32_t)nc, ctx->d_count, ctx->d_charge, ctx->stream));
-    ctx->since_fold = 0;
-    std::vector<unsigned long long> charge(nc);
-    uint32_t err = 0;
-    CK(cudaMemcpyAsync(&err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(charge.data(), ctx->d_charge, nc * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    if (err) {
-        ctx->failed = true;
-        return fail(ctx, ECRIS_ETIMEOUT, "update_ne: a kernel's bounded wait for its tile copies ran out; reload");
+    const uint32_t nc = (uint32_t)((size_t)h.nx * h.ny * h.nz);
+    if (ctx->dt_loaded < 0.0) {
+        ecris_status st = upload_dt(ctx, 1e-9);   // parameter block for the fold kernel
+        if (st != ECRIS_OK) return st;
     }
+    CK(launch_fold(*ctx->h_run, nc, ctx->d_count, ctx->d_charge, ctx->stream));
+    ctx->since_fold = 0;
     const double vol = (2.0 * h.geo.R0 / h.nx) * (2.0 * h.geo.R0 / h.ny) * (h.geo.L / h.nz);
     const double steps = (double)(ctx->steps_done - h.steps_mark);
-    std::vector<double> ne(nc);
-    for (size_t c = 0; c < nc; ++c)
-        ne[c] = ctx->weight * (double)(charge[c] - h.charge_mark[c]) / (steps * vol);
-    const std::vector<unsigned char> zone = h.cell_zone;
-    std::vector<float4> cell;
-    cell_records(h, ne, zone, cell);
-    CK(cudaMemcpyAsync(ctx->d_cell, cell.data(), nc * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));   // the host records die at return
-    h.charge_mark.swap(charge);
+    CK(launch_ne_update(ctx->d_charge, ctx->d_mark, ctx->d_ne64, ctx->d_rlc, ctx->d_cell, ctx->d_kdt, h.nx, h.ny,
+                        nc, ctx->weight, steps * vol, (h.mcc.flags & kFIsoheat) != 0, ctx->sm_count, ctx->stream));
     h.steps_mark = ctx->steps_done;
-    ctx->dt_loaded = -1.0;
+    // the gate now lives on the device (k_atom_gate ran with the update)
+    ctx->ne_device = true;
+    ctx->h_run->atom_gate = 0u;
     return ECRIS_OK;
 }
 
@@ -1128,7 +1142,15 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
     }
     CK(cudaMallocAsync((void**)&ctx->d_cell, nc * sizeof(float4), ctx->stream));
     CK(cudaMallocAsync((void**)&ctx->d_E, nc * sizeof(float4), ctx->stream));
-    CK(cudaMallocAsync((void**)&ctx->d_kdt, 6 * kQSlots * sizeof(float), ctx->stream));
+    CK(cudaMallocAsync((void**)&ctx->d_kdt, kKdtWords * sizeof(float), ctx->stream));
+    CK(cudaMallocAsync((void**)&ctx->d_rlc, nc * sizeof(double), ctx->stream));
+    // R_L n_e per cell for the device's rebuild of delta, in the order the
+    // host's records take it: 2.38e-6 sqrt(T_e) / (B dX)
+    std::vector<double> rlc(nc);
+    for (size_t c = 0; c < nc; ++c)
+        rlc[c] = 2.38e-6 * std::sqrt(zone[c] ? h.Te_w : h.Te_c) / (h.bmag[c] * dx);
+    // the gate word (set with the first rate table) and the largest n_e of each zone
+    const uint32_t gate_words[4] = {0xFFFFFFFFu, float_bits(h.ne_max[0]), float_bits(h.ne_max[1]), 0u};
     // the table's cubics in t per segment, from the FP64 spline:
     // a = y_k, b = y_{k+1} - y_k - h^2 (2 M_k + M_{k+1})/6, c = h^2 M_k/2,
     // d = h^2 (M_{k+1} - M_k)/6
@@ -1155,10 +1177,13 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
     CK(cudaMallocAsync((void**)&ctx->d_nanbu, kNanbuN * sizeof(float), ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_nanbu, nanbu.data(), kNanbuN * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_cell, cell.data(), nc * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_rlc, rlc.data(), nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_kdt + kGateWord, gate_words, sizeof gate_words, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_E, E.data(), nc * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
     // the host vectors die at return: wait for the copies
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->have_fields = true;
+    ctx->ne_device = false;
     ctx->failed = false;
     ctx->err.clear();
     return ECRIS_OK;
@@ -1203,6 +1228,8 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         CK(cudaMallocAsync((void**)&ctx->d_dep, nc * sizeof(unsigned long long), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_count, nc * sizeof(unsigned long long), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_charge, nc * sizeof(unsigned long long), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_mark, nc * sizeof(unsigned long long), ctx->stream));
+        CK(cudaMallocAsync((void**)&ctx->d_ne64, nc * sizeof(double), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_tally, kTallyWords * sizeof(unsigned long long), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_census, kQSlots * sizeof(unsigned long long), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_step, sizeof(uint32_t), ctx->stream));
@@ -1248,6 +1275,7 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
     CK(cudaMemsetAsync(ctx->d_dep, 0, nc * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_count, 0, nc * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_charge, 0, nc * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_mark, 0, nc * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_tally, 0, kTallyWords * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->d_birth, 0xFF, ctx->cap * sizeof(uint32_t), ctx->stream));   // births unknown
     CK(cudaMemsetAsync(ctx->d_fptd, 0, kFptdWords * sizeof(unsigned long long), ctx->stream));
@@ -1293,7 +1321,6 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
     ctx->weight = weight;
     ctx->seed = seed;
     ctx->steps_done = 0;
-    ctx->h.charge_mark.assign(nc, 0ull);
     ctx->h.steps_mark = 0;
     ctx->time_s = 0.0;
     ctx->dt_loaded = -1.0;
@@ -1806,8 +1833,9 @@ size_t ecris_run_bytes(size_t n, int32_t nx, int32_t ny, int32_t nz, int coulomb
     // two particle sets with ids, the sort's records, leaver list, births, load bytes, Coulomb lists
     size_t per_p = 2 * 32 + 32 + 4 + 4 + 4 + 1;
     if (coulomb) per_p += 16 + 16 + 8 + 16 + 4 + 4 + 1;
-    // cell records, E, deposit, time sums, sort histogram and scan, Coulomb counts
-    size_t per_c = 16 + 16 + 8 + 8 + 8 + 4 + 4 + (coulomb ? 12 : 0);
+    // cell records, E, deposit, time sums, sort histogram and scan, the n_e
+    // update's mark, scratch and R_L coefficients, Coulomb counts
+    size_t per_c = 16 + 16 + 8 + 8 + 8 + 4 + 4 + 8 + 8 + 8 + (coulomb ? 12 : 0);
     return cap * per_p + nc * per_c + (1u << 20);
 }
 
@@ -2051,12 +2079,17 @@ ecris_status ecris_batch_update_ne(ecris_batch* b, int32_t run)
     BCK(cudaSetDevice(b->device));
     ecris_ctx* c = b->runs[run];
     if (c->failed) return bfail(b, ECRIS_ESTATE, "batch_update_ne: the run failed earlier");
-    // the run's stream is the batch stream: the fold follows the queued steps
+    // the run's stream is the batch stream: the update follows the queued
+    // steps.  Only the first update changes the parameter block (its gate)
+    RunDev before;
+    std::memcpy(&before, c->h_run, sizeof before);
     ecris_status st = update_ne(c);
     if (st == ECRIS_OK) st = upload_dt(c, b->dt[run]);
     if (st != ECRIS_OK) return bfail(b, st, "batch_update_ne: " + c->err);
-    b->params_dirty = true;
-    if (c->h.mcc.flags & kFCoulomb) b->graph_dirty = true;
+    if (std::memcmp(&before, c->h_run, sizeof before) != 0) {
+        b->params_dirty = true;
+        if (c->h.mcc.flags & kFCoulomb) b->graph_dirty = true;
+    }
     return ECRIS_OK;
 }
 

@@ -126,9 +126,9 @@ struct alignas(16) RunDev {
     float ei_coef[2];            // D^2 = ei_coef[zone] * n_e * Q^p (zone 0 cold, 1 warm)
     int32_t ei_pow;
     float ke_scale;              // (M/2) / e * 1e6: micro-eV per (m/s)^2
-    float lam0_max;              // bound (with margin) on n_e k_0 dt over all cells
-    uint32_t atom_gate;          // an atom whose ionisation word is >= atom_gate cannot ionise
-                                 // in any cell (0xFFFFFFFF: no such bound)
+    uint32_t atom_gate;          // an atom whose ionisation word is >= atom_gate cannot ionise in
+                                 // any cell (0xFFFFFFFF: no such bound); 0: read the gate the device
+                                 // keeps after the rate table (set by a device update of n_e)
     float lnl_ii_coef;           // Nanbu s prefactor lnL/(4 pi) (e^2/(eps0 mu))^2 w / V_cell
     uint32_t seed_lo, seed_hi;
     // arrays
@@ -140,7 +140,10 @@ struct alignas(16) RunDev {
     const float4 *E;             // {E_x, E_y, E_z, 0} per cell centre
     const float *kdt;            // [zone * 64 + Q]: k dt with k = k1 (single ionisation) + k2 (double)
                                  // + kr (recombination) as switched on; then [2 * 64 + ...] the share
-                                 // k1 / k and [4 * 64 + ...] the share (k1 + k2) / k
+                                 // k1 / k and [4 * 64 + ...] the share (k1 + k2) / k; then at
+                                 // kGateWord the atom gate (uint32 bits): an atom whose ionisation
+                                 // word is >= the gate cannot ionise in any cell (0xFFFFFFFF: no
+                                 // such bound), and the largest n_e of the cold and warm cells
     unsigned long long *dep;     // packed deposit accumulator: count << 32 | charge
     unsigned long long *tally;   // kTallyWords
     uint4 *plist;                // Coulomb participants of each tile: (slot, cell, id, 0), kTile slots a tile
@@ -340,6 +343,20 @@ cudaError_t launch_leave(const RunDev& R, unsigned int* ticket, int bump_step, c
 cudaError_t launch_leave_batch(const RunDev* runs, uint32_t nruns, unsigned int* ticket, cudaStream_t s);
 cudaError_t launch_fold(const RunDev& R, uint32_t ncells, unsigned long long* count,
                         unsigned long long* charge, cudaStream_t s);
+// words of the rate table after its 6 kQSlots rates: the atom gate and the
+// FP32 bits of the largest n_e of the cold and the warm cells
+constexpr int kGateWord = 6 * kQSlots;
+constexpr int kKdtWords = kGateWord + 4;
+// the atom gate from the rate table's k_0 dt and the stored largest n_e of
+// each zone (ne_update.cu)
+cudaError_t launch_atom_gate(float* kdt, cudaStream_t s);
+// self-consistent n_e: every cell's n_e from the charge deposited since the
+// mark over steps_vol = steps V_cell, the mark moved on, the records {n_e,
+// zone, delta} rebuilt (rl_coef = 2.38e-6 sqrt(T_e)/(B dX) per cell) and the
+// atom gate recomputed; ne (Nc doubles) is scratch
+cudaError_t launch_ne_update(const unsigned long long* charge, unsigned long long* mark, double* ne,
+                             const double* rl_coef, float4* cell, float* kdt, int nx, int ny, uint32_t ncells,
+                             double weight, double steps_vol, bool isoheat, int sm_count, cudaStream_t s);
 // validity limits and padding point for ecris_load_ions
 struct LoadCheck {
     float R0sq, L;

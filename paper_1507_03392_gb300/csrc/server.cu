@@ -67,6 +67,7 @@ struct Served {
     bool have_prev = false;
     uint64_t issued = 0;             // steps enqueued for the run
     uint64_t snap_steps = 0;         // steps at its latest snapshot
+    bool ne_failed = false;          // a self-consistent n_e update could not be enqueued
     ecris::TallySnapshot* snap = nullptr;   // pinned
     cudaEvent_t ev = nullptr;        // the snapshot has landed
 };
@@ -348,6 +349,12 @@ void serve_loop(ecris_server* s)
                     v->snap_steps = v->issued;
                     taken.push_back(v);
                 }
+                // self-consistent n_e: updated on the device after every
+                // ne_windows windows, in stream order, as the same run alone
+                // would be between its calls of that many windows
+                if (r.ne_windows && v->issued % ((uint64_t)r.window_steps * r.ne_windows) == 0 &&
+                    ecris_batch_update_ne(s->batch, v->run) != ECRIS_OK)
+                    v->ne_failed = true;
             }
             std::lock_guard<std::mutex> lock(s->mu);
             s->ion_steps += advanced;
@@ -362,7 +369,7 @@ void serve_loop(ecris_server* s)
                 std::lock_guard<std::mutex> lock(s->mu);
                 res = v->res;
             }
-            const bool ok_diag = landed && read_snapshot(s, v, ext, res);
+            const bool ok_diag = landed && !v->ne_failed && read_snapshot(s, v, ext, res);
             const bool conv = ok_diag && converged(v, ext, res);
             const bool cap = v->snap_steps >= r.max_steps;
             res.converged = conv ? 1 : 0;
@@ -384,7 +391,10 @@ void serve_loop(ecris_server* s)
             ecris_batch_remove_run(s->batch, v->run);
             give_slot(s, v);
             std::lock_guard<std::mutex> lock(s->mu);
-            finish(s, v, rv.second, rv.second == ECRIS_REQ_DONE ? nullptr : "device error word set (bounded wait ran out)");
+            finish(s, v, rv.second,
+                   rv.second == ECRIS_REQ_DONE ? nullptr
+                   : v->ne_failed              ? "self-consistent n_e update failed"
+                                               : "device error word set (bounded wait ran out)");
             if (v->job) calib_advance(s, v, rv.second == ECRIS_REQ_DONE);
             v->req.reset();   // the host copy of the inputs is no longer needed
             s->active.erase(std::find(s->active.begin(), s->active.end(), v));

@@ -166,6 +166,17 @@ __device__ __noinline__ void elastic_scatter(const RunDev& R, const Words& u, ui
     vz = 0.5f * (vz + az) + 0.5f * gm * ct;
 }
 
+// false if no cell can ionise an atom whose ionisation word is w0: the gate
+// bounds the threshold of every cell.  It comes with the parameter block
+// while the host knows the densest cell, else from the word the device keeps
+// after the rate table (a gate of 0 reads the same either way)
+__device__ __forceinline__ bool atom_may_ionize(const RunDev& R, uint32_t w0)
+{
+    uint32_t gate = R.atom_gate;
+    if (gate == 0u) gate = __ldg(reinterpret_cast<const uint32_t*>(R.kdt) + kGateWord);
+    return w0 < gate || gate == 0xFFFFFFFFu;
+}
+
 // Advance one particle by one step.  pid is its stable id (the Philox counter
 // word).  On return dep_cell is the cell it deposits in and ckey the cell
 // where it takes part in Coulomb collisions (kNoCell if it does not).  A
@@ -240,7 +251,7 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
     // an atom needs its cell only if its ionisation word could fire in
     // the densest cell; otherwise no cell can ionise it this step
     const bool ionize = (R.flags & kFIonize) && (int)Q < R.qmax;
-    const bool need = Q > 0 || (ionize && (w.w0 < R.atom_gate || R.atom_gate == 0xFFFFFFFFu));
+    const bool need = Q > 0 || (ionize && atom_may_ionize(R, w.w0));
     if (need && cell != cell_pre) cr = __ldg(R.cell + cell);   // n_e, zone, delta_x, delta_y
     const int zone = cr.y > 0.5f ? 1 : 0;
     const bool recomb = kVar && (R.flags & kFRecomb) && Q >= 1;

@@ -83,7 +83,7 @@ class Request(ctypes.Structure):
                 ("n", ctypes.c_size_t), ("xyzv", ctypes.c_void_p * 6), ("q", ctypes.c_void_p),
                 ("weight", ctypes.c_double), ("seed", ctypes.c_uint64), ("dt", ctypes.c_double),
                 ("window_steps", ctypes.c_uint32), ("rel_tol", ctypes.c_double),
-                ("min_events", ctypes.c_int64), ("max_steps", ctypes.c_uint32)]
+                ("min_events", ctypes.c_int64), ("max_steps", ctypes.c_uint32), ("ne_windows", ctypes.c_uint32)]
 
 
 class Result(ctypes.Structure):
@@ -499,7 +499,8 @@ class Server:
         except Exception:
             pass
 
-    def _request(self, rp, state, E, ne_cells, window_steps, rel_tol, min_events, max_steps, weight, seed, dt):
+    def _request(self, rp, state, E, ne_cells, window_steps, rel_tol, min_events, max_steps, weight, seed, dt,
+                 ne_windows=0):
         """ecris_request for rp and state, with the arrays it points to."""
         f = field_structs(rp, E, ne_cells)
         arrs, q, dev = _state_arrays(state)
@@ -515,15 +516,17 @@ class Server:
         r.seed = rp.seed if seed is None else seed
         r.dt = rp.dt if dt is None else dt
         r.window_steps, r.rel_tol, r.min_events, r.max_steps = window_steps, rel_tol, min_events, max_steps
+        r.ne_windows = ne_windows
         return r, (f, arrs, q)
 
     def calibrate(self, rp, state, flow_target, power_target_W, tol=0.1, max_iter=8, E=None, ne_cells=None,
-                  window_steps=256, rel_tol=0.02, min_events=400, max_steps=4096, weight=None, seed=None, dt=None):
+                  window_steps=256, rel_tol=0.02, min_events=400, max_steps=4096, weight=None, seed=None, dt=None,
+                  ne_windows=0):
         """Queue a calibration job (ecris_server_calibrate): runs of rp with
         the weight and rp.Te_warm_eV adjusted until the last window's flow and
         power meet the targets within tol.  Returns the job handle."""
         r, keep = self._request(rp, state, E, ne_cells, window_steps, rel_tol, min_events, max_steps, weight, seed,
-                                dt)
+                                dt, ne_windows)
         c = CalibRequest()
         c.base = r
         c.flow_target, c.power_target_W, c.tol, c.max_iter = flow_target, power_target_W, tol, max_iter
@@ -545,9 +548,12 @@ class Server:
                 "steps": np.array(res.steps[:k]), "error": res.error.decode()}
 
     def submit(self, rp, state, E=None, ne_cells=None, window_steps=256, rel_tol=0.02, min_events=400,
-               max_steps=4096, weight=None, seed=None, dt=None):
+               max_steps=4096, weight=None, seed=None, dt=None, ne_windows=0):
+        """Queue a run (ecris_server_submit); ne_windows > 0 makes its n_e
+        self-consistent, updated after every ne_windows windows.  Returns the
+        ticket."""
         r, keep = self._request(rp, state, E, ne_cells, window_steps, rel_tol, min_events, max_steps, weight, seed,
-                                dt)
+                                dt, ne_windows)
         t = ctypes.c_int64(0)
         st = ecris_server_submit(self.s, ctypes.byref(r), ctypes.byref(t))
         if st != ECRIS_OK:

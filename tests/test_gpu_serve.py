@@ -91,6 +91,40 @@ def test_served_results_equal_runs_alone(E):
     srv.close()
 
 
+def busy_spec(seed):
+    """hot ions in a dense plasma: many wall hits within a few tens of steps"""
+    rp = I.RunParams(nx=16, ny=16, nz=32, ne_in_cm3=3e12, ne_out_cm3=3e11, n0_cm3=3e11, dt=3e-8,
+                     Te_warm_eV=500.0, flags=I.F_ALL, seed=seed)
+    wl = I.Workload("b", rp, n=8001, steps=0, atom_fraction=0.4, ion_qmax_init=8, ion_T_eV=60.0,
+                    atoms_fill_chamber=True, zone_box=(0.02, 0.05, 0.29))
+    return rp, I.make_particles(wl, seed=seed)
+
+
+def test_served_self_consistent_ne_equals_run_alone(E):
+    # n_e updated on the device after every 1 or 2 windows of 16 steps, with
+    # no read-back in the request loop: the same as the run alone with
+    # ecris_update_ne at the same steps, and not the same as without updates
+    sp = [busy_spec(17), busy_spec(18)]
+    srv = E.Server(steps_per_tick=4)
+    tickets = [srv.submit(rp, st, window_steps=16, rel_tol=1e-3, min_events=10**15, max_steps=64, ne_windows=k + 1)
+               for k, (rp, st) in enumerate(sp)]
+    res = wait_all(srv, tickets)
+    for k, (r, (rp, st)) in enumerate(zip(res, sp)):
+        assert r["state"] == E.REQ_DONE and r["steps"] == 64
+        run = E.Run(rp)
+        run.load(st)
+        for w in range(4):
+            run.step(16)
+            if (w + 1) % (k + 1) == 0:
+                run.update_ne()
+        check_equal(r, run.diag())
+        run.close()
+        d0 = alone_diag(E, rp, st, None, 64)   # the prescribed n_e throughout
+        assert d0["lost"][1:].sum() > 100
+        assert r["ke_lost_eV"] != d0["ke_lost_eV"]
+    srv.close()
+
+
 def test_budget_queues_in_arrival_order(E):
     sp = specs()
     rp, st, Ef = sp[1]
