@@ -92,6 +92,7 @@ typedef struct {
     double T_refl_eV;                /* re-emission temperature of ions neutralised at a wall (0: T0) */
     double sigma_el_m2;              /* elastic ion-atom cross section of Q = 1 (scaled by Q) */
     double k2_factor;                /* double-ionisation rate factor */
+    double k3_factor;                /* triple-ionisation rate factor (0: off) */
     int32_t ax_n;                    /* on-axis B0 table: samples at z_k = k L/(ax_n - 1); 0: mirror */
     const double *ax_y;              /* B0(z_k), T */
     const double *ax_M;              /* the natural cubic spline's B0''(z_k) (or_axial_setup) */
@@ -372,18 +373,26 @@ void or_build_rates(const or_params *p, const double *ip_eV, const int32_t *n_ou
     }
 }
 
-/* Double ionisation Q -> Q+2 (Sec. II; the fit of [22] is not available):
+/* Multiple ionisation (Sec. II; the fit of [22] for two electrons and the
+ * scaling of [23] for three are not available).  Double, Q -> Q+2:
  * k2_factor times the Lotz-Maxwellian rate with the threshold P_Q + P_{Q+1}
- * (both electrons removed) and q_Q outer electrons; rates2[zone*qmax + Q],
- * zero for Q = qmax - 1.  Removal of three or more electrons is left out
- * (the paper finds it a minor contributor). */
+ * (both electrons removed) and q_Q outer electrons, in rates2[zone*qmax + Q],
+ * zero for Q = qmax - 1.  Triple, Q -> Q+3: k3_factor times the same with
+ * the threshold P_Q + P_{Q+1} + P_{Q+2}, in rates2[2*qmax + zone*qmax + Q],
+ * zero for Q >= qmax - 2.  Four or more electrons are left out (the paper
+ * finds the processes beyond double ionisation minor contributors). */
 void or_build_rates2(const or_params *p, const double *ip_eV, const int32_t *n_outer, double *rates2)
 {
     for (int zone = 0; zone < 2; ++zone) {
         double Te = zone ? p->Te_warm : p->Te_cold;
-        for (int q = 0; q < p->qmax; ++q)
+        for (int q = 0; q < p->qmax; ++q) {
             rates2[zone * p->qmax + q] =
                 q + 1 < p->qmax ? p->k2_factor * or_lotz_rate(ip_eV[q] + ip_eV[q + 1], n_outer[q], Te) : 0.0;
+            rates2[2 * p->qmax + zone * p->qmax + q] =
+                q + 2 < p->qmax && p->k3_factor > 0.0
+                    ? p->k3_factor * or_lotz_rate(ip_eV[q] + ip_eV[q + 1] + ip_eV[q + 2], n_outer[q], Te)
+                    : 0.0;
+        }
     }
 }
 
@@ -408,47 +417,42 @@ void or_build_rates_rec(const or_params *p, double *ratesr)
     }
 }
 
+static int or_near(double w0, double t) { return fabs(w0 - t) < 1e-5 * t + 2.0; }
+
 /* Outcome of the ionisation word w0 in a cell: 0 none, 1 single, 2 double,
- * -1 recombination.
- * One step's probability of any ionisation is 1 - exp(-n_e (k1 + k2) dt); it
- * is shared between the two in proportion to k1 and k2, so w0 below the
- * single threshold ionises once and w0 between the two thresholds twice.
- * *near is set when w0 lies within rounding distance of either threshold. */
+ * 3 triple, -1 recombination.
+ * One step's probability of any of these is p = 1 - exp(-n_e k dt) with
+ * k = k1 + k2 + k3 + kr (the processes switched on); it is shared in
+ * proportion to the rates, so w0 below p k1/k ionises once, below
+ * p (k1+k2)/k twice, below p (k1+k2+k3)/k three times, and below p
+ * recombines.  *near is set when w0 lies within rounding distance of any of
+ * the thresholds. */
 static int or_ion_outcome(const or_params *p, double ne_c, int zc, const double *rates, const double *rates2,
                           const double *ratesr, int Q, uint32_t w0, int *near)
 {
-    if (ratesr && (p->flags & OR_F_RECOMB)) {
-        /* single, double and recombination share the word in proportion to
-         * their rates: w0 below p k1/k, then below p (k1+k2)/k, then below p,
-         * with k = k1 + k2 + kr and p = 1 - exp(-n_e k dt) */
-        int ion = (p->flags & OR_F_IONIZE) && Q < p->qmax;
-        double k1 = ion ? rates[zc * p->qmax + Q] : 0.0;
-        double k2 = (ion && rates2 && (p->flags & OR_F_DOUBLE)) ? rates2[zc * p->qmax + Q] : 0.0;
-        double kr = ratesr[zc * (p->qmax + 1) + Q];
-        double k = k1 + k2 + kr;
-        if (k <= 0.0) return 0;
-        double pt = -expm1(-ne_c * k * p->dt);
-        double t = or_threshold(pt), t1 = or_threshold(pt * (k1 / k)), t2 = or_threshold(pt * ((k1 + k2) / k));
-        if (near && (fabs((double)w0 - t) < 1e-5 * t + 2.0 || fabs((double)w0 - t1) < 1e-5 * t1 + 2.0 ||
-                     fabs((double)w0 - t2) < 1e-5 * t2 + 2.0))
-            *near = 1;
-        if ((double)w0 < floor(t1)) return 1;
-        if ((double)w0 < floor(t2)) return 2;
-        return (double)w0 < floor(t) ? -1 : 0;
-    }
-    double k1 = rates[zc * p->qmax + Q];
-    double k2 = (rates2 && (p->flags & OR_F_DOUBLE)) ? rates2[zc * p->qmax + Q] : 0.0;
-    if (k2 <= 0.0) {
+    const int rec = ratesr && (p->flags & OR_F_RECOMB);
+    const int ion = rec ? ((p->flags & OR_F_IONIZE) && Q < p->qmax) : 1;
+    const int multi = ion && rates2 && (p->flags & OR_F_DOUBLE);
+    double k1 = ion ? rates[zc * p->qmax + Q] : 0.0;
+    double k2 = multi ? rates2[zc * p->qmax + Q] : 0.0;
+    double k3 = multi ? rates2[2 * p->qmax + zc * p->qmax + Q] : 0.0;
+    double kr = rec ? ratesr[zc * (p->qmax + 1) + Q] : 0.0;
+    double w = (double)w0;
+    if (!rec && k2 <= 0.0 && k3 <= 0.0) {
         double thr = or_threshold(-expm1(-ne_c * k1 * p->dt));
-        if (near && fabs((double)w0 - thr) < 1e-5 * thr + 2.0) *near = 1;
-        return (double)w0 < floor(thr) ? 1 : 0;
+        if (near && or_near(w, thr)) *near = 1;
+        return w < floor(thr) ? 1 : 0;
     }
-    double pt = -expm1(-ne_c * (k1 + k2) * p->dt);
-    double thr = or_threshold(pt), thr1 = or_threshold(pt * (k1 / (k1 + k2)));
-    if (near && (fabs((double)w0 - thr) < 1e-5 * thr + 2.0 || fabs((double)w0 - thr1) < 1e-5 * thr1 + 2.0))
-        *near = 1;
-    if ((double)w0 < floor(thr1)) return 1;
-    return (double)w0 < floor(thr) ? 2 : 0;
+    double k = k1 + k2 + k3 + kr;
+    if (k <= 0.0) return 0;
+    double pt = -expm1(-ne_c * k * p->dt);
+    double t = or_threshold(pt), t1 = or_threshold(pt * (k1 / k)), t2 = or_threshold(pt * ((k1 + k2) / k)),
+           t3 = or_threshold(pt * ((k1 + k2 + k3) / k));
+    if (near && (or_near(w, t) || or_near(w, t1) || or_near(w, t2) || or_near(w, t3))) *near = 1;
+    if (w < floor(t1)) return 1;
+    if (w < floor(t2)) return 2;
+    if (w < floor(t3)) return 3;
+    return w < floor(t) ? -1 : 0;
 }
 
 /* ------------------------------------------------------------------------ */

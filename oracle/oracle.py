@@ -60,6 +60,7 @@ class Params(ctypes.Structure):
         ("ei_charge_power", ctypes.c_int32), ("flags", ctypes.c_uint32),
         ("weight", ctypes.c_double), ("seed", ctypes.c_uint64), ("dt", ctypes.c_double),
         ("T_refl_eV", ctypes.c_double), ("sigma_el_m2", ctypes.c_double), ("k2_factor", ctypes.c_double),
+        ("k3_factor", ctypes.c_double),
         ("ax_n", ctypes.c_int32), ("ax_y", ctypes.c_void_p), ("ax_M", ctypes.c_void_p),
     ]
 
@@ -151,6 +152,7 @@ def make_params(rp, dt=None) -> Params:
     p.T_refl_eV = rp.T_refl_eV
     p.sigma_el_m2 = rp.sigma_el1_cm2 * 1e-4
     p.k2_factor = rp.k2_factor
+    p.k3_factor = rp.k3_factor
     if rp.B_axial is not None:
         # on-axis table: the spline's second derivatives, kept alive with p
         y = np.ascontiguousarray(rp.B_axial, dtype=np.float64)
@@ -270,7 +272,7 @@ class OracleRun:
         self.ratesr = np.zeros(2 * (qmax + 1))
         if rp.flags & F_RECOMB:
             lib().or_build_rates_rec(ctypes.byref(self.p), _ptr(self.ratesr))
-        self.rates2 = np.zeros(2 * qmax)
+        self.rates2 = np.zeros(4 * qmax)   # double by zone, then triple by zone
         if rp.flags & F_DOUBLE:
             lib().or_build_rates2(ctypes.byref(self.p), _ptr(np.ascontiguousarray(ip, np.float64)),
                                   _ptr(np.ascontiguousarray(nout, np.int32)), _ptr(self.rates2))

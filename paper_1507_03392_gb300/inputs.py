@@ -130,10 +130,11 @@ class RunParams:
     B_axial: Optional[tuple] = None
     # opt-in processes: re-emission temperature of ions neutralised at a wall
     # (0: T0), synthetic elastic ion-atom cross section of Q = 1 (cm^2),
-    # double-ionisation rate factor
+    # double- and triple-ionisation rate factors (k3_factor = 0: no triple)
     T_refl_eV: float = 0.0
     sigma_el1_cm2: float = 4e-15
     k2_factor: float = 0.1
+    k3_factor: float = 0.0
     flags: int = F_ALL_NO_COULOMB
     # macroparticle weight and RNG key
     weight: float = 1e8

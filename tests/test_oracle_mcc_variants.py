@@ -1,8 +1,8 @@
 """Pins of the oracle's opt-in processes of the collision block (Sec. II) and
 the model variants of Secs. III.C and IV:
 
-* double ionisation Q -> Q+2 beside Q -> Q+1 (exact Markov chain with the
-  closed-form rates);
+* double ionisation Q -> Q+2 and triple ionisation Q -> Q+3 beside Q -> Q+1
+  (exact Markov chain with the closed-form rates);
 * elastic ion-atom scattering, isotropic in the centre-of-mass frame (rate,
   kinematics, isotropy, competition with charge exchange);
 * warm reflected atoms: ions neutralised at a wall come back at T_refl,
@@ -36,7 +36,8 @@ def test_double_ionisation_matches_markov_chain():
     k1 = np.array([closed_form(ip[q], nout[q], Te) for q in range(qm)])
     k2 = np.array([rp.k2_factor * closed_form(ip[q] + ip[q + 1], nout[q], Te) if q + 1 < qm else 0.0
                    for q in range(qm)])
-    assert np.allclose(r.rates2[qm:], k2, rtol=1e-6)
+    assert np.allclose(r.rates2[qm:2 * qm], k2, rtol=1e-6)
+    assert not r.rates2[2 * qm:].any()            # no triple ionisation unless k3_factor > 0
     T = np.zeros((qm + 1, qm + 1))
     for q in range(qm):
         pt = 1 - math.exp(-ne * (k1[q] + k2[q]) * rp.dt)
@@ -61,6 +62,46 @@ def test_double_ionisation_matches_markov_chain():
     assert (np.arange(qm + 1) * got).sum() > mean1 + 0.2
 
 
+def _chain(ks, ne, dt, qm):
+    """one step's transition matrix for Q -> Q+1..Q+len(ks) sharing one word"""
+    T = np.zeros((qm + 1, qm + 1))
+    for q in range(qm):
+        kq = [k[q] for k in ks]
+        pt = 1 - math.exp(-ne * sum(kq) * dt)
+        T[q, q] = 1 - pt
+        for n, kn in enumerate(kq, start=1):
+            if kn > 0:
+                T[q, q + n] = pt * kn / sum(kq)
+    T[qm, qm] = 1.0
+    return T
+
+
+def test_triple_ionisation_matches_markov_chain():
+    # Q -> Q+1, Q+2, Q+3 share one word in proportion to k1, k2, k3; k3 =
+    # k3_factor times the Lotz-Maxwellian rate of P_Q + P_{Q+1} + P_{Q+2}
+    rp = _uniform_params(flags=I.F_IONIZE | I.F_DOUBLE, dt=2e-7, k2_factor=0.3, k3_factor=1.0)
+    n, S = 40000, 150
+    r = O.OracleRun(rp, _static(n, 0, rp), deposit=False)
+    ip, nout = rp.species.ladder()
+    Te, ne = rp.Te_warm_eV, 1e18
+    qm = rp.species.qmax
+    k1 = np.array([closed_form(ip[q], nout[q], Te) for q in range(qm)])
+    k2 = np.array([rp.k2_factor * closed_form(ip[q] + ip[q + 1], nout[q], Te) if q + 1 < qm else 0.0
+                   for q in range(qm)])
+    k3 = np.array([rp.k3_factor * closed_form(ip[q] + ip[q + 1] + ip[q + 2], nout[q], Te) if q + 2 < qm else 0.0
+                   for q in range(qm)])
+    assert np.allclose(r.rates2[3 * qm:], k3, rtol=1e-6) and k3[qm - 2] == 0.0 and k3[qm - 3] > 0.0
+    r.step(S)
+    got = np.bincount(r.q, minlength=qm + 1) / n
+    want = np.linalg.matrix_power(_chain([k1, k2, k3], ne, rp.dt, qm), S)[0]
+    sig = np.sqrt(want * (1 - want) / n) + 1e-12
+    assert np.all(np.abs(got - want) < 5 * sig + 1e-4)
+    # the chain without the triple step is clearly rejected
+    want2 = np.linalg.matrix_power(_chain([k1, k2], ne, rp.dt, qm), S)[0]
+    sig2 = np.sqrt(want2 * (1 - want2) / n) + 1e-12
+    assert np.max(np.abs(got - want2) / sig2) > 10
+
+
 def test_double_ionisation_top_state():
     # from qmax - 1 only one electron is left: no double step there, and a
     # double step from qmax - 2 ends at qmax
@@ -75,6 +116,21 @@ def test_double_ionisation_top_state():
         assert ev.sum() > 200 and r.q.max() == qm
         if q0 == qm - 2:
             assert np.any(r.q[ev] == qm) and np.any(r.q[ev] == qm - 1)
+
+
+def test_triple_ionisation_top_state():
+    # a triple step needs three electrons: none from qmax - 2, and from
+    # qmax - 3 it is the only way to reach qmax in one step
+    rp = I.RunParams(species=I.OXYGEN, B_ecr=100.0, ne_in_cm3=1e14, Te_warm_eV=3000.0,
+                     flags=I.F_IONIZE | I.F_DOUBLE, k2_factor=1.0, k3_factor=1.0, dt=1e-5)
+    qm = rp.species.qmax
+    r = O.OracleRun(rp, _static(4000, qm - 3, rp), deposit=False)
+    assert r.rates2[2 * qm + qm + qm - 2] == 0.0 and r.rates2[2 * qm + qm + qm - 3] > 0.0
+    r.step(1)
+    assert r.q.max() == qm and np.any(r.q == qm - 1) and np.any(r.q == qm - 2)
+    r = O.OracleRun(rp, _static(4000, qm - 2, rp), deposit=False)
+    r.step(1)
+    assert r.q.max() == qm
 
 
 def _beam(rp, n, q, u):
