@@ -70,11 +70,13 @@ typedef enum {
 /* Opt-in processes and variants (Sec. II collision block; Secs. III.C, IV). */
 #define ECRIS_F_ISOHEAT (1u << 6) /* isotropic heating: the kick without the drift
                                      bias, delta = 0 (the paper's diffusion-off run) */
-#define ECRIS_F_DOUBLE (1u << 7)  /* double ionisation Q -> Q+2: rate k2_factor times
+#define ECRIS_F_DOUBLE (1u << 7)  /* multiple ionisation: Q -> Q+2 at k2_factor times
                                      the Lotz-Maxwellian rate with threshold
-                                     P_Q + P_{Q+1}; one word decides, single below
-                                     p k1/(k1+k2), double up to p = 1 - exp(-n_e
-                                     (k1+k2) dt) */
+                                     P_Q + P_{Q+1}, and, when k3_factor > 0, Q -> Q+3
+                                     at k3_factor times that of P_Q + P_{Q+1} + P_{Q+2};
+                                     one word decides, single below p k1/k, double
+                                     below p (k1+k2)/k, triple up to p = 1 - exp(-n_e
+                                     k dt), k = k1 + k2 + k3 */
 #define ECRIS_F_ELASTIC (1u << 8) /* elastic ion-atom scattering on the background,
                                      cross section sigma_el1_cm2 * Q, isotropic in
                                      the centre-of-mass frame with an atom drawn at
@@ -167,6 +169,7 @@ typedef struct {
                                (Sec. III.C warm atoms, 0.15 eV); 0: T0 */
     double sigma_el1_cm2;   /* elastic ion-atom cross section of Q=1, cm^2 (ECRIS_F_ELASTIC) */
     double k2_factor;       /* double-ionisation rate factor (ECRIS_F_DOUBLE), >= 0 */
+    double k3_factor;       /* triple-ionisation rate factor (ECRIS_F_DOUBLE), >= 0; 0: none */
 } ecris_mcc;
 
 /* Diagnostics filled by ecris_diag.  Arrays are caller-owned; each array

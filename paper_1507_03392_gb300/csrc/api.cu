@@ -97,6 +97,7 @@ struct HostRun {
     std::vector<int> nout;
     std::vector<double> rate[2];   // m^3/s per Q, zone 0 cold, 1 warm
     std::vector<double> rate2[2];  // double ionisation Q -> Q+2 (m^3/s), same layout
+    std::vector<double> rate3[2];  // triple ionisation Q -> Q+3 (m^3/s), same layout
     std::vector<double> rate_r[2]; // recombination Q -> Q-1 (m^3/s), Q = 0..qmax
     float ne_max[2] = {0.f, 0.f};  // largest FP32 n_e (as the kernels see it) of the cold and warm cells
     std::vector<unsigned char> cell_zone;
@@ -690,13 +691,15 @@ ecris_status upload_dt(ecris_ctx* ctx, double dt)
             const bool ion = q < ctx->h.qmax && (!rec || (fl & kFIonize));
             const double k1 = ion ? ctx->h.rate[zone][q] : 0.0;
             const double k2 = (dbl && ion) ? ctx->h.rate2[zone][q] : 0.0;
+            const double k3 = (dbl && ion) ? ctx->h.rate3[zone][q] : 0.0;
             const double kr = (rec && q <= ctx->h.qmax) ? ctx->h.rate_r[zone][q] : 0.0;
-            const double k = k1 + k2 + kr;
+            const double k = k1 + k2 + k3 + kr;
             ctx->h_kdt[zone * kQSlots + q] = (float)(k * dt);
             ctx->h_kdt[2 * kQSlots + zone * kQSlots + q] = k > 0.0 ? (float)(k1 / k) : 1.0f;
             ctx->h_kdt[4 * kQSlots + zone * kQSlots + q] = k > 0.0 ? (float)((k1 + k2) / k) : 1.0f;
+            ctx->h_kdt[6 * kQSlots + zone * kQSlots + q] = k > 0.0 ? (float)((k1 + k2 + k3) / k) : 1.0f;
         }
-    CK(cudaMemcpyAsync(ctx->d_kdt, ctx->h_kdt, 6 * kQSlots * sizeof(float), cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync(ctx->d_kdt, ctx->h_kdt, kGateWord * sizeof(float), cudaMemcpyHostToDevice,
                        ctx->stream));
     // the atom gate on the device, from the new k_0 dt and the largest n_e of
     // each zone that the device keeps (a device update of n_e changes them),
@@ -980,7 +983,7 @@ ecris_status ecris_create(ecris_ctx** out, int device, void* cuda_stream)
         }
     }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_run, sizeof(RunDev));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_kdt, 6 * kQSlots * sizeof(float));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_kdt, kGateWord * sizeof(float));
     if (e != cudaSuccess) {
         g_create_error = std::string("ecris_create: ") + cudaGetErrorString(e);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -1056,7 +1059,7 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
         !(mcc->lnL_ei >= 0.0) || (mcc->ei_charge_power != 1 && mcc->ei_charge_power != 2) ||
         (mcc->flags & ~kFlagMask) || !(mcc->T_refl_eV >= 0.0) || !std::isfinite(mcc->T_refl_eV) ||
         !(mcc->sigma_el1_cm2 >= 0.0) || !std::isfinite(mcc->sigma_el1_cm2) || !(mcc->k2_factor >= 0.0) ||
-        !std::isfinite(mcc->k2_factor))
+        !std::isfinite(mcc->k2_factor) || !(mcc->k3_factor >= 0.0) || !std::isfinite(mcc->k3_factor))
         return fail(ctx, ECRIS_EINVAL, "init_fields: invalid collision parameters");
 
     CK(cudaSetDevice(ctx->device));
@@ -1099,6 +1102,13 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
         if (mcc->flags & kFDouble)
             for (int q = 0; q + 1 < sp->qmax; ++q)
                 h.rate2[zone][q] = mcc->k2_factor * lotz_rate(h.ip[q] + h.ip[q + 1], h.nout[q], Te);
+        // triple ionisation (the scaling of [23] is not available): k3_factor
+        // times the same with threshold P_Q + P_{Q+1} + P_{Q+2}
+        h.rate3[zone].assign(sp->qmax, 0.0);
+        if ((mcc->flags & kFDouble) && mcc->k3_factor > 0.0)
+            for (int q = 0; q + 2 < sp->qmax; ++q)
+                h.rate3[zone][q] =
+                    mcc->k3_factor * lotz_rate(h.ip[q] + h.ip[q + 1] + h.ip[q + 2], h.nout[q], Te);
         // radiative recombination (the datasets [21] are not available):
         // Seaton's hydrogenic rate for charge Z = Q, lambda = 157890 Z^2 / T(K)
         h.rate_r[zone].assign(sp->qmax + 1, 0.0);

@@ -139,8 +139,9 @@ struct alignas(16) RunDev {
     const float4 *cell;          // {n_e (m^-3), zone (0/1), delta_x, delta_y}
     const float4 *E;             // {E_x, E_y, E_z, 0} per cell centre
     const float *kdt;            // [zone * 64 + Q]: k dt with k = k1 (single ionisation) + k2 (double)
-                                 // + kr (recombination) as switched on; then [2 * 64 + ...] the share
-                                 // k1 / k and [4 * 64 + ...] the share (k1 + k2) / k; then at
+                                 // + k3 (triple) + kr (recombination) as switched on; then
+                                 // [2 * 64 + ...] the share k1 / k, [4 * 64 + ...] the share
+                                 // (k1 + k2) / k and [6 * 64 + ...] (k1 + k2 + k3) / k; then at
                                  // kGateWord the atom gate (uint32 bits): an atom whose ionisation
                                  // word is >= the gate cannot ionise in any cell (0xFFFFFFFF: no
                                  // such bound), and the largest n_e of the cold and warm cells
@@ -343,9 +344,9 @@ cudaError_t launch_leave(const RunDev& R, unsigned int* ticket, int bump_step, c
 cudaError_t launch_leave_batch(const RunDev* runs, uint32_t nruns, unsigned int* ticket, cudaStream_t s);
 cudaError_t launch_fold(const RunDev& R, uint32_t ncells, unsigned long long* count,
                         unsigned long long* charge, cudaStream_t s);
-// words of the rate table after its 6 kQSlots rates: the atom gate and the
+// words of the rate table after its 8 kQSlots rates and shares: the atom gate and the
 // FP32 bits of the largest n_e of the cold and the warm cells
-constexpr int kGateWord = 6 * kQSlots;
+constexpr int kGateWord = 8 * kQSlots;
 constexpr int kKdtWords = kGateWord + 4;
 // the atom gate from the rate table's k_0 dt and the stored largest n_e of
 // each zone (ne_update.cu)

@@ -260,13 +260,16 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
         if constexpr (kVar) {
             const float p = event_prob(lam);
             if (fires(w.w0, p)) {
-                // single, double and recombination share [0, p) in proportion
-                // to their rates: below p k1/k one electron goes, below
-                // p (k1+k2)/k two, above that one is captured
+                // single, double, triple and recombination share [0, p) in
+                // proportion to their rates: below p k1/k one electron goes,
+                // below p (k1+k2)/k two, below p (k1+k2+k3)/k three, above
+                // that one is captured
                 int up = 1;
                 if (R.flags & (kFDouble | kFRecomb)) {
-                    if (!fires(w.w0, p * __ldg(R.kdt + 2 * kQSlots + zone * kQSlots + Q)))
-                        up = fires(w.w0, p * __ldg(R.kdt + 4 * kQSlots + zone * kQSlots + Q)) ? 2 : -1;
+                    if (!fires(w.w0, p * __ldg(R.kdt + 2 * kQSlots + zone * kQSlots + Q))) {
+                        if (fires(w.w0, p * __ldg(R.kdt + 4 * kQSlots + zone * kQSlots + Q))) up = 2;
+                        else up = fires(w.w0, p * __ldg(R.kdt + 6 * kQSlots + zone * kQSlots + Q)) ? 3 : -1;
+                    }
                 }
                 if (up > 0) {
                     if (Q == 0) R.birth[pid] = step;   // an ion is born (first-passage clock)

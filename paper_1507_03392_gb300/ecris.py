@@ -61,7 +61,8 @@ class Mcc(ctypes.Structure):
                 ("sigma1_cm2", ctypes.c_double), ("E_cx_eV", ctypes.c_double),
                 ("lnL_ii", ctypes.c_double), ("lnL_ei", ctypes.c_double),
                 ("ei_charge_power", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("T_refl_eV", ctypes.c_double), ("sigma_el1_cm2", ctypes.c_double), ("k2_factor", ctypes.c_double)]
+                ("T_refl_eV", ctypes.c_double), ("sigma_el1_cm2", ctypes.c_double), ("k2_factor", ctypes.c_double),
+                ("k3_factor", ctypes.c_double)]
 
 
 class DiagOut(ctypes.Structure):
@@ -333,7 +334,7 @@ def field_structs(rp, E=None, ne_cells=None):
     nout = np.ascontiguousarray(nout, np.int32)
     sp = Species(rp.species.mass_amu, rp.species.qmax, _ptr(ip), _ptr(nout))
     mcc = Mcc(rp.n0_cm3, rp.T0_eV, rp.sigma1_cm2, rp.E_cx_eV, rp.lnL_ii, rp.lnL_ei,
-              rp.ei_charge_power, rp.flags, rp.T_refl_eV, rp.sigma_el1_cm2, rp.k2_factor)
+              rp.ei_charge_power, rp.flags, rp.T_refl_eV, rp.sigma_el1_cm2, rp.k2_factor, rp.k3_factor)
     return geo, bf, grid, sp, mcc, (Eh, nh, ip, nout, bax)
 
 

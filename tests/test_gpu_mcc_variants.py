@@ -72,6 +72,32 @@ def test_lockstep_recombination(E):
     run.close()
 
 
+def test_lockstep_triple_ionisation(E):
+    # ions at rest in dense warm electrons: single, double and triple
+    # ionisation and recombination share one word; the triple steps and the
+    # top charge states match the oracle particle by particle
+    rp = V._uniform_params(species=I.OXYGEN, flags=I.F_IONIZE | I.F_DOUBLE | I.F_RECOMB, Te_warm_eV=3000.0,
+                           Te_cold_eV=3000.0, ne_in_cm3=1e13, ne_out_cm3=1e13, k2_factor=1.0, k3_factor=1.0,
+                           dt=5e-7)
+    st = V._static(4001, 1, rp)
+    st["q"][2000:] = rp.species.qmax - 3        # a triple step from here ends at qmax
+    st32 = {k: np.asarray(v, np.float32) for k, v in st.items() if k != "q"}
+    st32["q"] = st["q"].astype(np.uint8)
+    run = E.Run(rp)
+    run.load(st32)
+    triples = 0
+    orc = O.OracleRun(rp, st32)
+    for s in range(12):
+        g0 = run.state()
+        run.step(1)
+        orc.step(1)
+        g1 = run.state()
+        assert np.array_equal(g1["q"].astype(np.int64), orc.q), s
+        triples += int(((g1["q"].astype(np.int64) - g0["q"]) == 3).sum())
+    assert triples > 20 and g1["q"].max() == rp.species.qmax
+    run.close()
+
+
 def test_warm_reflection_each_particle(E):
     # ions and atoms driven onto the z = 0 flange come back at T_refl and T0
     rp = V._uniform_params(flags=I.F_PUSH | I.F_RECYCLE, T_refl_eV=0.15, dt=1e-9)
@@ -135,6 +161,9 @@ def test_batch_with_variants_equals_run_alone(E):
 
 def test_invalid_variant_parameters(E):
     rp = dataclasses.replace(G.busy_case()[0], k2_factor=-1.0)
+    with pytest.raises(E.EcrisError):
+        E.Run(rp)
+    rp = dataclasses.replace(G.busy_case()[0], k3_factor=-0.5)
     with pytest.raises(E.EcrisError):
         E.Run(rp)
     rp = dataclasses.replace(G.busy_case()[0], T_refl_eV=float("nan"))
