@@ -29,6 +29,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -92,17 +93,26 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        self.lines = []
+        self.reader = None
+        self.skip = 0
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
+        # drain the pipe while the benchmark runs, so the sampler never blocks
+        self.reader = threading.Thread(target=lambda: self.lines.extend(self.proc.stdout), daemon=True)
+        self.reader.start()
+        # the timed region starts once sampling has: samples before now are dropped
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.skip = len(self.lines)
 
     def stop(self):
         if self.proc is None:
@@ -112,10 +122,12 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        self.fh.close()
+        if self.reader is not None:
+            self.reader.join(timeout=5)
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        lines = list(self.lines)
+        for line in lines[self.skip:] if len(lines) > self.skip else lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -187,7 +199,9 @@ def run_reference(args, rank, world):
     from paper_1507_03392_gb300 import inputs as I
     O.build()
     st = I.make_particles(wl)
-    m = min(args.ref_sample, wl.n)
+    # particles per step: the sample, fewer when many steps are asked for, so
+    # that the whole run stays within about a minute of oracle time
+    m = min(args.ref_sample, wl.n, max(2000, int(1.2e8 / max(1, args.steps))))
     sub = {k: v[:m] for k, v in st.items()}
     orc = O.OracleRun(wl.params, sub, ne_cells=I.make_ne_cells(wl))
     for _ in range(args.warmup):
@@ -429,7 +443,7 @@ def workload_config(wl, coulomb):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=None, help="override the particle count")
