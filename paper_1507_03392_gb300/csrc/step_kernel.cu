@@ -876,12 +876,20 @@ struct SoaPtrs { float* p[6]; };
 
 // v * (hi + lo) rounded to the nearest integer: the FP32 product p = v hi is
 // an integer once |p| >= 2^24, and its rounding error (exact by FMA) plus
-// v lo is added as a small correction
+// v lo is added as a small correction.  Float-to-64-bit conversions run on
+// the narrow FP64 pipe, so values inside the signed or unsigned 32-bit range
+// (every position but the chamber's outermost points) convert in 32 bits, to
+// the same integers
 __device__ __forceinline__ long long scale_round(float v, float hi, float lo)
 {
     const float p = v * hi;
     const float e = fmaf(v, hi, -p) + v * lo;
-    return (long long)rintf(p) + (long long)rintf(e + (p - rintf(p)));
+    const float r = rintf(p);
+    long long P;
+    if (fabsf(r) < 2147483648.0f) P = (long long)__float2int_rn(r);
+    else if (r >= 0.0f && r < 4294967296.0f) P = (long long)__float2uint_rn(r);
+    else P = (long long)r;
+    return P + (long long)__float2int_rn(e + (p - r));
 }
 
 // metres -> fixed point, rounded to nearest, saturated

@@ -162,6 +162,48 @@ def test_invalid_inputs_rejected(E):
     run.close()
 
 
+def test_load_rounds_to_the_fixed_point_grid(E):
+    # positions at the chamber's extremes and across the whole range of the
+    # 32-bit fixed-point grid (x, y over [-R0, R0], z over [0, L], where the
+    # conversion crosses 2^31 and reaches 2^32) come back within one grid unit
+    rp = I.RunParams(nx=8, ny=8, nz=16, flags=0)
+    rng = np.random.default_rng(5)
+    R0, L = rp.R0, rp.L
+    ex = [(R0, 0.0, 0.0), (0.0, 0.0, L), (0.0, R0, 0.5 * L), (0.0, -R0, 0.5 * L * (1 + 1e-7)),
+          (0.0, 0.0, 0.5 * L * (1 - 1e-7)), (1e-12, -1e-12, 1e-12)]
+    n = 20000
+    r = R0 * np.sqrt(rng.random(n))
+    ph = 2 * np.pi * rng.random(n)
+    x = np.concatenate([[e[0] for e in ex], r * np.cos(ph)])
+    y = np.concatenate([[e[1] for e in ex], r * np.sin(ph)])
+    z = np.concatenate([[e[2] for e in ex], L * rng.random(n)])
+    m = len(x)
+    st = {"x": x.astype(np.float32), "y": y.astype(np.float32), "z": z.astype(np.float32),
+          "vx": np.zeros(m, np.float32), "vy": np.zeros(m, np.float32), "vz": np.zeros(m, np.float32),
+          "q": np.zeros(m, np.uint8)}
+    # the loader's own test, in FP32 without contraction: x x + y y <= (float)(R0 R0)
+    r2 = np.float32(R0 * R0)
+    inside = (st["x"] * st["x"] + st["y"] * st["y"]) <= r2
+    # the outermost x it accepts (just below 2^31 on the grid) joins the extremes
+    xm = np.float32(R0)
+    while xm * xm > r2:
+        xm = np.nextafter(xm, np.float32(0))
+    st = {k: v[inside] for k, v in st.items()}
+    for k, v in (("x", [xm, -xm]), ("y", [0, 0]), ("z", [0.25 * L, 0.75 * L]), ("vx", [0, 0]), ("vy", [0, 0]),
+                 ("vz", [0, 0]), ("q", [0, 0])):
+        st[k] = np.concatenate([st[k], np.asarray(v, dtype=st[k].dtype)])
+    assert inside.sum() >= n and st["z"].max() == np.float32(L)
+    run = E.Run(rp)
+    run.load(st)
+    g = run.state()
+    uxy, uz = 2 * R0 / 2.0 ** 32, L / 2.0 ** 32
+    for k, u in (("x", uxy), ("y", uxy), ("z", uz)):
+        want = st[k].astype(np.float64)
+        got = g[k].astype(np.float64)
+        assert np.all(np.abs(got - want) <= 1.01 * u + np.abs(np.spacing(st[k])).astype(np.float64)), k
+    run.close()
+
+
 def test_power_and_currents_follow_the_tallies(E):
     rp, st, Ef = busy_case(n=6000)
     run = E.Run(rp, E=Ef)
