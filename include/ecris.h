@@ -555,9 +555,13 @@ ecris_status ecris_server_calib_poll(ecris_server* s, int64_t job, ecris_calib_r
  *
  * Larger n or ncells return ECRIS_EINVAL with a message in
  * ecris_last_error(NULL).  Every call shares the one working array: calls whose
- * GPU work overlaps race and must be serialised by the caller.  The first call
- * on a device sets that device up (a synchronous copy), so make it before any
- * stream capture begins. */
+ * GPU work overlaps race and must be serialised by the caller.  If they do
+ * overlap, a bounded wait inside the call can run out; a call given
+ * collisions_out then returns ECRIS_ETIMEOUT (its velocities are not valid),
+ * while a call without it returns at once and cannot report this.  The first
+ * call on a device sets that device up (a synchronous copy), so make it before
+ * any stream capture begins.  That set-up lasts for the life of the process: a
+ * device reset (cudaDeviceReset) is not supported. */
 ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* cell, const uint8_t* q, float* vx,
                                            float* vy, float* vz, uint32_t* events, uint32_t ncells,
                                            double mass_amu, double weight, double cell_volume_m3,

@@ -566,11 +566,7 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     }
     R.ei_pow = h.mcc.ei_charge_power;
     R.ke_scale = (float)(0.5 * M / kE * 1e6);
-    {
-        const double mu = 0.5 * M;
-        const double k = kE * kE / (kEps0 * mu);
-        R.lnl_ii_coef = (float)(h.mcc.lnL_ii / (4.0 * kPi) * k * k * ctx->weight / (dx * dy * dz));
-    }
+    R.lnl_ii_coef = coulomb_s_coef(h.mcc.lnL_ii, h.mass_amu, ctx->weight, dx * dy * dz);
     R.seed_lo = (uint32_t)ctx->seed;
     R.seed_hi = (uint32_t)(ctx->seed >> 32);
     R.x = reinterpret_cast<int32_t*>(ctx->d_soa[0]);
@@ -1177,15 +1173,8 @@ ecris_status ecris_init_fields(ecris_ctx* ctx, const ecris_geometry* geo, const 
         CK(cudaMallocAsync((void**)&ctx->d_btab, nseg * sizeof(float4), ctx->stream));
         CK(cudaMemcpyAsync(ctx->d_btab, btab.data(), nseg * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
     }
-    // the same for every run: built once per process
-    static const std::vector<float> nanbu = [] {
-        std::vector<float> t(kNanbuN);
-        const double l0 = std::log(kNanbuSLo), dl = std::log(kNanbuSHi / kNanbuSLo) / (kNanbuN - 1);
-        for (int i = 0; i < kNanbuN; ++i) t[i] = (float)std::log(nanbu_A_host(std::exp(l0 + i * dl)));
-        return t;
-    }();
     CK(cudaMallocAsync((void**)&ctx->d_nanbu, kNanbuN * sizeof(float), ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d_nanbu, nanbu.data(), kNanbuN * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_nanbu, nanbu_table(), kNanbuN * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_cell, cell.data(), nc * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_rlc, rlc.data(), nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_kdt + kGateWord, gate_words, sizeof gate_words, cudaMemcpyHostToDevice, ctx->stream));
@@ -2262,6 +2251,25 @@ ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tu
 // Hooks of the served form
 // ---------------------------------------------------------------------------
 namespace ecris {
+
+const float* nanbu_table()
+{
+    // the same for every run: built once per process
+    static const std::vector<float> t = [] {
+        std::vector<float> v(kNanbuN);
+        const double l0 = std::log(kNanbuSLo), dl = std::log(kNanbuSHi / kNanbuSLo) / (kNanbuN - 1);
+        for (int i = 0; i < kNanbuN; ++i) v[i] = (float)std::log(nanbu_A_host(std::exp(l0 + i * dl)));
+        return v;
+    }();
+    return t.data();
+}
+
+float coulomb_s_coef(double lnL_ii, double mass_amu, double weight, double cell_volume_m3)
+{
+    const double mu = 0.5 * mass_amu * kAmu;
+    const double k = kE * kE / (kEps0 * mu);
+    return (float)(lnL_ii / (4.0 * kPi) * k * k * weight / cell_volume_m3);
+}
 
 ecris_status batch_snapshot(ecris_batch* b, int32_t run, TallySnapshot* dst)
 {

@@ -20,7 +20,14 @@
 // overlaps (different streams, or several host threads) race on the array
 // and must be serialised by the caller.  The first call on each device sets up
 // that device (symbol address, Nanbu table upload, a synchronous copy); make
-// that first call before any stream capture begins.
+// that first call before any stream capture begins.  That set-up is kept for
+// the life of the process: a device reset (cudaDeviceReset) is not supported,
+// and the entry point must not be called on a device after one.
+// A bounded wait inside the cell-count scan that runs out (possible only when
+// calls overlap) sets an error word in the array instead of faulting; a call
+// given collisions_out synchronises, reads that word and returns
+// ECRIS_ETIMEOUT.  A call without collisions_out returns at once and does not
+// report it.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -69,22 +76,6 @@ struct DeviceSetup {
 std::mutex g_setup_mutex;
 DeviceSetup g_setup[64];
 
-// Nanbu's A(s) from coth A - 1/A = exp(-s), bisection on ln A in FP64
-double nanbu_A_fp64(double s)
-{
-    const double y = std::exp(-s);
-    auto L = [](double A) {
-        if (A < 1e-3) return A / 3.0 - A * A * A / 45.0;
-        return 1.0 / std::tanh(A) - 1.0 / A;
-    };
-    double lo = std::log(1e-12), hi = std::log(2.0 / (-std::expm1(-s)) + 10.0);
-    for (int it = 0; it < 200; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (L(std::exp(mid)) < y) lo = mid; else hi = mid;
-    }
-    return std::exp(0.5 * (lo + hi));
-}
-
 // clear the per-call counters and store the step index
 __global__ void k_na_init(unsigned char* base, uint32_t ncells, uint32_t tiles, uint32_t step)
 {
@@ -101,7 +92,8 @@ __global__ void k_na_init(unsigned char* base, uint32_t ncells, uint32_t tiles, 
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < tiles; i += stride) tcount[i] = 0u;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         words[0] = step;
-        words[1] = 0u;
+        words[1] = 0u;   // the collision kernel's ticket
+        words[2] = 0u;   // error word: the scan sets ECRIS_ETIMEOUT if a bounded wait runs out
     }
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (uint32_t)kTallyWords; i += stride) tally[i] = 0ull;
 }
@@ -171,10 +163,8 @@ extern "C" ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* 
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess) return na_cuda(e, "cudaGetSymbolAddress");
-            std::vector<float> tab(kNanbuN);
-            const double l0 = std::log(kNanbuSLo), dl = std::log(kNanbuSHi / kNanbuSLo) / (kNanbuN - 1);
-            for (int i = 0; i < kNanbuN; ++i) tab[i] = (float)std::log(nanbu_A_fp64(std::exp(l0 + i * dl)));
-            e = cudaMemcpy(static_cast<unsigned char*>(p) + kOffNanbu, tab.data(), kNanbuN * sizeof(float),
+            // the same FP64-built table ecris_init_fields uploads for ecris_step
+            e = cudaMemcpy(static_cast<unsigned char*>(p) + kOffNanbu, nanbu_table(), kNanbuN * sizeof(float),
                            cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return na_cuda(e, "Nanbu table upload");
             int sms = 0;
@@ -193,9 +183,7 @@ extern "C" ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* 
     // the parameter block the collision kernels read, pointing into the scratch
     RunDev R;
     std::memset(&R, 0, sizeof R);
-    const double M = mass_amu * 1.66053906660e-27, e2 = 1.602176634e-19 * 1.602176634e-19;
-    const double k = e2 / (8.8541878128e-12 * 0.5 * M);
-    R.lnl_ii_coef = (float)(lnL_ii / (4.0 * 3.14159265358979323846) * k * k * weight / cell_volume_m3);
+    R.lnl_ii_coef = coulomb_s_coef(lnL_ii, mass_amu, weight, cell_volume_m3);
     R.dt = (float)dt;
     R.seed_lo = (uint32_t)seed;
     R.seed_hi = (uint32_t)(seed >> 32);
@@ -219,6 +207,7 @@ extern "C" ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* 
     R.nanbu_lnlo = (float)std::log(kNanbuSLo);
     R.nanbu_inv_dln = (float)((kNanbuN - 1) / std::log(kNanbuSHi / kNanbuSLo));
     R.step = reinterpret_cast<uint32_t*>(base + kOffWords);
+    R.err = reinterpret_cast<uint32_t*>(base + kOffWords) + 2;
     R.tally = reinterpret_cast<unsigned long long*>(base + kOffTally);
     unsigned int* ticket = reinterpret_cast<unsigned int*>(base + kOffWords) + 1;
 
@@ -231,10 +220,19 @@ extern "C" ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* 
     e = launch_coulomb(R, ncells, tiles, ticket, setup.grid, s);
     if (e != cudaSuccess) return na_cuda(e, "launch_coulomb");
     if (collisions_out) {
+        // the call synchronises: read the collision count and the error word
         unsigned long long c = 0;
+        uint32_t err = 0;
         e = cudaMemcpyAsync(&c, R.tally + kTallyCoulomb, sizeof c, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&err, R.err, sizeof err, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return na_cuda(e, "collision count");
+        if (err != 0u) {
+            ecris_internal_set_thread_error(
+                "coulomb_collide_noalloc: a bounded wait of the cell-count scan ran out (a call overlapping "
+                "this one on the GPU?); the velocities of this call are not valid");
+            return ECRIS_ETIMEOUT;
+        }
         *collisions_out = (int64_t)c;
     }
     return ECRIS_OK;

@@ -408,6 +408,12 @@ cudaError_t launch_step_batch(const RunDev* runs, const uint2* items, uint32_t n
 cudaError_t launch_bump_steps(const RunDev* runs, uint32_t nruns, cudaStream_t s);
 // message returned by ecris_last_error(NULL) on the calling thread
 void ecris_internal_set_thread_error(const char* msg);
+// host: ln A(s) of Nanbu's scattering law on kNanbuN points uniform in ln s
+// over [kNanbuSLo, kNanbuSHi], built in FP64 once per process (api.cu)
+const float* nanbu_table();
+// host: the prefactor of Nanbu's s = coef Qa^2 Qb^2 m g^-3 dt for m ions of
+// one cell: lnL/(4 pi) (e^2/(eps0 mu))^2 w / V_cell, mu = M/2 (api.cu)
+float coulomb_s_coef(double lnL_ii, double mass_amu, double weight, double cell_volume_m3);
 
 // Hooks of the served form (defined in api.cu, used by server.cu).  A tally
 // snapshot is a run's tally words and device error word, copied in stream

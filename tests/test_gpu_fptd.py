@@ -95,7 +95,7 @@ def test_busy_run_matches_oracle(E):
     run = E.Run(rp)
     run.load(st)
     t, orc = P.lockstep(run, rp, st, 150)
-    assert t["q"] == 0 and t["events"] == 0, t["first_bad"]
+    assert t["q"] == 0 and t["events"] == 0 and t["pos"] == 0 and t["vel"] == 0, t["first_bad"]
     f = run.fptd()
     q1 = rp.species.qmax + 1
     assert orc.fptd_hist.sum() >= 100, orc.fptd_hist.sum()
