@@ -221,9 +221,10 @@ __device__ __forceinline__ float nanbu_A(const RunDev& R, float s)
 }
 
 // One collision over time dtc of the records ra, rb (vx, vy, vz, Q bits),
-// using the stream-1 words of particle `first`; updates the records in place.
-__device__ __forceinline__ void collide(const RunDev& R, float4& ra, float4& rb, float dtc, float m_cell,
-                                        uint32_t first, uint32_t step)
+// with w1, w2 the stream-1 words 1 and 2 of the pair's first particle (the
+// angles); updates the records in place.
+__device__ __forceinline__ void collide_w(const RunDev& R, float4& ra, float4& rb, float dtc, float m_cell,
+                                          uint32_t w1, uint32_t w2)
 {
     const float gx = ra.x - rb.x, gy = ra.y - rb.y, gz = ra.z - rb.z;
     const float g2 = gx * gx + gy * gy + gz * gz;
@@ -231,11 +232,15 @@ __device__ __forceinline__ void collide(const RunDev& R, float4& ra, float4& rb,
     const float g = sqrtf(g2);
     const float qq = (float)((__float_as_uint(ra.w) & 63u) * (__float_as_uint(rb.w) & 63u));
     const float s = R.lnl_ii_coef * (qq * qq) * m_cell * dtc / (g2 * g);
-    const Words w = rng_words(R, first, step, 1u);
-    const float U = unit01(w.w1);
-    float cchi;
+    const float U = unit01(w1);
+    // eps = 1 - cos chi and epc = 1 + cos chi, each formed without
+    // cancellation: in a small-angle collision cos chi lies within FP32
+    // rounding of 1, so sin chi = sqrt(1 - cos^2 chi) would lose most of its
+    // digits, while sin chi = sqrt(eps epc) keeps them
+    float eps, epc;
     if (!(s <= (float)kNanbuSHi)) {
-        cchi = 2.0f * U - 1.0f;
+        eps = 2.0f * (1.0f - U);   // isotropic: cos chi = 2U - 1 (both exact in FP32)
+        epc = 2.0f * U;
     } else {
         const float A = nanbu_A(R, s);
         // ln(U + (1-U) e^-2A): for small A the sum is close to 1 and log1p of
@@ -244,12 +249,12 @@ __device__ __forceinline__ void collide(const RunDev& R, float4& ra, float4& rb,
         // spacing of expm1 near -1 while U is small as well
         const float lnarg = A < 0.5f ? log1pf((1.0f - U) * expm1f(-2.0f * A))
                                      : logf(U + (1.0f - U) * expf(-2.0f * A));
-        cchi = 1.0f + lnarg / A;
-        cchi = fminf(fmaxf(cchi, -1.0f), 1.0f);
+        eps = fminf(fmaxf(-lnarg / A, 0.0f), 2.0f);
+        epc = 2.0f - eps;
     }
-    const float schi = sqrtf(fmaxf(0.0f, 1.0f - cchi * cchi));
+    const float schi = sqrtf(eps * epc);
     float se, ce;
-    sincospif(2.0f * unit01(w.w2), &se, &ce);
+    sincospif(2.0f * unit01(w2), &se, &ce);
     const float gp = sqrtf(gy * gy + gz * gz);
     float hx, hy, hz;
     if (gp > 0.0f) {
@@ -261,11 +266,19 @@ __device__ __forceinline__ void collide(const RunDev& R, float4& ra, float4& rb,
         hy = g * ce;
         hz = g * se;
     }
-    const float dgx = 0.5f * (gx * (cchi - 1.0f) + hx * schi);
-    const float dgy = 0.5f * (gy * (cchi - 1.0f) + hy * schi);
-    const float dgz = 0.5f * (gz * (cchi - 1.0f) + hz * schi);
+    const float dgx = 0.5f * (hx * schi - gx * eps);
+    const float dgy = 0.5f * (hy * schi - gy * eps);
+    const float dgz = 0.5f * (hz * schi - gz * eps);
     ra.x += dgx; ra.y += dgy; ra.z += dgz;
     rb.x -= dgx; rb.y -= dgy; rb.z -= dgz;
+}
+
+// the same with the words of particle `first` at this step
+__device__ __forceinline__ void collide(const RunDev& R, float4& ra, float4& rb, float dtc, float m_cell,
+                                        uint32_t first, uint32_t step)
+{
+    const Words w = rng_words(R, first, step, 1u);
+    collide_w(R, ra, rb, dtc, m_cell, w.w1, w.w2);
 }
 
 __device__ __forceinline__ void write_back(const RunDev& R, uint32_t slot, const float4& r)

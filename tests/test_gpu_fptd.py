@@ -100,7 +100,7 @@ def test_busy_run_matches_oracle(E):
     q1 = rp.species.qmax + 1
     assert orc.fptd_hist.sum() >= 100, orc.fptd_hist.sum()
     diff = np.abs(f["hist"].astype(np.int64) - orc.fptd_hist[:q1]).sum()
-    assert diff <= 2 * t["guarded"], (diff, t["guarded"])
+    assert diff <= 2 * t["accepted"], (diff, t["accepted"])
     if diff == 0:
         assert np.array_equal(f["age_sum"].astype(np.int64), orc.fptd_sum[:q1])
     run.close()

@@ -37,12 +37,11 @@ def test_scaled_run_full_size(E):
     run.load(st)
     # velocities to the FP32 rounding of the collision arithmetic (tabulated
     # A(s), FP32 logarithms), as in the collision kernels' own lock-step tests
-    t, orc = P.lockstep(run, wl.params, st, 3, ne_cells=ne, vel_rel=2e-4)
+    t, orc = P.lockstep(run, wl.params, st, 3, ne_cells=ne, vel_rel=5e-5)
     assert _clean(t), t["first_bad"]
-    # with about 40 ions per zone cell, every ion near a decision surface
-    # excuses the ions of its cell and the 26 around it from the collision
-    # comparison: still nine in ten particle-steps are compared
-    assert t["guarded"] < 0.15 * wl.n * 3, t["guarded"]
+    # every particle is compared; few lie near a decision surface, and fewer
+    # still took the other side of one (explained by the oracle's probes)
+    assert t["guarded_frac"] < 0.02 and t["accepted_frac"] < 0.01, t
     # (at dt = 1 ns three steps see a few tens of ionisations and no wall
     # hits; the collision count below shows the pairing ran at full size)
     assert t["events_seen"][2] > 0, t["events_seen"]
@@ -62,7 +61,6 @@ def test_batched_scan_full_size(E):
         wl, h = wls[i], hs[i]
         s0 = int(b.diag(h)["steps"])
         orc = O.OracleRun(wl.params, states[i])
-        probe = O.OracleRun(wl.params, states[i], deposit=False)
         for s in range(s0, s0 + 2):
             g0 = b.state(h)
             orc.set_state({k: g0[k] for k in P.KEYS + ("q",)})
@@ -71,7 +69,7 @@ def test_batched_scan_full_size(E):
             orc.step(1)
             b.step(1)
             g1 = b.state(h)
-            r = P.compare_step(wl.params, g1, orc, probe=probe, g0=g0, step=s)
+            r = P.compare_step(wl.params, g1, orc, probes=P.Probes(wl.params, g0, s, orc))
             assert not (r["q"] or r["events"] or r["pos"] or r["vel"]), (i, s, r)
             checked += wl.n
     assert checked > 4 * 2e5

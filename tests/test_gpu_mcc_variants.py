@@ -34,7 +34,6 @@ def test_lockstep_double_elastic_warm_reflection(E):
     run = E.Run(rp, E=Ef)
     run.load(st)
     orc = O.OracleRun(rp, st, E=Ef)
-    probe = O.OracleRun(rp, st, E=Ef, deposit=False)
     seen = np.zeros(6, dtype=np.int64)
     doubles = 0
     for s in range(60):
@@ -45,7 +44,7 @@ def test_lockstep_double_elastic_warm_reflection(E):
         orc.step(1)
         run.step(1)
         g1 = run.state()
-        r = P.compare_step(rp, g1, orc, probe=probe, g0=g0, step=s)
+        r = P.compare_step(rp, g1, orc, probes=P.Probes(rp, g0, s, orc))
         assert not (r["q"] or r["events"] or r["pos"] or r["vel"]), (s, r)
         for b in range(6):
             seen[b] += int(((orc.events >> b) & 1).sum())

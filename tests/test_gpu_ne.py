@@ -94,14 +94,12 @@ def _lockstep_ne(E, update_every, steps=100):
     run = E.Run(rp, E=Ef)
     run.load(st)
     orc = O.OracleRun(rp, st, E=Ef)
-    probe = O.OracleRun(rp, st, E=Ef, deposit=False)
     excused = np.zeros(rp.ncells, dtype=bool)
     out = {"updates": 0, "ions_seen": 0, "excused_particles": 0, "handover": 0, "bad": []}
     for s in range(steps):
         if update_every and s and s % update_every == 0:
             run.update_ne()
             orc.update_ne()
-            probe.ne, probe.dlx, probe.dly = orc.ne.copy(), orc.dlx.copy(), orc.dly.copy()
             out["updates"] += 1
             c = run.cells()
             dep = run.diag(grids=True)["cell_charge"].astype(np.int64)
@@ -124,12 +122,14 @@ def _lockstep_ne(E, update_every, steps=100):
         orc.step(1)
         run.step(1)
         g1 = run.state()
+        hit = None
         if excused.any():
+            # cells whose electron record the device built from a deposit that
+            # differs by a guarded particle: their particles are exempt
             hit = excused[_cells_of(rp, g0["x"], g0["y"], g0["z"])] | \
                 excused[_cells_of(rp, orc.x, orc.y, orc.z)]
-            orc.guard[hit] |= O.G_CELLREC
             out["excused_particles"] += int(hit.sum())
-        r = P.compare_step(rp, g1, orc, probe=probe, g0=g0, step=s)
+        r = P.compare_step(rp, g1, orc, probes=P.Probes(rp, g0, s, orc), excuse=hit)
         out["handover"] += r["handover"]
         if r["q"] or r["events"] or r["pos"] or r["vel"]:
             i = r["detail"]["i"]

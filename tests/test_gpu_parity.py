@@ -48,10 +48,11 @@ def test_lockstep_busy_case_every_event_type(E):
     # every event type occurs (the oracle alone over seeds 4-8 sees 140-170
     # wall hits, 34-47 ionisations and 15-26 charge exchanges in these steps)
     assert wall > 50 and ion > 15 and cx > 5, t["events_seen"]
-    # tallies agree up to guarded boundary outcomes
+    # tallies agree up to the outcomes the probes explained (each moves one
+    # count from one bin to another)
     d = run.diag()
-    assert np.abs(d["lost"] - orc.lost()).sum() <= t["guarded"]
-    assert np.abs(d["extracted"] - orc.extracted()).sum() <= t["guarded"]
+    assert np.abs(d["lost"] - orc.lost()).sum() <= 2 * t["accepted"]
+    assert np.abs(d["extracted"] - orc.extracted()).sum() <= 2 * t["accepted"]
     assert d["ke_lost_eV"] == pytest.approx(orc.tally.ke_lost_eV, rel=1e-4)
     run.close()
 
@@ -63,6 +64,9 @@ def test_lockstep_small_config_1000_steps(E):
     run.load(st)
     t, orc = P.lockstep(run, wl.params, st, wl.steps)
     assert_clean(t)
+    print(f"\n[small plain run, 1000 steps] flagged near a decision surface: {t['guarded_frac']:.2e} of "
+          f"particle-steps; other side taken (explained by the probes): {t['accepted']}")
+    assert t["guarded_frac"] < 0.01 and t["accepted_frac"] < 1e-3, t
     run.close()
 
 
