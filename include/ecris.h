@@ -342,7 +342,9 @@ ecris_status ecris_get_profile(ecris_ctx* ctx, ecris_profile* out);
 typedef struct {
     int32_t sort_every;
     int32_t blocks_per_sm;  /* batches: resident step-kernel blocks per SM (0: as many as fit) */
-    int32_t reserved[6];    /* set to 0 */
+    int32_t threads;        /* batches: step-kernel threads per block, 128, 256 or 512 (0: 256) */
+    int32_t particles_per_thread;   /* batches: particles per thread and tile, 1, 2 or 4 (0: 2) */
+    int32_t reserved[4];    /* set to 0 */
 } ecris_tuning;
 ecris_status ecris_set_tuning(ecris_ctx* ctx, const ecris_tuning* t);
 
@@ -403,13 +405,23 @@ ecris_status ecris_batch_memory(const ecris_batch* b, size_t* used, size_t* budg
  * kernels of all runs, other_* sorts, deposit folds and step counters. */
 ecris_status ecris_batch_set_profiling(ecris_batch* b, int enable);
 ecris_status ecris_batch_get_profile(ecris_batch* b, ecris_profile* out);
-/* Launch-shape autotuner: for each candidate (resident step-kernel blocks
- * per SM, steps between particle sorts) times at least `trial_steps` steps of
- * the batch, in whole sort periods that each start with a sort, keeps the
- * candidate with the least time per step and returns it in *chosen (may be
- * NULL).  The trial steps are real steps of every run; no result depends on
- * the choice. */
+/* Launch-shape autotuner.  Times `trial_steps` steps of the batch (no sort
+ * among them) in each launch shape of the step kernel -- threads per block
+ * 128, 256 or 512 times particles per thread 1, 2 or 4 -- with as many
+ * resident blocks as fit; then, in the fastest shape, each count of resident
+ * blocks per SM; then each sort cadence (8, 32, 128 steps), in whole sort
+ * periods that each start with a sort.  Keeps the fastest of each and returns
+ * the choice in *chosen (may be NULL).  Before the trials every run's state
+ * (particles, tallies, deposit and time sums, first-passage records, step
+ * counter) is copied aside in device memory, and it is restored afterwards:
+ * the trials use no simulated time, and the runs continue from where they
+ * were.  ECRIS_ENOMEM if that copy does not fit (nothing is changed then).
+ * No result depends on the choice. */
 ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tuning* chosen);
+/* Set the batch's tuning directly (the fields of ecris_tuning: sort_every >= 1,
+ * blocks_per_sm >= 0, threads x particles_per_thread one of the shapes above
+ * or both 0).  No result depends on it. */
+ecris_status ecris_batch_set_tuning(ecris_batch* b, const ecris_tuning* t);
 
 /* ------------------------------------------------------------------------ */
 /* Served form: a request loop (a library thread) that keeps a batch on the  */

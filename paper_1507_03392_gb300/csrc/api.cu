@@ -383,6 +383,8 @@ struct ecris_ctx {
     uint32_t* d_nleave = nullptr;
     unsigned int* d_ticket = nullptr;
     uint32_t ntiles = 0;
+    uint32_t tile = kTile;      // particles per tile of the step kernel (a batch sets its launch shape's)
+    uint32_t btiles = 0;        // tiles of the run in its batch's launch shape
     RunDev* h_run = nullptr;    // parameter block passed by value to every kernel
     float* h_kdt = nullptr;     // pinned staging copy of the rate table
     double weight = 0.0;
@@ -624,6 +626,7 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.n = (uint32_t)ctx->n;
     R.n4 = (uint32_t)ctx->n4;
     R.ncells = (uint32_t)((size_t)h.nx * h.ny * h.nz);
+    R.tile = ctx->tile;
 }
 
 // The per-cell records the kernels read, {n_e, zone, delta_x, delta_y}, from
@@ -1240,12 +1243,13 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         CK(cudaMallocAsync((void**)&ctx->d_bad, 2 * sizeof(unsigned int), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_err, sizeof(uint32_t), ctx->stream));
         if (h.mcc.flags & kFCoulomb) {
-            const size_t slots = (cap / kTile + 1) * kTile;
+            // participant lists for tiles of up to kMaxTile particles
+            const size_t slots = cap + kMaxTile;
             CK(cudaMallocAsync((void**)&ctx->d_plist, slots * sizeof(uint4), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_cslot, cap * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_sslot, cap * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_pvel, slots * sizeof(float4), ctx->stream));
-            CK(cudaMallocAsync((void**)&ctx->d_tcount, (cap / kTile + 1) * sizeof(uint32_t), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_tcount, (cap / kMinTile + 1) * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_ckeys, cap * sizeof(unsigned long long), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_crec, cap * sizeof(float4), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_ccount, nc * sizeof(uint32_t), ctx->stream));
@@ -1598,7 +1602,8 @@ struct ecris_batch {
     bool own_stream = false;
     int sm_count = 0;
     int blocks_per_sm = 0;          // 0: as many as fit
-    int max_blocks_per_sm = 1;
+    int shape = kDefaultShape;      // launch shape of the batched step kernel
+    int max_bps[kStepShapes] = {};  // resident blocks per SM of each shape
     uint32_t sort_every = 32;
     size_t budget = 0, used = 0;
     std::string err;
@@ -1719,9 +1724,19 @@ ecris_status batch_upload(ecris_batch* b)
 ecris_status batch_items(ecris_batch* b)
 {
     std::vector<uint2> items;
-    for (size_t r = 0; r < b->runs.size(); ++r)
-        if (b->runs[r])
-            for (uint32_t t = 0; t < b->runs[r]->ntiles; ++t) items.push_back(make_uint2((uint32_t)r, t));
+    const uint32_t tile = shape_tile(b->shape), groups = tile / 4;
+    for (size_t r = 0; r < b->runs.size(); ++r) {
+        ecris_ctx* c = b->runs[r];
+        if (!c) continue;
+        // the run's tiles in the batch's launch shape
+        c->tile = tile;
+        if (c->h_run->tile != tile) {
+            c->h_run->tile = tile;
+            b->params_dirty = true;
+        }
+        c->btiles = (uint32_t)((c->n4 + groups - 1) / groups);
+        for (uint32_t t = 0; t < c->btiles; ++t) items.push_back(make_uint2((uint32_t)r, t));
+    }
     // the last upload must have read the staging copy before it is rewritten;
     // queued launches may still read the old device list, freed in stream order
     if (b->items_staged) BCK(cudaEventSynchronize(b->items_staged));
@@ -1754,7 +1769,8 @@ ecris_status batch_items(ecris_batch* b)
 // the runs that have them, and the step counters of the others
 int batch_bps(const ecris_batch* b)
 {
-    return b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, b->max_blocks_per_sm) : b->max_blocks_per_sm;
+    const int m = b->max_bps[b->shape];
+    return b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, m) : m;
 }
 
 cudaError_t batch_side_streams(ecris_batch* b)
@@ -1775,7 +1791,7 @@ cudaError_t batch_side_streams(ecris_batch* b)
 cudaError_t batch_launch(ecris_batch* b)
 {
     cudaError_t e = launch_step_batch(b->d_runs, b->d_items, b->nitems, b->sm_count * batch_bps(b), b->variants,
-                                      b->stream);
+                                      b->shape, b->stream);
     if (e == cudaSuccess) e = launch_leave_batch(b->d_runs, (uint32_t)b->runs.size(), b->d_ticket, b->stream);
     if (e == cudaSuccess) e = batch_side_streams(b);
     if (e == cudaSuccess) e = cudaEventRecord(b->side_fork, b->stream);
@@ -1787,7 +1803,7 @@ cudaError_t batch_launch(ecris_batch* b)
         if (used < kBatchSideStreams) e = cudaStreamWaitEvent(b->side[k], b->side_fork, 0);
         ++used;
         const uint32_t nc = (uint32_t)((size_t)c->h.nx * c->h.ny * c->h.nz);
-        if (e == cudaSuccess) e = launch_coulomb(*c->h_run, nc, c->ntiles, c->d_ticket, c->collide_grid, b->side[k]);
+        if (e == cudaSuccess) e = launch_coulomb(*c->h_run, nc, c->btiles, c->d_ticket, c->collide_grid, b->side[k]);
     }
     for (int k = 0; e == cudaSuccess && k < used && k < kBatchSideStreams; ++k) {
         e = cudaEventRecord(b->side_join[k], b->side[k]);
@@ -1879,7 +1895,7 @@ ecris_status ecris_batch_create(ecris_batch** out, int device, void* cuda_stream
         delete b;
         return ECRIS_ECUDA;
     }
-    b->max_blocks_per_sm = step_batch_blocks_per_sm();
+    for (int k = 0; k < kStepShapes; ++k) b->max_bps[k] = step_batch_blocks_per_sm(k);
     *out = b;
     return ECRIS_OK;
 }
@@ -2028,7 +2044,7 @@ ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps)
             // timed: the same launches as the graph, one by one
             BCK(b->timer.run(kKindStep, b->stream, [&] {
                 return launch_step_batch(b->d_runs, b->d_items, b->nitems, b->sm_count * batch_bps(b),
-                                         b->variants, b->stream);
+                                         b->variants, b->shape, b->stream);
             }));
             BCK(b->timer.run(kKindOther, b->stream, [&] {
                 return launch_leave_batch(b->d_runs, (uint32_t)b->runs.size(), b->d_ticket, b->stream);
@@ -2037,7 +2053,7 @@ ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps)
                 if (!c || !(c->h.mcc.flags & kFCoulomb)) continue;
                 const uint32_t nc = (uint32_t)((size_t)c->h.nx * c->h.ny * c->h.nz);
                 BCK(b->timer.run(kKindCoulomb, b->stream, [&] {
-                    return launch_coulomb(*c->h_run, nc, c->ntiles, c->d_ticket, c->collide_grid, b->stream);
+                    return launch_coulomb(*c->h_run, nc, c->btiles, c->d_ticket, c->collide_grid, b->stream);
                 }, kCoulombKernels));
             }
             BCK(b->timer.run(kKindOther, b->stream, [&] {
@@ -2190,59 +2206,226 @@ ecris_status ecris_batch_get_profile(ecris_batch* b, ecris_profile* out)
     return ECRIS_OK;
 }
 
+ecris_status ecris_batch_set_tuning(ecris_batch* b, const ecris_tuning* t)
+{
+    if (!b) return ECRIS_EINVAL;
+    if (!t) return bfail(b, ECRIS_EINVAL, "batch_set_tuning: NULL argument");
+    if (t->sort_every < 1 || t->blocks_per_sm < 0)
+        return bfail(b, ECRIS_EINVAL, "batch_set_tuning: need sort_every >= 1 and blocks_per_sm >= 0");
+    int shape = -1;
+    if (t->threads == 0 && t->particles_per_thread == 0) shape = kDefaultShape;
+    for (int k = 0; k < kStepShapes; ++k)
+        if (t->threads == kShapeThreads[k] && t->particles_per_thread == kShapeVec[k]) shape = k;
+    if (shape < 0)
+        return bfail(b, ECRIS_EINVAL,
+                     "batch_set_tuning: threads must be 128, 256 or 512 and particles_per_thread 1, 2 or 4 "
+                     "(both 0: 256 x 2)");
+    b->sort_every = (uint32_t)t->sort_every;
+    for (auto* c : b->runs)
+        if (c) {
+            c->sort_every = b->sort_every;
+            if (c->since_sort > c->sort_every) c->since_sort = c->sort_every;
+        }
+    b->blocks_per_sm = t->blocks_per_sm;
+    if (shape != b->shape) {
+        b->shape = shape;
+        b->layout_dirty = true;   // the runs' tiles and the work list change with the tile size
+    }
+    b->graph_dirty = true;
+    return ECRIS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Everything a step of a batch run changes, copied aside so that the
+// autotuner's trial steps can be undone: the current particle set, the
+// tallies, deposit and time sums, first-passage records, step counter and
+// error word on the device, and the host's step bookkeeping.
+struct RunSnapshot {
+    unsigned char* buf = nullptr;
+    size_t bytes = 0;
+    uint64_t steps_done = 0;
+    double time_s = 0.0;
+    uint32_t since_sort = 0, since_fold = 0, calls_since_load = 0;
+};
+
+template <class F>
+void snapshot_parts(ecris_ctx* c, F f)
+{
+    const size_t cap = c->cap, nc = c->cap_cells;
+    for (int k = 0; k < 6; ++k) f((void*)c->d_soa[k], cap * 4);
+    f((void*)c->d_meta, cap * 4);
+    f((void*)c->d_id, cap * 4);
+    f((void*)c->d_tally, kTallyWords * sizeof(unsigned long long));
+    f((void*)c->d_dep, nc * sizeof(unsigned long long));
+    f((void*)c->d_count, nc * sizeof(unsigned long long));
+    f((void*)c->d_charge, nc * sizeof(unsigned long long));
+    f((void*)c->d_birth, cap * 4);
+    f((void*)c->d_fptd, kFptdWords * sizeof(unsigned long long));
+    f((void*)c->d_step, sizeof(uint32_t));
+    f((void*)c->d_err, sizeof(uint32_t));
+}
+
+ecris_status snapshot_take(ecris_batch* b, ecris_ctx* c, RunSnapshot& sn)
+{
+    size_t total = 0;
+    snapshot_parts(c, [&](void*, size_t n) { total += (n + 255) & ~(size_t)255; });
+    BCK(cudaMallocAsync((void**)&sn.buf, total, b->stream));
+    sn.bytes = total;
+    size_t off = 0;
+    cudaError_t e = cudaSuccess;
+    snapshot_parts(c, [&](void* p, size_t n) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sn.buf + off, p, n, cudaMemcpyDeviceToDevice, b->stream);
+        off += (n + 255) & ~(size_t)255;
+    });
+    BCK(e);
+    sn.steps_done = c->steps_done;
+    sn.time_s = c->time_s;
+    sn.since_sort = c->since_sort;
+    sn.since_fold = c->since_fold;
+    sn.calls_since_load = c->calls_since_load;
+    return ECRIS_OK;
+}
+
+// copy back into the run's current particle set (a sort may have swapped the
+// sets since: the copies go wherever the arrays now are)
+ecris_status snapshot_restore(ecris_batch* b, ecris_ctx* c, RunSnapshot& sn)
+{
+    size_t off = 0;
+    cudaError_t e = cudaSuccess;
+    snapshot_parts(c, [&](void* p, size_t n) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p, sn.buf + off, n, cudaMemcpyDeviceToDevice, b->stream);
+        off += (n + 255) & ~(size_t)255;
+    });
+    BCK(e);
+    BCK(cudaFreeAsync(sn.buf, b->stream));
+    sn.buf = nullptr;
+    c->steps_done = sn.steps_done;
+    c->time_s = sn.time_s;
+    c->since_sort = sn.since_sort;
+    c->since_fold = sn.since_fold;
+    c->calls_since_load = sn.calls_since_load;
+    return ECRIS_OK;
+}
+
+// time per step of `steps` steps of the batch in its current tuning, with
+// no sort among them (hold = true) or in whole sort periods starting with a
+// sort; one untimed step first takes the graph capture out of the timing
+ecris_status time_steps(ecris_batch* b, uint32_t steps, bool hold, float* ms_per_step)
+{
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    BCK(cudaEventCreate(&t0));
+    BCK(cudaEventCreate(&t1));
+    const uint32_t keep = b->sort_every;
+    auto set_sort = [&](uint32_t every, bool due) {
+        for (auto* c : b->runs)
+            if (c) {
+                c->sort_every = every;
+                c->since_sort = due ? every : 0u;
+            }
+    };
+    if (hold) set_sort(0xFFFFFFFFu, false);
+    ecris_status st = ecris_batch_step(b, 1);
+    if (st == ECRIS_OK) {
+        if (!hold) set_sort(keep, true);
+        cudaEventRecord(t0, b->stream);
+        st = ecris_batch_step(b, steps);
+        cudaEventRecord(t1, b->stream);
+    }
+    if (cudaEventSynchronize(t1) != cudaSuccess && st == ECRIS_OK) st = ECRIS_ECUDA;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    *ms_per_step = ms / (float)(steps ? steps : 1);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    set_sort(keep, false);
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
 ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tuning* chosen)
 {
     if (!b) return ECRIS_EINVAL;
-    if (trial_steps == 0) return bfail(b, ECRIS_EINVAL, "batch_autotune: trial_steps must be > 0");
     BCK(cudaSetDevice(b->device));
-    cudaEvent_t t0, t1;
-    BCK(cudaEventCreate(&t0));
-    BCK(cudaEventCreate(&t1));
-    const int sorts[3] = {8, 32, 128};
-    float best = 1e30f;
-    int best_bps = b->max_blocks_per_sm, best_sort = (int)b->sort_every;
+    if (trial_steps < 1) trial_steps = 1;
+    // the runs' state before the trials, restored afterwards
+    std::vector<RunSnapshot> snaps(b->runs.size());
     ecris_status st = ECRIS_OK;
-    for (int bps = 1; bps <= b->max_blocks_per_sm && st == ECRIS_OK; ++bps) {
-        for (int k = 0; k < 3 && st == ECRIS_OK; ++k) {
-            b->blocks_per_sm = bps;
-            b->sort_every = (uint32_t)sorts[k];
-            for (auto* c : b->runs)
-                if (c) c->sort_every = b->sort_every;
-            b->graph_dirty = true;
-            st = ecris_batch_step(b, 1);   // capture outside the timing
-            if (st != ECRIS_OK) break;
-            // time whole sort periods, each starting with a sort, so every
-            // candidate pays its own share of sorting
-            for (auto* c : b->runs)
-                if (c) c->since_sort = c->sort_every;
-            const uint32_t steps = ((trial_steps + sorts[k] - 1) / sorts[k]) * sorts[k];
-            cudaEventRecord(t0, b->stream);
-            st = ecris_batch_step(b, steps);
-            cudaEventRecord(t1, b->stream);
-            if (cudaEventSynchronize(t1) != cudaSuccess) st = ECRIS_ECUDA;
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, t0, t1);
-            ms /= (float)steps;
-            if (st == ECRIS_OK && ms < best) {
-                best = ms;
-                best_bps = bps;
-                best_sort = sorts[k];
-            }
+    for (size_t r = 0; r < b->runs.size() && st == ECRIS_OK; ++r)
+        if (b->runs[r]) st = snapshot_take(b, b->runs[r], snaps[r]);
+    const int orig_shape = b->shape, orig_bps = b->blocks_per_sm;
+    const uint32_t orig_sort = b->sort_every;
+    int best_shape = orig_shape, best_bps = orig_bps;
+    uint32_t best_sort = orig_sort;
+    float best = 1e30f, ms = 0.0f;
+    auto apply = [&](int shape, int bps, uint32_t every) {
+        if (shape != b->shape) b->layout_dirty = true;
+        b->shape = shape;
+        b->blocks_per_sm = bps;
+        b->sort_every = every;
+        b->graph_dirty = true;
+    };
+    // 1. the launch shape (threads per block x particles per thread), as many
+    // resident blocks as fit, no sorts among the timed steps
+    for (int k = 0; k < kStepShapes && st == ECRIS_OK; ++k) {
+        apply(k, 0, orig_sort);
+        st = time_steps(b, trial_steps, true, &ms);
+        if (st == ECRIS_OK && ms < best) {
+            best = ms;
+            best_shape = k;
         }
     }
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
-    b->blocks_per_sm = best_bps;
-    b->sort_every = (uint32_t)best_sort;
+    // 2. resident blocks per SM of that shape
+    best = 1e30f;
+    for (int bps = 1; bps <= b->max_bps[best_shape] && st == ECRIS_OK; ++bps) {
+        apply(best_shape, bps, orig_sort);
+        st = time_steps(b, trial_steps, true, &ms);
+        if (st == ECRIS_OK && ms < best) {
+            best = ms;
+            best_bps = bps;
+        }
+    }
+    // 3. steps between sorts: whole sort periods, each starting with a sort,
+    // so that every cadence pays its own share of sorting
+    best = 1e30f;
+    const uint32_t cadences[3] = {8, 32, 128};
+    for (int k = 0; k < 3 && st == ECRIS_OK; ++k) {
+        apply(best_shape, best_bps, cadences[k]);
+        const uint32_t steps = ((trial_steps + cadences[k] - 1) / cadences[k]) * cadences[k];
+        st = time_steps(b, steps, false, &ms);
+        if (st == ECRIS_OK && ms < best) {
+            best = ms;
+            best_sort = cadences[k];
+        }
+    }
+    // undo the trial steps
+    for (size_t r = 0; r < b->runs.size(); ++r)
+        if (b->runs[r] && snaps[r].buf) {
+            const ecris_status s2 = snapshot_restore(b, b->runs[r], snaps[r]);
+            if (st == ECRIS_OK) st = s2;
+        }
+    if (st != ECRIS_OK) {
+        apply(orig_shape, orig_bps, orig_sort);
+        for (auto* c : b->runs)
+            if (c) c->sort_every = orig_sort;
+        return st;
+    }
+    apply(best_shape, best_bps, best_sort);
     for (auto* c : b->runs)
-        if (c) c->sort_every = b->sort_every;
-    b->graph_dirty = true;
+        if (c) c->sort_every = best_sort;
     if (chosen) {
         std::memset(chosen, 0, sizeof *chosen);
-        chosen->sort_every = best_sort;
+        chosen->sort_every = (int32_t)best_sort;
         chosen->blocks_per_sm = best_bps;
+        chosen->threads = kShapeThreads[best_shape];
+        chosen->particles_per_thread = kShapeVec[best_shape];
     }
-    return st;
+    return ECRIS_OK;
 }
 
 }  // extern "C"

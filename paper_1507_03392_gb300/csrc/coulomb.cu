@@ -185,8 +185,8 @@ __global__ void k_scatter(const __grid_constant__ RunDev R, uint32_t ntiles)
             uint4 pc = make_uint4(0u, kNoCell, 0u, 0u);   // (array slot, cell, id, -)
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (in) {
-                pc = R.plist[t * kTile + i];
-                v = R.pvel[t * kTile + i];
+                pc = R.plist[t * R.tile + i];
+                v = R.pvel[t * R.tile + i];
             }
             const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, pc.y, 1);
             const uint32_t heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || prev != pc.y);

@@ -203,6 +203,7 @@ extern "C" ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* 
     R.crec = reinterpret_cast<float4*>(base + kOffCrec);
     R.cslot = reinterpret_cast<uint32_t*>(base + kOffCslot);
     R.sslot = reinterpret_cast<uint32_t*>(base + kOffSslot);
+    R.tile = (uint32_t)kTile;   // the participant lists of k_na_pack, kTile slots a tile
     R.nanbu = reinterpret_cast<const float*>(base + kOffNanbu);
     R.nanbu_lnlo = (float)std::log(kNanbuSLo);
     R.nanbu_inv_dln = (float)((kNanbuN - 1) / std::log(kNanbuSHi / kNanbuSLo));

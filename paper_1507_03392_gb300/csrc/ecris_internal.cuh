@@ -147,7 +147,7 @@ struct alignas(16) RunDev {
                                  // such bound), and the largest n_e of the cold and warm cells
     unsigned long long *dep;     // packed deposit accumulator: count << 32 | charge
     unsigned long long *tally;   // kTallyWords
-    uint4 *plist;                // Coulomb participants of each tile: (slot, cell, id, 0), kTile slots a tile
+    uint4 *plist;                // Coulomb participants of each tile: (slot, cell, id, 0), `tile` slots a tile
     float4 *pvel;                // their (vx, vy, vz, Q as bits), same slots
     uint32_t *tcount;            // participants per tile
     uint32_t *ccount;            // Coulomb participants per cell (counted up by the step kernel,
@@ -172,6 +172,7 @@ struct alignas(16) RunDev {
     uint32_t n;                  // particles
     uint32_t n4;                 // float4 groups = ceil(n/4)
     uint32_t ncells;
+    uint32_t tile;               // particles per tile of the step kernel's launch shape
 };
 
 // ----------------------------------------------------------------------------
@@ -395,7 +396,16 @@ cudaError_t launch_probe(const RunDev& R, const ProbeDev& P, uint32_t n4, int sm
 
 // resident blocks per SM of the step kernel
 int step_blocks_per_sm();
-int step_batch_blocks_per_sm();
+// Launch shapes of the batched step kernel: threads per block x particles per
+// thread and tile, shape k = (kShapeThreads[k], kShapeVec[k]); tile sizes
+// from 128 to 2048 particles
+constexpr int kStepShapes = 9;
+constexpr int kDefaultShape = 4;   // 256 x 2, the one-run kernel's shape
+constexpr int kShapeThreads[kStepShapes] = {128, 128, 128, 256, 256, 256, 512, 512, 512};
+constexpr int kShapeVec[kStepShapes] = {1, 2, 4, 1, 2, 4, 1, 2, 4};
+constexpr int kMinTile = 128, kMaxTile = 2048;
+inline uint32_t shape_tile(int k) { return (uint32_t)(kShapeThreads[k] * kShapeVec[k]); }
+int step_batch_blocks_per_sm(int shape);
 // batch form: one persistent step-kernel launch over the work items (run,
 // tile) of many runs whose parameter blocks are in device memory (it leaves
 // the step counters alone); launch_bump_steps then advances the counters of
@@ -404,7 +414,7 @@ int step_batch_blocks_per_sm();
 // variants: launch the kernel with the opt-in processes' code (some run has
 // one of kFVariants)
 cudaError_t launch_step_batch(const RunDev* runs, const uint2* items, uint32_t nitems, int grid, bool variants,
-                              cudaStream_t s);
+                              int shape, cudaStream_t s);
 cudaError_t launch_bump_steps(const RunDev* runs, uint32_t nruns, cudaStream_t s);
 // message returned by ecris_last_error(NULL) on the calling thread
 void ecris_internal_set_thread_error(const char* msg);

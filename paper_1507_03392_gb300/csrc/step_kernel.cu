@@ -521,20 +521,32 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// One stage of the tile pipeline: SoA copies of a tile's particles.
+// One stage of the tile pipeline: SoA copies of a tile's particles (kG
+// float4 groups of four particles).
+template <int kG>
 struct Stage {
-    int4 x[kTileGroups], y[kTileGroups], z[kTileGroups];
-    float4 vx[kTileGroups], vy[kTileGroups], vz[kTileGroups];
-    uint4 meta[kTileGroups];
-    uint4 id[kTileGroups];
+    int4 x[kG], y[kG], z[kG];
+    float4 vx[kG], vy[kG], vz[kG];
+    uint4 meta[kG];
+    uint4 id[kG];
 };
 
+template <int kG>
 struct StepShared {
-    Stage st[2];
+    Stage<kG> st[2];
     RunDev rs[2];          // batch form: the stage's run parameter block (copied with the tile)
     uint32_t npart[2];     // Coulomb participants of the stage's tile
     uint64_t bar[2];
     int failed;
+};
+
+// Launch shape of the step kernel: kT threads per block, kV particles per
+// thread and tile (tile = kT kV particles), and the resident blocks per SM
+// asked of the register allocator (about 1280 threads per SM).
+template <int kT, int kV>
+struct Shape {
+    static constexpr int threads = kT, vec = kV, tile = kT * kV, groups = kT * kV / 4;
+    static constexpr int min_blocks = kT == 128 ? 10 : (kT == 256 ? ECRIS_STEP_MIN_BLOCKS : 2);
 };
 
 __device__ __forceinline__ float& sf(float4* a, uint32_t i) { return reinterpret_cast<float*>(a)[i]; }
@@ -543,10 +555,11 @@ __device__ __forceinline__ int32_t& si(int4* a, uint32_t i) { return reinterpret
 
 // issue the eight bulk loads of tile t into stage st (thread 0 only); in the
 // batch form also the run's parameter block into *rs, on the same barrier
-__device__ __forceinline__ void load_tile(const RunDev& R, Stage& st, uint64_t* bar, uint32_t t, RunDev* rs)
+template <int kG>
+__device__ __forceinline__ void load_tile(const RunDev& R, Stage<kG>& st, uint64_t* bar, uint32_t t, RunDev* rs)
 {
-    const uint32_t g0 = t * kTileGroups;
-    const uint32_t ng = min((uint32_t)kTileGroups, R.n4 - g0);
+    const uint32_t g0 = t * kG;
+    const uint32_t ng = min((uint32_t)kG, R.n4 - g0);
     const uint32_t bytes = ng * 16u;
     mbar_expect_tx(bar, 8u * bytes + (rs ? (uint32_t)sizeof(RunDev) : 0u));
     if (rs) bulk_load(rs, &R, (uint32_t)sizeof(RunDev), bar);
@@ -583,8 +596,9 @@ __device__ __forceinline__ void deposit_warp(const RunDev& R, uint32_t cell, uin
 // kernels: a slot in the tile's list (one shared-memory atomic per warp) and
 // a count in its cell (one global reduction per run of neighbouring lanes in
 // the same cell; the whole warp calls this)
-__device__ __forceinline__ void publish_warp(const RunDev& R, uint32_t& npart, uint32_t t, uint32_t slot_in_run,
-                                             uint32_t ck, uint32_t id, float vx, float vy, float vz, uint32_t Q)
+__device__ __forceinline__ void publish_warp(const RunDev& R, uint32_t& npart, uint32_t t, uint32_t tile,
+                                             uint32_t slot_in_run, uint32_t ck, uint32_t id, float vx, float vy,
+                                             float vz, uint32_t Q)
 {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t part = __ballot_sync(0xFFFFFFFFu, ck != kNoCell);
@@ -595,7 +609,7 @@ __device__ __forceinline__ void publish_warp(const RunDev& R, uint32_t& npart, u
     const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, ck, 1);
     const uint32_t heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || prev != ck);
     if (ck == kNoCell) return;
-    const uint32_t slot = t * kTile + base + (uint32_t)__popc(part & ((1u << lane) - 1u));
+    const uint32_t slot = t * tile + base + (uint32_t)__popc(part & ((1u << lane) - 1u));
     R.plist[slot] = make_uint4(slot_in_run, ck, id, 0u);
     R.pvel[slot] = make_float4(vx, vy, vz, __uint_as_float(Q));
     // every lane of a run shares ck, so all of them take part
@@ -642,11 +656,12 @@ __device__ __forceinline__ void list_leavers(const RunDev& R, bool leave, uint32
 // Persistent pass over the work items, two tiles in flight per block: while
 // the block advances one tile in one stage, the TMA engine brings the next
 // into the other stage; results leave through bulk stores.  The particles are
-// kept sorted by (ion/atom, cell), so each thread takes slots tid, tid + 256,
+// kept sorted by (ion/atom, cell), so each thread takes slots tid, tid + kT,
 // ... straight from the stage and the warps stay on one branch.
-template <bool kBatch, bool kVar, class Src>
-__device__ __forceinline__ void step_tiles(StepShared& S, const Src& src)
+template <bool kBatch, bool kVar, class Sh, class Src>
+__device__ __forceinline__ void step_tiles(StepShared<Sh::groups>& S, const Src& src)
 {
+    constexpr uint32_t kT = Sh::threads, kV = Sh::vec, kTl = Sh::tile, kG = Sh::groups;
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&S.bar[0], 1);
@@ -670,7 +685,7 @@ __device__ __forceinline__ void step_tiles(StepShared& S, const Src& src)
     // the barrier and used again two tiles on, past the next barrier.
     for (uint32_t it = 0; i < nitems; ++it, i += gridDim.x) {
         const uint32_t s = it & 1u;
-        Stage& st = S.st[s];
+        Stage<kG>& st = S.st[s];
         const uint2 item = src.item(i);
         const uint32_t in = i + gridDim.x;
         if (tid == 0 && in < nitems) {
@@ -686,14 +701,14 @@ __device__ __forceinline__ void step_tiles(StepShared& S, const Src& src)
             const RunDev& R = kBatch ? S.rs[s] : src.global(0);
             const bool coulomb = (R.flags & kFCoulomb) != 0;
             const uint32_t step = *R.step;
-            const uint32_t nslot = min((uint32_t)kTile, 4u * (R.n4 - t * kTileGroups));
-            // thread tid takes slots tid, tid + 256, ... (kVec of them) of the
+            const uint32_t nslot = min(kTl, 4u * (R.n4 - t * kG));
+            // thread tid takes slots tid, tid + kT, ... (kV of them) of the
             // tile: a warp covers 32 consecutive slots (one kind of particle, few
             // cells), the shared-memory accesses are free of bank conflicts, and
             // every particle runs through the same single copy of the code
 #pragma unroll 1
-            for (uint32_t j = 0; j < (uint32_t)kVec; ++j) {
-                const uint32_t k = (uint32_t)tid + j * kThreads;
+            for (uint32_t j = 0; j < kV; ++j) {
+                const uint32_t k = (uint32_t)tid + j * kT;
                 uint32_t meta = k < nslot ? su(st.meta, k) : kStPad;
                 int32_t x = si(st.x, k), y = si(st.y, k), z = si(st.z, k);
                 float vx = sf(st.vx, k), vy = sf(st.vy, k), vz = sf(st.vz, k);
@@ -701,13 +716,13 @@ __device__ __forceinline__ void step_tiles(StepShared& S, const Src& src)
                 uint32_t ck, dc;
                 const bool leave = step_particle<kVar>(R, id, step, x, y, z, vx, vy, vz, meta, ck, dc);
                 deposit_warp(R, dc, meta & kQMask);
-                list_leavers(R, leave, t * kTile + k);
+                list_leavers(R, leave, t * kTl + k);
                 if (k < nslot) {
                     si(st.x, k) = x; si(st.y, k) = y; si(st.z, k) = z;
                     sf(st.vx, k) = vx; sf(st.vy, k) = vy; sf(st.vz, k) = vz;
                     su(st.meta, k) = meta;
                 }
-                if (coulomb) publish_warp(R, S.npart[s], t, t * kTile + k, ck, id, vx, vy, vz, meta & kQMask);
+                if (coulomb) publish_warp(R, S.npart[s], t, kTl, t * kTl + k, ck, id, vx, vy, vz, meta & kQMask);
             }
         }
         fence_proxy_async();    // make this thread's stage writes visible to the bulk stores
@@ -721,8 +736,8 @@ __device__ __forceinline__ void step_tiles(StepShared& S, const Src& src)
         if (tid == 0) {
             const RunDev& R = kBatch ? S.rs[s] : src.global(0);
             const bool coulomb = (R.flags & kFCoulomb) != 0;
-            const uint32_t g0 = t * kTileGroups;
-            const uint32_t bytes = min((uint32_t)kTileGroups, R.n4 - g0) * 16u;
+            const uint32_t g0 = t * kG;
+            const uint32_t bytes = min(kG, R.n4 - g0) * 16u;
             bulk_store(reinterpret_cast<int4*>(R.x) + g0, st.x, bytes);
             bulk_store(reinterpret_cast<int4*>(R.y) + g0, st.y, bytes);
             bulk_store(reinterpret_cast<int4*>(R.z) + g0, st.z, bytes);
@@ -746,22 +761,26 @@ __device__ __forceinline__ void step_tiles(StepShared& S, const Src& src)
     }
 }
 
+using DefaultShape = Shape<kThreads, kVec>;
+
 template <bool kVar>
 __global__ void __launch_bounds__(kThreads, kStepMinBlocks) k_step(const __grid_constant__ RunDev R, uint32_t ntiles)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    StepShared& S = *reinterpret_cast<StepShared*>(smem_raw);
-    step_tiles<false, kVar>(S, SingleRun{R, ntiles});
+    auto& S = *reinterpret_cast<StepShared<DefaultShape::groups>*>(smem_raw);
+    step_tiles<false, kVar, DefaultShape>(S, SingleRun{R, ntiles});
 }
 
-// batch form: one persistent launch over the tiles of many runs
-template <bool kVar>
-__global__ void __launch_bounds__(kThreads, kStepMinBlocks) k_step_batch(const RunDev* __restrict__ runs,
-                                                            const uint2* __restrict__ items, uint32_t nitems)
+// batch form: one persistent launch over the tiles of many runs, in one of
+// the launch shapes the batch autotuner chooses from
+template <bool kVar, class Sh>
+__global__ void __launch_bounds__(Sh::threads, Sh::min_blocks) k_step_batch(const RunDev* __restrict__ runs,
+                                                                            const uint2* __restrict__ items,
+                                                                            uint32_t nitems)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    StepShared& S = *reinterpret_cast<StepShared*>(smem_raw);
-    step_tiles<true, kVar>(S, BatchRuns{runs, items, nitems});
+    auto& S = *reinterpret_cast<StepShared<Sh::groups>*>(smem_raw);
+    step_tiles<true, kVar, Sh>(S, BatchRuns{runs, items, nitems});
 }
 
 // The leaver pass of one run: finish the step of every listed particle, add
@@ -948,7 +967,7 @@ cudaError_t launch_load_init(const LoadCheck& lc, float* const soa[6], const uin
 
 int step_blocks_per_sm()
 {
-    const int smem = (int)sizeof(StepShared);
+    const int smem = (int)sizeof(StepShared<DefaultShape::groups>);
     if (cudaFuncSetAttribute(k_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
         cudaFuncSetAttribute(k_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return 1;
@@ -959,32 +978,69 @@ int step_blocks_per_sm()
     return b < bv ? b : bv;
 }
 
-constexpr size_t kBatchSmem = sizeof(StepShared);
-
-int step_batch_blocks_per_sm()
+// the batch kernel of launch shape Sh: resident blocks per SM (the smaller
+// of its two instantiations), and the launch
+template <class Sh>
+int batch_bps()
 {
-    if (cudaFuncSetAttribute(k_step_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) !=
+    constexpr int smem = (int)sizeof(StepShared<Sh::groups>);
+    if (cudaFuncSetAttribute(k_step_batch<false, Sh>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(k_step_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) !=
+        cudaFuncSetAttribute(k_step_batch<true, Sh>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
             cudaSuccess)
         return 1;
     int b = 0, bv = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_batch<false>, kThreads, kBatchSmem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_batch<false, Sh>, Sh::threads, smem) !=
+            cudaSuccess ||
         b < 1)
         b = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bv, k_step_batch<true>, kThreads, kBatchSmem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bv, k_step_batch<true, Sh>, Sh::threads, smem) !=
+            cudaSuccess ||
         bv < 1)
         bv = 1;
     return b < bv ? b : bv;
 }
 
+template <class Sh>
+void batch_launch_shape(const RunDev* runs, const uint2* items, uint32_t nitems, int grid, bool variants,
+                        cudaStream_t s)
+{
+    constexpr size_t smem = sizeof(StepShared<Sh::groups>);
+    if (variants) k_step_batch<true, Sh><<<grid, Sh::threads, smem, s>>>(runs, items, nitems);
+    else k_step_batch<false, Sh><<<grid, Sh::threads, smem, s>>>(runs, items, nitems);
+}
+
+// apply F to the Shape type of launch shape k (kStepShapes of them)
+template <class F>
+auto with_shape(int k, F f)
+{
+    switch (k) {
+    case 0: return f(Shape<128, 1>{});
+    case 1: return f(Shape<128, 2>{});
+    case 2: return f(Shape<128, 4>{});
+    case 3: return f(Shape<256, 1>{});
+    case 5: return f(Shape<256, 4>{});
+    case 6: return f(Shape<512, 1>{});
+    case 7: return f(Shape<512, 2>{});
+    case 8: return f(Shape<512, 4>{});
+    default: return f(Shape<256, 2>{});
+    }
+}
+
+int step_batch_blocks_per_sm(int shape)
+{
+    return with_shape(shape, [](auto sh) { return batch_bps<decltype(sh)>(); });
+}
+
 cudaError_t launch_step_batch(const RunDev* runs, const uint2* items, uint32_t nitems, int grid, bool variants,
-                              cudaStream_t s)
+                              int shape, cudaStream_t s)
 {
     if (nitems > 0) {
         if (grid > (int)nitems) grid = (int)nitems;
-        if (variants) k_step_batch<true><<<grid, kThreads, kBatchSmem, s>>>(runs, items, nitems);
-        else k_step_batch<false><<<grid, kThreads, kBatchSmem, s>>>(runs, items, nitems);
+        with_shape(shape, [&](auto sh) {
+            batch_launch_shape<decltype(sh)>(runs, items, nitems, grid, variants, s);
+            return 0;
+        });
     }
     return cudaGetLastError();
 }
@@ -999,8 +1055,9 @@ cudaError_t launch_step(const RunDev& R, uint32_t ntiles, int grid, cudaStream_t
 {
     if (ntiles == 0) return cudaSuccess;
     if (grid > (int)ntiles) grid = (int)ntiles;
-    if ((R.flags & kFVariants) || R.btab) k_step<true><<<grid, kThreads, sizeof(StepShared), s>>>(R, ntiles);
-    else k_step<false><<<grid, kThreads, sizeof(StepShared), s>>>(R, ntiles);
+    constexpr size_t smem = sizeof(StepShared<DefaultShape::groups>);
+    if ((R.flags & kFVariants) || R.btab) k_step<true><<<grid, kThreads, smem, s>>>(R, ntiles);
+    else k_step<false><<<grid, kThreads, smem, s>>>(R, ntiles);
     return cudaGetLastError();
 }
 

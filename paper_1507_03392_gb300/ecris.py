@@ -76,7 +76,8 @@ class DiagOut(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("sort_every", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("threads", ctypes.c_int32), ("particles_per_thread", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Request(ctypes.Structure):
@@ -216,6 +217,8 @@ def _load():
     lib.ecris_batch_memory.restype = st
     lib.ecris_batch_autotune.argtypes = [P, ctypes.c_uint32, ctypes.POINTER(Tuning)]
     lib.ecris_batch_autotune.restype = st
+    lib.ecris_batch_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
+    lib.ecris_batch_set_tuning.restype = st
     lib.ecris_batch_set_profiling.argtypes = [P, ctypes.c_int]
     lib.ecris_batch_set_profiling.restype = st
     lib.ecris_batch_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
@@ -282,6 +285,7 @@ ecris_batch_probe_sample = LIB.ecris_batch_probe_sample
 ecris_batch_get_probes = LIB.ecris_batch_get_probes
 ecris_batch_memory = LIB.ecris_batch_memory
 ecris_batch_autotune = LIB.ecris_batch_autotune
+ecris_batch_set_tuning = LIB.ecris_batch_set_tuning
 ecris_batch_set_profiling = LIB.ecris_batch_set_profiling
 ecris_batch_get_profile = LIB.ecris_batch_get_profile
 ecris_server_create = LIB.ecris_server_create
@@ -466,9 +470,18 @@ class Batch:
         return u.value, b.value
 
     def autotune(self, trial_steps=4):
+        """choose the launch shape, blocks per SM and sort cadence by timing
+        (the runs' state is restored after the trials)"""
         t = Tuning()
         self._check(ecris_batch_autotune(self.b, int(trial_steps), ctypes.byref(t)))
-        return {"sort_every": t.sort_every, "blocks_per_sm": t.blocks_per_sm}
+        return {"sort_every": t.sort_every, "blocks_per_sm": t.blocks_per_sm, "threads": t.threads,
+                "particles_per_thread": t.particles_per_thread}
+
+    def set_tuning(self, sort_every=32, blocks_per_sm=0, threads=0, particles_per_thread=0):
+        t = Tuning()
+        t.sort_every, t.blocks_per_sm = int(sort_every), int(blocks_per_sm)
+        t.threads, t.particles_per_thread = int(threads), int(particles_per_thread)
+        self._check(ecris_batch_set_tuning(self.b, ctypes.byref(t)))
 
     def set_profiling(self, on=True):
         self._check(ecris_batch_set_profiling(self.b, 1 if on else 0))

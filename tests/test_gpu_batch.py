@@ -101,17 +101,47 @@ def test_memory_budget_admission(E):
     b.close()
 
 
-def test_autotune_keeps_results(E):
+def test_autotune_keeps_results_and_time(E):
+    # the tuner's trial steps are undone: after it the runs stand where they
+    # stood, and stepping on gives what the runs give alone
     specs = run_specs()
     b = E.Batch()
     hs = [b.add(rp, st, E=Ef) for rp, st, Ef in specs]
+    b.step(3)
+    before = [(b.state(h), b.diag(h, grids=True)) for h in hs]
     t = b.autotune(trial_steps=2)
     assert t["sort_every"] in (8, 32, 128) and t["blocks_per_sm"] >= 1
-    done = b.diag(hs[0])["steps"]
+    assert (t["threads"], t["particles_per_thread"]) in [(a, v) for a in (128, 256, 512) for v in (1, 2, 4)]
+    for h, ref in zip(hs, before):
+        same((b.state(h), b.diag(h, grids=True)), ref)
     b.step(5)
-    total = done + 5
     for h, (rp, st, Ef) in zip(hs, specs):
-        same((b.state(h), b.diag(h, grids=True)), alone(E, rp, st, Ef, total))
+        same((b.state(h), b.diag(h, grids=True)), alone(E, rp, st, Ef, 8))
+    b.close()
+
+
+@pytest.mark.parametrize("threads", [128, 256, 512])
+def test_every_launch_shape_gives_the_same_results(E, threads):
+    # threads per block x particles per thread change the tiles a block
+    # streams and the work list; each run's result is that of the run alone
+    specs = run_specs()
+    refs = [alone(E, rp, st, Ef, 7) for rp, st, Ef in specs]
+    for vec in (1, 2, 4):
+        b = E.Batch()
+        b.set_tuning(sort_every=4, threads=threads, particles_per_thread=vec)
+        hs = [b.add(rp, st, E=Ef) for rp, st, Ef in specs]
+        b.step(7)
+        for h, ref in zip(hs, refs):
+            same((b.state(h), b.diag(h, grids=True)), ref)
+        b.close()
+
+
+def test_set_tuning_rejects_unknown_shapes(E):
+    b = E.Batch()
+    with pytest.raises(E.EcrisError):
+        b.set_tuning(threads=384, particles_per_thread=2)
+    with pytest.raises(E.EcrisError):
+        b.set_tuning(sort_every=0)
     b.close()
 
 
