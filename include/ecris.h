@@ -436,10 +436,12 @@ typedef struct ecris_server ecris_server;
 
 /* A run to serve: the arguments of ecris_init_fields / ecris_load_ions (host
  * memory; everything is copied at submission) and the convergence rule.
- * Converged: over two consecutive windows the total extracted current and
- * the currents of the three strongest charge states each change by less
- * than rel_tol times the larger of the two values, with at least
- * min_events extractions in the window. */
+ * Converged (stationary): over two consecutive windows the total extracted
+ * current and the currents of the three strongest charge states each change
+ * by no more than the larger of rel_tol times the larger of the two values
+ * and three standard deviations of the change that the Poisson counts of
+ * the two windows allow, with at least min_events extractions in the
+ * window. */
 typedef struct {
     ecris_geometry geo;
     ecris_bfield bf;
@@ -498,6 +500,12 @@ ecris_status ecris_server_poll(ecris_server* s, int64_t ticket, ecris_result* ou
  * run has advanced one tick past the boundary its result belongs to. */
 ecris_status ecris_server_stats(ecris_server* s, double* now, int64_t* queued, int64_t* running, int64_t* done,
                                 double* ion_steps);
+/* How often the request loop has tuned the batch's launch shape (thread-safe).
+ * The loop tunes (as ecris_batch_autotune, without the sort-cadence trials,
+ * two trial steps a candidate) when runs are resident and their particle
+ * count has doubled or halved since the last tuning; the tuner restores every
+ * run's state, so no result depends on it. */
+ecris_status ecris_server_tunings(ecris_server* s, int64_t* count);
 
 /* Calibration as a served workload (Sec. II: for a given field the model
  * needs two inputs, the macroparticle weight w and the warm-electron

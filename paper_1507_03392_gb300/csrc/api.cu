@@ -2350,6 +2350,15 @@ extern "C" {
 
 ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tuning* chosen)
 {
+    return ecris::batch_autotune(b, trial_steps, true, chosen);
+}
+
+}  // extern "C"
+
+namespace ecris {
+
+ecris_status batch_autotune(ecris_batch* b, uint32_t trial_steps, bool cadence, ecris_tuning* chosen)
+{
     if (!b) return ECRIS_EINVAL;
     BCK(cudaSetDevice(b->device));
     if (trial_steps < 1) trial_steps = 1;
@@ -2360,6 +2369,11 @@ ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tu
         if (b->runs[r]) st = snapshot_take(b, b->runs[r], snaps[r]);
     const int orig_shape = b->shape, orig_bps = b->blocks_per_sm;
     const uint32_t orig_sort = b->sort_every;
+    // the trials run on the grouped layout: every run is sorted first (the
+    // state is restored afterwards anyway)
+    for (auto* c : b->runs)
+        if (c) c->since_sort = c->sort_every;
+    if (st == ECRIS_OK) st = ecris_batch_step(b, 1);
     int best_shape = orig_shape, best_bps = orig_bps;
     uint32_t best_sort = orig_sort;
     float best = 1e30f, ms = 0.0f;
@@ -2394,7 +2408,7 @@ ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tu
     // so that every cadence pays its own share of sorting
     best = 1e30f;
     const uint32_t cadences[3] = {8, 32, 128};
-    for (int k = 0; k < 3 && st == ECRIS_OK; ++k) {
+    for (int k = 0; k < 3 && st == ECRIS_OK && cadence; ++k) {
         apply(best_shape, best_bps, cadences[k]);
         const uint32_t steps = ((trial_steps + cadences[k] - 1) / cadences[k]) * cadences[k];
         st = time_steps(b, steps, false, &ms);
@@ -2412,12 +2426,20 @@ ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tu
     if (st != ECRIS_OK) {
         apply(orig_shape, orig_bps, orig_sort);
         for (auto* c : b->runs)
-            if (c) c->sort_every = orig_sort;
+            if (c) {
+                c->sort_every = orig_sort;
+                c->since_sort = orig_sort;
+            }
         return st;
     }
     apply(best_shape, best_bps, best_sort);
+    // the restored particles are in the order they had before the trials:
+    // every run regroups at its next step (the layout changes no result)
     for (auto* c : b->runs)
-        if (c) c->sort_every = best_sort;
+        if (c) {
+            c->sort_every = best_sort;
+            c->since_sort = best_sort;
+        }
     if (chosen) {
         std::memset(chosen, 0, sizeof *chosen);
         chosen->sort_every = (int32_t)best_sort;
@@ -2427,6 +2449,10 @@ ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tu
     }
     return ECRIS_OK;
 }
+
+}  // namespace ecris
+
+extern "C" {
 
 }  // extern "C"
 

@@ -436,6 +436,9 @@ struct TallySnapshot {
 // enqueue the copies of run `run`'s tallies into *dst (pinned) on the batch stream
 ecris_status batch_snapshot(ecris_batch* b, int32_t run, TallySnapshot* dst);
 cudaStream_t batch_stream(const ecris_batch* b);
+// the batch autotuner (ecris_batch_autotune); without `cadence` it keeps the
+// sort cadence and times launch shapes and resident blocks only
+ecris_status batch_autotune(ecris_batch* b, uint32_t trial_steps, bool cadence, ecris_tuning* chosen);
 // fill out (extracted, lost, currents, power, wall energy, collisions) from a
 // snapshot taken after `steps` steps of the run (time steps * dt)
 void batch_snapshot_diag(const ecris_batch* b, int32_t run, const TallySnapshot& snap, uint64_t steps,

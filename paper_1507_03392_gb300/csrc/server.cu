@@ -63,6 +63,7 @@ struct Served {
     int32_t run = -1;
     std::vector<int64_t> last_ext;   // extracted counts at the previous window boundary
     std::vector<double> last_cur;    // currents of the previous window
+    std::vector<int64_t> last_dn;    // extractions by Q in the previous window
     double last_energy_J = 0.0;      // energy carried out up to the previous window boundary
     bool have_prev = false;
     uint64_t issued = 0;             // steps enqueued for the run
@@ -103,6 +104,9 @@ struct ecris_server {
     int64_t next_job = 1;
     int64_t n_done = 0;
     double ion_steps = 0.0;
+    double resident = 0.0;          // particles of the runs in the batch (loop thread)
+    double tuned_at = 0.0;          // ... when the launch shape was last tuned
+    int64_t n_tunes = 0;
     std::thread loop;
     // recycled pinned snapshot slots and events (only the loop thread uses them)
     std::vector<ecris::TallySnapshot*> free_snaps;
@@ -181,12 +185,14 @@ bool converged(Served* v, const std::vector<int64_t>& ext, ecris_result& res)
     const ecris_request& r = v->req->r;
     const int q1 = r.sp.qmax + 1;
     std::vector<double> cur(q1, 0.0);
+    std::vector<int64_t> dn(q1, 0);
     int64_t events = 0;
     const double window_s = r.window_steps * r.dt;
+    const double per_charge = 1.602176634e-19 * r.weight / window_s;   // current of one extracted charge
     for (int q = 0; q < q1; ++q) {
-        const int64_t dn = ext[q] - (v->last_ext.empty() ? 0 : v->last_ext[q]);
-        events += dn;
-        cur[q] = q * 1.602176634e-19 * r.weight * (double)dn / window_s;
+        dn[q] = ext[q] - (v->last_ext.empty() ? 0 : v->last_ext[q]);
+        events += dn[q];
+        cur[q] = q * per_charge * (double)dn[q];
     }
     for (int q = 0; q < q1 && q < 64; ++q) res.current_A[q] = cur[q];
     // gas flow and power losses over the window (the power from the
@@ -197,21 +203,33 @@ bool converged(Served* v, const std::vector<int64_t>& ext, ecris_result& res)
     v->last_energy_J = energy;
     bool ok = false;
     if (v->have_prev && events >= r.min_events) {
-        // relative change against the larger of the two (two zero currents agree)
-        auto rel = [&](double a, double b) { return std::abs(a - b) <= r.rel_tol * std::max(std::abs(a), std::abs(b)); };
-        double tot = 0.0, tot_prev = 0.0;
+        // two windows agree when their currents differ by at most rel_tol times
+        // the larger, or by no more than the counting noise of the two windows
+        // allows (three standard deviations of the difference of their
+        // Poisson counts): the source is stationary when no drift shows above
+        // what the extraction counts can resolve.  Two zero currents agree.
+        auto agree = [&](double a, double b, double var_counts) {
+            const double noise = 3.0 * per_charge * std::sqrt(var_counts);
+            return std::abs(a - b) <= std::max(r.rel_tol * std::max(std::abs(a), std::abs(b)), noise);
+        };
+        double tot = 0.0, tot_prev = 0.0, var_tot = 0.0;
         for (int q = 0; q < q1; ++q) {
             tot += cur[q];
             tot_prev += v->last_cur[q];
+            var_tot += (double)q * q * (double)(dn[q] + v->last_dn[q]);
         }
-        ok = rel(tot, tot_prev);
+        ok = agree(tot, tot_prev, var_tot);
         std::vector<int> order(q1);
         for (int q = 0; q < q1; ++q) order[q] = q;
         std::sort(order.begin(), order.end(), [&](int a, int b) { return cur[a] > cur[b]; });
-        for (int k = 0; k < 3 && k < q1 && ok; ++k) ok = rel(cur[order[k]], v->last_cur[order[k]]);
+        for (int k = 0; k < 3 && k < q1 && ok; ++k) {
+            const int q = order[k];
+            ok = agree(cur[q], v->last_cur[q], (double)q * q * (double)(dn[q] + v->last_dn[q]));
+        }
     }
     v->last_ext = ext;
     v->last_cur = cur;
+    v->last_dn = dn;
     v->have_prev = true;
     return ok;
 }
@@ -322,6 +340,18 @@ void serve_loop(ecris_server* s)
             v->res.state = ECRIS_REQ_RUNNING;
             v->res.t_admit = now_s(s);
             s->active.push_back(v);
+            s->resident += (double)r.n;
+        }
+        // the launch shape for the resident mix: tuned again when the resident
+        // particles have doubled or halved since the last tuning (the tuner
+        // restores every run's state, so results are unaffected)
+        if (!s->active.empty() && (s->tuned_at <= 0.0 || s->resident >= 2.0 * s->tuned_at ||
+                                   s->resident <= 0.5 * s->tuned_at)) {
+            if (ecris::batch_autotune(s->batch, 2, false, nullptr) == ECRIS_OK) {
+                s->tuned_at = s->resident;
+                std::lock_guard<std::mutex> lock(s->mu);
+                ++s->n_tunes;
+            }
         }
         // 2. one tick of the whole batch, and the snapshots at window boundaries
         std::vector<Served*> taken;
@@ -389,6 +419,7 @@ void serve_loop(ecris_server* s)
                 taken.erase(it);
             }
             ecris_batch_remove_run(s->batch, v->run);
+            s->resident -= (double)v->req->r.n;
             give_slot(s, v);
             std::lock_guard<std::mutex> lock(s->mu);
             finish(s, v, rv.second,
@@ -553,6 +584,14 @@ ecris_status ecris_server_stats(ecris_server* s, double* now, int64_t* queued, i
     if (running) *running = (int64_t)s->active.size();
     if (done) *done = s->n_done;
     if (ion_steps) *ion_steps = s->ion_steps;
+    return ECRIS_OK;
+}
+
+ecris_status ecris_server_tunings(ecris_server* s, int64_t* count)
+{
+    if (!s || !count) return ECRIS_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    *count = s->n_tunes;
     return ECRIS_OK;
 }
 

@@ -238,6 +238,8 @@ def _load():
     i64 = ctypes.POINTER(ctypes.c_int64)
     lib.ecris_server_stats.argtypes = [P, d, i64, i64, i64, d]
     lib.ecris_server_stats.restype = st
+    lib.ecris_server_tunings.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.ecris_server_tunings.restype = st
     lib.ecris_server_calibrate.argtypes = [P, ctypes.POINTER(CalibRequest), i64]
     lib.ecris_server_calibrate.restype = st
     lib.ecris_server_calib_poll.argtypes = [P, ctypes.c_int64, ctypes.POINTER(CalibResult)]
@@ -294,6 +296,7 @@ ecris_server_last_error = LIB.ecris_server_last_error
 ecris_server_submit = LIB.ecris_server_submit
 ecris_server_poll = LIB.ecris_server_poll
 ecris_server_stats = LIB.ecris_server_stats
+ecris_server_tunings = LIB.ecris_server_tunings
 ecris_server_calibrate = LIB.ecris_server_calibrate
 ecris_server_calib_poll = LIB.ecris_server_calib_poll
 
@@ -593,8 +596,10 @@ class Server:
         ist = ctypes.c_double()
         ecris_server_stats(self.s, ctypes.byref(now), ctypes.byref(qd), ctypes.byref(rn), ctypes.byref(dn),
                            ctypes.byref(ist))
+        tn = ctypes.c_int64()
+        ecris_server_tunings(self.s, ctypes.byref(tn))
         return {"now": now.value, "queued": qd.value, "running": rn.value, "done": dn.value,
-                "ion_steps": ist.value}
+                "ion_steps": ist.value, "tunings": tn.value}
 
 
 FPTD_BINS = 120   # ECRIS_FPTD_BINS

@@ -210,14 +210,17 @@ SERVED_MESHES = ((32, 32, 64), (64, 64, 128), (96, 96, 192))
 
 
 def served_stream(seed: int = 5, rate_per_s: float = 20.0, duration_s: float = 2.0,
-                  n_range: tuple = (1e4, 8e6)):
+                  n_range: tuple = (1e4, 8e6), dt: float = 1e-7):
     """A served request stream: Poisson arrivals (rate_per_s) over duration_s.
 
     Each request is a parameter-scan run: species uniform over O, Ar, Kr;
     N log-uniform in n_range; mesh uniform over SERVED_MESHES; neutral density
     (gas flow) log-uniform 3e9-3e11 cm^-3; zone electron density log-uniform
     5e10-2e12 cm^-3 and warm-electron temperature 0.3-3 keV (microwave power);
-    every process of the step on.  Returns a list of (arrival time s, Workload).
+    every process of the step on; time step dt (0.1 us by default: 4096 steps
+    span 0.4 ms, about one ion confinement time, and a 256-step window of a
+    run of a few 1e5 particles or more extracts the 400 ions the convergence
+    rule asks for).  Returns a list of (arrival time s, Workload).
     """
     rng = np.random.default_rng(seed)
     lu = lambda lo, hi: math.exp(rng.uniform(math.log(lo), math.log(hi)))
@@ -231,7 +234,7 @@ def served_stream(seed: int = 5, rate_per_s: float = 20.0, duration_s: float = 2
         nx, ny, nz = SERVED_MESHES[int(rng.integers(len(SERVED_MESHES)))]
         n = int(round(lu(*n_range)))
         p = RunParams(species=sp, nx=nx, ny=ny, nz=nz, n0_cm3=lu(3e9, 3e11), ne_in_cm3=lu(5e10, 2e12),
-                      Te_warm_eV=lu(300.0, 3000.0), flags=F_ALL, seed=5000 + i)
+                      Te_warm_eV=lu(300.0, 3000.0), flags=F_ALL, seed=5000 + i, dt=dt)
         out.append((t, Workload(f"served_{i}_{sp.name}", p, n=n, steps=4096, atom_fraction=0.75,
                                 ion_qmax_init=min(8, sp.qmax - 1), atoms_fill_chamber=True)))
         i += 1

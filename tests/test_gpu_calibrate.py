@@ -65,10 +65,41 @@ def test_calibration_meets_reachable_targets(E):
     assert res["weight"][-1] == pytest.approx(2.0 * rp.weight, rel=0.1)
     assert res["Te_warm_eV"][-1] > rp.Te_warm_eV
     # the last run, served as a plain request with the same inputs, gives the same outputs
-    rp2 = dataclasses.replace(rp, Te_warm_eV=float(res["Te_warm_eV"][-1]))
+    rp2 = dataclasses.replace(rp, Te_warm_eV=float(res["Te_warm_eV"][-1]), weight=float(res["weight"][-1]))
     again = _wait(srv, srv.poll, srv.submit(rp2, st, weight=float(res["weight"][-1]), **RULE))
     assert again["flow_per_s"] == res["flow_per_s"][-1] and again["power_window_W"] == res["power_W"][-1]
     srv.close()
+    # the FP64 oracle over the same run: its last window's gas flow and power
+    F_o, P_o, n_out, n_left = oracle_window_outputs(rp2, st, RULE["window_steps"], RULE["max_steps"])
+    print(f"\n[calibration, final run] gas flow GPU {res['flow_per_s'][-1]:.6e} / oracle {F_o:.6e} per s "
+          f"({n_out} particles out in the window); power GPU {res['power_W'][-1]:.6e} / oracle {P_o:.6e} W "
+          f"({n_left} ions left)")
+    assert abs(res["flow_per_s"][-1] - F_o) <= max(0.01, 3.0 / np.sqrt(max(n_out, 1))) * F_o
+    assert abs(res["power_W"][-1] - P_o) <= max(0.01, 3.0 / np.sqrt(max(n_left, 1))) * P_o
+
+
+def oracle_window_outputs(rp, st, window, steps):
+    """Gas flow and power of the oracle run's last window (Sec. II: the two
+    outputs of the model): the flow is the weight times the particles (ions
+    and atoms) that went out through the aperture in the window, per second;
+    the power is the weight times the energy the ions that left in the window
+    carried out -- kinetic energy, the ionisation energies of their charge
+    state, and 3/2 T_ew for each of their electrons -- per second."""
+    from oracle import oracle as O
+    orc = O.OracleRun(rp, st, deposit=False)
+    orc.step(steps - window)
+    ext0, lost0, ke0 = orc.extracted().copy(), orc.lost().copy(), orc.tally.ke_lost_eV
+    orc.step(window)
+    d_ext, d_lost = orc.extracted() - ext0, orc.lost() - lost0
+    t_win = window * rp.dt
+    flow = rp.weight * float(d_ext.sum()) / t_win
+    ip, _ = rp.species.ladder()
+    e_eV = orc.tally.ke_lost_eV - ke0
+    ip_cum = np.concatenate([[0.0], np.cumsum(ip)])
+    for q in range(1, rp.species.qmax + 1):
+        e_eV += float(d_ext[q] + d_lost[q]) * (ip_cum[q] + 1.5 * q * rp.Te_warm_eV)
+    power = rp.weight * e_eV * 1.602176634e-19 / t_win
+    return flow, power, int(d_ext.sum()), int((d_ext[1:] + d_lost[1:]).sum())
 
 
 def test_calibration_rejects_invalid_jobs(E):
