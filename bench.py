@@ -26,6 +26,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -153,10 +154,36 @@ def make_workload(rank, n=None):
     return wl
 
 
-def cpu_baseline(wl, target_s=12.0, sample=200_000):
+def host_cpu():
+    """(logical cores, CPU model) of the host"""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                v = line.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    model = v
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return os.cpu_count() or 1, model or platform.machine()
+
+
+def cpu_baseline(wl, target_s=12.0, sample=100_000):
     """The oracle as it stands, on the host cores, over a bounded sample: the
-    benchmark workload on all cores and on one, and the small plain run."""
-    ncores = os.cpu_count() or 1
+    benchmark workload on all cores and on one core (the same sample), and
+    the small plain run on one core."""
+    ncores, model = host_cpu()
     os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
     from oracle import oracle as O
     from paper_1507_03392_gb300 import inputs as I
@@ -177,14 +204,15 @@ def cpu_baseline(wl, target_s=12.0, sample=200_000):
     cores = O.lib().or_set_threads(int(os.environ["OMP_NUM_THREADS"]))
     m, steps, value = timed(wl, sample, target_s)
     O.lib().or_set_threads(1)
-    m1, steps1, value1 = timed(wl, sample // 4, target_s / 3)
+    m1, steps1, value1 = timed(wl, sample, target_s / 3)
     small = I.config_small()
     ms, steps_s, value_s = timed(small, small.n, target_s / 3)
     O.lib().or_set_threads(cores)
     return {"value": value, "unit": "ion-steps/s", "cores": cores, "kind": "oracle",
+            "host": {"nproc": ncores, "cpu": model},
             "sample": f"first {m} of the {wl.n} particles of the workload, {steps} steps, FP64 C oracle",
             "one_core": {"value": value1, "cores": 1,
-                         "sample": f"first {m1} of the {wl.n} particles, {steps1} steps"},
+                         "sample": f"the same first {m1} particles, {steps1} steps"},
             "small_run": {"value": value_s, "cores": 1, "workload": small.name,
                           "sample": f"all {ms} particles, {steps_s} steps"}}
 
@@ -193,7 +221,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     wl = make_workload(0)
-    ncores = os.cpu_count() or 1
+    ncores, model = host_cpu()
     os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
     from oracle import oracle as O
     from paper_1507_03392_gb300 import inputs as I
@@ -221,6 +249,7 @@ def run_reference(args, rank, world):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(wl, coulomb=bool(wl.params.flags & I.F_COULOMB)),
         "cpu_baseline": {"value": value, "unit": "ion-steps/s", "cores": cores, "kind": "oracle",
+                         "host": {"nproc": ncores, "cpu": model},
                          "sample": f"first {m} of the {wl.n} particles, one time step per step"},
         "e2e": {"value": value, "unit": "ion-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

@@ -685,14 +685,24 @@ static void or_coulomb(const or_params *p, int64_t n, const int64_t *cell, const
     or_key *keys = (or_key *)malloc((size_t)(total > 0 ? total : 1) * sizeof(or_key));
     int64_t *fill = (int64_t *)malloc((size_t)nc * sizeof(int64_t));
     for (int64_t c = 0; c < nc; ++c) fill[c] = cnt[c];
+    /* each participant's pairing word (independent per particle) */
+    uint32_t *hash = (uint32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(uint32_t));
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         if (!part[i]) continue;
         uint32_t w[4];
         or_words(p->seed, (uint32_t)i, step, 1, w);
-        or_key k = {w[0], (uint32_t)i};
+        hash[i] = w[0];
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (!part[i]) continue;
+        or_key k = {hash[i], (uint32_t)i};
         keys[fill[cell[i]]++] = k;
     }
     double vcell = or_dx(p) * or_dy(p) * or_dz(p);
+    /* the cells are independent: each collides only its own ions */
+    int64_t pairs = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : pairs)
     for (int64_t c = 0; c < nc; ++c) {
         int64_t m = cnt[c + 1] - cnt[c];
         if (m < 2) continue;
@@ -705,17 +715,18 @@ static void or_coulomb(const or_params *p, int64_t n, const int64_t *cell, const
             or_collide(p, vx, vy, vz, q, k[1].pid, k[2].pid, n_m3, 0.5 * dt, step, k[1].pid);
             or_collide(p, vx, vy, vz, q, k[2].pid, k[0].pid, n_m3, 0.5 * dt, step, k[2].pid);
             for (int j = 0; j < 3; ++j) events[k[j].pid] |= OR_EV_COULOMB;
-            t->coulomb_pairs += 3;
+            pairs += 3;
             start = 3;
         }
         for (int64_t j = start; j + 1 < m; j += 2) {
             or_collide(p, vx, vy, vz, q, k[j].pid, k[j + 1].pid, n_m3, dt, step, k[j].pid);
             events[k[j].pid] |= OR_EV_COULOMB;
             events[k[j + 1].pid] |= OR_EV_COULOMB;
-            t->coulomb_pairs += 1;
+            pairs += 1;
         }
     }
-    free(cnt); free(keys); free(fill);
+    t->coulomb_pairs += pairs;
+    free(cnt); free(keys); free(fill); free(hash);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -938,7 +949,8 @@ void or_step(const or_params *p, const double *rates, const double *rates2, cons
     /* phase 2: ion-ion Coulomb collisions among the ions that stayed */
     if (p->flags & OR_F_COULOMB) or_coulomb(p, n, cell, part, vx, vy, vz, q, step, dt, events, t);
 
-    /* phase 3: wall / aperture bookkeeping, then phase 4: deposition */
+    /* phase 3: wall / aperture bookkeeping of the particles that left (in
+     * particle order: the FP64 energy tally adds in a fixed order) */
     for (int64_t i = 0; i < n; ++i) {
         if (status[i] & 1u) continue;
         if (leave[i] != OR_LEAVE_NONE) {
@@ -986,9 +998,17 @@ void or_step(const or_params *p, const double *rates, const double *rates2, cons
                 continue;
             }
         }
-        if (dep_count) {
+    }
+    /* phase 4: NGP deposition at the final positions (integer sums, so the
+     * order of the additions does not matter) */
+    if (dep_count) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            if (status[i] & 1u) continue;
             int64_t c = or_cell(p, x[i], y[i], z[i], NULL);
+#pragma omp atomic
             dep_count[c] += 1;
+#pragma omp atomic
             dep_charge[c] += q[i];
         }
     }
