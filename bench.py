@@ -36,12 +36,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# step kernel, per particle: reads x,y,z (fixed point), vx,vy,vz, meta and the
-# stable id (32 B), writes all but the id (28 B)
-ALGO_BYTES_STEP_KERNEL = 60
-# per Coulomb participant (an ion that stayed inside): its published record,
-# (slot, cell, id, -) and (v, Q), 32 B written
-ALGO_BYTES_PARTICIPANT = 32
+# algorithmic bytes of the hot-path scope table: per ion-step, the read and
+# write of x, y, z, vx, vy, vz and the meta word, 7 x 4 B each way (56 B);
+# with collisions between ions the whole step adds about 16 B (the pairing
+# keys and records), 72 B.  The step kernel's own 4-byte id read and the
+# collision pipeline's list traffic are the implementation's, not counted.
+ALGO_BYTES_STEP_KERNEL = 56
+ALGO_BYTES_STEP_COULOMB = 72
 
 
 def env_int(name, default):
@@ -69,11 +70,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(n_particles):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary
+def ncu_traffic(n_particles, name="k_step_traffic.json"):
+    """DRAM bytes per launch of a step kernel from the committed ncu summary
     (a capture on a smaller case, scaled by the particle count); None if the
     kernel's sources changed since it was measured."""
-    path = os.path.join(ROOT, "profiles", "k_step_traffic.json")
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             d = json.load(f)
@@ -317,6 +318,8 @@ def bench_batched(E, I, args, local, stream, flush, peak, peak_kind):
     k_ms = prof["step_ms"] / max(1, prof["step_launches"])
     algo = total * ALGO_BYTES_STEP_KERNEL
     achieved = algo / (k_ms * 1e-3) / 1e9
+    whole = value * ALGO_BYTES_STEP_KERNEL / 1e9
+    ktraffic = ncu_traffic(total, "k_step_batch_traffic.json")
     # the plain single-run form: the first runs of the scan, one at a time
     plain_ion_steps, plain_ms = 0, 0.0
     for wl, st in list(zip(wls, states))[: args.plain_runs]:
@@ -347,9 +350,14 @@ def bench_batched(E, I, args, local, stream, flush, peak, peak_kind):
         "tuning": tune,
         "roofline": {"bound": "hbm", "kernel": "k_step_batch", "achieved": achieved, "peak": peak,
                      "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "algorithmic_bytes_per_launch": algo, "kernel_ms": k_ms, "traffic": None,
+                     "algorithmic_bytes_per_launch": algo, "kernel_ms": k_ms, "traffic": ktraffic,
+                     "kernel_ms_from": "a profiled pass (the step's kernels launched one by one, after "
+                                       "the timed graph-replayed steps)",
                      "share_of_step": prof["step_ms"] / max(1e-9, prof["step_ms"] + prof["coulomb_ms"]
-                                                            + prof["other_ms"])},
+                                                            + prof["other_ms"]),
+                     "whole_step": {"bytes_per_ion_step": ALGO_BYTES_STEP_KERNEL, "achieved": whole,
+                                    "frac": whole / peak,
+                                    "note": "the timed graph-replayed steps' ion-steps/s times 56 B"}},
         "plain_single_run": {"value": plain, "unit": "ion-steps/s",
                              "runs": min(args.plain_runs, len(wls)),
                              "note": "the first runs of the scan stepped one at a time through ecris_step"},
@@ -558,7 +566,7 @@ def main():
         dist.barrier()
     sampler = ClockSampler(local)
     sampler.start()
-    run.set_profiling(True)
+    # the timed steps: each one CUDA graph replay, as a user's ecris_step runs
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     torch.cuda.synchronize()
@@ -570,25 +578,41 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    # then a timed pass with the library's per-kernel events (the step's
+    # kernels launched one by one) for the step kernel's launch time
+    run.set_profiling(True)
+    for k in range(min(args.steps, 200)):
+        flush.zero_()
+        run.step(1)
+    torch.cuda.synchronize()
     clocks = sampler.stop()
     prof = run.profile()
     run.set_profiling(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     value, total_s = replica_throughput(n * args.steps, 1e-3 * sum(step_ms), dist, "cuda")
     total_ms = 1e3 * total_s
-    launches = prof["step_launches"] + prof["coulomb_launches"] + prof["other_launches"]
+    # kernels launched in the timed steps: a graph replay holds the same
+    # kernels the profiled pass launched one by one, step for step
+    nprof_steps = min(args.steps, 200)
+    launches = int(round((prof["step_launches"] + prof["coulomb_launches"] + prof["other_launches"])
+                         * args.steps / nprof_steps))
 
     # roofline of the dominant kernel (the fused step kernel)
     k_ms = prof["step_ms"] / max(1, prof["step_launches"])
-    ions = int(run.diag()["alive_by_q"][1:].sum()) if coulomb else 0
-    algo = n * ALGO_BYTES_STEP_KERNEL + ions * ALGO_BYTES_PARTICIPANT
+    algo = n * ALGO_BYTES_STEP_KERNEL
     achieved = algo / (k_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
+    step_bytes = ALGO_BYTES_STEP_COULOMB if coulomb else ALGO_BYTES_STEP_KERNEL
+    whole = value * step_bytes / 1e9
     roofline = {"bound": "hbm", "kernel": "k_step", "achieved": achieved, "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": ncu_traffic(n), "algorithmic_bytes_per_launch": algo,
                 "kernel_ms": k_ms,
-                "share_of_step": prof["step_ms"] / max(1e-9, prof["step_ms"] + prof["coulomb_ms"] + prof["other_ms"])}
+                "kernel_ms_from": "a timed pass with per-kernel CUDA events after the graph-replayed steps",
+                "share_of_step": prof["step_ms"] / max(1e-9, prof["step_ms"] + prof["coulomb_ms"] + prof["other_ms"]),
+                "whole_step": {"bytes_per_ion_step": step_bytes, "achieved": whole, "frac": whole / peak,
+                               "note": "ion-steps/s of the timed (graph-replayed) steps times the algorithmic "
+                                       "bytes of a whole step"}}
 
     # end to end through the public API with host buffers: H2D of the state,
     # one step, D2H of the diagnostics, every iteration
