@@ -344,7 +344,9 @@ typedef struct {
     int32_t blocks_per_sm;  /* batches: resident step-kernel blocks per SM (0: as many as fit) */
     int32_t threads;        /* batches: step-kernel threads per block, 128, 256 or 512 (0: 256) */
     int32_t particles_per_thread;   /* batches: particles per thread and tile, 1, 2 or 4 (0: 2) */
-    int32_t reserved[4];    /* set to 0 */
+    int32_t stages;         /* batches: tiles held in shared memory per block, 2 or 3 (0: 3 where the
+                               shape has a three-stage form, else 2) */
+    int32_t reserved[3];    /* set to 0 */
 } ecris_tuning;
 ecris_status ecris_set_tuning(ecris_ctx* ctx, const ecris_tuning* t);
 
@@ -407,8 +409,9 @@ ecris_status ecris_batch_set_profiling(ecris_batch* b, int enable);
 ecris_status ecris_batch_get_profile(ecris_batch* b, ecris_profile* out);
 /* Launch-shape autotuner.  Times `trial_steps` steps of the batch (no sort
  * among them) in each launch shape of the step kernel -- threads per block
- * 128, 256 or 512 times particles per thread 1, 2 or 4 -- with as many
- * resident blocks as fit; then, in the fastest shape, each count of resident
+ * 128, 256 or 512 times particles per thread 1, 2 or 4 with two stages, and
+ * 128 x 2, 256 x 1 and 256 x 2 with three -- with as many resident blocks as
+ * fit; then, in the fastest shape, each count of resident
  * blocks per SM; then each sort cadence (8, 32, 128 steps), in whole sort
  * periods that each start with a sort.  Keeps the fastest of each and returns
  * the choice in *chosen (may be NULL).  Before the trials every run's state
@@ -419,8 +422,9 @@ ecris_status ecris_batch_get_profile(ecris_batch* b, ecris_profile* out);
  * No result depends on the choice. */
 ecris_status ecris_batch_autotune(ecris_batch* b, uint32_t trial_steps, ecris_tuning* chosen);
 /* Set the batch's tuning directly (the fields of ecris_tuning: sort_every >= 1,
- * blocks_per_sm >= 0, threads x particles_per_thread one of the shapes above
- * or both 0).  No result depends on it. */
+ * blocks_per_sm >= 0, threads x particles_per_thread x stages one of the
+ * shapes above, or threads and particles_per_thread both 0 for 256 x 2 with
+ * three stages; ECRIS_EINVAL otherwise).  No result depends on it. */
 ecris_status ecris_batch_set_tuning(ecris_batch* b, const ecris_tuning* t);
 
 /* ------------------------------------------------------------------------ */

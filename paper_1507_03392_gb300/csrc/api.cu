@@ -2213,13 +2213,17 @@ ecris_status ecris_batch_set_tuning(ecris_batch* b, const ecris_tuning* t)
     if (t->sort_every < 1 || t->blocks_per_sm < 0)
         return bfail(b, ECRIS_EINVAL, "batch_set_tuning: need sort_every >= 1 and blocks_per_sm >= 0");
     int shape = -1;
-    if (t->threads == 0 && t->particles_per_thread == 0) shape = kDefaultShape;
+    if (t->threads == 0 && t->particles_per_thread == 0 && t->stages >= 0 && t->stages <= 3 && t->stages != 1)
+        shape = t->stages == 2 ? 4 : kDefaultShape;   // 256 x 2 with two or three stages
+    // stages 0: the three-stage form where the shape has one
     for (int k = 0; k < kStepShapes; ++k)
-        if (t->threads == kShapeThreads[k] && t->particles_per_thread == kShapeVec[k]) shape = k;
+        if (t->threads == kShapeThreads[k] && t->particles_per_thread == kShapeVec[k] &&
+            (t->stages == kShapeStages[k] || (t->stages == 0 && (shape < 0 || kShapeStages[k] == 3))))
+            shape = k;
     if (shape < 0)
         return bfail(b, ECRIS_EINVAL,
-                     "batch_set_tuning: threads must be 128, 256 or 512 and particles_per_thread 1, 2 or 4 "
-                     "(both 0: 256 x 2)");
+                     "batch_set_tuning: threads must be 128, 256 or 512, particles_per_thread 1, 2 or 4 and "
+                     "stages 2, or 3 for 128 x 2, 256 x 1 and 256 x 2 (all 0: 256 x 2 x 3)");
     b->sort_every = (uint32_t)t->sort_every;
     for (auto* c : b->runs)
         if (c) {
@@ -2446,6 +2450,7 @@ ecris_status batch_autotune(ecris_batch* b, uint32_t trial_steps, bool cadence, 
         chosen->blocks_per_sm = best_bps;
         chosen->threads = kShapeThreads[best_shape];
         chosen->particles_per_thread = kShapeVec[best_shape];
+        chosen->stages = kShapeStages[best_shape];
     }
     return ECRIS_OK;
 }

@@ -229,19 +229,21 @@ __device__ __forceinline__ void bfield(const RunDev& R, float x, float y, float 
     float b0, b1, b2, s, c;
     if (z <= R.zm) {
         __sincosf(3.14159265358979f * (z * R.inv_zm), &s, &c);   // argument in [0, pi]
-        b0 = R.B_min + R.aL * (1.0f + c);
+        b0 = fmaf(R.aL, 1.0f + c, R.B_min);
         b1 = -R.aLk * s;
         b2 = -R.aLk2 * c;
     } else {
         __sincosf(3.14159265358979f * ((z - R.zm) * R.inv_zr), &s, &c);
-        b0 = R.B_min + R.aR * (1.0f - c);
+        b0 = fmaf(R.aR, 1.0f - c, R.B_min);
         b1 = R.aRk * s;
         b2 = R.aRk2 * c;
     }
-    const float r2 = x * x + y * y;
-    Bx = -0.5f * x * b1 + R.hex_c * (2.0f * x * y);
-    By = -0.5f * y * b1 + R.hex_c * (x * x - y * y);
-    Bz = b0 - 0.25f * r2 * b2;
+    // (FMAs written out: the step kernel is compiled without contraction)
+    const float hx = -0.5f * b1, hz = -0.25f * b2;
+    const float r2 = fmaf(x, x, y * y);
+    Bx = fmaf(hx, x, R.hex_c * (2.0f * x * y));
+    By = fmaf(hx, y, R.hex_c * fmaf(x, x, -y * y));
+    Bz = fmaf(hz, r2, b0);
 }
 
 // the same from the on-axis table: the segment's cubic in t and its
@@ -399,10 +401,11 @@ int step_blocks_per_sm();
 // Launch shapes of the batched step kernel: threads per block x particles per
 // thread and tile, shape k = (kShapeThreads[k], kShapeVec[k]); tile sizes
 // from 128 to 2048 particles
-constexpr int kStepShapes = 9;
-constexpr int kDefaultShape = 4;   // 256 x 2, the one-run kernel's shape
-constexpr int kShapeThreads[kStepShapes] = {128, 128, 128, 256, 256, 256, 512, 512, 512};
-constexpr int kShapeVec[kStepShapes] = {1, 2, 4, 1, 2, 4, 1, 2, 4};
+constexpr int kStepShapes = 12;
+constexpr int kDefaultShape = 11;   // 256 x 2 with three stages
+constexpr int kShapeThreads[kStepShapes] = {128, 128, 128, 256, 256, 256, 512, 512, 512, 128, 256, 256};
+constexpr int kShapeVec[kStepShapes] = {1, 2, 4, 1, 2, 4, 1, 2, 4, 2, 1, 2};
+constexpr int kShapeStages[kStepShapes] = {2, 2, 2, 2, 2, 2, 2, 2, 2, 3, 3, 3};
 constexpr int kMinTile = 128, kMaxTile = 2048;
 inline uint32_t shape_tile(int k) { return (uint32_t)(kShapeThreads[k] * kShapeVec[k]); }
 int step_batch_blocks_per_sm(int shape);

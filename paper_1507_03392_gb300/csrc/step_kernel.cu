@@ -37,11 +37,28 @@ __device__ __forceinline__ void emit(float sigma, float nx, float ny, float nz, 
     vz = vn * nz + t1 * e1z + t2 * e2z;
 }
 
+// square root through the approximate hardware instruction (relative error
+// of a few units in the last place): for quantities that only set a
+// probability or the size of a random kick, where that error is far below the
+// statistical resolution; the push itself uses no square root
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// |v|^2 + a, contraction written out
+__device__ __forceinline__ float norm2_plus(float vx, float vy, float vz, float a)
+{
+    return fmaf(vx, vx, fmaf(vy, vy, fmaf(vz, vz, a)));
+}
+
 // probability 1 - exp(-lam) of at least one event in a step; for small lam
 // the cubic Taylor polynomial is exact to FP32 rounding (error < lam^4 / 24)
 __device__ __forceinline__ float event_prob(float lam)
 {
-    if (lam < 1e-3f) return lam * (1.0f - lam * (0.5f - lam * (1.0f / 6.0f)));
+    if (lam < 1e-3f) return lam * fmaf(-lam, fmaf(-lam, 1.0f / 6.0f, 0.5f), 1.0f);
     return -expm1f(-lam);
 }
 
@@ -292,14 +309,14 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
         if (Q >= 1) {
             // either process with probability 1 - exp(-n0 (sigma_cx + sigma_el)
             // v_rel dt), shared in proportion to the cross sections
-            const float vrel = sqrtf(vx * vx + vy * vy + vz * vz + R.vth2);
+            const float vrel = sqrt_approx(norm2_plus(vx, vy, vz, R.vth2));
             const float scx = ((R.flags & kFCx) && Q != 2) ? R.n0s1 * (float)Q : 0.0f;
             const float sel = R.n0sel * (float)Q;
             const float pt = event_prob((scx + sel) * vrel * R.dt);
             if (fires(w.w1, pt)) coll = fires(w.w1, pt * (scx / (scx + sel))) ? 1u : 2u;
         }
     } else if ((R.flags & kFCx) && R.n0s1 > 0.0f && Q >= 1 && Q != 2) {
-        const float vrel = sqrtf(vx * vx + vy * vy + vz * vz + R.vth2);
+        const float vrel = sqrt_approx(norm2_plus(vx, vy, vz, R.vth2));
         const float p = event_prob(R.n0s1 * (float)Q * vrel * R.dt);
         if (fires(w.w1, p)) coll = 1u;
     }
@@ -331,9 +348,9 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
     }
     if ((R.flags & kFEikick) && Q >= 1) {
         const float qp = R.ei_pow == 1 ? (float)Q : (float)(Q * Q);
-        const float D = sqrtf(R.ei_coef[zone] * cr.x * qp);
-        const float ct = 2.0f * unit01(w.w2) - 1.0f;
-        const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+        const float D = sqrt_approx(R.ei_coef[zone] * cr.x * qp);
+        const float ct = fmaf(2.0f, unit01(w.w2), -1.0f);
+        const float st = sqrt_approx(fmaxf(0.0f, fmaf(-ct, ct, 1.0f)));
         // azimuth 2 pi u through the fast intrinsic, kept inside [-pi, pi]
         // where its absolute error is below 2^-21: (cos, sin)(2 pi u) =
         // -(cos, sin)(pi (2u - 1))
@@ -341,13 +358,13 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
         __sincosf(3.14159265358979f * (2.0f * unit01(w.w3) - 1.0f), &sp, &cp);
         sp = -sp;
         cp = -cp;
-        const float dxv = st * cp + cr.z, dyv = st * sp + cr.w, dzv = ct;
-        const float m2 = dxv * dxv + dyv * dyv + dzv * dzv;
+        const float dxv = fmaf(st, cp, cr.z), dyv = fmaf(st, sp, cr.w), dzv = ct;
+        const float m2 = norm2_plus(dxv, dyv, dzv, 0.0f);
         if (m2 > 0.0f) {
             const float k = D * rsqrtf(m2);
-            vx += k * dxv;
-            vy += k * dyv;
-            vz += k * dzv;
+            vx = fmaf(k, dxv, vx);
+            vy = fmaf(k, dyv, vy);
+            vz = fmaf(k, dzv, vz);
         }
     }
     if (Q >= 1 && (R.flags & kFCoulomb)) ckey = cell;
@@ -531,22 +548,27 @@ struct Stage {
     uint4 id[kG];
 };
 
-template <int kG>
+template <int kG, int kS>
 struct StepShared {
-    Stage<kG> st[2];
-    RunDev rs[2];          // batch form: the stage's run parameter block (copied with the tile)
-    uint32_t npart[2];     // Coulomb participants of the stage's tile
-    uint64_t bar[2];
+    Stage<kG> st[kS];
+    RunDev rs[kS];         // batch form: the stage's run parameter block (copied with the tile)
+    uint32_t npart[kS];    // Coulomb participants of the stage's tile
+    uint32_t lastk;        // the block's last tile loaded (counted from 0), ~0 before the first
+    uint64_t bar[kS];
     int failed;
 };
 
 // Launch shape of the step kernel: kT threads per block, kV particles per
-// thread and tile (tile = kT kV particles), and the resident blocks per SM
-// asked of the register allocator (about 1280 threads per SM).
-template <int kT, int kV>
+// thread and tile (tile = kT kV particles), kS pipeline stages in shared
+// memory, and the resident blocks per SM asked of the register allocator:
+// about 1280 threads per SM with two stages; with three, as many blocks as
+// the stages' shared memory leaves room for.
+template <int kT, int kV, int kS = 2>
 struct Shape {
-    static constexpr int threads = kT, vec = kV, tile = kT * kV, groups = kT * kV / 4;
-    static constexpr int min_blocks = kT == 128 ? 10 : (kT == 256 ? ECRIS_STEP_MIN_BLOCKS : 2);
+    static constexpr int threads = kT, vec = kV, stages = kS, tile = kT * kV, groups = kT * kV / 4;
+    static constexpr int min_blocks =
+        kS == 2 ? (kT == 128 ? 10 : (kT == 256 ? ECRIS_STEP_MIN_BLOCKS : 2))
+                : (kT * kV <= 256 ? (kT == 128 ? 8 : 5) : 4);
 };
 
 __device__ __forceinline__ float& sf(float4* a, uint32_t i) { return reinterpret_cast<float*>(a)[i]; }
@@ -575,21 +597,26 @@ __device__ __forceinline__ void load_tile(const RunDev& R, Stage<kG>& st, uint64
 
 // NGP deposition of one particle per lane (the whole warp calls it), summed
 // over runs of neighbouring lanes in the same cell (particles are kept sorted
-// by cell, so neighbours mostly are): one reduction over each run's lanes, and
-// the last lane of the run adds count << 32 | charge for it.
+// by cell, so neighbours mostly are): a segmented inclusive scan of the charge
+// over each run's lanes (shuffles that stay inside the run), and the last lane
+// of the run adds count << 32 | charge for it.
 __device__ __forceinline__ void deposit_warp(const RunDev& R, uint32_t cell, uint32_t Q)
 {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, cell, 1);
     const uint32_t heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || prev != cell);
-    const uint32_t upto = 0xFFFFFFFFu >> (31u - lane);                // lanes 0..lane
-    const uint32_t h = 31u - (uint32_t)__clz(heads & upto);           // first lane of the run
-    const uint32_t after = heads & ~upto;
-    const uint32_t tl = after ? (uint32_t)(__ffs(after) - 2) : 31u;    // last lane of the run
-    const uint32_t run = (0xFFFFFFFFu >> (31u - tl)) & (0xFFFFFFFFu << h);
-    const uint32_t q = __reduce_add_sync(run, Q);
-    if (lane == tl && cell != kNoCell)
-        atomicAdd(R.dep + cell, ((unsigned long long)(tl - h + 1u) << 32) | (unsigned long long)q);
+    const uint32_t h = 31u - (uint32_t)__clz(heads & (0xFFFFFFFFu >> (31u - lane)));   // first lane of the run
+    uint32_t q = Q;
+    if (__any_sync(0xFFFFFFFFu, Q != 0u)) {   // a warp of atoms deposits counts only
+#pragma unroll
+        for (uint32_t d = 1; d < 32u; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, q, d);
+            if (lane >= h + d) q += o;   // lane - d lies in the same run
+        }
+    }
+    const bool last = lane == 31u || ((heads >> (lane + 1u)) & 1u);
+    if (last && cell != kNoCell)
+        atomicAdd(R.dep + cell, ((unsigned long long)(lane - h + 1u) << 32) | (unsigned long long)q);
 }
 
 // Publish this lane's Coulomb participant (ck != kNoCell) for the collision
@@ -653,22 +680,32 @@ __device__ __forceinline__ void list_leavers(const RunDev& R, bool leave, uint32
     if (leave) R.leave[base + (uint32_t)__popc(m & ((1u << lane) - 1u))] = slot;
 }
 
-// Persistent pass over the work items, two tiles in flight per block: while
-// the block advances one tile in one stage, the TMA engine brings the next
-// into the other stage; results leave through bulk stores.  The particles are
-// kept sorted by (ion/atom, cell), so each thread takes slots tid, tid + kT,
-// ... straight from the stage and the warps stay on one branch.
+// wait until at most n of this thread's bulk store groups have not yet read
+// their shared memory
+template <int n>
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(n) : "memory"); }
+
+// Persistent pass over the work items with kS shared-memory stages: while the
+// block advances one tile, the TMA engine brings in the next and the bulk
+// stores of the previous ones drain.  As tile j starts, thread 0 loads tile
+// j + 1 into stage (j + 1) mod kS, which tile j + 1 - kS used last: with two
+// stages that is tile j - 1, whose stores (issued a moment before) must first
+// have read the stage; with three it is tile j - 2, whose stores had a whole
+// tile's time to do so.  The particles are kept sorted by (ion/atom, cell),
+// so each thread takes slots tid, tid + kT, ... straight from the stage and
+// the warps stay on one branch.
 template <bool kBatch, bool kVar, class Sh, class Src>
-__device__ __forceinline__ void step_tiles(StepShared<Sh::groups>& S, const Src& src)
+__device__ __forceinline__ void step_tiles(StepShared<Sh::groups, Sh::stages>& S, const Src& src)
 {
-    constexpr uint32_t kT = Sh::threads, kV = Sh::vec, kTl = Sh::tile, kG = Sh::groups;
+    constexpr uint32_t kT = Sh::threads, kV = Sh::vec, kTl = Sh::tile, kG = Sh::groups, kS = Sh::stages;
     const int tid = threadIdx.x;
     if (tid == 0) {
-        mbar_init(&S.bar[0], 1);
-        mbar_init(&S.bar[1], 1);
-        S.npart[0] = 0u;
-        S.npart[1] = 0u;
+        for (uint32_t u = 0; u < kS; ++u) {
+            mbar_init(&S.bar[u], 1);
+            S.npart[u] = 0u;
+        }
         S.failed = 0;
+        S.lastk = ~0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -676,26 +713,28 @@ __device__ __forceinline__ void step_tiles(StepShared<Sh::groups>& S, const Src&
     uint32_t i = blockIdx.x;
     if (tid == 0 && i < nitems) {
         const uint2 it0 = src.item(i);
+        S.lastk = 0u;
         load_tile(src.global(it0.x), S.st[0], &S.bar[0], it0.y, kBatch ? &S.rs[0] : nullptr);
     }
-    // One block barrier per tile, before the stores.  Stage s ^ 1 is free
-    // when a tile starts: every thread stopped reading or writing it before
-    // the previous tile's barrier, and thread 0 waits for its bulk stores to
-    // have read it.  A stage's participant count is reset by thread 0 after
-    // the barrier and used again two tiles on, past the next barrier.
+    // this tile's stage s and the parity ph of its barrier phase (with two
+    // stages both follow from the tile count it)
+    uint32_t s3 = 0, ph3 = 0;
     for (uint32_t it = 0; i < nitems; ++it, i += gridDim.x) {
-        const uint32_t s = it & 1u;
+        const uint32_t s = kS == 2 ? (it & 1u) : s3;
+        const uint32_t ph = kS == 2 ? ((it >> 1) & 1u) : ph3;
         Stage<kG>& st = S.st[s];
         const uint2 item = src.item(i);
         const uint32_t in = i + gridDim.x;
         if (tid == 0 && in < nitems) {
+            const uint32_t sn = s + 1u == kS ? 0u : s + 1u;
             const uint2 itn = src.item(in);
-            bulk_wait_read_all();   // the other stage's previous stores have read their data
-            load_tile(src.global(itn.x), S.st[s ^ 1u], &S.bar[s ^ 1u], itn.y, kBatch ? &S.rs[s ^ 1u] : nullptr);
+            bulk_wait_read<kS - 2>();   // the stores of the stage's last tile have read it
+            S.lastk = it + 1u;
+            load_tile(src.global(itn.x), S.st[sn], &S.bar[sn], itn.y, kBatch ? &S.rs[sn] : nullptr);
         }
         // a warp whose wait ran out (in any lane) leaves the tile alone; the
         // block learns of it at the barrier and stops there
-        const bool ok = __all_sync(0xFFFFFFFFu, mbar_wait(&S.bar[s], (it >> 1) & 1u));
+        const bool ok = __all_sync(0xFFFFFFFFu, mbar_wait(&S.bar[s], ph));
         const uint32_t t = item.y;
         if (ok) {
             const RunDev& R = kBatch ? S.rs[s] : src.global(0);
@@ -726,6 +765,10 @@ __device__ __forceinline__ void step_tiles(StepShared<Sh::groups>& S, const Src&
             }
         }
         fence_proxy_async();    // make this thread's stage writes visible to the bulk stores
+        // One block barrier per tile, before the stores: every thread has
+        // written its slots, and none reads the stage again before it is
+        // reloaded.  A stage's participant count is reset here and used
+        // again kS tiles on, past the next barrier.
         if (__syncthreads_or(ok ? 0 : 1)) {
             if (tid == 0) {
                 S.failed = 1;
@@ -746,17 +789,25 @@ __device__ __forceinline__ void step_tiles(StepShared<Sh::groups>& S, const Src&
             bulk_store(reinterpret_cast<float4*>(R.vz) + g0, st.vz, bytes);
             bulk_store(reinterpret_cast<uint4*>(R.meta) + g0, st.meta, bytes);
             bulk_commit();
-            // the stage's count is next used two tiles on, past the next barrier
             if (coulomb) R.tcount[t] = S.npart[s];
             S.npart[s] = 0u;
+        }
+        if (kS != 2 && ++s3 == kS) {
+            s3 = 0u;
+            ph3 ^= 1u;
         }
     }
     if (tid == 0) {
         bulk_wait_all();        // stores complete before the block retires
         if (S.failed) {
-            // the loads this block issued may still land: wait (bounded) for them
-            mbar_wait(&S.bar[0], 0u);
-            mbar_wait(&S.bar[1], 0u);
+            // loads issued into a stage may still land: the block's tile k
+            // went into stage k mod kS at phase k / kS; wait (bounded) for
+            // each stage's last one (phases complete in order)
+            const uint32_t last = S.lastk;
+            for (uint32_t u = 0; u < kS && u <= last && last != ~0u; ++u) {
+                const uint32_t k = last - (last - u) % kS;
+                mbar_wait(&S.bar[u], (k / kS) & 1u);
+            }
         }
     }
 }
@@ -767,7 +818,7 @@ template <bool kVar>
 __global__ void __launch_bounds__(kThreads, kStepMinBlocks) k_step(const __grid_constant__ RunDev R, uint32_t ntiles)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    auto& S = *reinterpret_cast<StepShared<DefaultShape::groups>*>(smem_raw);
+    auto& S = *reinterpret_cast<StepShared<DefaultShape::groups, DefaultShape::stages>*>(smem_raw);
     step_tiles<false, kVar, DefaultShape>(S, SingleRun{R, ntiles});
 }
 
@@ -779,7 +830,7 @@ __global__ void __launch_bounds__(Sh::threads, Sh::min_blocks) k_step_batch(cons
                                                                             uint32_t nitems)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    auto& S = *reinterpret_cast<StepShared<Sh::groups>*>(smem_raw);
+    auto& S = *reinterpret_cast<StepShared<Sh::groups, Sh::stages>*>(smem_raw);
     step_tiles<true, kVar, Sh>(S, BatchRuns{runs, items, nitems});
 }
 
@@ -967,7 +1018,7 @@ cudaError_t launch_load_init(const LoadCheck& lc, float* const soa[6], const uin
 
 int step_blocks_per_sm()
 {
-    const int smem = (int)sizeof(StepShared<DefaultShape::groups>);
+    const int smem = (int)sizeof(StepShared<DefaultShape::groups, DefaultShape::stages>);
     if (cudaFuncSetAttribute(k_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
         cudaFuncSetAttribute(k_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return 1;
@@ -983,7 +1034,7 @@ int step_blocks_per_sm()
 template <class Sh>
 int batch_bps()
 {
-    constexpr int smem = (int)sizeof(StepShared<Sh::groups>);
+    constexpr int smem = (int)sizeof(StepShared<Sh::groups, Sh::stages>);
     if (cudaFuncSetAttribute(k_step_batch<false, Sh>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
             cudaSuccess ||
         cudaFuncSetAttribute(k_step_batch<true, Sh>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
@@ -1005,7 +1056,7 @@ template <class Sh>
 void batch_launch_shape(const RunDev* runs, const uint2* items, uint32_t nitems, int grid, bool variants,
                         cudaStream_t s)
 {
-    constexpr size_t smem = sizeof(StepShared<Sh::groups>);
+    constexpr size_t smem = sizeof(StepShared<Sh::groups, Sh::stages>);
     if (variants) k_step_batch<true, Sh><<<grid, Sh::threads, smem, s>>>(runs, items, nitems);
     else k_step_batch<false, Sh><<<grid, Sh::threads, smem, s>>>(runs, items, nitems);
 }
@@ -1023,6 +1074,9 @@ auto with_shape(int k, F f)
     case 6: return f(Shape<512, 1>{});
     case 7: return f(Shape<512, 2>{});
     case 8: return f(Shape<512, 4>{});
+    case 9: return f(Shape<128, 2, 3>{});
+    case 10: return f(Shape<256, 1, 3>{});
+    case 11: return f(Shape<256, 2, 3>{});
     default: return f(Shape<256, 2>{});
     }
 }
@@ -1055,7 +1109,7 @@ cudaError_t launch_step(const RunDev& R, uint32_t ntiles, int grid, cudaStream_t
 {
     if (ntiles == 0) return cudaSuccess;
     if (grid > (int)ntiles) grid = (int)ntiles;
-    constexpr size_t smem = sizeof(StepShared<DefaultShape::groups>);
+    constexpr size_t smem = sizeof(StepShared<DefaultShape::groups, DefaultShape::stages>);
     if ((R.flags & kFVariants) || R.btab) k_step<true><<<grid, kThreads, smem, s>>>(R, ntiles);
     else k_step<false><<<grid, kThreads, smem, s>>>(R, ntiles);
     return cudaGetLastError();

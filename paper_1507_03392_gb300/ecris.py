@@ -77,7 +77,7 @@ class DiagOut(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("sort_every", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("particles_per_thread", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("stages", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Request(ctypes.Structure):
@@ -478,12 +478,12 @@ class Batch:
         t = Tuning()
         self._check(ecris_batch_autotune(self.b, int(trial_steps), ctypes.byref(t)))
         return {"sort_every": t.sort_every, "blocks_per_sm": t.blocks_per_sm, "threads": t.threads,
-                "particles_per_thread": t.particles_per_thread}
+                "particles_per_thread": t.particles_per_thread, "stages": t.stages}
 
-    def set_tuning(self, sort_every=32, blocks_per_sm=0, threads=0, particles_per_thread=0):
+    def set_tuning(self, sort_every=32, blocks_per_sm=0, threads=0, particles_per_thread=0, stages=0):
         t = Tuning()
         t.sort_every, t.blocks_per_sm = int(sort_every), int(blocks_per_sm)
-        t.threads, t.particles_per_thread = int(threads), int(particles_per_thread)
+        t.threads, t.particles_per_thread, t.stages = int(threads), int(particles_per_thread), int(stages)
         self._check(ecris_batch_set_tuning(self.b, ctypes.byref(t)))
 
     def set_profiling(self, on=True):

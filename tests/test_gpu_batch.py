@@ -111,7 +111,8 @@ def test_autotune_keeps_results_and_time(E):
     before = [(b.state(h), b.diag(h, grids=True)) for h in hs]
     t = b.autotune(trial_steps=2)
     assert t["sort_every"] in (8, 32, 128) and t["blocks_per_sm"] >= 1
-    assert (t["threads"], t["particles_per_thread"]) in [(a, v) for a in (128, 256, 512) for v in (1, 2, 4)]
+    shapes = [(a, v, 2) for a in (128, 256, 512) for v in (1, 2, 4)] + [(128, 2, 3), (256, 1, 3), (256, 2, 3)]
+    assert (t["threads"], t["particles_per_thread"], t["stages"]) in shapes
     for h, ref in zip(hs, before):
         same((b.state(h), b.diag(h, grids=True)), ref)
     b.step(5)
@@ -122,13 +123,15 @@ def test_autotune_keeps_results_and_time(E):
 
 @pytest.mark.parametrize("threads", [128, 256, 512])
 def test_every_launch_shape_gives_the_same_results(E, threads):
-    # threads per block x particles per thread change the tiles a block
-    # streams and the work list; each run's result is that of the run alone
+    # threads per block x particles per thread x pipeline stages change the
+    # tiles a block streams and the work list; each run's result is that of
+    # the run alone
     specs = run_specs()
     refs = [alone(E, rp, st, Ef, 7) for rp, st, Ef in specs]
-    for vec in (1, 2, 4):
+    shapes = [(v, 2) for v in (1, 2, 4)] + {128: [(2, 3)], 256: [(1, 3), (2, 3)], 512: []}[threads]
+    for vec, stages in shapes:
         b = E.Batch()
-        b.set_tuning(sort_every=4, threads=threads, particles_per_thread=vec)
+        b.set_tuning(sort_every=4, threads=threads, particles_per_thread=vec, stages=stages)
         hs = [b.add(rp, st, E=Ef) for rp, st, Ef in specs]
         b.step(7)
         for h, ref in zip(hs, refs):
@@ -140,6 +143,8 @@ def test_set_tuning_rejects_unknown_shapes(E):
     b = E.Batch()
     with pytest.raises(E.EcrisError):
         b.set_tuning(threads=384, particles_per_thread=2)
+    with pytest.raises(E.EcrisError):
+        b.set_tuning(threads=512, particles_per_thread=2, stages=3)
     with pytest.raises(E.EcrisError):
         b.set_tuning(sort_every=0)
     b.close()
