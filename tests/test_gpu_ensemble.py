@@ -6,14 +6,17 @@ Sec. III: the currents).
 The GPU and the oracle each run freely from the same initial state with the
 same counter-based random words.  Their histories stay identical until a
 decision within rounding of its surface goes the other way; after that a
-particle's history, and through it the ensemble, evolves independently.  The
-bar: every charge state's count within max(1 %, 3 sigma) of the oracle's,
-sigma = sqrt(N_oracle) its Poisson error.  For N >= 9e4 the 1 % bound is the
-binding one; the extraction-heavy run below reaches N >= 1e5 in its leading
-charge states, so the 1 % bar is tested there.  The runs of the two batched
-scans extract few ions in any affordable number of steps (a 1 cm aperture in
-a 6.4 cm chamber, a mirror), so their bins are held to 3 sigma and their event
-counts are printed beside the result.
+particle's history, and through it the ensemble, evolves independently.  With
+collisions between ions a single flip re-pairs a cell and the two runs soon
+become independent samples of the same process, so a count's difference has
+the variance of a difference of two Poisson counts, N_gpu + N_oracle.  The
+bar: every charge state's count within max(1 % of the oracle's,
+3 sqrt(N_gpu + N_oracle)).  The extraction-heavy run below (no collisions
+between ions, histories shared but for the flips) reaches N >= 1e5 in its
+leading charge states, and there the test asserts the 1 % bar on its own.  The
+runs of the two batched scans extract few ions in any affordable number of
+steps (a 1 cm aperture in a 6.4 cm chamber, a mirror), so their bins are held
+to the 3 sigma bound and their event counts are printed beside the result.
 """
 import dataclasses
 
@@ -61,10 +64,15 @@ def cases():
     return out
 
 
-def within(g, o):
-    """max(1 %, 3 sigma) of the oracle's count"""
+def bound(g, o):
+    """max(1 % of the oracle's count, 3 sigma of the difference of two
+    independent Poisson counts)"""
     g, o = np.asarray(g, np.float64), np.asarray(o, np.float64)
-    return np.abs(g - o) <= np.maximum(0.01 * o, 3.0 * np.sqrt(o))
+    return np.maximum(0.01 * o, 3.0 * np.sqrt(g + o))
+
+
+def within(g, o):
+    return np.abs(np.asarray(g, np.float64) - np.asarray(o, np.float64)) <= bound(g, o)
 
 
 @pytest.mark.parametrize("k", range(3))
@@ -93,15 +101,15 @@ def test_ensemble_csd_and_currents(E, k, capsys):
             if ext_o[q] or ext_g[q] or alive_o[q] or alive_g[q]:
                 re = abs(ext_g[q] - ext_o[q]) / max(ext_o[q], 1)
                 ra = abs(alive_g[q] - alive_o[q]) / max(alive_o[q], 1)
-                bound = max(0.01, 3.0 / np.sqrt(max(ext_o[q], 1)))
-                print(f"  {q:2d} {ext_g[q]:10d} / {ext_o[q]:<10d} {re:8.2e} {bound:8.2e} | "
+                bq = float(bound(ext_g[q], ext_o[q])) / max(ext_o[q], 1)
+                print(f"  {q:2d} {ext_g[q]:10d} / {ext_o[q]:<10d} {re:8.2e} {bq:8.2e} | "
                       f"{alive_g[q]:8d} / {alive_o[q]:<8d} {ra:8.2e}")
         print(f"  extracted charge (sum Q N): GPU {cur_g:.0f}, oracle {cur_o:.0f}, rel "
               f"{abs(cur_g - cur_o) / max(cur_o, 1):.2e}; charge states with >= 1e5 events: "
               f"{int((ext_o >= 100_000).sum())}")
     assert within(ext_g, ext_o).all(), (ext_g, ext_o)
     assert within(alive_g, alive_o).all(), (alive_g, alive_o)
-    assert abs(cur_g - cur_o) <= max(0.01 * cur_o, 3.0 * np.sqrt((charges ** 2 * ext_o).sum()))
+    assert abs(cur_g - cur_o) <= max(0.01 * cur_o, 3.0 * np.sqrt((charges ** 2 * (ext_g + ext_o)).sum()))
     if k == 0:
         # the 1 % bar is exercised: at least two charge states carry >= 1e5
         # extraction events (Poisson error below 0.32 %)
