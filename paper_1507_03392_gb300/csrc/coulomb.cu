@@ -207,17 +207,21 @@ __global__ void k_scatter(const __grid_constant__ RunDev R, uint32_t ntiles)
     }
 }
 
-// A(s) for 1e-3 <= s <= 6 from the table of ln A, linear in ln s
+// A(s) for 1e-3 <= s <= 6 from the table of ln A, linear in ln s.  The
+// logarithm that indexes the table and the exponential of the interpolated
+// ln A use the fast intrinsics: their errors (below 1e-6 in ln s and a few
+// units in the last place of A) move A by far less than the table's own
+// interpolation error.
 __device__ __forceinline__ float nanbu_A(const RunDev& R, float s)
 {
     if (s < (float)kNanbuSLo) return 1.0f / (-expm1f(-s));
-    float t = (logf(s) - R.nanbu_lnlo) * R.nanbu_inv_dln;
+    float t = (__logf(s) - R.nanbu_lnlo) * R.nanbu_inv_dln;
     t = fminf(fmaxf(t, 0.0f), (float)(kNanbuN - 1));
     int i = (int)t;
     if (i > kNanbuN - 2) i = kNanbuN - 2;
     const float f = t - (float)i;
     const float la = (1.0f - f) * __ldg(R.nanbu + i) + f * __ldg(R.nanbu + i + 1);
-    return expf(la);
+    return __expf(la);
 }
 
 // One collision over time dtc of the records ra, rb (vx, vy, vz, Q bits),
@@ -229,9 +233,13 @@ __device__ __forceinline__ void collide_w(const RunDev& R, float4& ra, float4& r
     const float gx = ra.x - rb.x, gy = ra.y - rb.y, gz = ra.z - rb.z;
     const float g2 = gx * gx + gy * gy + gz * gz;
     if (!(g2 > 0.0f)) return;
-    const float g = sqrtf(g2);
+    // 1/g through the approximate reciprocal square root (a few units in the
+    // last place): it sets s and the scattering geometry, not the angle's
+    // small-angle digits (those come from eps below)
+    const float rg = rsqrtf(g2);
+    const float g = g2 * rg;
     const float qq = (float)((__float_as_uint(ra.w) & 63u) * (__float_as_uint(rb.w) & 63u));
-    const float s = R.lnl_ii_coef * (qq * qq) * m_cell * dtc / (g2 * g);
+    const float s = R.lnl_ii_coef * (qq * qq) * m_cell * dtc * (rg * rg * rg);
     const float U = unit01(w1);
     // eps = 1 - cos chi and epc = 1 + cos chi, each formed without
     // cancellation: in a small-angle collision cos chi lies within FP32
@@ -249,18 +257,19 @@ __device__ __forceinline__ void collide_w(const RunDev& R, float4& ra, float4& r
         // spacing of expm1 near -1 while U is small as well
         const float lnarg = A < 0.5f ? log1pf((1.0f - U) * expm1f(-2.0f * A))
                                      : logf(U + (1.0f - U) * expf(-2.0f * A));
-        eps = fminf(fmaxf(-lnarg / A, 0.0f), 2.0f);
+        eps = fminf(fmaxf(__fdividef(-lnarg, A), 0.0f), 2.0f);
         epc = 2.0f - eps;
     }
-    const float schi = sqrtf(eps * epc);
+    const float schi = sqrt_approx(eps * epc);
     float se, ce;
-    sincospif(2.0f * unit01(w2), &se, &ce);
-    const float gp = sqrtf(gy * gy + gz * gz);
+    sincos_2pi(unit01(w2), &se, &ce);
+    const float gp2 = gy * gy + gz * gz;
     float hx, hy, hz;
-    if (gp > 0.0f) {
-        hx = gp * ce;
-        hy = -(gx * gy * ce + g * gz * se) / gp;
-        hz = -(gx * gz * ce - g * gy * se) / gp;
+    if (gp2 > 0.0f) {
+        const float rgp = rsqrtf(gp2);
+        hx = gp2 * rgp * ce;
+        hy = -(gx * gy * ce + g * gz * se) * rgp;
+        hz = -(gx * gz * ce - g * gy * se) * rgp;
     } else {
         hx = 0.0f;
         hy = g * ce;
@@ -289,16 +298,20 @@ __device__ __forceinline__ void write_back(const RunDev& R, uint32_t slot, const
     atomicOr(R.meta + slot, kEvCoulomb);   // result unused: a fire-and-forget reduction
 }
 
-// Shared-memory image of one range of cells (see the header).
+// Shared-memory image of one range of cells (see the header).  The pairing
+// key (hash << 32 | pid) is kept as its two words.
 struct CellSmem {
-    unsigned long long key[kCellCap];
+    uint32_t hash[kCellCap];
+    uint32_t pid[kCellCap];
     float4 rec[kCellCap];
     uint32_t slot[kCellCap];
     uint32_t sidx[kCellCap];          // sorted position -> index in the range
     uint2 start[kCellCap / 2 + 1];    // (sorted position, cell count): pairs from the front,
                                       // triplets from the back, so a warp runs one kind
+    uint32_t claim[kCellCap / 32];    // sorted positions taken by the 32-bit ranking
     uint32_t npair, ntrip;
     uint32_t s0, s1;
+    int tie;                          // two keys of a cell share their hash word
     unsigned long long ncoll;
 };
 
@@ -318,13 +331,17 @@ __device__ __forceinline__ uint32_t collide_entry(const RunDev& R, const K& key,
         write_back(R, slot[ib], rb);
         return 1u;
     }
-    // ranks 0, 1, 2: (0,1), (1,2), (2,0) over dt/2 each
+    // ranks 0, 1, 2: (0,1), (1,2), (2,0) over dt/2 each; the three pairs'
+    // random words do not depend on the velocities, so they are drawn first
     const uint32_t ic = sidx[p + 2];
     float4 rc = rec[ic];
     const float mc = (float)m;
-    collide(R, ra, rb, 0.5f * dt, mc, (uint32_t)key[ia], step);
-    collide(R, rb, rc, 0.5f * dt, mc, (uint32_t)key[ib], step);
-    collide(R, rc, ra, 0.5f * dt, mc, (uint32_t)key[ic], step);
+    const Words wa = rng_words(R, (uint32_t)key[ia], step, 1u);
+    const Words wb = rng_words(R, (uint32_t)key[ib], step, 1u);
+    const Words wc = rng_words(R, (uint32_t)key[ic], step, 1u);
+    collide_w(R, ra, rb, 0.5f * dt, mc, wa.w1, wa.w2);
+    collide_w(R, rb, rc, 0.5f * dt, mc, wb.w1, wb.w2);
+    collide_w(R, rc, ra, 0.5f * dt, mc, wc.w1, wc.w2);
     write_back(R, slot[ia], ra);
     write_back(R, slot[ib], rb);
     write_back(R, slot[ic], rc);
@@ -344,6 +361,36 @@ __device__ __forceinline__ uint32_t rank_in_cell(const K& key, uint32_t seg, uin
     }
     if (i < m) r0 += key[seg + i] < mine ? 1u : 0u;
     return r0 + r1;
+}
+
+// the same from the hash words alone: exact when the cell's hashes are
+// distinct (then the order by hash is the order by key); a tie gives two
+// participants the same rank, which the caller detects
+__device__ __forceinline__ uint32_t rank_in_cell32(const uint32_t* hash, uint32_t seg, uint32_t m, uint32_t mine)
+{
+    const uint32_t* h = hash + seg;
+    uint32_t r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+    uint32_t i = 0;
+    for (; i + 4 <= m; i += 4) {
+        r0 += h[i] < mine ? 1u : 0u;
+        r1 += h[i + 1] < mine ? 1u : 0u;
+        r2 += h[i + 2] < mine ? 1u : 0u;
+        r3 += h[i + 3] < mine ? 1u : 0u;
+    }
+    for (; i < m; ++i) r0 += h[i] < mine ? 1u : 0u;
+    return (r0 + r1) + (r2 + r3);
+}
+
+// the rank by the whole key (hash, then pid) from the two word arrays
+__device__ __forceinline__ uint32_t rank_in_cell64(const uint32_t* hash, const uint32_t* pid, uint32_t seg,
+                                                   uint32_t m, uint32_t mh, uint32_t mp)
+{
+    uint32_t r = 0;
+    for (uint32_t i = 0; i < m; ++i) {
+        const uint32_t h = hash[seg + i];
+        r += (h < mh || (h == mh && pid[seg + i] < mp)) ? 1u : 0u;
+    }
+    return r;
 }
 
 // kind of sorted place r in a cell of m: 1 starts a pair, 2 starts a triplet
@@ -379,48 +426,71 @@ __global__ void __launch_bounds__(256, 5) k_cells(const __grid_constant__ RunDev
         const uint32_t s0 = S.s0, n = S.s1 - S.s0;
         if (n <= (uint32_t)kCellCap) {
             for (uint32_t j = tid; j < n; j += blockDim.x) {
-                S.key[j] = R.ckeys[s0 + j];
+                const unsigned long long k = R.ckeys[s0 + j];
+                S.hash[j] = (uint32_t)(k >> 32);
+                S.pid[j] = (uint32_t)k;
                 S.rec[j] = R.crec[s0 + j];
                 S.slot[j] = R.cslot[s0 + j];
             }
+            for (uint32_t w = tid; w < kCellCap / 32; w += blockDim.x) S.claim[w] = 0u;
+            if (tid == 0) S.tie = 0;
             __syncthreads();
-            // ranks, and the list of pair / triplet starters
+            // ranks, and the list of pair / triplet starters.  First by the
+            // hash words alone, each participant claiming its sorted place;
+            // if two claim one place (hash words tie, about once in 2^32
+            // pairs), again by the whole key.
             const uint32_t end = (n + 31u) & ~31u;
-            for (uint32_t j = tid; j < end; j += blockDim.x) {
-                uint32_t kind = 0u, pos = 0u, m = 0u;
-                if (j < n) {
-                    const uint32_t cell = __float_as_uint(S.rec[j].w) >> 6;
-                    const uint32_t seg = R.coff[cell] - s0;
-                    m = R.coff[cell + 1] - R.coff[cell];
-                    const uint32_t r = rank_in_cell(S.key, seg, m, S.key[j]);
-                    pos = seg + r;
-                    S.sidx[pos] = j;
-                    kind = start_kind(r, m);
-                }
-                const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, kind == 1u);
-                const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, kind == 2u);
-                if (b1 | b2) {
-                    uint32_t base1 = 0, base2 = 0;
-                    if (lane == 0) {
-                        if (b1) base1 = atomicAdd(&S.npair, (uint32_t)__popc(b1));
-                        if (b2) base2 = atomicAdd(&S.ntrip, (uint32_t)__popc(b2));
+            for (int exact = 0; exact < 2; ++exact) {
+                for (uint32_t j = tid; j < end; j += blockDim.x) {
+                    uint32_t kind = 0u, pos = 0u, m = 0u;
+                    if (j < n) {
+                        const uint32_t cell = __float_as_uint(S.rec[j].w) >> 6;
+                        const uint32_t seg = R.coff[cell] - s0;
+                        m = R.coff[cell + 1] - R.coff[cell];
+                        uint32_t r;
+                        if (!exact) {
+                            r = rank_in_cell32(S.hash, seg, m, S.hash[j]);
+                            const uint32_t bit = 1u << ((seg + r) & 31u);
+                            if (atomicOr(&S.claim[(seg + r) >> 5], bit) & bit) S.tie = 1;
+                        } else {
+                            r = rank_in_cell64(S.hash, S.pid, seg, m, S.hash[j], S.pid[j]);
+                        }
+                        pos = seg + r;
+                        S.sidx[pos] = j;
+                        kind = start_kind(r, m);
                     }
-                    base1 = __shfl_sync(0xFFFFFFFFu, base1, 0);
-                    base2 = __shfl_sync(0xFFFFFFFFu, base2, 0);
-                    const uint32_t below = (1u << lane) - 1u;
-                    if (kind == 1u) S.start[base1 + (uint32_t)__popc(b1 & below)] = make_uint2(pos, m);
-                    if (kind == 2u) S.start[kCellCap / 2 - (base2 + (uint32_t)__popc(b2 & below))] = make_uint2(pos, m);
+                    const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, kind == 1u);
+                    const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, kind == 2u);
+                    if (b1 | b2) {
+                        uint32_t base1 = 0, base2 = 0;
+                        if (lane == 0) {
+                            if (b1) base1 = atomicAdd(&S.npair, (uint32_t)__popc(b1));
+                            if (b2) base2 = atomicAdd(&S.ntrip, (uint32_t)__popc(b2));
+                        }
+                        base1 = __shfl_sync(0xFFFFFFFFu, base1, 0);
+                        base2 = __shfl_sync(0xFFFFFFFFu, base2, 0);
+                        const uint32_t below = (1u << lane) - 1u;
+                        if (kind == 1u) S.start[base1 + (uint32_t)__popc(b1 & below)] = make_uint2(pos, m);
+                        if (kind == 2u)
+                            S.start[kCellCap / 2 - (base2 + (uint32_t)__popc(b2 & below))] = make_uint2(pos, m);
+                    }
                 }
+                __syncthreads();
+                if (exact || !S.tie) break;
+                // a tie: rebuild the lists by the whole key
+                if (tid == 0) {
+                    S.npair = 0u;
+                    S.ntrip = 0u;
+                }
+                __syncthreads();
             }
-            __syncthreads();
+            // triplets (three collisions in a row) first, so that they run
+            // beside the pairs instead of after them
             const uint32_t np = S.npair, nt = S.ntrip;
-            for (uint32_t e = tid; e < np; e += blockDim.x) {
-                const uint2 st = S.start[e];
-                ncoll += collide_entry(R, S.key, S.rec, S.slot, S.sidx, st.x, st.y, false, step);
-            }
-            for (uint32_t e = tid; e < nt; e += blockDim.x) {
-                const uint2 st = S.start[kCellCap / 2 - e];
-                ncoll += collide_entry(R, S.key, S.rec, S.slot, S.sidx, st.x, st.y, true, step);
+            for (uint32_t e = tid; e < nt + np; e += blockDim.x) {
+                const bool trip = e < nt;
+                const uint2 st = S.start[trip ? kCellCap / 2 - e : e - nt];
+                ncoll += collide_entry(R, S.pid, S.rec, S.slot, S.sidx, st.x, st.y, trip, step);
             }
         } else {
             // the same in global memory: sorted positions in sslot

@@ -205,6 +205,28 @@ __device__ __forceinline__ Words rng_words(const RunDev& R, uint32_t pid, uint32
     return philox(pid, step * 4u + st, R.seed_lo, R.seed_hi);
 }
 
+// square root through the approximate hardware instruction (relative error
+// of a few units in the last place): for quantities that only set a
+// probability, the size of a random kick or a scattering geometry, where that
+// error is far below the parity tolerance; the push itself uses no square root
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// (cos, sin)(2 pi u) for u in (0, 1] through the fast intrinsic, its argument
+// kept inside [-pi, pi] where the absolute error is below 2^-21:
+// (cos, sin)(2 pi u) = -(cos, sin)(pi (2u - 1))
+__device__ __forceinline__ void sincos_2pi(float u, float* s, float* c)
+{
+    float sp, cp;
+    __sincosf(3.14159265358979f * (2.0f * u - 1.0f), &sp, &cp);
+    *s = -sp;
+    *c = -cp;
+}
+
 // uniform in (0, 1]: (top 24 bits + 1) * 2^-24, exact in FP32
 __device__ __forceinline__ float unit01(uint32_t w)
 {

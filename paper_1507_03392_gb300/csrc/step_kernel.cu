@@ -37,17 +37,6 @@ __device__ __forceinline__ void emit(float sigma, float nx, float ny, float nz, 
     vz = vn * nz + t1 * e1z + t2 * e2z;
 }
 
-// square root through the approximate hardware instruction (relative error
-// of a few units in the last place): for quantities that only set a
-// probability or the size of a random kick, where that error is far below the
-// statistical resolution; the push itself uses no square root
-__device__ __forceinline__ float sqrt_approx(float x)
-{
-    float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
 // |v|^2 + a, contraction written out
 __device__ __forceinline__ float norm2_plus(float vx, float vy, float vz, float a)
 {
@@ -351,13 +340,8 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
         const float D = sqrt_approx(R.ei_coef[zone] * cr.x * qp);
         const float ct = fmaf(2.0f, unit01(w.w2), -1.0f);
         const float st = sqrt_approx(fmaxf(0.0f, fmaf(-ct, ct, 1.0f)));
-        // azimuth 2 pi u through the fast intrinsic, kept inside [-pi, pi]
-        // where its absolute error is below 2^-21: (cos, sin)(2 pi u) =
-        // -(cos, sin)(pi (2u - 1))
         float sp, cp;
-        __sincosf(3.14159265358979f * (2.0f * unit01(w.w3) - 1.0f), &sp, &cp);
-        sp = -sp;
-        cp = -cp;
+        sincos_2pi(unit01(w.w3), &sp, &cp);   // azimuth
         const float dxv = fmaf(st, cp, cr.z), dyv = fmaf(st, sp, cr.w), dzv = ct;
         const float m2 = norm2_plus(dxv, dyv, dzv, 0.0f);
         if (m2 > 0.0f) {

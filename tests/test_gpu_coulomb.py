@@ -162,3 +162,54 @@ def test_thousand_steps_every_process_with_coulomb_lockstep(E):
     d = run.diag()
     assert abs(d["coulomb_collisions"] - orc.tally.coulomb_pairs) <= 2 * t["accepted"]
     run.close()
+
+
+def tied_hash_pids(seed, step=0, n_search=1 << 18):
+    """two particle ids whose pairing hashes (stream-1 word 0 at `step`, the
+    oracle's Philox) are equal: the pairing order then falls to the ids"""
+    lo, hi = seed & 0xFFFFFFFF, seed >> 32
+    seen = {}
+    for pid in range(n_search):
+        h = int(O.philox([pid, 0, 4 * step + 1, 0], [lo, hi])[0])
+        if h in seen:
+            return seen[h], pid
+        seen[h] = pid
+    return None
+
+
+def test_tied_pairing_hashes_order_by_id(E):
+    # two ions of one cell whose 32-bit pairing hashes are equal (about one
+    # pair in 2^32): the kernel ranks by the hash words first and must fall
+    # back to the whole key (hash, id) for that cell, as the oracle orders
+    seed = 77
+    pair = tied_hash_pids(seed)
+    assert pair is not None
+    p1, p2 = pair
+    rp = I.RunParams(nx=8, ny=8, nz=16, flags=I.F_COULOMB, weight=5e7, dt=1e-8, seed=seed)
+    n = p2 + 1
+    rng = np.random.default_rng(5)
+    dx, dz = 2 * rp.R0 / rp.nx, rp.L / rp.nz
+    # atoms (no part in collisions) spread over the chamber's inner cells
+    x = rng.uniform(-0.5, 0.5, n) * rp.R0
+    y = rng.uniform(-0.5, 0.5, n) * rp.R0
+    z = rng.uniform(0.1, 0.9, n) * rp.L
+    q = np.zeros(n, dtype=np.uint8)
+    # five ions in one cell: the tied pair and three others, an odd count so
+    # that the order decides the triplet and the pair
+    ions = [p1, p2, 0, 1, 2] if p1 > 2 else [p1, p2, n - 1, n - 2, n - 3]
+    cx, cy, cz = 3, 4, 7
+    for k, p in enumerate(ions):
+        x[p] = -rp.R0 + (cx + 0.3 + 0.1 * k) * dx
+        y[p] = -rp.R0 + (cy + 0.5) * dx
+        z[p] = (cz + 0.5) * dz
+        q[p] = 3
+    sig = math.sqrt(0.5 * QE / (rp.species.mass_amu * AMU))
+    v = rng.normal(0, sig, (3, n))
+    st = {"x": x.astype(np.float32), "y": y.astype(np.float32), "z": z.astype(np.float32),
+          "vx": v[0].astype(np.float32), "vy": v[1].astype(np.float32), "vz": v[2].astype(np.float32), "q": q}
+    run = E.Run(rp)
+    run.load(st)
+    t, orc = P.lockstep(run, rp, st, 1, vel_rel=5e-5)
+    assert t["q"] == 0 and t["events"] == 0 and t["pos"] == 0 and t["vel"] == 0, t
+    assert run.diag()["coulomb_collisions"] == orc.tally.coulomb_pairs == 4
+    run.close()
