@@ -84,6 +84,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ R
 {
     __shared__ uint32_t wsum[kScanThreads / 32];
     __shared__ uint32_t s_tile, s_epoch, s_prefix;
+    pdl_wait();
+    pdl_trigger();   // the scatter's blocks may be scheduled; they wait for this grid
     if (threadIdx.x == 0) {
         const unsigned long long t = atomicAdd(R.cctr, 1ull);
         s_tile = (uint32_t)(t % ntile);
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ R
 // its slots with one atomic.
 __global__ void k_scatter(const __grid_constant__ RunDev R, uint32_t ntiles)
 {
+    pdl_wait();
     const uint32_t step = *R.step;
     const uint32_t lane = threadIdx.x & 31;
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -404,10 +407,11 @@ __device__ __forceinline__ uint32_t start_kind(uint32_t r, uint32_t m)
     return (r & 1u) ? 0u : 1u;
 }
 
-__global__ void __launch_bounds__(256, 5) k_cells(const __grid_constant__ RunDev R, uint32_t ncells, unsigned int* ticket)
+__global__ void __launch_bounds__(256, 6) k_cells(const __grid_constant__ RunDev R, uint32_t ncells, unsigned int* ticket)
 {
     extern __shared__ __align__(16) unsigned char cell_smem_raw[];
     CellSmem& S = *reinterpret_cast<CellSmem*>(cell_smem_raw);
+    pdl_wait();
     const uint32_t total = R.coff[ncells];
     const uint32_t step = *R.step;
     const uint32_t tid = threadIdx.x, lane = tid & 31;
@@ -550,10 +554,10 @@ cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t ntiles, un
                            cudaStream_t s)
 {
     const int nb = coulomb_scan_blocks(ncells);
-    k_scan<<<nb, kScanThreads, 0, s>>>(R, ncells, (uint32_t)nb);
-    if (ntiles > 0) k_scatter<<<ntiles, 256, 0, s>>>(R, ntiles);
-    k_cells<<<grid, 256, sizeof(CellSmem), s>>>(R, ncells, ticket);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(k_scan, dim3(nb), dim3(kScanThreads), 0, s, R, ncells, (uint32_t)nb);
+    if (e == cudaSuccess && ntiles > 0) e = launch_pdl(k_scatter, dim3(ntiles), dim3(256), 0, s, R, ntiles);
+    if (e == cudaSuccess) e = launch_pdl(k_cells, dim3(grid), dim3(256), sizeof(CellSmem), s, R, ncells, ticket);
+    return e;
 }
 
 }  // namespace ecris

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/ecris.h"
 
 namespace ecris {
@@ -203,6 +205,32 @@ __device__ __forceinline__ Words philox(uint32_t c0, uint32_t c2, uint32_t k0, u
 __device__ __forceinline__ Words rng_words(const RunDev& R, uint32_t pid, uint32_t step, uint32_t st)
 {
     return philox(pid, step * 4u + st, R.seed_lo, R.seed_hi);
+}
+
+// Programmatic dependent launch: a kernel launched with launch_pdl may be
+// scheduled while the kernel before it in the stream finishes (that kernel's
+// blocks signal with pdl_trigger, or by exiting); it calls pdl_wait before it
+// touches memory, which waits until the kernel before it has completed and
+// its writes are visible.  This hides the launch latency between the
+// dependent kernels of a step.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // square root through the approximate hardware instruction (relative error

@@ -518,7 +518,6 @@ __device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t 
 }
 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -781,6 +780,7 @@ __device__ __forceinline__ void step_tiles(StepShared<Sh::groups, Sh::stages>& S
             ph3 ^= 1u;
         }
     }
+    pdl_trigger();              // the leaver pass may be scheduled (it waits for this grid)
     if (tid == 0) {
         bulk_wait_all();        // stores complete before the block retires
         if (S.failed) {
@@ -860,6 +860,8 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket)
 // collision kernels)
 __global__ void __launch_bounds__(256) k_leave(const __grid_constant__ RunDev R, unsigned int* ticket, int bump_step)
 {
+    pdl_wait();
+    pdl_trigger();
     const uint32_t n = *R.nleave;
     leave_run(R, n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
     if (last_block(ticket) && threadIdx.x == 0) {
@@ -874,6 +876,7 @@ __global__ void __launch_bounds__(256) k_leave(const __grid_constant__ RunDev R,
 __global__ void __launch_bounds__(256) k_leave_batch(const RunDev* __restrict__ runs, uint32_t nruns,
                                                      unsigned int* ticket)
 {
+    pdl_wait();
     for (uint32_t r = blockIdx.x; r < nruns; r += gridDim.x) {
         const RunDev& R = runs[r];
         if (!R.step) continue;
@@ -1101,16 +1104,14 @@ cudaError_t launch_step(const RunDev& R, uint32_t ntiles, int grid, cudaStream_t
 
 cudaError_t launch_leave(const RunDev& R, unsigned int* ticket, int bump_step, cudaStream_t s)
 {
-    k_leave<<<kLeaveBlocks, 256, 0, s>>>(R, ticket, bump_step);
-    return cudaGetLastError();
+    return launch_pdl(k_leave, dim3(kLeaveBlocks), dim3(256), 0, s, R, ticket, bump_step);
 }
 
 cudaError_t launch_leave_batch(const RunDev* runs, uint32_t nruns, unsigned int* ticket, cudaStream_t s)
 {
     if (nruns == 0) return cudaSuccess;
-    k_leave_batch<<<nruns < (uint32_t)kLeaveBlocks ? nruns : (uint32_t)kLeaveBlocks, 256, 0, s>>>(runs, nruns,
-                                                                                                     ticket);
-    return cudaGetLastError();
+    return launch_pdl(k_leave_batch, dim3(nruns < (uint32_t)kLeaveBlocks ? nruns : (uint32_t)kLeaveBlocks),
+                      dim3(256), 0, s, runs, nruns, ticket);
 }
 
 cudaError_t launch_fold(const RunDev& R, uint32_t ncells, unsigned long long* count, unsigned long long* charge,
