@@ -14,9 +14,11 @@
 //   3. cells     each block takes the cells whose segments start in its
 //                range of about kCellIons participants and copies their keys,
 //                records and array slots to shared memory; one thread per
-//                participant counts the keys of its cell that are smaller than
-//                its own, which is its place in the cell's order (by hash, then
-//                pid), independent of the atomic arrival order.  Consecutive
+//                participant counts the hashes of its cell that are smaller
+//                than its own, which is its place in the cell's order (by hash,
+//                then pid: a tie of hash words, about one pair in 2^32, sends
+//                the range to a count by the whole key), independent of the
+//                atomic arrival order.  Consecutive
 //                ranks pair up; a cell with an odd count puts ranks 0, 1, 2 in a
 //                triplet that collides (0,1), (1,2), (2,0) over dt/2 each.  The
 //                first ion of every pair and triplet is listed in shared memory
@@ -29,7 +31,7 @@
 // (tabulated in FP64 on the host, s >= 1e-3; 1/(1 - e^-s) below, where coth A
 // is 1 to working precision; isotropic for s > 6);
 //   cos chi = 1 + ln(U + (1-U) e^-2A) / A,  eps = 2 pi U'
-// (the logarithm's argument formed without cancellation in FP32, see collide);
+// (the logarithm's argument formed without cancellation in FP32, see collide_w);
 // the relative velocity g is turned by (chi, eps) and the change is shared
 // equally, which conserves momentum and energy of the pair.
 #include "ecris_internal.cuh"
