@@ -293,7 +293,11 @@ def bench_batched(E, I, args, local, stream, flush, peak, peak_kind):
     b = E.Batch(device=local, stream=stream.cuda_stream)
     for wl, st in zip(wls, states):
         b.add(wl.params, st)
-    tune = b.autotune(trial_steps=4)
+    if args.batch_no_tune:
+        b.set_tuning(sort_every=32)   # the default launch shape (a profiling aid)
+        tune = {"sort_every": 32, "blocks_per_sm": 0, "threads": 0, "particles_per_thread": 0, "stages": 0}
+    else:
+        tune = b.autotune(trial_steps=4)
     b.step(args.warmup)
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.batch_steps)]
@@ -511,6 +515,8 @@ def main():
     ap.add_argument("--batch-runs", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--plain-runs", type=int, default=8)
+    ap.add_argument("--batch-no-tune", action="store_true",
+                    help="skip the batch autotuner and use the default launch shape (for profiling captures)")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-power-scan", action="store_true")
     ap.add_argument("--power-runs", type=int, default=128)
