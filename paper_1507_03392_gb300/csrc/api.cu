@@ -1785,9 +1785,10 @@ cudaError_t batch_side_streams(ecris_batch* b)
 }
 
 // The step of every run (captured into the batch graph): the batched step
-// kernel and leaver pass on the batch stream; the collision kernels of the
-// runs that have them forked onto the side streams, so different runs'
-// collision kernels overlap; then the step counters of the others.
+// kernel and leaver pass on the batch stream (the leaver pass advances the
+// step counters of the runs without collisions between ions); the collision
+// kernels of the runs that have them forked onto the side streams, so
+// different runs' collision kernels overlap, and joined back.
 cudaError_t batch_launch(ecris_batch* b)
 {
     cudaError_t e = launch_step_batch(b->d_runs, b->d_items, b->nitems, b->sm_count * batch_bps(b), b->variants,
@@ -1809,7 +1810,6 @@ cudaError_t batch_launch(ecris_batch* b)
         e = cudaEventRecord(b->side_join[k], b->side[k]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->side_join[k], 0);
     }
-    if (e == cudaSuccess) e = launch_bump_steps(b->d_runs, (uint32_t)b->runs.size(), b->stream);
     return e;
 }
 
@@ -2056,9 +2056,6 @@ ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps)
                     return launch_coulomb(*c->h_run, nc, c->btiles, c->d_ticket, c->collide_grid, b->stream);
                 }, kCoulombKernels));
             }
-            BCK(b->timer.run(kKindOther, b->stream, [&] {
-                return launch_bump_steps(b->d_runs, (uint32_t)b->runs.size(), b->stream);
-            }));
         }
         for (size_t r = 0; r < b->runs.size(); ++r) {
             ecris_ctx* c = b->runs[r];

@@ -461,14 +461,14 @@ inline uint32_t shape_tile(int k) { return (uint32_t)(kShapeThreads[k] * kShapeV
 int step_batch_blocks_per_sm(int shape);
 // batch form: one persistent step-kernel launch over the work items (run,
 // tile) of many runs whose parameter blocks are in device memory (it leaves
-// the step counters alone); launch_bump_steps then advances the counters of
-// the runs without Coulomb collisions (the collision kernels of the others,
-// launched in between, advance theirs); entries with step == NULL are skipped
+// the step counters alone); the batch leaver pass then advances the counters
+// of the runs without Coulomb collisions (the collision kernels of the
+// others, launched after it, advance theirs); entries with step == NULL are
+// skipped
 // variants: launch the kernel with the opt-in processes' code (some run has
 // one of kFVariants)
 cudaError_t launch_step_batch(const RunDev* runs, const uint2* items, uint32_t nitems, int grid, bool variants,
                               int shape, cudaStream_t s);
-cudaError_t launch_bump_steps(const RunDev* runs, uint32_t nruns, cudaStream_t s);
 // message returned by ecris_last_error(NULL) on the calling thread
 void ecris_internal_set_thread_error(const char* msg);
 // host: ln A(s) of Nanbu's scattering law on kNanbuN points uniform in ln s

@@ -871,8 +871,9 @@ __global__ void __launch_bounds__(256) k_leave(const __grid_constant__ RunDev R,
 }
 
 // every run of a batch: block b takes runs b, b + grid, ...; the last block
-// clears the lists (step counters are left to k_bump_steps and the collision
-// kernels)
+// clears the lists and advances the step counter of every run without
+// Coulomb collisions (nothing reads those counters again in this step; the
+// collision kernels of the other runs advance their own)
 __global__ void __launch_bounds__(256) k_leave_batch(const RunDev* __restrict__ runs, uint32_t nruns,
                                                      unsigned int* ticket)
 {
@@ -884,15 +885,10 @@ __global__ void __launch_bounds__(256) k_leave_batch(const RunDev* __restrict__ 
     }
     if (last_block(ticket))
         for (uint32_t r = threadIdx.x; r < nruns; r += blockDim.x)
-            if (runs[r].step) *runs[r].nleave = 0u;
-}
-
-// advance the step counter of every run of a batch without Coulomb
-// collisions (the collision kernels of the others advance their own)
-__global__ void k_bump_steps(const RunDev* __restrict__ runs, uint32_t nruns)
-{
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += gridDim.x * blockDim.x)
-        if (runs[r].step && !(runs[r].flags & kFCoulomb)) *runs[r].step += 1u;
+            if (runs[r].step) {
+                *runs[r].nleave = 0u;
+                if (!(runs[r].flags & kFCoulomb)) *runs[r].step += 1u;
+            }
 }
 
 // Fold the packed per-step deposit into the time-summed count and charge
@@ -1083,12 +1079,6 @@ cudaError_t launch_step_batch(const RunDev* runs, const uint2* items, uint32_t n
             return 0;
         });
     }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_bump_steps(const RunDev* runs, uint32_t nruns, cudaStream_t s)
-{
-    if (nruns > 0) k_bump_steps<<<(nruns + 127) / 128, 128, 0, s>>>(runs, nruns);
     return cudaGetLastError();
 }
 
