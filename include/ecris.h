@@ -412,7 +412,7 @@ ecris_status ecris_batch_get_profile(ecris_batch* b, ecris_profile* out);
  * 128, 256 or 512 times particles per thread 1, 2 or 4 with two stages, and
  * 128 x 2, 256 x 1 and 256 x 2 with three -- with as many resident blocks as
  * fit; then, in the fastest shape, each count of resident
- * blocks per SM; then each sort cadence (8, 32, 128 steps), in whole sort
+ * blocks per SM; then each sort cadence (8, 32, 128, 256, 512 steps), in whole sort
  * periods that each start with a sort.  Keeps the fastest of each and returns
  * the choice in *chosen (may be NULL).  Before the trials every run's state
  * (particles, tallies, deposit and time sums, first-passage records, step

@@ -1629,6 +1629,10 @@ struct ecris_batch {
     cudaStream_t side[kBatchSideStreams] = {};
     cudaEvent_t side_join[kBatchSideStreams] = {};
     cudaEvent_t side_fork = nullptr;
+    // the layout sorts of the runs due for one, spread over the same side
+    // streams outside the graph, with their own fork and join events
+    cudaEvent_t sort_join[kBatchSideStreams] = {};
+    cudaEvent_t sort_fork = nullptr;
     // added runs are set up on their own stream, so the batch's queued steps
     // keep running meanwhile
     cudaStream_t setup = nullptr;
@@ -1777,9 +1781,11 @@ cudaError_t batch_side_streams(ecris_batch* b)
 {
     if (b->side_fork) return cudaSuccess;
     cudaError_t e = cudaEventCreateWithFlags(&b->side_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->sort_fork, cudaEventDisableTiming);
     for (int k = 0; e == cudaSuccess && k < kBatchSideStreams; ++k) {
         e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side_join[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->sort_join[k], cudaEventDisableTiming);
     }
     return e;
 }
@@ -1915,8 +1921,10 @@ void ecris_batch_destroy(ecris_batch* b)
     for (int k = 0; k < kBatchSideStreams; ++k) {
         if (b->side[k]) cudaStreamDestroy(b->side[k]);
         if (b->side_join[k]) cudaEventDestroy(b->side_join[k]);
+        if (b->sort_join[k]) cudaEventDestroy(b->sort_join[k]);
     }
     if (b->side_fork) cudaEventDestroy(b->side_fork);
+    if (b->sort_fork) cudaEventDestroy(b->sort_fork);
     for (auto& g : b->old_graphs) {
         cudaGraphExecDestroy(g.second);
         cudaEventDestroy(g.first);
@@ -2021,16 +2029,36 @@ ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps)
         // regroup the particles of the runs that are due; their parameter
         // blocks change (the arrays swap), and so does the captured graph
         // when a run's collision kernels take the block by value
+        // (several at once: the runs' sorts go to the side streams, whose
+        // work the batch stream then waits for; timed steps sort one by one)
+        int nsort = 0;
         for (auto* c : b->runs) {
             if (!c || c->n4 == 0 || c->since_sort < c->sort_every) continue;
             ecris_status st = ECRIS_OK;
-            BCK(b->timer.run(kKindOther, b->stream, [&] {
+            if (b->timer.on) {
+                BCK(b->timer.run(kKindOther, b->stream, [&] {
+                    st = sort_particles(c);
+                    return cudaSuccess;
+                }, 6));
+            } else {
+                const int k = nsort % kBatchSideStreams;
+                if (nsort == 0) {
+                    BCK(batch_side_streams(b));
+                    BCK(cudaEventRecord(b->sort_fork, b->stream));
+                }
+                if (nsort < kBatchSideStreams) BCK(cudaStreamWaitEvent(b->side[k], b->sort_fork, 0));
+                c->stream = b->side[k];
                 st = sort_particles(c);
-                return cudaSuccess;
-            }, 6));
+                c->stream = b->stream;
+                ++nsort;
+            }
             if (st != ECRIS_OK) return bfail(b, st, "batch_step: " + c->err);
             b->params_dirty = true;
             if (c->h.mcc.flags & kFCoulomb) b->graph_dirty = true;
+        }
+        for (int k = 0; k < nsort && k < kBatchSideStreams; ++k) {
+            BCK(cudaEventRecord(b->sort_join[k], b->side[k]));
+            BCK(cudaStreamWaitEvent(b->stream, b->sort_join[k], 0));
         }
         if (b->params_dirty) {
             ecris_status st = batch_upload(b);
@@ -2408,8 +2436,8 @@ ecris_status batch_autotune(ecris_batch* b, uint32_t trial_steps, bool cadence, 
     // 3. steps between sorts: whole sort periods, each starting with a sort,
     // so that every cadence pays its own share of sorting
     best = 1e30f;
-    const uint32_t cadences[3] = {8, 32, 128};
-    for (int k = 0; k < 3 && st == ECRIS_OK && cadence; ++k) {
+    const uint32_t cadences[5] = {8, 32, 128, 256, 512};
+    for (int k = 0; k < 5 && st == ECRIS_OK && cadence; ++k) {
         apply(best_shape, best_bps, cadences[k]);
         const uint32_t steps = ((trial_steps + cadences[k] - 1) / cadences[k]) * cadences[k];
         st = time_steps(b, steps, false, &ms);

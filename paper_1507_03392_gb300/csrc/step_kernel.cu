@@ -337,7 +337,7 @@ __device__ __forceinline__ bool step_particle(const RunDev& R, uint32_t pid, uin
     }
     if ((R.flags & kFEikick) && Q >= 1) {
         const float qp = R.ei_pow == 1 ? (float)Q : (float)(Q * Q);
-        const float D = sqrt_approx(R.ei_coef[zone] * cr.x * qp);
+        const float D = sqrt_approx((zone ? R.ei_coef[1] : R.ei_coef[0]) * cr.x * qp);
         const float ct = fmaf(2.0f, unit01(w.w2), -1.0f);
         const float st = sqrt_approx(fmaxf(0.0f, fmaf(-ct, ct, 1.0f)));
         float sp, cp;

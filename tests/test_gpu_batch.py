@@ -110,7 +110,7 @@ def test_autotune_keeps_results_and_time(E):
     b.step(3)
     before = [(b.state(h), b.diag(h, grids=True)) for h in hs]
     t = b.autotune(trial_steps=2)
-    assert t["sort_every"] in (8, 32, 128) and t["blocks_per_sm"] >= 1
+    assert t["sort_every"] in (8, 32, 128, 256, 512) and t["blocks_per_sm"] >= 1
     shapes = [(a, v, 2) for a in (128, 256, 512) for v in (1, 2, 4)] + [(128, 2, 3), (256, 1, 3), (256, 2, 3)]
     assert (t["threads"], t["particles_per_thread"], t["stages"]) in shapes
     for h, ref in zip(hs, before):
