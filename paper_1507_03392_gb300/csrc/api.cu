@@ -345,7 +345,6 @@ struct ecris_ctx {
     uint32_t* d_hist = nullptr;    // sort histogram (2 Nc + 1), kept zero between sorts
     uint32_t* d_hoff = nullptr;    // its exclusive scan (2 Nc + 2)
     uint32_t* d_hblk = nullptr;    // scan block totals
-    uint4* d_aos = nullptr;        // 32-byte particle records for the sort
     uint32_t sort_every = 32;      // steps between sorts
     uint32_t since_sort = 0;
     bool fresh = false;         // loaded, not yet sorted
@@ -455,7 +454,6 @@ void free_ions(ecris_ctx* ctx)
     free_async(ctx, ctx->d_hist);
     free_async(ctx, ctx->d_hoff);
     free_async(ctx, ctx->d_hblk);
-    free_async(ctx, ctx->d_aos);
     free_async(ctx, ctx->d_cslot);
     free_async(ctx, ctx->d_sslot);
     free_async(ctx, ctx->d_dep);
@@ -927,7 +925,7 @@ ecris_status sort_particles(ecris_ctx* ctx)
     dst.id = ctx->d_id2;
     CK(timed(ctx, kKindOther, [&] {
         return launch_sort(*ctx->h_run, (uint32_t)(4 * ctx->n4), dst, ctx->d_hist, ctx->d_hoff, ctx->d_hblk,
-                           ctx->d_aos, ctx->stream);
+                           ctx->stream);
     }, 6));
     for (int k = 0; k < 6; ++k) std::swap(ctx->d_soa[k], ctx->d_soa2[k]);
     std::swap(ctx->d_meta, ctx->d_meta2);
@@ -1225,7 +1223,6 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         CK(cudaMallocAsync((void**)&ctx->d_hblk, (size_t)sort_scan_blocks((uint32_t)(2 * nc + 1)) * sizeof(uint32_t),
                            ctx->stream));
         CK(cudaMemsetAsync(ctx->d_hist, 0, (2 * nc + 1) * sizeof(uint32_t), ctx->stream));
-        CK(cudaMallocAsync((void**)&ctx->d_aos, 2 * cap * sizeof(uint4), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_q8, cap, ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_dep, nc * sizeof(unsigned long long), ctx->stream));
         CK(cudaMallocAsync((void**)&ctx->d_count, nc * sizeof(unsigned long long), ctx->stream));
@@ -1851,8 +1848,8 @@ size_t ecris_run_bytes(size_t n, int32_t nx, int32_t ny, int32_t nz, int coulomb
 {
     const size_t cap = 4 * ((n + 3) / 4) + 4;
     const size_t nc = (size_t)(nx > 0 ? nx : 0) * (ny > 0 ? ny : 0) * (nz > 0 ? nz : 0);
-    // two particle sets with ids, the sort's records, leaver list, births, load bytes, Coulomb lists
-    size_t per_p = 2 * 32 + 32 + 4 + 4 + 4 + 1;
+    // two particle sets with ids, leaver list, births, load bytes, Coulomb lists
+    size_t per_p = 2 * 32 + 4 + 4 + 4 + 1;
     if (coulomb) per_p += 16 + 16 + 8 + 16 + 4 + 4 + 1;
     // cell records, E, deposit, time sums, sort histogram and scan, the n_e
     // update's mark, scratch and R_L coefficients, Coulomb counts
