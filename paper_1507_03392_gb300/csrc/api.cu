@@ -923,10 +923,16 @@ ecris_status sort_particles(ecris_ctx* ctx)
     dst.vz = ctx->d_soa2[5];
     dst.meta = ctx->d_meta2;
     dst.id = ctx->d_id2;
+    // the first sort after a load sees the load order: it moves 32-byte
+    // records through a scratch buffer taken from the stream's pool for it
+    const size_t cap4 = 4 * ctx->n4;
+    uint4* aos = nullptr;
+    if (ctx->fresh) CK(cudaMallocAsync((void**)&aos, 2 * cap4 * sizeof(uint4), ctx->stream));
     CK(timed(ctx, kKindOther, [&] {
-        return launch_sort(*ctx->h_run, (uint32_t)(4 * ctx->n4), dst, ctx->d_hist, ctx->d_hoff, ctx->d_hblk,
+        return launch_sort(*ctx->h_run, (uint32_t)cap4, dst, ctx->d_hist, ctx->d_hoff, ctx->d_hblk, aos,
                            ctx->stream);
-    }, 6));
+    }, aos ? 7 : 6));
+    if (aos) CK(cudaFreeAsync(aos, ctx->stream));
     for (int k = 0; k < 6; ++k) std::swap(ctx->d_soa[k], ctx->d_soa2[k]);
     std::swap(ctx->d_meta, ctx->d_meta2);
     std::swap(ctx->d_id, ctx->d_id2);
@@ -1848,8 +1854,9 @@ size_t ecris_run_bytes(size_t n, int32_t nx, int32_t ny, int32_t nz, int coulomb
 {
     const size_t cap = 4 * ((n + 3) / 4) + 4;
     const size_t nc = (size_t)(nx > 0 ? nx : 0) * (ny > 0 ? ny : 0) * (nz > 0 ? nz : 0);
-    // two particle sets with ids, leaver list, births, load bytes, Coulomb lists
-    size_t per_p = 2 * 32 + 4 + 4 + 4 + 1;
+    // two particle sets with ids, the first sort's records (held while it
+    // runs), leaver list, births, load bytes, Coulomb lists
+    size_t per_p = 2 * 32 + 32 + 4 + 4 + 4 + 1;
     if (coulomb) per_p += 16 + 16 + 8 + 16 + 4 + 4 + 1;
     // cell records, E, deposit, time sums, sort histogram and scan, the n_e
     // update's mark, scratch and R_L coefficients, Coulomb counts

@@ -434,9 +434,11 @@ struct ParticleSet {
 // Counting sort of the run's particles (in R) by (ion/atom, cell) into `dst`:
 // live ions first, then live atoms, each by cell; frozen and padding slots
 // last.  hist (2 Nc + 1 words) must be zero and is left zero; off (2 Nc + 2)
-// and blk (scan block totals) are scratch.
+// and blk (scan block totals) are scratch.  aos (2 cap uint4 of scratch, or
+// NULL): move through 32-byte records, for input in arbitrary order (the
+// first sort after a load); NULL writes the destination arrays directly.
 cudaError_t launch_sort(const RunDev& R, uint32_t cap, const ParticleSet& dst, uint32_t* hist, uint32_t* off,
-                        uint32_t* blk, cudaStream_t s);
+                        uint32_t* blk, uint4* aos, cudaStream_t s);
 int sort_scan_blocks(uint32_t nbins);
 // state in load order: out[id[slot]] = state[slot] for id < n (positions to
 // metres), into device arrays

@@ -11,11 +11,14 @@
 //
 // Passes: count keys into a histogram (2 Nc + 1 bins: ions by cell, atoms by
 // cell, one bin for frozen and padding slots); exclusive scan; move every
-// particle into the destination arrays at off[key] + (histogram counted down
-// by one), which leaves the histogram zero for the next sort.  The input is
-// mostly in key order already, so a warp's lanes mostly land on consecutive
-// places and the eight arrays' writes coalesce.  Order inside a bin follows
-// the atomics and does not matter.
+// particle to off[key] + (histogram counted down by one), which leaves the
+// histogram zero for the next sort.  Order inside a bin follows the atomics
+// and does not matter.  The move writes the destination arrays directly when
+// the input is mostly in key order already (every sort but the first after a
+// load), since a warp's lanes then land on consecutive places and the eight
+// arrays' writes coalesce.  For input in arbitrary order it writes one
+// 32-byte record per particle, a full sector for a random destination instead
+// of eight partial ones, and a second pass unpacks the records coalesced.
 #include "ecris_internal.cuh"
 
 namespace ecris {
@@ -131,7 +134,10 @@ __global__ void __launch_bounds__(kSortThreads) k_scan3(uint32_t* __restrict__ o
         if (base + j < n) out[base + j] += add;
 }
 
-__global__ void k_sort_move(const __grid_constant__ RunDev R, uint32_t cap, ParticleSet dst,
+// kRecords: write 32-byte records to aos (unpacked by k_sort_unpack), else
+// the destination arrays
+template <bool kRecords>
+__global__ void k_sort_move(const __grid_constant__ RunDev R, uint32_t cap, ParticleSet dst, uint4* __restrict__ aos,
                             uint32_t* __restrict__ hist, const uint32_t* __restrict__ off)
 {
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -151,14 +157,35 @@ __global__ void k_sort_move(const __grid_constant__ RunDev R, uint32_t cap, Part
         top = __shfl_sync(grp, top, leader);
         const uint32_t rank = (uint32_t)__popc(grp & ((1u << lane) - 1u));
         const uint32_t d = off[key] + top - 1u - rank;
-        dst.x[d] = R.x[i];
-        dst.y[d] = R.y[i];
-        dst.z[d] = R.z[i];
-        dst.vx[d] = R.vx[i];
-        dst.vy[d] = R.vy[i];
-        dst.vz[d] = R.vz[i];
-        dst.meta[d] = R.meta[i];
-        dst.id[d] = R.id[i];
+        if (kRecords) {
+            aos[2 * d] = make_uint4((uint32_t)R.x[i], (uint32_t)R.y[i], (uint32_t)R.z[i], __float_as_uint(R.vx[i]));
+            aos[2 * d + 1] = make_uint4(__float_as_uint(R.vy[i]), __float_as_uint(R.vz[i]), R.meta[i], R.id[i]);
+        } else {
+            dst.x[d] = R.x[i];
+            dst.y[d] = R.y[i];
+            dst.z[d] = R.z[i];
+            dst.vx[d] = R.vx[i];
+            dst.vy[d] = R.vy[i];
+            dst.vz[d] = R.vz[i];
+            dst.meta[d] = R.meta[i];
+            dst.id[d] = R.id[i];
+        }
+    }
+}
+
+// records in sorted order -> the destination arrays, coalesced both ways
+__global__ void k_sort_unpack(const uint4* __restrict__ aos, uint32_t cap, ParticleSet dst)
+{
+    for (uint32_t d = blockIdx.x * blockDim.x + threadIdx.x; d < cap; d += gridDim.x * blockDim.x) {
+        const uint4 a = aos[2 * d], b = aos[2 * d + 1];
+        dst.x[d] = (int32_t)a.x;
+        dst.y[d] = (int32_t)a.y;
+        dst.z[d] = (int32_t)a.z;
+        dst.vx[d] = __uint_as_float(a.w);
+        dst.vy[d] = __uint_as_float(b.x);
+        dst.vz[d] = __uint_as_float(b.y);
+        dst.meta[d] = b.z;
+        dst.id[d] = b.w;
     }
 }
 
@@ -192,7 +219,7 @@ int grid_for(uint32_t n, int threads, int cap_blocks)
 int sort_scan_blocks(uint32_t nbins) { return (int)((nbins + kSortScanBlock - 1) / kSortScanBlock); }
 
 cudaError_t launch_sort(const RunDev& R, uint32_t cap, const ParticleSet& dst, uint32_t* hist, uint32_t* off,
-                        uint32_t* blk, cudaStream_t s)
+                        uint32_t* blk, uint4* aos, cudaStream_t s)
 {
     const uint32_t nbins = 2u * R.ncells + 1u;
     const int nb = sort_scan_blocks(nbins);
@@ -200,7 +227,12 @@ cudaError_t launch_sort(const RunDev& R, uint32_t cap, const ParticleSet& dst, u
     k_scan1<<<nb, kSortThreads, 0, s>>>(hist, off, blk, nbins);
     k_scan2<<<1, 1024, 0, s>>>(blk, (uint32_t)nb, off, nbins);
     k_scan3<<<nb, kSortThreads, 0, s>>>(off, blk, nbins);
-    k_sort_move<<<grid_for(cap, 256, 8192), 256, 0, s>>>(R, cap, dst, hist, off);
+    if (aos) {
+        k_sort_move<true><<<grid_for(cap, 256, 8192), 256, 0, s>>>(R, cap, dst, aos, hist, off);
+        k_sort_unpack<<<grid_for(cap, 256, 8192), 256, 0, s>>>(aos, cap, dst);
+    } else {
+        k_sort_move<false><<<grid_for(cap, 256, 8192), 256, 0, s>>>(R, cap, dst, nullptr, hist, off);
+    }
     return cudaGetLastError();
 }
 
