@@ -23,8 +23,11 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--cudart", "s
 # every operation the same way, so a run gives identical results alone and in
 # a batch.  Explicit fmaf() calls in that code still compile to FMAs.
 # The device update of n_e builds the cell records in FP64 as the host does,
-# operation by operation, so it is compiled without contraction too.
-FILE_FLAGS = {"step_kernel.cu": ["-fmad=false"], "ne_update.cu": ["-fmad=false"]}
+# operation by operation, so it is compiled without contraction too.  So is
+# the collision kernel: its shared-memory and global-memory paths inline the
+# same collision arithmetic, and a cell goes to one or the other depending on
+# how the cells fall into ranges; without contraction both round the same.
+FILE_FLAGS = {"step_kernel.cu": ["-fmad=false"], "ne_update.cu": ["-fmad=false"], "coulomb.cu": ["-fmad=false"]}
 
 
 def _nvcc():

@@ -330,6 +330,7 @@ struct ecris_ctx {
     float4* d_crec = nullptr;
     uint32_t* d_ccount = nullptr;
     uint32_t* d_cstart = nullptr;
+    uint32_t* d_crange = nullptr;   // collision ranges: size this step, largest cell count seen
     uint32_t* d_coff = nullptr;
     unsigned long long* d_cstat = nullptr;   // scan tile status words and ticket counter
     unsigned long long* d_ckeys = nullptr;
@@ -478,6 +479,7 @@ void free_ions(ecris_ctx* ctx)
     free_async(ctx, ctx->d_crec);
     free_async(ctx, ctx->d_ccount);
     free_async(ctx, ctx->d_cstart);
+    free_async(ctx, ctx->d_crange);
     free_async(ctx, ctx->d_coff);
     free_async(ctx, ctx->d_cstat);
     free_async(ctx, ctx->d_ckeys);
@@ -606,6 +608,7 @@ void fill_rundev(ecris_ctx* ctx, double dt, RunDev& R)
     R.crec = ctx->d_crec;
     R.ccount = ctx->d_ccount;
     R.cstart = ctx->d_cstart;
+    R.crange = ctx->d_crange;
     R.coff = ctx->d_coff;
     R.cstat = ctx->d_cstat;
     R.cctr = ctx->d_cstat ? ctx->d_cstat + coulomb_scan_blocks((uint32_t)ctx->cap_cells) : nullptr;
@@ -1256,7 +1259,8 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
             CK(cudaMallocAsync((void**)&ctx->d_ckeys, cap * sizeof(unsigned long long), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_crec, cap * sizeof(float4), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_ccount, nc * sizeof(uint32_t), ctx->stream));
-            CK(cudaMallocAsync((void**)&ctx->d_cstart, (cap / kCellIons + 2) * sizeof(uint32_t), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_cstart, (cap / kCellIonsMin + 2) * sizeof(uint32_t), ctx->stream));
+            CK(cudaMallocAsync((void**)&ctx->d_crange, 2 * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_coff, (nc + 1) * sizeof(uint32_t), ctx->stream));
             CK(cudaMallocAsync((void**)&ctx->d_cstat, (size_t)(coulomb_scan_blocks((uint32_t)nc) + 1) * sizeof(unsigned long long),
                                ctx->stream));
@@ -1275,6 +1279,10 @@ ecris_status ecris_load_ions(ecris_ctx* ctx, size_t n, const float* const xyzv[6
         CK(cudaMemcpyAsync(ctx->d_q8, q, n, kind, ctx->stream));
     }
     if (ctx->d_ccount) CK(cudaMemsetAsync(ctx->d_ccount, 0, nc * sizeof(uint32_t), ctx->stream));
+    if (ctx->d_crange) {
+        static const uint32_t crange0[2] = {(uint32_t)kCellIons, 0u};
+        CK(cudaMemcpyAsync(ctx->d_crange, crange0, sizeof crange0, cudaMemcpyHostToDevice, ctx->stream));
+    }
     if (ctx->d_cstat)
         CK(cudaMemsetAsync(ctx->d_cstat, 0, (size_t)(coulomb_scan_blocks((uint32_t)nc) + 1) * sizeof(unsigned long long),
                            ctx->stream));

@@ -12,7 +12,9 @@
 //                being word 0 of the particle's stream-1 Philox block, and the
 //                record (v, cell << 6 | Q), so each cell's records are contiguous;
 //   3. cells     each block takes the cells whose segments start in its
-//                range of about kCellIons participants and copies their keys,
+//                range of participants (kCellIons at the first step after a
+//                load; later as many as keep the largest cell of the step
+//                before inside shared memory) and copies their keys,
 //                records and array slots to shared memory; one thread per
 //                participant counts the hashes of its cell that are smaller
 //                than its own, which is its place in the cell's order (by hash,
@@ -52,13 +54,14 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
     return v;
 }
 
-// range b of the collision kernel starts at the first cell c with
-// coff[c] >= b kCellIons: cell c starts the ranges b with
-// coff[c - 1] < b kCellIons <= coff[c]
-__device__ __forceinline__ void mark_ranges(const RunDev& R, uint32_t c, uint32_t prev, uint32_t cur)
+// range b of the collision kernel (stride participants a range) starts at the
+// first cell c with coff[c] >= b stride: cell c starts the ranges b with
+// coff[c - 1] < b stride <= coff[c]
+__device__ __forceinline__ void mark_ranges(const RunDev& R, uint32_t c, uint32_t prev, uint32_t cur,
+                                            uint32_t stride)
 {
-    const uint32_t b0 = c == 0 ? 0u : prev / (uint32_t)kCellIons + 1u;
-    for (uint32_t b = b0; b <= cur / (uint32_t)kCellIons; ++b) R.cstart[b] = c;
+    const uint32_t b0 = c == 0 ? 0u : prev / stride + 1u;
+    for (uint32_t b = b0; b <= cur / stride; ++b) R.cstart[b] = c;
 }
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p)
@@ -85,10 +88,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ R
                                                       uint32_t ntile)
 {
     __shared__ uint32_t wsum[kScanThreads / 32];
-    __shared__ uint32_t s_tile, s_epoch, s_prefix;
+    __shared__ uint32_t s_tile, s_epoch, s_prefix, s_stride, s_max;
     pdl_wait();
     pdl_trigger();   // the scatter's blocks may be scheduled; they wait for this grid
     if (threadIdx.x == 0) {
+        s_stride = R.crange[0];
+        s_max = 0u;
         const unsigned long long t = atomicAdd(R.cctr, 1ull);
         s_tile = (uint32_t)(t % ntile);
         s_epoch = (uint32_t)(t / ntile) + 1u;
@@ -111,12 +116,21 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ R
             for (int k = 0; k < 4; ++k) v[j + k] = idx + k < ncells ? R.ccount[idx + k] : 0u;
         }
     }
+    uint32_t vmax = 0;
 #pragma unroll
-    for (int j = 0; j < kScanPerThread; ++j) sum += v[j];
+    for (int j = 0; j < kScanPerThread; ++j) {
+        sum += v[j];
+        vmax = max(vmax, v[j]);
+    }
+    // the largest cell count, for the next step's range size
+    vmax = __reduce_max_sync(0xFFFFFFFFu, vmax);
+    if ((threadIdx.x & 31) == 0 && vmax) atomicMax(&s_max, vmax);
+    const uint32_t stride = s_stride;
     const uint32_t incl = warp_incl_scan(sum);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
+    if (threadIdx.x == 0 && s_max) atomicMax(R.crange + 1, s_max);
     if (warp == 0) {
         const uint32_t w = lane < kScanThreads / 32 ? wsum[lane] : 0u;
         const uint32_t wi = warp_incl_scan(w);
@@ -162,10 +176,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ R
         if (idx < ncells) {
             R.coff[idx] = cur;
             const uint32_t prev = idx == 0 ? 0u : (j > 0 ? cur - v[j - 1] : cur - R.ccount[idx - 1]);
-            mark_ranges(R, idx, prev, cur);
+            mark_ranges(R, idx, prev, cur, stride);
             if (idx == ncells - 1) {
                 R.coff[ncells] = cur + v[j];
-                mark_ranges(R, ncells, cur, cur + v[j]);
+                mark_ranges(R, ncells, cur, cur + v[j], stride);
             }
         }
         cur += v[j];
@@ -225,7 +239,8 @@ __device__ __forceinline__ float nanbu_A(const RunDev& R, float s)
     int i = (int)t;
     if (i > kNanbuN - 2) i = kNanbuN - 2;
     const float f = t - (float)i;
-    const float la = (1.0f - f) * __ldg(R.nanbu + i) + f * __ldg(R.nanbu + i + 1);
+    const float a0 = __ldg(R.nanbu + i);
+    const float la = fmaf(f, __ldg(R.nanbu + i + 1) - a0, a0);
     return __expf(la);
 }
 
@@ -235,8 +250,11 @@ __device__ __forceinline__ float nanbu_A(const RunDev& R, float s)
 __device__ __forceinline__ void collide_w(const RunDev& R, float4& ra, float4& rb, float dtc, float m_cell,
                                           uint32_t w1, uint32_t w2)
 {
+    // (FMAs written out: this file is compiled without contraction, so that
+    // every inlined copy of this code rounds the same way, whichever path of
+    // the collision kernel takes a cell)
     const float gx = ra.x - rb.x, gy = ra.y - rb.y, gz = ra.z - rb.z;
-    const float g2 = gx * gx + gy * gy + gz * gz;
+    const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
     if (!(g2 > 0.0f)) return;
     // 1/g through the approximate reciprocal square root (a few units in the
     // last place): it sets s and the scattering geometry, not the angle's
@@ -261,28 +279,28 @@ __device__ __forceinline__ void collide_w(const RunDev& R, float4& ra, float4& r
         // terms are formed directly, since e^-2A can lie below the FP32
         // spacing of expm1 near -1 while U is small as well
         const float lnarg = A < 0.5f ? log1pf((1.0f - U) * expm1f(-2.0f * A))
-                                     : logf(U + (1.0f - U) * expf(-2.0f * A));
+                                     : logf(fmaf(1.0f - U, expf(-2.0f * A), U));
         eps = fminf(fmaxf(__fdividef(-lnarg, A), 0.0f), 2.0f);
         epc = 2.0f - eps;
     }
     const float schi = sqrt_approx(eps * epc);
     float se, ce;
     sincos_2pi(unit01(w2), &se, &ce);
-    const float gp2 = gy * gy + gz * gz;
+    const float gp2 = fmaf(gy, gy, gz * gz);
     float hx, hy, hz;
     if (gp2 > 0.0f) {
         const float rgp = rsqrtf(gp2);
         hx = gp2 * rgp * ce;
-        hy = -(gx * gy * ce + g * gz * se) * rgp;
-        hz = -(gx * gz * ce - g * gy * se) * rgp;
+        hy = -fmaf(gx * gy, ce, g * gz * se) * rgp;
+        hz = -fmaf(gx * gz, ce, -(g * gy * se)) * rgp;
     } else {
         hx = 0.0f;
         hy = g * ce;
         hz = g * se;
     }
-    const float dgx = 0.5f * (hx * schi - gx * eps);
-    const float dgy = 0.5f * (hy * schi - gy * eps);
-    const float dgz = 0.5f * (hz * schi - gz * eps);
+    const float dgx = 0.5f * fmaf(hx, schi, -(gx * eps));
+    const float dgy = 0.5f * fmaf(hy, schi, -(gy * eps));
+    const float dgz = 0.5f * fmaf(hz, schi, -(gz * eps));
     ra.x += dgx; ra.y += dgy; ra.z += dgz;
     rb.x -= dgx; rb.y -= dgy; rb.z -= dgz;
 }
@@ -419,9 +437,10 @@ __global__ void __launch_bounds__(256, 6) k_cells(const __grid_constant__ RunDev
     const uint32_t tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) S.ncoll = 0ull;
     uint32_t ncoll = 0;
-    for (uint32_t b = blockIdx.x; b * (uint32_t)kCellIons < total; b += gridDim.x) {
+    const uint32_t stride = R.crange[0];   // participants a range, as the scan marked them
+    for (uint32_t b = blockIdx.x; b * stride < total; b += gridDim.x) {
         if (tid == 0) {
-            const uint32_t hi = (b + 1u) * (uint32_t)kCellIons;
+            const uint32_t hi = (b + 1u) * stride;
             const uint32_t c1 = hi >= total ? ncells : R.cstart[b + 1];
             S.s0 = R.coff[R.cstart[b]];
             S.s1 = R.coff[c1];
@@ -536,6 +555,12 @@ __global__ void __launch_bounds__(256, 6) k_cells(const __grid_constant__ RunDev
     if (s_last && tid == 0) {
         *R.step += 1u;
         *ticket = 0u;
+        // the next step's range size: as large as keeps this step's largest
+        // cell, with a range's cells whole, inside shared memory
+        const uint32_t mx = R.crange[1];
+        const uint32_t room = mx < (uint32_t)kCellCap ? (uint32_t)kCellCap - mx : 0u;
+        R.crange[0] = min(max(room, (uint32_t)kCellIonsMin), (uint32_t)kCellIonsMax);
+        R.crange[1] = 0u;
     }
 }
 

@@ -59,9 +59,9 @@ constexpr size_t kOffCrec = kOffCkeys + align256(sizeof(unsigned long long) * kN
 constexpr size_t kOffCslot = kOffCrec + align256(sizeof(float4) * kNaMaxIons);
 constexpr size_t kOffSslot = kOffCslot + align256(sizeof(uint32_t) * kNaMaxIons);
 constexpr size_t kOffCstart = kOffSslot + align256(sizeof(uint32_t) * kNaMaxIons);
-constexpr size_t kOffNanbu = kOffCstart + align256(sizeof(uint32_t) * (kNaMaxIons / kCellIons + 2));
+constexpr size_t kOffNanbu = kOffCstart + align256(sizeof(uint32_t) * (kNaMaxIons / kCellIonsMin + 2));
 constexpr size_t kOffWords = kOffNanbu + align256(sizeof(float) * kNanbuN);
-// words: step, ticket; then the tally block
+// words: step, ticket, error word, -, collision range size and largest cell count; then the tally block
 constexpr size_t kOffTally = kOffWords + 256;
 constexpr size_t kNaScratchBytes = kOffTally + align256(sizeof(unsigned long long) * kTallyWords);
 
@@ -94,6 +94,8 @@ __global__ void k_na_init(unsigned char* base, uint32_t ncells, uint32_t tiles, 
         words[0] = step;
         words[1] = 0u;   // the collision kernel's ticket
         words[2] = 0u;   // error word: the scan sets ECRIS_ETIMEOUT if a bounded wait runs out
+        words[4] = (uint32_t)kCellIons;   // collision range size of this call
+        words[5] = 0u;
     }
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (uint32_t)kTallyWords; i += stride) tally[i] = 0ull;
 }
@@ -199,6 +201,7 @@ extern "C" ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* 
     R.cstat = reinterpret_cast<unsigned long long*>(base + kOffCstat);
     R.cctr = R.cstat + kNaScanTiles;
     R.cstart = reinterpret_cast<uint32_t*>(base + kOffCstart);
+    R.crange = reinterpret_cast<uint32_t*>(base + kOffWords) + 4;
     R.ckeys = reinterpret_cast<unsigned long long*>(base + kOffCkeys);
     R.crec = reinterpret_cast<float4*>(base + kOffCrec);
     R.cslot = reinterpret_cast<uint32_t*>(base + kOffCslot);

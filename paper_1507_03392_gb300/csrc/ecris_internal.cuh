@@ -157,7 +157,9 @@ struct alignas(16) RunDev {
     uint32_t *coff;              // exclusive scan of ccount, Nc + 1 entries
     unsigned long long *cstat;   // scan tile status words (decoupled look-back), one per scan tile
     unsigned long long *cctr;    // scan tile tickets handed out so far
-    uint32_t *cstart;            // first cell of each range of kCellIons participants (collision kernel)
+    uint32_t *cstart;            // first cell of each range of participants (collision kernel)
+    uint32_t *crange;            // [0] participants per range this step, [1] largest cell count seen by
+                                 // this step's scan (sets the next step's range size)
     unsigned long long *ckeys;   // (pairing hash << 32 | pid) per participant, grouped by cell
     float4 *crec;                // (vx, vy, vz, cell << 6 | Q as bits) per participant, grouped by cell
     uint32_t *cslot;             // array slot of each participant, grouped by cell
@@ -504,7 +506,13 @@ void batch_snapshot_diag(const ecris_batch* b, int32_t run, const TallySnapshot&
 // the per-cell sort / pair / collide kernel, whose last block advances the
 // step counter.
 constexpr int kCoulombKernels = 3;   // kernels per launch_coulomb
-constexpr int kCellIons = 512;       // participants per range of cells of the collision kernel
+// participants per range of cells of the collision kernel: the first step
+// after a load takes kCellIons; each later step takes kCellCap minus the
+// largest cell count of the step before, within [kCellIonsMin, kCellIonsMax],
+// so that a range (its cells whole) still fits in shared memory while ranges
+// stay as large as it allows (fewer ranges, fewer per-range waits)
+constexpr int kCellIons = 512;
+constexpr int kCellIonsMin = 256, kCellIonsMax = 896;
 constexpr int kCellCap = 1024;       // participants of a range held in shared memory
 cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t ntiles, unsigned int* ticket, int grid,
                            cudaStream_t s);
