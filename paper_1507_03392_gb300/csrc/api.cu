@@ -894,12 +894,16 @@ ecris_status step_graph(ecris_ctx* ctx, int kind, cudaGraphExec_t* out)
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
+    // kind 0, the whole step: with collisions the scan kernel also runs the
+    // leaver pass; kind 1, the collision kernels alone (timed steps run the
+    // leaver pass on its own before them)
     if (kind == 0) {
         e = launch_step(*ctx->h_run, ctx->ntiles, ctx->step_grid, ctx->stream);
-        if (e == cudaSuccess) e = launch_leave(*ctx->h_run, ctx->d_ticket, coulomb ? 0 : 1, ctx->stream);
+        if (e == cudaSuccess && !coulomb) e = launch_leave(*ctx->h_run, ctx->d_ticket, 1, ctx->stream);
     }
     if (e == cudaSuccess && coulomb)
-        e = launch_coulomb(*ctx->h_run, nc, ctx->ntiles, ctx->d_ticket, ctx->collide_grid, ctx->stream);
+        e = launch_coulomb(*ctx->h_run, nc, ctx->ntiles, ctx->d_ticket, ctx->collide_grid, (uint32_t)kLeaveBlocks,
+                           kind == 0 ? 1 : 0, ctx->stream);
     const cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
     CK(e);
     CK(e2);
@@ -1821,7 +1825,8 @@ cudaError_t batch_launch(ecris_batch* b)
         if (used < kBatchSideStreams) e = cudaStreamWaitEvent(b->side[k], b->side_fork, 0);
         ++used;
         const uint32_t nc = (uint32_t)((size_t)c->h.nx * c->h.ny * c->h.nz);
-        if (e == cudaSuccess) e = launch_coulomb(*c->h_run, nc, c->btiles, c->d_ticket, c->collide_grid, b->side[k]);
+        if (e == cudaSuccess)
+            e = launch_coulomb(*c->h_run, nc, c->btiles, c->d_ticket, c->collide_grid, 0u, 0, b->side[k]);
     }
     for (int k = 0; e == cudaSuccess && k < used && k < kBatchSideStreams; ++k) {
         e = cudaEventRecord(b->side_join[k], b->side[k]);
@@ -2093,7 +2098,7 @@ ecris_status ecris_batch_step(ecris_batch* b, uint32_t nsteps)
                 if (!c || !(c->h.mcc.flags & kFCoulomb)) continue;
                 const uint32_t nc = (uint32_t)((size_t)c->h.nx * c->h.ny * c->h.nz);
                 BCK(b->timer.run(kKindCoulomb, b->stream, [&] {
-                    return launch_coulomb(*c->h_run, nc, c->btiles, c->d_ticket, c->collide_grid, b->stream);
+                    return launch_coulomb(*c->h_run, nc, c->btiles, c->d_ticket, c->collide_grid, 0u, 0, b->stream);
                 }, kCoulombKernels));
             }
         }

@@ -221,7 +221,7 @@ extern "C" ecris_status ecris_coulomb_collide_noalloc(size_t n, const uint32_t* 
         k_na_pack<<<(uint32_t)((n + 255) / 256), 256, 0, s>>>(base, (uint32_t)n, cell, q, vx, vy, vz, ncells);
     e = cudaGetLastError();
     if (e != cudaSuccess) return na_cuda(e, "launch");
-    e = launch_coulomb(R, ncells, tiles, ticket, setup.grid, s);
+    e = launch_coulomb(R, ncells, tiles, ticket, setup.grid, 0u, 0, s);
     if (e != cudaSuccess) return na_cuda(e, "launch_coulomb");
     if (collisions_out) {
         // the call synchronises: read the collision count and the error word

@@ -501,10 +501,14 @@ ecris_status batch_autotune(ecris_batch* b, uint32_t trial_steps, bool cadence, 
 void batch_snapshot_diag(const ecris_batch* b, int32_t run, const TallySnapshot& snap, uint64_t steps,
                          ecris_diag_out* out);
 
-// Coulomb collisions of one run for the current step (after launch_step with
-// bump_step = 0): scan of the cell counts, scatter of the pairing keys, and
-// the per-cell sort / pair / collide kernel, whose last block advances the
-// step counter.
+// Coulomb collisions of one run for the current step, after the step
+// kernel: scan of the cell counts, scatter of the pairing keys, and the
+// per-cell sort / pair / collide kernel, whose last block advances the step
+// counter and clears the leaver list.  leave_blocks extra blocks of the scan
+// kernel (the same count at every launch of a run: kLeaveBlocks for one run,
+// 0 in a batch) run the step's leaver pass if do_leave, in place of
+// launch_leave; else the leavers were finished before, by launch_leave or
+// the batch's pass.
 constexpr int kCoulombKernels = 3;   // kernels per launch_coulomb
 // participants per range of cells of the collision kernel: the first step
 // after a load takes kCellIons; each later step takes kCellCap minus the
@@ -515,7 +519,11 @@ constexpr int kCellIons = 512;
 constexpr int kCellIonsMin = 256, kCellIonsMax = 896;
 constexpr int kCellCap = 1024;       // participants of a range held in shared memory
 cudaError_t launch_coulomb(const RunDev& R, uint32_t ncells, uint32_t ntiles, unsigned int* ticket, int grid,
-                           cudaStream_t s);
+                           uint32_t leave_blocks, int do_leave, cudaStream_t s);
+// the cell-count scan of the collisions, with leave_blocks extra blocks for
+// the leaver pass (step_kernel.cu)
+cudaError_t launch_scan(const RunDev& R, uint32_t ncells, uint32_t nscan, uint32_t leave_blocks, int do_leave,
+                        cudaStream_t s);
 int coulomb_scan_blocks(uint32_t ncells);
 int collide_blocks_per_sm();
 

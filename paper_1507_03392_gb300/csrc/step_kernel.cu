@@ -891,6 +891,163 @@ __global__ void __launch_bounds__(256) k_leave_batch(const RunDev* __restrict__ 
             }
 }
 
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// range b of the collision kernel (stride participants a range) starts at the
+// first cell c with coff[c] >= b stride: cell c starts the ranges b with
+// coff[c - 1] < b stride <= coff[c]
+__device__ __forceinline__ void mark_ranges(const RunDev& R, uint32_t c, uint32_t prev, uint32_t cur,
+                                            uint32_t stride)
+{
+    const uint32_t b0 = c == 0 ? 0u : prev / stride + 1u;
+    for (uint32_t b = b0; b <= cur / stride; ++b) R.cstart[b] = c;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// One-pass exclusive scan of ccount into coff (coff[ncells] = total) with
+// decoupled look-back: each block takes the next scan tile in ticket order,
+// scans its kScanBlock counts, publishes the tile's total, then adds up the
+// totals (or the first inclusive prefix) of the tiles before it.  A status
+// word is epoch << 33 | inclusive << 32 | value; the epoch (launch number,
+// from the ticket) tells this launch's words from stale ones.  A wait that
+// runs out of its bounded spin sets the run's error word.  The kernel also
+// marks where the collision kernel's ranges start.
+//
+// It is the first kernel after the step kernel in a one-run step with
+// Coulomb collisions, and blocks past the nscan scan tiles do that step's
+// leaver pass meanwhile if do_leave (the leavers take no part in the
+// collisions); the collision kernel clears the leaver list at its end.
+// ntile = blocks in all; it must not change between the launches of a run
+// (the tickets' cycle gives the epoch), so a one-run step whose leaver pass
+// ran on its own still launches the extra blocks, with do_leave = 0.
+__global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ RunDev R, uint32_t ncells,
+                                                      uint32_t ntile, uint32_t nscan, int do_leave)
+{
+    __shared__ uint32_t wsum[kScanThreads / 32];
+    __shared__ uint32_t s_tile, s_epoch, s_prefix, s_stride, s_max;
+    pdl_wait();
+    pdl_trigger();   // the scatter's blocks may be scheduled; they wait for this grid
+    if (threadIdx.x == 0) {
+        s_stride = R.crange[0];
+        s_max = 0u;
+        const unsigned long long t = atomicAdd(R.cctr, 1ull);
+        s_tile = (uint32_t)(t % ntile);
+        s_epoch = (uint32_t)(t / ntile) + 1u;
+    }
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= nscan) {   // the last tickets: the leaver pass
+        if (do_leave)
+            leave_run(R, *R.nleave, (tile - nscan) * blockDim.x + threadIdx.x, (ntile - nscan) * blockDim.x);
+        return;
+    }
+    const unsigned long long ep = (unsigned long long)s_epoch << 33;
+    const uint32_t base = tile * kScanBlock + threadIdx.x * kScanPerThread;
+    uint32_t v[kScanPerThread];
+    uint32_t sum = 0;
+    // four counts per load where the group lies inside the mesh
+#pragma unroll
+    for (int j = 0; j < kScanPerThread; j += 4) {
+        const uint32_t idx = base + j;
+        if (idx + 3u < ncells) {
+            const uint4 c4 = *reinterpret_cast<const uint4*>(R.ccount + idx);
+            v[j] = c4.x; v[j + 1] = c4.y; v[j + 2] = c4.z; v[j + 3] = c4.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[j + k] = idx + k < ncells ? R.ccount[idx + k] : 0u;
+        }
+    }
+    uint32_t vmax = 0;
+#pragma unroll
+    for (int j = 0; j < kScanPerThread; ++j) {
+        sum += v[j];
+        vmax = max(vmax, v[j]);
+    }
+    // the largest cell count, for the next step's range size
+    vmax = __reduce_max_sync(0xFFFFFFFFu, vmax);
+    if ((threadIdx.x & 31) == 0 && vmax) atomicMax(&s_max, vmax);
+    const uint32_t stride = s_stride;
+    const uint32_t incl = warp_incl_scan(sum);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0 && s_max) atomicMax(R.crange + 1, s_max);
+    if (warp == 0) {
+        const uint32_t w = lane < kScanThreads / 32 ? wsum[lane] : 0u;
+        const uint32_t wi = warp_incl_scan(w);
+        if (lane < kScanThreads / 32) wsum[lane] = wi - w;
+        // the tile's total: publish it, look back over up to 32 earlier tiles
+        // at a time (lane k reads tile p - k), publish the inclusive prefix
+        const uint32_t agg = __shfl_sync(0xFFFFFFFFu, wi, kScanThreads / 32 - 1);
+        uint32_t prefix = 0;
+        if (tile == 0) {
+            if (lane == 0) st_release(R.cstat, ep | (1ull << 32) | agg);
+        } else {
+            if (lane == 0) st_release(R.cstat + tile, ep | agg);
+            bool ok = true;
+            for (int p = (int)tile - 1; p >= 0; p -= 32) {
+                const int q = p - (int)lane;
+                unsigned long long st = 0;
+                if (q >= 0) {
+                    uint32_t it = 0;
+                    do {
+                        st = ld_acquire(R.cstat + q);
+                    } while ((st >> 33) != (ep >> 33) && ++it < kWaitLimit);
+                    if ((st >> 33) != (ep >> 33)) ok = false;
+                }
+                // sum up to and including the nearest inclusive prefix
+                const uint32_t incl_mask = __ballot_sync(0xFFFFFFFFu, q >= 0 && (st & (1ull << 32)));
+                const uint32_t first = incl_mask ? (uint32_t)(__ffs(incl_mask) - 1) : 31u;
+                uint32_t val = (q >= 0 && lane <= first) ? (uint32_t)st : 0u;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xFFFFFFFFu, val, o);
+                prefix += val;
+                if (incl_mask) break;
+            }
+            if (__any_sync(0xFFFFFFFFu, !ok) && lane == 0) atomicExch(R.err, kErrTimeout);
+            if (lane == 0) st_release(R.cstat + tile, ep | (1ull << 32) | (prefix + agg));
+        }
+        if (lane == 0) s_prefix = prefix;
+    }
+    __syncthreads();
+    uint32_t cur = s_prefix + wsum[warp] + incl - sum;
+#pragma unroll
+    for (int j = 0; j < kScanPerThread; ++j) {
+        const uint32_t idx = base + j;
+        if (idx < ncells) {
+            R.coff[idx] = cur;
+            const uint32_t prev = idx == 0 ? 0u : (j > 0 ? cur - v[j - 1] : cur - R.ccount[idx - 1]);
+            mark_ranges(R, idx, prev, cur, stride);
+            if (idx == ncells - 1) {
+                R.coff[ncells] = cur + v[j];
+                mark_ranges(R, ncells, cur, cur + v[j], stride);
+            }
+        }
+        cur += v[j];
+    }
+}
+
+
 // Fold the packed per-step deposit into the time-summed count and charge
 // grids and clear it.
 __global__ void k_fold(const __grid_constant__ RunDev R, uint32_t ncells,
@@ -1090,6 +1247,13 @@ cudaError_t launch_step(const RunDev& R, uint32_t ntiles, int grid, cudaStream_t
     if ((R.flags & kFVariants) || R.btab) k_step<true><<<grid, kThreads, smem, s>>>(R, ntiles);
     else k_step<false><<<grid, kThreads, smem, s>>>(R, ntiles);
     return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const RunDev& R, uint32_t ncells, uint32_t nscan, uint32_t leave_blocks, int do_leave,
+                        cudaStream_t s)
+{
+    return launch_pdl(k_scan, dim3(nscan + leave_blocks), dim3(kScanThreads), 0, s, R, ncells, nscan + leave_blocks,
+                      nscan, do_leave);
 }
 
 cudaError_t launch_leave(const RunDev& R, unsigned int* ticket, int bump_step, cudaStream_t s)
