@@ -605,7 +605,9 @@ def main():
     value, total_s = replica_throughput(n * args.steps, 1e-3 * sum(step_ms), dist, "cuda")
     total_ms = 1e3 * total_s
     # kernels launched in the timed steps: a graph replay holds the same
-    # kernels the profiled pass launched one by one, step for step
+    # kernels the profiled pass launched one by one, step for step (with
+    # collisions the profiled pass, like the graph, runs the leaver pass inside
+    # the scan kernel)
     nprof_steps = min(args.steps, 200)
     launches = int(round((prof["step_launches"] + prof["coulomb_launches"] + prof["other_launches"])
                          * args.steps / nprof_steps))

@@ -325,9 +325,11 @@ ecris_status ecris_get_state(ecris_ctx* ctx, float* const xyzv[6], uint32_t* met
 typedef struct {
     int64_t step_launches;     /* fused push/MCC/boundary/deposit kernel */
     double step_ms;
-    int64_t coulomb_launches;  /* ion-ion collision kernels (binning, pairing) */
+    int64_t coulomb_launches;  /* ion-ion collision kernels (binning, pairing; one run's leaver
+                                  pass runs inside them when the run has collisions) */
     double coulomb_ms;
-    int64_t other_launches;    /* deposit fold and bookkeeping kernels */
+    int64_t other_launches;    /* leaver pass of runs without collisions, sorts, deposit fold and
+                                  bookkeeping kernels */
     double other_ms;
 } ecris_profile;
 

@@ -894,16 +894,16 @@ ecris_status step_graph(ecris_ctx* ctx, int kind, cudaGraphExec_t* out)
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    // kind 0, the whole step: with collisions the scan kernel also runs the
-    // leaver pass; kind 1, the collision kernels alone (timed steps run the
-    // leaver pass on its own before them)
+    // kind 0, the whole step; kind 1, the collision kernels alone (timed
+    // steps launch the step kernel on its own before them).  With collisions
+    // the scan kernel also runs the leaver pass.
     if (kind == 0) {
         e = launch_step(*ctx->h_run, ctx->ntiles, ctx->step_grid, ctx->stream);
         if (e == cudaSuccess && !coulomb) e = launch_leave(*ctx->h_run, ctx->d_ticket, 1, ctx->stream);
     }
     if (e == cudaSuccess && coulomb)
         e = launch_coulomb(*ctx->h_run, nc, ctx->ntiles, ctx->d_ticket, ctx->collide_grid, (uint32_t)kLeaveBlocks,
-                           kind == 0 ? 1 : 0, ctx->stream);
+                           1, ctx->stream);
     const cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
     CK(e);
     CK(e2);
@@ -1392,9 +1392,8 @@ ecris_status ecris_step(ecris_ctx* ctx, uint32_t nsteps, double dt)
             CK(timed(ctx, kKindStep, [&] {
                 return launch_step(*ctx->h_run, ctx->ntiles, ctx->step_grid, ctx->stream);
             }));
-            CK(timed(ctx, kKindOther, [&] {
-                return launch_leave(*ctx->h_run, ctx->d_ticket, coulomb ? 0 : 1, ctx->stream);
-            }));
+            if (!coulomb)
+                CK(timed(ctx, kKindOther, [&] { return launch_leave(*ctx->h_run, ctx->d_ticket, 1, ctx->stream); }));
             if (coulomb) {
                 cudaGraphExec_t x = nullptr;
                 st = step_graph(ctx, 1, &x);
