@@ -5,7 +5,9 @@
 // Per step, after the fused step kernel has counted the ions that stayed inside
 // per cell (ccount) and published each one's (pid, cell) and (v, Q) record in
 // its tile's participant list:
-//   1. scan      exclusive scan of ccount -> coff (one pass, decoupled look-back);
+//   1. scan      exclusive scan of ccount -> coff (one pass, decoupled look-back;
+//                the kernel lives in step_kernel.cu beside the leaver pass it
+//                can run in extra blocks);
 //   2. scatter   each participant takes slot coff[cell] + (ccount[cell] counted
 //                down by one), which leaves ccount at zero for the next step;
 //                the slot receives key = (pairing hash << 32 | pid), the hash

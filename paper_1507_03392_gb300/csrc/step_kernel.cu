@@ -2,7 +2,8 @@
 // deposition) of the ECRIS model of Mironov et al. (arXiv:1507.03392, Sec.
 // II), the wall and aperture bookkeeping of the particles that left the
 // chamber in the step, the deposit fold and the charge-state census used by
-// the diagnostics.
+// the diagnostics, and the cell-count scan that starts the Coulomb collisions
+// (which, in a one-run step, also runs the leaver pass in extra blocks).
 //
 // Data layout: each run's particles are SoA arrays x, y, z (fixed point), vx,
 // vy, vz, a u32 meta word and a u32 stable id, padded to a multiple of 4.
@@ -11,7 +12,7 @@
 // records read through L1/L2; the rate table is read through L1.  The deposit
 // is one packed 64-bit reduction per run of lanes in the same cell (count in
 // the high word, charge in the low word).  A particle that leaves the chamber
-// is only listed by the step kernel; a second, small kernel does its crossing
+// is only listed by the step kernel; a second, small pass does its crossing
 // geometry (FP64), tallies and re-emission, so the step kernel carries no
 // FP64 code and no per-tile tally traffic.
 #include "ecris_internal.cuh"
