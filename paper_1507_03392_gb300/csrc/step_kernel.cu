@@ -944,8 +944,8 @@ __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long 
 __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ RunDev R, uint32_t ncells,
                                                       uint32_t ntile, uint32_t nscan, int do_leave)
 {
-    __shared__ uint32_t wsum[kScanThreads / 32];
-    __shared__ uint32_t s_tile, s_epoch, s_prefix, s_stride, s_max;
+    __shared__ uint32_t wsum[kScanThreads / 32], wred[kScanThreads / 32];
+    __shared__ uint32_t s_tile, s_epoch, s_agg, s_first, s_bad, s_stride, s_max;
     pdl_wait();
     pdl_trigger();   // the scatter's blocks may be scheduled; they wait for this grid
     if (threadIdx.x == 0) {
@@ -978,6 +978,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ R
             for (int k = 0; k < 4; ++k) v[j + k] = idx + k < ncells ? R.ccount[idx + k] : 0u;
         }
     }
+    // the count of the cell before this thread's first (for its range marks)
+    const uint32_t vprev = base > 0u && base - 1u < ncells ? R.ccount[base - 1u] : 0u;
     uint32_t vmax = 0;
 #pragma unroll
     for (int j = 0; j < kScanPerThread; ++j) {
@@ -997,54 +999,75 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ R
         const uint32_t w = lane < kScanThreads / 32 ? wsum[lane] : 0u;
         const uint32_t wi = warp_incl_scan(w);
         if (lane < kScanThreads / 32) wsum[lane] = wi - w;
-        // the tile's total: publish it, look back over up to 32 earlier tiles
-        // at a time (lane k reads tile p - k), publish the inclusive prefix
+        // the tile's total: publish it (tile 0 as its inclusive prefix)
         const uint32_t agg = __shfl_sync(0xFFFFFFFFu, wi, kScanThreads / 32 - 1);
-        uint32_t prefix = 0;
-        if (tile == 0) {
-            if (lane == 0) st_release(R.cstat, ep | (1ull << 32) | agg);
-        } else {
-            if (lane == 0) st_release(R.cstat + tile, ep | agg);
-            bool ok = true;
-            for (int p = (int)tile - 1; p >= 0; p -= 32) {
-                const int q = p - (int)lane;
-                unsigned long long st = 0;
-                if (q >= 0) {
-                    uint32_t it = 0;
-                    do {
-                        st = ld_acquire(R.cstat + q);
-                    } while ((st >> 33) != (ep >> 33) && ++it < kWaitLimit);
-                    if ((st >> 33) != (ep >> 33)) ok = false;
-                }
-                // sum up to and including the nearest inclusive prefix
-                const uint32_t incl_mask = __ballot_sync(0xFFFFFFFFu, q >= 0 && (st & (1ull << 32)));
-                const uint32_t first = incl_mask ? (uint32_t)(__ffs(incl_mask) - 1) : 31u;
-                uint32_t val = (q >= 0 && lane <= first) ? (uint32_t)st : 0u;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xFFFFFFFFu, val, o);
-                prefix += val;
-                if (incl_mask) break;
-            }
-            if (__any_sync(0xFFFFFFFFu, !ok) && lane == 0) atomicExch(R.err, kErrTimeout);
-            if (lane == 0) st_release(R.cstat + tile, ep | (1ull << 32) | (prefix + agg));
+        if (lane == 0) {
+            st_release(R.cstat + tile, ep | (tile == 0 ? (1ull << 32) : 0ull) | agg);
+            s_agg = agg;
+            s_first = kScanThreads;
+            s_bad = 0u;
         }
-        if (lane == 0) s_prefix = prefix;
     }
     __syncthreads();
-    uint32_t cur = s_prefix + wsum[warp] + incl - sum;
+    // look back over up to kScanThreads earlier tiles a round, thread k reading
+    // tile p - k, and add up the totals down to the nearest inclusive prefix:
+    // every tile's total is published before its look-back starts, so one
+    // round reaches tile 0 when there are at most kScanThreads tiles
+    uint32_t prefix = 0;
+    if (tile > 0) {
+        for (int p = (int)tile - 1; p >= 0; p -= kScanThreads) {
+            const int q = p - (int)threadIdx.x;
+            unsigned long long st = 0;
+            if (q >= 0) {
+                uint32_t it = 0;
+                do {
+                    st = ld_acquire(R.cstat + q);
+                } while ((st >> 33) != (ep >> 33) && ++it < kWaitLimit);
+                if ((st >> 33) != (ep >> 33)) s_bad = 1u;
+                if (st & (1ull << 32)) atomicMin(&s_first, threadIdx.x);
+            }
+            __syncthreads();
+            const uint32_t first = s_first;
+            const uint32_t val = __reduce_add_sync(0xFFFFFFFFu, (q >= 0 && threadIdx.x <= first) ? (uint32_t)st : 0u);
+            if (lane == 0) wred[warp] = val;
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kScanThreads / 32; ++k) prefix += wred[k];
+            if (first < (uint32_t)kScanThreads) break;
+            __syncthreads();   // every thread has read wred before the next round writes it
+        }
+        if (threadIdx.x == 0) {
+            if (s_bad) atomicExch(R.err, kErrTimeout);
+            st_release(R.cstat + tile, ep | (1ull << 32) | (prefix + s_agg));
+        }
+    }
+    uint32_t o[kScanPerThread];
+    uint32_t cur = prefix + wsum[warp] + incl - sum;
+#pragma unroll
+    for (int j = 0; j < kScanPerThread; ++j) {
+        o[j] = cur;
+        cur += v[j];
+    }
+    if (base + kScanPerThread <= ncells) {
+#pragma unroll
+        for (int j = 0; j < kScanPerThread; j += 4)
+            *reinterpret_cast<uint4*>(R.coff + base + j) = make_uint4(o[j], o[j + 1], o[j + 2], o[j + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kScanPerThread; ++j)
+            if (base + j < ncells) R.coff[base + j] = o[j];
+    }
+    // the collision kernel's ranges that start at each cell
 #pragma unroll
     for (int j = 0; j < kScanPerThread; ++j) {
         const uint32_t idx = base + j;
         if (idx < ncells) {
-            R.coff[idx] = cur;
-            const uint32_t prev = idx == 0 ? 0u : (j > 0 ? cur - v[j - 1] : cur - R.ccount[idx - 1]);
-            mark_ranges(R, idx, prev, cur, stride);
+            mark_ranges(R, idx, j > 0 ? o[j - 1] : o[0] - vprev, o[j], stride);
             if (idx == ncells - 1) {
-                R.coff[ncells] = cur + v[j];
-                mark_ranges(R, ncells, cur, cur + v[j], stride);
+                R.coff[ncells] = o[j] + v[j];
+                mark_ranges(R, ncells, o[j], o[j] + v[j], stride);
             }
         }
-        cur += v[j];
     }
 }
 
