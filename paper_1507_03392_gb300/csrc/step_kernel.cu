@@ -905,12 +905,13 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
 
 // range b of the collision kernel (stride participants a range) starts at the
 // first cell c with coff[c] >= b stride: cell c starts the ranges b with
-// coff[c - 1] < b stride <= coff[c]
+// coff[c - 1] < b stride <= coff[c], and each of them records coff[c], its
+// first participant
 __device__ __forceinline__ void mark_ranges(const RunDev& R, uint32_t c, uint32_t prev, uint32_t cur,
                                             uint32_t stride)
 {
     const uint32_t b0 = c == 0 ? 0u : prev / stride + 1u;
-    for (uint32_t b = b0; b <= cur / stride; ++b) R.cstart[b] = c;
+    for (uint32_t b = b0; b <= cur / stride; ++b) R.cstart[b] = cur;
 }
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p)
