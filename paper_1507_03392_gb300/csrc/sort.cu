@@ -29,13 +29,16 @@ constexpr int kSortThreads = 256;
 constexpr int kSortPerThread = 8;
 constexpr int kSortScanBlock = kSortThreads * kSortPerThread;
 
-__device__ __forceinline__ uint32_t sort_key(const RunDev& R, uint32_t i)
+__device__ __forceinline__ uint32_t key_of(const RunDev& R, int32_t x, int32_t y, int32_t z, uint32_t m)
 {
-    const uint32_t m = R.meta[i];
     const uint32_t nc = R.ncells;
     if (m & (kStFrozen | kStPad)) return 2u * nc;
-    const uint32_t cell = ngp_cell(R, R.x[i], R.y[i], R.z[i]);
-    return ((m & kQMask) ? 0u : nc) + cell;
+    return ((m & kQMask) ? 0u : nc) + ngp_cell(R, x, y, z);
+}
+
+__device__ __forceinline__ uint32_t sort_key(const RunDev& R, uint32_t i)
+{
+    return key_of(R, R.x[i], R.y[i], R.z[i], R.meta[i]);
 }
 
 // lanes with equal keys add once per group (input already in order makes
@@ -145,9 +148,25 @@ __global__ void k_sort_move(const __grid_constant__ RunDev R, uint32_t cap, Part
     const uint32_t lane = threadIdx.x & 31;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < end; i += stride) {
         const bool in = i < cap;
-        const uint32_t key = in ? sort_key(R, i) : 0xFFFFFFFFu;
+        // the particle's words and its bin's offset are loaded before the
+        // atomic below, so their round trips overlap instead of following it
+        int32_t x = 0, y = 0, z = 0;
+        float vx = 0.0f, vy = 0.0f, vz = 0.0f;
+        uint32_t meta = 0u, id = 0u, key = 0xFFFFFFFFu;
+        if (in) {
+            x = R.x[i];
+            y = R.y[i];
+            z = R.z[i];
+            meta = R.meta[i];
+            vx = R.vx[i];
+            vy = R.vy[i];
+            vz = R.vz[i];
+            id = R.id[i];
+            key = key_of(R, x, y, z, meta);
+        }
         const uint32_t act = __ballot_sync(0xFFFFFFFFu, in);
         if (!in) continue;
+        const uint32_t base = off[key];
         // one atomic per group of lanes with the same key; lanes take
         // consecutive places below the group's previous count
         const uint32_t grp = __match_any_sync(act, key);
@@ -156,19 +175,19 @@ __global__ void k_sort_move(const __grid_constant__ RunDev R, uint32_t cap, Part
         if (lane == leader) top = atomicSub(hist + key, (uint32_t)__popc(grp));
         top = __shfl_sync(grp, top, leader);
         const uint32_t rank = (uint32_t)__popc(grp & ((1u << lane) - 1u));
-        const uint32_t d = off[key] + top - 1u - rank;
+        const uint32_t d = base + top - 1u - rank;
         if (kRecords) {
-            aos[2 * d] = make_uint4((uint32_t)R.x[i], (uint32_t)R.y[i], (uint32_t)R.z[i], __float_as_uint(R.vx[i]));
-            aos[2 * d + 1] = make_uint4(__float_as_uint(R.vy[i]), __float_as_uint(R.vz[i]), R.meta[i], R.id[i]);
+            aos[2 * d] = make_uint4((uint32_t)x, (uint32_t)y, (uint32_t)z, __float_as_uint(vx));
+            aos[2 * d + 1] = make_uint4(__float_as_uint(vy), __float_as_uint(vz), meta, id);
         } else {
-            dst.x[d] = R.x[i];
-            dst.y[d] = R.y[i];
-            dst.z[d] = R.z[i];
-            dst.vx[d] = R.vx[i];
-            dst.vy[d] = R.vy[i];
-            dst.vz[d] = R.vz[i];
-            dst.meta[d] = R.meta[i];
-            dst.id[d] = R.id[i];
+            dst.x[d] = x;
+            dst.y[d] = y;
+            dst.z[d] = z;
+            dst.vx[d] = vx;
+            dst.vy[d] = vy;
+            dst.vz[d] = vz;
+            dst.meta[d] = meta;
+            dst.id[d] = id;
         }
     }
 }
