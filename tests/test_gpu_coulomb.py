@@ -70,6 +70,25 @@ def test_coulomb_only_lockstep_all_sort_paths(E, sizes, seed):
     run.close()
 
 
+def test_coulomb_lockstep_on_a_mesh_of_many_scan_tiles(E):
+    # 96 x 96 x 192 cells: the per-cell count scan runs 864 tiles of 2048
+    # cells, so a tile's look-back over the totals before it (256 tiles a
+    # round) may take several rounds; ions sit in cells spread over the whole
+    # mesh, one of them above the shared-memory capacity of a range
+    rp = I.RunParams(nx=96, ny=96, nz=192, flags=I.F_COULOMB, weight=5e7, dt=1e-8, seed=11)
+    rng = np.random.default_rng(11)
+    sizes = [int(m) for m in rng.integers(1, 40, 500)] + [1100]
+    st = cells_state(rp, sizes, 11)
+    run = E.Run(rp)
+    run.load(st)
+    t, orc = P.lockstep(run, rp, st, 3, vel_rel=5e-5)
+    assert t["q"] == 0 and t["events"] == 0 and t["pos"] == 0 and t["vel"] == 0, t
+    d = run.diag()
+    assert d["coulomb_collisions"] == orc.tally.coulomb_pairs
+    assert d["coulomb_collisions"] > 3000
+    run.close()
+
+
 def test_coulomb_conserves_momentum_and_energy_per_cell(E):
     rp = I.RunParams(nx=8, ny=8, nz=16, flags=I.F_COULOMB, weight=2e8, dt=2e-8, seed=5)
     sizes = [2, 5, 64, 300, 2000]
