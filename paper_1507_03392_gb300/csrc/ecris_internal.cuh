@@ -157,7 +157,7 @@ struct alignas(16) RunDev {
     uint32_t *coff;              // exclusive scan of ccount, Nc + 1 entries
     unsigned long long *cstat;   // scan tile status words (decoupled look-back), one per scan tile
     unsigned long long *cctr;    // scan tile tickets handed out so far
-    uint32_t *cstart;            // first participant of each range (collision kernel; a cell's whole)
+    uint32_t *cstart;            // first participant of each collision range (a range holds whole cells)
     uint32_t *crange;            // [0] participants per range this step, [1] largest cell count seen by
                                  // this step's scan (sets the next step's range size)
     unsigned long long *ckeys;   // (pairing hash << 32 | pid) per participant, grouped by cell
